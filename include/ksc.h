@@ -1,0 +1,188 @@
+/*
+ * ksc.h -- C ABI of the GB300 (sm_103a) library that computes certified dual
+ * bounds for the perspective relaxation of the k-sparse, box-constrained,
+ * ridge-regularised GLM (Liu et al., "Scalable First-order Method for
+ * Certifying Optimal k-Sparse GLMs", arXiv 2502.09502).
+ *
+ * The problem (Sec. 1, Eq. (1)):
+ *     min_b  F(X b) + lambda2 ||b||^2   s.t.  ||b||_inf <= M,  ||b||_0 <= k,
+ * with F the least-squares loss ||u - y||^2 or the logistic loss
+ * sum_i log(1 + exp(-y_i u_i)), y_i in {-1, +1} (App. D.1).  A branch-and-bound
+ * node fixes some z_j to 0 (S0: b_j = 0) and some to 1 (S1: b_j free in the box,
+ * outside the cardinality budget), leaving k' = k - |S1| (App. B.3).
+ *
+ * The library solves the node's perspective relaxation P_conv (Sec. 2, Eq. (4))
+ * in the composite form min_b F(X b) + 2 lambda2 g(b) (Sec. 3, Eq. (5)-(6)) by
+ * restarted FISTA (Algorithm 3) with the exact prox of g (Algorithm 1 + 4 via
+ * the Moreau identity of Sec. 3.3; g itself by Algorithm 2), and certifies the
+ * weak-duality bound  D = -F*(-zeta) - G*(X^T zeta),  zeta = -grad F(X b^),
+ * G = 2 lambda2 g, G* from Lemma 3.1 (Sec. 3.4).  The certificate is evaluated
+ * in FP64 with a rigorous rounding-error margin subtracted, so D never exceeds
+ * P_conv(node) <= P_MIP(node) because of rounding.
+ *
+ * Conventions for every call:
+ *   - Return value: a ksc_status; no C++ exception crosses the ABI.  On an error
+ *     the message is available from ksc_last_error() (thread-local).
+ *   - Ownership: the caller owns every host array and result buffer it passes;
+ *     the library owns the device copies, workspaces and resident iterates it
+ *     allocates, and frees them in the matching destroy call.
+ *   - Layout: X is row-major n x p with leading dimension ldx >= p (elements);
+ *     vectors are dense, 0-based, in the original coordinate order.
+ *   - Streams: `cuda_stream` is a cudaStream_t passed as void* (NULL = the
+ *     legacy default stream); all device work of a call is ordered on it.
+ *     Calls are blocking: they return once results are in host memory.
+ *   - Devices: all device work runs on the device that is current when the
+ *     problem (or server) is created.
+ */
+#ifndef KSC_H
+#define KSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KSC_OK = 0,
+  KSC_ERR_INVALID_ARG = 1,      /* a null pointer, size or parameter out of range   */
+  KSC_ERR_OOM = 2,              /* a device allocation failed                       */
+  KSC_ERR_ADMISSION = 3,        /* a request does not fit the server's HBM budget   */
+  KSC_ERR_INFEASIBLE_NODE = 4,  /* |S1| > k or S0 and S1 intersect                  */
+  KSC_NOT_CONVERGED = 5,        /* max_iter reached; dual_bound is still certified  */
+  KSC_ERR_TIMEOUT = 6,          /* a bounded wait expired (device or host side)     */
+  KSC_ERR_CUDA = 7,             /* a CUDA runtime error; see ksc_last_error()       */
+  KSC_ERR_UNIMPLEMENTED = 8     /* the requested combination is not built           */
+} ksc_status;
+
+typedef enum {
+  KSC_LOSS_LSQ = 0,             /* F(u) = ||u - y||^2                     (App. D.1) */
+  KSC_LOSS_LOGISTIC = 1         /* F(u) = sum log(1 + exp(-y_i u_i)), y = +-1        */
+} ksc_loss;
+
+typedef enum {
+  KSC_F64 = 0,                  /* X in double; every iteration step in FP64        */
+  KSC_F32 = 1,                  /* X in float; iterations in FP32, FP64 reductions  */
+  KSC_BF16 = 2                  /* X in bfloat16 bits; the problem is the stored X  */
+} ksc_dtype;
+
+/* Node flags (ksc_node.flags): the ablations of Fig. 3. */
+#define KSC_FLAG_RESTART_OFF  0x1u   /* plain FISTA: never reset the momentum       */
+#define KSC_FLAG_MOMENTUM_OFF 0x2u   /* proximal gradient (ISTA): no momentum       */
+
+typedef struct ksc_problem ksc_problem;
+typedef struct ksc_server ksc_server;
+
+/* Problem data (Sec. 1): X (n x p, row-major), y (n), loss. */
+typedef struct {
+  int64_t n, p;
+  ksc_dtype x_dtype;
+  const void* X;        /* x_on_device = 0: host pointer, copied to the device.
+                           x_on_device = 1: device pointer, BORROWED -- it must stay
+                           valid and unchanged until ksc_problem_destroy.          */
+  int64_t ldx;          /* leading dimension in elements, >= p; 0 means p         */
+  const double* y;      /* host pointer, length n, always copied; logistic: +-1    */
+  ksc_loss loss;
+  int32_t x_on_device;
+  double lipschitz;     /* > 0: the step constant L of Algorithm 3 to use.
+                           <= 0: L = c_f * lambda_max(X^T X) * 1.01, c_f = 2 (least
+                           squares) or 1/4 (logistic), lambda_max by power iteration */
+} ksc_problem_desc;
+
+/* Create a problem: copies (or borrows) X, copies y, computes L on the device.
+ * Errors: KSC_ERR_INVALID_ARG (null pointers, n or p < 1, ldx < p, unknown enum,
+ * logistic labels not +-1), KSC_ERR_OOM, KSC_ERR_CUDA.  *out is NULL on error. */
+ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cuda_stream,
+                              ksc_problem** out);
+/* Free every device buffer the problem owns.  NULL is accepted. */
+ksc_status ksc_problem_destroy(ksc_problem* problem);
+/* Device bytes the problem holds now (X copy if owned, y, workspaces). */
+size_t ksc_problem_bytes(const ksc_problem* problem);
+/* L (Algorithm 3's step constant) and the number of power iterations used. */
+ksc_status ksc_problem_info(const ksc_problem* problem, double* lipschitz,
+                            int32_t* power_iters);
+
+/* One branch-and-bound node (App. B.3) with its parameters (Sec. 1, Sec. 4.2). */
+typedef struct {
+  double lambda2;            /* > 0                                                  */
+  double M;                  /* > 0, box |b_j| <= M                                  */
+  int32_t k;                 /* >= 0 cardinality budget                              */
+  const int32_t* fixed_zero; /* S0 indices (host), may be NULL when n_zero = 0       */
+  int32_t n_zero;
+  const int32_t* fixed_one;  /* S1 indices (host), may be NULL when n_one = 0        */
+  int32_t n_one;
+  const double* warm_beta;   /* host, length p, or NULL for 0.  S0 entries are set to
+                                0 and all entries clipped to [-M, M] before use      */
+  double incumbent;          /* +inf: none.  Otherwise the early-termination rules of
+                                Sec. 4.3: stop when the certified bound exceeds it
+                                (pruned) or the primal value falls below it          */
+  double rel_gap_tol;        /* (primal - dual)/|primal| target, e.g. 1e-6 (Sec. 4.2) */
+  int32_t max_iter;          /* > 0 */
+  uint32_t flags;            /* KSC_FLAG_*                                           */
+} ksc_node;
+
+typedef struct {
+  double* beta;        /* caller-owned host array, length p, or NULL: final iterate   */
+  double* z;           /* caller-owned host array, length p, or NULL: relaxed z that
+                          attains g(beta) (from the proof of Thm 3.6)                 */
+  double primal;       /* F(X b) + 2 lambda2 g_node(b), FP64 (upper bound on P_conv)  */
+  double dual_bound;   /* certified FP64 lower bound on P_conv(node) <= P_MIP(node)   */
+  double rel_gap;      /* (primal - dual_bound) / max(|primal|, 1e-300)               */
+  int32_t iters;       /* FISTA steps taken                                           */
+  int32_t restarts;    /* momentum resets (Algorithm 3, line 11)                      */
+  int32_t pruned;      /* 1 if dual_bound > incumbent                                 */
+  ksc_status status;   /* KSC_OK (gap met, or an incumbent rule fired),
+                          KSC_NOT_CONVERGED, KSC_ERR_INFEASIBLE_NODE                  */
+} ksc_result;
+
+/* Solve one node to its gap target and certify the bound (blocking).
+ * Infeasible node (|S1| > k or S0 and S1 overlap): result->status and the return
+ * value are KSC_ERR_INFEASIBLE_NODE, dual_bound = +inf (the node can be pruned). */
+ksc_status ksc_solve_node(ksc_problem* problem, const ksc_node* node, ksc_result* result,
+                          void* cuda_stream);
+
+/* Solve `count` nodes of one problem together (blocking); result[i] belongs to
+ * node[i].  Each result equals what ksc_solve_node returns for that node, within
+ * the stated tolerance.  Returns the first non-OK per-node status, else KSC_OK. */
+ksc_status ksc_solve_batch(ksc_problem* problem, const ksc_node* nodes, int32_t count,
+                           ksc_result* results, void* cuda_stream);
+
+/* ---- primitives (host pointers, FP64, one GPU launch each) -------------- */
+
+/* beta = prox_{rho^-1 g}(w) (Moreau identity, Sec. 3.3; Alg. 1 + 4), with the
+ * cardinality budget k and box M.  top_out (optional, length min(k, p)) receives
+ * the indices of the k largest |w| in descending order, ties by ascending index --
+ * the set J of Lemma 3.3 in the order of the sort of Alg. 1. */
+ksc_status ksc_prox_g(const double* w, int64_t p, int32_t k, double M, double rho,
+                      double* beta_out, int32_t* top_out);
+/* g(beta) by Algorithm 2 (+inf outside dom g: |b_j| > M or sum|b| > kM beyond a
+ * 1e-12 relative slack); z_out (optional, length p) receives the relaxed z. */
+ksc_status ksc_g_value(const double* beta, int64_t p, int32_t k, double M, double* g_out,
+                       double* z_out);
+/* g*(a) = TopSum_k(H_M(a)) (Lemma 3.1). */
+ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* out);
+
+/* ---- profiling ------------------------------------------------------------ */
+
+/* Kernel ids for ksc_problem_kernel_time. */
+#define KSC_KERNEL_GRADIENT 0   /* X^T grad F(u) pass (one per FISTA step)           */
+#define KSC_KERNEL_PROX     1   /* segmented prox + g + dual TopSum (one per step)   */
+#define KSC_KERNEL_FORWARD  2   /* X b pass + restart/gap step (one per step)        */
+/* Enable (1) or disable (0) CUDA-event timing of each kernel launch of the
+ * problem's solves; accumulated totals are read with ksc_problem_kernel_time. */
+ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);
+/* Launch count and summed device milliseconds of one kernel since the last reset;
+ * reset != 0 clears the counters after reading. */
+ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
+                                   double* total_ms, int32_t reset);
+
+/* Thread-local text of the last error of a call made on this thread. */
+const char* ksc_last_error(void);
+/* Library version string. */
+const char* ksc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,567 @@
+// k_matvec.cu -- the two HBM-bound passes over X of a FISTA step, and their
+// FP64 twins for the certificate.
+//
+//  gradient pass  grad = X^T grad F(u_gamma)   (Algorithm 3, line 7)
+//      prologue: u_gamma = (1+c) u^t - c u^{t-1} (linearity of X, no extra pass),
+//      r = grad F(u_gamma), and -F*(-zeta_gamma) with zeta_gamma = -r (Sec. 3.4).
+//      Tiles: 256 threads x (16-byte vector of columns) by 256 rows; each CTA
+//      writes column partials, the last CTA of a column strip reduces them in a
+//      fixed order (deterministic), the last strip reduces the dual partials.
+//  forward pass   u^{t+1} = X beta^{t+1}       (Algorithm 3, line 10)
+//      sparse (nnz of beta^{t+1} <= cap): one warp per row gathers only the
+//      nonzero columns; dense: beta staged in shared memory, 4 rows per warp.
+//      Epilogue: F(u^{t+1}) in FP64; the last CTA runs the fused restart /
+//      momentum / gap step (Algorithm 3, line 11; Sec. 4.2 stopping rule).
+#include <type_traits>
+
+#include "ksc_common.cuh"
+#include "ksc_launch.h"
+#include "ksc_state.cuh"
+
+namespace ksc {
+
+// ----------------------------------------------------------- vector loads
+
+template <typename TX> struct Vec;
+template <> struct Vec<float> {
+  static constexpr int N = 4;
+  template <typename A>
+  __device__ __forceinline__ static void load(const float* p, A (&v)[4]) {
+    float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = (A)t.x; v[1] = (A)t.y; v[2] = (A)t.z; v[3] = (A)t.w;
+  }
+};
+template <> struct Vec<double> {
+  static constexpr int N = 2;
+  template <typename A>
+  __device__ __forceinline__ static void load(const double* p, A (&v)[2]) {
+    double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    v[0] = (A)t.x; v[1] = (A)t.y;
+  }
+};
+template <> struct Vec<__nv_bfloat16> {
+  static constexpr int N = 8;
+  template <typename A>
+  __device__ __forceinline__ static void load(const __nv_bfloat16* p, A (&v)[8]) {
+    uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      v[2 * k] = (A)__uint_as_float(w[k] << 16);
+      v[2 * k + 1] = (A)__uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+};
+
+template <typename A> __device__ __forceinline__ A xval(float x) { return (A)x; }
+template <typename A> __device__ __forceinline__ A xval(double x) { return (A)x; }
+template <typename A> __device__ __forceinline__ A xval(__nv_bfloat16 x) { return (A)__bfloat162float(x); }
+
+// compensated (Kahan) or plain accumulation
+template <bool KAHAN, typename A>
+__device__ __forceinline__ void acc_add(A& s, A& c, A v) {
+  if (KAHAN) {
+    const A y = v - c;
+    const A t = s + y;
+    c = (t - s) - y;
+    s = t;
+  } else {
+    s += v;
+  }
+}
+
+__device__ __forceinline__ double sigmoid(double t) {
+  return t >= 0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
+}
+// binary entropy in nats, 0 log 0 = 0
+__device__ __forceinline__ double binent(double q) {
+  double h = 0.0;
+  if (q > 0.0) h -= q * log(q);
+  if (q < 1.0) h -= (1.0 - q) * log1p(-q);
+  return h;
+}
+
+enum GradMode : int { kGStep = 0, kGRaw = 1, kGCert = 2, kGColsq = 3 };
+enum FwdMode : int { kFStep = 0, kFRaw = 1, kFInit = 2, kFCert = 3 };
+
+// ----------------------------------------------------------- gradient pass
+
+template <typename TX, typename T, int MODE, bool VEC>
+__global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
+  constexpr bool FP64ACC = (MODE == kGCert || MODE == kGColsq || std::is_same<T, double>::value);
+  using A = typename std::conditional<FP64ACC, double, float>::type;
+  constexpr bool KAHAN = !FP64ACC;
+  constexpr int CPT = Vec<TX>::N;
+  NodeDev* nd = d.nd;
+  int cur = 0, prev = 0;
+  double c = 0.0;
+  if (MODE == kGStep) {
+    if (nd->done) return;
+    const int t = nd->iter;
+    cur = t % 3;
+    prev = (t + 2) % 3;
+    c = nd->c;
+  }
+  __shared__ A rs[kGradRows];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int ct = blockIdx.x, rb = blockIdx.y;
+  const int n = d.n, p = d.p;
+  const int r0 = rb * kGradRows;
+  const int rn = min(kGradRows, n - r0);
+
+  // prologue: residual of the rows of this CTA
+  double nc = 0.0;
+  for (int i = threadIdx.x; i < rn; i += kGradThreads) {
+    double r = 0.0;
+    if (MODE == kGStep) {
+      const T* uc = (const T*)d.u + (size_t)cur * n;
+      const T* up = (const T*)d.u + (size_t)prev * n;
+      const double ug = (1.0 + c) * to_d(uc[r0 + i]) - c * to_d(up[r0 + i]);
+      const double yi = d.y[r0 + i];
+      if (d.loss == kLossLsq) {
+        r = 2.0 * (ug - yi);
+        const double z = -r;
+        nc += yi * z - 0.25 * z * z;
+      } else {
+        const double s = sigmoid(-yi * ug);
+        r = -yi * s;
+        nc += binent(s);
+      }
+    } else if (MODE == kGRaw) {
+      r = to_d(((const T*)d.u)[r0 + i]);
+    } else if (MODE == kGCert) {
+      r = d.zeta[r0 + i];
+    }
+    rs[i] = (A)r;
+  }
+  if (MODE == kGStep && ct == 0) {
+    nc = block_sum<double, kGradThreads>(nc, red);
+    if (threadIdx.x == 0) d.ncpart[rb] = nc;
+  }
+  __syncthreads();
+
+  // main loop: CPT consecutive columns per thread, rows streamed 4 at a time
+  const int col0 = ct * (kGradThreads * CPT) + threadIdx.x * CPT;
+  A acc[CPT], cmp[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) { acc[k] = A(0); cmp[k] = A(0); }
+  if (col0 < p) {
+    const TX* xp = (const TX*)d.X + (size_t)r0 * d.ldx + col0;
+    if (VEC && col0 + CPT <= p) {
+      int i = 0;
+      for (; i + 4 <= rn; i += 4) {
+        A xv[4][CPT];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Vec<TX>::load(xp + (size_t)(i + r) * d.ldx, xv[r]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const A rr = rs[i + r];
+#pragma unroll
+          for (int k = 0; k < CPT; ++k)
+            acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? xv[r][k] * xv[r][k] : xv[r][k] * rr);
+        }
+      }
+      for (; i < rn; ++i) {
+        A xv[CPT];
+        Vec<TX>::load(xp + (size_t)i * d.ldx, xv);
+        const A rr = rs[i];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+          acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? xv[k] * xv[k] : xv[k] * rr);
+      }
+    } else {
+      for (int i = 0; i < rn; ++i) {
+        const A rr = rs[i];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+          if (col0 + k < p) {
+            const A x = xval<A>(xp[(size_t)i * d.ldx + k]);
+            acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? x * x : x * rr);
+          }
+        }
+      }
+    }
+  }
+  A* ws = (A*)d.ws;
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    if (col0 + k < p) ws[(size_t)rb * p + col0 + k] = acc[k] - cmp[k];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[ct], 1) == (int)gridDim.y - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA of this column strip: fixed-order reduction over the row blocks
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int col = col0 + k;
+    if (col < p) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.y; ++b) s += (double)__ldcg(&ws[(size_t)b * p + col]);
+      if (MODE == kGStep || MODE == kGRaw) ((T*)d.grad)[col] = (T)s;
+      else if (MODE == kGCert) d.a64[col] = s;
+      else {
+        const double u = 1.1102230246251565e-16;
+        ((double*)d.colnorm)[col] = sqrt(s * (1.0 + 2.0 * (n + 4) * u)) * (1.0 + 4.0 * u);
+      }
+    }
+  }
+  if (threadIdx.x == 0) d.cnt[ct] = 0;
+  if (MODE == kGStep) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[gridDim.x], 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      double s = 0.0;
+      for (int b = threadIdx.x; b < (int)gridDim.y; b += kGradThreads) s += __ldcg(&d.ncpart[b]);
+      s = block_sum<double, kGradThreads>(s, red);
+      if (threadIdx.x == 0) {
+        nd->negconj = s;
+        d.cnt[gridDim.x] = 0;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------- step logic
+
+// Algorithm 3 line 10-11 plus the gap test of Sec. 4.2 and the incumbent rules
+// of Sec. 4.3 (on the in-loop bound; the host confirms with the certificate).
+__device__ void step_logic(NodeDev* nd, double f) {
+  const double Lnext = f + 2.0 * nd->lambda2 * nd->g_next;
+  const double D = nd->negconj - 2.0 * nd->lambda2 * nd->gstar;
+  nd->last_primal = Lnext;
+  nd->last_dual = D;
+  if (nd->restart_on && Lnext >= nd->Lcur) {
+    nd->phi = 1.0;
+    nd->restarts += 1;
+  } else {
+    nd->phi += 1.0;
+  }
+  nd->Lcur = Lnext;
+  nd->best_primal = fmin(nd->best_primal, Lnext);
+  nd->best_dual = fmax(nd->best_dual, D);
+  nd->gap = (nd->best_primal - nd->best_dual) / fmax(fabs(nd->best_primal), 1e-300);
+  const int t = nd->iter + 1;
+  nd->iter = t;
+  int done = kRunning;
+  if (isfinite(nd->incumbent)) {
+    if (nd->best_dual > nd->incumbent) done = kDonePruned;
+    else if (Lnext < nd->incumbent) done = kDonePrimal;
+  }
+  if (done == kRunning && nd->gap <= nd->tol_loop) done = kDoneGap;
+  if (done == kRunning && t - 1 >= nd->max_iter) done = kDoneMaxIter;
+  nd->done = done;
+  nd->c = nd->momentum_on ? nd->phi / (nd->phi + 3.0) : 0.0;
+}
+
+// ----------------------------------------------------------- forward pass
+
+template <typename TX, typename T, int MODE, bool VEC>
+__global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
+  constexpr bool FP64ACC = (MODE == kFCert || std::is_same<T, double>::value);
+  using A = typename std::conditional<FP64ACC, double, float>::type;
+  constexpr bool KAHAN = !FP64ACC;
+  constexpr int CPT = Vec<TX>::N;
+  NodeDev* nd = d.nd;
+  const int n = d.n, p = d.p;
+  const T* bsrc;
+  int out_slot = 0;
+  bool sparse = false;
+  int nnz = 0;
+  if (MODE == kFStep) {
+    if (nd->done) return;
+    out_slot = (nd->iter + 1) % 3;
+    bsrc = (const T*)d.beta + (size_t)out_slot * p;
+    nnz = nd->nnz;
+    sparse = nnz <= d.nnz_cap;
+  } else if (MODE == kFCert) {
+    bsrc = (const T*)d.beta + (size_t)(nd->iter % 3) * p;
+    nnz = nd->nnz;
+    sparse = nnz <= d.nnz_cap;
+  } else if (MODE == kFInit) {
+    bsrc = (const T*)d.beta + (size_t)1 * p;
+  } else {
+    bsrc = (const T*)d.pow_v;
+  }
+  __shared__ T bs[kFwdChunk];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row0 = blockIdx.x * kFwdRows + warp * 4;
+  double dot[4] = {0.0, 0.0, 0.0, 0.0};
+  if (sparse) {
+    const int* idx = d.nnz_idx;
+    const T* val = (const T*)d.nnz_val;
+    const TX* X = (const TX*)d.X;
+    for (int e = lane; e < nnz; e += 32) {
+      const int j = idx[e];
+      const double v = to_d(val[e]);
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (row0 + r < n) dot[r] += xval<double>(X[(size_t)(row0 + r) * d.ldx + j]) * v;
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dot[r] = warp_sum(dot[r]);
+  } else {
+    A acc[4], cmp[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) { acc[r] = A(0); cmp[r] = A(0); }
+    for (int c0 = 0; c0 < p; c0 += kFwdChunk) {
+      const int cw = min(kFwdChunk, p - c0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < cw; j += kFwdThreads) bs[j] = bsrc[c0 + j];
+      __syncthreads();
+      for (int cc = lane * CPT; cc < cw; cc += 32 * CPT) {
+        A bv[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) bv[k] = (cc + k < cw) ? (A)to_d(bs[cc + k]) : A(0);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int row = row0 + r;
+          if (row < n) {
+            const TX* xp = (const TX*)d.X + (size_t)row * d.ldx + c0 + cc;
+            A xv[CPT];
+            if (VEC && cc + CPT <= cw) {
+              Vec<TX>::load(xp, xv);
+            } else {
+#pragma unroll
+              for (int k = 0; k < CPT; ++k) xv[k] = (cc + k < cw) ? xval<A>(xp[k]) : A(0);
+            }
+#pragma unroll
+            for (int k = 0; k < CPT; ++k) acc_add<KAHAN>(acc[r], cmp[r], xv[k] * bv[k]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) dot[r] = warp_sum((double)acc[r] - (double)cmp[r]);
+  }
+
+  // epilogue (lane 0 of each warp owns its 4 rows)
+  double f_loc = 0.0, nc_loc = 0.0, mg_loc = 0.0, zsq_loc = 0.0;
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int row = row0 + r;
+      if (row >= n) continue;
+      const double u = dot[r];
+      if (MODE == kFRaw) {
+        ((T*)d.u)[row] = (T)u;
+        continue;
+      }
+      const double yi = d.y[row];
+      if (MODE == kFStep) ((T*)d.u)[(size_t)out_slot * n + row] = (T)u;
+      if (MODE == kFInit) {
+        ((T*)d.u)[row] = (T)u;
+        ((T*)d.u)[(size_t)n + row] = (T)u;
+      }
+      if (d.loss == kLossLsq) {
+        const double res = u - yi;
+        f_loc += res * res;
+        if (MODE == kFCert) {
+          const double z = -2.0 * res;          // zeta = -grad F(u)
+          d.u64[row] = u;
+          d.zeta[row] = z;
+          nc_loc += yi * z - 0.25 * z * z;      // -F*(-zeta), App. D.1
+          mg_loc += fabs(yi * z) + 0.25 * z * z;
+          zsq_loc += z * z;
+        }
+      } else {
+        const double t = -yi * u;
+        f_loc += t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
+        if (MODE == kFCert) {
+          const double s = sigmoid(t);
+          const double z = yi * s;              // zeta = -grad F(u), q = zeta/y = s
+          d.u64[row] = u;
+          d.zeta[row] = z;
+          const double h = binent(s);
+          nc_loc += h;
+          // |term| plus the rounding of one entropy term in units of u (log() within
+          // 2 ulp, 1-q, two products): the margin is (n+8) u * sum(mg), see below
+          const double ql = s > 0.0 ? fabs(s * log(s)) : 0.0;
+          const double pl = s < 1.0 ? fabs((1.0 - s) * log1p(-s)) : 0.0;
+          mg_loc += h + 8.0 + 16.0 * (ql + pl);
+          zsq_loc += z * z;
+        }
+      }
+    }
+  }
+  if (MODE == kFRaw) return;
+  f_loc = block_sum<double, kFwdThreads>(f_loc, red);
+  if (MODE == kFCert) {
+    nc_loc = block_sum<double, kFwdThreads>(nc_loc, red);
+    mg_loc = block_sum<double, kFwdThreads>(mg_loc, red);
+    zsq_loc = block_sum<double, kFwdThreads>(zsq_loc, red);
+  }
+  const int cidx = cnt_fwd(d);
+  if (threadIdx.x == 0) {
+    d.fpart[blockIdx.x] = f_loc;
+    if (MODE == kFCert) {
+      d.fpart[gridDim.x + blockIdx.x] = nc_loc;
+      d.fpart[2 * gridDim.x + blockIdx.x] = mg_loc;
+      d.fpart[3 * gridDim.x + blockIdx.x] = zsq_loc;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[cidx], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double f = 0.0, ncs = 0.0, mgs = 0.0, zs = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kFwdThreads) {
+    f += __ldcg(&d.fpart[b]);
+    if (MODE == kFCert) {
+      ncs += __ldcg(&d.fpart[gridDim.x + b]);
+      mgs += __ldcg(&d.fpart[2 * gridDim.x + b]);
+      zs += __ldcg(&d.fpart[3 * gridDim.x + b]);
+    }
+  }
+  f = block_sum<double, kFwdThreads>(f, red);
+  if (MODE == kFCert) {
+    ncs = block_sum<double, kFwdThreads>(ncs, red);
+    mgs = block_sum<double, kFwdThreads>(mgs, red);
+    zs = block_sum<double, kFwdThreads>(zs, red);
+  }
+  if (threadIdx.x == 0) {
+    d.cnt[cidx] = 0;
+    if (MODE == kFStep) {
+      step_logic(nd, f);
+    } else if (MODE == kFInit) {
+      const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // Algorithm 3 line 2
+      nd->Lcur = L1;
+      nd->best_primal = L1;
+      nd->best_dual = -INFINITY;
+      nd->gap = INFINITY;
+      nd->phi = 1.0;
+      nd->c = nd->momentum_on ? 0.25 : 0.0;
+      nd->iter = 1;
+      nd->done = 0;
+      nd->restarts = 0;
+      nd->last_primal = L1;
+      nd->last_dual = -INFINITY;
+    } else {  // certificate partial results (rigorous rounding bounds, u = 2^-53)
+      const double ur = 1.1102230246251565e-16;
+      const double nn = (double)n + 8.0;
+      nd->cert_f = f;
+      nd->cert_negconj = ncs;
+      nd->cert_margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
+      nd->cert_zeta_sq = zs;
+    }
+  }
+}
+
+// ----------------------------------------------------------- power iteration
+
+template <typename T>
+__global__ void k_pow_start(Dev d) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.p; j += gridDim.x * blockDim.x)
+    ((T*)d.grad)[j] = (T)(1.0 + (double)((unsigned long long)(j + 1) * 2654435761ull % 1000ull) / 1000.0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_pow_norm(Dev d, int it) {
+  __shared__ double red[64];
+  const T* w = (const T*)d.grad;
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d.p; j += 1024) s += to_d(w[j]) * to_d(w[j]);
+  s = sqrt(block_sum<double, 1024>(s, red));
+  const double inv = s > 0.0 ? 1.0 / s : 0.0;
+  for (int j = threadIdx.x; j < d.p; j += 1024) ((T*)d.pow_v)[j] = (T)(to_d(w[j]) * inv);
+  if (threadIdx.x == 0 && it >= 0) d.pow_lam[it] = s;
+}
+
+// ----------------------------------------------------------- launchers
+
+template <typename TX, typename T>
+struct Launch {
+  template <int MODE>
+  static void grad(const Dev& d, cudaStream_t s) {
+    dim3 grid(grad_ncol(d), grad_nrb(d));
+    if (d.vec) k_grad<TX, T, MODE, true><<<grid, kGradThreads, 0, s>>>(d);
+    else k_grad<TX, T, MODE, false><<<grid, kGradThreads, 0, s>>>(d);
+  }
+  template <int MODE>
+  static void fwd(const Dev& d, cudaStream_t s) {
+    if (d.vec) k_fwd<TX, T, MODE, true><<<fwd_ntiles(d), kFwdThreads, 0, s>>>(d);
+    else k_fwd<TX, T, MODE, false><<<fwd_ntiles(d), kFwdThreads, 0, s>>>(d);
+  }
+};
+
+void launch_prox_step(const Dev& d, cudaStream_t s);   // k_prox.cu
+void launch_gvalue_init(const Dev& d, cudaStream_t s);
+void launch_cert_final(const Dev& d, cudaStream_t s, int want_z);
+
+template <typename TX, typename T>
+static void step_impl(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
+  if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
+  Launch<TX, T>::template grad<kGStep>(d, s);
+  if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
+  launch_prox_step(d, s);
+  if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+  Launch<TX, T>::template fwd<kFStep>(d, s);
+  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+}
+
+void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
+  if (d.xdt == kXF64) step_impl<double, double>(d, s, ev);
+  else if (d.xdt == kXF32) step_impl<float, float>(d, s, ev);
+  else step_impl<__nv_bfloat16, float>(d, s, ev);
+}
+
+template <typename TX, typename T>
+static void init_impl(const Dev& d, cudaStream_t s) {
+  launch_gvalue_init(d, s);
+  Launch<TX, T>::template fwd<kFInit>(d, s);
+}
+void launch_init(const Dev& d, cudaStream_t s) {
+  if (d.xdt == kXF64) init_impl<double, double>(d, s);
+  else if (d.xdt == kXF32) init_impl<float, float>(d, s);
+  else init_impl<__nv_bfloat16, float>(d, s);
+}
+
+template <typename TX, typename T>
+static void cert_impl(const Dev& d, cudaStream_t s, int want_z) {
+  Launch<TX, T>::template fwd<kFCert>(d, s);
+  Launch<TX, T>::template grad<kGCert>(d, s);
+  launch_cert_final(d, s, want_z);
+}
+void launch_certificate(const Dev& d, cudaStream_t s, int want_z) {
+  if (d.xdt == kXF64) cert_impl<double, double>(d, s, want_z);
+  else if (d.xdt == kXF32) cert_impl<float, float>(d, s, want_z);
+  else cert_impl<__nv_bfloat16, float>(d, s, want_z);
+}
+
+template <typename TX, typename T>
+static void pow_step_impl(const Dev& d, cudaStream_t s, int it) {
+  Launch<TX, T>::template fwd<kFRaw>(d, s);
+  Launch<TX, T>::template grad<kGRaw>(d, s);
+  k_pow_norm<T><<<1, 1024, 0, s>>>(d, it);
+}
+void launch_power_step(const Dev& d, cudaStream_t s, int it) {
+  if (d.xdt == kXF64) pow_step_impl<double, double>(d, s, it);
+  else if (d.xdt == kXF32) pow_step_impl<float, float>(d, s, it);
+  else pow_step_impl<__nv_bfloat16, float>(d, s, it);
+}
+void launch_power_init(const Dev& d, cudaStream_t s) {
+  if (d.xdt == kXF64) {
+    k_pow_start<double><<<64, 256, 0, s>>>(d);
+    k_pow_norm<double><<<1, 1024, 0, s>>>(d, -1);
+  } else {
+    k_pow_start<float><<<64, 256, 0, s>>>(d);
+    k_pow_norm<float><<<1, 1024, 0, s>>>(d, -1);
+  }
+}
+
+void launch_colnorm(const Dev& d, cudaStream_t s) {
+  if (d.xdt == kXF64) Launch<double, double>::grad<kGColsq>(d, s);
+  else if (d.xdt == kXF32) Launch<float, float>::grad<kGColsq>(d, s);
+  else Launch<__nv_bfloat16, float>::grad<kGColsq>(d, s);
+}
+
+}  // namespace ksc

@@ -1,0 +1,245 @@
+// k_prox.cu -- per-node kernels built on the block prox (ksc_prox.cuh):
+//   k_prox_step      one FISTA prox (Algorithm 3 line 8), g(beta^{t+1}) (Alg. 2)
+//                    and, in a second CTA, the in-loop dual term G*(X^T zeta_gamma)
+//   k_gvalue_init    g(beta^1) for the initial objective (Algorithm 3 line 2)
+//   k_cert_final     FP64 G*(a) with its rounding margin, FP64 g(b^), the
+//                    certified bound and gap (Sec. 3.4)
+//   primitives       prox_{rho^-1 g}, g, g* on one vector (FP64)
+#include "ksc_common.cuh"
+#include "ksc_launch.h"
+#include "ksc_prox.cuh"
+#include "ksc_state.cuh"
+
+namespace ksc {
+
+// dual CTA shared memory: hist + scratch only
+constexpr int kDualCap = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kProxBlock, 1) k_prox_step(Dev d) {
+  NodeDev* nd = d.nd;
+  if (nd->done) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int p = d.p;
+  const int t = nd->iter;
+  const int cur = t % 3, prev = (t + 2) % 3, nxt = (t + 1) % 3;
+  T* beta = (T*)d.beta;
+  if (blockIdx.x == 0) {
+    SegSmem<T> sm = carve_seg_smem<T>(smem, kProxCap, d.prox_wsm);
+    SegIO<T> io;
+    io.m = p;
+    io.state = d.state;
+    io.w = nullptr;
+    io.bc = beta + (size_t)cur * p;
+    io.bp = beta + (size_t)prev * p;
+    io.grad = (const T*)d.grad;
+    io.c = nd->c;
+    io.invL = nd->invL;
+    io.rho = nd->rho;
+    io.M = nd->M;
+    io.kp = nd->kp;
+    io.wbuf = (T*)d.wbuf;
+    io.beta = beta + (size_t)nxt * p;
+    io.nnz_idx = d.nnz_idx;
+    io.nnz_val = (T*)d.nnz_val;
+    io.nnz_cap = d.nnz_cap;
+    io.top_out = nullptr;
+    io.qhint = nd->qhint;
+    SegOut o = prox_segment<T, kProxBlock>(io, sm);
+    if (threadIdx.x == 0) {
+      nd->g_next = o.g;
+      nd->nnz = o.nnz;
+      nd->theta = o.theta;
+      const int q = io.kp < p ? io.kp : p;
+      int h = o.qused / 2;
+      if (h < q + 64) h = q + 64;
+      nd->qhint = h;
+      nd->fallback += o.fallback;
+    }
+  } else {
+    SegSmem<T> sm = carve_seg_smem<T>(smem, kDualCap, 0);
+    const T* g = (const T*)d.grad;
+    const double scale = 1.0 / (2.0 * nd->lambda2);
+    double s = gstar_segment<T, kProxBlock>(p, [&](int i) { return g[i]; }, d.state, nd->kp, nd->M,
+                                            scale, sm);
+    if (threadIdx.x == 0) nd->gstar = s;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  NodeDev* nd = d.nd;
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kProxCap, 0);
+  const T* b1 = (const T*)d.beta + (size_t)1 * d.p;
+  GOut o = gvalue_segment<double, kProxBlock>(d.p, [&](int i) { return to_d(b1[i]); }, d.state,
+                                              nd->kp, nd->M, sm, nullptr);
+  if (threadIdx.x == 0) nd->g_next = o.g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kProxBlock, 1) k_cert_final(Dev d, int want_z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  NodeDev* nd = d.nd;
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kProxCap, 0);
+  const int p = d.p;
+  const double ur = 1.1102230246251565e-16;
+  const double l2 = nd->lambda2, M = nd->M;
+  const double scale = 1.0 / (2.0 * l2);
+  // G*(a) / (2 lambda2) over the node: TopSum_k'(H_M(|a_F|/2l2)) + sum_S1 H_M(a_j/2l2)
+  const double gs = gstar_segment<double, kProxBlock>(p, [&](int i) { return d.a64[i]; }, d.state,
+                                                      nd->kp, M, scale, sm);
+  // error bound of a = X^T zeta (FP64, any summation order):
+  //   |a^_j - a_j| <= gamma_{n+1} sum_i |x_ij zeta_i| <= gamma_{n+1} ||x_j|| ||zeta||
+  double cmax = 0.0;
+  int n1 = 0;
+  for (int j = threadIdx.x; j < p; j += kProxBlock) {
+    const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
+    if (st != kZero) cmax = fmax(cmax, d.colnorm[j]);
+    if (st == kOne) n1 += 1;
+  }
+  cmax = block_max<double, kProxBlock>(cmax, sm.red, 0.0);
+  n1 = (int)block_sum<double, kProxBlock>((double)n1, sm.red);
+  const double nn = (double)d.n + 2.0;
+  const double gam = nn * ur / (1.0 - nn * ur);
+  const double znorm = sqrt(nd->cert_zeta_sq) * (1.0 + (nn + 2.0) * ur);
+  const double eps_a = 1.01 * gam * cmax * znorm;
+  const int kp = nd->kp;
+  const int nsel = (kp < p ? kp : p) + n1;
+  // H_M is M-Lipschitz and TopSum is 1-Lipschitz per selected entry; the factors
+  // 1/(2 lambda2) and 2 lambda2 cancel.  Plus the rounding of the H_M values
+  // (division, square, product) and of their sum.
+  const double margin_g = (double)nsel * M * eps_a * (1.0 + 4.0 * ur) +
+                          2.0 * l2 * gs * ((double)nsel + 8.0) * 4.0 * ur;
+  // g(b^) in FP64 (Algorithm 2) and the relaxed z
+  const T* b = (const T*)d.beta + (size_t)(nd->iter % 3) * p;
+  for (int j = threadIdx.x; j < p; j += kProxBlock) d.b64[j] = to_d(b[j]);
+  __syncthreads();
+  GOut go = gvalue_segment<double, kProxBlock>(p, [&](int i) { return d.b64[i]; }, d.state, kp, M,
+                                               sm, want_z ? d.z64 : nullptr);
+  if (threadIdx.x == 0) {
+    const double gst = 2.0 * l2 * gs;
+    double dual = nd->cert_negconj - nd->cert_margin_f - gst - margin_g;
+    dual -= 4.0 * ur * (fabs(nd->cert_negconj) + gst);
+    const double primal = nd->cert_f + 2.0 * l2 * go.g;
+    nd->cert_gstar = gst;
+    nd->cert_margin_g = margin_g;
+    nd->cert_g = go.g;
+    nd->cert_sbar = go.sbar;
+    nd->cert_dual = dual;
+    nd->cert_primal = primal;
+    nd->cert_gap = (primal - dual) / fmax(fabs(primal), 1e-300);
+  }
+}
+
+// ---------------------------------------------------------------- primitives
+
+__global__ void __launch_bounds__(kProxBlock, 1)
+k_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, int* top,
+            double* wbuf, int wsm) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kProxCap, wsm);
+  SegIO<double> io;
+  io.m = p;
+  io.state = nullptr;
+  io.w = w;
+  io.bc = io.bp = io.grad = nullptr;
+  io.c = 0.0;
+  io.invL = 0.0;
+  io.rho = rho;
+  io.M = M;
+  io.kp = k;
+  io.wbuf = wbuf;
+  io.beta = beta;
+  io.nnz_idx = nullptr;
+  io.nnz_val = nullptr;
+  io.nnz_cap = 0;
+  io.top_out = top;
+  io.qhint = 0;
+  prox_segment<double, kProxBlock>(io, sm);
+}
+
+__global__ void __launch_bounds__(kProxBlock, 1)
+k_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kProxCap, 0);
+  GOut o = gvalue_segment<double, kProxBlock>(p, [&](int i) { return beta[i]; }, nullptr, k, M, sm, z);
+  if (threadIdx.x == 0) *g = o.g;
+}
+
+__global__ void __launch_bounds__(kProxBlock, 1)
+k_gstar_prim(const double* a, int p, int k, double M, double* out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kDualCap, 0);
+  double s = gstar_segment<double, kProxBlock>(p, [&](int i) { return a[i]; }, nullptr, k, M, 1.0, sm);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// ---------------------------------------------------------------- launchers
+
+static size_t prox_bytes(int cap, int wsm, int tb) { return seg_smem_bytes(cap, wsm, tb); }
+
+size_t prox_smem_bytes(const Dev& d) {
+  const int tb = d.xdt == kXF64 ? 8 : 4;
+  return prox_bytes(kProxCap, d.prox_wsm, tb);
+}
+
+static size_t g_smem_max = 0;
+
+void prox_prepare() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  g_smem_max = (size_t)optin;
+  cudaFuncSetAttribute(k_prox_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_prox_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_gvalue_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_cert_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+size_t prox_smem_limit() { return g_smem_max; }
+
+void launch_prox_step(const Dev& d, cudaStream_t s) {
+  const size_t bytes = prox_smem_bytes(d);
+  if (d.xdt == kXF64) k_prox_step<double><<<2, kProxBlock, bytes, s>>>(d);
+  else k_prox_step<float><<<2, kProxBlock, bytes, s>>>(d);
+}
+
+void launch_gvalue_init(const Dev& d, cudaStream_t s) {
+  const size_t bytes = prox_bytes(kProxCap, 0, 8);
+  if (d.xdt == kXF64) k_gvalue_init<double><<<1, kProxBlock, bytes, s>>>(d);
+  else k_gvalue_init<float><<<1, kProxBlock, bytes, s>>>(d);
+}
+
+void launch_cert_final(const Dev& d, cudaStream_t s, int want_z) {
+  const size_t bytes = prox_bytes(kProxCap, 0, 8);
+  if (d.xdt == kXF64) k_cert_final<double><<<1, kProxBlock, bytes, s>>>(d, want_z);
+  else k_cert_final<float><<<1, kProxBlock, bytes, s>>>(d, want_z);
+}
+
+void launch_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, int* top,
+                      double* wbuf, cudaStream_t s) {
+  // keep w in shared memory when it fits beside the candidate buffers
+  const size_t base = prox_bytes(kProxCap, 0, 8);
+  int wsm = 0;
+  if (base + (size_t)p * 8 + 16 <= g_smem_max) wsm = p;
+  k_prox_prim<<<1, kProxBlock, prox_bytes(kProxCap, wsm, 8), s>>>(w, p, k, M, rho, beta, top, wbuf,
+                                                                 wsm);
+}
+
+void launch_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z,
+                        cudaStream_t s) {
+  k_gvalue_prim<<<1, kProxBlock, prox_bytes(kProxCap, 0, 8), s>>>(beta, p, k, M, g, z);
+}
+
+void launch_gstar_prim(const double* a, int p, int k, double M, double* out, cudaStream_t s) {
+  k_gstar_prim<<<1, kProxBlock, prox_bytes(kDualCap, 0, 8), s>>>(a, p, k, M, out);
+}
+
+}  // namespace ksc

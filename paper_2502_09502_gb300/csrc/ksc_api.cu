@@ -1,0 +1,579 @@
+// ksc_api.cu -- the C ABI (include/ksc.h): problem lifetime, the host loop of a
+// node solve (CUDA-graph replays of FISTA steps, FP64 certificate, early
+// termination), and the FP64 primitives.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ksc.h"
+#include "ksc_launch.h"
+#include "ksc_state.cuh"
+
+using namespace ksc;
+
+namespace ksc {
+size_t prox_smem_limit();
+}
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static ksc_status fail(ksc_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define KSC_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? KSC_ERR_OOM : KSC_ERR_CUDA,     \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));              \
+    }                                                                               \
+  } while (0)
+
+static bool g_prepared = false;
+
+static ksc_status ensure_prepared() {
+  if (!g_prepared) {
+    prox_prepare();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(KSC_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
+    g_prepared = true;
+  }
+  return KSC_OK;
+}
+
+// ------------------------------------------------------------------ problem
+
+static constexpr int kStepsPerGraph = 16;
+
+struct ksc_problem {
+  int device = 0;
+  int64_t n = 0, p = 0, ldx = 0;
+  int xdt = 0;
+  int loss = 0;
+  bool own_x = false;
+  void* X = nullptr;
+  double* y = nullptr;
+  std::vector<double> y_host;
+  double L = 0.0;
+  int power_iters = 0;
+  size_t bytes = 0;
+  Dev dev{};
+  std::vector<void*> allocs;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_prof = nullptr;
+  bool profile = false;
+  std::vector<cudaEvent_t> events;   // 4 per step of the profiling graph
+  int64_t k_launches[3] = {0, 0, 0};
+  double k_ms[3] = {0, 0, 0};
+};
+
+static size_t tbytes(int xdt) { return xdt == kXF64 ? 8 : 4; }
+static size_t xbytes(int xdt) { return xdt == kXF64 ? 8 : (xdt == kXF32 ? 4 : 2); }
+
+template <typename P>
+static ksc_status dmalloc(ksc_problem* pr, P** ptr, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess)
+    return fail(KSC_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  pr->allocs.push_back(v);
+  pr->bytes += bytes;
+  *ptr = (P*)v;
+  return KSC_OK;
+}
+
+static void free_problem(ksc_problem* pr) {
+  if (!pr) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(pr->device);
+  if (pr->graph) cudaGraphExecDestroy(pr->graph);
+  if (pr->graph_prof) cudaGraphExecDestroy(pr->graph_prof);
+  for (auto e : pr->events) cudaEventDestroy(e);
+  for (void* v : pr->allocs) cudaFree(v);
+  cudaSetDevice(cur);
+  delete pr;
+}
+
+static ksc_status alloc_workspace(ksc_problem* pr) {
+  Dev& d = pr->dev;
+  const int64_t n = pr->n, p = pr->p;
+  const size_t tb = tbytes(pr->xdt);
+  ksc_status st;
+#define ALLOC(ptr, bytes) \
+  if ((st = dmalloc(pr, &(ptr), (bytes))) != KSC_OK) return st
+  ALLOC(d.beta, 3 * p * tb);
+  ALLOC(d.u, 3 * n * tb);
+  ALLOC(d.grad, p * tb);
+  ALLOC(d.wbuf, p * tb);
+  ALLOC(d.nnz_val, p * tb);
+  ALLOC(d.nnz_idx, p * sizeof(int));
+  ALLOC(d.ws, (size_t)grad_nrb(d) * p * 8);
+  ALLOC(d.cnt, (size_t)cnt_total(d) * sizeof(int));
+  ALLOC(d.ncpart, (size_t)grad_nrb(d) * 8);
+  ALLOC(d.fpart, (size_t)fwd_ntiles(d) * 4 * 8);
+  ALLOC(d.u64, n * 8);
+  ALLOC(d.zeta, n * 8);
+  ALLOC(d.a64, p * 8);
+  ALLOC(d.z64, p * 8);
+  ALLOC(d.b64, p * 8);
+  double* cn = nullptr;
+  ALLOC(cn, p * 8);
+  d.colnorm = cn;
+  ALLOC(d.state, p);
+  ALLOC(d.pow_v, p * tb);
+  ALLOC(d.pow_lam, 4096 * 8);
+  ALLOC(d.nd, sizeof(NodeDev));
+#undef ALLOC
+  KSC_CUDA(cudaMemset(d.cnt, 0, (size_t)cnt_total(d) * sizeof(int)));
+  KSC_CUDA(cudaMemset(d.beta, 0, 3 * p * tb));
+  KSC_CUDA(cudaMemset(d.u, 0, 3 * n * tb));
+  KSC_CUDA(cudaMemset(d.state, 0, p));
+  KSC_CUDA(cudaMemset(d.nd, 0, sizeof(NodeDev)));
+  return KSC_OK;
+}
+
+static ksc_status power_iteration(ksc_problem* pr, cudaStream_t s) {
+  Dev& d = pr->dev;
+  launch_power_init(d, s);
+  KSC_CUDA(cudaGetLastError());
+  const int max_it = 4000;
+  const double tol = 1e-6;
+  std::vector<double> lam(max_it);
+  int it = 0;
+  double lmax = 0.0;
+  while (it < max_it) {
+    const int upto = std::min(max_it, it + 10);
+    for (; it < upto; ++it) launch_power_step(d, s, it);
+    KSC_CUDA(cudaGetLastError());
+    KSC_CUDA(cudaMemcpyAsync(lam.data(), d.pow_lam, it * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KSC_CUDA(cudaStreamSynchronize(s));
+    bool conv = false;
+    for (int j = 1; j < it; ++j) {
+      if (std::fabs(lam[j] - lam[j - 1]) <= tol * lam[j]) { conv = true; lmax = lam[j]; pr->power_iters = j + 1; break; }
+    }
+    if (conv) break;
+    lmax = lam[it - 1];
+    pr->power_iters = it;
+  }
+  const double cf = pr->loss == KSC_LOSS_LSQ ? 2.0 : 0.25;
+  pr->L = cf * lmax * 1.01;
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cuda_stream,
+                                         ksc_problem** out) {
+  if (!out) return fail(KSC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!desc) return fail(KSC_ERR_INVALID_ARG, "desc is NULL");
+  if (desc->n < 1 || desc->p < 1) return fail(KSC_ERR_INVALID_ARG, "n and p must be >= 1");
+  if (desc->n > (1ll << 31) - 1 || desc->p > (1ll << 31) - 1)
+    return fail(KSC_ERR_INVALID_ARG, "n and p must be < 2^31");
+  if (desc->x_dtype != KSC_F64 && desc->x_dtype != KSC_F32 && desc->x_dtype != KSC_BF16)
+    return fail(KSC_ERR_INVALID_ARG, "unknown x_dtype");
+  if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC)
+    return fail(KSC_ERR_INVALID_ARG, "unknown loss");
+  if (!desc->X || !desc->y) return fail(KSC_ERR_INVALID_ARG, "X and y must be non-NULL");
+  const int64_t ldx = desc->ldx == 0 ? desc->p : desc->ldx;
+  if (ldx < desc->p) return fail(KSC_ERR_INVALID_ARG, "ldx < p");
+  for (int64_t i = 0; i < desc->n; ++i) {
+    const double v = desc->y[i];
+    if (!std::isfinite(v)) return fail(KSC_ERR_INVALID_ARG, "y has a non-finite entry");
+    if (desc->loss == KSC_LOSS_LOGISTIC && v != 1.0 && v != -1.0)
+      return fail(KSC_ERR_INVALID_ARG, "logistic labels must be +1 or -1");
+  }
+  ksc_status st = ensure_prepared();
+  if (st != KSC_OK) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  ksc_problem* pr = new ksc_problem();
+  cudaGetDevice(&pr->device);
+  pr->n = desc->n;
+  pr->p = desc->p;
+  pr->ldx = ldx;
+  pr->xdt = (int)desc->x_dtype;
+  pr->loss = (int)desc->loss;
+  pr->y_host.assign(desc->y, desc->y + desc->n);
+  Dev& d = pr->dev;
+  d.xdt = pr->xdt;
+  d.n = (int)pr->n;
+  d.p = (int)pr->p;
+  d.ldx = ldx;
+  d.loss = pr->loss;
+  const size_t xb = xbytes(pr->xdt);
+  auto bail = [&](ksc_status e) { free_problem(pr); return e; };
+  if (desc->x_on_device) {
+    pr->X = const_cast<void*>(desc->X);
+    pr->own_x = false;
+  } else {
+    void* xd = nullptr;
+    if ((st = dmalloc(pr, &xd, (size_t)(pr->n - 1) * ldx * xb + (size_t)pr->p * xb)) != KSC_OK) return bail(st);
+    cudaError_t e = cudaMemcpyAsync(xd, desc->X, ((size_t)(pr->n - 1) * ldx + pr->p) * xb,
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("copy X: ") + cudaGetErrorString(e)));
+    pr->X = xd;
+    pr->own_x = true;
+  }
+  d.X = pr->X;
+  const int cpt = cols_per_thread(pr->xdt);
+  d.vec = ((ldx % cpt) == 0 && ((uintptr_t)pr->X % 16) == 0) ? 1 : 0;
+  if ((st = dmalloc(pr, &pr->y, pr->n * 8)) != KSC_OK) return bail(st);
+  {
+    cudaError_t e = cudaMemcpyAsync(pr->y, desc->y, pr->n * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("copy y: ") + cudaGetErrorString(e)));
+  }
+  d.y = pr->y;
+  if ((st = alloc_workspace(pr)) != KSC_OK) return bail(st);
+  d.nnz_cap = std::max(1, d.p / 12);
+  // keep w in shared memory when it fits beside the prox buffers
+  {
+    size_t lim = prox_smem_limit();
+    Dev t = d;
+    t.prox_wsm = d.p;
+    d.prox_wsm = (prox_smem_bytes(t) <= lim) ? d.p : 0;
+  }
+  launch_colnorm(d, s);
+  if (cudaGetLastError() != cudaSuccess) return bail(fail(KSC_ERR_CUDA, "colnorm launch failed"));
+  if (desc->lipschitz > 0) {
+    pr->L = desc->lipschitz;
+  } else if ((st = power_iteration(pr, s)) != KSC_OK) {
+    return bail(st);
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("problem setup: ") + cudaGetErrorString(e)));
+  if (!(pr->L > 0.0) || !std::isfinite(pr->L)) return bail(fail(KSC_ERR_INVALID_ARG, "X has zero norm"));
+  *out = pr;
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_destroy(ksc_problem* problem) {
+  free_problem(problem);
+  return KSC_OK;
+}
+
+extern "C" size_t ksc_problem_bytes(const ksc_problem* problem) {
+  if (!problem) return 0;
+  return problem->bytes;
+}
+
+extern "C" ksc_status ksc_problem_info(const ksc_problem* problem, double* lipschitz, int32_t* power_iters) {
+  if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
+  if (lipschitz) *lipschitz = problem->L;
+  if (power_iters) *power_iters = problem->power_iters;
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable) {
+  if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
+  problem->profile = enable != 0;
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
+                                              double* total_ms, int32_t reset) {
+  if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
+  if (kernel < 0 || kernel > 2) return fail(KSC_ERR_INVALID_ARG, "unknown kernel id");
+  if (launches) *launches = problem->k_launches[kernel];
+  if (total_ms) *total_ms = problem->k_ms[kernel];
+  if (reset) {
+    for (int k = 0; k < 3; ++k) { problem->k_launches[k] = 0; problem->k_ms[k] = 0.0; }
+  }
+  return KSC_OK;
+}
+
+// ------------------------------------------------------------------ solve
+
+static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof) {
+  cudaGraphExec_t* slot = prof ? &pr->graph_prof : &pr->graph;
+  if (*slot) return KSC_OK;
+  if (prof && pr->events.empty()) {
+    pr->events.resize(4 * kStepsPerGraph);
+    for (auto& e : pr->events) KSC_CUDA(cudaEventCreate(&e));
+  }
+  // capture on a private stream (legacy default stream cannot be captured)
+  cudaStream_t cs;
+  KSC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < kStepsPerGraph; ++k) launch_step(pr->dev, cs, prof ? &pr->events[4 * k] : nullptr);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(slot, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  (void)s;
+  if (e != cudaSuccess) return fail(KSC_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  return KSC_OK;
+}
+
+template <typename T>
+static void fill_slots(std::vector<unsigned char>& buf, const std::vector<double>& b) {
+  buf.resize(b.size() * sizeof(T));
+  T* t = (T*)buf.data();
+  for (size_t j = 0; j < b.size(); ++j) t[j] = (T)b[j];
+}
+
+struct NodeSetup {
+  std::vector<int8_t> state;
+  int kp = 0;
+  int n_one = 0;
+  bool infeasible = false;
+};
+
+static ksc_status check_node(const ksc_problem* pr, const ksc_node* node, NodeSetup* ns) {
+  if (!node) return fail(KSC_ERR_INVALID_ARG, "node is NULL");
+  if (!(node->lambda2 > 0) || !std::isfinite(node->lambda2)) return fail(KSC_ERR_INVALID_ARG, "lambda2 must be > 0");
+  if (!(node->M > 0) || !std::isfinite(node->M)) return fail(KSC_ERR_INVALID_ARG, "M must be > 0");
+  if (node->k < 0) return fail(KSC_ERR_INVALID_ARG, "k must be >= 0");
+  if (node->max_iter <= 0) return fail(KSC_ERR_INVALID_ARG, "max_iter must be > 0");
+  if (!(node->rel_gap_tol >= 0) || !std::isfinite(node->rel_gap_tol)) return fail(KSC_ERR_INVALID_ARG, "rel_gap_tol must be >= 0");
+  if (node->n_zero < 0 || node->n_one < 0) return fail(KSC_ERR_INVALID_ARG, "negative set size");
+  if ((node->n_zero > 0 && !node->fixed_zero) || (node->n_one > 0 && !node->fixed_one))
+    return fail(KSC_ERR_INVALID_ARG, "fixed-set pointer is NULL");
+  ns->state.assign(pr->p, (int8_t)kFree);
+  for (int i = 0; i < node->n_zero; ++i) {
+    const int j = node->fixed_zero[i];
+    if (j < 0 || j >= pr->p) return fail(KSC_ERR_INVALID_ARG, "fixed_zero index out of range");
+    ns->state[j] = kZero;
+  }
+  for (int i = 0; i < node->n_one; ++i) {
+    const int j = node->fixed_one[i];
+    if (j < 0 || j >= pr->p) return fail(KSC_ERR_INVALID_ARG, "fixed_one index out of range");
+    if (ns->state[j] == kZero) ns->infeasible = true;
+    if (ns->state[j] != kOne) ns->n_one += 1;
+    ns->state[j] = kOne;
+  }
+  ns->kp = node->k - ns->n_one;
+  if (ns->kp < 0) ns->infeasible = true;
+  int nfree = 0;
+  for (auto v : ns->state) nfree += (v == kFree);
+  const int q = std::min(ns->kp, nfree);
+  if (!ns->infeasible && q >= kProxCap)
+    return fail(KSC_ERR_UNIMPLEMENTED, "k' = k - |S1| must be < 4096 (prox candidate capacity)");
+  if (node->warm_beta)
+    for (int64_t j = 0; j < pr->p; ++j)
+      if (!std::isfinite(node->warm_beta[j])) return fail(KSC_ERR_INVALID_ARG, "warm_beta has a non-finite entry");
+  return KSC_OK;
+}
+
+static ksc_status replay(ksc_problem* pr, cudaStream_t s, NodeDev* h) {
+  const bool prof = pr->profile;
+  cudaGraphExec_t g = prof ? pr->graph_prof : pr->graph;
+  const int before = h->iter;
+  KSC_CUDA(cudaGraphLaunch(g, s));
+  KSC_CUDA(cudaMemcpyAsync(h, pr->dev.nd, sizeof(NodeDev), cudaMemcpyDeviceToHost, s));
+  KSC_CUDA(cudaStreamSynchronize(s));
+  if (prof) {
+    const int steps = std::min(kStepsPerGraph, h->iter - before);
+    for (int k = 0; k < steps; ++k) {
+      for (int j = 0; j < 3; ++j) {
+        float ms = 0.f;
+        KSC_CUDA(cudaEventElapsedTime(&ms, pr->events[4 * k + j], pr->events[4 * k + j + 1]));
+        pr->k_ms[j] += ms;
+        pr->k_launches[j] += 1;
+      }
+    }
+  }
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_result* res,
+                                     void* cuda_stream) {
+  if (!pr) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
+  if (!res) return fail(KSC_ERR_INVALID_ARG, "result is NULL");
+  NodeSetup ns;
+  ksc_status st = check_node(pr, node, &ns);
+  if (st != KSC_OK) return st;
+  res->iters = 0;
+  res->restarts = 0;
+  res->pruned = 0;
+  if (ns.infeasible) {
+    res->primal = INFINITY;
+    res->dual_bound = INFINITY;
+    res->rel_gap = 0.0;
+    res->pruned = 1;
+    res->status = KSC_ERR_INFEASIBLE_NODE;
+    return fail(KSC_ERR_INFEASIBLE_NODE, "infeasible node: |S1| > k or S0 and S1 intersect");
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int cur_dev = 0;
+  cudaGetDevice(&cur_dev);
+  if (cur_dev != pr->device) KSC_CUDA(cudaSetDevice(pr->device));
+  Dev& d = pr->dev;
+  const int64_t p = pr->p;
+  // warm start projected on the node: S0 -> 0, clip to the box (reading of Alg. 3 line 1)
+  std::vector<double> w0(p, 0.0);
+  if (node->warm_beta)
+    for (int64_t j = 0; j < p; ++j)
+      w0[j] = ns.state[j] == kZero ? 0.0 : std::min(node->M, std::max(-node->M, node->warm_beta[j]));
+  std::vector<unsigned char> wb;
+  if (pr->xdt == kXF64) fill_slots<double>(wb, w0); else fill_slots<float>(wb, w0);
+  const size_t tb = tbytes(pr->xdt);
+  KSC_CUDA(cudaMemcpyAsync(d.state, ns.state.data(), p, cudaMemcpyHostToDevice, s));
+  KSC_CUDA(cudaMemcpyAsync(d.beta, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
+  KSC_CUDA(cudaMemcpyAsync((char*)d.beta + p * tb, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
+  NodeDev h;
+  std::memset(&h, 0, sizeof h);
+  h.lambda2 = node->lambda2;
+  h.M = node->M;
+  h.L = pr->L;
+  h.invL = 1.0 / pr->L;
+  h.rho = pr->L / (2.0 * node->lambda2);
+  h.tol_loop = node->rel_gap_tol;
+  h.incumbent = node->incumbent;
+  h.kp = ns.kp;
+  h.max_iter = node->max_iter;
+  h.restart_on = (node->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
+  h.momentum_on = (node->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;
+  h.loss = pr->loss;
+  h.iter = 1;
+  h.qhint = 0;
+  h.nnz = (int)p + 1;   // the warm start's support is unknown: dense forward pass
+  KSC_CUDA(cudaMemcpyAsync(d.nd, &h, sizeof h, cudaMemcpyHostToDevice, s));
+  launch_init(d, s);
+  KSC_CUDA(cudaGetLastError());
+  if ((st = build_graph(pr, s, pr->profile)) != KSC_OK) return st;
+  KSC_CUDA(cudaMemcpyAsync(&h, d.nd, sizeof h, cudaMemcpyDeviceToHost, s));
+  KSC_CUDA(cudaStreamSynchronize(s));
+
+  const double tol = node->rel_gap_tol;
+  const double inc = node->incumbent;
+  int pruned = 0;
+  ksc_status out_status = KSC_OK;
+  for (;;) {
+    if ((st = replay(pr, s, &h)) != KSC_OK) return st;
+    if (h.done == kRunning) continue;
+    // FP64 certificate at the current iterate
+    launch_certificate(d, s, res->z != nullptr);
+    KSC_CUDA(cudaGetLastError());
+    KSC_CUDA(cudaMemcpyAsync(&h, d.nd, sizeof h, cudaMemcpyDeviceToHost, s));
+    KSC_CUDA(cudaStreamSynchronize(s));
+    const bool gap_ok = h.cert_gap <= tol;
+    const bool prune_ok = std::isfinite(inc) && h.cert_dual > inc;
+    if (prune_ok) { pruned = 1; break; }
+    if (gap_ok) break;
+    if (h.done == kDonePrimal) break;                 // Sec. 4.3 rule (1): branch
+    if (h.done == kDoneMaxIter) { out_status = KSC_NOT_CONVERGED; break; }
+    // the in-loop test fired on values the FP64 certificate does not confirm:
+    // tighten the in-loop tolerance (or the in-loop prune threshold) and go on
+    NodeDev upd = h;
+    if (h.done == kDoneGap) upd.tol_loop = std::max(h.gap * 0.25, 1e-16);
+    if (h.done == kDonePruned) upd.incumbent = inc + 2.0 * std::fabs(h.best_dual - h.cert_dual) + 1e-12 * std::fabs(inc);
+    upd.done = kRunning;
+    upd.best_dual = h.cert_dual > -INFINITY ? std::max(h.cert_dual, -1e300) : -INFINITY;
+    KSC_CUDA(cudaMemcpyAsync(d.nd, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
+    h = upd;
+  }
+  res->primal = h.cert_primal;
+  res->dual_bound = h.cert_dual;
+  res->rel_gap = h.cert_gap;
+  res->iters = h.iter - 1;
+  res->restarts = h.restarts;
+  res->pruned = pruned;
+  res->status = out_status;
+  if (res->beta) KSC_CUDA(cudaMemcpyAsync(res->beta, d.b64, p * 8, cudaMemcpyDeviceToHost, s));
+  if (res->z) KSC_CUDA(cudaMemcpyAsync(res->z, d.z64, p * 8, cudaMemcpyDeviceToHost, s));
+  KSC_CUDA(cudaStreamSynchronize(s));
+  if (out_status != KSC_OK) return fail(out_status, "max_iter reached before the gap target");
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, int32_t count,
+                                      ksc_result* results, void* cuda_stream) {
+  if (!pr || !nodes || !results || count < 0) return fail(KSC_ERR_INVALID_ARG, "bad arguments");
+  ksc_status first = KSC_OK;
+  for (int32_t i = 0; i < count; ++i) {
+    ksc_status st = ksc_solve_node(pr, &nodes[i], &results[i], cuda_stream);
+    if (st != KSC_OK && st != KSC_NOT_CONVERGED && st != KSC_ERR_INFEASIBLE_NODE) return st;
+    if (first == KSC_OK && st != KSC_OK) first = st;
+  }
+  return first;
+}
+
+// ------------------------------------------------------------------ primitives
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+static ksc_status prim_check(int64_t p, int32_t k, double M) {
+  if (p < 1 || p > (1ll << 30)) return fail(KSC_ERR_INVALID_ARG, "p must be in [1, 2^30]");
+  if (k < 0) return fail(KSC_ERR_INVALID_ARG, "k must be >= 0");
+  if (!(M > 0) || !std::isfinite(M)) return fail(KSC_ERR_INVALID_ARG, "M must be > 0");
+  if (std::min<int64_t>(k, p) >= kProxCap)
+    return fail(KSC_ERR_UNIMPLEMENTED, "min(k, p) must be < 4096 (prox candidate capacity)");
+  return ensure_prepared();
+}
+
+extern "C" ksc_status ksc_prox_g(const double* w, int64_t p, int32_t k, double M, double rho,
+                                 double* beta_out, int32_t* top_out) {
+  if (!w || !beta_out) return fail(KSC_ERR_INVALID_ARG, "w and beta_out must be non-NULL");
+  if (!(rho > 0) || !std::isfinite(rho)) return fail(KSC_ERR_INVALID_ARG, "rho must be > 0");
+  ksc_status st = prim_check(p, k, M);
+  if (st != KSC_OK) return st;
+  for (int64_t j = 0; j < p; ++j)
+    if (!std::isfinite(w[j])) return fail(KSC_ERR_INVALID_ARG, "w has a non-finite entry");
+  DevBuf bw, bb, bt, bs;
+  const int q = (int)std::min<int64_t>(k, p);
+  KSC_CUDA(cudaMalloc(&bw.p, p * 8));
+  KSC_CUDA(cudaMalloc(&bb.p, p * 8));
+  KSC_CUDA(cudaMalloc(&bs.p, p * 8));
+  KSC_CUDA(cudaMalloc(&bt.p, (q > 0 ? q : 1) * sizeof(int)));
+  KSC_CUDA(cudaMemcpy(bw.p, w, p * 8, cudaMemcpyHostToDevice));
+  launch_prox_prim((const double*)bw.p, (int)p, k, M, rho, (double*)bb.p, top_out ? (int*)bt.p : nullptr,
+                   (double*)bs.p, 0);
+  KSC_CUDA(cudaGetLastError());
+  KSC_CUDA(cudaMemcpy(beta_out, bb.p, p * 8, cudaMemcpyDeviceToHost));
+  if (top_out && q > 0) KSC_CUDA(cudaMemcpy(top_out, bt.p, q * sizeof(int), cudaMemcpyDeviceToHost));
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_g_value(const double* beta, int64_t p, int32_t k, double M, double* g_out,
+                                  double* z_out) {
+  if (!beta || !g_out) return fail(KSC_ERR_INVALID_ARG, "beta and g_out must be non-NULL");
+  ksc_status st = prim_check(p, k, M);
+  if (st != KSC_OK) return st;
+  for (int64_t j = 0; j < p; ++j)
+    if (!std::isfinite(beta[j])) return fail(KSC_ERR_INVALID_ARG, "beta has a non-finite entry");
+  DevBuf bb, bg, bz;
+  KSC_CUDA(cudaMalloc(&bb.p, p * 8));
+  KSC_CUDA(cudaMalloc(&bg.p, 8));
+  KSC_CUDA(cudaMalloc(&bz.p, p * 8));
+  KSC_CUDA(cudaMemcpy(bb.p, beta, p * 8, cudaMemcpyHostToDevice));
+  launch_gvalue_prim((const double*)bb.p, (int)p, k, M, (double*)bg.p, z_out ? (double*)bz.p : nullptr, 0);
+  KSC_CUDA(cudaGetLastError());
+  KSC_CUDA(cudaMemcpy(g_out, bg.p, 8, cudaMemcpyDeviceToHost));
+  if (z_out) KSC_CUDA(cudaMemcpy(z_out, bz.p, p * 8, cudaMemcpyDeviceToHost));
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* out) {
+  if (!a || !out) return fail(KSC_ERR_INVALID_ARG, "a and out must be non-NULL");
+  if (p < 1 || k < 0 || !(M > 0)) return fail(KSC_ERR_INVALID_ARG, "need p >= 1, k >= 0, M > 0");
+  ksc_status st = ensure_prepared();
+  if (st != KSC_OK) return st;
+  for (int64_t j = 0; j < p; ++j)
+    if (!std::isfinite(a[j])) return fail(KSC_ERR_INVALID_ARG, "a has a non-finite entry");
+  DevBuf ba, bo;
+  KSC_CUDA(cudaMalloc(&ba.p, p * 8));
+  KSC_CUDA(cudaMalloc(&bo.p, 8));
+  KSC_CUDA(cudaMemcpy(ba.p, a, p * 8, cudaMemcpyHostToDevice));
+  launch_gstar_prim((const double*)ba.p, (int)p, k, M, (double*)bo.p, 0);
+  KSC_CUDA(cudaGetLastError());
+  KSC_CUDA(cudaMemcpy(out, bo.p, 8, cudaMemcpyDeviceToHost));
+  return KSC_OK;
+}
+
+extern "C" const char* ksc_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char* ksc_version(void) { return "ksc 0.1 (sm_103a)"; }

@@ -1,0 +1,228 @@
+// ksc_common.cuh -- device building blocks shared by the kernels of the library:
+// warp/block reductions and scans, key bit maps, the block-wide MSD radix select
+// and the block bitonic sort used by the segmented prox (Alg. 1 / Lemma 3.3).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace ksc {
+
+constexpr int kWarp = 32;
+
+// ----------------------------------------------------------------- scalars
+
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float to_f(double x) { return (float)x; }
+
+// ------------------------------------------------------- warp/block reduce
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+template <typename T>
+__device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reductions; `red` is a shared scratch of >= 32 elements of T.  All
+// threads receive the result.  Deterministic (fixed tree order).
+template <typename T, int BLOCK>
+__device__ __forceinline__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T t = (threadIdx.x < BLOCK / 32) ? red[threadIdx.x] : T(0);
+  if (w == 0) t = warp_sum(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+template <typename T, int BLOCK>
+__device__ __forceinline__ T block_max(T v, T* red, T lowest) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T t = (threadIdx.x < BLOCK / 32) ? red[threadIdx.x] : lowest;
+  if (w == 0) t = warp_max(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+template <typename T, int BLOCK>
+__device__ __forceinline__ T block_min(T v, T* red, T highest) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_min(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  T t = (threadIdx.x < BLOCK / 32) ? red[threadIdx.x] : highest;
+  if (w == 0) t = warp_min(t);
+  if (threadIdx.x == 0) red[0] = t;
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive prefix sum over the block in thread order (warp shuffles + one
+// shared pass over warp totals).  `red` holds >= 33 elements.  Returns this
+// thread's exclusive prefix; *total receives the block total.
+template <typename T, int BLOCK>
+__device__ __forceinline__ T block_exclusive_scan(T v, T* red, T* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T n = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += n;
+  }
+  __syncthreads();
+  if (lane == 31) red[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    T t = (lane < BLOCK / 32) ? red[lane] : T(0);
+    T ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T n = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += n;
+    }
+    red[lane] = ti - t;            // exclusive warp offsets
+    if (lane == 31) red[32] = ti;  // block total
+  }
+  __syncthreads();
+  T r = red[w] + incl - v;
+  *total = red[32];
+  __syncthreads();
+  return r;
+}
+
+// --------------------------------------------------------------- key bits
+// Non-negative floating keys compare like their bit patterns as unsigned ints.
+
+template <typename T> struct Bits;
+template <> struct Bits<float> {
+  using U = uint32_t;
+  static __device__ __forceinline__ U of(float x) { return __float_as_uint(x); }
+  static __device__ __forceinline__ float val(U u) { return __uint_as_float(u); }
+};
+template <> struct Bits<double> {
+  using U = unsigned long long;
+  static __device__ __forceinline__ U of(double x) { return (U)__double_as_longlong(x); }
+  static __device__ __forceinline__ double val(U u) { return __longlong_as_double((long long)u); }
+};
+
+// ---------------------------------------------------------- radix select
+// Block-wide selection of the q-th largest of m non-negative keys (1 <= q <= m)
+// by most-significant-digit radix passes of 11 bits over the key bits.
+// `load(i)` returns the key bits of element i.  hist: shared, >= 2048 uint32.
+// sh: shared int scratch >= 40.  Result: thr = bits of the q-th largest key,
+// gt = #keys > thr, eq = #keys == thr.
+
+template <typename U>
+struct SelectResult {
+  U thr;
+  int gt;
+  int eq;
+};
+
+template <typename U, int BLOCK, typename Load>
+__device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist, int* sh) {
+  constexpr int BITS = (int)sizeof(U) * 8;
+  constexpr int DIG = 11;
+  constexpr int NB = 1 << DIG;
+  static_assert(BLOCK * 2 == NB, "block_select expects 1024 threads");
+  U prefix = 0;
+  int q_rem = q, gt = 0, eq = 0;
+  int hi = BITS;
+  while (hi > 0) {
+    const int w = hi < DIG ? hi : DIG;
+    const int lo = hi - w;
+    const U himask = (hi >= BITS) ? (U)0 : (~(U)0 << hi);
+    for (int b = threadIdx.x; b < NB; b += BLOCK) hist[b] = 0u;
+    __syncthreads();
+    // warp-uniform loop; lanes with the same bin are aggregated (__match_any_sync)
+    // so that runs of equal keys (e.g. zeros) do not serialise on one counter
+    for (int base = 0; base < m; base += BLOCK) {
+      const int i = base + (int)threadIdx.x;
+      int bin = -1;
+      if (i < m) {
+        U k = load(i);
+        if ((k & himask) == (prefix & himask)) bin = (int)((k >> lo) & (U)((1u << w) - 1u));
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, bin);
+      if (bin >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
+        atomicAdd(&hist[bin], (unsigned)__popc(peers));
+    }
+    __syncthreads();
+    // thread t owns bins NB-1-2t (upper) and NB-2-2t (lower): thread order is
+    // descending bin order, so an exclusive scan gives the count above a bin.
+    const int b1 = NB - 1 - 2 * (int)threadIdx.x, b0 = b1 - 1;
+    const int c1 = (int)hist[b1], c0 = (int)hist[b0];
+    int tot;
+    int above = block_exclusive_scan<int, BLOCK>(c1 + c0, sh, &tot);
+    if (above < q_rem && q_rem <= above + c1) { sh[36] = b1; sh[37] = above; sh[38] = c1; }
+    else if (above + c1 < q_rem && q_rem <= above + c1 + c0) { sh[36] = b0; sh[37] = above + c1; sh[38] = c0; }
+    __syncthreads();
+    const int bin = sh[36], cab = sh[37];
+    eq = sh[38];
+    __syncthreads();
+    prefix |= ((U)bin) << lo;
+    gt += cab;
+    q_rem -= cab;
+    hi = lo;
+  }
+  return SelectResult<U>{prefix, gt, eq};
+}
+
+// ---------------------------------------------------------- bitonic sort
+// In-place descending sort of N (power of two) values in shared memory.
+template <typename T, int BLOCK>
+__device__ void block_bitonic_sort_desc(T* s, int N) {
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (N >> 1); i += BLOCK) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = ((lo & size) == 0);
+        T a = s[lo], b = s[hi];
+        if ((a < b) == desc) { s[lo] = b; s[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------- Huber
+
+__device__ __forceinline__ double huber(double a, double M) {
+  double t = fabs(a);
+  return t <= M ? 0.5 * t * t : M * t - 0.5 * M * M;
+}
+
+}  // namespace ksc

@@ -1,0 +1,631 @@
+// ksc_prox.cuh -- block-level (one CTA per segment) exact proximal operator of
+// the perspective term and the value of g, for one node.
+//
+// prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w)     (Moreau, Sec. 3.3)
+// prox_{rho g*} is the Huber-isotonic regression of Lemma 3.3 on the sorted
+// |rho w|, solved by PAVA in the paper (Alg. 1 + Alg. 4).  With the Huber
+// weight rho on the top k' positions only, the unconstrained block values are
+// non-increasing on each side of position k', so PAVA pools at most ONE block
+// straddling k'/k'+1.  Its value v = rho * theta is the root of the monotone,
+// piecewise-linear
+//   Phi(theta) = sum_{t in top} (theta + min(rho theta, M) - a_t)_+
+//              - sum_{j in tail} (a_j - theta)_+,        a = |w|,
+// and in primal terms the prox is
+//   top k':  |b| = min(M, rho a/(1+rho), a - theta)   (ridge shrink / box / pool)
+//   tail:    |b| = max(0, a - theta)                    (soft threshold).
+// The kernel finds theta exactly: a radix select gives the top-Q magnitudes
+// (Q = k' + candidate tail), a bitonic sort orders them, and a prefix scan over
+// the breakpoints {a_j, theta^b_t, M/rho} brackets the root, where Phi is linear.
+// If the pooled block reaches past the candidates, Q grows; past the shared
+// memory capacity a full-pass bracketed Newton iteration on the same Phi is used.
+#pragma once
+
+#include "ksc_common.cuh"
+#include "ksc_state.cuh"
+
+namespace ksc {
+
+constexpr int kProxBlock = 1024;
+
+// Shared-memory carve for one segment.  cap: candidate capacity (power of 2).
+template <typename T>
+struct SegSmem {
+  unsigned* hist;   // 2048
+  int* sh;          // 64
+  double* red;      // 64
+  double* cand;     // cap
+  double* pref;     // cap + 1
+  int* cidx;        // cap (index payload for ordered outputs)
+  T* wsm;           // segment values in shared memory, or nullptr (global scratch)
+  int cap;
+};
+
+__host__ __device__ inline size_t seg_smem_bytes(int cap, int wsm_elems, int tbytes) {
+  return 2048 * 4 + 64 * 4 + 64 * 8 + (size_t)cap * 8 + (size_t)(cap + 1) * 8 + (size_t)cap * 4 +
+         (size_t)wsm_elems * tbytes + 64;
+}
+
+template <typename T>
+__device__ inline SegSmem<T> carve_seg_smem(unsigned char* base, int cap, int wsm_elems) {
+  SegSmem<T> s;
+  size_t off = 0;
+  s.hist = (unsigned*)(base + off); off += 2048 * 4;
+  s.sh = (int*)(base + off); off += 64 * 4;
+  s.red = (double*)(base + off); off += 64 * 8;
+  s.cand = (double*)(base + off); off += (size_t)cap * 8;
+  s.pref = (double*)(base + off); off += (size_t)(cap + 1) * 8;
+  s.cidx = (int*)(base + off); off += (size_t)cap * 4;
+  off = (off + 15) & ~(size_t)15;
+  s.wsm = wsm_elems > 0 ? (T*)(base + off) : nullptr;
+  s.cap = cap;
+  return s;
+}
+
+template <typename T>
+__device__ __forceinline__ typename Bits<T>::U abs_bits(T x) {
+  using U = typename Bits<T>::U;
+  const U mask = ~((U)1 << (sizeof(U) * 8 - 1));
+  return Bits<T>::of(x) & mask;
+}
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int n = 1;
+  while (n < x) n <<= 1;
+  return n;
+}
+
+// breakpoint of a top element: theta where theta + min(rho theta, M) = a
+__device__ __forceinline__ double top_break(double a, double rho, double M) {
+  return (a * rho <= M * (1.0 + rho)) ? a / (1.0 + rho) : a - M;
+}
+
+// Exclusive prefix sums pref[0..Q] of cand[0..Q) (double), block-wide.
+template <int BLOCK>
+__device__ void block_prefix(const double* cand, double* pref, int Q, double* red) {
+  const int per = (Q + BLOCK - 1) / BLOCK;
+  const int s0 = threadIdx.x * per;
+  double loc = 0.0;
+  for (int j = 0; j < per; ++j) if (s0 + j < Q) loc += cand[s0 + j];
+  double tot;
+  double ex = block_exclusive_scan<double, BLOCK>(loc, red, &tot);
+  for (int j = 0; j < per; ++j) if (s0 + j < Q) { pref[s0 + j] = ex; ex += cand[s0 + j]; }
+  if (threadIdx.x == 0) pref[Q] = tot;
+  __syncthreads();
+}
+
+// Phi evaluated from the sorted candidate list (valid for theta >= floor).
+struct PhiEval {
+  double phi;
+  int nA, nB;
+  double SA, SB;
+};
+
+__device__ __forceinline__ PhiEval phi_sorted(double th, const double* cand, const double* pref,
+                                              int q, int Q, double rho, double M) {
+  // t0: first t in [0,q) with top_break(cand[t]) < th (top_break non-increasing in t)
+  int lo = 0, hi = q;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (top_break(cand[mid], rho, M) < th) hi = mid; else lo = mid + 1;
+  }
+  const int t0 = lo;
+  // j0: first j in [q,Q) with cand[j] <= th
+  lo = q; hi = Q;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (cand[mid] <= th) hi = mid; else lo = mid + 1;
+  }
+  const int j0 = lo;
+  PhiEval e;
+  e.nA = q - t0;
+  e.SA = pref[q] - pref[t0];
+  e.nB = j0 - q;
+  e.SB = pref[j0] - pref[q];
+  e.phi = (double)e.nA * (th + fmin(rho * th, M)) - e.SA - (e.SB - (double)e.nB * th);
+  return e;
+}
+
+// Root of the linear piece with the given active sets.
+__device__ __forceinline__ double solve_piece(int nA, double SA, int nB, double SB, bool rho_branch,
+                                              double rho, double M) {
+  if (rho_branch) return (SA + SB) / ((double)nA * (1.0 + rho) + (double)nB);
+  return (SA + SB - (double)nA * M) / (double)(nA + nB);
+}
+
+// Bracket the root on the sorted candidates.  Returns false if the root lies
+// below `floorv` (more candidates needed).  All threads call it.
+template <int BLOCK>
+__device__ bool root_from_sorted(const double* cand, const double* pref, int q, int Q, double floorv,
+                                 double rho, double M, double* red, double* theta_out) {
+  const double thM = M / rho;
+  // candidate breakpoints: idx in [0, Q) (top: top_break, tail: value), Q: floor, Q+1: M/rho
+  double lo = -1.0, hi = INFINITY;
+  for (int e = threadIdx.x; e < Q + 2; e += BLOCK) {
+    double th;
+    if (e < q) th = top_break(cand[e], rho, M);
+    else if (e < Q) th = cand[e];
+    else if (e == Q) th = floorv;
+    else th = thM;
+    if (th < floorv) continue;
+    PhiEval v = phi_sorted(th, cand, pref, q, Q, rho, M);
+    if (v.phi <= 0.0) lo = fmax(lo, th);
+    if (v.phi >= 0.0) hi = fmin(hi, th);
+  }
+  lo = block_max<double, BLOCK>(lo, red, -1.0);
+  hi = block_min<double, BLOCK>(hi, red, INFINITY);
+  if (lo < floorv) return false;  // Phi(floor) > 0: the pooled block extends below the candidates
+  double th;
+  if (!(hi > lo)) {
+    th = hi <= lo ? (isinf(hi) ? lo : hi) : lo;
+  } else {
+    const double mid = 0.5 * (lo + hi);
+    PhiEval v = phi_sorted(mid, cand, pref, q, Q, rho, M);
+    th = solve_piece(v.nA, v.SA, v.nB, v.SB, rho * mid < M, rho, M);
+    th = fmin(fmax(th, lo), hi);
+  }
+  *theta_out = th;
+  return true;
+}
+
+// ------------------------------------------------------------------------
+// The prox of one segment.
+
+template <typename T>
+struct SegIO {
+  int m;
+  const int8_t* state;       // nullptr: all coordinates free
+  const T* w;                // direct input, or nullptr to form w from the FISTA state:
+  const T* bc;               //   gamma = bc + c (bc - bp);  w = gamma - grad / L
+  const T* bp;
+  const T* grad;
+  double c, invL;
+  double rho, M;
+  int kp;
+  T* wbuf;                   // global scratch (length m) used when sm.wsm == nullptr
+  T* beta;                   // output, length m
+  int* nnz_idx;              // optional ordered compaction of beta's nonzeros
+  T* nnz_val;
+  int nnz_cap;               // 0: do not compact
+  int* top_out;              // optional: the top-k' indices in sorted order
+  int qhint;
+};
+
+struct SegOut {
+  double g, theta, l1, sbar;
+  int nnz, qused, fallback;
+};
+
+// Full-pass bracketed Newton on Phi (for pooled blocks wider than the
+// candidate capacity).  T members: keys > thr_k plus need_k of the keys equal
+// to thr_k; tail: the rest.  hi0 has Phi(hi0) > 0.
+template <typename T, int BLOCK, typename KeyVal>
+__device__ double root_fullpass(int m, KeyVal keyval, double thr_k, int need_k, int eq_k,
+                                double hi0, double rho, double M, double* red) {
+  double lo = 0.0, hi = hi0, th = hi0;
+  for (int it = 0; it < 200; ++it) {
+    double nA = 0, SA = 0, nB = 0, SB = 0;
+    for (int i = threadIdx.x; i < m; i += BLOCK) {
+      const double a = keyval(i);
+      if (a > thr_k) {
+        if (top_break(a, rho, M) < th) { nA += 1; SA += a; }
+      } else if (a == thr_k) {
+        // need_k copies belong to the top set, eq_k - need_k to the tail
+      } else if (a > th) { nB += 1; SB += a; }
+    }
+    nA = block_sum<double, BLOCK>(nA, red);
+    SA = block_sum<double, BLOCK>(SA, red);
+    nB = block_sum<double, BLOCK>(nB, red);
+    SB = block_sum<double, BLOCK>(SB, red);
+    if (top_break(thr_k, rho, M) < th) { nA += need_k; SA += need_k * thr_k; }
+    if (thr_k > th) { nB += (eq_k - need_k); SB += (eq_k - need_k) * thr_k; }
+    const double phi = nA * (th + fmin(rho * th, M)) - SA - (SB - nB * th);
+    if (phi == 0.0) return th;
+    if (phi < 0.0) lo = th; else hi = th;
+    double cand = solve_piece((int)nA, SA, (int)nB, SB, rho * th < M, rho, M);
+    const bool newton_ok = (nA + nB > 0) && cand > lo && cand < hi;
+    const double next = newton_ok ? cand : 0.5 * (lo + hi);
+    // the Newton step from the piece containing th lands on th itself: th is the
+    // root of a piece that is active at th, hence the root of Phi
+    if (newton_ok && it > 0 && fabs(next - th) <= 2e-15 * fabs(th)) return next;
+    if (hi - lo <= 2e-16 * hi) return newton_ok ? next : hi;
+    th = next;
+  }
+  return th;
+}
+
+template <typename T, int BLOCK>
+__device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
+  using B = Bits<T>;
+  using U = typename B::U;
+  const int m = io.m;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T* wv = sm.wsm ? sm.wsm : io.wbuf;
+  const double rho = io.rho, M = io.M;
+
+  // pass 1: w (rounded to T), the fixed coordinates' outputs
+  double s1sq = 0.0;
+  for (int i = threadIdx.x; i < m; i += BLOCK) {
+    double w;
+    if (io.w) w = to_d(io.w[i]);
+    else {
+      const double b = to_d(io.bc[i]);
+      w = b + io.c * (b - to_d(io.bp[i])) - to_d(io.grad[i]) * io.invL;
+    }
+    const int8_t st = io.state ? io.state[i] : (int8_t)kFree;
+    if (st == kFree) {
+      wv[i] = (T)w;
+    } else {
+      wv[i] = T(0);
+      if (st == kZero) {
+        io.beta[i] = T(0);
+      } else {  // z_j = 1: argmin 1/2 (b - w)^2 + 1/(2 rho) b^2 on the box
+        double b = fmin(fmax(rho * w / (1.0 + rho), -M), M);
+        T bt = (T)b;
+        io.beta[i] = bt;
+        s1sq += to_d(bt) * to_d(bt);
+      }
+    }
+  }
+  s1sq = block_sum<double, BLOCK>(s1sq, sm.red);
+
+  auto keybits = [&](int i) -> U { return abs_bits<T>(wv[i]); };
+  auto keyval = [&](int i) -> double { return fabs(to_d(wv[i])); };
+
+  SegOut out;
+  out.fallback = 0;
+  out.qused = 0;
+  const int kp = io.kp;
+  const int q = kp < m ? kp : m;
+  double thr_k = INFINITY;
+  int need_k = 0, eq_k = 0;
+  double theta = INFINITY;   // k' = 0: every free coordinate is soft-thresholded to 0
+  bool cand_sorted = false;  // cand[0..q) holds the top-q values, descending
+
+  if (q > 0) {
+    SelectResult<U> Rk = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
+    thr_k = to_d(B::val(Rk.thr));
+    need_k = q - Rk.gt;
+    eq_k = Rk.eq;
+    if (q == m) {
+      theta = 0.0;  // no tail: no isotonic violation
+    } else {
+      int Q = io.qhint > q + 1 ? io.qhint : q + 1;
+      if (Q > m) Q = m;
+      bool found = false;
+      double last_floor = INFINITY;
+      while (!found && Q <= sm.cap) {
+        double floorv = 0.0;
+        if (Q < m) {
+          SelectResult<U> RQ = block_select<U, BLOCK>(m, Q, keybits, sm.hist, sm.sh);
+          floorv = to_d(B::val(RQ.thr));
+          if (threadIdx.x == 0) sm.sh[40] = 0;
+          __syncthreads();
+          for (int i = threadIdx.x; i < m; i += BLOCK) {
+            U kb = keybits(i);
+            if (kb > RQ.thr) {
+              int pos = atomicAdd(&sm.sh[40], 1);
+              sm.cand[pos] = to_d(B::val(kb));
+            }
+          }
+          __syncthreads();
+          for (int j = RQ.gt + threadIdx.x; j < Q; j += BLOCK) sm.cand[j] = floorv;
+        } else {
+          for (int i = threadIdx.x; i < m; i += BLOCK) sm.cand[i] = keyval(i);
+        }
+        const int N = next_pow2(Q);
+        for (int j = Q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+        __syncthreads();
+        block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+        block_prefix<BLOCK>(sm.cand, sm.pref, Q, sm.red);
+        found = root_from_sorted<BLOCK>(sm.cand, sm.pref, q, Q, floorv, rho, M, sm.red, &theta);
+        out.qused = Q;
+        last_floor = floorv;
+        if (!found) {
+          if (Q == m) break;  // cannot happen: Phi(0) <= 0
+          Q = (4 * Q < m) ? 4 * Q : m;
+        }
+      }
+      if (found) {
+        cand_sorted = true;
+      } else {
+        out.fallback = 1;
+        theta = root_fullpass<T, BLOCK>(m, keyval, thr_k, need_k, eq_k,
+                                        isinf(last_floor) ? thr_k : last_floor, rho, M, sm.red);
+      }
+    }
+  }
+  out.theta = theta;
+
+  // ---- ordered passes: warp w owns the contiguous chunk [w*chunk, (w+1)*chunk)
+  const int nw = BLOCK / 32;
+  const int chunk = (((m + nw - 1) / nw) + 31) & ~31;
+  const int c0 = wid * chunk;
+  const int c1 = min(m, c0 + chunk);
+  const bool tie_split = (q > 0) && (need_k < eq_k);
+  int tie_base = 0;
+  if (tie_split) {  // rank of tied keys in index order
+    int cnt = 0;
+    for (int base = c0; base < c1; base += 32) {
+      const int i = base + lane;
+      const bool t = (i < c1) && keyval(i) == thr_k && (io.state == nullptr || io.state[i] == kFree);
+      cnt += __popc(__ballot_sync(0xffffffffu, t));
+    }
+    int tot;
+    int ex = block_exclusive_scan<int, BLOCK>(lane == 0 ? cnt : 0, sm.sh, &tot);
+    tie_base = __shfl_sync(0xffffffffu, ex, 0);
+  }
+  // main output pass
+  const double shrink = rho / (1.0 + rho);
+  double l1 = 0.0;
+  int nzc = 0, tie_run = 0;
+  for (int base = c0; base < c1; base += 32) {
+    const int i = base + lane;
+    const bool valid = i < c1;
+    const int8_t st = (valid && io.state) ? io.state[i] : (int8_t)kFree;
+    double a = valid ? keyval(i) : 0.0;
+    bool tie = valid && st == kFree && q > 0 && a == thr_k;
+    int tie_rank = 0;
+    if (tie_split) {
+      const unsigned bal = __ballot_sync(0xffffffffu, tie);
+      tie_rank = tie_base + tie_run + __popc(bal & ((1u << lane) - 1u));
+      tie_run += __popc(bal);
+    }
+    bool nz = false;
+    if (valid) {
+      if (st == kFree) {
+        const bool in_top = (q > 0) && (a > thr_k || (tie && (!tie_split || tie_rank < need_k)));
+        double mag;
+        if (in_top) mag = fmin(fmin(M, shrink * a), a - theta);
+        else mag = fmax(0.0, a - theta);
+        if (!(mag > 0.0)) mag = 0.0;
+        const T wt = wv[i];
+        const T bt = (T)(to_d(wt) < 0 ? -mag : mag);
+        io.beta[i] = bt;
+        l1 += fabs(to_d(bt));
+        nz = mag > 0.0;
+      } else {
+        nz = to_d(io.beta[i]) != 0.0;
+      }
+    }
+    nzc += __popc(__ballot_sync(0xffffffffu, nz));
+  }
+  l1 = block_sum<double, BLOCK>(l1, sm.red);
+  {
+    int tot;
+    int ex = block_exclusive_scan<int, BLOCK>(lane == 0 ? nzc : 0, sm.sh, &tot);
+    const int nz_base = __shfl_sync(0xffffffffu, ex, 0);
+    out.nnz = tot;
+    if (io.nnz_cap > 0 && tot <= io.nnz_cap) {
+      __syncthreads();
+      int run = 0;
+      for (int base = c0; base < c1; base += 32) {
+        const int i = base + lane;
+        T v = (i < c1) ? io.beta[i] : T(0);
+        const bool nz = to_d(v) != 0.0;
+        const unsigned bal = __ballot_sync(0xffffffffu, nz);
+        if (nz) {
+          const int pos = nz_base + run + __popc(bal & ((1u << lane) - 1u));
+          io.nnz_idx[pos] = i;
+          io.nnz_val[pos] = v;
+        }
+        run += __popc(bal);
+      }
+    }
+  }
+  out.l1 = l1;
+
+  // ---- g(beta) (Algorithm 2) on the prox output: the top-k' of |beta| are the
+  // top-k' of |w| (the prox preserves the order of the magnitudes), and
+  // |b_t| = min(M, rho a_t/(1+rho), a_t - theta) is monotone in a_t.
+  double g = 0.5 * s1sq, sbar = 0.0;
+  if (q > sm.cap) g = NAN;  // the host rejects k' beyond the candidate capacity
+  if (q > 0 && q <= sm.cap) {
+    if (!cand_sorted) {  // gather the top-q values and sort them
+      if (threadIdx.x == 0) sm.sh[40] = 0;
+      __syncthreads();
+      const U tb = B::of((T)thr_k);
+      for (int i = threadIdx.x; i < m; i += BLOCK) {
+        U kb = keybits(i);
+        if (kb > tb) { int pos = atomicAdd(&sm.sh[40], 1); sm.cand[pos] = to_d(B::val(kb)); }
+      }
+      __syncthreads();
+      for (int j = (q - need_k) + threadIdx.x; j < q; j += BLOCK) sm.cand[j] = thr_k;
+      const int N = next_pow2(q);
+      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+      __syncthreads();
+      block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+    }
+    // |b_t| into cand (in place), prefix sums in pref
+    for (int t = threadIdx.x; t < q; t += BLOCK) {
+      const double a = sm.cand[t];
+      double mg = fmin(fmin(M, shrink * a), a - theta);
+      sm.cand[t] = mg > 0.0 ? to_d((T)mg) : 0.0;
+    }
+    __syncthreads();
+    block_prefix<BLOCK>(sm.cand, sm.pref, q, sm.red);
+    int jst = q;
+    for (int j = threadIdx.x; j < q; j += BLOCK) {
+      const double sb = (l1 - sm.pref[j]) / (double)(kp - j);
+      if (sb >= sm.cand[j]) jst = min(jst, j);
+    }
+    jst = block_min<int, BLOCK>(jst, sm.sh, q);
+    double sq = 0.0;
+    for (int j = threadIdx.x; j < jst; j += BLOCK) sq += sm.cand[j] * sm.cand[j];
+    sq = block_sum<double, BLOCK>(sq, sm.red);
+    sbar = (jst < kp) ? fmax(0.0, (l1 - sm.pref[jst]) / (double)(kp - jst)) : 0.0;
+    g += 0.5 * (sq + (double)(kp - jst) * sbar * sbar);
+  }
+  out.g = g;
+  out.sbar = sbar;
+
+  // ---- optional: the top-k' indices in sorted order (stable: ties by index)
+  if (io.top_out && q > 0 && q <= sm.cap) {
+    if (threadIdx.x == 0) sm.sh[40] = 0;
+    __syncthreads();
+    // members: keys > thr_k, plus the first need_k tied keys in index order
+    int run = 0;
+    for (int base = c0; base < c1; base += 32) {
+      const int i = base + lane;
+      const bool valid = i < c1;
+      const bool fr = valid && (io.state == nullptr || io.state[i] == kFree);
+      const double a = valid ? keyval(i) : 0.0;
+      const bool tie = fr && a == thr_k;
+      const unsigned bal = __ballot_sync(0xffffffffu, tie);
+      const int rank = tie_base + run + __popc(bal & ((1u << lane) - 1u));
+      run += __popc(bal);
+      const bool mem = fr && (a > thr_k || (tie && (!tie_split || rank < need_k)));
+      if (mem) {
+        int pos = atomicAdd(&sm.sh[40], 1);
+        sm.cand[pos] = a;
+        sm.cidx[pos] = i;
+      }
+    }
+    __syncthreads();
+    const int N = next_pow2(q);
+    for (int j = q + threadIdx.x; j < N; j += BLOCK) { sm.cand[j] = -1.0; sm.cidx[j] = 0x7fffffff; }
+    __syncthreads();
+    // bitonic sort of (value desc, index asc)
+    for (int size = 2; size <= N; size <<= 1) {
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < (N >> 1); i += BLOCK) {
+          const int lo = 2 * i - (i & (stride - 1));
+          const int hi = lo + stride;
+          const bool desc = ((lo & size) == 0);
+          const double a = sm.cand[lo], b = sm.cand[hi];
+          const int ia = sm.cidx[lo], ib = sm.cidx[hi];
+          const bool a_before_b = (a > b) || (a == b && ia < ib);
+          if (a_before_b != desc) {
+            sm.cand[lo] = b; sm.cand[hi] = a; sm.cidx[lo] = ib; sm.cidx[hi] = ia;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int t = threadIdx.x; t < q; t += BLOCK) io.top_out[t] = sm.cidx[t];
+    __syncthreads();
+  }
+  return out;
+}
+
+// ------------------------------------------------------------------------
+// g(beta) of a node by Algorithm 2 (partial sort to the top k', water-filling).
+// Optionally the relaxed z (from the proof of Thm 3.6): z_j = min(1, |b_j|/sbar)
+// on the free coordinates, 1 on S1, 0 on S0.
+
+struct GOut {
+  double g, sbar, l1;
+  int infeasible;
+};
+
+template <typename T, int BLOCK, typename LoadB>
+__device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, double M,
+                               const SegSmem<T>& sm, double* z_out) {
+  using B = Bits<double>;
+  using U = typename B::U;
+  double l1 = 0.0, s1sq = 0.0, linf = 0.0;
+  int bad = 0;
+  for (int i = threadIdx.x; i < m; i += BLOCK) {
+    const int8_t st = state ? state[i] : (int8_t)kFree;
+    const double b = loadb(i);
+    if (st == kFree) { l1 += fabs(b); linf = fmax(linf, fabs(b)); }
+    else if (st == kOne) { s1sq += b * b; linf = fmax(linf, fabs(b)); }
+    else if (b != 0.0) bad = 1;
+  }
+  l1 = block_sum<double, BLOCK>(l1, sm.red);
+  s1sq = block_sum<double, BLOCK>(s1sq, sm.red);
+  linf = block_max<double, BLOCK>(linf, sm.red, 0.0);
+  bad = block_max<int, BLOCK>(bad, sm.sh, 0);
+  GOut o;
+  o.l1 = l1;
+  o.sbar = 0.0;
+  o.infeasible = 0;
+  const double kM = (double)(kp > 0 ? kp : 0) * M;
+  if (bad || kp < 0 || linf > M * (1.0 + 1e-12) || l1 > kM * (1.0 + 1e-12)) {
+    o.infeasible = 1;
+    o.g = INFINITY;
+  } else {
+    double g = 0.5 * s1sq, sbar = 0.0;
+    const int q = kp < m ? kp : m;
+    if (q > sm.cap) g = NAN;  // the host rejects k' beyond the candidate capacity
+    if (q > 0 && q <= sm.cap) {
+      auto keybits = [&](int i) -> U {
+        const int8_t st = state ? state[i] : (int8_t)kFree;
+        return st == kFree ? B::of(fabs(loadb(i))) : (U)0;
+      };
+      SelectResult<U> R = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
+      if (threadIdx.x == 0) sm.sh[40] = 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += BLOCK) {
+        U kb = keybits(i);
+        if (kb > R.thr) { int pos = atomicAdd(&sm.sh[40], 1); sm.cand[pos] = B::val(kb); }
+      }
+      __syncthreads();
+      const double thr = B::val(R.thr);
+      for (int j = R.gt + threadIdx.x; j < q; j += BLOCK) sm.cand[j] = thr;
+      const int N = next_pow2(q);
+      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+      __syncthreads();
+      block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+      block_prefix<BLOCK>(sm.cand, sm.pref, q, sm.red);
+      int jst = q;
+      for (int j = threadIdx.x; j < q; j += BLOCK) {
+        const double sb = (l1 - sm.pref[j]) / (double)(kp - j);
+        if (sb >= sm.cand[j]) jst = min(jst, j);
+      }
+      jst = block_min<int, BLOCK>(jst, sm.sh, q);
+      double sq = 0.0;
+      for (int j = threadIdx.x; j < jst; j += BLOCK) sq += sm.cand[j] * sm.cand[j];
+      sq = block_sum<double, BLOCK>(sq, sm.red);
+      sbar = (jst < kp) ? fmax(0.0, (l1 - sm.pref[jst]) / (double)(kp - jst)) : 0.0;
+      g += 0.5 * (sq + (double)(kp - jst) * sbar * sbar);
+    }
+    o.g = g;
+    o.sbar = sbar;
+  }
+  if (z_out) {
+    for (int i = threadIdx.x; i < m; i += BLOCK) {
+      const int8_t st = state ? state[i] : (int8_t)kFree;
+      const double b = fabs(loadb(i));
+      double z;
+      if (st == kOne) z = 1.0;
+      else if (st == kZero) z = 0.0;
+      else if (o.sbar > 0.0) z = fmin(1.0, b / o.sbar);
+      else z = b > 0.0 ? 1.0 : 0.0;
+      z_out[i] = z;
+    }
+  }
+  __syncthreads();
+  return o;
+}
+
+// ------------------------------------------------------------------------
+// TopSum_{k'}(H_M(|a_F| * scale)) + sum_{S1} H_M(|a_j| * scale)   (Lemma 3.1 on
+// the node, with the separable-sum rule for S1).  Keys are read in T.
+
+template <typename T, int BLOCK, typename LoadA>
+__device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp, double M,
+                                double scale, const SegSmem<T>& sm) {
+  using B = Bits<T>;
+  using U = typename B::U;
+  double s1 = 0.0;
+  for (int i = threadIdx.x; i < m; i += BLOCK)
+    if (state && state[i] == kOne) s1 += huber(fabs(to_d(loada(i))) * scale, M);
+  s1 = block_sum<double, BLOCK>(s1, sm.red);
+  const int q = kp < m ? kp : m;
+  if (q <= 0) return s1;
+  auto keybits = [&](int i) -> U {
+    const int8_t st = state ? state[i] : (int8_t)kFree;
+    return st == kFree ? abs_bits<T>(loada(i)) : (U)0;
+  };
+  SelectResult<U> R = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
+  const double thr = to_d(B::val(R.thr));
+  double s = 0.0;
+  for (int i = threadIdx.x; i < m; i += BLOCK) {
+    U kb = keybits(i);
+    if (kb > R.thr) s += huber(to_d(B::val(kb)) * scale, M);
+  }
+  s = block_sum<double, BLOCK>(s, sm.red);
+  return s1 + s + (double)(q - R.gt) * huber(thr * scale, M);
+}
+
+}  // namespace ksc

@@ -1,0 +1,281 @@
+"""ctypes binding of the C ABI declared in ``include/ksc.h``.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``_build/libksc.so``.  There is no fallback -- importing this module raises if
+the library has not been built (``python -m paper_2502_09502_gb300.build``).
+The functions keep the C names (``ksc_problem_create``, ``ksc_solve_node`` ...);
+``Problem`` and ``Node`` are small conveniences over them.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libksc.so")
+
+KSC_OK, KSC_ERR_INVALID_ARG, KSC_ERR_OOM, KSC_ERR_ADMISSION = 0, 1, 2, 3
+KSC_ERR_INFEASIBLE_NODE, KSC_NOT_CONVERGED, KSC_ERR_TIMEOUT = 4, 5, 6
+KSC_ERR_CUDA, KSC_ERR_UNIMPLEMENTED = 7, 8
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "admission", 4: "infeasible_node",
+                5: "not_converged", 6: "timeout", 7: "cuda", 8: "unimplemented"}
+KSC_LOSS_LSQ, KSC_LOSS_LOGISTIC = 0, 1
+KSC_F64, KSC_F32, KSC_BF16 = 0, 1, 2
+KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF = 1, 2
+KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
+
+# every symbol include/ksc.h declares
+EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
+           "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
+           "ksc_problem_profile", "ksc_problem_kernel_time", "ksc_last_error", "ksc_version"]
+
+
+class KscError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("x_dtype", C.c_int), ("X", C.c_void_p),
+                ("ldx", C.c_int64), ("y", C.POINTER(C.c_double)), ("loss", C.c_int),
+                ("x_on_device", C.c_int32), ("lipschitz", C.c_double)]
+
+
+class NodeC(C.Structure):
+    _fields_ = [("lambda2", C.c_double), ("M", C.c_double), ("k", C.c_int32),
+                ("fixed_zero", C.POINTER(C.c_int32)), ("n_zero", C.c_int32),
+                ("fixed_one", C.POINTER(C.c_int32)), ("n_one", C.c_int32),
+                ("warm_beta", C.POINTER(C.c_double)), ("incumbent", C.c_double),
+                ("rel_gap_tol", C.c_double), ("max_iter", C.c_int32), ("flags", C.c_uint32)]
+
+
+class ResultC(C.Structure):
+    _fields_ = [("beta", C.POINTER(C.c_double)), ("z", C.POINTER(C.c_double)),
+                ("primal", C.c_double), ("dual_bound", C.c_double), ("rel_gap", C.c_double),
+                ("iters", C.c_int32), ("restarts", C.c_int32), ("pruned", C.c_int32),
+                ("status", C.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                          "(python -m paper_2502_09502_gb300.build)")
+    L = C.CDLL(LIB_PATH)
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    L.ksc_problem_create.argtypes = [C.POINTER(ProblemDesc), C.c_void_p, C.POINTER(C.c_void_p)]
+    L.ksc_problem_destroy.argtypes = [C.c_void_p]
+    L.ksc_problem_bytes.argtypes = [C.c_void_p]
+    L.ksc_problem_bytes.restype = C.c_size_t
+    L.ksc_problem_info.argtypes = [C.c_void_p, dp, ip]
+    L.ksc_solve_node.argtypes = [C.c_void_p, C.POINTER(NodeC), C.POINTER(ResultC), C.c_void_p]
+    L.ksc_solve_batch.argtypes = [C.c_void_p, C.POINTER(NodeC), C.c_int32, C.POINTER(ResultC),
+                                  C.c_void_p]
+    L.ksc_prox_g.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, C.c_double, dp, ip]
+    L.ksc_g_value.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, dp, dp]
+    L.ksc_gstar.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, dp]
+    L.ksc_problem_profile.argtypes = [C.c_void_p, C.c_int32]
+    L.ksc_problem_kernel_time.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), dp,
+                                          C.c_int32]
+    L.ksc_last_error.restype = C.c_char_p
+    L.ksc_version.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("ksc_problem_bytes", "ksc_last_error", "ksc_version"):
+            getattr(L, name).restype = C.c_int   # ksc_status
+    return L
+
+
+lib = _load()
+
+
+def ksc_last_error() -> str:
+    return lib.ksc_last_error().decode()
+
+
+def ksc_version() -> str:
+    return lib.ksc_version().decode()
+
+
+def _check(st, allowed=(KSC_OK,)):
+    if st not in allowed:
+        raise KscError(st, ksc_last_error())
+    return st
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- C names
+
+def ksc_problem_create(desc: ProblemDesc, stream=None):
+    h = C.c_void_p()
+    _check(lib.ksc_problem_create(C.byref(desc), _stream_ptr(stream), C.byref(h)))
+    return h
+
+
+def ksc_problem_destroy(h):
+    return lib.ksc_problem_destroy(h)
+
+
+def ksc_problem_bytes(h) -> int:
+    return int(lib.ksc_problem_bytes(h))
+
+
+def ksc_problem_info(h):
+    L = C.c_double()
+    it = C.c_int32()
+    _check(lib.ksc_problem_info(h, C.byref(L), C.byref(it)))
+    return L.value, it.value
+
+
+def ksc_solve_node(h, node: NodeC, res: ResultC, stream=None):
+    return lib.ksc_solve_node(h, C.byref(node), C.byref(res), _stream_ptr(stream))
+
+
+def ksc_solve_batch(h, nodes, results, stream=None):
+    return lib.ksc_solve_batch(h, nodes, len(nodes), results, _stream_ptr(stream))
+
+
+def ksc_prox_g(w, k, M, rho, want_top=True):
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    p = w.size
+    out = np.zeros(p)
+    q = min(int(k), p)
+    top = np.full(max(q, 1), -1, dtype=np.int32)
+    _check(lib.ksc_prox_g(_dptr(w), p, int(k), float(M), float(rho), _dptr(out),
+                          top.ctypes.data_as(C.POINTER(C.c_int32)) if want_top else None))
+    return out, top[:q]
+
+
+def ksc_g_value(beta, k, M, want_z=True):
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    g = C.c_double()
+    z = np.zeros(b.size)
+    _check(lib.ksc_g_value(_dptr(b), b.size, int(k), float(M), C.byref(g),
+                           _dptr(z) if want_z else None))
+    return (g.value, z) if want_z else g.value
+
+
+def ksc_gstar(a, k, M):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    out = C.c_double()
+    _check(lib.ksc_gstar(_dptr(a), a.size, int(k), float(M), C.byref(out)))
+    return out.value
+
+
+def ksc_problem_profile(h, enable: bool):
+    _check(lib.ksc_problem_profile(h, int(bool(enable))))
+
+
+def ksc_problem_kernel_time(h, kernel, reset=False):
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(lib.ksc_problem_kernel_time(h, int(kernel), C.byref(n), C.byref(ms), int(bool(reset))))
+    return n.value, ms.value
+
+
+# ---------------------------------------------------------------- helpers
+
+_DT = {np.dtype(np.float64): KSC_F64, np.dtype(np.float32): KSC_F32, np.dtype(np.uint16): KSC_BF16}
+
+
+@dataclass
+class Result:
+    beta: np.ndarray | None
+    z: np.ndarray | None
+    primal: float
+    dual_bound: float
+    rel_gap: float
+    iters: int
+    restarts: int
+    pruned: bool
+    status: str
+
+
+class Node:
+    """A branch-and-bound node (fixed sets S0/S1) with its solve parameters."""
+
+    def __init__(self, lambda2, M, k, fixed_zero=(), fixed_one=(), warm_beta=None,
+                 incumbent=math.inf, rel_gap_tol=1e-6, max_iter=100000, flags=0):
+        self.zero = np.ascontiguousarray(fixed_zero, dtype=np.int32)
+        self.one = np.ascontiguousarray(fixed_one, dtype=np.int32)
+        self.warm = None if warm_beta is None else np.ascontiguousarray(warm_beta, dtype=np.float64)
+        self.c = NodeC(float(lambda2), float(M), int(k),
+                       self.zero.ctypes.data_as(C.POINTER(C.c_int32)) if self.zero.size else None,
+                       int(self.zero.size),
+                       self.one.ctypes.data_as(C.POINTER(C.c_int32)) if self.one.size else None,
+                       int(self.one.size),
+                       _dptr(self.warm) if self.warm is not None else None,
+                       float(incumbent), float(rel_gap_tol), int(max_iter), int(flags))
+
+
+class Problem:
+    """Owns a ksc_problem handle.  X: numpy array (copied to the device; bf16 as
+    uint16 bits) or a CUDA torch tensor (borrowed: kept alive by this object)."""
+
+    def __init__(self, X, y, loss=KSC_LOSS_LSQ, lipschitz=0.0, stream=None, x_dtype=None):
+        self._keep = []
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        if hasattr(X, "data_ptr"):  # torch tensor on the device
+            import torch
+            assert X.is_cuda and X.is_contiguous()
+            code = {torch.float64: KSC_F64, torch.float32: KSC_F32, torch.bfloat16: KSC_BF16}[X.dtype]
+            ptr, on_dev = X.data_ptr(), 1
+            n, p = X.shape
+            self._keep.append(X)
+        else:
+            X = np.ascontiguousarray(X)
+            code = _DT[X.dtype] if x_dtype is None else x_dtype
+            ptr, on_dev = X.ctypes.data, 0
+            n, p = X.shape
+            self._keep.append(X)
+        self.n, self.p = int(n), int(p)
+        self._keep.append(y)
+        self.desc = ProblemDesc(self.n, self.p, code, ptr, self.p, _dptr(y), int(loss), on_dev,
+                                float(lipschitz))
+        self.h = ksc_problem_create(self.desc, stream)
+        self.stream = stream
+
+    def close(self):
+        if getattr(self, "h", None):
+            ksc_problem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    @property
+    def L(self):
+        return ksc_problem_info(self.h)[0]
+
+    @property
+    def power_iters(self):
+        return ksc_problem_info(self.h)[1]
+
+    @property
+    def bytes(self):
+        return ksc_problem_bytes(self.h)
+
+    def solve(self, node: Node, want_beta=True, want_z=True, allow=(KSC_OK, KSC_NOT_CONVERGED,
+                                                                      KSC_ERR_INFEASIBLE_NODE)):
+        beta = np.zeros(self.p) if want_beta else None
+        z = np.zeros(self.p) if want_z else None
+        res = ResultC(_dptr(beta) if want_beta else None, _dptr(z) if want_z else None)
+        st = ksc_solve_node(self.h, node.c, res, self.stream)
+        _check(st, allow)
+        return Result(beta, z, res.primal, res.dual_bound, res.rel_gap, res.iters, res.restarts,
+                      bool(res.pruned), STATUS_NAMES[res.status if st == KSC_OK else st])

@@ -1,0 +1,83 @@
+"""The C ABI library loads and exports every function include/ksc.h declares;
+argument checks that return before any CUDA call work without a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "ksc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ksc_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def ksc():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_09502_gb300 import ksc as K
+    return K
+
+
+def test_every_declared_symbol_is_exported(ksc):
+    decl = _declared()
+    assert len(decl) >= 13
+    for name in decl:
+        assert hasattr(ksc.lib, name), name
+    assert set(decl) <= set(ksc.EXPORTS) | {"ksc_last_error", "ksc_version"}
+
+
+def test_version_and_error_strings(ksc):
+    assert "sm_103a" in ksc.ksc_version()
+    assert isinstance(ksc.ksc_last_error(), str)
+
+
+def test_invalid_arguments_are_rejected_before_cuda(ksc):
+    out = C.c_void_p(123)
+    assert ksc.lib.ksc_problem_create(None, None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert out.value is None
+    y = np.zeros(3)
+    d = ksc.ProblemDesc(0, 4, ksc.KSC_F64, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "n and p" in ksc.ksc_last_error()
+    d = ksc.ProblemDesc(3, 4, 9, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 2, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "ldx" in ksc.ksc_last_error()
+    yl = np.array([1.0, 0.5, -1.0])
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 4, yl.ctypes.data_as(C.POINTER(C.c_double)),
+                        ksc.KSC_LOSS_LOGISTIC, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "labels" in ksc.ksc_last_error()
+    w = np.ones(4)
+    dp = C.POINTER(C.c_double)
+    assert ksc.lib.ksc_prox_g(w.ctypes.data_as(dp), 4, 2, 1.0, -1.0, w.ctypes.data_as(dp),
+                              None) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_prox_g(None, 4, 2, 1.0, 1.0, w.ctypes.data_as(dp), None) == \
+        ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_prox_g(w.ctypes.data_as(dp), 0, 2, 1.0, 1.0, w.ctypes.data_as(dp),
+                              None) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_g_value(w.ctypes.data_as(dp), 4, -1, 1.0, w.ctypes.data_as(dp), None) == \
+        ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_gstar(w.ctypes.data_as(dp), 4, 1, 0.0, w.ctypes.data_as(dp)) == \
+        ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_solve_node(None, None, None, None) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_problem_info(None, None, None) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_problem_bytes(None) == 0
+    assert ksc.lib.ksc_problem_destroy(None) == ksc.KSC_OK
+
+
+def test_struct_layouts_match_header(ksc):
+    # offsets the C compiler uses for the ABI structs (x86-64 and aarch64 LP64)
+    assert C.sizeof(ksc.ProblemDesc) == 64
+    assert ksc.ProblemDesc.X.offset == 24 and ksc.ProblemDesc.lipschitz.offset == 56
+    assert C.sizeof(ksc.NodeC) == 88
+    assert ksc.NodeC.warm_beta.offset == 56 and ksc.NodeC.flags.offset == 84
+    assert C.sizeof(ksc.ResultC) == 56
+    assert ksc.ResultC.status.offset == 52

@@ -1,0 +1,299 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, on the same seeded inputs.
+
+Tolerances (from the floating-point arithmetic of each path):
+  * FP64 primitives (prox, g, g*): the GPU evaluates the pooled-block threshold
+    form, the oracle the sort + PAVA merge; both are exact up to rounding, so the
+    outputs agree to 1e-11 relative to the input scale.  Integer outputs (the
+    sorted top-k' index set of Alg. 1) are compared bit-exactly.
+  * FP64 solves: objective and certified bound within 1e-6 relative of the
+    oracle's values at a 1e-12 gap; beta within 1e-5 where the solution is unique
+    (n >= p), else u = X beta within 1e-4.
+  * FP32 / BF16 solves: objective and bound within 1e-6 relative; beta (or u)
+    within 1e-4 relative to its max-norm.
+  * The certified bound never exceeds the oracle's primal value (an upper bound
+    on the relaxation optimum).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import ksc_inputs as G
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def K():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2502_09502_gb300 import ksc
+    return ksc
+
+
+# ------------------------------------------------------------------ primitives
+
+def _prox_cases():
+    rng = np.random.default_rng(2024)
+    cases = []
+    for t in range(40):
+        p = int(rng.choice([1, 2, 3, 7, 31, 64, 100, 257, 1000, 4099, 20011]))
+        k = int(rng.integers(0, min(p, 60) + 2))
+        rho = float(10 ** rng.uniform(-2, 3))
+        M = float(10 ** rng.uniform(-1, 1))
+        scale = float(10 ** rng.uniform(-2, 1))
+        tie = t % 5 == 0
+        cases.append((t, p, k, rho, M, scale, tie))
+    return cases
+
+
+@pytest.mark.parametrize("case", _prox_cases(), ids=lambda c: f"p{c[1]}k{c[2]}t{c[0]}")
+def test_prox_primitive_matches_oracle(K, case):
+    t, p, k, rho, M, scale, tie = case
+    rng = np.random.default_rng(10_000 + t)
+    w = rng.standard_normal(p) * scale
+    if tie:
+        w = np.round(w / scale, 1) * scale
+    beta, top = K.ksc_prox_g(w, k, M, rho)
+    ref, perm = O.prox_g(w, k, rho, M)
+    tol = 1e-11 * max(1.0, np.abs(w).max())
+    assert np.max(np.abs(beta - ref)) <= tol
+    q = min(k, p)
+    assert np.array_equal(top, perm[:q].astype(np.int32))
+
+
+def test_prox_primitive_wide_pooled_block_fallback(K):
+    # values nearly equal and a small rho: the pooled block takes most of the tail,
+    # beyond the shared-memory candidate capacity -> full-pass root finder
+    rng = np.random.default_rng(7)
+    p, k = 20000, 5
+    w = rng.uniform(0.95, 1.0, p) * np.where(rng.random(p) < 0.5, -1, 1)
+    beta, top = K.ksc_prox_g(w, k, 3.0, 0.01)
+    ref, perm = O.prox_g(w, k, 0.01, 3.0)
+    assert np.count_nonzero(ref) > 4096
+    assert np.max(np.abs(beta - ref)) <= 1e-12
+    assert np.array_equal(top, perm[:k].astype(np.int32))
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_g_value_primitive_matches_oracle(K, seed):
+    rng = np.random.default_rng(300 + seed)
+    p = int(rng.choice([1, 5, 64, 333, 5000]))
+    k = int(rng.integers(1, min(p, 50) + 2))
+    M = float(rng.uniform(0.5, 3))
+    b = rng.uniform(-1, 1, p) * M
+    if np.abs(b).sum() > k * M:
+        b *= 0.97 * k * M / np.abs(b).sum()
+    if seed % 3 == 0:
+        b[rng.random(p) < 0.6] = 0.0
+    g, z = K.ksc_g_value(b, k, M)
+    gr, zr = O.g_value(b, k, M, want_z=True)
+    assert abs(g - gr) <= 1e-12 * max(1.0, gr)
+    nz = b != 0
+    assert np.max(np.abs(z[nz] - zr[nz]), initial=0.0) <= 1e-12
+    assert np.all(z >= 0) and np.all(z <= 1) and z.sum() <= k + 1e-9
+    # infeasible point
+    g_bad, _ = K.ksc_g_value(np.full(p, 1.01 * M), k, M)
+    assert g_bad == math.inf
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_gstar_primitive_matches_oracle(K, seed):
+    rng = np.random.default_rng(400 + seed)
+    p = int(rng.choice([1, 9, 100, 7777]))
+    k = int(rng.integers(0, p + 2))
+    M = float(rng.uniform(0.2, 4))
+    a = rng.standard_normal(p) * 3
+    assert abs(K.ksc_gstar(a, k, M) - O.gstar(a, k, M)) <= 1e-12 * max(1.0, O.gstar(a, k, M))
+
+
+# ------------------------------------------------------------------ solves
+
+def _oracle(P, **kw):
+    return O.solve(P.X64() if P.x_dtype == G.BF16 else P.X, P.y, P.loss, P.lambda2, P.M, P.k,
+                   tol=1e-12, max_iter=200000, **kw)
+
+
+def _rel(a, b):
+    return abs(a - b) / max(1.0, abs(b))
+
+
+def test_small_lsq_f64_configuration_matches_oracle(K):
+    # least squares, FP64, n=500, p=100, k=5, lambda2=1, M=2, Toeplitz 0.5, SNR 5
+    P = G.cfg_small_lsq(seed=0)
+    prob = K.Problem(P.X, P.y, K.KSC_LOSS_LSQ)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-10, max_iter=50000))
+    ref = _oracle(P)
+    assert r.status == "ok" and r.rel_gap <= 1e-10
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.max(np.abs(r.beta - ref.beta)) <= 1e-5
+    assert np.max(np.abs(r.z - ref.z)[np.abs(ref.beta) > 1e-6]) <= 1e-4
+    # the default 1e-6 target
+    r6 = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    assert r6.rel_gap <= 1e-6 and r6.dual_bound <= ref.primal
+    assert _rel(r6.dual_bound, ref.dual) <= 1e-6
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_logistic_f64_matches_oracle(K, seed):
+    P = G.make_problem(400, 90, r=0.5, seed=seed, loss=G.LOGISTIC, k_true=5, x_dtype=G.F64,
+                       lambda2=0.5, M=2.0, k=5)
+    prob = K.Problem(P.X, P.y, K.KSC_LOSS_LOGISTIC)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-10, max_iter=50000))
+    ref = _oracle(P)
+    assert r.status == "ok"
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.max(np.abs(r.beta - ref.beta)) <= 1e-5
+
+
+def test_node_with_fixed_sets_matches_oracle(K):
+    P = G.make_problem(300, 70, r=0.5, seed=3, k_true=6, x_dtype=G.F64, lambda2=0.7, M=1.5, k=6)
+    nz = np.nonzero(P.beta_star)[0]
+    zero = np.array(sorted({int(nz[0]), 3, 11, 40}), np.int32)
+    one = np.array([int(nz[1]), 50], np.int32)
+    state = np.zeros(P.p, np.int8)
+    state[zero] = O.ZERO
+    state[one] = O.ONE
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, fixed_zero=zero, fixed_one=one, rel_gap_tol=1e-10))
+    ref = _oracle(P, state=state)
+    assert r.status == "ok"
+    assert np.all(r.beta[zero] == 0) and np.all(r.z[zero] == 0) and np.all(r.z[one] == 1)
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.max(np.abs(r.beta - ref.beta)) <= 1e-5
+
+
+def test_f32_under_determined_matches_oracle(K):
+    # FP32 X with n < p (beta not unique: compare u = X beta), Toeplitz 0.9
+    P = G.make_problem(700, 1500, r=0.9, seed=4, k_true=10, x_dtype=G.F32, lambda2=0.1, M=1.5,
+                       k=10)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=100000))
+    ref = _oracle(P)
+    assert r.status == "ok" and r.rel_gap <= 1e-6
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    X = P.X.astype(np.float64)
+    u, ur = X @ r.beta, X @ ref.beta
+    assert np.max(np.abs(u - ur)) <= 1e-4 * np.abs(ur).max()
+
+
+def test_bf16_logistic_matches_oracle_on_stored_matrix(K):
+    P = G.make_problem(800, 300, r=0.5, seed=5, loss=G.LOGISTIC, k_true=10, x_dtype=G.BF16,
+                       lambda2=0.05, M=3.0, k=10)
+    prob = K.Problem(P.X, P.y, K.KSC_LOSS_LOGISTIC)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-7, max_iter=100000))
+    ref = _oracle(P)
+    assert r.status == "ok"
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.max(np.abs(r.beta - ref.beta)) <= 1e-4 * max(1.0, np.abs(ref.beta).max())
+
+
+def test_lipschitz_constant_matches_power_iteration(K):
+    P = G.make_problem(400, 120, r=0.7, seed=6, x_dtype=G.F64)
+    prob = K.Problem(P.X, P.y)
+    lam, _ = O.power_iteration(P.X, tol=1e-13)
+    assert abs(prob.L - 2 * lam * 1.01) <= 1e-5 * prob.L
+    Pl = G.make_problem(400, 120, r=0.7, seed=6, x_dtype=G.F32, loss=G.LOGISTIC)
+    probl = K.Problem(Pl.X, Pl.y, K.KSC_LOSS_LOGISTIC)
+    laml, _ = O.power_iteration(Pl.X, tol=1e-13)
+    assert abs(probl.L - 0.25 * laml * 1.01) <= 1e-4 * probl.L
+
+
+def test_ragged_shapes_without_vector_loads(K):
+    # p not a multiple of the vector width, n not a multiple of any tile
+    P = G.make_problem(37, 257, r=0.3, seed=7, k_true=3, x_dtype=G.F32, lambda2=0.3, M=2.0, k=3)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    ref = _oracle(P)
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and r.dual_bound <= ref.primal
+    P2 = G.make_problem(1, 3, seed=8, k_true=1, x_dtype=G.F64, lambda2=1.0, M=1.0, k=1)
+    prob2 = K.Problem(P2.X, P2.y)
+    r2 = prob2.solve(K.Node(P2.lambda2, P2.M, P2.k, rel_gap_tol=1e-9))
+    ref2 = _oracle(P2)
+    assert _rel(r2.dual_bound, ref2.dual) <= 1e-6 and r2.dual_bound <= ref2.primal
+
+
+def test_incumbent_rules_and_infeasible_nodes(K):
+    P = G.make_problem(200, 50, seed=9, k_true=4, x_dtype=G.F64, lambda2=1.0, M=2.0, k=4)
+    prob = K.Problem(P.X, P.y)
+    ref = _oracle(P)
+    pr = prob.solve(K.Node(P.lambda2, P.M, P.k, incumbent=0.5 * ref.dual))
+    assert pr.pruned and pr.dual_bound > 0.5 * ref.dual and pr.dual_bound <= ref.primal
+    lo = prob.solve(K.Node(P.lambda2, P.M, P.k, incumbent=2.0 * ref.primal))
+    assert not lo.pruned and lo.status == "ok" and lo.dual_bound <= ref.primal
+    bad = prob.solve(K.Node(P.lambda2, P.M, 1, fixed_one=[1, 2]))
+    assert bad.status == "infeasible_node" and bad.dual_bound == math.inf
+    over = prob.solve(K.Node(P.lambda2, P.M, P.k, fixed_zero=[3], fixed_one=[3]))
+    assert over.status == "infeasible_node"
+    with pytest.raises(K.KscError):
+        prob.solve(K.Node(P.lambda2, P.M, P.k, fixed_zero=[P.p]))
+    with pytest.raises(K.KscError):
+        prob.solve(K.Node(-1.0, P.M, P.k))
+
+
+def test_max_iter_returns_a_valid_bound(K):
+    P = G.make_problem(300, 80, seed=10, k_true=5, x_dtype=G.F64, lambda2=1.0, M=2.0, k=5)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-14, max_iter=5))
+    ref = _oracle(P)
+    assert r.status == "not_converged" and r.iters == 5
+    assert r.dual_bound <= ref.primal
+
+
+@pytest.mark.parametrize("flags", [1, 3])
+def test_ablations_converge_to_the_same_bound(K, flags):
+    # plain FISTA (restart off) and ISTA (momentum off), Fig. 3
+    P = G.make_problem(200, 40, seed=11, k_true=3, x_dtype=G.F64, lambda2=1.0, M=2.0, k=3)
+    prob = K.Problem(P.X, P.y)
+    base = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-8))
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-8, flags=flags, max_iter=200000))
+    assert r.status == "ok"
+    assert _rel(r.dual_bound, base.dual_bound) <= 1e-6
+    assert r.restarts == 0
+    assert r.iters >= base.iters
+
+
+def test_warm_start_and_determinism(K):
+    P = G.make_problem(300, 120, seed=12, k_true=6, x_dtype=G.F32, lambda2=0.2, M=1.5, k=6)
+    prob = K.Problem(P.X, P.y)
+    a = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    b = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    assert a.dual_bound == b.dual_bound and np.array_equal(a.beta, b.beta) and a.iters == b.iters
+    w = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6,
+                          warm_beta=a.beta + 1e-3 * G.warm_perturbation(P.p, 1, seed=1)[0]))
+    assert w.iters < a.iters
+    assert _rel(w.dual_bound, a.dual_bound) <= 2e-6
+
+
+def test_device_resident_matrix_is_borrowed(K):
+    import torch
+    P = G.make_problem(256, 96, seed=13, k_true=4, x_dtype=G.F32, lambda2=0.5, M=2.0, k=4)
+    Xd = torch.from_numpy(P.X).cuda()
+    prob = K.Problem(Xd, P.y)
+    host = K.Problem(P.X, P.y)
+    a = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-7))
+    b = host.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-7))
+    assert a.dual_bound == b.dual_bound
+    assert host.bytes - prob.bytes >= P.X.nbytes
+
+
+def test_full_size_single_node_f32_properties(K):
+    # least squares, FP32, n=20000, p=50000, k=20, lambda2=0.1, M=1.5, Toeplitz 0.9:
+    # the oracle cannot solve it in test time, so check what holds at any size --
+    # the gap target, and the certified bound below a feasible k-sparse value
+    # (ridge on the true support, computed on the host).
+    P = G.cfg_single_node_f32(seed=0)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=20000))
+    assert r.status == "ok" and r.rel_gap <= 1e-6
+    S = np.nonzero(P.beta_star)[0]
+    from tests import _pins
+    ub, _ = _pins.ridge_box(P.X[:, S].astype(np.float64), P.y, P.lambda2, P.M)
+    assert r.dual_bound <= r.primal <= ub * (1 + 1e-9)
+    assert np.count_nonzero(r.beta) >= 1 and np.all(np.abs(r.beta) <= P.M)
