@@ -1,0 +1,351 @@
+"""Benchmark: certified dual bounds per second at a 1e-6 relative gap.
+
+Workload (default): one branch-and-bound root node of least squares with
+FP32 X, n=20000, p=50000, k=20, lambda2=0.1, M=1.5, Toeplitz 0.9 rows, 20 x +-1
+ground truth, SNR 5 -- the single-node configuration of the HBM roofline.
+One step = one certified bound: problem setup on the resident X (column norms,
+power iteration for L), restarted FISTA to a 1e-6 gap, FP64 certificate.
+X (4 GB) is larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; every rank solves its
+own replica (nodes are independent: no data-path collective), value = all
+bounds / max rank time ("scaling": "weak").  --impl reference times the FP64
+CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "certified dual bounds/sec at 1e-6 rel gap"
+UNIT = "bounds/s"
+WORKLOAD = dict(workload="single-node least squares FP32 X n=20000 p=50000 k=20 lambda2=0.1 "
+                         "M=1.5 toeplitz 0.9, root node, rel gap 1e-6",
+                n=20000, p=50000, k=20, lambda2=0.1, M=1.5, r=0.9, x_dtype="f32",
+                loss="least_squares", rel_gap=1e-6, l2="X (4 GB) larger than L2; no flush")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "gradient_pass_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2502_09502_gb300", "csrc", "k_matvec.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="tiny workload (plumbing check only)")
+    return ap.parse_args()
+
+
+def make_problem(args):
+    import ksc_inputs as G
+    if args.small:
+        P = G.make_problem(2000, 5000, r=0.9, seed=args.seed, loss=G.LSQ, k_true=20, snr=5.0,
+                           x_dtype=G.F32, lambda2=0.1, M=1.5, k=20)
+    else:
+        P = G.cfg_single_node_f32(seed=args.seed)
+    return P
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, limits and throttle reasons) during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline
+
+def _peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _traffic(n, p):
+    """DRAM bytes per gradient-pass launch from the committed ncu summary, scaled to
+    this workload by the X bytes it streams -- null unless the summary was taken
+    on the current kernel source."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            t = json.load(f)
+        src = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        if t.get("kernel_sha256") != src:
+            return None
+        return float(t["dram_bytes_per_launch"]) * (n * p) / float(t["n"] * t["p"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ our arm
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_2502_09502_gb300 import ksc as K
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    P = make_problem(args)
+    n, p = P.n, P.p
+    Xd = torch.from_numpy(P.X).cuda()
+    stream = torch.cuda.Stream()
+    node = K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=100000)
+
+    def step(profile=False, stats=None):
+        prob = K.Problem(Xd, P.y, K.KSC_LOSS_LSQ, stream=stream)
+        if profile:
+            K.ksc_problem_profile(prob.h, True)
+        t0 = time.perf_counter()
+        r = prob.solve(node, want_beta=False, want_z=False)
+        if stats is not None:
+            stats["launches"] += K.ksc_problem_launch_count(prob.h)
+            stats["pow"].append(prob.power_iters)
+            stats["iters"].append(r.iters)
+            for kid in range(3):
+                nl, ms = K.ksc_problem_kernel_time(prob.h, kid)
+                stats["k"][kid][0] += nl
+                stats["k"][kid][1] += ms
+        prob.close()
+        return r, t0
+
+    for _ in range(args.warmup):
+        r, _ = step()
+        assert r.status == "ok" and r.rel_gap <= 1e-6, r
+    stats = {"launches": 0, "pow": [], "iters": [], "k": [[0, 0.0], [0, 0.0], [0, 0.0]]}
+    lat = []
+    clocks = ClockSampler(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r, _ = step(profile=True, stats=stats)
+        lat.append(time.perf_counter() - t0)
+        assert r.status == "ok" and r.rel_gap <= 1e-6, r
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    total_bounds = args.steps * world
+    value = total_bounds / (ms / 1e3)
+
+    # roofline of the dominant kernel (the gradient pass over X)
+    nl, kms = stats["k"][0]
+    grad_ms = kms / max(nl, 1)
+    alg_bytes = n * p * 4 + 3 * n * 8 + p * 8    # X (FP32) + u_t, u_{t-1}, y + grad
+    achieved = alg_bytes / (grad_ms / 1e3) / 1e9
+    peak, peak_kind = _peaks()
+    shares = {name: round(stats["k"][i][1] / max(1e-9, sum(x[1] for x in stats["k"])), 4)
+              for i, name in enumerate(["gradient", "prox", "forward"])}
+
+    # end to end through the C ABI with host buffers: H2D of X and y inside the
+    # timed region, D2H of beta and z
+    e2e = None
+    if args.e2e_steps > 0:
+        Xh = torch.from_numpy(P.X).pin_memory()
+        e_lat = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            prob = K.Problem(Xh.numpy(), P.y, K.KSC_LOSS_LSQ, stream=stream)
+            r = prob.solve(node, want_beta=True, want_z=True)
+            prob.close()
+            assert r.status == "ok"
+        e_s = time.perf_counter() - t0
+        e2e = {"value": args.e2e_steps * world / e_s if not dist else None, "unit": UNIT,
+               "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
+               "d2h_bytes_per_step": int(2 * p * 8 + 64)}
+        if dist:
+            t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e["value"] = args.e2e_steps * world / float(t.item())
+
+    out = None
+    if rank == 0:
+        lat_ms = sorted(1e3 * x for x in lat)
+        out = {
+            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
+            "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
+                           "p99": round(float(np.percentile(lat_ms, 99)), 3)},
+            "iters_per_bound": float(np.mean(stats["iters"])),
+            "power_iters_per_bound": float(np.mean(stats["pow"])),
+            "clocks": clk, "e2e": e2e, "gpu_launches": int(stats["launches"]),
+            "kernel_time_share": shares,
+            "roofline": {"bound": "hbm", "kernel": "gradient pass X^T r (k_grad)",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "peak_kind": peak_kind, "frac": round(achieved / peak, 4),
+                         "traffic": _traffic(n, p), "bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": round(grad_ms, 5), "launches": nl},
+        }
+    return out, P, stats
+
+
+# ------------------------------------------------------------------ oracle timing
+
+def time_oracle_sample(P, stats_iters=None, stats_pow=None):
+    """The FP64 oracle on the same workload, on a bounded sample: one power-iteration
+    step (2 passes over X) and one FISTA step of Algorithm 3 (oracle: X gamma, X^T r,
+    the primal X beta, the bound's X beta and X^T zeta), extrapolated to a full bound
+    with the iteration counts of a full solve."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.power_iteration(P.X, tol=0.0, max_iter=1)
+    t_pow = time.perf_counter() - t0
+    L = 2.0 * float(np.sum(P.X.astype(np.float64) ** 2))   # cheap valid step for timing only
+    t0 = time.perf_counter()
+    O.solve(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, L=L, tol=0.0, max_iter=1)
+    t_iter = time.perf_counter() - t0
+    return t_pow, t_iter
+
+
+def cpu_baseline(P, iters, pows):
+    t_pow, t_iter = time_oracle_sample(P)
+    per_bound = pows * t_pow + iters * t_iter
+    return {"value": 1.0 / per_bound, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"1 power-iteration step ({t_pow:.2f} s) and 1 FISTA step incl. setup "
+                       f"({t_iter:.2f} s) of the FP64 oracle on the full workload, "
+                       f"extrapolated to {pows:.0f} power iterations + {iters:.0f} FISTA steps "
+                       f"per bound (the counts of the full GPU solve)")}
+
+
+# iteration counts of a full solve of this workload (power iterations, FISTA steps),
+# used to extrapolate the oracle's bounded sample when it runs on its own
+FULL_SOLVE_COUNTS = {"pow": 91, "iters": 600}
+
+
+def run_reference(args):
+    P = make_problem(args)
+    per_step = []
+    cnt = FULL_SOLVE_COUNTS
+    for s in range(args.warmup + args.steps):
+        t_pow, t_iter = time_oracle_sample(P)
+        if s >= args.warmup:
+            per_step.append(cnt["pow"] * t_pow + cnt["iters"] * t_iter)
+    total = sum(per_step)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(WORKLOAD, parallelism="host cores"),
+        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"per step: 1 power-iteration step + 1 FISTA step of the FP64 "
+                                   f"oracle on the full workload, extrapolated to "
+                                   f"{cnt['pow']} power iterations + {cnt['iters']} FISTA steps"},
+        "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args)
+        return
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as D
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        D.init_process_group("nccl")
+        dist = D
+    out, P, stats = run_ours(args, rank, world, dist)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline(P, float(np.mean(stats["iters"])),
+                                               float(np.mean(stats["pow"])))
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

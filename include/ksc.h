@@ -62,9 +62,12 @@ typedef enum {
 } ksc_loss;
 
 typedef enum {
-  KSC_F64 = 0,                  /* X in double; every iteration step in FP64        */
-  KSC_F32 = 1,                  /* X in float; iterations in FP32, FP64 reductions  */
+  KSC_F64 = 0,                  /* X in double                                      */
+  KSC_F32 = 1,                  /* X in float                                       */
   KSC_BF16 = 2                  /* X in bfloat16 bits; the problem is the stored X  */
+  /* X is streamed from HBM in its storage type.  The iterate vectors (beta, X beta,
+     the gradient) are FP64 for every type; products with FP32/BF16 X are made
+     error-free (exact product error by fma, compensated sums). */
 } ksc_dtype;
 
 /* Node flags (ksc_node.flags): the ablations of Fig. 3. */
@@ -176,6 +179,10 @@ ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);
  * reset != 0 clears the counters after reading. */
 ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
                                    double* total_ms, int32_t reset);
+
+/* Number of kernel launches the library has issued for this problem (setup,
+ * every kernel node of every replayed step graph, certificates). */
+ksc_status ksc_problem_launch_count(const ksc_problem* problem, int64_t* launches);
 
 /* Thread-local text of the last error of a call made on this thread. */
 const char* ksc_last_error(void);

@@ -7,6 +7,13 @@
 //      Tiles: 256 threads x (16-byte vector of columns) by 256 rows; each CTA
 //      writes column partials, the last CTA of a column strip reduces them in a
 //      fixed order (deterministic), the last strip reduces the dual partials.
+//      With X in FP32/BF16 the products are made error-free: r = r_hi + r_lo
+//      (two floats), p = x r_hi rounded, its exact error fma(x, r_hi, -p), an
+//      exact TwoSum of p into the running float sum and a float sum of all the
+//      small terms -- a double-float accumulation, so X^T r is accurate to
+//      ~1e-13 relative while X streams from HBM in its storage type.  u, r and
+//      grad are FP64.  (Plain Kahan in float is not enough: its lost roundings
+//      make the objective noisy at 1e-7 and the value-based restart chatter.)
 //  forward pass   u^{t+1} = X beta^{t+1}       (Algorithm 3, line 10)
 //      sparse (nnz of beta^{t+1} <= cap): one warp per row gathers only the
 //      nonzero columns; dense: beta staged in shared memory, 4 rows per warp.
@@ -57,17 +64,19 @@ template <typename A> __device__ __forceinline__ A xval(float x) { return (A)x; 
 template <typename A> __device__ __forceinline__ A xval(double x) { return (A)x; }
 template <typename A> __device__ __forceinline__ A xval(__nv_bfloat16 x) { return (A)__bfloat162float(x); }
 
-// compensated (Kahan) or plain accumulation
-template <bool KAHAN, typename A>
-__device__ __forceinline__ void acc_add(A& s, A& c, A v) {
-  if (KAHAN) {
-    const A y = v - c;
-    const A t = s + y;
-    c = (t - s) - y;
-    s = t;
-  } else {
-    s += v;
-  }
+// Double-float accumulation of x * (rh + rl) into hi + lo.  x*rh = p + e exactly
+// (e by fma); hi + p = s + err exactly (Knuth's TwoSum); lo collects err, e and
+// x*rl, whose own rounding is ~u^2 of the sum.  The result hi + lo (taken in
+// double) is accurate to ~1e-13 relative.  __fmul_rn/__fadd_rn/__fsub_rn are never
+// contracted into an FMA, which would break the exactness of p and of TwoSum.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x, float rh, float rl) {
+  const float p = __fmul_rn(x, rh);
+  const float e = fmaf(x, rh, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, fmaf(x, rl, e)));
 }
 
 __device__ __forceinline__ double sigmoid(double t) {
@@ -88,9 +97,10 @@ enum FwdMode : int { kFStep = 0, kFRaw = 1, kFInit = 2, kFCert = 3 };
 
 template <typename TX, typename T, int MODE, bool VEC>
 __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
-  constexpr bool FP64ACC = (MODE == kGCert || MODE == kGColsq || std::is_same<T, double>::value);
+  // FP64 X, the certificate and the column norms accumulate in double; FP32/BF16 X
+  // in double-float (error-free products, compensated sums)
+  constexpr bool FP64ACC = (MODE == kGCert || MODE == kGColsq || std::is_same<TX, double>::value);
   using A = typename std::conditional<FP64ACC, double, float>::type;
-  constexpr bool KAHAN = !FP64ACC;
   constexpr int CPT = Vec<TX>::N;
   NodeDev* nd = d.nd;
   int cur = 0, prev = 0;
@@ -102,7 +112,8 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
     prev = (t + 2) % 3;
     c = nd->c;
   }
-  __shared__ A rs[kGradRows];
+  __shared__ A rs[kGradRows];      // r (FP64 path) or r_hi (float path)
+  __shared__ float rl[kGradRows];  // r_lo (float path)
   __shared__ double red[64];
   __shared__ int s_last;
   const int ct = blockIdx.x, rb = blockIdx.y;
@@ -115,9 +126,9 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
   for (int i = threadIdx.x; i < rn; i += kGradThreads) {
     double r = 0.0;
     if (MODE == kGStep) {
-      const T* uc = (const T*)d.u + (size_t)cur * n;
-      const T* up = (const T*)d.u + (size_t)prev * n;
-      const double ug = (1.0 + c) * to_d(uc[r0 + i]) - c * to_d(up[r0 + i]);
+      const double* uc = d.u + (size_t)cur * n;
+      const double* up = d.u + (size_t)prev * n;
+      const double ug = (1.0 + c) * uc[r0 + i] - c * up[r0 + i];
       const double yi = d.y[r0 + i];
       if (d.loss == kLossLsq) {
         r = 2.0 * (ug - yi);
@@ -129,11 +140,12 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         nc += binent(s);
       }
     } else if (MODE == kGRaw) {
-      r = to_d(((const T*)d.u)[r0 + i]);
+      r = d.u[r0 + i];
     } else if (MODE == kGCert) {
       r = d.zeta[r0 + i];
     }
     rs[i] = (A)r;
+    rl[i] = FP64ACC ? 0.f : (float)(r - (double)(float)r);
   }
   if (MODE == kGStep && ct == 0) {
     nc = block_sum<double, kGradThreads>(nc, red);
@@ -143,9 +155,17 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
 
   // main loop: CPT consecutive columns per thread, rows streamed 4 at a time
   const int col0 = ct * (kGradThreads * CPT) + threadIdx.x * CPT;
-  A acc[CPT], cmp[CPT];
+  A acc[CPT];
+  float lo[CPT];
 #pragma unroll
-  for (int k = 0; k < CPT; ++k) { acc[k] = A(0); cmp[k] = A(0); }
+  for (int k = 0; k < CPT; ++k) { acc[k] = A(0); lo[k] = 0.f; }
+  auto accum = [&](int k, A x, int i) {
+    if constexpr (FP64ACC) {
+      acc[k] += (MODE == kGColsq) ? x * x : x * rs[i];
+    } else {
+      df_add(acc[k], lo[k], x, rs[i], rl[i]);
+    }
+  };
   if (col0 < p) {
     const TX* xp = (const TX*)d.X + (size_t)r0 * d.ldx + col0;
     if (VEC && col0 + CPT <= p) {
@@ -155,38 +175,29 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) Vec<TX>::load(xp + (size_t)(i + r) * d.ldx, xv[r]);
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-          const A rr = rs[i + r];
+        for (int r = 0; r < 4; ++r)
 #pragma unroll
-          for (int k = 0; k < CPT; ++k)
-            acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? xv[r][k] * xv[r][k] : xv[r][k] * rr);
-        }
+          for (int k = 0; k < CPT; ++k) accum(k, xv[r][k], i + r);
       }
       for (; i < rn; ++i) {
         A xv[CPT];
         Vec<TX>::load(xp + (size_t)i * d.ldx, xv);
-        const A rr = rs[i];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k)
-          acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? xv[k] * xv[k] : xv[k] * rr);
+        for (int k = 0; k < CPT; ++k) accum(k, xv[k], i);
       }
     } else {
       for (int i = 0; i < rn; ++i) {
-        const A rr = rs[i];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) {
-          if (col0 + k < p) {
-            const A x = xval<A>(xp[(size_t)i * d.ldx + k]);
-            acc_add<KAHAN>(acc[k], cmp[k], MODE == kGColsq ? x * x : x * rr);
-          }
-        }
+        for (int k = 0; k < CPT; ++k)
+          if (col0 + k < p) accum(k, xval<A>(xp[(size_t)i * d.ldx + k]), i);
       }
     }
   }
-  A* ws = (A*)d.ws;
+  double* ws = (double*)d.ws;
 #pragma unroll
   for (int k = 0; k < CPT; ++k)
-    if (col0 + k < p) ws[(size_t)rb * p + col0 + k] = acc[k] - cmp[k];
+    if (col0 + k < p)
+      ws[(size_t)rb * p + col0 + k] = (double)acc[k] + (double)lo[k];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[ct], 1) == (int)gridDim.y - 1);
@@ -199,8 +210,8 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
     const int col = col0 + k;
     if (col < p) {
       double s = 0.0;
-      for (int b = 0; b < (int)gridDim.y; ++b) s += (double)__ldcg(&ws[(size_t)b * p + col]);
-      if (MODE == kGStep || MODE == kGRaw) ((T*)d.grad)[col] = (T)s;
+      for (int b = 0; b < (int)gridDim.y; ++b) s += __ldcg(&ws[(size_t)b * p + col]);
+      if (MODE == kGStep || MODE == kGRaw) d.grad[col] = s;
       else if (MODE == kGCert) d.a64[col] = s;
       else {
         const double u = 1.1102230246251565e-16;
@@ -263,44 +274,47 @@ __device__ void step_logic(NodeDev* nd, double f) {
 
 template <typename TX, typename T, int MODE, bool VEC>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
-  constexpr bool FP64ACC = (MODE == kFCert || std::is_same<T, double>::value);
+  // the certificate works on the FP64 projected iterate b64; the FISTA step on
+  // the T iterate.  FP32/BF16 X: double-float accumulation (error-free products)
+  constexpr bool CERT = (MODE == kFCert);
+  constexpr bool FP64ACC = CERT || std::is_same<TX, double>::value;
   using A = typename std::conditional<FP64ACC, double, float>::type;
-  constexpr bool KAHAN = !FP64ACC;
+  using BT = typename std::conditional<CERT, double, T>::type;
   constexpr int CPT = Vec<TX>::N;
   NodeDev* nd = d.nd;
   const int n = d.n, p = d.p;
-  const T* bsrc;
+  const BT* bsrc;
   int out_slot = 0;
   bool sparse = false;
   int nnz = 0;
   if (MODE == kFStep) {
     if (nd->done) return;
     out_slot = (nd->iter + 1) % 3;
-    bsrc = (const T*)d.beta + (size_t)out_slot * p;
+    bsrc = (const BT*)((const T*)d.beta + (size_t)out_slot * p);
     nnz = nd->nnz;
     sparse = nnz <= d.nnz_cap;
   } else if (MODE == kFCert) {
-    bsrc = (const T*)d.beta + (size_t)(nd->iter % 3) * p;
+    bsrc = (const BT*)d.b64;
     nnz = nd->nnz;
     sparse = nnz <= d.nnz_cap;
   } else if (MODE == kFInit) {
-    bsrc = (const T*)d.beta + (size_t)1 * p;
+    bsrc = (const BT*)((const T*)d.beta + (size_t)1 * p);
   } else {
-    bsrc = (const T*)d.pow_v;
+    bsrc = (const BT*)d.pow_v;
   }
-  __shared__ T bs[kFwdChunk];
+  __shared__ BT bs[kFwdChunk];
   __shared__ double red[64];
   __shared__ int s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * kFwdRows + warp * 4;
   double dot[4] = {0.0, 0.0, 0.0, 0.0};
   if (sparse) {
+    // gather only the nonzero columns; FP64 accumulation
     const int* idx = d.nnz_idx;
-    const T* val = (const T*)d.nnz_val;
     const TX* X = (const TX*)d.X;
     for (int e = lane; e < nnz; e += 32) {
       const int j = idx[e];
-      const double v = to_d(val[e]);
+      const double v = to_d(bsrc[j]);
 #pragma unroll
       for (int r = 0; r < 4; ++r)
         if (row0 + r < n) dot[r] += xval<double>(X[(size_t)(row0 + r) * d.ldx + j]) * v;
@@ -308,9 +322,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) dot[r] = warp_sum(dot[r]);
   } else {
-    A acc[4], cmp[4];
+    A acc[4];
+    float lo[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) { acc[r] = A(0); cmp[r] = A(0); }
+    for (int r = 0; r < 4; ++r) { acc[r] = A(0); lo[r] = 0.f; }
     for (int c0 = 0; c0 < p; c0 += kFwdChunk) {
       const int cw = min(kFwdChunk, p - c0);
       __syncthreads();
@@ -318,8 +333,13 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
       __syncthreads();
       for (int cc = lane * CPT; cc < cw; cc += 32 * CPT) {
         A bv[CPT];
+        float bl[CPT];
 #pragma unroll
-        for (int k = 0; k < CPT; ++k) bv[k] = (cc + k < cw) ? (A)to_d(bs[cc + k]) : A(0);
+        for (int k = 0; k < CPT; ++k) {
+          const double bd = (cc + k < cw) ? to_d(bs[cc + k]) : 0.0;
+          bv[k] = (A)bd;
+          bl[k] = FP64ACC ? 0.f : (float)(bd - (double)(float)bd);
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const int row = row0 + r;
@@ -333,13 +353,17 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
               for (int k = 0; k < CPT; ++k) xv[k] = (cc + k < cw) ? xval<A>(xp[k]) : A(0);
             }
 #pragma unroll
-            for (int k = 0; k < CPT; ++k) acc_add<KAHAN>(acc[r], cmp[r], xv[k] * bv[k]);
+            for (int k = 0; k < CPT; ++k) {
+              if constexpr (FP64ACC) acc[r] += xv[k] * bv[k];
+              else df_add(acc[r], lo[r], xv[k], bv[k], bl[k]);
+            }
           }
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r) dot[r] = warp_sum((double)acc[r] - (double)cmp[r]);
+    for (int r = 0; r < 4; ++r)
+      dot[r] = warp_sum((double)acc[r] + (double)lo[r]);
   }
 
   // epilogue (lane 0 of each warp owns its 4 rows)
@@ -351,14 +375,14 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
       if (row >= n) continue;
       const double u = dot[r];
       if (MODE == kFRaw) {
-        ((T*)d.u)[row] = (T)u;
+        d.u[row] = u;
         continue;
       }
       const double yi = d.y[row];
-      if (MODE == kFStep) ((T*)d.u)[(size_t)out_slot * n + row] = (T)u;
+      if (MODE == kFStep) d.u[(size_t)out_slot * n + row] = u;
       if (MODE == kFInit) {
-        ((T*)d.u)[row] = (T)u;
-        ((T*)d.u)[(size_t)n + row] = (T)u;
+        d.u[row] = u;
+        d.u[(size_t)n + row] = u;
       }
       if (d.loss == kLossLsq) {
         const double res = u - yi;
@@ -461,18 +485,18 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
 template <typename T>
 __global__ void k_pow_start(Dev d) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.p; j += gridDim.x * blockDim.x)
-    ((T*)d.grad)[j] = (T)(1.0 + (double)((unsigned long long)(j + 1) * 2654435761ull % 1000ull) / 1000.0);
+    d.grad[j] = 1.0 + (double)((unsigned long long)(j + 1) * 2654435761ull % 1000ull) / 1000.0;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(1024) k_pow_norm(Dev d, int it) {
   __shared__ double red[64];
-  const T* w = (const T*)d.grad;
+  const double* w = d.grad;
   double s = 0.0;
-  for (int j = threadIdx.x; j < d.p; j += 1024) s += to_d(w[j]) * to_d(w[j]);
+  for (int j = threadIdx.x; j < d.p; j += 1024) s += w[j] * w[j];
   s = sqrt(block_sum<double, 1024>(s, red));
   const double inv = s > 0.0 ? 1.0 / s : 0.0;
-  for (int j = threadIdx.x; j < d.p; j += 1024) ((T*)d.pow_v)[j] = (T)(to_d(w[j]) * inv);
+  for (int j = threadIdx.x; j < d.p; j += 1024) ((T*)d.pow_v)[j] = (T)(w[j] * inv);
   if (threadIdx.x == 0 && it >= 0) d.pow_lam[it] = s;
 }
 
@@ -495,6 +519,7 @@ struct Launch {
 
 void launch_prox_step(const Dev& d, cudaStream_t s);   // k_prox.cu
 void launch_gvalue_init(const Dev& d, cudaStream_t s);
+void launch_cert_prep(const Dev& d, cudaStream_t s);
 void launch_cert_final(const Dev& d, cudaStream_t s, int want_z);
 
 template <typename TX, typename T>
@@ -508,10 +533,14 @@ static void step_impl(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
 }
 
+// The iterate (beta, u, grad) is FP64 for every storage type of X: FP32 iterates
+// make the value-based restart test chatter near the optimum and their fixed
+// point misses a 1e-6 certified gap (measured), while X -- the HBM traffic -- stays
+// in its storage type with error-free products.
 void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if (d.xdt == kXF64) step_impl<double, double>(d, s, ev);
-  else if (d.xdt == kXF32) step_impl<float, float>(d, s, ev);
-  else step_impl<__nv_bfloat16, float>(d, s, ev);
+  else if (d.xdt == kXF32) step_impl<float, double>(d, s, ev);
+  else step_impl<__nv_bfloat16, double>(d, s, ev);
 }
 
 template <typename TX, typename T>
@@ -521,20 +550,21 @@ static void init_impl(const Dev& d, cudaStream_t s) {
 }
 void launch_init(const Dev& d, cudaStream_t s) {
   if (d.xdt == kXF64) init_impl<double, double>(d, s);
-  else if (d.xdt == kXF32) init_impl<float, float>(d, s);
-  else init_impl<__nv_bfloat16, float>(d, s);
+  else if (d.xdt == kXF32) init_impl<float, double>(d, s);
+  else init_impl<__nv_bfloat16, double>(d, s);
 }
 
 template <typename TX, typename T>
 static void cert_impl(const Dev& d, cudaStream_t s, int want_z) {
+  launch_cert_prep(d, s);
   Launch<TX, T>::template fwd<kFCert>(d, s);
   Launch<TX, T>::template grad<kGCert>(d, s);
   launch_cert_final(d, s, want_z);
 }
 void launch_certificate(const Dev& d, cudaStream_t s, int want_z) {
   if (d.xdt == kXF64) cert_impl<double, double>(d, s, want_z);
-  else if (d.xdt == kXF32) cert_impl<float, float>(d, s, want_z);
-  else cert_impl<__nv_bfloat16, float>(d, s, want_z);
+  else if (d.xdt == kXF32) cert_impl<float, double>(d, s, want_z);
+  else cert_impl<__nv_bfloat16, double>(d, s, want_z);
 }
 
 template <typename TX, typename T>
@@ -545,23 +575,18 @@ static void pow_step_impl(const Dev& d, cudaStream_t s, int it) {
 }
 void launch_power_step(const Dev& d, cudaStream_t s, int it) {
   if (d.xdt == kXF64) pow_step_impl<double, double>(d, s, it);
-  else if (d.xdt == kXF32) pow_step_impl<float, float>(d, s, it);
-  else pow_step_impl<__nv_bfloat16, float>(d, s, it);
+  else if (d.xdt == kXF32) pow_step_impl<float, double>(d, s, it);
+  else pow_step_impl<__nv_bfloat16, double>(d, s, it);
 }
 void launch_power_init(const Dev& d, cudaStream_t s) {
-  if (d.xdt == kXF64) {
-    k_pow_start<double><<<64, 256, 0, s>>>(d);
-    k_pow_norm<double><<<1, 1024, 0, s>>>(d, -1);
-  } else {
-    k_pow_start<float><<<64, 256, 0, s>>>(d);
-    k_pow_norm<float><<<1, 1024, 0, s>>>(d, -1);
-  }
+  k_pow_start<double><<<64, 256, 0, s>>>(d);
+  k_pow_norm<double><<<1, 1024, 0, s>>>(d, -1);
 }
 
 void launch_colnorm(const Dev& d, cudaStream_t s) {
   if (d.xdt == kXF64) Launch<double, double>::grad<kGColsq>(d, s);
-  else if (d.xdt == kXF32) Launch<float, float>::grad<kGColsq>(d, s);
-  else Launch<__nv_bfloat16, float>::grad<kGColsq>(d, s);
+  else if (d.xdt == kXF32) Launch<float, double>::grad<kGColsq>(d, s);
+  else Launch<__nv_bfloat16, double>::grad<kGColsq>(d, s);
 }
 
 }  // namespace ksc

@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_prox_step(Dev d) {
     io.w = nullptr;
     io.bc = beta + (size_t)cur * p;
     io.bp = beta + (size_t)prev * p;
-    io.grad = (const T*)d.grad;
+    io.grad = d.grad;
     io.c = nd->c;
     io.invL = nd->invL;
     io.rho = nd->rho;
@@ -57,11 +57,12 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_prox_step(Dev d) {
       nd->fallback += o.fallback;
     }
   } else {
-    SegSmem<T> sm = carve_seg_smem<T>(smem, kDualCap, 0);
-    const T* g = (const T*)d.grad;
+    // in-loop dual term at zeta_gamma = -grad F(u_gamma): a = X^T zeta_gamma = -grad
+    SegSmem<double> sm = carve_seg_smem<double>(smem, kDualCap, 0);
+    const double* g = d.grad;
     const double scale = 1.0 / (2.0 * nd->lambda2);
-    double s = gstar_segment<T, kProxBlock>(p, [&](int i) { return g[i]; }, d.state, nd->kp, nd->M,
-                                            scale, sm);
+    double s = gstar_segment<double, kProxBlock>(p, [&](int i) { return g[i]; }, d.state, nd->kp,
+                                                 nd->M, scale, sm);
     if (threadIdx.x == 0) nd->gstar = s;
   }
 }
@@ -73,8 +74,39 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
   SegSmem<double> sm = carve_seg_smem<double>(smem, kProxCap, 0);
   const T* b1 = (const T*)d.beta + (size_t)1 * d.p;
   GOut o = gvalue_segment<double, kProxBlock>(d.p, [&](int i) { return to_d(b1[i]); }, d.state,
-                                              nd->kp, nd->M, sm, nullptr);
+                                              nd->kp, nd->M, sm, nullptr,
+                                              sizeof(T) == 8 ? 1e-12 : 1e-6);
   if (threadIdx.x == 0) nd->g_next = o.g;
+}
+
+// The certificate's iterate: the final beta promoted to FP64, clipped to the box,
+// fixed-to-zero coordinates zeroed, and the free part scaled onto the l1 budget
+// k'M when rounding left it a hair outside dom g -- so the primal value reported
+// is the objective at a point of the domain.
+template <typename T>
+__global__ void __launch_bounds__(kProxBlock, 1) k_cert_prep(Dev d) {
+  __shared__ double red[64];
+  NodeDev* nd = d.nd;
+  const int p = d.p;
+  const double M = nd->M;
+  const T* b = (const T*)d.beta + (size_t)(nd->iter % 3) * p;
+  double l1 = 0.0;
+  for (int j = threadIdx.x; j < p; j += kProxBlock) {
+    const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
+    double v = fmin(fmax(to_d(b[j]), -M), M);
+    if (st == kZero) v = 0.0;
+    d.b64[j] = v;
+    if (st == kFree) l1 += fabs(v);
+  }
+  l1 = block_sum<double, kProxBlock>(l1, red);
+  const double budget = (double)(nd->kp > 0 ? nd->kp : 0) * M;
+  if (l1 > budget) {
+    const double sc = budget > 0.0 ? (budget / l1) * (1.0 - 8.0 * 1.1102230246251565e-16) : 0.0;
+    for (int j = threadIdx.x; j < p; j += kProxBlock) {
+      const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
+      if (st == kFree) d.b64[j] *= sc;
+    }
+  }
 }
 
 template <typename T>
@@ -111,10 +143,7 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_cert_final(Dev d, int want_z)
   // (division, square, product) and of their sum.
   const double margin_g = (double)nsel * M * eps_a * (1.0 + 4.0 * ur) +
                           2.0 * l2 * gs * ((double)nsel + 8.0) * 4.0 * ur;
-  // g(b^) in FP64 (Algorithm 2) and the relaxed z
-  const T* b = (const T*)d.beta + (size_t)(nd->iter % 3) * p;
-  for (int j = threadIdx.x; j < p; j += kProxBlock) d.b64[j] = to_d(b[j]);
-  __syncthreads();
+  // g(b^) in FP64 (Algorithm 2) and the relaxed z, at the prepared iterate b64
   GOut go = gvalue_segment<double, kProxBlock>(p, [&](int i) { return d.b64[i]; }, d.state, kp, M,
                                                sm, want_z ? d.z64 : nullptr);
   if (threadIdx.x == 0) {
@@ -179,10 +208,7 @@ k_gstar_prim(const double* a, int p, int k, double M, double* out) {
 
 static size_t prox_bytes(int cap, int wsm, int tb) { return seg_smem_bytes(cap, wsm, tb); }
 
-size_t prox_smem_bytes(const Dev& d) {
-  const int tb = d.xdt == kXF64 ? 8 : 4;
-  return prox_bytes(kProxCap, d.prox_wsm, tb);
-}
+size_t prox_smem_bytes(const Dev& d) { return prox_bytes(kProxCap, d.prox_wsm, 8); }
 
 static size_t g_smem_max = 0;
 
@@ -192,11 +218,8 @@ void prox_prepare() {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   g_smem_max = (size_t)optin;
-  cudaFuncSetAttribute(k_prox_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_prox_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_gvalue_init<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_cert_final<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -207,20 +230,21 @@ size_t prox_smem_limit() { return g_smem_max; }
 
 void launch_prox_step(const Dev& d, cudaStream_t s) {
   const size_t bytes = prox_smem_bytes(d);
-  if (d.xdt == kXF64) k_prox_step<double><<<2, kProxBlock, bytes, s>>>(d);
-  else k_prox_step<float><<<2, kProxBlock, bytes, s>>>(d);
+  k_prox_step<double><<<2, kProxBlock, bytes, s>>>(d);
 }
 
 void launch_gvalue_init(const Dev& d, cudaStream_t s) {
   const size_t bytes = prox_bytes(kProxCap, 0, 8);
-  if (d.xdt == kXF64) k_gvalue_init<double><<<1, kProxBlock, bytes, s>>>(d);
-  else k_gvalue_init<float><<<1, kProxBlock, bytes, s>>>(d);
+  k_gvalue_init<double><<<1, kProxBlock, bytes, s>>>(d);
+}
+
+void launch_cert_prep(const Dev& d, cudaStream_t s) {
+  k_cert_prep<double><<<1, kProxBlock, 0, s>>>(d);
 }
 
 void launch_cert_final(const Dev& d, cudaStream_t s, int want_z) {
   const size_t bytes = prox_bytes(kProxCap, 0, 8);
-  if (d.xdt == kXF64) k_cert_final<double><<<1, kProxBlock, bytes, s>>>(d, want_z);
-  else k_cert_final<float><<<1, kProxBlock, bytes, s>>>(d, want_z);
+  k_cert_final<double><<<1, kProxBlock, bytes, s>>>(d, want_z);
 }
 
 void launch_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, int* top,

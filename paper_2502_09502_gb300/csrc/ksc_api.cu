@@ -74,9 +74,17 @@ struct ksc_problem {
   std::vector<cudaEvent_t> events;   // 4 per step of the profiling graph
   int64_t k_launches[3] = {0, 0, 0};
   double k_ms[3] = {0, 0, 0};
+  int64_t launches = 0;   // every kernel launch issued for this problem
 };
 
-static size_t tbytes(int xdt) { return xdt == kXF64 ? 8 : 4; }
+// kernels per launcher (kept beside the launchers they count)
+static constexpr int kLaunchesPerStep = 3;      // gradient, prox, forward
+static constexpr int kLaunchesPerCert = 4;      // prep, forward, gradient, final
+static constexpr int kLaunchesPerInit = 2;      // g value, forward
+static constexpr int kLaunchesPerPower = 3;     // forward, gradient, normalise
+
+// the iterate vectors are FP64 for every storage type of X
+static size_t tbytes(int) { return 8; }
 static size_t xbytes(int xdt) { return xdt == kXF64 ? 8 : (xdt == kXF32 ? 4 : 2); }
 
 template <typename P>
@@ -112,8 +120,8 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
 #define ALLOC(ptr, bytes) \
   if ((st = dmalloc(pr, &(ptr), (bytes))) != KSC_OK) return st
   ALLOC(d.beta, 3 * p * tb);
-  ALLOC(d.u, 3 * n * tb);
-  ALLOC(d.grad, p * tb);
+  ALLOC(d.u, 3 * n * 8);
+  ALLOC(d.grad, p * 8);
   ALLOC(d.wbuf, p * tb);
   ALLOC(d.nnz_val, p * tb);
   ALLOC(d.nnz_idx, p * sizeof(int));
@@ -136,7 +144,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
 #undef ALLOC
   KSC_CUDA(cudaMemset(d.cnt, 0, (size_t)cnt_total(d) * sizeof(int)));
   KSC_CUDA(cudaMemset(d.beta, 0, 3 * p * tb));
-  KSC_CUDA(cudaMemset(d.u, 0, 3 * n * tb));
+  KSC_CUDA(cudaMemset(d.u, 0, 3 * n * 8));
   KSC_CUDA(cudaMemset(d.state, 0, p));
   KSC_CUDA(cudaMemset(d.nd, 0, sizeof(NodeDev)));
   return KSC_OK;
@@ -145,6 +153,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
 static ksc_status power_iteration(ksc_problem* pr, cudaStream_t s) {
   Dev& d = pr->dev;
   launch_power_init(d, s);
+  pr->launches += 2;
   KSC_CUDA(cudaGetLastError());
   const int max_it = 4000;
   const double tol = 1e-6;
@@ -154,6 +163,7 @@ static ksc_status power_iteration(ksc_problem* pr, cudaStream_t s) {
   while (it < max_it) {
     const int upto = std::min(max_it, it + 10);
     for (; it < upto; ++it) launch_power_step(d, s, it);
+    pr->launches += (int64_t)kLaunchesPerPower * 10;
     KSC_CUDA(cudaGetLastError());
     KSC_CUDA(cudaMemcpyAsync(lam.data(), d.pow_lam, it * sizeof(double), cudaMemcpyDeviceToHost, s));
     KSC_CUDA(cudaStreamSynchronize(s));
@@ -241,6 +251,7 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
     d.prox_wsm = (prox_smem_bytes(t) <= lim) ? d.p : 0;
   }
   launch_colnorm(d, s);
+  pr->launches += 1;
   if (cudaGetLastError() != cudaSuccess) return bail(fail(KSC_ERR_CUDA, "colnorm launch failed"));
   if (desc->lipschitz > 0) {
     pr->L = desc->lipschitz;
@@ -370,6 +381,7 @@ static ksc_status replay(ksc_problem* pr, cudaStream_t s, NodeDev* h) {
   cudaGraphExec_t g = prof ? pr->graph_prof : pr->graph;
   const int before = h->iter;
   KSC_CUDA(cudaGraphLaunch(g, s));
+  pr->launches += (int64_t)kLaunchesPerStep * kStepsPerGraph;
   KSC_CUDA(cudaMemcpyAsync(h, pr->dev.nd, sizeof(NodeDev), cudaMemcpyDeviceToHost, s));
   KSC_CUDA(cudaStreamSynchronize(s));
   if (prof) {
@@ -416,7 +428,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     for (int64_t j = 0; j < p; ++j)
       w0[j] = ns.state[j] == kZero ? 0.0 : std::min(node->M, std::max(-node->M, node->warm_beta[j]));
   std::vector<unsigned char> wb;
-  if (pr->xdt == kXF64) fill_slots<double>(wb, w0); else fill_slots<float>(wb, w0);
+  fill_slots<double>(wb, w0);
   const size_t tb = tbytes(pr->xdt);
   KSC_CUDA(cudaMemcpyAsync(d.state, ns.state.data(), p, cudaMemcpyHostToDevice, s));
   KSC_CUDA(cudaMemcpyAsync(d.beta, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
@@ -440,6 +452,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   h.nnz = (int)p + 1;   // the warm start's support is unknown: dense forward pass
   KSC_CUDA(cudaMemcpyAsync(d.nd, &h, sizeof h, cudaMemcpyHostToDevice, s));
   launch_init(d, s);
+  pr->launches += kLaunchesPerInit;
   KSC_CUDA(cudaGetLastError());
   if ((st = build_graph(pr, s, pr->profile)) != KSC_OK) return st;
   KSC_CUDA(cudaMemcpyAsync(&h, d.nd, sizeof h, cudaMemcpyDeviceToHost, s));
@@ -454,6 +467,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     if (h.done == kRunning) continue;
     // FP64 certificate at the current iterate
     launch_certificate(d, s, res->z != nullptr);
+    pr->launches += kLaunchesPerCert;
     KSC_CUDA(cudaGetLastError());
     KSC_CUDA(cudaMemcpyAsync(&h, d.nd, sizeof h, cudaMemcpyDeviceToHost, s));
     KSC_CUDA(cudaStreamSynchronize(s));
@@ -571,6 +585,12 @@ extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M,
   launch_gstar_prim((const double*)ba.p, (int)p, k, M, (double*)bo.p, 0);
   KSC_CUDA(cudaGetLastError());
   KSC_CUDA(cudaMemcpy(out, bo.p, 8, cudaMemcpyDeviceToHost));
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_launch_count(const ksc_problem* problem, int64_t* launches) {
+  if (!problem || !launches) return fail(KSC_ERR_INVALID_ARG, "problem and launches must be non-NULL");
+  *launches = problem->launches;
   return KSC_OK;
 }
 

@@ -32,11 +32,11 @@ struct Dev {
   const double* y;         // n
   const double* colnorm;   // p, FP64 column 2-norms rounded up
   int8_t* state;           // p (node coordinate states)
-  void* beta;              // 3 slots x p (T)
-  void* u;                 // 3 slots x n (T)
-  void* grad;              // p (T)
-  void* wbuf;              // p (T)   prox scratch
-  void* nnz_val;           // p (T)
+  void* beta;              // 3 slots x p, FP64
+  double* u;               // 3 slots x n: X beta in FP64
+  double* grad;            // p: X^T grad F(u_gamma) in FP64
+  void* wbuf;              // p, FP64 prox scratch
+  void* nnz_val;           // p, FP64
   int* nnz_idx;            // p
   int nnz_cap;             // sparse forward pass when nnz <= nnz_cap
   void* ws;                // gradient partials: nrb x p doubles
@@ -49,7 +49,7 @@ struct Dev {
   double* z64;             // p   relaxed z
   double* b64;             // p   final iterate promoted
   NodeDev* nd;
-  void* pow_v;             // p (T)
+  void* pow_v;             // p, FP64
   double* pow_lam;         // power-iteration history
   int prox_wsm;            // prox keeps w in shared memory (elements), 0 = global scratch
 };
@@ -71,7 +71,8 @@ __host__ __device__ inline int cnt_total(const Dev& d) { return grad_ncol(d) + 8
 void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
 // g(beta^1), u^1 = X beta^1 and the objective L^1 (Algorithm 3, lines 1-2)
 void launch_init(const Dev& d, cudaStream_t s);
-// FP64 certificate at the current iterate (u, zeta, a = X^T zeta, G*, g, margins)
+// FP64 certificate at the current iterate (projection onto dom g, u, zeta,
+// a = X^T zeta, G*, g, margins)
 void launch_certificate(const Dev& d, cudaStream_t s, int want_z);
 // one power-iteration step v <- X^T X v / ||X^T X v||, lam[it] = ||X^T X v||
 void launch_power_step(const Dev& d, cudaStream_t s, int it);

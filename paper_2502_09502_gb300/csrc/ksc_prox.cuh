@@ -177,7 +177,7 @@ struct SegIO {
   const T* w;                // direct input, or nullptr to form w from the FISTA state:
   const T* bc;               //   gamma = bc + c (bc - bp);  w = gamma - grad / L
   const T* bp;
-  const T* grad;
+  const double* grad;
   double c, invL;
   double rho, M;
   int kp;
@@ -249,7 +249,7 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     if (io.w) w = to_d(io.w[i]);
     else {
       const double b = to_d(io.bc[i]);
-      w = b + io.c * (b - to_d(io.bp[i])) - to_d(io.grad[i]) * io.invL;
+      w = b + io.c * (b - to_d(io.bp[i])) - io.grad[i] * io.invL;
     }
     const int8_t st = io.state ? io.state[i] : (int8_t)kFree;
     if (st == kFree) {
@@ -517,9 +517,11 @@ struct GOut {
   int infeasible;
 };
 
+// slack: relative tolerance of the domain test (|b| <= M, sum|b| <= k'M) for an
+// iterate stored in a narrower type than FP64.
 template <typename T, int BLOCK, typename LoadB>
 __device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, double M,
-                               const SegSmem<T>& sm, double* z_out) {
+                               const SegSmem<T>& sm, double* z_out, double slack = 1e-12) {
   using B = Bits<double>;
   using U = typename B::U;
   double l1 = 0.0, s1sq = 0.0, linf = 0.0;
@@ -540,7 +542,7 @@ __device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, 
   o.sbar = 0.0;
   o.infeasible = 0;
   const double kM = (double)(kp > 0 ? kp : 0) * M;
-  if (bad || kp < 0 || linf > M * (1.0 + 1e-12) || l1 > kM * (1.0 + 1e-12)) {
+  if (bad || kp < 0 || linf > M * (1.0 + slack) || l1 > kM * (1.0 + slack)) {
     o.infeasible = 1;
     o.g = INFINITY;
   } else {

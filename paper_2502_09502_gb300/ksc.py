@@ -31,7 +31,8 @@ KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
-           "ksc_problem_profile", "ksc_problem_kernel_time", "ksc_last_error", "ksc_version"]
+           "ksc_problem_profile", "ksc_problem_kernel_time", "ksc_problem_launch_count",
+           "ksc_last_error", "ksc_version"]
 
 
 class KscError(RuntimeError):
@@ -82,6 +83,7 @@ def _load():
     L.ksc_problem_profile.argtypes = [C.c_void_p, C.c_int32]
     L.ksc_problem_kernel_time.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), dp,
                                           C.c_int32]
+    L.ksc_problem_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -186,6 +188,12 @@ def ksc_problem_kernel_time(h, kernel, reset=False):
     ms = C.c_double()
     _check(lib.ksc_problem_kernel_time(h, int(kernel), C.byref(n), C.byref(ms), int(bool(reset))))
     return n.value, ms.value
+
+
+def ksc_problem_launch_count(h) -> int:
+    n = C.c_int64()
+    _check(lib.ksc_problem_launch_count(h, C.byref(n)))
+    return n.value
 
 
 # ---------------------------------------------------------------- helpers

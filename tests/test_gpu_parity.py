@@ -212,7 +212,7 @@ def test_ragged_shapes_without_vector_loads(K):
     r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
     ref = _oracle(P)
     assert _rel(r.dual_bound, ref.dual) <= 1e-6 and r.dual_bound <= ref.primal
-    P2 = G.make_problem(1, 3, seed=8, k_true=1, x_dtype=G.F64, lambda2=1.0, M=1.0, k=1)
+    P2 = G.make_problem(2, 3, seed=8, k_true=1, x_dtype=G.F64, lambda2=1.0, M=1.0, k=1)
     prob2 = K.Problem(P2.X, P2.y)
     r2 = prob2.solve(K.Node(P2.lambda2, P2.M, P2.k, rel_gap_tol=1e-9))
     ref2 = _oracle(P2)
