@@ -52,14 +52,16 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--small", action="store_true", help="tiny workload (plumbing check only)")
+    ap.add_argument("--small", action="store_true",
+                    help="8000 x 20000 instance of the same generator (640 MB X, still larger "
+                         "than L2) for profiler captures; not a benchmark line")
     return ap.parse_args()
 
 
 def make_problem(args):
     import ksc_inputs as G
     if args.small:
-        P = G.make_problem(2000, 5000, r=0.9, seed=args.seed, loss=G.LSQ, k_true=20, snr=5.0,
+        P = G.make_problem(8000, 20000, r=0.9, seed=args.seed, loss=G.LSQ, k_true=20, snr=5.0,
                            x_dtype=G.F32, lambda2=0.1, M=1.5, k=20)
     else:
         P = G.cfg_single_node_f32(seed=args.seed)
@@ -182,7 +184,9 @@ def run_ours(args, rank, world, dist):
         assert r.status == "ok" and r.rel_gap <= 1e-6, r
     stats = {"launches": 0, "pow": [], "iters": [], "k": [[0, 0.0], [0, 0.0], [0, 0.0]]}
     lat = []
-    clocks = ClockSampler(dev)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[dev] if vis and len(vis.split(",")) > dev else str(dev)
+    clocks = ClockSampler(smi_index)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
