@@ -166,6 +166,24 @@ ksc_status ksc_g_value(const double* beta, int64_t p, int32_t k, double M, doubl
 /* g*(a) = TopSum_k(H_M(a)) (Lemma 3.1). */
 ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* out);
 
+/* Allocation-free variant of ksc_prox_g on DEVICE buffers (the paper has no
+ * counterpart: this is a deployment convenience).  For callers that must not call
+ * cudaMalloc -- code issued during CUDA-graph capture, runtimes that manage all
+ * device memory through their own pools, loops that cannot afford the implicit
+ * synchronisation of an allocation.  w (p doubles), beta_out (p doubles) and
+ * top_out (min(k, p) int32, or NULL) are device pointers owned by the caller; the
+ * results equal ksc_prox_g's.  Work is enqueued on cuda_stream; the call returns
+ * without waiting.  No cudaMalloc, cudaFree or allocating library routine is
+ * called: the scratch is a fixed device array of 2^19 doubles (4 MiB) that every
+ * GPU loading the library holds until exit, so p above 524288 is rejected with
+ * KSC_ERR_INVALID_ARG.  The first call on a device does a one-time set-up (the
+ * scratch's device address and a kernel attribute): make it before any stream
+ * capture.  All calls on a device share the scratch, so calls that may overlap on
+ * the GPU (different streams without ordering) race; order them on one stream.
+ * Non-finite entries of w give unspecified (but bounded-time) results. */
+ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, double rho,
+                              double* beta_out, int32_t* top_out, void* cuda_stream);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Kernel ids for ksc_problem_kernel_time. */

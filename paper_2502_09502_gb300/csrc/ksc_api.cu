@@ -29,6 +29,9 @@ static ksc_status fail(ksc_status st, const std::string& msg) {
   return st;
 }
 
+// shared with the other translation units of the library
+ksc_status ksc_internal_fail(ksc_status st, const char* msg) { return fail(st, msg); }
+
 #define KSC_CUDA(call)                                                              \
   do {                                                                              \
     cudaError_t e_ = (call);                                                        \

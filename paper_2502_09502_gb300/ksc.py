@@ -31,7 +31,8 @@ KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
-           "ksc_problem_profile", "ksc_problem_kernel_time", "ksc_problem_launch_count",
+           "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
+           "ksc_problem_launch_count",
            "ksc_last_error", "ksc_version"]
 
 
@@ -84,6 +85,8 @@ def _load():
     L.ksc_problem_kernel_time.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), dp,
                                           C.c_int32]
     L.ksc_problem_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+    L.ksc_prox_g_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_double,
+                                     C.c_void_p, C.c_void_p, C.c_void_p]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -177,6 +180,14 @@ def ksc_gstar(a, k, M):
     out = C.c_double()
     _check(lib.ksc_gstar(_dptr(a), a.size, int(k), float(M), C.byref(out)))
     return out.value
+
+
+def ksc_prox_g_noalloc(w_ptr, p, k, M, rho, beta_ptr, top_ptr=None, stream=None):
+    """Device-pointer prox without any device allocation (see include/ksc.h).
+    Returns the ksc_status; the work is enqueued on `stream`."""
+    return lib.ksc_prox_g_noalloc(C.c_void_p(w_ptr), int(p), int(k), float(M), float(rho),
+                                  C.c_void_p(beta_ptr), C.c_void_p(top_ptr) if top_ptr else None,
+                                  _stream_ptr(stream))
 
 
 def ksc_problem_profile(h, enable: bool):
