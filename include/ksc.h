@@ -198,6 +198,12 @@ ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);
 ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
                                    double* total_ms, int32_t reset);
 
+/* Statistics of the last ksc_solve_node on this problem: FISTA steps whose
+ * forward pass gathered only the nonzero columns of X, and steps whose prox
+ * needed the full-pass root finder (pooled block wider than 4096). */
+ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* sparse_steps,
+                                   int32_t* fallback_steps);
+
 /* Number of kernel launches the library has issued for this problem (setup,
  * every kernel node of every replayed step graph, certificates). */
 ksc_status ksc_problem_launch_count(const ksc_problem* problem, int64_t* launches);

@@ -15,8 +15,9 @@
 //      grad are FP64.  (Plain Kahan in float is not enough: its lost roundings
 //      make the objective noisy at 1e-7 and the value-based restart chatter.)
 //  forward pass   u^{t+1} = X beta^{t+1}       (Algorithm 3, line 10)
-//      sparse (nnz of beta^{t+1} <= cap): one warp per row gathers only the
-//      nonzero columns; dense: beta staged in shared memory, 4 rows per warp.
+//      sparse (nnz of beta^{t+1} <= p/2): the nonzero columns streamed from a
+//      column-major copy of X; dense: beta staged in shared memory, 4 rows per
+//      warp over row-major X.
 //      Epilogue: F(u^{t+1}) in FP64; the last CTA runs the fused restart /
 //      momentum / gap step (Algorithm 3, line 11; Sec. 4.2 stopping rule).
 #include <type_traits>
@@ -204,19 +205,47 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last CTA of this column strip: fixed-order reduction over the row blocks
+  // last CTA of this column strip: fixed-order reduction over the row blocks, and
+  // (FISTA step) the prox input w = gamma - grad / L with its selection keys
+  const double* bc = (const double*)d.beta + (size_t)cur * p;
+  const double* bpv = (const double*)d.beta + (size_t)prev * p;
+  const double invL = (MODE == kGStep) ? nd->invL : 0.0;
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int col = col0 + k;
+    unsigned kb = 0xffffffffu, db = 0xffffffffu;   // histogram bins (none off the strip)
     if (col < p) {
       double s = 0.0;
       for (int b = 0; b < (int)gridDim.y; ++b) s += __ldcg(&ws[(size_t)b * p + col]);
-      if (MODE == kGStep || MODE == kGRaw) d.grad[col] = s;
-      else if (MODE == kGCert) d.a64[col] = s;
-      else {
+      if (MODE == kGStep) {
+        d.grad[col] = s;
+        const double b0 = bc[col];
+        const double w = b0 + c * (b0 - bpv[col]) - s * invL;   // Algorithm 3 lines 5, 7
+        ((double*)d.wbuf)[col] = w;
+        const bool fr = d.state == nullptr || d.state[col] == kFree;
+        const unsigned kk = fr ? (__float_as_uint((float)w) & 0x7fffffffu) : 0u;
+        const unsigned dk = fr ? (__float_as_uint((float)s) & 0x7fffffffu) : 0u;
+        d.key[col] = kk;
+        d.dkey[col] = dk;
+        kb = kk >> 21;
+        db = dk >> 21;
+      } else if (MODE == kGRaw) {
+        d.grad[col] = s;
+      } else if (MODE == kGCert) {
+        d.a64[col] = s;
+      } else {
         const double u = 1.1102230246251565e-16;
         ((double*)d.colnorm)[col] = sqrt(s * (1.0 + 2.0 * (n + 4) * u)) * (1.0 + 4.0 * u);
       }
+    }
+    if (MODE == kGStep) {
+      // first radix digit of the keys, aggregated over equal bins of the warp
+      const unsigned pk = __match_any_sync(0xffffffffu, kb);
+      if (kb != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(pk) - 1))
+        atomicAdd(&d.hist[kb], (unsigned)__popc(pk));
+      const unsigned pd = __match_any_sync(0xffffffffu, db);
+      if (db != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(pd) - 1))
+        atomicAdd(&d.hist[2048 + db], (unsigned)__popc(pd));
     }
   }
   if (threadIdx.x == 0) d.cnt[ct] = 0;
@@ -270,75 +299,200 @@ __device__ void step_logic(NodeDev* nd, double f) {
   nd->c = nd->momentum_on ? nd->phi / (nd->phi + 3.0) : 0.0;
 }
 
+// ----------------------------------------------------------- forward epilogue
+
+struct RowAcc {
+  double f = 0.0, nc = 0.0, mg = 0.0, zsq = 0.0;
+};
+
+// per row: store u, accumulate F(u); the certificate also forms zeta = -grad F(u),
+// -F*(-zeta) (App. D.1) and its rounding bound
+template <int MODE>
+__device__ __forceinline__ void row_epilogue(const Dev& d, int row, double u, int out_slot, RowAcc& a) {
+  const int n = d.n;
+  if (MODE == kFRaw) {
+    d.u[row] = u;
+    return;
+  }
+  const double yi = d.y[row];
+  if (MODE == kFStep) d.u[(size_t)out_slot * n + row] = u;
+  if (MODE == kFInit) {
+    d.u[row] = u;
+    d.u[(size_t)n + row] = u;
+  }
+  if (d.loss == kLossLsq) {
+    const double res = u - yi;
+    a.f += res * res;
+    if (MODE == kFCert) {
+      const double z = -2.0 * res;          // zeta = -grad F(u)
+      d.u64[row] = u;
+      d.zeta[row] = z;
+      a.nc += yi * z - 0.25 * z * z;        // -F*(-zeta), App. D.1
+      a.mg += fabs(yi * z) + 0.25 * z * z;
+      a.zsq += z * z;
+    }
+  } else {
+    const double t = -yi * u;
+    a.f += t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
+    if (MODE == kFCert) {
+      const double s = sigmoid(t);
+      const double z = yi * s;              // zeta = -grad F(u), q = zeta/y = s
+      d.u64[row] = u;
+      d.zeta[row] = z;
+      const double h = binent(s);
+      a.nc += h;
+      // |term| plus the rounding of one entropy term in units of u (log() within
+      // 2 ulp, 1-q, two products): the margin is (n+8) u * sum(mg)
+      const double ql = s > 0.0 ? fabs(s * log(s)) : 0.0;
+      const double pl = s < 1.0 ? fabs((1.0 - s) * log1p(-s)) : 0.0;
+      a.mg += h + 8.0 + 16.0 * (ql + pl);
+      a.zsq += z * z;
+    }
+  }
+}
+
+// block partials, then the last of `nparts` CTAs reduces them in a fixed order and
+// finishes: FISTA step logic, initial objective, or certificate partial results
+template <int MODE, int BLOCK>
+__device__ void finish_rows(const Dev& d, RowAcc a, double* red, int* s_last, int nparts, int part,
+                            bool sparse) {
+  NodeDev* nd = d.nd;
+  a.f = block_sum<double, BLOCK>(a.f, red);
+  if (MODE == kFCert) {
+    a.nc = block_sum<double, BLOCK>(a.nc, red);
+    a.mg = block_sum<double, BLOCK>(a.mg, red);
+    a.zsq = block_sum<double, BLOCK>(a.zsq, red);
+  }
+  const int cidx = cnt_fwd(d);
+  if (threadIdx.x == 0) {
+    d.fpart[part] = a.f;
+    if (MODE == kFCert) {
+      d.fpart[nparts + part] = a.nc;
+      d.fpart[2 * nparts + part] = a.mg;
+      d.fpart[3 * nparts + part] = a.zsq;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *s_last = (atomicAdd(&d.cnt[cidx], 1) == nparts - 1);
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  double f = 0.0, ncs = 0.0, mgs = 0.0, zs = 0.0;
+  for (int b = threadIdx.x; b < nparts; b += BLOCK) {
+    f += __ldcg(&d.fpart[b]);
+    if (MODE == kFCert) {
+      ncs += __ldcg(&d.fpart[nparts + b]);
+      mgs += __ldcg(&d.fpart[2 * nparts + b]);
+      zs += __ldcg(&d.fpart[3 * nparts + b]);
+    }
+  }
+  f = block_sum<double, BLOCK>(f, red);
+  if (MODE == kFCert) {
+    ncs = block_sum<double, BLOCK>(ncs, red);
+    mgs = block_sum<double, BLOCK>(mgs, red);
+    zs = block_sum<double, BLOCK>(zs, red);
+  }
+  if (threadIdx.x == 0) {
+    d.cnt[cidx] = 0;
+    if (MODE == kFStep) {
+      nd->sparse_steps += sparse ? 1 : 0;
+      step_logic(nd, f);
+    } else if (MODE == kFInit) {
+      const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // Algorithm 3 line 2
+      nd->Lcur = L1;
+      nd->best_primal = L1;
+      nd->best_dual = -INFINITY;
+      nd->gap = INFINITY;
+      nd->phi = 1.0;
+      nd->c = nd->momentum_on ? 0.25 : 0.0;
+      nd->iter = 1;
+      nd->done = 0;
+      nd->restarts = 0;
+      nd->last_primal = L1;
+      nd->last_dual = -INFINITY;
+    } else if (MODE == kFCert) {  // rigorous rounding bounds, u = 2^-53
+      const double ur = 1.1102230246251565e-16;
+      const double nn = (double)d.n + 8.0;
+      nd->cert_f = f;
+      nd->cert_negconj = ncs;
+      nd->cert_margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
+      nd->cert_zeta_sq = zs;
+    }
+  }
+}
+
 // ----------------------------------------------------------- forward pass
 
 template <typename TX, typename T, int MODE, bool VEC>
 __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
-  // the certificate works on the FP64 projected iterate b64; the FISTA step on
-  // the T iterate.  FP32/BF16 X: double-float accumulation (error-free products)
+  // FISTA step / initial point / power: the FP64 vector is read as its float split
+  // (hi + lo) and multiplied error-free; the certificate reads the FP64 b64.
   constexpr bool CERT = (MODE == kFCert);
   constexpr bool FP64ACC = CERT || std::is_same<TX, double>::value;
   using A = typename std::conditional<FP64ACC, double, float>::type;
-  using BT = typename std::conditional<CERT, double, T>::type;
   constexpr int CPT = Vec<TX>::N;
   NodeDev* nd = d.nd;
   const int n = d.n, p = d.p;
-  const BT* bsrc;
   int out_slot = 0;
   bool sparse = false;
   int nnz = 0;
+  const double* bfull = nullptr;   // FP64 values (sparse gather; dense pass with FP64 X)
+  const float* bh = nullptr;       // float split for the dense pass with FP32/BF16 X
+  const float* bl = nullptr;
   if (MODE == kFStep) {
     if (nd->done) return;
     out_slot = (nd->iter + 1) % 3;
-    bsrc = (const BT*)((const T*)d.beta + (size_t)out_slot * p);
+    bfull = (const double*)d.beta + (size_t)out_slot * p;
+    bh = d.bhi;
+    bl = d.blo;
     nnz = nd->nnz;
-    sparse = nnz <= d.nnz_cap;
+    if (nnz <= d.sp_cap && d.nseg <= kMaxSegSparse) return;   // the column pass runs
   } else if (MODE == kFCert) {
-    bsrc = (const BT*)d.b64;
+    bfull = d.b64;
     nnz = nd->nnz;
-    sparse = nnz <= d.nnz_cap;
+    if (nnz <= d.sp_cap && d.nseg <= kMaxSegSparse) return;
   } else if (MODE == kFInit) {
-    bsrc = (const BT*)((const T*)d.beta + (size_t)1 * p);
+    bfull = (const double*)d.beta + p;
+    bh = d.bhi;
+    bl = d.blo;
   } else {
-    bsrc = (const BT*)d.pow_v;
+    bfull = d.vcur;
+    bh = d.vhi;
+    bl = d.vlo;
   }
-  __shared__ BT bs[kFwdChunk];
+  // shared memory: one chunk of the vector (float hi/lo, or FP64)
+  __shared__ __align__(16) unsigned char sbuf[kFwdChunk * 8];
   __shared__ double red[64];
   __shared__ int s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row0 = blockIdx.x * kFwdRows + warp * 4;
   double dot[4] = {0.0, 0.0, 0.0, 0.0};
-  if (sparse) {
-    // gather only the nonzero columns; FP64 accumulation
-    const int* idx = d.nnz_idx;
-    const TX* X = (const TX*)d.X;
-    for (int e = lane; e < nnz; e += 32) {
-      const int j = idx[e];
-      const double v = to_d(bsrc[j]);
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        if (row0 + r < n) dot[r] += xval<double>(X[(size_t)(row0 + r) * d.ldx + j]) * v;
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) dot[r] = warp_sum(dot[r]);
-  } else {
+  {
+    constexpr int CH = FP64ACC ? kFwdChunk / 2 : kFwdChunk;
+    float* sh_hi = (float*)sbuf;
+    float* sh_lo = sh_hi + kFwdChunk;
+    double* sh_d = (double*)sbuf;
     A acc[4];
     float lo[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) { acc[r] = A(0); lo[r] = 0.f; }
-    for (int c0 = 0; c0 < p; c0 += kFwdChunk) {
-      const int cw = min(kFwdChunk, p - c0);
+    for (int c0 = 0; c0 < p; c0 += CH) {
+      const int cw = min(CH, p - c0);
       __syncthreads();
-      for (int j = threadIdx.x; j < cw; j += kFwdThreads) bs[j] = bsrc[c0 + j];
+      for (int j = threadIdx.x; j < cw; j += kFwdThreads) {
+        if (FP64ACC) sh_d[j] = bfull[c0 + j];
+        else { sh_hi[j] = bh[c0 + j]; sh_lo[j] = bl[c0 + j]; }
+      }
       __syncthreads();
       for (int cc = lane * CPT; cc < cw; cc += 32 * CPT) {
         A bv[CPT];
-        float bl[CPT];
+        float blv[CPT];
 #pragma unroll
         for (int k = 0; k < CPT; ++k) {
-          const double bd = (cc + k < cw) ? to_d(bs[cc + k]) : 0.0;
-          bv[k] = (A)bd;
-          bl[k] = FP64ACC ? 0.f : (float)(bd - (double)(float)bd);
+          const bool in = cc + k < cw;
+          if (FP64ACC) { bv[k] = in ? (A)sh_d[cc + k] : A(0); blv[k] = 0.f; }
+          else { bv[k] = in ? (A)sh_hi[cc + k] : A(0); blv[k] = in ? sh_lo[cc + k] : 0.f; }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
@@ -355,149 +509,131 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
 #pragma unroll
             for (int k = 0; k < CPT; ++k) {
               if constexpr (FP64ACC) acc[r] += xv[k] * bv[k];
-              else df_add(acc[r], lo[r], xv[k], bv[k], bl[k]);
+              else df_add(acc[r], lo[r], xv[k], bv[k], blv[k]);
             }
           }
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < 4; ++r)
-      dot[r] = warp_sum((double)acc[r] + (double)lo[r]);
+    for (int r = 0; r < 4; ++r) dot[r] = warp_sum((double)acc[r] + (double)lo[r]);
   }
 
   // epilogue (lane 0 of each warp owns its 4 rows)
-  double f_loc = 0.0, nc_loc = 0.0, mg_loc = 0.0, zsq_loc = 0.0;
+  RowAcc ra;
   if (lane == 0) {
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int row = row0 + r;
-      if (row >= n) continue;
-      const double u = dot[r];
-      if (MODE == kFRaw) {
-        d.u[row] = u;
-        continue;
-      }
-      const double yi = d.y[row];
-      if (MODE == kFStep) d.u[(size_t)out_slot * n + row] = u;
-      if (MODE == kFInit) {
-        d.u[row] = u;
-        d.u[(size_t)n + row] = u;
-      }
-      if (d.loss == kLossLsq) {
-        const double res = u - yi;
-        f_loc += res * res;
-        if (MODE == kFCert) {
-          const double z = -2.0 * res;          // zeta = -grad F(u)
-          d.u64[row] = u;
-          d.zeta[row] = z;
-          nc_loc += yi * z - 0.25 * z * z;      // -F*(-zeta), App. D.1
-          mg_loc += fabs(yi * z) + 0.25 * z * z;
-          zsq_loc += z * z;
-        }
-      } else {
-        const double t = -yi * u;
-        f_loc += t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
-        if (MODE == kFCert) {
-          const double s = sigmoid(t);
-          const double z = yi * s;              // zeta = -grad F(u), q = zeta/y = s
-          d.u64[row] = u;
-          d.zeta[row] = z;
-          const double h = binent(s);
-          nc_loc += h;
-          // |term| plus the rounding of one entropy term in units of u (log() within
-          // 2 ulp, 1-q, two products): the margin is (n+8) u * sum(mg), see below
-          const double ql = s > 0.0 ? fabs(s * log(s)) : 0.0;
-          const double pl = s < 1.0 ? fabs((1.0 - s) * log1p(-s)) : 0.0;
-          mg_loc += h + 8.0 + 16.0 * (ql + pl);
-          zsq_loc += z * z;
-        }
-      }
-    }
+    for (int r = 0; r < 4; ++r)
+      if (row0 + r < n) row_epilogue<MODE>(d, row0 + r, dot[r], out_slot, ra);
   }
   if (MODE == kFRaw) return;
-  f_loc = block_sum<double, kFwdThreads>(f_loc, red);
-  if (MODE == kFCert) {
-    nc_loc = block_sum<double, kFwdThreads>(nc_loc, red);
-    mg_loc = block_sum<double, kFwdThreads>(mg_loc, red);
-    zsq_loc = block_sum<double, kFwdThreads>(zsq_loc, red);
-  }
-  const int cidx = cnt_fwd(d);
-  if (threadIdx.x == 0) {
-    d.fpart[blockIdx.x] = f_loc;
-    if (MODE == kFCert) {
-      d.fpart[gridDim.x + blockIdx.x] = nc_loc;
-      d.fpart[2 * gridDim.x + blockIdx.x] = mg_loc;
-      d.fpart[3 * gridDim.x + blockIdx.x] = zsq_loc;
+  finish_rows<MODE, kFwdThreads>(d, ra, red, &s_last, (int)gridDim.x, (int)blockIdx.x, sparse);
+}
+
+// ----------------------------------------------------------- sparse forward pass
+// u = X_S b_S over the nonzero columns S of the iterate, read from the column-major
+// copy of X: each column segment is contiguous, so the pass streams n |S| elements
+// fully coalesced (instead of one 32-byte sector per element of row-major X).
+// Grid: (row blocks of 256 rows) x (kSpSplit chunks of the nonzero list); a thread
+// owns one row; the last CTA of a row block adds the chunks in a fixed order.
+
+template <typename TX, int MODE>
+__global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
+  constexpr bool CERT = (MODE == kFCert);
+  constexpr bool FP64ACC = CERT || std::is_same<TX, double>::value;
+  using A = typename std::conditional<FP64ACC, double, float>::type;
+  NodeDev* nd = d.nd;
+  if (MODE == kFStep && nd->done) return;
+  const int nnz = nd->nnz;
+  if (!(nnz <= d.sp_cap && d.nseg <= kMaxSegSparse)) return;   // the dense pass runs
+  const int n = d.n, p = d.p;
+  const int out_slot = (MODE == kFStep) ? (nd->iter + 1) % 3 : 0;
+  __shared__ int soff[kMaxSegSparse + 1];
+  __shared__ int sj[kSpStage];
+  __shared__ double sv[kSpStage];    // FP64 values (certificate, FP64 X)
+  __shared__ float sh[kSpStage];     // float split (FP32 / BF16 X)
+  __shared__ float sl[kSpStage];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  for (int i = threadIdx.x; i <= d.nseg; i += kSpRows) soff[i] = __ldcg(&d.seg_off[i]);
+  __syncthreads();
+  const int rb = blockIdx.x, ks = blockIdx.y;
+  const int row = rb * kSpRows + (int)threadIdx.x;
+  const int e0 = (int)((long long)nnz * ks / kSpSplit);
+  const int e1 = (int)((long long)nnz * (ks + 1) / kSpSplit);
+  const double* bfull = CERT ? d.b64 : (const double*)d.beta + (size_t)out_slot * p;
+  const TX* Xc = (const TX*)d.Xc;
+  A acc = A(0);
+  float lo = 0.f;
+  for (int base = e0; base < e1; base += kSpStage) {
+    const int cnt = min(kSpStage, e1 - base);
+    for (int e = threadIdx.x; e < cnt; e += kSpRows) {
+      const int E = base + e;
+      int a = 0, b = d.nseg;   // segment s with soff[s] <= E < soff[s+1]
+      while (b - a > 1) {
+        const int m = (a + b) >> 1;
+        if (soff[m] <= E) a = m; else b = m;
+      }
+      const int j = __ldcg(&d.nnz_idx[a * kSegLen + (E - soff[a])]);
+      sj[e] = j;
+      if (FP64ACC) sv[e] = __ldcg(&bfull[j]);
+      else { sh[e] = __ldcg(&d.bhi[j]); sl[e] = __ldcg(&d.blo[j]); }
     }
+    __syncthreads();
+    if (row < n) {
+      int e = 0;
+      for (; e + 4 <= cnt; e += 4) {
+        A x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = xval<A>(__ldcs(&Xc[(size_t)sj[e + k] * d.ldc + row]));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if constexpr (FP64ACC) acc += x[k] * (A)sv[e + k];
+          else df_add(acc, lo, x[k], sh[e + k], sl[e + k]);
+        }
+      }
+      for (; e < cnt; ++e) {
+        const A x = xval<A>(__ldcs(&Xc[(size_t)sj[e] * d.ldc + row]));
+        if constexpr (FP64ACC) acc += x * (A)sv[e];
+        else df_add(acc, lo, x, sh[e], sl[e]);
+      }
+    }
+    __syncthreads();
   }
+  if (row < n) d.sp_part[(size_t)ks * n + row] = (double)acc + (double)lo;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[cidx], 1) == (int)gridDim.x - 1);
+  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt_sp[rb], 1) == kSpSplit - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double f = 0.0, ncs = 0.0, mgs = 0.0, zs = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += kFwdThreads) {
-    f += __ldcg(&d.fpart[b]);
-    if (MODE == kFCert) {
-      ncs += __ldcg(&d.fpart[gridDim.x + b]);
-      mgs += __ldcg(&d.fpart[2 * gridDim.x + b]);
-      zs += __ldcg(&d.fpart[3 * gridDim.x + b]);
-    }
+  RowAcc ra;
+  if (row < n) {
+    double u = 0.0;
+    for (int k = 0; k < kSpSplit; ++k) u += __ldcg(&d.sp_part[(size_t)k * n + row]);
+    row_epilogue<MODE>(d, row, u, out_slot, ra);
   }
-  f = block_sum<double, kFwdThreads>(f, red);
-  if (MODE == kFCert) {
-    ncs = block_sum<double, kFwdThreads>(ncs, red);
-    mgs = block_sum<double, kFwdThreads>(mgs, red);
-    zs = block_sum<double, kFwdThreads>(zs, red);
-  }
-  if (threadIdx.x == 0) {
-    d.cnt[cidx] = 0;
-    if (MODE == kFStep) {
-      step_logic(nd, f);
-    } else if (MODE == kFInit) {
-      const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // Algorithm 3 line 2
-      nd->Lcur = L1;
-      nd->best_primal = L1;
-      nd->best_dual = -INFINITY;
-      nd->gap = INFINITY;
-      nd->phi = 1.0;
-      nd->c = nd->momentum_on ? 0.25 : 0.0;
-      nd->iter = 1;
-      nd->done = 0;
-      nd->restarts = 0;
-      nd->last_primal = L1;
-      nd->last_dual = -INFINITY;
-    } else {  // certificate partial results (rigorous rounding bounds, u = 2^-53)
-      const double ur = 1.1102230246251565e-16;
-      const double nn = (double)n + 8.0;
-      nd->cert_f = f;
-      nd->cert_negconj = ncs;
-      nd->cert_margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
-      nd->cert_zeta_sq = zs;
-    }
-  }
+  if (threadIdx.x == 0) d.cnt_sp[rb] = 0;
+  finish_rows<MODE, kSpRows>(d, ra, red, &s_last, (int)gridDim.x, rb, true);
 }
 
-// ----------------------------------------------------------- power iteration
+// ----------------------------------------------------------- column-major copy
 
-template <typename T>
-__global__ void k_pow_start(Dev d) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.p; j += gridDim.x * blockDim.x)
-    d.grad[j] = 1.0 + (double)((unsigned long long)(j + 1) * 2654435761ull % 1000ull) / 1000.0;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_pow_norm(Dev d, int it) {
-  __shared__ double red[64];
-  const double* w = d.grad;
-  double s = 0.0;
-  for (int j = threadIdx.x; j < d.p; j += 1024) s += w[j] * w[j];
-  s = sqrt(block_sum<double, 1024>(s, red));
-  const double inv = s > 0.0 ? 1.0 / s : 0.0;
-  for (int j = threadIdx.x; j < d.p; j += 1024) ((T*)d.pow_v)[j] = (T)(w[j] * inv);
-  if (threadIdx.x == 0 && it >= 0) d.pow_lam[it] = s;
+template <typename TX>
+__global__ void __launch_bounds__(256) k_transpose(const TX* __restrict__ X, int64_t ldx, TX* __restrict__ Xc,
+                                                   int64_t ldc, int n, int p) {
+  __shared__ TX tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    if (r < n && c < p) tile[k][tx] = X[(size_t)r * ldx + c];
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (r < n && c < p) Xc[(size_t)c * ldc + r] = tile[tx][k];
+  }
 }
 
 // ----------------------------------------------------------- launchers
@@ -515,10 +651,15 @@ struct Launch {
     if (d.vec) k_fwd<TX, T, MODE, true><<<fwd_ntiles(d), kFwdThreads, 0, s>>>(d);
     else k_fwd<TX, T, MODE, false><<<fwd_ntiles(d), kFwdThreads, 0, s>>>(d);
   }
+  template <int MODE>
+  static void fwd_col(const Dev& d, cudaStream_t s) {
+    k_fwd_col<TX, MODE><<<dim3(sp_nrb(d), kSpSplit), kSpRows, 0, s>>>(d);
+  }
 };
 
-void launch_prox_step(const Dev& d, cudaStream_t s);   // k_prox.cu
-void launch_gvalue_init(const Dev& d, cudaStream_t s);
+void launch_prox_select(const Dev& d, cudaStream_t s);   // k_prox_grid.cu
+void launch_prox_apply(const Dev& d, cudaStream_t s);
+void launch_gvalue_init(const Dev& d, cudaStream_t s);  // k_prox.cu
 void launch_cert_prep(const Dev& d, cudaStream_t s);
 void launch_cert_final(const Dev& d, cudaStream_t s, int want_z);
 
@@ -527,9 +668,11 @@ static void step_impl(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if (ev) cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal);
   Launch<TX, T>::template grad<kGStep>(d, s);
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
-  launch_prox_step(d, s);
+  launch_prox_select(d, s);
+  launch_prox_apply(d, s);
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
-  Launch<TX, T>::template fwd<kFStep>(d, s);
+  Launch<TX, T>::template fwd_col<kFStep>(d, s);   // sparse iterate (one of the two runs)
+  Launch<TX, T>::template fwd<kFStep>(d, s);       // dense iterate
   if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
 }
 
@@ -546,6 +689,7 @@ void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
 template <typename TX, typename T>
 static void init_impl(const Dev& d, cudaStream_t s) {
   launch_gvalue_init(d, s);
+  launch_split((const double*)d.beta + d.p, d.bhi, d.blo, d.p, s);
   Launch<TX, T>::template fwd<kFInit>(d, s);
 }
 void launch_init(const Dev& d, cudaStream_t s) {
@@ -557,6 +701,7 @@ void launch_init(const Dev& d, cudaStream_t s) {
 template <typename TX, typename T>
 static void cert_impl(const Dev& d, cudaStream_t s, int want_z) {
   launch_cert_prep(d, s);
+  Launch<TX, T>::template fwd_col<kFCert>(d, s);
   Launch<TX, T>::template fwd<kFCert>(d, s);
   Launch<TX, T>::template grad<kGCert>(d, s);
   launch_cert_final(d, s, want_z);
@@ -567,20 +712,27 @@ void launch_certificate(const Dev& d, cudaStream_t s, int want_z) {
   else cert_impl<__nv_bfloat16, double>(d, s, want_z);
 }
 
-template <typename TX, typename T>
-static void pow_step_impl(const Dev& d, cudaStream_t s, int it) {
-  Launch<TX, T>::template fwd<kFRaw>(d, s);
-  Launch<TX, T>::template grad<kGRaw>(d, s);
-  k_pow_norm<T><<<1, 1024, 0, s>>>(d, it);
+void launch_fwd_raw(const Dev& d, cudaStream_t s) {
+  if (d.xdt == kXF64) Launch<double, double>::fwd<kFRaw>(d, s);
+  else if (d.xdt == kXF32) Launch<float, double>::fwd<kFRaw>(d, s);
+  else Launch<__nv_bfloat16, double>::fwd<kFRaw>(d, s);
 }
-void launch_power_step(const Dev& d, cudaStream_t s, int it) {
-  if (d.xdt == kXF64) pow_step_impl<double, double>(d, s, it);
-  else if (d.xdt == kXF32) pow_step_impl<float, double>(d, s, it);
-  else pow_step_impl<__nv_bfloat16, double>(d, s, it);
+
+void launch_grad_raw(const Dev& d, cudaStream_t s) {
+  if (d.xdt == kXF64) Launch<double, double>::grad<kGRaw>(d, s);
+  else if (d.xdt == kXF32) Launch<float, double>::grad<kGRaw>(d, s);
+  else Launch<__nv_bfloat16, double>::grad<kGRaw>(d, s);
 }
-void launch_power_init(const Dev& d, cudaStream_t s) {
-  k_pow_start<double><<<64, 256, 0, s>>>(d);
-  k_pow_norm<double><<<1, 1024, 0, s>>>(d, -1);
+
+void launch_transpose(const Dev& d, cudaStream_t s) {
+  dim3 grid((d.p + 31) / 32, (d.n + 31) / 32);
+  if (d.xdt == kXF64)
+    k_transpose<double><<<grid, 256, 0, s>>>((const double*)d.X, d.ldx, (double*)d.Xc, d.ldc, d.n, d.p);
+  else if (d.xdt == kXF32)
+    k_transpose<float><<<grid, 256, 0, s>>>((const float*)d.X, d.ldx, (float*)d.Xc, d.ldc, d.n, d.p);
+  else
+    k_transpose<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)d.X, d.ldx,
+                                                     (__nv_bfloat16*)d.Xc, d.ldc, d.n, d.p);
 }
 
 void launch_colnorm(const Dev& d, cudaStream_t s) {

@@ -1,6 +1,5 @@
-// k_prox.cu -- per-node kernels built on the block prox (ksc_prox.cuh):
-//   k_prox_step      one FISTA prox (Algorithm 3 line 8), g(beta^{t+1}) (Alg. 2)
-//                    and, in a second CTA, the in-loop dual term G*(X^T zeta_gamma)
+// k_prox.cu -- per-node kernels built on the block prox (ksc_prox.cuh); the prox
+// of a FISTA step itself is spread over the GPU in k_prox_grid.cu.
 //   k_gvalue_init    g(beta^1) for the initial objective (Algorithm 3 line 2)
 //   k_cert_final     FP64 G*(a) with its rounding margin, FP64 g(b^), the
 //                    certified bound and gap (Sec. 3.4)
@@ -12,60 +11,10 @@
 
 namespace ksc {
 
-// dual CTA shared memory: hist + scratch only
+// g* primitive shared memory: hist + scratch only
 constexpr int kDualCap = 16;
 
-template <typename T>
-__global__ void __launch_bounds__(kProxBlock, 1) k_prox_step(Dev d) {
-  NodeDev* nd = d.nd;
-  if (nd->done) return;
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int p = d.p;
-  const int t = nd->iter;
-  const int cur = t % 3, prev = (t + 2) % 3, nxt = (t + 1) % 3;
-  T* beta = (T*)d.beta;
-  if (blockIdx.x == 0) {
-    SegSmem<T> sm = carve_seg_smem<T>(smem, kProxCap, d.prox_wsm);
-    SegIO<T> io;
-    io.m = p;
-    io.state = d.state;
-    io.w = nullptr;
-    io.bc = beta + (size_t)cur * p;
-    io.bp = beta + (size_t)prev * p;
-    io.grad = d.grad;
-    io.c = nd->c;
-    io.invL = nd->invL;
-    io.rho = nd->rho;
-    io.M = nd->M;
-    io.kp = nd->kp;
-    io.wbuf = (T*)d.wbuf;
-    io.beta = beta + (size_t)nxt * p;
-    io.nnz_idx = d.nnz_idx;
-    io.nnz_val = (T*)d.nnz_val;
-    io.nnz_cap = d.nnz_cap;
-    io.top_out = nullptr;
-    io.qhint = nd->qhint;
-    SegOut o = prox_segment<T, kProxBlock>(io, sm);
-    if (threadIdx.x == 0) {
-      nd->g_next = o.g;
-      nd->nnz = o.nnz;
-      nd->theta = o.theta;
-      const int q = io.kp < p ? io.kp : p;
-      int h = o.qused / 2;
-      if (h < q + 64) h = q + 64;
-      nd->qhint = h;
-      nd->fallback += o.fallback;
-    }
-  } else {
-    // in-loop dual term at zeta_gamma = -grad F(u_gamma): a = X^T zeta_gamma = -grad
-    SegSmem<double> sm = carve_seg_smem<double>(smem, kDualCap, 0);
-    const double* g = d.grad;
-    const double scale = 1.0 / (2.0 * nd->lambda2);
-    double s = gstar_segment<double, kProxBlock>(p, [&](int i) { return g[i]; }, d.state, nd->kp,
-                                                 nd->M, scale, sm);
-    if (threadIdx.x == 0) nd->gstar = s;
-  }
-}
+void prox_grid_prepare(int optin);   // k_prox_grid.cu
 
 template <typename T>
 __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
@@ -218,7 +167,7 @@ void prox_prepare() {
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   g_smem_max = (size_t)optin;
-  cudaFuncSetAttribute(k_prox_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  prox_grid_prepare(optin);
   cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
@@ -227,11 +176,6 @@ void prox_prepare() {
 }
 
 size_t prox_smem_limit() { return g_smem_max; }
-
-void launch_prox_step(const Dev& d, cudaStream_t s) {
-  const size_t bytes = prox_smem_bytes(d);
-  k_prox_step<double><<<2, kProxBlock, bytes, s>>>(d);
-}
 
 void launch_gvalue_init(const Dev& d, cudaStream_t s) {
   const size_t bytes = prox_bytes(kProxCap, 0, 8);

@@ -1,0 +1,656 @@
+// k_prox_grid.cu -- the prox of one FISTA step (Algorithm 3 line 8) spread over
+// the GPU, and the Lanczos iteration that gives L.
+//
+// prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w) (Moreau, Sec. 3.3).  With the
+// Huber weight on the top k' positions only, PAVA (Alg. 1 + 4) pools at most one
+// block across positions k'/k'+1: the result is fixed by the top-k' set and one
+// threshold theta, the root of the monotone piecewise-linear
+//   Phi(t) = sum_top (t + min(rho t, M) - a)_+ - sum_tail (a - t)_+,   a = |w|,
+// top coordinates get |b| = min(M, rho a/(1+rho), a - theta), the rest max(0, a - theta).
+//
+//  gradient pass epilogue (k_matvec.cu): w (FP64), 32-bit selection keys = float
+//      bits of |w| (monotone: fl(a) > fl(b) implies a > b), first radix digit
+//      histogram -- fused into the CTA that finishes each column strip.
+//  k_prox_select (2 CTAs): integer radix passes give the top-k' key threshold;
+//      ties of the float key are broken exactly on |w| then index (Alg. 1 order);
+//      the top-Q candidates (float key >= the Q-th) are sorted as 64-bit patterns
+//      of |w| and a binary search over the breakpoints {a_j, theta_t, M/rho} of
+//      Phi finds the linear piece holding the root.  Q grows if the pooled block
+//      reaches below the candidates; beyond the shared-memory capacity a bracketed
+//      Newton iteration over full passes is used.  CTA 1: the in-loop dual term
+//      G*(X^T zeta_gamma) (Lemma 3.1 on the node) from keys of |grad|.
+//  k_prox_apply (grid): b, its float split for the dense forward pass, the
+//      nonzero list (one compaction segment per CTA, ascending index), sum |b_F|,
+//      and in the last CTA g(b) by the water-filling of Algorithm 2.
+#include "ksc_common.cuh"
+#include "ksc_launch.h"
+#include "ksc_prox.cuh"
+#include "ksc_state.cuh"
+
+namespace ksc {
+
+constexpr int kSelBlock = 1024;
+
+struct SelSmem {
+  unsigned hist[2048];
+  int sh[64];
+  double red[64];
+  unsigned long long cand[kProxCap];   // bit patterns of non-negative doubles
+  double pref[kProxCap + 1];
+  double tb[kProxCap];
+  int cidx[kProxCap];
+  double root[2];
+  int flag[2];
+};
+
+__device__ __forceinline__ double dval(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+// descending sort of 64-bit keys (non-negative doubles compare like their bits)
+__device__ void sort_u64_desc(unsigned long long* s, int N) {
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (N >> 1); i += kSelBlock) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = ((lo & size) == 0);
+        const unsigned long long a = s[lo], b = s[hi];
+        if ((a < b) == desc) { s[lo] = b; s[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// descending by value, ascending by index
+__device__ void sort_pairs_desc(unsigned long long* s, int* ix, int N) {
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < (N >> 1); i += kSelBlock) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool desc = ((lo & size) == 0);
+        const unsigned long long a = s[lo], b = s[hi];
+        const int ia = ix[lo], ib = ix[hi];
+        const bool a_first = (a > b) || (a == b && ia < ib);
+        if (a_first != desc) { s[lo] = b; s[hi] = a; ix[lo] = ib; ix[hi] = ia; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// prefix sums pref[0..C] of the candidate values
+__device__ void prefix_values(SelSmem& sm, int C) {
+  const int per = (C + kSelBlock - 1) / kSelBlock;
+  const int s0 = threadIdx.x * per;
+  double loc = 0.0;
+  for (int j = 0; j < per; ++j) if (s0 + j < C) loc += dval(sm.cand[s0 + j]);
+  double tot;
+  double ex = block_exclusive_scan<double, kSelBlock>(loc, sm.red, &tot);
+  for (int j = 0; j < per; ++j) if (s0 + j < C) { sm.pref[s0 + j] = ex; ex += dval(sm.cand[s0 + j]); }
+  if (threadIdx.x == 0) sm.pref[C] = tot;
+  __syncthreads();
+}
+
+// Phi on the sorted candidates (valid for t >= the smallest candidate); also the
+// active sets of the piece that holds t.
+struct Piece {
+  double phi, SA, SB;
+  int nA, nB;
+};
+
+__device__ Piece phi_at(const SelSmem& sm, double th, int q, int C, double rho, double M) {
+  int lo = 0, hi = q;   // first top t with theta_t < th (theta_t non-increasing)
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (sm.tb[mid] < th) hi = mid; else lo = mid + 1;
+  }
+  const int t0 = lo;
+  lo = q; hi = C;       // first tail j with a_j <= th
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (dval(sm.cand[mid]) <= th) hi = mid; else lo = mid + 1;
+  }
+  Piece e;
+  e.nA = q - t0;
+  e.SA = sm.pref[q] - sm.pref[t0];
+  e.nB = lo - q;
+  e.SB = sm.pref[lo] - sm.pref[q];
+  e.phi = (double)e.nA * (th + fmin(rho * th, M)) - e.SA - (e.SB - (double)e.nB * th);
+  return e;
+}
+
+// Root of Phi on [floorv, inf) by binary search over the two sorted breakpoint
+// sequences (thread 0).  Returns false when Phi(floorv) > 0 and floorv is a
+// true floor (the pooled block reaches below the candidates).
+__device__ bool root_search(const SelSmem& sm, int q, int C, double floorv, bool floor_is_zero,
+                            double rho, double M, double* theta) {
+  if (!floor_is_zero && phi_at(sm, floorv, q, C, rho, M).phi > 0.0) return false;
+  double lo = floorv, hi = INFINITY;
+  // tail breakpoints a_j, j in [q, C): Phi(a_j) is non-increasing in j
+  int a = q, b = C;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (phi_at(sm, dval(sm.cand[m]), q, C, rho, M).phi <= 0.0) b = m; else a = m + 1;
+  }
+  if (a < C) lo = fmax(lo, dval(sm.cand[a]));
+  if (a > q) hi = fmin(hi, dval(sm.cand[a - 1]));
+  // top breakpoints theta_t, t in [0, q): non-increasing in t
+  a = 0; b = q;
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if (phi_at(sm, sm.tb[m], q, C, rho, M).phi <= 0.0) b = m; else a = m + 1;
+  }
+  if (a < q && sm.tb[a] >= floorv) lo = fmax(lo, sm.tb[a]);
+  if (a > 0) hi = fmin(hi, sm.tb[a - 1]);
+  const double thM = M / rho;
+  if (thM >= floorv) {
+    const double v = phi_at(sm, thM, q, C, rho, M).phi;
+    if (v <= 0.0) lo = fmax(lo, thM);
+    if (v >= 0.0) hi = fmin(hi, thM);
+  }
+  double th;
+  if (!(hi > lo)) {
+    th = isinf(hi) ? lo : hi;
+  } else {
+    const double mid = 0.5 * (lo + hi);
+    const Piece e = phi_at(sm, mid, q, C, rho, M);
+    th = (rho * mid < M) ? (e.SA + e.SB) / ((double)e.nA * (1.0 + rho) + (double)e.nB)
+                         : (e.SA + e.SB - (double)e.nA * M) / (double)(e.nA + e.nB);
+    th = fmin(fmax(th, lo), hi);
+  }
+  *theta = th;
+  return true;
+}
+
+// the magnitude a selection key stands for: |w_i| on the free set; key 0 marks a
+// coordinate off the free set (or one below the float range), taken as 0
+__device__ __forceinline__ double key_value(unsigned kk, const double* w, int i) {
+  return kk == 0u ? 0.0 : fabs(__ldcg(&w[i]));
+}
+
+// membership of coordinate i in the top set (exact Alg. 1 order)
+__device__ __forceinline__ bool in_top(unsigned kk, double a, int i, unsigned thr, int q,
+                                       double bnd_a, int bnd_i) {
+  if (q <= 0) return false;
+  if (kk != thr) return kk > thr;
+  return bnd_a < 0.0 || a > bnd_a || (a == bnd_a && i <= bnd_i);
+}
+
+// bracketed Newton on Phi over full passes of w (pooled blocks wider than the
+// candidate capacity); hi0 has Phi(hi0) > 0
+__device__ double root_fullpass_global(const Dev& d, SelSmem& sm, int q, unsigned thr, double bnd_a,
+                                       int bnd_i, double hi0, double rho, double M) {
+  const int p = d.p;
+  const double* w = (const double*)d.wbuf;
+  double lo = 0.0, hi = hi0, th = hi0;
+  for (int it = 0; it < 200; ++it) {
+    double nA = 0, SA = 0, nB = 0, SB = 0;
+    for (int i = threadIdx.x; i < p; i += kSelBlock) {
+      const unsigned kk = __ldcg(&d.key[i]);
+      const double a = key_value(kk, w, i);
+      if (in_top(kk, a, i, thr, q, bnd_a, bnd_i)) {
+        if (top_break(a, rho, M) < th) { nA += 1; SA += a; }
+      } else if (a > th) {
+        nB += 1;
+        SB += a;
+      }
+    }
+    nA = block_sum<double, kSelBlock>(nA, sm.red);
+    SA = block_sum<double, kSelBlock>(SA, sm.red);
+    nB = block_sum<double, kSelBlock>(nB, sm.red);
+    SB = block_sum<double, kSelBlock>(SB, sm.red);
+    const double phi = nA * (th + fmin(rho * th, M)) - SA - (SB - nB * th);
+    if (phi == 0.0) return th;
+    if (phi < 0.0) lo = th; else hi = th;
+    const double cand = (nA + nB > 0) ? ((rho * th < M) ? (SA + SB) / (nA * (1.0 + rho) + nB)
+                                                        : (SA + SB - nA * M) / (nA + nB))
+                                      : 0.5 * (lo + hi);
+    const bool ok = cand > lo && cand < hi;
+    const double next = ok ? cand : 0.5 * (lo + hi);
+    if (ok && it > 0 && fabs(next - th) <= 2e-15 * fabs(th)) return next;
+    if (hi - lo <= 2e-16 * hi) return ok ? next : hi;
+    th = next;
+  }
+  return th;
+}
+
+__device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
+  const int p = d.p;
+  const double rho = nd->rho, M = nd->M;
+  const double shrink = rho / (1.0 + rho);
+  const unsigned* key = d.key;
+  const double* w = (const double*)d.wbuf;
+  auto kload = [&](int i) -> unsigned { return __ldcg(&key[i]); };
+  unsigned thr = 0xffffffffu;
+  double bnd_a = -1.0, theta = INFINITY;
+  int bnd_i = 0x7fffffff, qused = 0, fb = 0;
+  bool sorted_top = false;
+  if (q > 0) {
+    const SelectResult<unsigned> Rk = block_select<unsigned, kSelBlock>(p, q, kload, sm.hist, sm.sh, d.hist);
+    thr = Rk.thr;
+    const int need = q - Rk.gt, eq = Rk.eq;
+    if (need < eq && eq <= kProxCap && thr != 0u) {
+      // exact order among equal float keys: |w| descending, then index ascending
+      if (threadIdx.x == 0) sm.flag[0] = 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < p; i += kSelBlock) {
+        if (__ldcg(&key[i]) == thr) {
+          const int pos = atomicAdd(&sm.flag[0], 1);
+          sm.cand[pos] = dbits(fabs(__ldcg(&w[i])));
+          sm.cidx[pos] = i;
+        }
+      }
+      __syncthreads();
+      const int N = next_pow2(eq);
+      for (int j = eq + threadIdx.x; j < N; j += kSelBlock) { sm.cand[j] = 0ull; sm.cidx[j] = 0x7fffffff; }
+      __syncthreads();
+      sort_pairs_desc(sm.cand, sm.cidx, N);
+      bnd_a = dval(sm.cand[need - 1]);
+      bnd_i = sm.cidx[need - 1];
+      __syncthreads();
+    }
+    if (q == p || thr == 0u) {
+      theta = 0.0;   // no tail (or only zeros in it): no isotonic violation
+    } else {
+      int Q = nd->qhint > q + 1 ? nd->qhint : q + 1;
+      if (Q > p) Q = p;
+      bool found = false;
+      double last_floor = INFINITY;
+      while (!found && Q <= kProxCap) {
+        unsigned thrQ = 0u;
+        int C = p;
+        if (Q < p) {
+          const SelectResult<unsigned> RQ =
+              block_select<unsigned, kSelBlock>(p, Q, kload, sm.hist, sm.sh, d.hist);
+          thrQ = RQ.thr;
+          C = RQ.gt + RQ.eq;
+        }
+        if (C > kProxCap) break;
+        if (threadIdx.x == 0) sm.flag[0] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < p; i += kSelBlock) {
+          const unsigned kk = __ldcg(&key[i]);
+          if (Q >= p || kk >= thrQ) {
+            const int pos = atomicAdd(&sm.flag[0], 1);
+            sm.cand[pos] = dbits(key_value(kk, w, i));
+          }
+        }
+        __syncthreads();
+        const int N = next_pow2(C);
+        for (int j = C + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
+        __syncthreads();
+        sort_u64_desc(sm.cand, N);
+        prefix_values(sm, C);
+        for (int t = threadIdx.x; t < q; t += kSelBlock) sm.tb[t] = top_break(dval(sm.cand[t]), rho, M);
+        __syncthreads();
+        const double floorv = (Q < p) ? dval(sm.cand[C - 1]) : 0.0;
+        if (threadIdx.x == 0) {
+          double th = 0.0;
+          sm.flag[1] = root_search(sm, q, C, floorv, Q >= p, rho, M, &th) ? 1 : 0;
+          sm.root[0] = th;
+        }
+        __syncthreads();
+        found = sm.flag[1] != 0;
+        theta = sm.root[0];
+        qused = C;
+        last_floor = floorv;
+        __syncthreads();
+        if (!found) {   // grow, and try the full capacity before giving up
+          if (Q >= p || Q >= kProxCap) break;
+          Q = 4 * Q;
+          if (Q > kProxCap) Q = kProxCap;
+          if (Q > p) Q = p;
+        }
+      }
+      if (found) {
+        sorted_top = true;
+      } else {
+        fb = 1;
+        theta = root_fullpass_global(d, sm, q, thr, bnd_a, bnd_i,
+                                     isinf(last_floor) ? (double)__uint_as_float(thr) * 2.0 + 1e-300
+                                                       : last_floor, rho, M);
+      }
+    }
+    // |b| on the top set, descending (its order is the order of |w|), for Alg. 2
+    if (!sorted_top) {
+      if (threadIdx.x == 0) sm.flag[0] = 0;
+      __syncthreads();
+      const int C = Rk.gt + Rk.eq;
+      if (C <= kProxCap) {
+        for (int i = threadIdx.x; i < p; i += kSelBlock) {
+          const unsigned kk = __ldcg(&key[i]);
+          if (kk >= thr) sm.cand[atomicAdd(&sm.flag[0], 1)] = dbits(key_value(kk, w, i));
+        }
+        __syncthreads();
+        const int N = next_pow2(C);
+        for (int j = C + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
+        __syncthreads();
+        sort_u64_desc(sm.cand, N);
+      } else {  // massive ties of the float key: its value stands for the tied ones
+        for (int i = threadIdx.x; i < p; i += kSelBlock) {
+          const unsigned kk = __ldcg(&key[i]);
+          if (kk > thr) sm.cand[atomicAdd(&sm.flag[0], 1)] = dbits(key_value(kk, w, i));
+        }
+        __syncthreads();
+        for (int j = Rk.gt + threadIdx.x; j < q; j += kSelBlock)
+          sm.cand[j] = dbits((double)__uint_as_float(thr));
+        const int N = next_pow2(q);
+        for (int j = q + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
+        __syncthreads();
+        sort_u64_desc(sm.cand, N);
+      }
+    }
+    for (int t = threadIdx.x; t < q; t += kSelBlock) {
+      const double a = dval(sm.cand[t]);
+      const double mg = fmin(fmin(M, shrink * a), a - theta);
+      d.tbeta[t] = mg > 0.0 ? mg : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    nd->theta = theta;
+    nd->thr_kf = thr;
+    nd->bnd_a = bnd_a;
+    nd->bnd_i = bnd_i;
+    nd->q = q;
+    int h = qused / 2;
+    if (h < q + 64) h = q + 64;
+    nd->qhint = h;
+    nd->fallback += fb;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < 2048; b += kSelBlock) d.hist[b] = 0u;   // ready for the next step
+}
+
+// In-loop dual term (Sec. 3.4) at zeta_gamma: a = X^T zeta_gamma = -grad;
+// G*(a)/(2 lambda2) = TopSum_k'(H_M(|a_F|/2l2)) + sum_S1 H_M(|a_j|/2l2).
+__device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
+  const int p = d.p;
+  const double scale = 1.0 / (2.0 * nd->lambda2), M = nd->M;
+  const double* g = d.grad;
+  const int8_t* st = d.state;
+  double s1 = 0.0;
+  for (int i = threadIdx.x; i < p; i += kSelBlock)
+    if (st && st[i] == kOne) s1 += huber(fabs(g[i]) * scale, M);
+  s1 = block_sum<double, kSelBlock>(s1, sm.red);
+  double s = 0.0;
+  if (q > 0) {
+    auto kload = [&](int i) -> unsigned { return __ldcg(&d.dkey[i]); };
+    const SelectResult<unsigned> R =
+        block_select<unsigned, kSelBlock>(p, q, kload, sm.hist, sm.sh, d.hist + 2048);
+    for (int i = threadIdx.x; i < p; i += kSelBlock)
+      if (__ldcg(&d.dkey[i]) > R.thr) s += huber(fabs(g[i]) * scale, M);
+    s = block_sum<double, kSelBlock>(s, sm.red);
+    const int need = q - R.gt;
+    if (need > 0) {
+      if (R.eq <= kProxCap) {   // the `need` largest exact values among equal float keys
+        if (threadIdx.x == 0) sm.flag[0] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < p; i += kSelBlock) {
+          const unsigned kk = __ldcg(&d.dkey[i]);
+          if (kk == R.thr) sm.cand[atomicAdd(&sm.flag[0], 1)] = dbits(key_value(kk, g, i));
+        }
+        __syncthreads();
+        const int N = next_pow2(R.eq);
+        for (int j = R.eq + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
+        __syncthreads();
+        sort_u64_desc(sm.cand, N);
+        double b = 0.0;
+        for (int j = threadIdx.x; j < need; j += kSelBlock) b += huber(dval(sm.cand[j]) * scale, M);
+        s += block_sum<double, kSelBlock>(b, sm.red);
+      } else {
+        s += (double)need * huber((double)__uint_as_float(R.thr) * scale, M);
+      }
+    }
+  }
+  if (threadIdx.x == 0) nd->gstar = s1 + s;
+  __syncthreads();
+  for (int b = threadIdx.x; b < 2048; b += kSelBlock) d.hist[2048 + b] = 0u;
+}
+
+__global__ void __launch_bounds__(kSelBlock, 1) k_prox_select(Dev d) {
+  NodeDev* nd = d.nd;
+  if (nd->done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SelSmem& sm = *reinterpret_cast<SelSmem*>(smem_raw);
+  const int kp = nd->kp;
+  const int q = kp <= 0 ? 0 : (kp < d.p ? kp : d.p);
+  if (blockIdx.x == 0) prox_select_cta(d, nd, sm, q);
+  else dual_cta(d, nd, sm, q);
+}
+
+// ------------------------------------------------------------------ apply
+
+__global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
+  NodeDev* nd = d.nd;
+  if (nd->done) return;
+  __shared__ double red[64];
+  __shared__ int shi[64];
+  __shared__ int wcnt[kSegLen / 32];
+  __shared__ int s_last;
+  const int p = d.p, seg = blockIdx.x;
+  const int j = seg * kSegLen + (int)threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nxt = (nd->iter + 1) % 3;
+  double* bn = (double*)d.beta + (size_t)nxt * p;
+  const double theta = nd->theta, rho = nd->rho, M = nd->M, bnd_a = nd->bnd_a;
+  const double shrink = rho / (1.0 + rho);
+  const unsigned thr = nd->thr_kf;
+  const int q = nd->q, bnd_i = nd->bnd_i;
+  double l1 = 0.0, s1 = 0.0;
+  bool nz = false;
+  if (j < p) {
+    const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
+    const double w = ((const double*)d.wbuf)[j];
+    double b;
+    if (st == kFree) {
+      const double a = fabs(w);
+      double mag = in_top(d.key[j], a, j, thr, q, bnd_a, bnd_i) ? fmin(fmin(M, shrink * a), a - theta)
+                                                                 : fmax(0.0, a - theta);
+      if (!(mag > 0.0)) mag = 0.0;
+      b = w < 0.0 ? -mag : mag;
+      l1 = mag;
+    } else if (st == kZero) {
+      b = 0.0;
+    } else {   // z_j = 1: argmin 1/2 (b - w)^2 + b^2/(2 rho) on the box
+      b = fmin(fmax(rho * w / (1.0 + rho), -M), M);
+      s1 = b * b;
+    }
+    bn[j] = b;
+    const float hi = (float)b;
+    d.bhi[j] = hi;
+    d.blo[j] = (float)(b - (double)hi);
+    nz = b != 0.0;
+  }
+  // ordered compaction of this segment's nonzeros
+  const unsigned bal = __ballot_sync(0xffffffffu, nz);
+  if (lane == 0) wcnt[warp] = __popc(bal);
+  __syncthreads();
+  int base = 0, tot = 0;
+  for (int k = 0; k < kSegLen / 32; ++k) {
+    if (k < warp) base += wcnt[k];
+    tot += wcnt[k];
+  }
+  if (nz) d.nnz_idx[seg * kSegLen + base + __popc(bal & ((1u << lane) - 1u))] = j;
+  l1 = block_sum<double, kSegLen>(l1, red);
+  s1 = block_sum<double, kSegLen>(s1, red);
+  if (threadIdx.x == 0) {
+    d.seg_cnt[seg] = tot;
+    d.segpart[seg] = l1;
+    d.segpart[d.nseg + seg] = s1;
+  }
+  __threadfence();
+  __syncthreads();
+  const int ci = cnt_apply(d);
+  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[ci], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: segment offsets, totals, and g(b) by Algorithm 2's water-filling on
+  // the top set (its |b| in descending order from the select kernel)
+  int running = 0;
+  for (int b0 = 0; b0 < d.nseg; b0 += kSegLen) {
+    const int i = b0 + (int)threadIdx.x;
+    const int v = i < d.nseg ? __ldcg(&d.seg_cnt[i]) : 0;
+    int t2;
+    const int ex = block_exclusive_scan<int, kSegLen>(v, shi, &t2);
+    if (i < d.nseg) d.seg_off[i] = running + ex;
+    running += t2;
+  }
+  double L1 = 0.0, S1 = 0.0;
+  for (int i = threadIdx.x; i < d.nseg; i += kSegLen) {
+    L1 += __ldcg(&d.segpart[i]);
+    S1 += __ldcg(&d.segpart[d.nseg + i]);
+  }
+  L1 = block_sum<double, kSegLen>(L1, red);
+  S1 = block_sum<double, kSegLen>(S1, red);
+  if (threadIdx.x == 0) {
+    d.seg_off[d.nseg] = running;
+    nd->nnz = running;
+    nd->l1 = L1;
+    nd->s1sq = S1;
+    const int kp = nd->kp;
+    double g = 0.0, sq = 0.0, cum = 0.0;
+    bool brk = false;
+    for (int t = 0; t < q; ++t) {
+      const double bt = __ldcg(&d.tbeta[t]);
+      const double sbar = (L1 - cum) / (double)(kp - t);
+      if (sbar >= bt) {
+        g = 0.5 * (sq + (double)(kp - t) * sbar * sbar);
+        brk = true;
+        break;
+      }
+      sq += bt * bt;
+      cum += bt;
+    }
+    if (!brk) {
+      if (q < kp) {
+        const double sbar = fmax(0.0, (L1 - cum) / (double)(kp - q));
+        g = 0.5 * (sq + (double)(kp - q) * sbar * sbar);
+      } else {
+        g = 0.5 * sq;
+      }
+    }
+    nd->g_next = 0.5 * S1 + g;
+    d.cnt[ci] = 0;
+  }
+}
+
+// ------------------------------------------------------------------ Lanczos
+
+constexpr int kVecBlock = 256;
+
+__host__ __device__ inline int vec_grid(int n) {
+  const int g = (n + kVecBlock - 1) / kVecBlock;
+  return g < 1216 ? g : 1216;   // 8 CTAs per SM; partials fit the segment arrays
+}
+
+__global__ void __launch_bounds__(kVecBlock) k_split(const double* src, float* hi, float* lo, int n) {
+  for (int i = blockIdx.x * kVecBlock + threadIdx.x; i < n; i += gridDim.x * kVecBlock) {
+    const double v = src[i];
+    const float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
+
+__global__ void __launch_bounds__(kVecBlock) k_lz_start(Dev d, double inv_norm) {
+  for (int i = blockIdx.x * kVecBlock + threadIdx.x; i < d.p; i += gridDim.x * kVecBlock) {
+    const double v = (1.0 + (double)((unsigned long long)(i + 1) * 2654435761ull % 1000ull) / 1000.0) * inv_norm;
+    d.vcur[i] = v;
+    d.vprev[i] = 0.0;
+    const float h = (float)v;
+    d.vhi[i] = h;
+    d.vlo[i] = (float)(v - (double)h);
+  }
+}
+
+// phase 0: w = X^T X v - beta_{it-1} v_prev, alpha = w.v
+// phase 1: w -= alpha v, beta = ||w||
+// phase 2: v_prev = v, v = w / beta (and its float split)
+template <int PHASE>
+__global__ void __launch_bounds__(kVecBlock) k_lz(Dev d, int it) {
+  __shared__ double red[64];
+  __shared__ int s_last;
+  double* w = (double*)d.wbuf;
+  const double* alpha = d.lz;
+  const double* beta = d.lz + kLanczosMax;
+  double acc = 0.0;
+  const double bprev = (PHASE == 0 && it > 0) ? beta[it - 1] : 0.0;
+  const double al = (PHASE == 1) ? alpha[it] : 0.0;
+  const double inv_b = (PHASE == 2) ? (beta[it] > 0.0 ? 1.0 / beta[it] : 0.0) : 0.0;
+  for (int i = blockIdx.x * kVecBlock + threadIdx.x; i < d.p; i += gridDim.x * kVecBlock) {
+    if (PHASE == 0) {
+      const double v = d.grad[i] - bprev * d.vprev[i];
+      w[i] = v;
+      acc += v * d.vcur[i];
+    } else if (PHASE == 1) {
+      const double v = w[i] - al * d.vcur[i];
+      w[i] = v;
+      acc += v * v;
+    } else {
+      const double v = w[i] * inv_b;
+      d.vprev[i] = d.vcur[i];
+      d.vcur[i] = v;
+      const float h = (float)v;
+      d.vhi[i] = h;
+      d.vlo[i] = (float)(v - (double)h);
+    }
+  }
+  if (PHASE == 2) return;
+  acc = block_sum<double, kVecBlock>(acc, red);
+  if (threadIdx.x == 0) d.segpart[blockIdx.x] = acc;
+  __threadfence();
+  __syncthreads();
+  const int ci = cnt_lz(d);
+  if (threadIdx.x == 0) s_last = (atomicAdd(&d.cnt[ci], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kVecBlock) s += __ldcg(&d.segpart[b]);
+  s = block_sum<double, kVecBlock>(s, red);
+  if (threadIdx.x == 0) {
+    if (PHASE == 0) d.lz[it] = s;
+    else d.lz[kLanczosMax + it] = sqrt(s);
+    d.cnt[ci] = 0;
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+
+void launch_fwd_raw(const Dev& d, cudaStream_t s);   // k_matvec.cu
+void launch_grad_raw(const Dev& d, cudaStream_t s);
+
+void prox_grid_prepare(int optin) {
+  cudaFuncSetAttribute(k_prox_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(SelSmem) < optin ? (int)sizeof(SelSmem) : optin);
+}
+
+void launch_prox_select(const Dev& d, cudaStream_t s) {
+  k_prox_select<<<2, kSelBlock, sizeof(SelSmem), s>>>(d);
+}
+
+void launch_prox_apply(const Dev& d, cudaStream_t s) {
+  k_prox_apply<<<d.nseg, kSegLen, 0, s>>>(d);
+}
+
+void launch_split(const double* src, float* hi, float* lo, int n, cudaStream_t s) {
+  k_split<<<vec_grid(n), kVecBlock, 0, s>>>(src, hi, lo, n);
+}
+
+void launch_lanczos_start(const Dev& d, cudaStream_t s, double inv_norm) {
+  k_lz_start<<<vec_grid(d.p), kVecBlock, 0, s>>>(d, inv_norm);
+}
+
+void launch_lanczos_step(const Dev& d, cudaStream_t s, int it) {
+  launch_fwd_raw(d, s);
+  launch_grad_raw(d, s);
+  const int g = vec_grid(d.p);
+  k_lz<0><<<g, kVecBlock, 0, s>>>(d, it);
+  k_lz<1><<<g, kVecBlock, 0, s>>>(d, it);
+  k_lz<2><<<g, kVecBlock, 0, s>>>(d, it);
+}
+
+}  // namespace ksc

@@ -78,13 +78,14 @@ struct ksc_problem {
   int64_t k_launches[3] = {0, 0, 0};
   double k_ms[3] = {0, 0, 0};
   int64_t launches = 0;   // every kernel launch issued for this problem
+  int32_t last_sparse_steps = 0, last_fallback_steps = 0;
 };
 
 // kernels per launcher (kept beside the launchers they count)
-static constexpr int kLaunchesPerStep = 3;      // gradient, prox, forward
-static constexpr int kLaunchesPerCert = 4;      // prep, forward, gradient, final
-static constexpr int kLaunchesPerInit = 2;      // g value, forward
-static constexpr int kLaunchesPerPower = 3;     // forward, gradient, normalise
+static constexpr int kLaunchesPerStep = 5;      // gradient, prox select, prox apply, 2 forward
+static constexpr int kLaunchesPerCert = 5;      // prep, 2 forward, gradient, final
+static constexpr int kLaunchesPerInit = 3;      // g value, split, forward
+static constexpr int kLaunchesPerLanczos = 5;   // forward, gradient, three vector phases
 
 // the iterate vectors are FP64 for every storage type of X
 static size_t tbytes(int) { return 8; }
@@ -126,7 +127,6 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.u, 3 * n * 8);
   ALLOC(d.grad, p * 8);
   ALLOC(d.wbuf, p * tb);
-  ALLOC(d.nnz_val, p * tb);
   ALLOC(d.nnz_idx, p * sizeof(int));
   ALLOC(d.ws, (size_t)grad_nrb(d) * p * 8);
   ALLOC(d.cnt, (size_t)cnt_total(d) * sizeof(int));
@@ -141,45 +141,104 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(cn, p * 8);
   d.colnorm = cn;
   ALLOC(d.state, p);
-  ALLOC(d.pow_v, p * tb);
-  ALLOC(d.pow_lam, 4096 * 8);
+  d.nseg = (int)((p + kSegLen - 1) / kSegLen);
+  ALLOC(d.key, p * 4);
+  ALLOC(d.dkey, p * 4);
+  ALLOC(d.hist, 2 * 2048 * 4);
+  ALLOC(d.bhi, p * 4);
+  ALLOC(d.blo, p * 4);
+  ALLOC(d.seg_cnt, (size_t)d.nseg * 4);
+  ALLOC(d.seg_off, (size_t)(d.nseg + 1) * 4);
+  ALLOC(d.segpart, (size_t)2 * d.nseg * 8);
+  ALLOC(d.tbeta, (size_t)kProxCap * 8);
+  ALLOC(d.vcur, p * 8);
+  ALLOC(d.vprev, p * 8);
+  ALLOC(d.vhi, p * 4);
+  ALLOC(d.vlo, p * 4);
+  ALLOC(d.lz, 2 * kLanczosMax * 8);
   ALLOC(d.nd, sizeof(NodeDev));
+  ALLOC(d.sp_part, (size_t)kSpSplit * n * 8);
+  ALLOC(d.cnt_sp, (size_t)sp_nrb(d) * 4);
+  {
+    void* xc = nullptr;
+    d.ldc = (n + 7) / 8 * 8;
+    ALLOC(xc, (size_t)d.ldc * p * xbytes(pr->xdt));
+    d.Xc = xc;
+  }
 #undef ALLOC
   KSC_CUDA(cudaMemset(d.cnt, 0, (size_t)cnt_total(d) * sizeof(int)));
   KSC_CUDA(cudaMemset(d.beta, 0, 3 * p * tb));
   KSC_CUDA(cudaMemset(d.u, 0, 3 * n * 8));
   KSC_CUDA(cudaMemset(d.state, 0, p));
   KSC_CUDA(cudaMemset(d.nd, 0, sizeof(NodeDev)));
+  KSC_CUDA(cudaMemset(d.hist, 0, 2 * 2048 * 4));
+  KSC_CUDA(cudaMemset(d.cnt_sp, 0, (size_t)sp_nrb(d) * 4));
   return KSC_OK;
 }
 
-static ksc_status power_iteration(ksc_problem* pr, cudaStream_t s) {
-  Dev& d = pr->dev;
-  launch_power_init(d, s);
-  pr->launches += 2;
-  KSC_CUDA(cudaGetLastError());
-  const int max_it = 4000;
-  const double tol = 1e-6;
-  std::vector<double> lam(max_it);
-  int it = 0;
-  double lmax = 0.0;
-  while (it < max_it) {
-    const int upto = std::min(max_it, it + 10);
-    for (; it < upto; ++it) launch_power_step(d, s, it);
-    pr->launches += (int64_t)kLaunchesPerPower * 10;
-    KSC_CUDA(cudaGetLastError());
-    KSC_CUDA(cudaMemcpyAsync(lam.data(), d.pow_lam, it * sizeof(double), cudaMemcpyDeviceToHost, s));
-    KSC_CUDA(cudaStreamSynchronize(s));
-    bool conv = false;
-    for (int j = 1; j < it; ++j) {
-      if (std::fabs(lam[j] - lam[j - 1]) <= tol * lam[j]) { conv = true; lmax = lam[j]; pr->power_iters = j + 1; break; }
+// Largest eigenvalue of the symmetric tridiagonal (alpha[0..m), beta[0..m-1))
+// by bisection on the Sturm count (number of eigenvalues below x).
+static double tridiag_max_eig(const double* alpha, const double* beta, int m) {
+  double lo = alpha[0], hi = alpha[0];
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(beta[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(beta[i]) : 0.0);
+    lo = std::min(lo, alpha[i] - r);
+    hi = std::max(hi, alpha[i] + r);
+  }
+  auto below = [&](double x) {
+    int c = 0;
+    double q = alpha[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < m; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = (alpha[i] - x) - beta[i - 1] * beta[i - 1] / q;
+      if (q < 0) ++c;
     }
-    if (conv) break;
-    lmax = lam[it - 1];
-    pr->power_iters = it;
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fabs(hi); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (below(mid) >= m) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// lambda_max(X^T X) by the Lanczos iteration (FP64 vectors, error-free products):
+// the largest Ritz value converges far faster than power iteration on spectra
+// with a small relative gap at the top.
+static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
+  Dev& d = pr->dev;
+  double nrm = 0.0;
+  for (int64_t j = 0; j < pr->p; ++j) {
+    const double v = 1.0 + (double)((unsigned long long)(j + 1) * 2654435761ull % 1000ull) / 1000.0;
+    nrm += v * v;
+  }
+  launch_lanczos_start(d, s, 1.0 / std::sqrt(nrm));
+  pr->launches += 1;
+  KSC_CUDA(cudaGetLastError());
+  std::vector<double> hlz(2 * kLanczosMax);
+  const int maxit = (int)std::min<int64_t>(kLanczosMax, pr->p);
+  double theta = 0.0, prev = -1.0;
+  int it = 0;
+  while (it < maxit) {
+    const int upto = std::min(maxit, it + 8);
+    for (; it < upto; ++it) launch_lanczos_step(d, s, it);
+    pr->launches += (int64_t)kLaunchesPerLanczos * 8;
+    KSC_CUDA(cudaGetLastError());
+    KSC_CUDA(cudaMemcpyAsync(hlz.data(), d.lz, 2 * kLanczosMax * sizeof(double), cudaMemcpyDeviceToHost, s));
+    KSC_CUDA(cudaStreamSynchronize(s));
+    int m = it;
+    bool breakdown = false;
+    for (int j = 0; j < it; ++j) {
+      if (!(hlz[kLanczosMax + j] > 1e-13 * std::fabs(hlz[0]) + 1e-300)) { m = j + 1; breakdown = true; break; }
+    }
+    theta = tridiag_max_eig(hlz.data(), hlz.data() + kLanczosMax, m);
+    pr->power_iters = m;
+    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-9 * theta)) break;
+    prev = theta;
   }
   const double cf = pr->loss == KSC_LOSS_LSQ ? 2.0 : 0.25;
-  pr->L = cf * lmax * 1.01;
+  pr->L = cf * theta * 1.01;
   return KSC_OK;
 }
 
@@ -245,7 +304,7 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   }
   d.y = pr->y;
   if ((st = alloc_workspace(pr)) != KSC_OK) return bail(st);
-  d.nnz_cap = std::max(1, d.p / 12);
+  d.sp_cap = std::max(1, d.p / 2);
   // keep w in shared memory when it fits beside the prox buffers
   {
     size_t lim = prox_smem_limit();
@@ -253,12 +312,13 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
     t.prox_wsm = d.p;
     d.prox_wsm = (prox_smem_bytes(t) <= lim) ? d.p : 0;
   }
+  launch_transpose(d, s);
   launch_colnorm(d, s);
-  pr->launches += 1;
+  pr->launches += 2;
   if (cudaGetLastError() != cudaSuccess) return bail(fail(KSC_ERR_CUDA, "colnorm launch failed"));
   if (desc->lipschitz > 0) {
     pr->L = desc->lipschitz;
-  } else if ((st = power_iteration(pr, s)) != KSC_OK) {
+  } else if ((st = lanczos_lmax(pr, s)) != KSC_OK) {
     return bail(st);
   }
   cudaError_t e = cudaStreamSynchronize(s);
@@ -390,7 +450,7 @@ static ksc_status replay(ksc_problem* pr, cudaStream_t s, NodeDev* h) {
   if (prof) {
     const int steps = std::min(kStepsPerGraph, h->iter - before);
     for (int k = 0; k < steps; ++k) {
-      for (int j = 0; j < 3; ++j) {
+      for (int j = 0; j < 3; ++j) {   // gradient, prox (select + apply), forward
         float ms = 0.f;
         KSC_CUDA(cudaEventElapsedTime(&ms, pr->events[4 * k + j], pr->events[4 * k + j + 1]));
         pr->k_ms[j] += ms;
@@ -490,6 +550,8 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     KSC_CUDA(cudaMemcpyAsync(d.nd, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
     h = upd;
   }
+  pr->last_sparse_steps = h.sparse_steps;
+  pr->last_fallback_steps = h.fallback;
   res->primal = h.cert_primal;
   res->dual_bound = h.cert_dual;
   res->rel_gap = h.cert_gap;
@@ -588,6 +650,14 @@ extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M,
   launch_gstar_prim((const double*)ba.p, (int)p, k, M, (double*)bo.p, 0);
   KSC_CUDA(cudaGetLastError());
   KSC_CUDA(cudaMemcpy(out, bo.p, 8, cudaMemcpyDeviceToHost));
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* sparse_steps,
+                                              int32_t* fallback_steps) {
+  if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
+  if (sparse_steps) *sparse_steps = problem->last_sparse_steps;
+  if (fallback_steps) *fallback_steps = problem->last_fallback_steps;
   return KSC_OK;
 }
 

@@ -151,8 +151,11 @@ struct SelectResult {
   int eq;
 };
 
+// first (optional): the histogram of the first digit (key >> (BITS - 11)), already
+// counted elsewhere -- it replaces the first pass over the keys.
 template <typename U, int BLOCK, typename Load>
-__device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist, int* sh) {
+__device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist, int* sh,
+                                        const unsigned* first = nullptr) {
   constexpr int BITS = (int)sizeof(U) * 8;
   constexpr int DIG = 11;
   constexpr int NB = 1 << DIG;
@@ -164,11 +167,12 @@ __device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist,
     const int w = hi < DIG ? hi : DIG;
     const int lo = hi - w;
     const U himask = (hi >= BITS) ? (U)0 : (~(U)0 << hi);
-    for (int b = threadIdx.x; b < NB; b += BLOCK) hist[b] = 0u;
+    const bool given = (hi == BITS) && first != nullptr;
+    for (int b = threadIdx.x; b < NB; b += BLOCK) hist[b] = given ? __ldcg(&first[b]) : 0u;
     __syncthreads();
     // warp-uniform loop; lanes with the same bin are aggregated (__match_any_sync)
     // so that runs of equal keys (e.g. zeros) do not serialise on one counter
-    for (int base = 0; base < m; base += BLOCK) {
+    for (int base = 0; base < (given ? 0 : m); base += BLOCK) {
       const int i = base + (int)threadIdx.x;
       int bin = -1;
       if (i < m) {

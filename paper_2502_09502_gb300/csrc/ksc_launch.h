@@ -19,6 +19,12 @@ constexpr int kFwdThreads = 256;    // forward pass: 8 warps
 constexpr int kFwdRows = 32;        // forward pass: 4 rows per warp
 constexpr int kFwdChunk = 2048;     // forward pass: staged columns of beta
 constexpr int kProxCap = 4096;      // prox candidates (k' + pooled tail) in shared memory
+constexpr int kSegLen = 256;        // prox apply: coordinates per CTA (one compaction segment)
+constexpr int kMaxSegSparse = 4096; // sparse forward pass needs p <= kSegLen * this
+constexpr int kSpRows = 256;        // sparse forward pass: rows per CTA (one per thread)
+constexpr int kSpSplit = 8;         // sparse forward pass: chunks of the nonzero list
+constexpr int kSpStage = 1024;      // sparse forward pass: list entries staged per round
+constexpr int kLanczosMax = 512;    // Lanczos steps for lambda_max(X^T X)
 
 __host__ __device__ inline int cols_per_thread(int xdt) { return xdt == kXF64 ? 2 : (xdt == kXF32 ? 4 : 8); }
 
@@ -26,6 +32,8 @@ struct Dev {
   int xdt;
   const void* X;
   int64_t ldx;
+  const void* Xc;          // column-major copy of X (ldc >= n), for the sparse forward pass
+  int64_t ldc;
   int n, p;
   int vec;                 // rows are 16-byte aligned: vector loads
   int loss;
@@ -36,9 +44,10 @@ struct Dev {
   double* u;               // 3 slots x n: X beta in FP64
   double* grad;            // p: X^T grad F(u_gamma) in FP64
   void* wbuf;              // p, FP64 prox scratch
-  void* nnz_val;           // p, FP64
-  int* nnz_idx;            // p
-  int nnz_cap;             // sparse forward pass when nnz <= nnz_cap
+  int* nnz_idx;            // p: nonzeros of the newest iterate, kSegLen-long segments
+  int sp_cap;              // sparse (column-major) forward pass when nnz <= sp_cap
+  double* sp_part;         // kSpSplit x n partial products of the sparse forward pass
+  int* cnt_sp;             // ceil(n / kSpRows) completion counters
   void* ws;                // gradient partials: nrb x p doubles
   int* cnt;                // completion counters (zeroed once; kernels reset them)
   double* ncpart;          // nrb
@@ -49,9 +58,24 @@ struct Dev {
   double* z64;             // p   relaxed z
   double* b64;             // p   final iterate promoted
   NodeDev* nd;
-  void* pow_v;             // p, FP64
-  double* pow_lam;         // power-iteration history
   int prox_wsm;            // prox keeps w in shared memory (elements), 0 = global scratch
+  // grid prox
+  unsigned* key;           // p: float bits of |w| on the free set, 0 elsewhere
+  unsigned* dkey;          // p: float bits of |grad| on the free set, 0 elsewhere
+  unsigned* hist;          // 2 x 2048: first radix digit of key / dkey (zero between steps)
+  float* bhi;              // p: newest iterate split b = bhi + blo (dense forward pass)
+  float* blo;
+  int* seg_cnt;            // nseg: nonzeros per apply segment
+  int* seg_off;            // nseg + 1: exclusive prefix of seg_cnt
+  double* segpart;         // 2 x nseg: sum |b_F| and sum_{S1} b^2 per segment
+  double* tbeta;           // kProxCap: |b| of the top set, descending (for Algorithm 2)
+  int nseg;
+  // Lanczos for lambda_max(X^T X)
+  double* vcur;            // p
+  double* vprev;           // p
+  float* vhi;              // p: vcur = vhi + vlo
+  float* vlo;
+  double* lz;              // alpha[kLanczosMax], beta[kLanczosMax]
 };
 
 __host__ __device__ inline int grad_ncol(const Dev& d) {
@@ -60,25 +84,34 @@ __host__ __device__ inline int grad_ncol(const Dev& d) {
 }
 __host__ __device__ inline int grad_nrb(const Dev& d) { return (d.n + kGradRows - 1) / kGradRows; }
 __host__ __device__ inline int fwd_ntiles(const Dev& d) { return (d.n + kFwdRows - 1) / kFwdRows; }
+__host__ __device__ inline int sp_nrb(const Dev& d) { return (d.n + kSpRows - 1) / kSpRows; }
 size_t prox_smem_bytes(const Dev& d);
 // counters layout inside Dev::cnt
 __host__ __device__ inline int cnt_grad(const Dev&) { return 0; }
 __host__ __device__ inline int cnt_fwd(const Dev& d) { return grad_ncol(d) + 1; }
+__host__ __device__ inline int cnt_apply(const Dev& d) { return grad_ncol(d) + 2; }
+__host__ __device__ inline int cnt_lz(const Dev& d) { return grad_ncol(d) + 3; }
 __host__ __device__ inline int cnt_total(const Dev& d) { return grad_ncol(d) + 8; }
 
-// one FISTA step: gradient pass, prox (+ g, dual TopSum), forward pass + step logic.
-// ev (optional): 6 events recorded around the three kernels.
+// one FISTA step: gradient pass (+ prox input and keys), prox select and apply
+// (+ g, dual TopSum), forward pass + step logic.  ev (optional): 4 events around
+// the gradient pass, the prox kernels and the forward pass.
 void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
 // g(beta^1), u^1 = X beta^1 and the objective L^1 (Algorithm 3, lines 1-2)
 void launch_init(const Dev& d, cudaStream_t s);
 // FP64 certificate at the current iterate (projection onto dom g, u, zeta,
 // a = X^T zeta, G*, g, margins)
 void launch_certificate(const Dev& d, cudaStream_t s, int want_z);
-// one power-iteration step v <- X^T X v / ||X^T X v||, lam[it] = ||X^T X v||
-void launch_power_step(const Dev& d, cudaStream_t s, int it);
-void launch_power_init(const Dev& d, cudaStream_t s);
+// Lanczos on X^T X: start vector (scaled by inv_norm), then step `it`
+// (v_{it+1}, alpha_it, beta_it into d.lz)
+void launch_lanczos_start(const Dev& d, cudaStream_t s, double inv_norm);
+void launch_lanczos_step(const Dev& d, cudaStream_t s, int it);
+// split the FP64 vector src into hi + lo floats (grid-wide)
+void launch_split(const double* src, float* hi, float* lo, int n, cudaStream_t s);
 // FP64 column norms (rounded up) for the certificate's error bound
 void launch_colnorm(const Dev& d, cudaStream_t s);
+// column-major copy Xc of X
+void launch_transpose(const Dev& d, cudaStream_t s);
 // set the prox kernels' dynamic shared memory limits once per process
 void prox_prepare();
 

@@ -36,6 +36,8 @@ struct NodeDev {
   int nnz;           // nonzeros of the newest iterate (written by the prox)
   int qhint;         // candidate count that sufficed at the previous step
   int fallback;      // number of steps that needed the full-pass root finder
+  int sparse_steps;  // number of steps whose forward pass gathered nonzero columns
+  int pad2;
   double phi;        // momentum counter of Algorithm 3
   double c;          // momentum coefficient phi/(phi+3) of the next step
   double Lcur;       // objective at beta^t (restart test)
@@ -45,6 +47,13 @@ struct NodeDev {
   double gstar;      // G*(X^T zeta_gamma) over the node (prox kernel, dual CTA)
   double theta;      // pooled-block threshold of the last prox
   double last_primal, last_dual;
+  // ---- prox selection result (select kernel -> apply kernel)
+  unsigned thr_kf;   // float bits of the k'-th largest |w| (top-set key threshold)
+  int q;             // min(k', p): size of the top set
+  double bnd_a;      // exact |w| of the last top member among keys == thr_kf (-1: all)
+  int bnd_i;         // its index (ties broken by ascending index)
+  int pad1;
+  double l1, s1sq;   // sum |b_F| and sum_{S1} b^2 of the newest iterate
   // ---- certificate (FP64 kernels at exit)
   double cert_f;        // F(X b^) in FP64
   double cert_negconj;  // -F*(-zeta) at zeta = -grad F(X b^)

@@ -32,7 +32,7 @@ KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
-           "ksc_problem_launch_count",
+           "ksc_problem_launch_count", "ksc_problem_solve_stats",
            "ksc_last_error", "ksc_version"]
 
 
@@ -85,6 +85,7 @@ def _load():
     L.ksc_problem_kernel_time.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), dp,
                                           C.c_int32]
     L.ksc_problem_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+    L.ksc_problem_solve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.ksc_prox_g_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p]
     L.ksc_last_error.restype = C.c_char_p
@@ -205,6 +206,12 @@ def ksc_problem_launch_count(h) -> int:
     n = C.c_int64()
     _check(lib.ksc_problem_launch_count(h, C.byref(n)))
     return n.value
+
+
+def ksc_problem_solve_stats(h):
+    a, b = C.c_int32(), C.c_int32()
+    _check(lib.ksc_problem_solve_stats(h, C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 # ---------------------------------------------------------------- helpers

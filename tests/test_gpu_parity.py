@@ -297,3 +297,31 @@ def test_full_size_single_node_f32_properties(K):
     ub, _ = _pins.ridge_box(P.X[:, S].astype(np.float64), P.y, P.lambda2, P.M)
     assert r.dual_bound <= r.primal <= ub * (1 + 1e-9)
     assert np.count_nonzero(r.beta) >= 1 and np.all(np.abs(r.beta) <= P.M)
+
+
+def test_sparse_forward_path_matches_oracle(K):
+    # the iterate keeps fewer than p/2 nonzeros: the forward pass streams only those
+    # columns from the column-major copy of X
+    P = G.make_problem(300, 900, r=0.9, seed=14, k_true=6, x_dtype=G.F32, lambda2=0.1, M=1.5, k=6)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-8, max_iter=50000))
+    sparse_steps, _ = K.ksc_problem_solve_stats(prob.h)
+    assert sparse_steps > 0
+    ref = _oracle(P)
+    assert r.status == "ok"
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+
+
+def test_dense_forward_path_matches_oracle(K):
+    # k = p: every coordinate stays nonzero, the row-major dense forward pass runs
+    P = G.make_problem(300, 80, r=0.5, seed=15, k_true=6, x_dtype=G.F32, lambda2=0.5, M=5.0, k=80)
+    prob = K.Problem(P.X, P.y)
+    r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-9, max_iter=50000))
+    sparse_steps, _ = K.ksc_problem_solve_stats(prob.h)
+    assert sparse_steps < r.iters
+    ref = _oracle(P)
+    assert r.status == "ok"
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.max(np.abs(r.beta - ref.beta)) <= 1e-5
