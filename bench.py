@@ -170,9 +170,11 @@ def run_ours(args, rank, world, dist):
         r = prob.solve(node, want_beta=False, want_z=False)
         if stats is not None:
             stats["launches"] += K.ksc_problem_launch_count(prob.h)
-            sp, fb = K.ksc_problem_solve_stats(prob.h)
-            stats["sparse"].append(sp)
-            stats["fallback"].append(fb)
+            st = K.ksc_problem_solve_stats(prob.h)
+            stats["sparse"].append(st["sparse_forward"])
+            stats["fallback"].append(st["prox_fallback"])
+            stats["pfast"].append(st["prox_predicted"])
+            stats["dfast"].append(st["dual_predicted"])
             stats["pow"].append(prob.power_iters)
             stats["iters"].append(r.iters)
             for kid in range(3):
@@ -185,7 +187,8 @@ def run_ours(args, rank, world, dist):
     for _ in range(args.warmup):
         r, _ = step()
         assert r.status == "ok" and r.rel_gap <= 1e-6, r
-    stats = {"launches": 0, "pow": [], "iters": [], "sparse": [], "fallback": [],
+    stats = {"launches": 0, "pow": [], "iters": [], "sparse": [], "fallback": [], "pfast": [],
+             "dfast": [],
              "k": [[0, 0.0], [0, 0.0], [0, 0.0]]}
     lat = []
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
@@ -261,6 +264,8 @@ def run_ours(args, rank, world, dist):
             "lanczos_steps_per_bound": float(np.mean(stats["pow"])),
             "sparse_forward_steps_per_bound": float(np.mean(stats["sparse"])),
             "prox_fallback_steps_per_bound": float(np.mean(stats["fallback"])),
+            "prox_predicted_steps_per_bound": float(np.mean(stats["pfast"])),
+            "dual_predicted_steps_per_bound": float(np.mean(stats["dfast"])),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(stats["launches"]),
             "kernel_time_share": shares,
             "roofline": {"bound": "hbm", "kernel": "gradient pass X^T r (k_grad)",
@@ -300,9 +305,10 @@ def cpu_baseline(P, iters, pows):
                        f"FISTA steps per bound (the counts of the full GPU solve)")}
 
 
-# iteration counts of a full solve of this workload (power iterations, FISTA steps),
-# used to extrapolate the oracle's bounded sample when it runs on its own
-FULL_SOLVE_COUNTS = {"pow": 91, "iters": 600}
+# iteration counts of a full solve of this workload (matrix-vector pairs for L, FISTA
+# steps), as the GPU solve reports them; they extrapolate the oracle's bounded sample
+# when it runs on its own
+FULL_SOLVE_COUNTS = {"pow": 80, "iters": 350}
 
 
 def run_reference(args):

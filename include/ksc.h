@@ -198,11 +198,15 @@ ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);
 ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
                                    double* total_ms, int32_t reset);
 
-/* Statistics of the last ksc_solve_node on this problem: FISTA steps whose
- * forward pass gathered only the nonzero columns of X, and steps whose prox
- * needed the full-pass root finder (pooled block wider than 4096). */
-ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* sparse_steps,
-                                   int32_t* fallback_steps);
+/* Statistics of the last ksc_solve_node on this problem, written to stats[0..n):
+ *   0  FISTA steps taken
+ *   1  steps whose forward pass streamed only the nonzero columns of X
+ *   2  steps whose prox needed the full-pass root finder (pooled block > 4096)
+ *   3  steps whose prox used the candidates predicted from the previous step
+ *   4  steps whose dual term used the predicted candidates
+ *   5  Lanczos steps taken for L when the problem was created
+ * Entries beyond 6 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
+ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n);
 
 /* Number of kernel launches the library has issued for this problem (setup,
  * every kernel node of every replayed step graph, certificates). */

@@ -210,14 +210,19 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
   const double* bc = (const double*)d.beta + (size_t)cur * p;
   const double* bpv = (const double*)d.beta + (size_t)prev * p;
   const double invL = (MODE == kGStep) ? nd->invL : 0.0;
+  const unsigned cg = (MODE == kGStep) ? nd->cguess : 0u;
+  const unsigned dg = (MODE == kGStep) ? nd->dguess : 0u;
+  const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < CPT; ++k) {
     const int col = col0 + k;
     unsigned kb = 0xffffffffu, db = 0xffffffffu;   // histogram bins (none off the strip)
+    bool pc = false, pd = false;
+    double wa = 0.0, ga = 0.0;
     if (col < p) {
       double s = 0.0;
       for (int b = 0; b < (int)gridDim.y; ++b) s += __ldcg(&ws[(size_t)b * p + col]);
-      if (MODE == kGStep) {
+      if constexpr (MODE == kGStep) {
         d.grad[col] = s;
         const double b0 = bc[col];
         const double w = b0 + c * (b0 - bpv[col]) - s * invL;   // Algorithm 3 lines 5, 7
@@ -229,6 +234,10 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         d.dkey[col] = dk;
         kb = kk >> 21;
         db = dk >> 21;
+        pc = fr && kk >= cg;   // predicted candidates (appended below)
+        pd = fr && dk >= dg;
+        wa = fabs(w);
+        ga = fabs(s);
       } else if (MODE == kGRaw) {
         d.grad[col] = s;
       } else if (MODE == kGCert) {
@@ -238,14 +247,34 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         ((double*)d.colnorm)[col] = sqrt(s * (1.0 + 2.0 * (n + 4) * u)) * (1.0 + 4.0 * u);
       }
     }
-    if (MODE == kGStep) {
+    if constexpr (MODE == kGStep) {
       // first radix digit of the keys, aggregated over equal bins of the warp
       const unsigned pk = __match_any_sync(0xffffffffu, kb);
       if (kb != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(pk) - 1))
         atomicAdd(&d.hist[kb], (unsigned)__popc(pk));
-      const unsigned pd = __match_any_sync(0xffffffffu, db);
-      if (db != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(pd) - 1))
-        atomicAdd(&d.hist[2048 + db], (unsigned)__popc(pd));
+      const unsigned pdm = __match_any_sync(0xffffffffu, db);
+      if (db != 0xffffffffu && (threadIdx.x & 31) == (unsigned)(__ffs(pdm) - 1))
+        atomicAdd(&d.hist[2048 + db], (unsigned)__popc(pdm));
+      // append the predicted candidates: one atomic per warp for each list
+      const unsigned bc_ = __ballot_sync(0xffffffffu, pc);
+      if (bc_) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&d.ccount[0], __popc(bc_));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int pos = base + __popc(bc_ & ((1u << lane) - 1u));
+        if (pc && pos < kProxCap) {
+          d.cand_a[pos] = (unsigned long long)__double_as_longlong(wa);
+          d.cand_i[pos] = col;
+        }
+      }
+      const unsigned bd_ = __ballot_sync(0xffffffffu, pd);
+      if (bd_) {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&d.ccount[1], __popc(bd_));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const int pos = base + __popc(bd_ & ((1u << lane) - 1u));
+        if (pd && pos < kProxCap) d.dcand[pos] = (unsigned long long)__double_as_longlong(ga);
+      }
     }
   }
   if (threadIdx.x == 0) d.cnt[ct] = 0;
@@ -582,12 +611,12 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
     __syncthreads();
     if (row < n) {
       int e = 0;
-      for (; e + 4 <= cnt; e += 4) {
-        A x[4];
+      for (; e + 8 <= cnt; e += 8) {
+        A x[8];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) x[k] = xval<A>(__ldcs(&Xc[(size_t)sj[e + k] * d.ldc + row]));
+        for (int k = 0; k < 8; ++k) x[k] = xval<A>(__ldcs(&Xc[(size_t)sj[e + k] * d.ldc + row]));
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 8; ++k) {
           if constexpr (FP64ACC) acc += x[k] * (A)sv[e + k];
           else df_add(acc, lo, x[k], sh[e + k], sl[e + k]);
         }
@@ -615,6 +644,98 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
   }
   if (threadIdx.x == 0) d.cnt_sp[rb] = 0;
   finish_rows<MODE, kSpRows>(d, ra, red, &s_last, (int)gridDim.x, rb, true);
+}
+
+// ----------------------------------------------------------- generic streaming matvec
+// out[c] = sum_r A[r, c] vec[r] for a row-major A (rows x cols, leading dim lda):
+// the gradient pass's access pattern (threads across contiguous columns,
+// accumulate over rows) with double-float products.  Used with A = X for X^T u
+// and with A = Xc (the column-major copy, p x n) for X v.
+
+template <typename TX, bool VEC>
+__global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ A, int64_t lda, int rows,
+                                                         int cols, const double* __restrict__ vec,
+                                                         double* __restrict__ out, double* __restrict__ ws,
+                                                         int* __restrict__ cnt) {
+  constexpr bool FP64ACC = std::is_same<TX, double>::value;
+  using Acc = typename std::conditional<FP64ACC, double, float>::type;
+  constexpr int CPT = Vec<TX>::N;
+  __shared__ Acc rs[kGradRows];
+  __shared__ float rl[kGradRows];
+  __shared__ int s_last;
+  const int ct = blockIdx.x, rb = blockIdx.y;
+  const int r0 = rb * kGradRows;
+  const int rn = min(kGradRows, rows - r0);
+  for (int i = threadIdx.x; i < rn; i += kGradThreads) {
+    const double r = vec[r0 + i];
+    rs[i] = (Acc)r;
+    rl[i] = FP64ACC ? 0.f : (float)(r - (double)(float)r);
+  }
+  __syncthreads();
+  const int col0 = ct * (kGradThreads * CPT) + threadIdx.x * CPT;
+  Acc acc[CPT];
+  float lo[CPT];
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) { acc[k] = Acc(0); lo[k] = 0.f; }
+  auto accum = [&](int k, Acc x, int i) {
+    if constexpr (FP64ACC) acc[k] += x * rs[i];
+    else df_add(acc[k], lo[k], x, rs[i], rl[i]);
+  };
+  if (col0 < cols) {
+    const TX* ap = A + (size_t)r0 * lda + col0;
+    if (VEC && col0 + CPT <= cols) {
+      int i = 0;
+      for (; i + 4 <= rn; i += 4) {
+        Acc xv[4][CPT];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) Vec<TX>::load(ap + (size_t)(i + r) * lda, xv[r]);
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int k = 0; k < CPT; ++k) accum(k, xv[r][k], i + r);
+      }
+      for (; i < rn; ++i) {
+        Acc xv[CPT];
+        Vec<TX>::load(ap + (size_t)i * lda, xv);
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) accum(k, xv[k], i);
+      }
+    } else {
+      for (int i = 0; i < rn; ++i)
+#pragma unroll
+        for (int k = 0; k < CPT; ++k)
+          if (col0 + k < cols) accum(k, xval<Acc>(ap[(size_t)i * lda + k]), i);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < CPT; ++k)
+    if (col0 + k < cols) ws[(size_t)rb * cols + col0 + k] = (double)acc[k] + (double)lo[k];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&cnt[ct], 1) == (int)gridDim.y - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < CPT; ++k) {
+    const int col = col0 + k;
+    if (col < cols) {
+      double sum = 0.0;
+      for (int b = 0; b < (int)gridDim.y; ++b) sum += __ldcg(&ws[(size_t)b * cols + col]);
+      out[col] = sum;
+    }
+  }
+  if (threadIdx.x == 0) cnt[ct] = 0;
+}
+
+template <typename TX>
+static void colsum_launch(const TX* A, int64_t lda, int rows, int cols, const double* vec, double* out,
+                          double* ws, int* cnt, cudaStream_t s) {
+  const int tile = kGradThreads * Vec<TX>::N;
+  dim3 grid((cols + tile - 1) / tile, (rows + kGradRows - 1) / kGradRows);
+  const bool vec_ok = (lda % Vec<TX>::N) == 0 && ((uintptr_t)A % 16) == 0;
+  if (vec_ok) k_colsum<TX, true><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt);
+  else k_colsum<TX, false><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt);
 }
 
 // ----------------------------------------------------------- column-major copy
@@ -712,16 +833,25 @@ void launch_certificate(const Dev& d, cudaStream_t s, int want_z) {
   else cert_impl<__nv_bfloat16, double>(d, s, want_z);
 }
 
+// u = X v (over the column-major copy) and grad = X^T u, for the Lanczos steps
 void launch_fwd_raw(const Dev& d, cudaStream_t s) {
-  if (d.xdt == kXF64) Launch<double, double>::fwd<kFRaw>(d, s);
-  else if (d.xdt == kXF32) Launch<float, double>::fwd<kFRaw>(d, s);
-  else Launch<__nv_bfloat16, double>::fwd<kFRaw>(d, s);
+  int* cnt = d.cnt + cnt_colsum(d);
+  if (d.xdt == kXF64)
+    colsum_launch<double>((const double*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXF32)
+    colsum_launch<float>((const float*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
+  else
+    colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
 }
 
 void launch_grad_raw(const Dev& d, cudaStream_t s) {
-  if (d.xdt == kXF64) Launch<double, double>::grad<kGRaw>(d, s);
-  else if (d.xdt == kXF32) Launch<float, double>::grad<kGRaw>(d, s);
-  else Launch<__nv_bfloat16, double>::grad<kGRaw>(d, s);
+  int* cnt = d.cnt + cnt_colsum(d);
+  if (d.xdt == kXF64)
+    colsum_launch<double>((const double*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXF32)
+    colsum_launch<float>((const float*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
+  else
+    colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
 }
 
 void launch_transpose(const Dev& d, cudaStream_t s) {

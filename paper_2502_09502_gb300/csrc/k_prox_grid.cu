@@ -227,7 +227,72 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
   double bnd_a = -1.0, theta = INFINITY;
   int bnd_i = 0x7fffffff, qused = 0, fb = 0;
   bool sorted_top = false;
-  if (q > 0) {
+  unsigned next_guess = 0u;
+  // ---- fast path: the candidates predicted from the previous step (every free
+  // coordinate with key >= cguess, appended by the gradient epilogue)
+  bool done = false;
+  const int cc = __ldcg(&d.ccount[0]);
+  const unsigned cg = nd->cguess;
+  if (q > 0 && cc <= kProxCap && (cc >= q + 1 || cg == 0u)) {
+    for (int j = threadIdx.x; j < cc; j += kSelBlock) {
+      sm.cand[j] = __ldcg(&d.cand_a[j]);
+      sm.cidx[j] = __ldcg(&d.cand_i[j]);
+    }
+    const int N = next_pow2(cc > 0 ? cc : 1);
+    for (int j = cc + threadIdx.x; j < N; j += kSelBlock) { sm.cand[j] = 0ull; sm.cidx[j] = 0x7fffffff; }
+    __syncthreads();
+    sort_pairs_desc(sm.cand, sm.cidx, N);   // |w| descending, index ascending (Alg. 1)
+    if (cc <= q) {
+      // every free coordinate is in the top set (the rest of it are zeros)
+      thr = 0u;
+      bnd_a = -1.0;
+      theta = 0.0;
+      for (int t = threadIdx.x; t < q; t += kSelBlock) {
+        const double a = t < cc ? dval(sm.cand[t]) : 0.0;
+        const double mg = fmin(fmin(M, shrink * a), a);
+        d.tbeta[t] = mg > 0.0 ? mg : 0.0;
+      }
+      done = true;
+    } else {
+      prefix_values(sm, cc);
+      for (int t = threadIdx.x; t < q; t += kSelBlock) sm.tb[t] = top_break(dval(sm.cand[t]), rho, M);
+      __syncthreads();
+      const bool all = (cg == 0u);
+      const double floorv = all ? 0.0 : dval(sm.cand[cc - 1]);
+      if (threadIdx.x == 0) {
+        double th = 0.0;
+        sm.flag[1] = root_search(sm, q, cc, floorv, all, rho, M, &th) ? 1 : 0;
+        sm.root[0] = th;
+        // next step's guess: keep about twice the pooled block, 5% below
+        int lo = q, hi = cc;
+        while (lo < hi) {
+          const int mid = (lo + hi) >> 1;
+          if (dval(sm.cand[mid]) <= th) hi = mid; else lo = mid + 1;
+        }
+        int g = lo + lo / 2 + 32;
+        if (g > cc - 1) g = cc - 1;
+        sm.flag[0] = (int)(__float_as_uint((float)(0.98 * dval(sm.cand[g]))) & 0x7fffffffu);
+      }
+      __syncthreads();
+      if (sm.flag[1]) {
+        theta = sm.root[0];
+        const double aq = dval(sm.cand[q - 1]);
+        bnd_a = aq;
+        bnd_i = sm.cidx[q - 1];
+        thr = __float_as_uint((float)aq) & 0x7fffffffu;   // the key of the boundary element
+        next_guess = (unsigned)sm.flag[0];
+        qused = cc;
+        for (int t = threadIdx.x; t < q; t += kSelBlock) {
+          const double a = dval(sm.cand[t]);
+          const double mg = fmin(fmin(M, shrink * a), a - theta);
+          d.tbeta[t] = mg > 0.0 ? mg : 0.0;
+        }
+        done = true;
+      }
+      __syncthreads();
+    }
+  }
+  if (q > 0 && !done) {
     const SelectResult<unsigned> Rk = block_select<unsigned, kSelBlock>(p, q, kload, sm.hist, sm.sh, d.hist);
     thr = Rk.thr;
     const int need = q - Rk.gt, eq = Rk.eq;
@@ -347,8 +412,14 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
       const double mg = fmin(fmin(M, shrink * a), a - theta);
       d.tbeta[t] = mg > 0.0 ? mg : 0.0;
     }
+    // next step's guess from the threshold just found
+    next_guess = (theta > 0.0 && isfinite(theta))
+                     ? (__float_as_uint((float)(0.95 * theta)) & 0x7fffffffu) : 0u;
   }
   if (threadIdx.x == 0) {
+    nd->cguess = next_guess;
+    nd->fast_steps += done ? 1 : 0;
+    d.ccount[0] = 0;
     nd->theta = theta;
     nd->thr_kf = thr;
     nd->bnd_a = bnd_a;
@@ -375,7 +446,23 @@ __device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
     if (st && st[i] == kOne) s1 += huber(fabs(g[i]) * scale, M);
   s1 = block_sum<double, kSelBlock>(s1, sm.red);
   double s = 0.0;
-  if (q > 0) {
+  unsigned next_guess = 0u;
+  const int dc = __ldcg(&d.ccount[1]);
+  const unsigned dg = nd->dguess;
+  if (q > 0 && dc <= kProxCap && (dc >= q || dg == 0u)) {
+    // the predicted candidates hold the top-k' magnitudes of the gradient
+    for (int j = threadIdx.x; j < dc; j += kSelBlock) sm.cand[j] = __ldcg(&d.dcand[j]);
+    const int N = next_pow2(dc > 0 ? dc : 1);
+    for (int j = dc + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
+    __syncthreads();
+    sort_u64_desc(sm.cand, N);
+    const int top = q < dc ? q : dc;
+    double b = 0.0;
+    for (int j = threadIdx.x; j < top; j += kSelBlock) b += huber(dval(sm.cand[j]) * scale, M);
+    s = block_sum<double, kSelBlock>(b, sm.red);
+    if (top > 0) next_guess = __float_as_uint((float)(0.995 * dval(sm.cand[top - 1]))) & 0x7fffffffu;
+    if (threadIdx.x == 0) nd->dfast_steps += 1;
+  } else if (q > 0) {
     auto kload = [&](int i) -> unsigned { return __ldcg(&d.dkey[i]); };
     const SelectResult<unsigned> R =
         block_select<unsigned, kSelBlock>(p, q, kload, sm.hist, sm.sh, d.hist + 2048);
@@ -403,8 +490,13 @@ __device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
         s += (double)need * huber((double)__uint_as_float(R.thr) * scale, M);
       }
     }
+    next_guess = __float_as_uint(0.995f * __uint_as_float(R.thr)) & 0x7fffffffu;
   }
-  if (threadIdx.x == 0) nd->gstar = s1 + s;
+  if (threadIdx.x == 0) {
+    nd->gstar = s1 + s;
+    nd->dguess = next_guess;
+    d.ccount[1] = 0;
+  }
   __syncthreads();
   for (int b = threadIdx.x; b < 2048; b += kSelBlock) d.hist[2048 + b] = 0u;
 }

@@ -78,7 +78,7 @@ struct ksc_problem {
   int64_t k_launches[3] = {0, 0, 0};
   double k_ms[3] = {0, 0, 0};
   int64_t launches = 0;   // every kernel launch issued for this problem
-  int32_t last_sparse_steps = 0, last_fallback_steps = 0;
+  int32_t last_stats[6] = {0, 0, 0, 0, 0, 0};
 };
 
 // kernels per launcher (kept beside the launchers they count)
@@ -128,7 +128,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.grad, p * 8);
   ALLOC(d.wbuf, p * tb);
   ALLOC(d.nnz_idx, p * sizeof(int));
-  ALLOC(d.ws, (size_t)grad_nrb(d) * p * 8);
+  ALLOC(d.ws, ws_elems(d) * 8);
   ALLOC(d.cnt, (size_t)cnt_total(d) * sizeof(int));
   ALLOC(d.ncpart, (size_t)grad_nrb(d) * 8);
   ALLOC(d.fpart, (size_t)fwd_ntiles(d) * 4 * 8);
@@ -151,6 +151,10 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.seg_off, (size_t)(d.nseg + 1) * 4);
   ALLOC(d.segpart, (size_t)2 * d.nseg * 8);
   ALLOC(d.tbeta, (size_t)kProxCap * 8);
+  ALLOC(d.cand_a, (size_t)kProxCap * 8);
+  ALLOC(d.cand_i, (size_t)kProxCap * 4);
+  ALLOC(d.dcand, (size_t)kProxCap * 8);
+  ALLOC(d.ccount, 2 * 4);
   ALLOC(d.vcur, p * 8);
   ALLOC(d.vprev, p * 8);
   ALLOC(d.vhi, p * 4);
@@ -173,6 +177,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   KSC_CUDA(cudaMemset(d.nd, 0, sizeof(NodeDev)));
   KSC_CUDA(cudaMemset(d.hist, 0, 2 * 2048 * 4));
   KSC_CUDA(cudaMemset(d.cnt_sp, 0, (size_t)sp_nrb(d) * 4));
+  KSC_CUDA(cudaMemset(d.ccount, 0, 2 * 4));
   return KSC_OK;
 }
 
@@ -234,7 +239,8 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     }
     theta = tridiag_max_eig(hlz.data(), hlz.data() + kLanczosMax, m);
     pr->power_iters = m;
-    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-9 * theta)) break;
+    // the Ritz value rises monotonically to lambda_max; L keeps a 1% margin
+    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-7 * theta)) break;
     prev = theta;
   }
   const double cf = pr->loss == KSC_LOSS_LSQ ? 2.0 : 0.25;
@@ -550,8 +556,12 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     KSC_CUDA(cudaMemcpyAsync(d.nd, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
     h = upd;
   }
-  pr->last_sparse_steps = h.sparse_steps;
-  pr->last_fallback_steps = h.fallback;
+  pr->last_stats[0] = h.iter - 1;
+  pr->last_stats[1] = h.sparse_steps;
+  pr->last_stats[2] = h.fallback;
+  pr->last_stats[3] = h.fast_steps;
+  pr->last_stats[4] = h.dfast_steps;
+  pr->last_stats[5] = pr->power_iters;
   res->primal = h.cert_primal;
   res->dual_bound = h.cert_dual;
   res->rel_gap = h.cert_gap;
@@ -653,11 +663,10 @@ extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M,
   return KSC_OK;
 }
 
-extern "C" ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* sparse_steps,
-                                              int32_t* fallback_steps) {
+extern "C" ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n) {
   if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
-  if (sparse_steps) *sparse_steps = problem->last_sparse_steps;
-  if (fallback_steps) *fallback_steps = problem->last_fallback_steps;
+  if (n < 0 || (n > 0 && !stats)) return fail(KSC_ERR_INVALID_ARG, "bad stats buffer");
+  for (int32_t i = 0; i < n; ++i) stats[i] = i < 6 ? problem->last_stats[i] : 0;
   return KSC_OK;
 }
 

@@ -22,7 +22,7 @@ constexpr int kProxCap = 4096;      // prox candidates (k' + pooled tail) in sha
 constexpr int kSegLen = 256;        // prox apply: coordinates per CTA (one compaction segment)
 constexpr int kMaxSegSparse = 4096; // sparse forward pass needs p <= kSegLen * this
 constexpr int kSpRows = 256;        // sparse forward pass: rows per CTA (one per thread)
-constexpr int kSpSplit = 8;         // sparse forward pass: chunks of the nonzero list
+constexpr int kSpSplit = 16;        // sparse forward pass: chunks of the nonzero list
 constexpr int kSpStage = 1024;      // sparse forward pass: list entries staged per round
 constexpr int kLanczosMax = 512;    // Lanczos steps for lambda_max(X^T X)
 
@@ -63,6 +63,10 @@ struct Dev {
   unsigned* key;           // p: float bits of |w| on the free set, 0 elsewhere
   unsigned* dkey;          // p: float bits of |grad| on the free set, 0 elsewhere
   unsigned* hist;          // 2 x 2048: first radix digit of key / dkey (zero between steps)
+  unsigned long long* cand_a;  // kProxCap: |w| bits of the predicted prox candidates
+  int* cand_i;                 // kProxCap: their indices
+  unsigned long long* dcand;   // kProxCap: |grad| bits of the predicted dual candidates
+  int* ccount;                 // 2: appended prox / dual candidates (may exceed kProxCap)
   float* bhi;              // p: newest iterate split b = bhi + blo (dense forward pass)
   float* blo;
   int* seg_cnt;            // nseg: nonzeros per apply segment
@@ -91,7 +95,21 @@ __host__ __device__ inline int cnt_grad(const Dev&) { return 0; }
 __host__ __device__ inline int cnt_fwd(const Dev& d) { return grad_ncol(d) + 1; }
 __host__ __device__ inline int cnt_apply(const Dev& d) { return grad_ncol(d) + 2; }
 __host__ __device__ inline int cnt_lz(const Dev& d) { return grad_ncol(d) + 3; }
-__host__ __device__ inline int cnt_total(const Dev& d) { return grad_ncol(d) + 8; }
+// the generic streaming matvec's per-strip counters (max of its column strips over
+// the two shapes p x n and n x p)
+__host__ __device__ inline int cnt_colsum(const Dev& d) { return grad_ncol(d) + 8; }
+__host__ __device__ inline int colsum_strips(const Dev& d) {
+  const int tile = kGradThreads * cols_per_thread(d.xdt);
+  const int a = (d.n + tile - 1) / tile, b = (d.p + tile - 1) / tile;
+  return a > b ? a : b;
+}
+__host__ __device__ inline int cnt_total(const Dev& d) { return grad_ncol(d) + 8 + colsum_strips(d) + 1; }
+// gradient-partials workspace (doubles): max of the two streaming shapes
+__host__ __device__ inline size_t ws_elems(const Dev& d) {
+  const size_t a = (size_t)((d.n + kGradRows - 1) / kGradRows) * d.p;
+  const size_t b = (size_t)((d.p + kGradRows - 1) / kGradRows) * d.n;
+  return a > b ? a : b;
+}
 
 // one FISTA step: gradient pass (+ prox input and keys), prox select and apply
 // (+ g, dual TopSum), forward pass + step logic.  ev (optional): 4 events around

@@ -54,6 +54,12 @@ struct NodeDev {
   int bnd_i;         // its index (ties broken by ascending index)
   int pad1;
   double l1, s1sq;   // sum |b_F| and sum_{S1} b^2 of the newest iterate
+  // warm-started candidate selection: float-bit key thresholds predicted from the
+  // previous step (0 = take every coordinate, i.e. no prediction yet)
+  unsigned cguess;   // prox: keys >= cguess are appended by the gradient epilogue
+  unsigned dguess;   // dual: |grad| keys >= dguess
+  int fast_steps;    // steps whose prox used the predicted candidates
+  int dfast_steps;   // steps whose dual term used the predicted candidates
   // ---- certificate (FP64 kernels at exit)
   double cert_f;        // F(X b^) in FP64
   double cert_negconj;  // -F*(-zeta) at zeta = -grad F(X b^)

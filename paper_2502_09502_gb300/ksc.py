@@ -85,7 +85,7 @@ def _load():
     L.ksc_problem_kernel_time.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_int64), dp,
                                           C.c_int32]
     L.ksc_problem_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
-    L.ksc_problem_solve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.ksc_problem_solve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
     L.ksc_prox_g_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p]
     L.ksc_last_error.restype = C.c_char_p
@@ -208,10 +208,14 @@ def ksc_problem_launch_count(h) -> int:
     return n.value
 
 
+SOLVE_STATS = ("iters", "sparse_forward", "prox_fallback", "prox_predicted", "dual_predicted",
+               "lanczos")
+
+
 def ksc_problem_solve_stats(h):
-    a, b = C.c_int32(), C.c_int32()
-    _check(lib.ksc_problem_solve_stats(h, C.byref(a), C.byref(b)))
-    return a.value, b.value
+    buf = (C.c_int32 * len(SOLVE_STATS))()
+    _check(lib.ksc_problem_solve_stats(h, buf, len(SOLVE_STATS)))
+    return dict(zip(SOLVE_STATS, list(buf)))
 
 
 # ---------------------------------------------------------------- helpers

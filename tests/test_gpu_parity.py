@@ -305,8 +305,8 @@ def test_sparse_forward_path_matches_oracle(K):
     P = G.make_problem(300, 900, r=0.9, seed=14, k_true=6, x_dtype=G.F32, lambda2=0.1, M=1.5, k=6)
     prob = K.Problem(P.X, P.y)
     r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-8, max_iter=50000))
-    sparse_steps, _ = K.ksc_problem_solve_stats(prob.h)
-    assert sparse_steps > 0
+    st = K.ksc_problem_solve_stats(prob.h)
+    assert st["sparse_forward"] > 0 and st["iters"] == r.iters
     ref = _oracle(P)
     assert r.status == "ok"
     assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
@@ -318,8 +318,8 @@ def test_dense_forward_path_matches_oracle(K):
     P = G.make_problem(300, 80, r=0.5, seed=15, k_true=6, x_dtype=G.F32, lambda2=0.5, M=5.0, k=80)
     prob = K.Problem(P.X, P.y)
     r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-9, max_iter=50000))
-    sparse_steps, _ = K.ksc_problem_solve_stats(prob.h)
-    assert sparse_steps < r.iters
+    st = K.ksc_problem_solve_stats(prob.h)
+    assert st["sparse_forward"] < r.iters
     ref = _oracle(P)
     assert r.status == "ok"
     assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
