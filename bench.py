@@ -55,6 +55,13 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="8000 x 20000 instance of the same generator (640 MB X, still larger "
                          "than L2) for profiler captures; not a benchmark line")
+    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+                    help="single: the single-node FP32 line (default); batched: 512 nodes of "
+                         "the batched logistic BF16 workload in one ksc_solve_batch call")
+    ap.add_argument("--nodes", type=int, default=512, help="batched: nodes per call")
+    ap.add_argument("--plain-nodes", type=int, default=16,
+                    help="batched: nodes of the same batch solved one at a time by the "
+                         "single-node solver for the comparison")
     return ap.parse_args()
 
 
@@ -277,6 +284,120 @@ def run_ours(args, rank, world, dist):
     return out, P, stats
 
 
+# ------------------------------------------------------------------ batched workload
+
+BATCHED = dict(workload="batched logistic BF16 X n=10000 p=5000 k=10 lambda2=0.01 M=3 toeplitz 0.5, "
+                        "512 nodes per call (|S0|~U{0..200}, |S1|~U{0..9}), warm start = root "
+                        "iterate + N(0,1e-2), rel gap 1e-6",
+               n=10000, p=5000, k=10, lambda2=0.01, M=3.0, r=0.5, x_dtype="bf16", loss="logistic",
+               rel_gap=1e-6, l2="X (100 MB) and its column-major copy read by every step; no flush")
+
+
+def run_batched(args):
+    """One step = one ksc_solve_batch call over `nodes` nodes of the batched logistic
+    workload (X resident; L computed once at problem creation)."""
+    import torch
+    import ksc_inputs as G
+    from paper_2502_09502_gb300 import ksc as K
+    torch.cuda.set_device(0)
+    P = G.cfg_batched_logistic(seed=args.seed)
+    n, p, B = P.n, P.p, args.nodes
+    Xd = torch.from_numpy(P.X.view(np.int16)).cuda().view(torch.bfloat16)
+    stream = torch.cuda.Stream()
+    prob = K.Problem(Xd, P.y, K.KSC_LOSS_LOGISTIC, stream=stream)
+    root = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    sets = G.node_sets(p, B, seed=args.seed, max_zero=200, max_one=9)
+    pert = G.warm_perturbation(p, B, seed=args.seed)
+    nodes = [K.Node(P.lambda2, P.M, P.k, fixed_zero=z, fixed_one=o, warm_beta=root.beta + pert[b],
+                    rel_gap_tol=1e-6, max_iter=100000) for b, (z, o) in enumerate(sets)]
+
+    def check(res):
+        bad = [r for r in res if not (r.status == "ok" and r.rel_gap <= 1e-6) and not r.pruned]
+        assert not bad, bad[:2]
+
+    for _ in range(args.warmup):
+        check(prob.solve_batch(nodes, want_beta=False))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clocks = ClockSampler(vis.split(",")[0] if vis else "0")
+    K.ksc_problem_profile(prob.h, True)
+    K.ksc_problem_kernel_time(prob.h, 0, reset=True)
+    l0 = K.ksc_problem_launch_count(prob.h)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat, iters = [], []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        res = prob.solve_batch(nodes, want_beta=False)
+        lat.append(time.perf_counter() - t0)
+        check(res)
+        iters.append(float(np.mean([r.iters for r in res])))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    launches = K.ksc_problem_launch_count(prob.h) - l0
+    kt = {name: K.ksc_problem_kernel_time(prob.h, kid)
+          for name, kid in [("residual", K.KSC_KERNEL_B_RESID), ("xt_r", K.KSC_KERNEL_B_GRAD),
+                            ("prox", K.KSC_KERNEL_B_PROX), ("x_dbeta", K.KSC_KERNEL_B_FWD),
+                            ("step", K.KSC_KERNEL_B_STEP)]}
+    K.ksc_problem_profile(prob.h, False)
+    value = B * args.steps / (ms / 1e3)
+    tot = sum(v[1] for v in kt.values())
+    shares = {k: round(v[1] / max(tot, 1e-9), 4) for k, v in kt.items()}
+    # tensor roofline of the X^T r product: algorithmic flops 2 n p B per launch
+    nl, gms = kt["xt_r"]
+    g_ms = gms / max(nl, 1)
+    alg = 2.0 * n * p * B
+    achieved = alg / (g_ms / 1e3) / 1e12
+    try:
+        pk = json.load(open(PEAKS_FILE))
+        peak, peak_kind = float(pk["bf16_tflops"]), "measured"
+    except Exception:
+        peak, peak_kind = 1900.0, "fallback"
+    # the plain single-node solver on the same nodes, one at a time
+    sub = nodes[:args.plain_nodes]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for nd in sub:
+        r = prob.solve(nd, want_beta=False, want_z=False)
+        assert r.status == "ok" or r.pruned, r
+    plain = len(sub) / (time.perf_counter() - t0)
+    # end to end: X from pinned host memory into a new problem, the batched call, results back
+    Xh = torch.from_numpy(P.X.view(np.int16)).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob2 = K.Problem(Xh.numpy().view(np.uint16), P.y, K.KSC_LOSS_LOGISTIC, stream=stream,
+                      x_dtype=K.KSC_BF16)
+    res = prob2.solve_batch(nodes, want_beta=True)
+    e_s = time.perf_counter() - t0
+    prob2.close()
+    check(res)
+    lat_ms = sorted(1e3 * x for x in lat)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
+        "config": dict(BATCHED, nodes=B, parallelism="single GPU"),
+        "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
+                       "p99": round(float(np.percentile(lat_ms, 99)), 3)},
+        "iters_per_bound": float(np.mean(iters)),
+        "plain_single_node": {"value": round(plain, 3), "unit": UNIT, "nodes": len(sub),
+                              "ratio": round(value / plain, 2)},
+        "clocks": clk, "gpu_launches": int(launches), "kernel_time_share": shares,
+        "e2e": {"value": round(B / e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
+                "d2h_bytes_per_step": int(B * (p * 8 + 64))},
+        "roofline": {"bound": "tensor", "kernel": "X^T r for all nodes (k_tcgemm, 3 BF16 pieces)",
+                     "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
+                     "peak_kind": peak_kind, "frac": round(achieved / peak, 4), "traffic": None,
+                     "flops_per_launch": alg, "executed_flops_per_launch": 3 * alg,
+                     "avg_launch_ms": round(g_ms, 5), "launches": nl},
+    }
+    return line
+
+
 # ------------------------------------------------------------------ oracle timing
 
 def time_oracle_sample(P, stats_iters=None, stats_pow=None):
@@ -352,6 +473,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         D.init_process_group("nccl")
         dist = D
+    if args.workload == "batched":
+        if world > 1:
+            raise SystemExit("the batched workload runs on one GPU")
+        print(json.dumps(run_batched(args)), flush=True)
+        return
     out, P, stats = run_ours(args, rank, world, dist)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:

@@ -184,12 +184,35 @@ ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* ou
 ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, double rho,
                               double* beta_out, int32_t* top_out, void* cuda_stream);
 
+/* The tensor-core product of the batched solver, exported so that it can be
+ * tested on its own.  The paper has no counterpart: it is the product X beta (and
+ * X^T r) of Algorithm 3 for many nodes at once, with each node's FP32 vector split
+ * into `pieces` BF16 vectors whose sum is exact.
+ *   D[i][j] = sum_{q < pieces} sum_{t < k} A[q * m_pad + i][t] * B[j][t]   (FP32 accumulation)
+ * A, B: device BF16 arrays, row-major with row strides lda, ldb (elements; >= k and
+ * multiples of 8), 16-byte aligned; A has pieces * m_pad rows (m_pad a multiple of
+ * 128; rows m..m_pad-1 of each piece are read but not stored).  D: device FP32,
+ * m rows of stride ldd (>= n, a multiple of 4), 16-byte aligned, caller-owned.
+ * pieces in 1..3, tile_n (columns of B per CTA) in {64, 128, 256}.  Blocks until
+ * the product is done.  KSC_ERR_INVALID_ARG for shapes outside these rules,
+ * KSC_ERR_TIMEOUT when a device wait of the kernel gave up (nothing is left
+ * running), KSC_ERR_CUDA on a runtime error. */
+ksc_status ksc_tc_gemm(const void* A, int32_t pieces, int32_t m, int32_t m_pad, int32_t k, int64_t lda,
+                       const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd, int32_t tile_n,
+                       void* cuda_stream);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Kernel ids for ksc_problem_kernel_time. */
 #define KSC_KERNEL_GRADIENT 0   /* X^T grad F(u) pass (one per FISTA step)           */
 #define KSC_KERNEL_PROX     1   /* segmented prox + g + dual TopSum (one per step)   */
 #define KSC_KERNEL_FORWARD  2   /* X b pass + restart/gap step (one per step)        */
+/* batched solves (ksc_solve_batch), one launch each per batched step:          */
+#define KSC_KERNEL_B_RESID  3   /* u_gamma, grad F, its BF16 pieces, -F* terms       */
+#define KSC_KERNEL_B_GRAD   4   /* tensor-core X^T r for every node                  */
+#define KSC_KERNEL_B_PROX   5   /* one prox / g / dual-term CTA per node             */
+#define KSC_KERNEL_B_FWD    6   /* tensor-core X beta for every node + loss partials */
+#define KSC_KERNEL_B_STEP   7   /* restart / gap step per node                       */
 /* Enable (1) or disable (0) CUDA-event timing of each kernel launch of the
  * problem's solves; accumulated totals are read with ksc_problem_kernel_time. */
 ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);

@@ -300,33 +300,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
 
 // Algorithm 3 line 10-11 plus the gap test of Sec. 4.2 and the incumbent rules
 // of Sec. 4.3 (on the in-loop bound; the host confirms with the certificate).
-__device__ void step_logic(NodeDev* nd, double f) {
-  const double Lnext = f + 2.0 * nd->lambda2 * nd->g_next;
-  const double D = nd->negconj - 2.0 * nd->lambda2 * nd->gstar;
-  nd->last_primal = Lnext;
-  nd->last_dual = D;
-  if (nd->restart_on && Lnext >= nd->Lcur) {
-    nd->phi = 1.0;
-    nd->restarts += 1;
-  } else {
-    nd->phi += 1.0;
-  }
-  nd->Lcur = Lnext;
-  nd->best_primal = fmin(nd->best_primal, Lnext);
-  nd->best_dual = fmax(nd->best_dual, D);
-  nd->gap = (nd->best_primal - nd->best_dual) / fmax(fabs(nd->best_primal), 1e-300);
-  const int t = nd->iter + 1;
-  nd->iter = t;
-  int done = kRunning;
-  if (isfinite(nd->incumbent)) {
-    if (nd->best_dual > nd->incumbent) done = kDonePruned;
-    else if (Lnext < nd->incumbent) done = kDonePrimal;
-  }
-  if (done == kRunning && nd->gap <= nd->tol_loop) done = kDoneGap;
-  if (done == kRunning && t - 1 >= nd->max_iter) done = kDoneMaxIter;
-  nd->done = done;
-  nd->c = nd->momentum_on ? nd->phi / (nd->phi + 3.0) : 0.0;
-}
+__device__ void step_logic(NodeDev* nd, double f) { fista_step_logic(nd, f); }
 
 // ----------------------------------------------------------- forward epilogue
 

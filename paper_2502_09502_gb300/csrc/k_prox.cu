@@ -15,6 +15,7 @@ namespace ksc {
 constexpr int kDualCap = 16;
 
 void prox_grid_prepare(int optin);   // k_prox_grid.cu
+void batch_prepare(int optin);       // k_batch.cu
 
 template <typename T>
 __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
@@ -121,7 +122,9 @@ k_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, i
   io.m = p;
   io.state = nullptr;
   io.w = w;
-  io.bc = io.bp = io.grad = nullptr;
+  io.bc = io.bp = nullptr;
+  io.grad = nullptr;
+  io.gradf = nullptr;
   io.c = 0.0;
   io.invL = 0.0;
   io.rho = rho;
@@ -168,6 +171,7 @@ void prox_prepare() {
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   g_smem_max = (size_t)optin;
   prox_grid_prepare(optin);
+  batch_prepare(optin);
   cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);

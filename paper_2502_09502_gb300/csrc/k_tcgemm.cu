@@ -1,0 +1,478 @@
+// k_tcgemm.cu -- the batched solver's products on the 5th-generation tensor cores.
+//
+// One CTA computes a 128 x BN tile of D = sum_q A_q B^T (ksc_tc.h):
+//   warp 0      TMA producer: per 64-wide K block, the P pieces of the 128 A rows
+//               and the BN rows of B land in one shared-memory stage (128-byte
+//               swizzle), signalled on the stage's "full" mbarrier;
+//   warp 1      allocates the TMEM accumulator (128 lanes x BN FP32 columns) and,
+//               from one thread, issues tcgen05.mma (M = 128, N = BN, K = 16; four
+//               per piece per K block) and tcgen05.commit to free each stage;
+//   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes (one output row per
+//               thread): row-major FP32 stores, or the FP64 update u += D with
+//               the loss partials of the row.
+// Every wait is bounded (%globaltimer); a wait that gives up sets the error word,
+// raises the CTA's abort flag and the CTA drains its copies and MMAs before it
+// frees TMEM and exits.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "ksc_state.cuh"
+#include "ksc_tc.h"
+
+namespace ksc {
+
+constexpr int kTcThreads = 192;
+constexpr int kTcBM = 128;
+constexpr int kTcBK = 64;                       // 64 BF16 = one 128-byte swizzle row
+constexpr uint32_t kTcATile = kTcBM * 128;      // bytes of one A piece per stage
+constexpr uint64_t kTcWaitNs = 2000000000ull;   // 2 s
+constexpr int kTcSmemMax = 232448 - 2048;       // opt-in limit minus alignment and barriers
+
+__device__ int g_tc_err;
+
+__host__ __device__ constexpr int tc_stage_bytes(int P, int BN) { return P * (int)kTcATile + BN * 128; }
+__host__ __device__ constexpr int tc_stages(int P, int BN) {
+  return (kTcSmemMax / tc_stage_bytes(P, BN)) > 6 ? 6 : (kTcSmemMax / tc_stage_bytes(P, BN));
+}
+__host__ __device__ constexpr int tc_smem_bytes(int P, int BN) {
+  return tc_stages(P, BN) * tc_stage_bytes(P, BN) + 1024 + 256;
+}
+__host__ __device__ constexpr uint32_t tc_tmem_cols(int BN) {
+  return BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+}
+
+// instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1), A and B
+// BF16 (bits 7-9, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 in bits
+// 17-22, M >> 4 in bits 24-28
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------ PTX wrappers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase of `parity` to complete; false on timeout or abort
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255u) == 0u) {
+      if (*abort_flag) return false;
+      if (gtimer() - t0 > kTcWaitNs) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// shared-memory matrix descriptor, K-major, 128-byte swizzle: start address >> 4
+// (bits 0-13), leading offset (unused for this layout, bits 16-29), stride offset
+// 1024 B = 8 rows of 128 B (bits 32-45), descriptor version 1 (bit 46), swizzle
+// mode 2 = 128 B (bits 61-63).  Tiles start on 1024-byte boundaries; the K step
+// of 16 BF16 inside the swizzle row advances the start address by 32 B.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// F_i(u) in FP32 (summed in FP64 by the caller)
+__device__ __forceinline__ float loss_term(float u, float y, int loss) {
+  if (loss == kLossLsq) {
+    const float r = u - y;
+    return r * r;
+  }
+  const float t = -y * u;
+  return fmaxf(t, 0.0f) + log1pf(__expf(-fabsf(t)));
+}
+
+// F_i(u + d) - F_i(u) without cancellation: least squares d (2 (u - y) + d);
+// logistic log1p(expm1(-y d) sigma(-y u)), since
+// (1 + e^{-y(u+d)}) / (1 + e^{-y u}) = 1 + (e^{-y d} - 1) e^{-y u} / (1 + e^{-y u})
+__device__ __forceinline__ float loss_change(double u, float d, float y, int loss) {
+  if (loss == kLossLsq) {
+    const float r = (float)(u - (double)y);
+    return d * (2.0f * r + d);
+  }
+  if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
+  const float s = 1.0f / (1.0f + __expf(y * (float)u));   // sigma(-y u)
+  return log1pf(expm1f(-y * d) * s);
+}
+
+// ------------------------------------------------------------------ kernel
+
+struct TcShape {
+  int M, Mpad, N, K;
+};
+
+template <int P, int BN, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tcgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
+             TcEpi ep) {
+  constexpr int S = tc_stages(P, BN);
+  constexpr uint32_t B_TILE = BN * 128;
+  constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
+  constexpr uint32_t TCOLS = tc_tmem_cols(BN);
+  static_assert(S >= 2, "at least two pipeline stages");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N for M = 128");
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + S * P * kTcATile;
+  uint64_t* full = (uint64_t*)(sB + S * B_TILE);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* drain = accf + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+  const int nkb = (sh.K + kTcBK - 1) / kTcBK;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % S;
+        const uint32_t ph = (uint32_t)(kb / S) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+          atomicExch(&g_tc_err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE_TX);
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+          tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * kTcBK, q * sh.Mpad + m0);
+        tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * kTcBK, n0);
+        issued = kb + 1;
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA leaves
+        for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb) {
+          volatile int never = 0;
+          mbar_wait(&full[kb % S], (uint32_t)(kb / S) & 1u, &never);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(kTcBM, BN);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % S;
+        const uint32_t ph = (uint32_t)(kb / S) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag)) {
+          atomicExch(&g_tc_err, 2);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t b_addr = smem_u32(sB + s * B_TILE);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
+#pragma unroll
+          for (int kk = 0; kk < kTcBK / 16; ++kk)
+            umma_bf16(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                      (kb | q | kk) != 0 ? 1u : 0u);
+        }
+        umma_commit(&empty[s]);
+      }
+      if (ok) {
+        umma_commit(accf);
+      } else {
+        // wait for the MMAs already issued before TMEM is released
+        umma_commit(drain);
+        volatile int never = 0;
+        mbar_wait(drain, 0, &never);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int qd = warp & 3;   // TMEM lanes 32 qd .. 32 qd + 31
+    const int m = m0 + 32 * qd + lane;
+    // warp-uniform: tcgen05.ld is a warp-collective instruction
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0, abort_flag) ? 1 : 0) != 0;
+    tc_fence_after();
+    if (ok) {
+      const bool row_ok = m < sh.M;
+      float* orow = nullptr;
+      const double* uin = nullptr;
+      double* uout = nullptr;
+      if (row_ok) {
+        if (MODE == kTcStore) {
+          orow = ep.out + (int64_t)m * ep.ldo;
+        } else {
+          uin = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_in[m] * ep.slot_stride;
+          uout = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_out[m] * ep.slot_stride;
+        }
+      }
+      double fsum = 0.0, dsum = 0.0;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)c, v);
+        const int nc = n0 + c;
+        if (row_ok && nc < sh.N) {
+          if (MODE == kTcStore) {
+            if (nc + 16 <= sh.N) {
+              float4* o4 = (float4*)(orow + nc);
+#pragma unroll
+              for (int i = 0; i < 4; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (nc + i < sh.N) orow[nc + i] = v[i];
+            }
+          } else {
+            float fa = 0.0f, da = 0.0f;
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i) {
+              if (nc + i < sh.N) {
+                const double uo = uin[nc + i];
+                const double un = uo + (double)v[i];
+                uout[nc + i] = un;
+                const float yi = __ldg(&ep.y[nc + i]);
+                fa += loss_term((float)un, yi, ep.loss);
+                da += loss_change(uo, v[i], yi, ep.loss);
+              }
+            }
+            fsum += (double)fa;
+            dsum += (double)da;
+            // one pair of partials per 64 columns, whatever the tile width: the
+            // sums do not depend on the tiling
+            if (((c + 16) & 63) == 0 || nc + 16 >= sh.N) {
+              double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
+              pp[0] = fsum;
+              pp[1] = dsum;
+              fsum = 0.0;
+              dsum = 0.0;
+            }
+          }
+        }
+      }
+    } else {
+      atomicExch(&g_tc_err, 3);
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
+// ------------------------------------------------------------------ host
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+static bool make_map(void* out, const void* base, uint64_t inner, uint64_t rows, int64_t ld, uint32_t box_rows,
+                     const char** why) {
+  PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+  if (!fn) {
+    *why = "cuTensorMapEncodeTiled is not available from the driver";
+    return false;
+  }
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)kTcBK, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+                  box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *why = "cuTensorMapEncodeTiled rejected the operand layout";
+    return false;
+  }
+  return true;
+}
+
+bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t lda, const void* B, int N,
+             int64_t ldb, int bn, const char** why) {
+  plan->ok = 0;
+  if (P < 1 || P > 3) { *why = "pieces must be 1, 2 or 3"; return false; }
+  if (bn != 64 && bn != 128 && bn != 256) { *why = "tile width must be 64, 128 or 256"; return false; }
+  if (M <= 0 || N <= 0 || K <= 0) { *why = "empty product"; return false; }
+  if (Mpad % kTcBM != 0 || Mpad < M) { *why = "Mpad must be a multiple of 128 and >= M"; return false; }
+  if ((lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0 || lda < K || ldb < K) {
+    *why = "row strides must be >= K and multiples of 16 bytes";
+    return false;
+  }
+  if (((uintptr_t)A % 16) != 0 || ((uintptr_t)B % 16) != 0) { *why = "operands must be 16-byte aligned"; return false; }
+  if (!make_map(plan->tmA, A, (uint64_t)K, (uint64_t)P * Mpad, lda, kTcBM, why)) return false;
+  if (!make_map(plan->tmB, B, (uint64_t)K, (uint64_t)N, ldb, (uint32_t)bn, why)) return false;
+  plan->P = P;
+  plan->M = M;
+  plan->Mpad = Mpad;
+  plan->N = N;
+  plan->K = K;
+  plan->bn = bn;
+  plan->ok = 1;
+  return true;
+}
+
+template <int P, int BN, int MODE>
+static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
+  static bool attr = false;
+  constexpr int bytes = tc_smem_bytes(P, BN);
+  if (!attr) {
+    cudaFuncSetAttribute(k_tcgemm<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    attr = true;
+  }
+  dim3 grid((g.N + BN - 1) / BN, (g.M + kTcBM - 1) / kTcBM);
+  TcShape sh{g.M, g.Mpad, g.N, g.K};
+  k_tcgemm<P, BN, MODE><<<grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA, *(const CUtensorMap*)g.tmB,
+                                                        sh, e);
+}
+
+template <int P, int MODE>
+static void launch_bn(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
+  if (g.bn == 64) launch_one<P, 64, MODE>(g, e, s);
+  else if (g.bn == 128) launch_one<P, 128, MODE>(g, e, s);
+  else launch_one<P, 256, MODE>(g, e, s);
+}
+
+template <int MODE>
+static void launch_p(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
+  if (g.P == 1) launch_bn<1, MODE>(g, e, s);
+  else if (g.P == 2) launch_bn<2, MODE>(g, e, s);
+  else launch_bn<3, MODE>(g, e, s);
+}
+
+void tc_launch(const TcPlan& plan, const TcEpi& epi, int mode, cudaStream_t s) {
+  if (mode == kTcDelta) launch_p<kTcDelta>(plan, epi, s);
+  else launch_p<kTcStore>(plan, epi, s);
+}
+
+int* tc_error_word() {
+  void* p = nullptr;
+  cudaGetSymbolAddress(&p, g_tc_err);
+  return (int*)p;
+}
+
+void tc_clear_error(cudaStream_t s) { cudaMemsetAsync(tc_error_word(), 0, sizeof(int), s); }
+
+}  // namespace ksc

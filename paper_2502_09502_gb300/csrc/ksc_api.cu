@@ -12,6 +12,7 @@
 
 #include "../../include/ksc.h"
 #include "ksc_launch.h"
+#include "ksc_problem.h"
 #include "ksc_state.cuh"
 
 using namespace ksc;
@@ -31,6 +32,7 @@ static ksc_status fail(ksc_status st, const std::string& msg) {
 
 // shared with the other translation units of the library
 ksc_status ksc_internal_fail(ksc_status st, const char* msg) { return fail(st, msg); }
+ksc_status ksc::api_fail(ksc_status st, const std::string& msg) { return fail(st, msg); }
 
 #define KSC_CUDA(call)                                                              \
   do {                                                                              \
@@ -43,7 +45,7 @@ ksc_status ksc_internal_fail(ksc_status st, const char* msg) { return fail(st, m
 
 static bool g_prepared = false;
 
-static ksc_status ensure_prepared() {
+ksc_status ksc::ensure_prepared() {
   if (!g_prepared) {
     prox_prepare();
     cudaError_t e = cudaGetLastError();
@@ -54,32 +56,6 @@ static ksc_status ensure_prepared() {
 }
 
 // ------------------------------------------------------------------ problem
-
-static constexpr int kStepsPerGraph = 16;
-
-struct ksc_problem {
-  int device = 0;
-  int64_t n = 0, p = 0, ldx = 0;
-  int xdt = 0;
-  int loss = 0;
-  bool own_x = false;
-  void* X = nullptr;
-  double* y = nullptr;
-  std::vector<double> y_host;
-  double L = 0.0;
-  int power_iters = 0;
-  size_t bytes = 0;
-  Dev dev{};
-  std::vector<void*> allocs;
-  cudaGraphExec_t graph = nullptr;
-  cudaGraphExec_t graph_prof = nullptr;
-  bool profile = false;
-  std::vector<cudaEvent_t> events;   // 4 per step of the profiling graph
-  int64_t k_launches[3] = {0, 0, 0};
-  double k_ms[3] = {0, 0, 0};
-  int64_t launches = 0;   // every kernel launch issued for this problem
-  int32_t last_stats[6] = {0, 0, 0, 0, 0, 0};
-};
 
 // kernels per launcher (kept beside the launchers they count)
 static constexpr int kLaunchesPerStep = 5;      // gradient, prox select, prox apply, 2 forward
@@ -110,6 +86,7 @@ static void free_problem(ksc_problem* pr) {
   cudaSetDevice(pr->device);
   if (pr->graph) cudaGraphExecDestroy(pr->graph);
   if (pr->graph_prof) cudaGraphExecDestroy(pr->graph_prof);
+  free_batch(pr->batch);
   for (auto e : pr->events) cudaEventDestroy(e);
   for (void* v : pr->allocs) cudaFree(v);
   cudaSetDevice(cur);
@@ -360,11 +337,11 @@ extern "C" ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable) 
 extern "C" ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
                                               double* total_ms, int32_t reset) {
   if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
-  if (kernel < 0 || kernel > 2) return fail(KSC_ERR_INVALID_ARG, "unknown kernel id");
+  if (kernel < 0 || kernel >= kKernelIds) return fail(KSC_ERR_INVALID_ARG, "unknown kernel id");
   if (launches) *launches = problem->k_launches[kernel];
   if (total_ms) *total_ms = problem->k_ms[kernel];
   if (reset) {
-    for (int k = 0; k < 3; ++k) { problem->k_launches[k] = 0; problem->k_ms[k] = 0.0; }
+    for (int k = 0; k < kKernelIds; ++k) { problem->k_launches[k] = 0; problem->k_ms[k] = 0.0; }
   }
   return KSC_OK;
 }
@@ -402,14 +379,7 @@ static void fill_slots(std::vector<unsigned char>& buf, const std::vector<double
   for (size_t j = 0; j < b.size(); ++j) t[j] = (T)b[j];
 }
 
-struct NodeSetup {
-  std::vector<int8_t> state;
-  int kp = 0;
-  int n_one = 0;
-  bool infeasible = false;
-};
-
-static ksc_status check_node(const ksc_problem* pr, const ksc_node* node, NodeSetup* ns) {
+ksc_status ksc::check_node(const ksc_problem* pr, const ksc_node* node, NodeSetup* ns) {
   if (!node) return fail(KSC_ERR_INVALID_ARG, "node is NULL");
   if (!(node->lambda2 > 0) || !std::isfinite(node->lambda2)) return fail(KSC_ERR_INVALID_ARG, "lambda2 must be > 0");
   if (!(node->M > 0) || !std::isfinite(node->M)) return fail(KSC_ERR_INVALID_ARG, "M must be > 0");
@@ -574,18 +544,6 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   KSC_CUDA(cudaStreamSynchronize(s));
   if (out_status != KSC_OK) return fail(out_status, "max_iter reached before the gap target");
   return KSC_OK;
-}
-
-extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, int32_t count,
-                                      ksc_result* results, void* cuda_stream) {
-  if (!pr || !nodes || !results || count < 0) return fail(KSC_ERR_INVALID_ARG, "bad arguments");
-  ksc_status first = KSC_OK;
-  for (int32_t i = 0; i < count; ++i) {
-    ksc_status st = ksc_solve_node(pr, &nodes[i], &results[i], cuda_stream);
-    if (st != KSC_OK && st != KSC_NOT_CONVERGED && st != KSC_ERR_INFEASIBLE_NODE) return st;
-    if (first == KSC_OK && st != KSC_OK) first = st;
-  }
-  return first;
 }
 
 // ------------------------------------------------------------------ primitives

@@ -159,7 +159,8 @@ __device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist,
   constexpr int BITS = (int)sizeof(U) * 8;
   constexpr int DIG = 11;
   constexpr int NB = 1 << DIG;
-  static_assert(BLOCK * 2 == NB, "block_select expects 1024 threads");
+  constexpr int PER = NB / BLOCK;   // bins per thread
+  static_assert(NB % BLOCK == 0 && PER >= 1, "block_select: 2048 bins over the block");
   U prefix = 0;
   int q_rem = q, gt = 0, eq = 0;
   int hi = BITS;
@@ -184,14 +185,23 @@ __device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist,
         atomicAdd(&hist[bin], (unsigned)__popc(peers));
     }
     __syncthreads();
-    // thread t owns bins NB-1-2t (upper) and NB-2-2t (lower): thread order is
+    // thread t owns bins NB-1-PER*t down to NB-PER*(t+1): thread order is
     // descending bin order, so an exclusive scan gives the count above a bin.
-    const int b1 = NB - 1 - 2 * (int)threadIdx.x, b0 = b1 - 1;
-    const int c1 = (int)hist[b1], c0 = (int)hist[b0];
+    const int btop = NB - 1 - PER * (int)threadIdx.x;
+    int cnt[PER];
+    int own = 0;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      cnt[k] = (int)hist[btop - k];
+      own += cnt[k];
+    }
     int tot;
-    int above = block_exclusive_scan<int, BLOCK>(c1 + c0, sh, &tot);
-    if (above < q_rem && q_rem <= above + c1) { sh[36] = b1; sh[37] = above; sh[38] = c1; }
-    else if (above + c1 < q_rem && q_rem <= above + c1 + c0) { sh[36] = b0; sh[37] = above + c1; sh[38] = c0; }
+    int run = block_exclusive_scan<int, BLOCK>(own, sh, &tot);
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      if (run < q_rem && q_rem <= run + cnt[k]) { sh[36] = btop - k; sh[37] = run; sh[38] = cnt[k]; }
+      run += cnt[k];
+    }
     __syncthreads();
     const int bin = sh[36], cab = sh[37];
     eq = sh[38];

@@ -1,0 +1,62 @@
+// ksc_problem.h -- the library's view of a problem handle, shared by the C-ABI
+// translation units (single-node loop in ksc_api.cu, batched loop in
+// ksc_batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ksc.h"
+#include "ksc_launch.h"
+#include "ksc_state.cuh"
+
+namespace ksc {
+struct BatchWs;
+void free_batch(BatchWs* ws);
+}  // namespace ksc
+
+static constexpr int kStepsPerGraph = 16;
+static constexpr int kKernelIds = 8;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
+
+struct ksc_problem {
+  int device = 0;
+  int64_t n = 0, p = 0, ldx = 0;
+  int xdt = 0;
+  int loss = 0;
+  bool own_x = false;
+  void* X = nullptr;
+  double* y = nullptr;
+  std::vector<double> y_host;
+  double L = 0.0;
+  int power_iters = 0;
+  size_t bytes = 0;
+  ksc::Dev dev{};
+  std::vector<void*> allocs;
+  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph_prof = nullptr;
+  bool profile = false;
+  std::vector<cudaEvent_t> events;   // 4 per step of the profiling graph
+  int64_t k_launches[kKernelIds] = {};
+  double k_ms[kKernelIds] = {};
+  int64_t launches = 0;   // every kernel launch issued for this problem
+  int32_t last_stats[6] = {0, 0, 0, 0, 0, 0};
+  ksc::BatchWs* batch = nullptr;   // batched-solve workspace (created on first use)
+};
+
+namespace ksc {
+
+// a node's coordinate states and reduced budget, validated
+struct NodeSetup {
+  std::vector<int8_t> state;
+  int kp = 0;
+  int n_one = 0;
+  bool infeasible = false;
+};
+
+ksc_status check_node(const ksc_problem* pr, const ksc_node* node, NodeSetup* ns);
+ksc_status ensure_prepared();
+ksc_status api_fail(ksc_status st, const std::string& msg);
+
+}  // namespace ksc

@@ -177,7 +177,8 @@ struct SegIO {
   const T* w;                // direct input, or nullptr to form w from the FISTA state:
   const T* bc;               //   gamma = bc + c (bc - bp);  w = gamma - grad / L
   const T* bp;
-  const double* grad;
+  const double* grad;         // FP64 gradient, or
+  const float* gradf;         //   FP32 gradient (batched solves)
   double c, invL;
   double rho, M;
   int kp;
@@ -249,7 +250,8 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     if (io.w) w = to_d(io.w[i]);
     else {
       const double b = to_d(io.bc[i]);
-      w = b + io.c * (b - to_d(io.bp[i])) - io.grad[i] * io.invL;
+      const double gi = io.grad ? io.grad[i] : (double)io.gradf[i];
+      w = b + io.c * (b - to_d(io.bp[i])) - gi * io.invL;
     }
     const int8_t st = io.state ? io.state[i] : (int8_t)kFree;
     if (st == kFree) {

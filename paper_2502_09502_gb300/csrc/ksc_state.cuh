@@ -72,4 +72,39 @@ struct NodeDev {
   double cert_dual, cert_primal, cert_gap;
 };
 
+// The restart, best-bound and termination logic closing one FISTA step
+// (Algorithm 3 lines 9-10, the gap test of Sec. 4.1, the early-termination rules
+// of Sec. 4.3), for any node record with these fields (NodeDev, BNode).
+// dL (optional): the change L^{t+1} - L^t evaluated as a difference (the batched
+// solver's cancellation-free form); otherwise the two values are compared.
+template <class N>
+__device__ __forceinline__ void fista_step_logic(N* nd, double f, const double* dL = nullptr) {
+  const double Lnext = f + 2.0 * nd->lambda2 * nd->g_next;
+  const double D = nd->negconj - 2.0 * nd->lambda2 * nd->gstar;
+  nd->last_primal = Lnext;
+  nd->last_dual = D;
+  const bool up = dL ? (*dL >= 0.0) : (Lnext >= nd->Lcur);
+  if (nd->restart_on && up) {
+    nd->phi = 1.0;
+    nd->restarts += 1;
+  } else {
+    nd->phi += 1.0;
+  }
+  nd->Lcur = Lnext;
+  nd->best_primal = fmin(nd->best_primal, Lnext);
+  nd->best_dual = fmax(nd->best_dual, D);
+  nd->gap = (nd->best_primal - nd->best_dual) / fmax(fabs(nd->best_primal), 1e-300);
+  const int t = nd->iter + 1;
+  nd->iter = t;
+  int done = kRunning;
+  if (isfinite(nd->incumbent)) {
+    if (nd->best_dual > nd->incumbent) done = kDonePruned;
+    else if (Lnext < nd->incumbent) done = kDonePrimal;
+  }
+  if (done == kRunning && nd->gap <= nd->tol_loop) done = kDoneGap;
+  if (done == kRunning && t - 1 >= nd->max_iter) done = kDoneMaxIter;
+  nd->done = done;
+  nd->c = nd->momentum_on ? nd->phi / (nd->phi + 3.0) : 0.0;
+}
+
 }  // namespace ksc

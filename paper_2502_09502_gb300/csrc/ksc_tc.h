@@ -1,0 +1,65 @@
+// ksc_tc.h -- the tensor-core product of the batched solver (k_tcgemm.cu).
+//
+//   D[m][j] = sum_{q < P} sum_k A_q[m][k] * B[j][k]        (FP32 accumulation)
+//
+// A_q and B are BF16, K contiguous ("K-major"); A holds P pieces of the same
+// M x K matrix stacked as rows [q * Mpad, q * Mpad + M).  The batched FISTA step
+// (Algorithm 3 over many nodes) puts the nodes in M: A = the split iterates
+// (X beta for all nodes, B = X) or the split residuals (X^T r, B = the column-major
+// copy of X).  A vector split into P BF16 pieces whose sum is exact (P = 3 holds
+// any FP32 value) accumulates all pieces into one FP32 accumulator, so the product
+// is that of the FP32 vector up to the FP32 accumulation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ksc {
+
+enum : int { kTcStore = 0, kTcDelta = 1 };
+
+// epilogue kTcStore: row m of the product D goes to out + m * ldo (FP32).
+// epilogue kTcDelta (D = X dbeta, the change of the iterate): in FP64,
+//   u_new = u_old + D,  u_old at u64 + m * ldo + slot_in[m] * slot_stride,
+//                       u_new at u64 + m * ldo + slot_out[m] * slot_stride,
+// and per row and per 64 columns j the sums of the loss terms F_j(u_new) (least
+// squares (u - y_j)^2, logistic log(1 + e^{-y_j u})) and of their changes
+// F_j(u_new) - F_j(u_old), evaluated without cancellation, to
+// part[2 * (m * npart + j / 64) + {0, 1}]  (npart >= ceil(N / 64)).
+struct TcEpi {
+  float* out;
+  int64_t ldo;
+  double* u64;
+  const int* slot_in;
+  const int* slot_out;
+  int64_t slot_stride;
+  const float* y;
+  int loss;
+  int npart;
+  double* part;
+};
+
+struct TcPlan {
+  alignas(64) unsigned char tmA[128];   // CUtensorMap of the stacked A pieces
+  alignas(64) unsigned char tmB[128];   // CUtensorMap of B
+  int P, M, Mpad, N, K, bn;
+  int ok;
+};
+
+// tile widths (columns of B per CTA) the kernel is built for
+constexpr int kTcBNs[3] = {64, 128, 256};
+
+// Build the tensor maps.  A: device BF16, (P * Mpad) x lda elements, lda * 2 a
+// multiple of 16 bytes, Mpad (the row stride of the pieces) a multiple of 128;
+// rows M .. round_up(M, 128) - 1 of each piece are read (and must be finite) but
+// not stored.  B: device BF16, N x ldb.  Returns false (with a message in *why)
+// when the shapes or the driver refuse.
+bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t lda, const void* B,
+             int N, int64_t ldb, int bn, const char** why);
+// enqueue one product; mode kTcStore or kTcDelta
+void tc_launch(const TcPlan& plan, const TcEpi& epi, int mode, cudaStream_t s);
+// device error word of the product kernels (nonzero: a wait gave up); reset by tc_clear_error
+int* tc_error_word();
+void tc_clear_error(cudaStream_t s);
+
+}  // namespace ksc

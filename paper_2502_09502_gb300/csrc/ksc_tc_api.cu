@@ -1,0 +1,38 @@
+// ksc_tc_api.cu -- ksc_tc_gemm: the batched solver's tensor-core product on
+// caller-owned device buffers, exported so that tests can check it on its own.
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/ksc.h"
+#include "ksc_tc.h"
+
+ksc_status ksc_internal_fail(ksc_status st, const char* msg);
+
+using namespace ksc;
+
+extern "C" ksc_status ksc_tc_gemm(const void* A, int32_t pieces, int32_t m, int32_t m_pad, int32_t k,
+                                  int64_t lda, const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd,
+                                  int32_t tile_n, void* cuda_stream) {
+  if (!A || !B || !D) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "NULL operand");
+  if (ldd < n || (ldd % 4) != 0 || ((uintptr_t)D % 16) != 0)
+    return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldd must be >= n, a multiple of 4, D 16-byte aligned");
+  TcPlan plan;
+  const char* why = "";
+  if (!tc_plan(&plan, A, pieces, m, m_pad, k, lda, B, n, ldb, tile_n, &why))
+    return ksc_internal_fail(KSC_ERR_INVALID_ARG, why);
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  tc_clear_error(s);
+  TcEpi e{};
+  e.out = D;
+  e.ldo = ldd;
+  tc_launch(plan, e, kTcStore, s);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess)
+    return ksc_internal_fail(KSC_ERR_CUDA, (std::string("tensor-core product: ") + cudaGetErrorString(err)).c_str());
+  int word = 0;
+  cudaMemcpy(&word, tc_error_word(), sizeof word, cudaMemcpyDeviceToHost);
+  if (word != 0) return ksc_internal_fail(KSC_ERR_TIMEOUT, "tensor-core product: a device wait gave up");
+  return KSC_OK;
+}

@@ -27,12 +27,14 @@ KSC_LOSS_LSQ, KSC_LOSS_LOGISTIC = 0, 1
 KSC_F64, KSC_F32, KSC_BF16 = 0, 1, 2
 KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF = 1, 2
 KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
+KSC_KERNEL_B_RESID, KSC_KERNEL_B_GRAD, KSC_KERNEL_B_PROX, KSC_KERNEL_B_FWD, KSC_KERNEL_B_STEP = (
+    3, 4, 5, 6, 7)
 
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
-           "ksc_problem_launch_count", "ksc_problem_solve_stats",
+           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
            "ksc_last_error", "ksc_version"]
 
 
@@ -88,6 +90,9 @@ def _load():
     L.ksc_problem_solve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
     L.ksc_prox_g_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ksc_tc_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                              C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                              C.c_void_p]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -189,6 +194,13 @@ def ksc_prox_g_noalloc(w_ptr, p, k, M, rho, beta_ptr, top_ptr=None, stream=None)
     return lib.ksc_prox_g_noalloc(C.c_void_p(w_ptr), int(p), int(k), float(M), float(rho),
                                   C.c_void_p(beta_ptr), C.c_void_p(top_ptr) if top_ptr else None,
                                   _stream_ptr(stream))
+
+
+def ksc_tc_gemm(a_ptr, pieces, m, m_pad, k, lda, b_ptr, n, ldb, d_ptr, ldd, tile_n, stream=None):
+    """Tensor-core product on device buffers (see include/ksc.h); blocks until done."""
+    _check(lib.ksc_tc_gemm(C.c_void_p(a_ptr), int(pieces), int(m), int(m_pad), int(k), int(lda),
+                           C.c_void_p(b_ptr), int(n), int(ldb), C.c_void_p(d_ptr), int(ldd),
+                           int(tile_n), _stream_ptr(stream)))
 
 
 def ksc_problem_profile(h, enable: bool):
@@ -309,3 +321,20 @@ class Problem:
         _check(st, allow)
         return Result(beta, z, res.primal, res.dual_bound, res.rel_gap, res.iters, res.restarts,
                       bool(res.pruned), STATUS_NAMES[res.status if st == KSC_OK else st])
+
+    def solve_batch(self, nodes, want_beta=True, want_z=False,
+                    allow=(KSC_OK, KSC_NOT_CONVERGED, KSC_ERR_INFEASIBLE_NODE)):
+        """ksc_solve_batch over a list of Node; returns one Result per node."""
+        B = len(nodes)
+        arr = (NodeC * B)(*[nd.c for nd in nodes])
+        res = (ResultC * B)()
+        betas = [np.zeros(self.p) if want_beta else None for _ in range(B)]
+        zs = [np.zeros(self.p) if want_z else None for _ in range(B)]
+        for i in range(B):
+            res[i].beta = _dptr(betas[i]) if want_beta else None
+            res[i].z = _dptr(zs[i]) if want_z else None
+        st = lib.ksc_solve_batch(self.h, arr, B, res, _stream_ptr(self.stream))
+        _check(st, allow)
+        return [Result(betas[i], zs[i], res[i].primal, res[i].dual_bound, res[i].rel_gap,
+                       res[i].iters, res[i].restarts, bool(res[i].pruned),
+                       STATUS_NAMES[res[i].status]) for i in range(B)]
