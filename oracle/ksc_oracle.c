@@ -135,7 +135,11 @@ int kso_prox_gstar(const double *mu, int64_t p, int64_t k, double rho, double M,
   return 0;
 }
 
-/* Moreau identity (Sec. 3.3): prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w). */
+/* Moreau identity (Sec. 3.3): prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w).
+ * Where prox_{rho g*} leaves a coordinate unchanged (alpha_j = mu_j: the tail
+ * outside the pooled block, and every coordinate when k = 0, where g is the
+ * indicator of {0}) the identity gives beta_j = w_j - rho w_j / rho = 0 exactly;
+ * it is set to 0 rather than to the rounding residue of that difference. */
 int kso_prox_g(const double *w, int64_t p, int64_t k, double rho, double M,
                double *beta, int64_t *perm) {
   if (p <= 0) return 0;
@@ -143,7 +147,7 @@ int kso_prox_g(const double *w, int64_t p, int64_t k, double rho, double M,
   double *al = (double *)malloc((size_t)p * sizeof(double));
   for (int64_t j = 0; j < p; ++j) mu[j] = rho * w[j];
   kso_prox_gstar(mu, p, k, rho, M, al, perm);
-  for (int64_t j = 0; j < p; ++j) beta[j] = w[j] - al[j] / rho;
+  for (int64_t j = 0; j < p; ++j) beta[j] = (al[j] == mu[j]) ? 0.0 : w[j] - al[j] / rho;
   free(mu); free(al);
   return 0;
 }
