@@ -156,6 +156,28 @@ def _traffic(n, p):
         return None
 
 
+# ------------------------------------------------------------------ ranks
+
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of every rank's x (the job's wall time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(items, rank, world):
+    """Rank r's share of independent work units (nodes, requests): r, r + world, ..."""
+    return items[rank::world]
+
+
+def whole_job_rate(units_per_rank, world, ms_max):
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_ours(args, rank, world, dist):
@@ -218,12 +240,8 @@ def run_ours(args, rank, world, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_bounds = args.steps * world
-    value = total_bounds / (ms / 1e3)
+    ms = max_over_ranks(ms, dist)
+    value = whole_job_rate(args.steps, world, ms)
 
     # roofline of the dominant kernel (the gradient pass over X)
     nl, kms = stats["k"][0]
@@ -252,9 +270,7 @@ def run_ours(args, rank, world, dist):
                "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
                "d2h_bytes_per_step": int(2 * p * 8 + 64)}
         if dist:
-            t = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e["value"] = args.e2e_steps * world / float(t.item())
+            e2e["value"] = args.e2e_steps * world / max_over_ranks(e_s, dist)
 
     out = None
     if rank == 0:

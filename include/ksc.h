@@ -147,7 +147,13 @@ ksc_status ksc_solve_node(ksc_problem* problem, const ksc_node* node, ksc_result
 
 /* Solve `count` nodes of one problem together (blocking); result[i] belongs to
  * node[i].  Each result equals what ksc_solve_node returns for that node, within
- * the stated tolerance.  Returns the first non-OK per-node status, else KSC_OK. */
+ * the stated tolerance.  Returns the first non-OK per-node status, else KSC_OK.
+ * With BF16 X the nodes advance in lock step (up to 1024 per device pass): both
+ * products of every FISTA step run on the tensor cores for all nodes at once, on
+ * differences from per-node anchor points whose products are exact, and every
+ * reported bound is the FP64 certificate.  Other storage types (and nodes with
+ * k' >= 2048) are solved one by one by the single-node path.  The problem's
+ * batched workspace is allocated on first use and kept (ksc_problem_bytes). */
 ksc_status ksc_solve_batch(ksc_problem* problem, const ksc_node* nodes, int32_t count,
                            ksc_result* results, void* cuda_stream);
 
@@ -183,6 +189,44 @@ ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* ou
  * Non-finite entries of w give unspecified (but bounded-time) results. */
 ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, double rho,
                               double* beta_out, int32_t* top_out, void* cuda_stream);
+
+/* ---- serving -------------------------------------------------------------- */
+
+/* A request loop on the current device for dual-bound solves of many nodes of
+ * many problems (continuous batching).  A worker thread keeps one batched session
+ * of max_slots node slots per problem with pending work; nodes that arrive while
+ * others run take free slots between CUDA-graph replays (16 FISTA steps), the
+ * sessions of different problems run on their own streams and overlap on the
+ * device, and finished slots are refilled at once.  A session is opened only
+ * while the bytes of its problem (ksc_problem_bytes) plus the session's own
+ * workspace, summed over the open sessions, stay within hbm_budget_bytes;
+ * requests of other problems wait.  Problems whose X is not BF16 are solved one
+ * node at a time by the single-node path on the worker.  While a problem has
+ * requests in a server, the caller must not solve on it directly, nor destroy it.
+ * max_slots in 1..1024.  KSC_ERR_INVALID_ARG on bad arguments. */
+ksc_status ksc_server_create(size_t hbm_budget_bytes, int32_t max_slots, ksc_server** out);
+/* Queue one node (non-blocking); the node and its arrays are copied.  *ticket
+ * identifies the request.  KSC_ERR_INVALID_ARG for a malformed node (nothing is
+ * queued); KSC_ERR_ADMISSION when the problem alone exceeds the budget. */
+ksc_status ksc_server_submit(ksc_server* server, ksc_problem* problem, const ksc_node* node,
+                             uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request.  When done, fills *result
+ * (beta and z copied to the caller's arrays when non-NULL, length p), releases
+ * the ticket and returns the node's status (KSC_OK, KSC_NOT_CONVERGED,
+ * KSC_ERR_INFEASIBLE_NODE, or the error that ended it).  KSC_ERR_TIMEOUT when
+ * the wait expires (the request stays queued); KSC_ERR_INVALID_ARG for an
+ * unknown or released ticket. */
+ksc_status ksc_server_poll(ksc_server* server, uint64_t ticket, ksc_result* result, int32_t timeout_ms);
+/* Seconds from submission to completion of a polled request (kept until the
+ * server is destroyed). */
+ksc_status ksc_server_latency(ksc_server* server, uint64_t ticket, double* seconds);
+/* Server counters into stats[0..n): 0 completed requests, 1 graph replays,
+ * 2 sessions opened, 3 peak budgeted bytes, 4 requests that waited for budget,
+ * 5 requests admitted into a session that was already running. */
+ksc_status ksc_server_stats(ksc_server* server, int64_t* stats, int32_t n);
+/* Stop the worker (requests not yet finished end with KSC_ERR_TIMEOUT) and free
+ * every session. */
+ksc_status ksc_server_destroy(ksc_server* server);
 
 /* The tensor-core product of the batched solver, exported so that it can be
  * tested on its own.  The paper has no counterpart: it is the product X beta (and
@@ -221,14 +265,18 @@ ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);
 ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t* launches,
                                    double* total_ms, int32_t reset);
 
-/* Statistics of the last ksc_solve_node on this problem, written to stats[0..n):
- *   0  FISTA steps taken
+/* Statistics of the last ksc_solve_node (or batched ksc_solve_batch) on this
+ * problem, written to stats[0..n):
+ *   0  FISTA steps taken (batched: summed over the nodes)
  *   1  steps whose forward pass streamed only the nonzero columns of X
  *   2  steps whose prox needed the full-pass root finder (pooled block > 4096)
  *   3  steps whose prox used the candidates predicted from the previous step
  *   4  steps whose dual term used the predicted candidates
  *   5  Lanczos steps taken for L when the problem was created
- * Entries beyond 6 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
+ *   6  batched: FP64 certificates computed (one per in-loop stop)
+ *   7  batched: anchor products computed (exact X beta_ref and X^T r_ref)
+ * Entries 1-4 are 0 after a batched solve, 6-7 after a single-node one; entries
+ * beyond 8 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
 ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n);
 
 /* Number of kernel launches the library has issued for this problem (setup,

@@ -1,18 +1,19 @@
 // k_batch.cu -- the per-node kernels of a batched FISTA step (Algorithm 3 over B
 // nodes of one problem).  Between them run the two tensor-core products of
-// k_tcgemm.cu:
+// k_tcgemm.cu, each on a difference from the node's anchor (ksc_batch.cuh):
 //
 //   k_bresid   u_gamma = u_t + c (u_t - u_{t-1}) (linearity: no extra pass over X),
-//              r = grad F(u_gamma), its BF16 pieces (A of X^T r), and the terms of
-//              -F*(-zeta_gamma), zeta_gamma = -r (App. D), per CTA
-//   [tensor]   G = X^T r                      (node-major rows, FP32)
+//              r - r_ref = grad F(u_gamma) - grad F(u_ref) without cancellation,
+//              its BF16 pieces, and the terms of -F*(-zeta_gamma),
+//              zeta_gamma = -grad F(u_gamma) (App. D.1), per CTA
+//   [tensor]   G = G_ref + X^T (r - r_ref)                       (FP64 out)
 //   k_bprox    one CTA per node: w = gamma - G/L, the exact prox of g_node (block
 //              radix select + bitonic sort + breakpoint scan, Alg. 1 + 4 in the
 //              threshold form), g(beta^{t+1}) (Alg. 2), the in-loop dual term
 //              G*(X^T zeta_gamma) (Lemma 3.1 on the node), and the BF16 pieces of
-//              the step dbeta = beta^{t+1} - beta^t
-//   [tensor]   u^{t+1} = u^t + X dbeta (FP64), partials of F(u^{t+1}) and of its
-//              change F(u^{t+1}) - F(u^t)
+//              beta^{t+1} - beta_ref
+//   [tensor]   u^{t+1} = u_ref + X (beta^{t+1} - beta_ref) (FP64), partials of
+//              F(u^{t+1}) and of its change F(u^{t+1}) - F(u^t)
 //   k_bstep    the restart test on L^{t+1} - L^t (a sum of changes, free of the
 //              cancellation of two nearly equal objective values) and the gap
 //              test per node (the step logic shared with the single-node solver)
@@ -40,6 +41,20 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* dst, size_t 
 
 __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
 
+__device__ __forceinline__ double sigmoid_d(double t) {
+  return t >= 0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
+}
+
+// F_i(u) in FP64
+__device__ __forceinline__ double loss_d(double u, double y, int loss) {
+  if (loss == kLossLsq) {
+    const double r = u - y;
+    return r * r;
+  }
+  const double t = -y * u;
+  return t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
+}
+
 // ------------------------------------------------------------------ residual
 
 __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
@@ -50,30 +65,38 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
   const double c = nd->c;
   const double* Uc = d.U + ((size_t)b * 3 + nd->cur) * d.ldn;
   const double* Up = d.U + ((size_t)b * 3 + nd->prev) * d.ldn;
+  const double* Ur = d.u_ref + (size_t)b * d.ldn;
   const size_t pstride = (size_t)d.Bpad * d.ldn;
   __nv_bfloat16* rrow = d.rpc + (size_t)b * d.ldn;
   double nc = 0.0;
   const int i0 = blockIdx.x * kBThreads * kBRows;
-#pragma unroll 4
+#pragma unroll 2
   for (int r = 0; r < kBRows; ++r) {
     const int i = i0 + r * kBThreads + (int)threadIdx.x;
     if (i < d.n) {
       const double uc = __ldg(&Uc[i]);
-      const float ug = (float)(uc + c * (uc - __ldg(&Up[i])));
+      const double ug = uc + c * (uc - __ldg(&Up[i]));
+      const double du = ug - __ldg(&Ur[i]);
       const float y = __ldg(&d.yf[i]);
-      float res, term;
+      float dr, term;
       if (d.loss == kLossLsq) {
-        res = 2.0f * (ug - y);          // grad F
-        const float z = -res;           // zeta = -grad F
-        term = y * z - 0.25f * z * z;   // -F*(-zeta), App. D.1
+        dr = (float)(2.0 * du);                          // grad F = 2 (u - y)
+        const double z = -2.0 * (ug - (double)y);        // zeta = -grad F (FP64: u - y cancels)
+        nc += (double)y * z - 0.25 * z * z;              // -F*(-zeta), App. D.1
+        term = 0.0f;
       } else {
-        const float t = -y * ug;
-        const float s = 1.0f / (1.0f + __expf(-t));   // sigma(t)
-        res = -y * s;
-        // binary entropy of q = zeta_i y_i = s:  s softplus(-t) + (1-s) softplus(t)
+        // grad F = -y sigma(t), t = -y u;  sigma(t) - sigma(t_ref)
+        //   = sigma(t) (1 - sigma(t_ref)) (1 - e^{-(t - t_ref)})
+        const float t = -y * (float)ug;
+        const float tr = -y * (float)__ldg(&Ur[i]);
+        const float dt = (float)(-(double)y * du);
+        const float s = 1.0f / (1.0f + __expf(-t));
+        const float sr = 1.0f / (1.0f + __expf(tr));    // 1 - sigma(t_ref)
+        dr = -y * (s * sr * (-expm1f(-dt)));
+        // binary entropy of q = zeta_i y_i = sigma(t)
         term = s * softplusf(-t) + (1.0f - s) * softplusf(t);
       }
-      split_store(res, rrow + i, pstride, d.P);
+      split_store(dr, rrow + i, pstride, d.P);
       nc += (double)term;
     }
   }
@@ -92,24 +115,24 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
     if (threadIdx.x == 0) d.slot_new[b] = nw;
     return;
   }
-  SegSmem<float> sm = carve_seg_smem<float>(smem, kBatchCap, d.wsm);
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kBatchCap, d.wsm);
   const int p = d.p;
   const int8_t* st = d.state + (size_t)b * d.ldp;
-  float* brow = d.beta + (size_t)b * 3 * d.ldp;
-  const float* G = d.G + (size_t)b * d.ldp;
+  double* brow = d.beta + (size_t)b * 3 * d.ldp;
+  const double* G = d.G + (size_t)b * d.ldp;
   const double lambda2 = nd->lambda2, M = nd->M;
   const int kp = nd->kp;
   // in-loop dual term at gamma: a = X^T zeta_gamma = -G, |a| = |G|
-  const double gs = gstar_segment<float, kBProxBlock>(p, [&](int i) { return G[i]; }, st, kp, M,
-                                                      0.5 / lambda2, sm);
-  SegIO<float> io;
+  const double gs = gstar_segment<double, kBProxBlock>(p, [&](int i) { return G[i]; }, st, kp, M,
+                                                       0.5 / lambda2, sm);
+  SegIO<double> io;
   io.m = p;
   io.state = st;
   io.w = nullptr;
   io.bc = brow + (size_t)cur * d.ldp;
   io.bp = brow + (size_t)prev * d.ldp;
-  io.grad = nullptr;
-  io.gradf = G;
+  io.grad = G;
+  io.gradf = nullptr;
   io.c = nd->c;
   io.invL = nd->invL;
   io.rho = nd->rho;
@@ -122,14 +145,14 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   io.nnz_cap = 0;
   io.top_out = nullptr;
   io.qhint = nd->qhint;
-  const SegOut o = prox_segment<float, kBProxBlock>(io, sm);
+  const SegOut o = prox_segment<double, kBProxBlock>(io, sm);
   __syncthreads();
-  // BF16 pieces of the step beta^{t+1} - beta^t
+  // BF16 pieces of fl32(beta^{t+1} - beta_ref)
   const size_t pstride = (size_t)d.Bpad * d.ldp;
   __nv_bfloat16* prow = d.bpc + (size_t)b * d.ldp;
-  const float* bn = io.beta;
-  const float* bc = io.bc;
-  for (int j = threadIdx.x; j < p; j += kBProxBlock) split_store(__fsub_rn(bn[j], bc[j]), prow + j, pstride, d.P);
+  const double* bn = io.beta;
+  const double* br = d.beta_ref + (size_t)b * d.ldp;
+  for (int j = threadIdx.x; j < p; j += kBProxBlock) split_store((float)(bn[j] - br[j]), prow + j, pstride, d.P);
   if (threadIdx.x == 0) {
     double nc = 0.0;
     for (int t = 0; t < d.nrt; ++t) nc += d.ncpart[(size_t)b * d.nrt + t];
@@ -166,48 +189,38 @@ __global__ void __launch_bounds__(128) k_bstep(BatchDev d) {
   d.slot_cur[b] = nd->cur;
 }
 
-// ------------------------------------------------------------------ init
+// ------------------------------------------------------------------ admission
 
-// beta^0 = beta^1 = the projected warm start (uploaded into slot 1): copy to slot
-// 0, pieces of slot 1, u slot 0 = 0; the forward product then writes
-// u^1 = 0 + X beta^1 into slot 1
-__global__ void __launch_bounds__(256) k_binit_split(BatchDev d) {
-  const int b = blockIdx.y;
-  const int j = blockIdx.x * 256 + (int)threadIdx.x;
-  float* brow = d.beta + (size_t)b * 3 * d.ldp;
-  if (j < d.p) {
-    const float v = brow[(size_t)d.ldp + j];
+// beta^0 = beta^1 = beta_ref = the projected warm start (uploaded into slot 1)
+__global__ void __launch_bounds__(256) k_binit_copy(BatchDev d, const int* list) {
+  const int b = list[blockIdx.y];
+  double* brow = d.beta + (size_t)b * 3 * d.ldp;
+  for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
+    const double v = brow[(size_t)d.ldp + j];
     brow[j] = v;
-    split_store(v, d.bpc + (size_t)b * d.ldp + j, (size_t)d.Bpad * d.ldp, d.P);
-  }
-  if (j < d.n) d.U[(size_t)b * 3 * d.ldn + j] = 0.0;
-  if (j == 0) {
-    d.slot_cur[b] = 0;
-    d.slot_new[b] = 1;
+    d.beta_ref[(size_t)b * d.ldp + j] = v;
   }
 }
 
-// u^0 = u^1, g(beta^1) (Alg. 2) and L^1 = F(u^1) + 2 lambda2 g(beta^1)
-__global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d) {
+// u^0 = u^1 = u_ref (set by the anchor), F(u^1) in FP64, g(beta^1) (Alg. 2),
+// L^1 = F(u^1) + 2 lambda2 g(beta^1)  (Algorithm 3 line 2)
+__global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const int* list) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int b = blockIdx.x;
+  const int b = list[blockIdx.x];
   BNode* nd = d.nodes + b;
-  double* U1 = d.U + ((size_t)b * 3 + 1) * d.ldn;
-  double* U0 = d.U + ((size_t)b * 3 + 0) * d.ldn;
-  for (int i = threadIdx.x; i < d.n; i += kBProxBlock) U0[i] = U1[i];
-  SegSmem<float> sm = carve_seg_smem<float>(smem, kBatchCap, 0);
-  const float* b1 = d.beta + ((size_t)b * 3 + 1) * d.ldp;
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kBatchCap, 0);
+  const double* ur = d.u_ref + (size_t)b * d.ldn;
+  double f = 0.0;
+  for (int i = threadIdx.x; i < d.n; i += kBProxBlock) f += loss_d(ur[i], d.y[i], d.loss);
+  f = block_sum<double, kBProxBlock>(f, sm.red);
+  const double* b1 = d.beta + ((size_t)b * 3 + 1) * d.ldp;
   const int8_t* st = d.state + (size_t)b * d.ldp;
-  const GOut o = gvalue_segment<float, kBProxBlock>(d.p, [&](int i) { return (double)b1[i]; }, st, nd->kp,
-                                                    nd->M, sm, nullptr, 1e-6);
+  const GOut o = gvalue_segment<double, kBProxBlock>(d.p, [&](int i) { return b1[i]; }, st, nd->kp, nd->M, sm,
+                                                     nullptr, 1e-12);
   if (threadIdx.x == 0) {
-    double f = 0.0;
-    const double* fp = d.fpart + (size_t)2 * b * d.nft;
-    for (int t = 0; t < d.nft; ++t) f += fp[2 * t];
-    const double L1 = f + 2.0 * nd->lambda2 * o.g;   // Algorithm 3 line 2
+    const double L1 = f + 2.0 * nd->lambda2 * o.g;
     nd->g_next = o.g;
     nd->g_cur = o.g;
-    d.slot_cur[b] = 1;
     nd->Lcur = L1;
     nd->best_primal = L1;
     nd->best_dual = -INFINITY;
@@ -224,6 +237,37 @@ __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d) {
     nd->nnz = d.p;
     nd->qhint = 0;
     nd->fallback = 0;
+    d.slot_cur[b] = 1;
+    d.slot_new[b] = 2;
+  }
+}
+
+// ------------------------------------------------------------------ anchors
+
+__global__ void __launch_bounds__(256) k_banchor_copy(BatchDev d, int b) {
+  const BNode* nd = d.nodes + b;
+  const double* src = d.beta + ((size_t)b * 3 + nd->cur) * d.ldp;
+  double* dst = d.beta_ref + (size_t)b * d.ldp;
+  for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) dst[j] = src[j];
+}
+
+// r_ref = grad F(u_ref) in FP64; the u slot(s) of the current iterate take the
+// accurate u_ref
+__global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, int b, int init) {
+  const BNode* nd = d.nodes + b;
+  const double* ur = d.u_ref + (size_t)b * d.ldn;
+  double* rr = d.r_ref + (size_t)b * d.ldn;
+  double* U = d.U + (size_t)b * 3 * d.ldn;
+  const int cur = nd->cur;
+  for (int i = blockIdx.x * 256 + (int)threadIdx.x; i < d.n; i += gridDim.x * 256) {
+    const double u = ur[i], y = d.y[i];
+    rr[i] = d.loss == kLossLsq ? 2.0 * (u - y) : -y * sigmoid_d(-y * u);
+    if (init) {
+      U[i] = u;
+      U[(size_t)d.ldn + i] = u;
+    } else {
+      U[(size_t)cur * d.ldn + i] = u;
+    }
   }
 }
 
@@ -232,11 +276,11 @@ __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d) {
 // node b's state and newest iterate into the single-node workspace (FP64 slot 1)
 __global__ void __launch_bounds__(256) k_bcert_load(BatchDev bd, int b, Dev d) {
   const BNode* nb = bd.nodes + b;
-  const float* src = bd.beta + ((size_t)b * 3 + nb->cur) * bd.ldp;
+  const double* src = bd.beta + ((size_t)b * 3 + nb->cur) * bd.ldp;
   const int8_t* st = bd.state + (size_t)b * bd.ldp;
   double* dst = (double*)d.beta + (size_t)1 * d.p;
   for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
-    dst[j] = (double)src[j];
+    dst[j] = src[j];
     d.state[j] = st[j];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -252,7 +296,7 @@ __global__ void __launch_bounds__(256) k_bcert_load(BatchDev bd, int b, Dev d) {
 
 __global__ void __launch_bounds__(256) k_bcert_store(BatchDev bd, int b, Dev d, int want_z) {
   double* bo = bd.beta_out + (size_t)b * bd.p;
-  double* zo = want_z && bd.z_out ? bd.z_out + (size_t)b * bd.p : nullptr;
+  double* zo = want_z ? bd.z_out + (size_t)b * bd.p : nullptr;
   for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
     bo[j] = d.b64[j];
     if (zo) zo[j] = d.z64[j];
@@ -270,11 +314,16 @@ __global__ void __launch_bounds__(256) k_bcert_store(BatchDev bd, int b, Dev d, 
 
 // ------------------------------------------------------------------ launchers
 
-size_t bprox_smem_bytes(int wsm) { return seg_smem_bytes(kBatchCap, wsm, 4); }
+size_t bprox_smem_bytes(int wsm) { return seg_smem_bytes(kBatchCap, wsm, 8); }
 
 void batch_prepare(int optin) {
   cudaFuncSetAttribute(k_bprox, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_binit_node, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+static int vec_blocks(int m) {
+  const int g = (m + 255) / 256;
+  return g < 64 ? g : 64;
 }
 
 void launch_bresid(const BatchDev& d, cudaStream_t s) {
@@ -287,23 +336,28 @@ void launch_bprox(const BatchDev& d, cudaStream_t s) {
 
 void launch_bstep(const BatchDev& d, cudaStream_t s) { k_bstep<<<(d.B + 127) / 128, 128, 0, s>>>(d); }
 
-void launch_binit_split(const BatchDev& d, cudaStream_t s) {
-  const int m = d.p > d.n ? d.p : d.n;
-  k_binit_split<<<dim3((m + 255) / 256, d.B), 256, 0, s>>>(d);
+void launch_binit_copy(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_binit_copy<<<dim3(vec_blocks(d.p), count), 256, 0, s>>>(d, list);
 }
 
-void launch_binit_node(const BatchDev& d, cudaStream_t s) {
-  k_binit_node<<<d.B, kBProxBlock, bprox_smem_bytes(0), s>>>(d);
+void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_binit_node<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list);
+}
+
+void launch_banchor_copy(const BatchDev& d, int b, cudaStream_t s) {
+  k_banchor_copy<<<vec_blocks(d.p), 256, 0, s>>>(d, b);
+}
+
+void launch_banchor_resid(const BatchDev& d, int b, int init, cudaStream_t s) {
+  k_banchor_resid<<<vec_blocks(d.n), 256, 0, s>>>(d, b, init);
 }
 
 void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s) {
-  const int g = (d.p + 255) / 256;
-  k_bcert_load<<<g < 304 ? g : 304, 256, 0, s>>>(bd, b, d);
+  k_bcert_load<<<vec_blocks(d.p), 256, 0, s>>>(bd, b, d);
 }
 
 void launch_bcert_store(const BatchDev& bd, int b, const Dev& d, int want_z, cudaStream_t s) {
-  const int g = (d.p + 255) / 256;
-  k_bcert_store<<<g < 304 ? g : 304, 256, 0, s>>>(bd, b, d, want_z);
+  k_bcert_store<<<vec_blocks(d.p), 256, 0, s>>>(bd, b, d, want_z);
 }
 
 }  // namespace ksc

@@ -828,6 +828,21 @@ void launch_grad_raw(const Dev& d, cudaStream_t s) {
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
 }
 
+// out = A^T vec for A = X (vec of length n, out of length p) or A = Xc (vec of
+// length p, out of length n): the double-float streaming product
+void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s) {
+  int* cnt = d.cnt + cnt_colsum(d);
+  const void* A = use_xc ? d.Xc : d.X;
+  const int64_t lda = use_xc ? d.ldc : d.ldx;
+  const int rows = use_xc ? d.p : d.n, cols = use_xc ? d.n : d.p;
+  if (d.xdt == kXF64)
+    colsum_launch<double>((const double*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXF32)
+    colsum_launch<float>((const float*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
+  else
+    colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
+}
+
 void launch_transpose(const Dev& d, cudaStream_t s) {
   dim3 grid((d.p + 31) / 32, (d.n + 31) / 32);
   if (d.xdt == kXF64)

@@ -8,8 +8,8 @@
 //               from one thread, issues tcgen05.mma (M = 128, N = BN, K = 16; four
 //               per piece per K block) and tcgen05.commit to free each stage;
 //   warps 2..5  epilogue: tcgen05.ld of their 32 TMEM lanes (one output row per
-//               thread): row-major FP32 stores, or the FP64 update u += D with
-//               the loss partials of the row.
+//               thread): row-major FP32 stores, or FP64 anchor + D with the loss
+//               partials of the row.
 // Every wait is bounded (%globaltimer); a wait that gives up sets the error word,
 // raises the CTA's abort flag and the CTA drains its copies and MMAs before it
 // frees TMEM and exits.
@@ -307,12 +307,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (ok) {
       const bool row_ok = m < sh.M;
       float* orow = nullptr;
+      const double* brow = nullptr;
+      double* o64 = nullptr;
       const double* uin = nullptr;
       double* uout = nullptr;
       if (row_ok) {
         if (MODE == kTcStore) {
           orow = ep.out + (int64_t)m * ep.ldo;
+        } else if (MODE == kTcAdd) {
+          brow = ep.base + (int64_t)m * ep.ldb;
+          o64 = ep.out64 + (int64_t)m * ep.ldo;
         } else {
+          brow = ep.base + (int64_t)m * ep.ldb;
           uin = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_in[m] * ep.slot_stride;
           uout = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_out[m] * ep.slot_stride;
         }
@@ -335,20 +341,31 @@ __global__ void __launch_bounds__(kTcThreads, 1)
               for (int i = 0; i < 16; ++i)
                 if (nc + i < sh.N) orow[nc + i] = v[i];
             }
+          } else if (MODE == kTcAdd) {
+#pragma unroll 4
+            for (int i = 0; i < 16; ++i)
+              if (nc + i < sh.N) o64[nc + i] = brow[nc + i] + (double)v[i];
           } else {
             float fa = 0.0f, da = 0.0f;
+            double fd = 0.0;
 #pragma unroll 4
             for (int i = 0; i < 16; ++i) {
               if (nc + i < sh.N) {
                 const double uo = uin[nc + i];
-                const double un = uo + (double)v[i];
+                const double un = brow[nc + i] + (double)v[i];
                 uout[nc + i] = un;
                 const float yi = __ldg(&ep.y[nc + i]);
-                fa += loss_term((float)un, yi, ep.loss);
-                da += loss_change(uo, v[i], yi, ep.loss);
+                if (ep.loss == kLossLsq) {
+                  // (u - y)^2 in FP64: u - y cancels when the fit is good
+                  const double r = un - (double)yi;
+                  fd += r * r;
+                } else {
+                  fa += loss_term((float)un, yi, ep.loss);
+                }
+                da += loss_change(uo, (float)(un - uo), yi, ep.loss);
               }
             }
-            fsum += (double)fa;
+            fsum += (double)fa + fd;
             dsum += (double)da;
             // one pair of partials per 64 columns, whatever the tile width: the
             // sums do not depend on the tiling
@@ -463,7 +480,8 @@ static void launch_p(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
 }
 
 void tc_launch(const TcPlan& plan, const TcEpi& epi, int mode, cudaStream_t s) {
-  if (mode == kTcDelta) launch_p<kTcDelta>(plan, epi, s);
+  if (mode == kTcAnchor) launch_p<kTcAnchor>(plan, epi, s);
+  else if (mode == kTcAdd) launch_p<kTcAdd>(plan, epi, s);
   else launch_p<kTcStore>(plan, epi, s);
 }
 

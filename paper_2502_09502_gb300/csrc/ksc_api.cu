@@ -526,6 +526,8 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     KSC_CUDA(cudaMemcpyAsync(d.nd, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
     h = upd;
   }
+  pr->last_stats[6] = 0;
+  pr->last_stats[7] = 0;
   pr->last_stats[0] = h.iter - 1;
   pr->last_stats[1] = h.sparse_steps;
   pr->last_stats[2] = h.fallback;
@@ -624,7 +626,7 @@ extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M,
 extern "C" ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n) {
   if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
   if (n < 0 || (n > 0 && !stats)) return fail(KSC_ERR_INVALID_ARG, "bad stats buffer");
-  for (int32_t i = 0; i < n; ++i) stats[i] = i < 6 ? problem->last_stats[i] : 0;
+  for (int32_t i = 0; i < n; ++i) stats[i] = i < 8 ? problem->last_stats[i] : 0;
   return KSC_OK;
 }
 

@@ -1,13 +1,17 @@
-// ksc_batch.cu -- ksc_solve_batch: many nodes of one problem solved together.
+// ksc_batch.cu -- batched solves: sessions of node slots of one problem
+// (ksc_session.h) and ksc_solve_batch on top of them.
 //
 // Nodes with BF16 X advance in lock step through restarted FISTA (Algorithm 3):
-// per step one residual kernel, the product X^T r on the tensor cores, one prox
-// CTA per node, the product X beta on the tensor cores, and the per-node step
-// logic -- 16 steps per CUDA-graph replay.  A node whose in-loop test fires is
-// frozen; its FP64 certificate (Sec. 3.4) is computed through the single-node
-// workspace, and the node either finishes or resumes with a tighter in-loop
-// tolerance, exactly as in ksc_solve_node.  Nodes the batched path does not take
-// (X not BF16, k' beyond the per-node candidate capacity) are solved one by one.
+// per step one residual kernel, the product X^T (r - r_ref) on the tensor cores,
+// one prox CTA per node, the product X (beta - beta_ref) on the tensor cores,
+// and the per-node step logic -- 16 steps per CUDA-graph replay.  Anchors
+// (u_ref = X beta_ref, G_ref = X^T grad F(u_ref)) come from the double-float
+// streaming product at admission and again as a node's gap falls.  A node whose
+// in-loop test fires is frozen; its FP64 certificate (Sec. 3.4) is computed
+// through the single-node workspace, and the node either finishes or resumes with
+// a tighter in-loop tolerance, exactly as in ksc_solve_node.  Nodes the batched
+// path does not take (X not BF16, k' beyond the per-node candidate capacity) are
+// solved one by one.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +22,7 @@
 
 #include "ksc_batch.cuh"
 #include "ksc_problem.h"
+#include "ksc_session.h"
 #include "ksc_tc.h"
 
 namespace ksc {
@@ -26,12 +31,12 @@ struct BatchWs {
   int Bcap = 0;      // nodes the buffers hold
   int Bpad = 0;      // Bcap rounded up to 128 (row stride of the BF16 pieces)
   int ldp = 0, ldn = 0;
-  int B = -1;        // nodes of the current plans and graph
+  int B = -1;        // nodes of the current plans and graphs
   int bn_fwd = 0, bn_grad = 0;
-  int nft_max = 0;
   std::vector<void*> allocs;
   size_t bytes = 0;
   BatchDev bd{};
+  int* dlist = nullptr;   // device slot list for admissions (Bcap ints)
   TcPlan fwd{}, grad{};
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t graph_prof = nullptr;   // the same steps with events between the kernels
@@ -49,6 +54,8 @@ void free_batch(BatchWs* ws) {
   delete ws;
 }
 
+size_t Session::bytes() const { return ws ? ws->bytes : 0; }
+
 }  // namespace ksc
 
 using namespace ksc;
@@ -58,6 +65,7 @@ namespace {
 constexpr int kBatchStepsPerGraph = 16;
 constexpr int kLaunchesPerBatchStep = 5;   // residual, X^T r, prox, X beta, step
 constexpr int kLaunchesPerBatchCert = 7;   // load, 5 certificate kernels, store
+constexpr int kLaunchesPerAnchor = 4;      // copy, X beta_ref, grad F, X^T r_ref
 
 #define KB_CUDA(call)                                                                        \
   do {                                                                                       \
@@ -67,69 +75,94 @@ constexpr int kLaunchesPerBatchCert = 7;   // load, 5 certificate kernels, store
                       std::string(#call) + ": " + cudaGetErrorString(e_));                   \
   } while (0)
 
+BNode* hnodes(Session* se) { return (BNode*)se->hn_raw.data(); }
+BCert* hcerts(Session* se) { return (BCert*)se->hc_raw.data(); }
+
 template <typename P>
-ksc_status balloc(ksc_problem* pr, BatchWs* ws, P** ptr, size_t bytes) {
+ksc_status balloc(BatchWs* ws, P** ptr, size_t bytes) {
   void* v = nullptr;
   cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
   if (e != cudaSuccess)
     return api_fail(KSC_ERR_OOM, std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
   ws->allocs.push_back(v);
   ws->bytes += bytes;
-  pr->bytes += bytes;
   *ptr = (P*)v;
   return KSC_OK;
 }
 
 bool batch_supported(const ksc_problem* pr) { return pr->xdt == kXBF16; }
 
-// buffers for up to `need` nodes
-ksc_status ensure_ws(ksc_problem* pr, int need, cudaStream_t s) {
-  BatchWs* ws = pr->batch;
-  if (ws && ws->Bcap >= need) return KSC_OK;
-  if (ws) {
-    pr->bytes -= ws->bytes;
-    free_batch(ws);
-    pr->batch = nullptr;
-  }
-  ws = new BatchWs();
-  pr->batch = ws;
+int pad8(int64_t v) { return (int)((v + 7) / 8 * 8); }
+
+bool needs_xcopy(const ksc_problem* pr) { return !((pr->ldx * 2) % 16 == 0 && ((uintptr_t)pr->X % 16) == 0); }
+
+// workspace bytes for `need` slots (the allocations of alloc_ws)
+size_t ws_bytes(const ksc_problem* pr, int need) {
+  const size_t n = pr->n, p = pr->p;
+  const size_t ldp = pad8(p), ldn = pad8(n), Bc = need, Bp = (need + 127) / 128 * 128;
+  const size_t nft = (n + 63) / 64;
+  size_t b = 0;
+  b += Bc * ldp;                                // state
+  b += Bc * 3 * ldp * 8 + Bc * ldp * 8;         // beta slots, beta_ref
+  b += (size_t)kBatchPieces * Bp * ldp * 2;     // pieces of beta - beta_ref
+  b += Bc * 3 * ldn * 8 + 2 * Bc * ldn * 8;     // u slots, u_ref, r_ref
+  b += (size_t)kBatchPieces * Bp * ldn * 2;     // pieces of r - r_ref
+  b += 2 * Bc * ldp * 8;                        // G, G_ref
+  b += 2 * Bc * 4 + Bc * nft * 16 + Bc * batch_nrt((int)n) * 8;
+  b += Bc * (sizeof(BNode) + sizeof(BCert)) + 2 * Bc * p * 8 + Bc * 4 + n * 12;
+  if (p > 2048) b += Bc * ldp * 8;              // prox scratch
+  if (needs_xcopy(pr)) b += n * ldp * 2;
+  return b;
+}
+
+ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
+  BatchWs* ws = new BatchWs();
+  *out = ws;
   const int n = (int)pr->n, p = (int)pr->p;
   ws->Bcap = need;
   ws->Bpad = (need + 127) / 128 * 128;
-  ws->ldp = (p + 7) / 8 * 8;
-  ws->ldn = (n + 7) / 8 * 8;
-  ws->nft_max = (n + 63) / 64;   // loss partials: one per 64 columns
+  ws->ldp = pad8(p);
+  ws->ldn = pad8(n);
   const int Bc = ws->Bcap, Bp = ws->Bpad, P = kBatchPieces;
   const size_t ldp = ws->ldp, ldn = ws->ldn;
+  const int nft = (n + 63) / 64;
   BatchDev& d = ws->bd;
   ksc_status st;
 #define BA(ptr, bytes) \
-  if ((st = balloc(pr, ws, &(ptr), (bytes))) != KSC_OK) return st
+  if ((st = balloc(ws, &(ptr), (bytes))) != KSC_OK) return st
   int8_t* state = nullptr;
   BA(state, (size_t)Bc * ldp);
   d.state = state;
-  BA(d.beta, (size_t)Bc * 3 * ldp * 4);
+  BA(d.beta, (size_t)Bc * 3 * ldp * 8);
+  BA(d.beta_ref, (size_t)Bc * ldp * 8);
   BA(d.bpc, (size_t)P * Bp * ldp * 2);
   BA(d.U, (size_t)Bc * 3 * ldn * 8);
+  BA(d.u_ref, (size_t)Bc * ldn * 8);
+  BA(d.r_ref, (size_t)Bc * ldn * 8);
   BA(d.rpc, (size_t)P * Bp * ldn * 2);
-  BA(d.G, (size_t)Bc * ldp * 4);
+  BA(d.G, (size_t)Bc * ldp * 8);
+  BA(d.G_ref, (size_t)Bc * ldp * 8);
   BA(d.slot_cur, (size_t)Bc * 4);
   BA(d.slot_new, (size_t)Bc * 4);
-  BA(d.fpart, (size_t)Bc * ws->nft_max * 2 * 8);
+  BA(d.fpart, (size_t)Bc * nft * 2 * 8);
   BA(d.ncpart, (size_t)Bc * batch_nrt(n) * 8);
   BA(d.nodes, (size_t)Bc * sizeof(BNode));
   BA(d.cert, (size_t)Bc * sizeof(BCert));
   BA(d.beta_out, (size_t)Bc * p * 8);
   BA(d.z_out, (size_t)Bc * p * 8);
+  BA(ws->dlist, (size_t)Bc * 4);
   float* yf = nullptr;
   BA(yf, (size_t)n * 4);
   d.yf = yf;
-  // w of the prox in shared memory when it fits (4 CTAs per SM at p = 5000)
-  d.wsm = bprox_smem_bytes(p) <= 200 * 1024 ? p : 0;
+  double* yd = nullptr;
+  BA(yd, (size_t)n * 8);
+  d.y = yd;
+  // w of the prox in shared memory for short segments, else in (L2-resident) global scratch
+  d.wsm = p <= 2048 ? p : 0;
   d.wbuf = nullptr;
-  if (d.wsm == 0) BA(d.wbuf, (size_t)Bc * ldp * 4);
+  if (d.wsm == 0) BA(d.wbuf, (size_t)Bc * ldp * 8);
   // X for the TMA loads: row stride a multiple of 16 bytes, 16-byte aligned base
-  if ((pr->ldx * 2) % 16 == 0 && ((uintptr_t)pr->X % 16) == 0) {
+  if (!needs_xcopy(pr)) {
     ws->Xb = pr->X;
     ws->ldxb = pr->ldx;
   } else {
@@ -140,15 +173,18 @@ ksc_status ensure_ws(ksc_problem* pr, int need, cudaStream_t s) {
     ws->ldxb = (int64_t)ldp;
   }
 #undef BA
-  // every row the products read must be finite: zero the pieces once
+  // every row the products read must be finite: zero the buffers once
   KB_CUDA(cudaMemsetAsync(d.bpc, 0, (size_t)P * Bp * ldp * 2, s));
   KB_CUDA(cudaMemsetAsync(d.rpc, 0, (size_t)P * Bp * ldn * 2, s));
-  KB_CUDA(cudaMemsetAsync(d.beta, 0, (size_t)Bc * 3 * ldp * 4, s));
+  KB_CUDA(cudaMemsetAsync(d.beta, 0, (size_t)Bc * 3 * ldp * 8, s));
   KB_CUDA(cudaMemsetAsync(d.U, 0, (size_t)Bc * 3 * ldn * 8, s));
+  KB_CUDA(cudaMemsetAsync(d.u_ref, 0, (size_t)Bc * ldn * 8, s));
+  KB_CUDA(cudaMemsetAsync(d.G_ref, 0, (size_t)Bc * ldp * 8, s));
   {
     std::vector<float> yh(n);
     for (int i = 0; i < n; ++i) yh[i] = (float)pr->y_host[i];
     KB_CUDA(cudaMemcpyAsync(yf, yh.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaMemcpyAsync(yd, pr->y_host.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
     KB_CUDA(cudaStreamSynchronize(s));
   }
   d.n = n;
@@ -158,14 +194,17 @@ ksc_status ensure_ws(ksc_problem* pr, int need, cudaStream_t s) {
   d.ldp = ws->ldp;
   d.ldn = ws->ldn;
   d.nrt = batch_nrt(n);
-  d.nft = ws->nft_max;
+  d.nft = nft;
   d.Bpad = ws->Bpad;
+  d.B = Bc;
   return KSC_OK;
 }
 
 TcEpi fwd_epi(const BatchWs* ws) {
   const BatchDev& d = ws->bd;
   TcEpi e{};
+  e.base = d.u_ref;
+  e.ldb = d.ldn;
   e.u64 = d.U;
   e.ldo = 3 * (int64_t)d.ldn;
   e.slot_in = d.slot_cur;
@@ -179,9 +218,12 @@ TcEpi fwd_epi(const BatchWs* ws) {
 }
 
 TcEpi grad_epi(const BatchWs* ws) {
+  const BatchDev& d = ws->bd;
   TcEpi e{};
-  e.out = ws->bd.G;
-  e.ldo = ws->bd.ldp;
+  e.base = d.G_ref;
+  e.ldb = d.ldp;
+  e.out64 = d.G;
+  e.ldo = d.ldp;
   return e;
 }
 
@@ -193,11 +235,11 @@ void enqueue_step(const BatchWs* ws, cudaStream_t s, const cudaEvent_t* ev) {
   mark(0);
   launch_bresid(ws->bd, s);
   mark(1);
-  tc_launch(ws->grad, grad_epi(ws), kTcStore, s);
+  tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
   mark(2);
   launch_bprox(ws->bd, s);
   mark(3);
-  tc_launch(ws->fwd, fwd_epi(ws), kTcDelta, s);
+  tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
   mark(4);
   launch_bstep(ws->bd, s);
   mark(5);
@@ -228,9 +270,8 @@ ksc_status capture(BatchWs* ws, bool prof) {
   return KSC_OK;
 }
 
-// tensor maps, tile widths (timed once per batch size) and the step graph for B nodes
-ksc_status plan_batch(ksc_problem* pr, int B, cudaStream_t s) {
-  BatchWs* ws = pr->batch;
+// tensor maps, tile widths (timed once per slot count) and the step graphs
+ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   if (ws->B == B && ws->graph) return KSC_OK;
   BatchDev& d = ws->bd;
   d.B = B;
@@ -240,30 +281,32 @@ ksc_status plan_batch(ksc_problem* pr, int B, cudaStream_t s) {
     return tc_plan(&ws->fwd, d.bpc, d.P, B, ws->Bpad, d.p, d.ldp, ws->Xb, d.n, ws->ldxb, bf, &why) &&
            tc_plan(&ws->grad, d.rpc, d.P, B, ws->Bpad, d.n, d.ldn, sd.Xc, d.p, sd.ldc, bg, &why);
   };
-  // autotune: time each tile width of each product on the current buffers
+  // autotune: time each tile width of each product (their outputs go to scratch:
+  // u slot 2 and G of every row, before any node is admitted)
   cudaEvent_t e0, e1;
   KB_CUDA(cudaEventCreate(&e0));
   KB_CUDA(cudaEventCreate(&e1));
   float best_f = 1e30f, best_g = 1e30f;
   int bf = 128, bg = 128;
+  std::vector<int> two(B, 2), zero(B, 0);
+  KB_CUDA(cudaMemcpyAsync(d.slot_new, two.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
+  KB_CUDA(cudaMemcpyAsync(d.slot_cur, zero.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
   for (int bn : kTcBNs) {
     if (!make(bn, bn)) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
     }
-    KB_CUDA(cudaMemsetAsync(d.slot_new, 0, (size_t)B * 4, s));
-    KB_CUDA(cudaMemsetAsync(d.slot_cur, 0, (size_t)B * 4, s));
     for (int rep = 0; rep < 3; ++rep) {
+      float ms = 0.f;
       KB_CUDA(cudaEventRecord(e0, s));
-      tc_launch(ws->fwd, fwd_epi(ws), kTcDelta, s);
+      tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
       KB_CUDA(cudaEventRecord(e1, s));
       KB_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
       KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
       if (rep > 0 && ms < best_f) { best_f = ms; bf = bn; }
       KB_CUDA(cudaEventRecord(e0, s));
-      tc_launch(ws->grad, grad_epi(ws), kTcStore, s);
+      tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
       KB_CUDA(cudaEventRecord(e1, s));
       KB_CUDA(cudaEventSynchronize(e1));
       KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
@@ -276,7 +319,6 @@ ksc_status plan_batch(ksc_problem* pr, int B, cudaStream_t s) {
   if (!make(bf, bg)) return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
   ws->bn_fwd = bf;
   ws->bn_grad = bg;
-  // the step graphs (plain, and with events for ksc_problem_kernel_time)
   ksc_status st;
   if ((st = capture(ws, false)) != KSC_OK) return st;
   if ((st = capture(ws, true)) != KSC_OK) return st;
@@ -292,142 +334,287 @@ ksc_status check_tc(cudaStream_t s) {
   return KSC_OK;
 }
 
-struct Job {
-  int idx;            // position in the caller's arrays
-  NodeSetup ns;
-};
-
-// solve up to kBatchMax nodes in one device pass
-ksc_status solve_group(ksc_problem* pr, const ksc_node* nodes, ksc_result* results, std::vector<Job>& jobs,
-                       cudaStream_t s) {
-  const int B = (int)jobs.size();
-  const int p = (int)pr->p;
-  ksc_status st;
-  if ((st = ensure_ws(pr, std::max(B, pr->batch ? pr->batch->Bcap : 0), s)) != KSC_OK) return st;
-  BatchWs* ws = pr->batch;
-  BatchDev& d = ws->bd;
-  d.B = B;
-  const size_t ldp = ws->ldp;
-  // per-node inputs: coordinate states, projected warm starts (slot 1), parameters
-  {
-    std::vector<int8_t> hs((size_t)B * ldp, (int8_t)kZero);
-    std::vector<float> hb((size_t)B * ldp, 0.0f);
-    std::vector<BNode> hn(B);
-    for (int b = 0; b < B; ++b) {
-      const ksc_node* nd = &nodes[jobs[b].idx];
-      const NodeSetup& ns = jobs[b].ns;
-      std::memcpy(&hs[(size_t)b * ldp], ns.state.data(), p);
-      if (nd->warm_beta)
-        for (int j = 0; j < p; ++j)
-          hb[(size_t)b * ldp + j] =
-              ns.state[j] == kZero ? 0.0f : (float)std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
-      BNode& h = hn[b];
-      std::memset(&h, 0, sizeof h);
-      h.lambda2 = nd->lambda2;
-      h.M = nd->M;
-      h.rho = pr->L / (2.0 * nd->lambda2);
-      h.invL = 1.0 / pr->L;
-      h.tol_loop = nd->rel_gap_tol;
-      h.incumbent = nd->incumbent;
-      h.kp = ns.kp;
-      h.max_iter = nd->max_iter;
-      h.restart_on = (nd->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
-      h.momentum_on = (nd->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;
-    }
-    KB_CUDA(cudaMemcpy2DAsync((void*)d.state, ldp, hs.data(), ldp, (size_t)p, B, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaMemcpy2DAsync(d.beta + ldp, 3 * ldp * 4, hb.data(), ldp * 4, ldp * 4, B, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaMemcpyAsync(d.nodes, hn.data(), (size_t)B * sizeof(BNode), cudaMemcpyHostToDevice, s));
-  }
-  if ((st = plan_batch(pr, B, s)) != KSC_OK) return st;
-  tc_clear_error(s);
-  launch_binit_split(d, s);
-  tc_launch(ws->fwd, fwd_epi(ws), kTcDelta, s);
-  launch_binit_node(d, s);
-  pr->launches += 3;
-  KB_CUDA(cudaGetLastError());
-
-  std::vector<BNode> hn(B);
-  std::vector<BCert> hc(B);
-  std::vector<char> fin(B, 0);
-  std::vector<int> pruned(B, 0);
-  std::vector<ksc_status> status(B, KSC_OK);
-  int remaining = B;
-  while (remaining > 0) {
-    KB_CUDA(cudaGraphLaunch(pr->profile ? ws->graph_prof : ws->graph, s));
-    pr->launches += (int64_t)kLaunchesPerBatchStep * kBatchStepsPerGraph;
-    KB_CUDA(cudaMemcpyAsync(hn.data(), d.nodes, (size_t)B * sizeof(BNode), cudaMemcpyDeviceToHost, s));
-    if ((st = check_tc(s)) != KSC_OK) return st;
-    if (pr->profile) {
-      for (int k = 0; k < kBatchStepsPerGraph; ++k)
-        for (int j = 0; j < 5; ++j) {
-          float ms = 0.f;
-          KB_CUDA(cudaEventElapsedTime(&ms, ws->events[6 * k + j], ws->events[6 * k + j + 1]));
-          pr->k_ms[KSC_KERNEL_B_RESID + j] += ms;
-          pr->k_launches[KSC_KERNEL_B_RESID + j] += 1;
-        }
-    }
-    std::vector<int> fired;
-    for (int b = 0; b < B; ++b)
-      if (!fin[b] && hn[b].done != kRunning) fired.push_back(b);
-    if (fired.empty()) continue;
-    // FP64 certificates of the nodes whose in-loop test fired
-    for (int b : fired) {
-      const int want_z = results[jobs[b].idx].z != nullptr;
-      launch_bcert_load(d, b, pr->dev, s);
-      launch_certificate(pr->dev, s, want_z);
-      launch_bcert_store(d, b, pr->dev, want_z, s);
-      pr->launches += kLaunchesPerBatchCert;
-    }
-    KB_CUDA(cudaGetLastError());
-    KB_CUDA(cudaMemcpyAsync(hc.data(), d.cert, (size_t)B * sizeof(BCert), cudaMemcpyDeviceToHost, s));
-    KB_CUDA(cudaStreamSynchronize(s));
-    for (int b : fired) {
-      const ksc_node* nd = &nodes[jobs[b].idx];
-      const double tol = nd->rel_gap_tol, inc = nd->incumbent;
-      const BNode& h = hn[b];
-      const BCert& c = hc[b];
-      bool done = false;
-      if (std::isfinite(inc) && c.dual > inc) { pruned[b] = 1; done = true; }
-      else if (c.gap <= tol) done = true;
-      else if (h.done == kDonePrimal) done = true;                       // Sec. 4.3 rule (1): branch
-      else if (h.done == kDoneMaxIter) { status[b] = KSC_NOT_CONVERGED; done = true; }
-      if (done) {
-        fin[b] = 1;
-        --remaining;
-        continue;
-      }
-      // the in-loop test fired on values the certificate does not confirm
-      BNode upd = h;
-      if (h.done == kDoneGap) upd.tol_loop = std::max(h.gap * 0.25, 1e-16);
-      if (h.done == kDonePruned) upd.incumbent = inc + 2.0 * std::fabs(h.best_dual - c.dual) + 1e-12 * std::fabs(inc);
-      upd.done = kRunning;
-      upd.best_dual = c.dual > -INFINITY ? std::max(c.dual, -1e300) : -INFINITY;
-      KB_CUDA(cudaMemcpyAsync(d.nodes + b, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
-      hn[b] = upd;
-    }
-    KB_CUDA(cudaStreamSynchronize(s));
-  }
-  // results
-  for (int b = 0; b < B; ++b) {
-    ksc_result* r = &results[jobs[b].idx];
-    r->primal = hc[b].primal;
-    r->dual_bound = hc[b].dual;
-    r->rel_gap = hc[b].gap;
-    r->iters = hn[b].iter - 1;
-    r->restarts = hn[b].restarts;
-    r->pruned = pruned[b];
-    r->status = status[b];
-    if (r->beta) KB_CUDA(cudaMemcpyAsync(r->beta, d.beta_out + (size_t)b * p, (size_t)p * 8, cudaMemcpyDeviceToHost, s));
-    if (r->z) KB_CUDA(cudaMemcpyAsync(r->z, d.z_out + (size_t)b * p, (size_t)p * 8, cudaMemcpyDeviceToHost, s));
-  }
-  KB_CUDA(cudaStreamSynchronize(s));
-  int64_t it = 0;
-  for (int b = 0; b < B; ++b) it += hn[b].iter - 1;
-  pr->last_stats[0] = (int32_t)std::min<int64_t>(it, INT32_MAX);
-  return KSC_OK;
+// anchor of slot b at its current iterate (init: at the warm start of slot 1)
+void anchor(Session* se, int b, bool init) {
+  const BatchDev& d = se->ws->bd;
+  const Dev& sd = se->pr->dev;
+  if (!init) launch_banchor_copy(d, b, se->s);
+  launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, se->s);
+  launch_banchor_resid(d, b, init ? 1 : 0, se->s);
+  launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, se->s);
+  se->pr->launches += kLaunchesPerAnchor;
+  se->anchors += 1;
 }
 
 }  // namespace
+
+// ------------------------------------------------------------------ sessions
+
+namespace ksc {
+
+size_t session_bytes(const ksc_problem* pr, int slots) { return ws_bytes(pr, slots); }
+
+ksc_status session_open(Session* se, ksc_problem* pr, int slots, bool use_problem_ws, cudaStream_t s) {
+  if (slots < 1 || slots > kBatchMax) return api_fail(KSC_ERR_INVALID_ARG, "session slots out of range");
+  if (!batch_supported(pr)) return api_fail(KSC_ERR_UNIMPLEMENTED, "batched solves need BF16 X");
+  se->pr = pr;
+  se->s = s;
+  se->B = slots;
+  ksc_status st;
+  if (use_problem_ws) {
+    if (!pr->batch || pr->batch->Bcap < slots) {
+      if (pr->batch) {
+        pr->bytes -= pr->batch->bytes;
+        free_batch(pr->batch);
+        pr->batch = nullptr;
+      }
+      BatchWs* ws = nullptr;
+      st = alloc_ws(pr, std::max(slots, 128), s, &ws);
+      if (st != KSC_OK) {
+        free_batch(ws);
+        return st;
+      }
+      pr->batch = ws;
+      pr->bytes += ws->bytes;
+    }
+    se->ws = pr->batch;
+    se->own_ws = false;
+  } else {
+    BatchWs* ws = nullptr;
+    st = alloc_ws(pr, slots, s, &ws);
+    if (st != KSC_OK) {
+      free_batch(ws);
+      return st;
+    }
+    se->ws = ws;
+    se->own_ws = true;
+  }
+  if ((st = plan_batch(pr, se->ws, slots, s)) != KSC_OK) return st;
+  // every slot starts empty
+  se->slot.assign(slots, SlotHost());
+  se->hn_raw.assign((size_t)slots * sizeof(BNode), 0);
+  se->hc_raw.assign((size_t)slots * sizeof(BCert), 0);
+  BNode* hn = hnodes(se);
+  for (int b = 0; b < slots; ++b) {
+    hn[b].done = kSlotIdle;
+    hn[b].cur = 1;
+    hn[b].prev = 0;
+  }
+  KB_CUDA(cudaMemcpyAsync(se->ws->bd.nodes, hn, (size_t)slots * sizeof(BNode), cudaMemcpyHostToDevice, s));
+  KB_CUDA(cudaStreamSynchronize(s));
+  return KSC_OK;
+}
+
+void session_close(Session* se) {
+  if (se->own_ws) free_batch(se->ws);
+  se->ws = nullptr;
+  se->slot.clear();
+}
+
+int session_free_slots(const Session* se) {
+  int f = 0;
+  for (const auto& sl : se->slot) f += sl.busy ? 0 : 1;
+  return f;
+}
+
+int session_running(const Session* se) {
+  int r = 0;
+  for (const auto& sl : se->slot) r += (sl.busy && !sl.fin) ? 1 : 0;
+  return r;
+}
+
+ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes, const std::vector<const NodeSetup*>& ns,
+                         const std::vector<int>& want_z, std::vector<int>* slots) {
+  const int cnt = (int)nodes.size();
+  slots->clear();
+  if (cnt == 0) return KSC_OK;
+  if (cnt > session_free_slots(se)) return api_fail(KSC_ERR_ADMISSION, "no free slot");
+  ksc_problem* pr = se->pr;
+  BatchWs* ws = se->ws;
+  BatchDev& d = ws->bd;
+  const int p = (int)pr->p;
+  const size_t ldp = ws->ldp;
+  cudaStream_t s = se->s;
+  BNode* hn = hnodes(se);
+  std::vector<int8_t> hs(ldp);
+  std::vector<double> hb(ldp);
+  int next = 0;
+  for (int i = 0; i < cnt; ++i) {
+    while (se->slot[next].busy) ++next;
+    const int b = next++;
+    slots->push_back(b);
+    const ksc_node* nd = nodes[i];
+    const NodeSetup& setup = *ns[i];
+    std::fill(hs.begin(), hs.end(), (int8_t)kZero);
+    std::memcpy(hs.data(), setup.state.data(), p);
+    std::fill(hb.begin(), hb.end(), 0.0);
+    if (nd->warm_beta)
+      for (int j = 0; j < p; ++j)
+        hb[j] = setup.state[j] == kZero ? 0.0 : std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
+    BNode& h = hn[b];
+    std::memset(&h, 0, sizeof h);
+    h.lambda2 = nd->lambda2;
+    h.M = nd->M;
+    h.rho = pr->L / (2.0 * nd->lambda2);
+    h.invL = 1.0 / pr->L;
+    h.tol_loop = nd->rel_gap_tol;
+    h.incumbent = nd->incumbent;
+    h.kp = setup.kp;
+    h.max_iter = nd->max_iter;
+    h.restart_on = (nd->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
+    h.momentum_on = (nd->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;
+    h.done = kSlotIdle;   // k_binit_node starts it
+    h.cur = 1;
+    h.prev = 0;
+    SlotHost& sl = se->slot[b];
+    sl = SlotHost();
+    sl.busy = true;
+    sl.want_z = want_z[i];
+    sl.tol = nd->rel_gap_tol;
+    sl.inc = nd->incumbent;
+    sl.anchor_gap = 100.0 * nd->rel_gap_tol;
+    // pageable sources: each copy completes before the host buffers are reused
+    KB_CUDA(cudaMemcpyAsync((void*)(d.state + (size_t)b * ldp), hs.data(), ldp, cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaMemcpyAsync(d.beta + ((size_t)b * 3 + 1) * ldp, hb.data(), ldp * 8, cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaMemcpyAsync(d.nodes + b, &h, sizeof h, cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaStreamSynchronize(s));
+  }
+  KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
+  launch_binit_copy(d, ws->dlist, cnt, s);
+  pr->launches += 1;
+  for (int b : *slots) anchor(se, b, true);
+  launch_binit_node(d, ws->dlist, cnt, s);
+  pr->launches += 1;
+  KB_CUDA(cudaGetLastError());
+  KB_CUDA(cudaStreamSynchronize(s));
+  return KSC_OK;
+}
+
+bool session_advance(Session* se, ksc_status* st) {
+  *st = KSC_OK;
+  if (session_running(se) == 0) return false;
+  ksc_problem* pr = se->pr;
+  cudaError_t e = cudaGraphLaunch(pr->profile ? se->ws->graph_prof : se->ws->graph, se->s);
+  if (e != cudaSuccess) {
+    *st = api_fail(KSC_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
+    return false;
+  }
+  pr->launches += (int64_t)kLaunchesPerBatchStep * kBatchStepsPerGraph;
+  return true;
+}
+
+ksc_status session_collect(Session* se, std::vector<int>* finished) {
+  ksc_problem* pr = se->pr;
+  BatchWs* ws = se->ws;
+  BatchDev& d = ws->bd;
+  cudaStream_t s = se->s;
+  const int B = se->B;
+  BNode* hn = hnodes(se);
+  BCert* hc = hcerts(se);
+  KB_CUDA(cudaMemcpyAsync(hn, d.nodes, (size_t)B * sizeof(BNode), cudaMemcpyDeviceToHost, s));
+  ksc_status st;
+  if ((st = check_tc(s)) != KSC_OK) return st;
+  if (pr->profile) {
+    for (int k = 0; k < kBatchStepsPerGraph; ++k)
+      for (int j = 0; j < 5; ++j) {
+        float ms = 0.f;
+        KB_CUDA(cudaEventElapsedTime(&ms, ws->events[6 * k + j], ws->events[6 * k + j + 1]));
+        pr->k_ms[KSC_KERNEL_B_RESID + j] += ms;
+        pr->k_launches[KSC_KERNEL_B_RESID + j] += 1;
+      }
+  }
+  std::vector<int> fired;
+  for (int b = 0; b < B; ++b)
+    if (se->slot[b].busy && !se->slot[b].fin && hn[b].done != kRunning) fired.push_back(b);
+  // FP64 certificates of the nodes whose in-loop test fired
+  for (int b : fired) {
+    launch_bcert_load(d, b, pr->dev, s);
+    launch_certificate(pr->dev, s, se->slot[b].want_z);
+    launch_bcert_store(d, b, pr->dev, se->slot[b].want_z, s);
+    pr->launches += kLaunchesPerBatchCert;
+    se->certificates += 1;
+  }
+  if (!fired.empty()) {
+    KB_CUDA(cudaGetLastError());
+    KB_CUDA(cudaMemcpyAsync(hc, d.cert, (size_t)B * sizeof(BCert), cudaMemcpyDeviceToHost, s));
+    KB_CUDA(cudaStreamSynchronize(s));
+  }
+  for (int b : fired) {
+    SlotHost& sl = se->slot[b];
+    const BNode& h = hn[b];
+    const BCert& c = hc[b];
+    bool done = false;
+    if (std::isfinite(sl.inc) && c.dual > sl.inc) { sl.pruned = 1; done = true; }
+    else if (c.gap <= sl.tol) done = true;
+    else if (h.done == kDonePrimal) done = true;                       // Sec. 4.3 rule (1): branch
+    else if (h.done == kDoneMaxIter) { sl.status = KSC_NOT_CONVERGED; done = true; }
+    if (done) {
+      sl.fin = true;
+      finished->push_back(b);
+      continue;
+    }
+    // the in-loop test fired on values the certificate does not confirm:
+    // re-anchor at the current iterate, tighten, go on
+    BNode upd = h;
+    if (h.done == kDoneGap) upd.tol_loop = std::max(h.gap * 0.25, 1e-16);
+    if (h.done == kDonePruned) upd.incumbent = sl.inc + 2.0 * std::fabs(h.best_dual - c.dual) + 1e-12 * std::fabs(sl.inc);
+    upd.done = kRunning;
+    upd.best_dual = c.dual > -INFINITY ? std::max(c.dual, -1e300) : -INFINITY;
+    KB_CUDA(cudaMemcpyAsync(d.nodes + b, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaStreamSynchronize(s));
+    hn[b] = upd;
+    anchor(se, b, false);
+    sl.last_anchor = upd.iter;
+    sl.anchors += 1;
+  }
+  // anchors of running nodes whose gap fell (or that ran long without one)
+  for (int b = 0; b < B; ++b) {
+    SlotHost& sl = se->slot[b];
+    const BNode& h = hn[b];
+    if (!sl.busy || sl.fin || h.done != kRunning) continue;
+    const bool by_gap = h.gap <= sl.anchor_gap;
+    const bool by_age = h.iter - sl.last_anchor >= 512 && h.gap > sl.tol;
+    if (by_gap || by_age) {
+      anchor(se, b, false);
+      sl.last_anchor = h.iter;
+      sl.anchors += 1;
+      if (by_gap) sl.anchor_gap = std::max(h.gap * 0.01, sl.tol * 1e-4);
+    }
+  }
+  KB_CUDA(cudaGetLastError());
+  KB_CUDA(cudaStreamSynchronize(s));
+  return KSC_OK;
+}
+
+ksc_status session_fetch(Session* se, int b, ksc_result* r) {
+  SlotHost& sl = se->slot[b];
+  if (!sl.busy || !sl.fin) return api_fail(KSC_ERR_INVALID_ARG, "slot has no finished node");
+  const BNode h = hnodes(se)[b];
+  const BCert c = hcerts(se)[b];
+  const BatchDev& d = se->ws->bd;
+  const int p = d.p;
+  r->primal = c.primal;
+  r->dual_bound = c.dual;
+  r->rel_gap = c.gap;
+  r->iters = h.iter - 1;
+  r->restarts = h.restarts;
+  r->pruned = sl.pruned;
+  r->status = sl.status;
+  if (r->beta) KB_CUDA(cudaMemcpyAsync(r->beta, d.beta_out + (size_t)b * p, (size_t)p * 8, cudaMemcpyDeviceToHost, se->s));
+  if (r->z) KB_CUDA(cudaMemcpyAsync(r->z, d.z_out + (size_t)b * p, (size_t)p * 8, cudaMemcpyDeviceToHost, se->s));
+  // empty the slot: every kernel skips it
+  BNode idle = h;
+  idle.done = kSlotIdle;
+  KB_CUDA(cudaMemcpyAsync(d.nodes + b, &idle, sizeof idle, cudaMemcpyHostToDevice, se->s));
+  KB_CUDA(cudaStreamSynchronize(se->s));
+  hnodes(se)[b] = idle;
+  sl = SlotHost();
+  return KSC_OK;
+}
+
+}  // namespace ksc
+
+// ------------------------------------------------------------------ ksc_solve_batch
 
 extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, int32_t count, ksc_result* results,
                                       void* cuda_stream) {
@@ -440,18 +627,16 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
   cudaGetDevice(&cur_dev);
   if (cur_dev != pr->device) KB_CUDA(cudaSetDevice(pr->device));
   // validate every node first: nothing runs on a bad batch
-  std::vector<Job> batch;
-  std::vector<int> single;
+  std::vector<NodeSetup> setups(count);
+  std::vector<int> batch, single;
   ksc_status first = KSC_OK;
   for (int32_t i = 0; i < count; ++i) {
-    Job j;
-    j.idx = i;
-    if ((st = check_node(pr, &nodes[i], &j.ns)) != KSC_OK) return st;
+    if ((st = check_node(pr, &nodes[i], &setups[i])) != KSC_OK) return st;
     ksc_result* r = &results[i];
     r->iters = 0;
     r->restarts = 0;
     r->pruned = 0;
-    if (j.ns.infeasible) {
+    if (setups[i].infeasible) {
       r->primal = INFINITY;
       r->dual_bound = INFINITY;
       r->rel_gap = 0.0;
@@ -460,15 +645,48 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       if (first == KSC_OK) first = KSC_ERR_INFEASIBLE_NODE;
       continue;
     }
-    if (batch_supported(pr) && std::min<int64_t>(j.ns.kp, pr->p) < kBatchCap) batch.push_back(std::move(j));
+    if (batch_supported(pr) && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
     else single.push_back(i);
   }
+  int64_t iters = 0, anchors = 0, certs = 0;
   for (size_t g0 = 0; g0 < batch.size(); g0 += kBatchMax) {
-    std::vector<Job> grp(std::make_move_iterator(batch.begin() + g0),
-                         std::make_move_iterator(batch.begin() + std::min(batch.size(), g0 + kBatchMax)));
-    if ((st = solve_group(pr, nodes, results, grp, s)) != KSC_OK) return st;
-    for (auto& j : grp)
-      if (first == KSC_OK && results[j.idx].status != KSC_OK) first = results[j.idx].status;
+    const int cnt = (int)std::min<size_t>(kBatchMax, batch.size() - g0);
+    Session se;
+    if ((st = session_open(&se, pr, cnt, true, s)) != KSC_OK) return st;
+    std::vector<const ksc_node*> nv;
+    std::vector<const NodeSetup*> sv;
+    std::vector<int> wz, slots;
+    for (int i = 0; i < cnt; ++i) {
+      const int idx = batch[g0 + i];
+      nv.push_back(&nodes[idx]);
+      sv.push_back(&setups[idx]);
+      wz.push_back(results[idx].z != nullptr);
+    }
+    if ((st = session_admit(&se, nv, sv, wz, &slots)) != KSC_OK) return st;
+    std::vector<int> fin;
+    while (session_running(&se) > 0) {
+      if (!session_advance(&se, &st)) {
+        if (st != KSC_OK) return st;
+        break;
+      }
+      if ((st = session_collect(&se, &fin)) != KSC_OK) return st;
+    }
+    for (int i = 0; i < cnt; ++i) {
+      const int idx = batch[g0 + i];
+      if ((st = session_fetch(&se, slots[i], &results[idx])) != KSC_OK) return st;
+      iters += results[idx].iters;
+      if (first == KSC_OK && results[idx].status != KSC_OK) first = results[idx].status;
+    }
+    anchors += se.anchors;
+    certs += se.certificates;
+    session_close(&se);
+  }
+  if (!batch.empty()) {
+    for (int i = 0; i < 8; ++i) pr->last_stats[i] = 0;
+    pr->last_stats[0] = (int32_t)std::min<int64_t>(iters, INT32_MAX);
+    pr->last_stats[5] = pr->power_iters;
+    pr->last_stats[6] = (int32_t)std::min<int64_t>(certs, INT32_MAX);
+    pr->last_stats[7] = (int32_t)std::min<int64_t>(anchors, INT32_MAX);
   }
   for (int i : single) {
     st = ksc_solve_node(pr, &nodes[i], &results[i], cuda_stream);

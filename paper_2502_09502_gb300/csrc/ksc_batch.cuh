@@ -3,16 +3,26 @@
 // of each step on the tensor cores (k_tcgemm.cu) and one CTA per node for the
 // prox, g and the dual term (k_batch.cu).
 //
+// Precision.  The iterate (beta, u = X beta, G = X^T grad F) is FP64.  The tensor
+// cores multiply BF16 X by a difference from a per-node anchor, split into three
+// BF16 pieces whose sum is the FP32 value exactly:
+//   u^{t+1} = u_ref + X (beta^{t+1} - beta_ref),   G = G_ref + X^T (r - r_ref),
+// where u_ref = X beta_ref and G_ref = X^T r_ref come from the double-float
+// streaming product (accurate to ~1e-13).  The FP32 accumulation error is then
+// relative to the difference, which shrinks as the node converges; an FP32
+// product of the full vectors would shift the fixed point of the iteration by
+// ~ (L / mu) * 1e-7 and stall above a 1e-6 gap.  Nodes re-anchor at their
+// current iterate as their gap falls.
+//
 // Layout (node-major; rows padded to multiples of 8 elements for TMA):
-//   beta   B x 3 x ldp   FP32 iterate slots (cur, prev, new rotate per node)
-//   bpc    P x Bpad x ldp  BF16 pieces of the step dbeta = beta^{t+1} - beta^t
-//                        (A of the product X dbeta)
-//   U      B x 3 x ldn   FP64 u = X beta per slot, advanced as u^{t+1} = u^t + X dbeta:
-//                        the FP32 accumulation error of the product is relative
-//                        to the step, not to u (the residual correction that lets
-//                        an FP32 iteration reach a 1e-6 certified gap)
-//   rpc    P x Bpad x ldn  BF16 pieces of grad F(u_gamma) (A of X^T r)
-//   G      B x ldp       FP32 X^T grad F(u_gamma)
+//   beta      B x 3 x ldp   FP64 iterate slots (cur, prev, new rotate per node)
+//   beta_ref  B x ldp       FP64 anchor iterate
+//   bpc       P x Bpad x ldp  BF16 pieces of fl32(beta^{t+1} - beta_ref)
+//   U         B x 3 x ldn   FP64 u per slot
+//   u_ref     B x ldn       FP64 X beta_ref
+//   r_ref     B x ldn       FP64 grad F(u_ref)
+//   rpc       P x Bpad x ldn  BF16 pieces of fl32(grad F(u_gamma) - r_ref)
+//   G, G_ref  B x ldp       FP64 X^T grad F(u_gamma), X^T r_ref
 #pragma once
 
 #include <cuda_bf16.h>
@@ -25,11 +35,12 @@
 namespace ksc {
 
 constexpr int kBatchPieces = 3;     // BF16 pieces of an FP32 vector (exact sum)
-constexpr int kBatchCap = 1024;     // prox candidates per node in shared memory
+constexpr int kBatchCap = 2048;     // prox candidates per node in shared memory
 constexpr int kBatchMax = 1024;     // nodes per device pass
 constexpr int kBProxBlock = 256;    // threads of the per-node prox CTA
 constexpr int kBThreads = 256;      // residual kernel
 constexpr int kBRows = 8;           // rows per residual thread
+constexpr int kSlotIdle = 5;        // BNode::done of an empty slot (every kernel skips it)
 
 // one node of a batched solve (field names follow NodeDev: the restart/gap step
 // logic is shared)
@@ -53,17 +64,22 @@ struct BCert {
 struct BatchDev {
   int n, p, B, Bpad, loss, P;
   int ldp, ldn;
-  int nft;             // forward-product tiles per node (loss partials)
+  int nft;             // loss partials per node (one per 64 rows of X)
   int nrt;             // residual CTAs per node
   int wsm;             // prox keeps w in shared memory (elements), else wbuf
   const float* yf;     // n
+  const double* y;     // n
   const int8_t* state; // B x ldp
-  float* beta;
+  double* beta;
+  double* beta_ref;
   __nv_bfloat16* bpc;
   double* U;
+  double* u_ref;
+  double* r_ref;
   __nv_bfloat16* rpc;
-  float* G;
-  float* wbuf;         // B x ldp, or NULL
+  double* G;
+  double* G_ref;
+  double* wbuf;        // B x ldp, or NULL
   int* slot_cur;       // B: slot of u^t (read by the forward product)
   int* slot_new;       // B: slot the forward product writes
   double* fpart;       // B x nft x 2: sums of F(u^{t+1}) and of F(u^{t+1}) - F(u^t)
@@ -71,7 +87,7 @@ struct BatchDev {
   BNode* nodes;        // B
   BCert* cert;         // B
   double* beta_out;    // B x p (certified iterate, FP64)
-  double* z_out;       // B x p (relaxed z), or NULL
+  double* z_out;       // B x p (relaxed z)
 };
 
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }
@@ -81,10 +97,20 @@ void batch_prepare(int optin);
 void launch_bresid(const BatchDev& d, cudaStream_t s);
 void launch_bprox(const BatchDev& d, cudaStream_t s);
 void launch_bstep(const BatchDev& d, cudaStream_t s);
-void launch_binit_split(const BatchDev& d, cudaStream_t s);
-void launch_binit_node(const BatchDev& d, cudaStream_t s);
+// admission of the slots in `list` (device int array, count entries): beta slots
+// 0 and 1 and the anchor from the warm start uploaded into slot 1
+void launch_binit_copy(const BatchDev& d, const int* list, int count, cudaStream_t s);
+// after the slots' anchors: u slots, F(u^1), g(beta^1), L^1 and the node state
+void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream_t s);
+// anchor of node b at its current iterate: beta_ref = beta^t (mid-solve only),
+// then (after u_ref = X beta_ref) r_ref = grad F(u_ref) and u slot(s) = u_ref
+void launch_banchor_copy(const BatchDev& d, int b, cudaStream_t s);
+void launch_banchor_resid(const BatchDev& d, int b, int init, cudaStream_t s);
 // FP64 certificate of node b through the single-node workspace d
 void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s);
 void launch_bcert_store(const BatchDev& bd, int b, const Dev& d, int want_z, cudaStream_t s);
+// out = A^T vec with A = X (rows n, vec n -> out p) or A = Xc (vec p -> out n),
+// double-float products (the single-node streaming kernel; uses d's partials)
+void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s);
 
 }  // namespace ksc

@@ -41,7 +41,7 @@ struct ksc_problem {
   int64_t k_launches[kKernelIds] = {};
   double k_ms[kKernelIds] = {};
   int64_t launches = 0;   // every kernel launch issued for this problem
-  int32_t last_stats[6] = {0, 0, 0, 0, 0, 0};
+  int32_t last_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   ksc::BatchWs* batch = nullptr;   // batched-solve workspace (created on first use)
 };
 

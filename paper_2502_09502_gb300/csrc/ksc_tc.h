@@ -16,19 +16,27 @@
 
 namespace ksc {
 
-enum : int { kTcStore = 0, kTcDelta = 1 };
+enum : int { kTcStore = 0, kTcAdd = 1, kTcAnchor = 2 };
 
-// epilogue kTcStore: row m of the product D goes to out + m * ldo (FP32).
-// epilogue kTcDelta (D = X dbeta, the change of the iterate): in FP64,
-//   u_new = u_old + D,  u_old at u64 + m * ldo + slot_in[m] * slot_stride,
-//                       u_new at u64 + m * ldo + slot_out[m] * slot_stride,
-// and per row and per 64 columns j the sums of the loss terms F_j(u_new) (least
-// squares (u - y_j)^2, logistic log(1 + e^{-y_j u})) and of their changes
-// F_j(u_new) - F_j(u_old), evaluated without cancellation, to
-// part[2 * (m * npart + j / 64) + {0, 1}]  (npart >= ceil(N / 64)).
+// Epilogues (row m of the product D, columns j < N):
+//   kTcStore   out[m * ldo + j] = D                                   (FP32)
+//   kTcAdd     out64[m * ldo + j] = base[m * ldb + j] + D             (FP64)
+//   kTcAnchor  u_new = base[m * ldb + j] + D in FP64, written to
+//              u64 + m * ldo + slot_out[m] * slot_stride; with u_old read at
+//              u64 + m * ldo + slot_in[m] * slot_stride, per row and per 64
+//              columns the sums of the loss terms F_j(u_new) (least squares
+//              (u - y_j)^2, logistic log(1 + e^{-y_j u})) and of their changes
+//              F_j(u_new) - F_j(u_old), evaluated without cancellation, go to
+//              part[2 * (m * npart + j / 64) + {0, 1}]  (npart >= ceil(N / 64)).
+// The batched solver multiplies differences from an anchor (beta - beta_ref,
+// r - r_ref) and adds the anchor's exact product here, so the FP32 accumulation
+// error is relative to the difference.
 struct TcEpi {
   float* out;
   int64_t ldo;
+  const double* base;
+  int64_t ldb;
+  double* out64;
   double* u64;
   const int* slot_in;
   const int* slot_out;
@@ -56,7 +64,7 @@ constexpr int kTcBNs[3] = {64, 128, 256};
 // when the shapes or the driver refuse.
 bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t lda, const void* B,
              int N, int64_t ldb, int bn, const char** why);
-// enqueue one product; mode kTcStore or kTcDelta
+// enqueue one product; mode kTcStore, kTcAdd or kTcAnchor
 void tc_launch(const TcPlan& plan, const TcEpi& epi, int mode, cudaStream_t s);
 // device error word of the product kernels (nonzero: a wait gave up); reset by tc_clear_error
 int* tc_error_word();

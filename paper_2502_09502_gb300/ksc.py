@@ -35,6 +35,8 @@ EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ks
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
            "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
+           "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
+           "ksc_server_stats", "ksc_server_destroy",
            "ksc_last_error", "ksc_version"]
 
 
@@ -93,6 +95,12 @@ def _load():
     L.ksc_tc_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                               C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.c_void_p]
+    L.ksc_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)]
+    L.ksc_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(NodeC), C.POINTER(C.c_uint64)]
+    L.ksc_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(ResultC), C.c_int32]
+    L.ksc_server_latency.argtypes = [C.c_void_p, C.c_uint64, dp]
+    L.ksc_server_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]
+    L.ksc_server_destroy.argtypes = [C.c_void_p]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -221,7 +229,7 @@ def ksc_problem_launch_count(h) -> int:
 
 
 SOLVE_STATS = ("iters", "sparse_forward", "prox_fallback", "prox_predicted", "dual_predicted",
-               "lanczos")
+               "lanczos", "batch_certificates", "batch_anchors")
 
 
 def ksc_problem_solve_stats(h):
@@ -338,3 +346,62 @@ class Problem:
         return [Result(betas[i], zs[i], res[i].primal, res[i].dual_bound, res[i].rel_gap,
                        res[i].iters, res[i].restarts, bool(res[i].pruned),
                        STATUS_NAMES[res[i].status]) for i in range(B)]
+
+
+SERVER_STATS = ("completed", "replays", "sessions", "peak_bytes", "waited_for_budget",
+                "admitted_while_running")
+
+
+class Server:
+    """ksc_server_*: continuous batching of node solves over resident problems."""
+
+    def __init__(self, hbm_budget_bytes, max_slots=128):
+        h = C.c_void_p()
+        _check(lib.ksc_server_create(C.c_size_t(int(hbm_budget_bytes)), int(max_slots), C.byref(h)))
+        self.h = h
+        self._p = {}
+
+    def submit(self, problem: "Problem", node: Node) -> int:
+        t = C.c_uint64()
+        _check(lib.ksc_server_submit(self.h, problem.h, C.byref(node.c), C.byref(t)))
+        self._p[t.value] = problem.p
+        return t.value
+
+    def poll(self, ticket, timeout_ms=-1, want_beta=True, want_z=False,
+             allow=(KSC_OK, KSC_NOT_CONVERGED, KSC_ERR_INFEASIBLE_NODE)):
+        """Result of a request, or None when the wait expires."""
+        p = self._p.get(ticket, 0)
+        want_beta = want_beta and p > 0
+        want_z = want_z and p > 0
+        beta = np.zeros(p) if want_beta else None
+        z = np.zeros(p) if want_z else None
+        res = ResultC(_dptr(beta) if want_beta else None, _dptr(z) if want_z else None)
+        st = lib.ksc_server_poll(self.h, C.c_uint64(ticket), C.byref(res), int(timeout_ms))
+        if st == KSC_ERR_TIMEOUT and self._pending(ticket):
+            return None
+        self._p.pop(ticket, None)
+        _check(st, allow)
+        return Result(beta, z, res.primal, res.dual_bound, res.rel_gap, res.iters, res.restarts,
+                      bool(res.pruned), STATUS_NAMES[res.status if st == KSC_OK else st])
+
+    def _pending(self, ticket):
+        # a timed-out poll leaves the ticket queued; a released one is unknown
+        return ticket in self._p
+
+    def latency(self, ticket) -> float:
+        s = C.c_double()
+        _check(lib.ksc_server_latency(self.h, C.c_uint64(ticket), C.byref(s)))
+        return s.value
+
+    def stats(self):
+        arr = (C.c_int64 * len(SERVER_STATS))()
+        _check(lib.ksc_server_stats(self.h, arr, len(SERVER_STATS)))
+        return dict(zip(SERVER_STATS, list(arr)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib.ksc_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -81,3 +81,18 @@ def test_struct_layouts_match_header(ksc):
     assert ksc.NodeC.warm_beta.offset == 56 and ksc.NodeC.flags.offset == 84
     assert C.sizeof(ksc.ResultC) == 56
     assert ksc.ResultC.status.offset == 52
+
+
+def test_server_arguments_are_rejected_before_cuda(ksc):
+    out = C.c_void_p(7)
+    assert ksc.lib.ksc_server_create(C.c_size_t(0), 16, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert out.value is None
+    assert ksc.lib.ksc_server_create(C.c_size_t(1 << 30), 0, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_server_create(C.c_size_t(1 << 30), 2000, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "max_slots" in ksc.ksc_last_error()
+    t = C.c_uint64()
+    assert ksc.lib.ksc_server_submit(None, None, None, C.byref(t)) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_server_poll(None, 1, None, 0) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_server_destroy(None) == ksc.KSC_OK
+    st = (C.c_int64 * 6)()
+    assert ksc.lib.ksc_server_stats(None, st, 6) == ksc.KSC_ERR_INVALID_ARG
