@@ -357,7 +357,9 @@ def run_batched(args):
     kt = {name: K.ksc_problem_kernel_time(prob.h, kid)
           for name, kid in [("residual", K.KSC_KERNEL_B_RESID), ("xt_r", K.KSC_KERNEL_B_GRAD),
                             ("prox", K.KSC_KERNEL_B_PROX), ("x_dbeta", K.KSC_KERNEL_B_FWD),
-                            ("step", K.KSC_KERNEL_B_STEP)]}
+                            ("step", K.KSC_KERNEL_B_STEP), ("certificates", K.KSC_KERNEL_B_CERT),
+                            ("anchors", K.KSC_KERNEL_B_ANCHOR)]}
+    bstats = K.ksc_problem_solve_stats(prob.h)
     K.ksc_problem_profile(prob.h, False)
     value = B * args.steps / (ms / 1e3)
     tot = sum(v[1] for v in kt.values())
@@ -400,6 +402,10 @@ def run_batched(args):
         "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                        "p99": round(float(np.percentile(lat_ms, 99)), 3)},
         "iters_per_bound": float(np.mean(iters)),
+        "lockstep_steps_per_call": kt["xt_r"][0] / max(args.steps, 1),
+        "certificates_per_call": bstats["batch_certificates"],
+        "anchors_per_call": bstats["batch_anchors"],
+        "device_ms_per_call": {k: round(v[1] / max(args.steps, 1), 2) for k, v in kt.items()},
         "plain_single_node": {"value": round(plain, 3), "unit": UNIT, "nodes": len(sub),
                               "ratio": round(value / plain, 2)},
         "clocks": clk, "gpu_launches": int(launches), "kernel_time_share": shares,

@@ -257,6 +257,8 @@ ksc_status ksc_tc_gemm(const void* A, int32_t pieces, int32_t m, int32_t m_pad, 
 #define KSC_KERNEL_B_PROX   5   /* one prox / g / dual-term CTA per node             */
 #define KSC_KERNEL_B_FWD    6   /* tensor-core X beta for every node + loss partials */
 #define KSC_KERNEL_B_STEP   7   /* restart / gap step per node                       */
+#define KSC_KERNEL_B_CERT   8   /* FP64 certificates between replays (per node)       */
+#define KSC_KERNEL_B_ANCHOR 9   /* exact anchor products between replays (per node)   */
 /* Enable (1) or disable (0) CUDA-event timing of each kernel launch of the
  * problem's solves; accumulated totals are read with ksc_problem_kernel_time. */
 ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);

@@ -39,7 +39,7 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* dst, size_t 
   }
 }
 
-__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(__expf(-fabsf(x))); }
+__device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
 
 __device__ __forceinline__ double sigmoid_d(double t) {
   return t >= 0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
         const float t = -y * (float)ug;
         const float tr = -y * (float)__ldg(&Ur[i]);
         const float dt = (float)(-(double)y * du);
-        const float s = 1.0f / (1.0f + __expf(-t));
-        const float sr = 1.0f / (1.0f + __expf(tr));    // 1 - sigma(t_ref)
+        const float s = 1.0f / (1.0f + expf(-t));
+        const float sr = 1.0f / (1.0f + expf(tr));    // 1 - sigma(t_ref)
         dr = -y * (s * sr * (-expm1f(-dt)));
         // binary entropy of q = zeta_i y_i = sigma(t)
         term = s * softplusf(-t) + (1.0f - s) * softplusf(t);
@@ -244,7 +244,8 @@ __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const in
 
 // ------------------------------------------------------------------ anchors
 
-__global__ void __launch_bounds__(256) k_banchor_copy(BatchDev d, int b) {
+__global__ void __launch_bounds__(256) k_banchor_copy(BatchDev d, const int* list) {
+  const int b = list[blockIdx.y];
   const BNode* nd = d.nodes + b;
   const double* src = d.beta + ((size_t)b * 3 + nd->cur) * d.ldp;
   double* dst = d.beta_ref + (size_t)b * d.ldp;
@@ -252,9 +253,16 @@ __global__ void __launch_bounds__(256) k_banchor_copy(BatchDev d, int b) {
 }
 
 // r_ref = grad F(u_ref) in FP64; the u slot(s) of the current iterate take the
-// accurate u_ref
-__global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, int b, int init) {
-  const BNode* nd = d.nodes + b;
+// accurate u_ref.  Mid-solve, the in-loop best values restart: those recorded
+// against the old anchor carry its rounding, and a running minimum (maximum)
+// keeps a value that rounding pushed down (up).
+__global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, const int* list, int init) {
+  const int b = list[blockIdx.y];
+  BNode* nd = d.nodes + b;
+  if (!init && blockIdx.x == 0 && threadIdx.x == 0) {
+    nd->best_primal = INFINITY;
+    nd->best_dual = -INFINITY;
+  }
   const double* ur = d.u_ref + (size_t)b * d.ldn;
   double* rr = d.r_ref + (size_t)b * d.ldn;
   double* U = d.U + (size_t)b * 3 * d.ldn;
@@ -344,12 +352,12 @@ void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream
   k_binit_node<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list);
 }
 
-void launch_banchor_copy(const BatchDev& d, int b, cudaStream_t s) {
-  k_banchor_copy<<<vec_blocks(d.p), 256, 0, s>>>(d, b);
+void launch_banchor_copy(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_banchor_copy<<<dim3(vec_blocks(d.p), count), 256, 0, s>>>(d, list);
 }
 
-void launch_banchor_resid(const BatchDev& d, int b, int init, cudaStream_t s) {
-  k_banchor_resid<<<vec_blocks(d.n), 256, 0, s>>>(d, b, init);
+void launch_banchor_resid(const BatchDev& d, const int* list, int count, int init, cudaStream_t s) {
+  k_banchor_resid<<<dim3(vec_blocks(d.n), count), 256, 0, s>>>(d, list, init);
 }
 
 void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s) {

@@ -828,6 +828,88 @@ void launch_grad_raw(const Dev& d, cudaStream_t s) {
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
 }
 
+// ----------------------------------------------------------- batched exact product
+// D[list[r]][c] = sum_k A[k][c] V[list[r]][k] for the rows r < R of a node list
+// (A row-major K x C with leading dim lda): the exact products of many nodes in
+// one launch.  Each CTA stages a 32 x 128 tile of A once for 16 node vectors
+// (split into float hi + lo) and accumulates in double-float like the streaming
+// product; every output element sums its K terms in the same order, whatever the
+// list.
+constexpr int kDfCols = 128, kDfNodes = 16, kDfK = 32;
+
+template <typename TX>
+__global__ void __launch_bounds__(256) k_dfprod(const TX* __restrict__ A, int64_t lda, int K, int C,
+                                                const double* __restrict__ V, int64_t ldv,
+                                                const int* __restrict__ list, int R, double* __restrict__ D,
+                                                int64_t ldd) {
+  __shared__ __align__(16) float As[kDfK][kDfCols + 4];
+  __shared__ float Vh[kDfNodes][kDfK + 1];
+  __shared__ float Vl[kDfNodes][kDfK + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 4 columns x 2 nodes per thread
+  const int c0 = blockIdx.x * kDfCols, r0 = blockIdx.y * kDfNodes;
+  float hi[2][4], lo[2][4];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { hi[q][j] = 0.f; lo[q][j] = 0.f; }
+  for (int k0 = 0; k0 < K; k0 += kDfK) {
+    for (int e = threadIdx.x; e < kDfK * kDfCols; e += 256) {
+      const int kk = e / kDfCols, cc = e % kDfCols;
+      const int k = k0 + kk, c = c0 + cc;
+      As[kk][cc] = (k < K && c < C) ? xval<float>(A[(size_t)k * lda + c]) : 0.f;
+    }
+    for (int e = threadIdx.x; e < kDfNodes * kDfK; e += 256) {
+      const int rr = e / kDfK, kk = e % kDfK;
+      const int r = r0 + rr, k = k0 + kk;
+      const double v = (r < R && k < K) ? V[(size_t)list[r] * ldv + k] : 0.0;
+      const float h = (float)v;
+      Vh[rr][kk] = h;
+      Vl[rr][kk] = (float)(v - (double)h);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kDfK; ++kk) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[kk][tx * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float vh = Vh[ty * 2 + q][kk], vl = Vl[ty * 2 + q][kk];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) df_add(hi[q][j], lo[q][j], av[j], vh, vl);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int r = r0 + ty * 2 + q;
+    if (r >= R) continue;
+    double* drow = D + (size_t)list[r] * ldd;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx * 4 + j;
+      if (c < C) drow[c] = (double)hi[q][j] + (double)lo[q][j];
+    }
+  }
+}
+
+// D rows = A^T V rows for the listed nodes (A = X: V of length n, D of length p;
+// A = Xc: V of length p, D of length n)
+void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
+                   int64_t ldd, cudaStream_t s) {
+  if (R <= 0) return;
+  const int K = use_xc ? d.p : d.n, C = use_xc ? d.n : d.p;
+  const int64_t lda = use_xc ? d.ldc : d.ldx;
+  const void* A = use_xc ? d.Xc : d.X;
+  dim3 grid((C + kDfCols - 1) / kDfCols, (R + kDfNodes - 1) / kDfNodes);
+  if (d.xdt == kXF64)
+    k_dfprod<double><<<grid, 256, 0, s>>>((const double*)A, lda, K, C, V, ldv, list, R, D, ldd);
+  else if (d.xdt == kXF32)
+    k_dfprod<float><<<grid, 256, 0, s>>>((const float*)A, lda, K, C, V, ldv, list, R, D, ldd);
+  else
+    k_dfprod<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)A, lda, K, C, V, ldv, list, R, D, ldd);
+}
+
 // out = A^T vec for A = X (vec of length n, out of length p) or A = Xc (vec of
 // length p, out of length n): the double-float streaming product
 void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s) {

@@ -170,7 +170,7 @@ __device__ __forceinline__ float loss_term(float u, float y, int loss) {
     return r * r;
   }
   const float t = -y * u;
-  return fmaxf(t, 0.0f) + log1pf(__expf(-fabsf(t)));
+  return fmaxf(t, 0.0f) + log1pf(expf(-fabsf(t)));
 }
 
 // F_i(u + d) - F_i(u) without cancellation: least squares d (2 (u - y) + d);
@@ -182,7 +182,7 @@ __device__ __forceinline__ float loss_change(double u, float d, float y, int los
     return d * (2.0f * r + d);
   }
   if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
-  const float s = 1.0f / (1.0f + __expf(y * (float)u));   // sigma(-y u)
+  const float s = 1.0f / (1.0f + expf(y * (float)u));   // sigma(-y u)
   return log1pf(expm1f(-y * d) * s);
 }
 

@@ -41,6 +41,7 @@ struct BatchWs {
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t graph_prof = nullptr;   // the same steps with events between the kernels
   std::vector<cudaEvent_t> events;        // 6 per step of graph_prof
+  cudaEvent_t ph0 = nullptr, ph1 = nullptr;   // around certificate / anchor phases (profiling)
   const void* Xb = nullptr;   // X with a TMA-compatible row stride (the problem's, or a copy)
   int64_t ldxb = 0;
 };
@@ -50,6 +51,8 @@ void free_batch(BatchWs* ws) {
   if (ws->graph) cudaGraphExecDestroy(ws->graph);
   if (ws->graph_prof) cudaGraphExecDestroy(ws->graph_prof);
   for (auto e : ws->events) cudaEventDestroy(e);
+  if (ws->ph0) cudaEventDestroy(ws->ph0);
+  if (ws->ph1) cudaEventDestroy(ws->ph1);
   for (void* v : ws->allocs) cudaFree(v);
   delete ws;
 }
@@ -326,6 +329,36 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   return KSC_OK;
 }
 
+// device time of a phase of the host loop (profiling only): mark(true) before,
+// mark(false) after; the elapsed time goes to kernel id `kid`
+struct Phase {
+  ksc_problem* pr;
+  BatchWs* ws;
+  cudaStream_t s;
+  int kid;
+  int count = 0;
+  bool on = false;
+  void begin() {
+    if (!pr->profile) return;
+    if (!ws->ph0) {
+      cudaEventCreate(&ws->ph0);
+      cudaEventCreate(&ws->ph1);
+    }
+    cudaEventRecord(ws->ph0, s);
+    on = true;
+  }
+  void end() {
+    if (!on) return;
+    cudaEventRecord(ws->ph1, s);
+    cudaEventSynchronize(ws->ph1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ws->ph0, ws->ph1);
+    pr->k_ms[kid] += ms;
+    pr->k_launches[kid] += count;
+    on = false;
+  }
+};
+
 ksc_status check_tc(cudaStream_t s) {
   int word = 0;
   KB_CUDA(cudaMemcpyAsync(&word, tc_error_word(), sizeof word, cudaMemcpyDeviceToHost, s));
@@ -334,16 +367,36 @@ ksc_status check_tc(cudaStream_t s) {
   return KSC_OK;
 }
 
-// anchor of slot b at its current iterate (init: at the warm start of slot 1)
-void anchor(Session* se, int b, bool init) {
-  const BatchDev& d = se->ws->bd;
+// anchors of the listed slots at their current iterates (init: at the warm starts
+// in slot 1).  Many nodes share one tiled exact product; a few take the streaming
+// product, one node at a time.
+constexpr int kAnchorTiled = 24;
+
+ksc_status anchor(Session* se, const std::vector<int>& list, bool init) {
+  if (list.empty()) return KSC_OK;
+  BatchWs* ws = se->ws;
+  const BatchDev& d = ws->bd;
   const Dev& sd = se->pr->dev;
-  if (!init) launch_banchor_copy(d, b, se->s);
-  launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, se->s);
-  launch_banchor_resid(d, b, init ? 1 : 0, se->s);
-  launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, se->s);
-  se->pr->launches += kLaunchesPerAnchor;
-  se->anchors += 1;
+  cudaStream_t s = se->s;
+  const int cnt = (int)list.size();
+  KB_CUDA(cudaMemcpyAsync(ws->dlist, list.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
+  if (!init) launch_banchor_copy(d, ws->dlist, cnt, s);
+  const bool tiled = cnt >= kAnchorTiled;
+  if (tiled) {
+    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, s);
+  } else {
+    for (int b : list) launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, s);
+  }
+  launch_banchor_resid(d, ws->dlist, cnt, init ? 1 : 0, s);
+  if (tiled) {
+    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, s);
+  } else {
+    for (int b : list) launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, s);
+  }
+  se->pr->launches += tiled ? kLaunchesPerAnchor : 2 + 2 * cnt;
+  se->anchors += cnt;
+  KB_CUDA(cudaStreamSynchronize(s));   // the list buffer is reused by the next anchor
+  return KSC_OK;
 }
 
 }  // namespace
@@ -472,7 +525,7 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
     sl.want_z = want_z[i];
     sl.tol = nd->rel_gap_tol;
     sl.inc = nd->incumbent;
-    sl.anchor_gap = 100.0 * nd->rel_gap_tol;
+    sl.anchor_gap = std::max(1e-3, 100.0 * nd->rel_gap_tol);
     // pageable sources: each copy completes before the host buffers are reused
     KB_CUDA(cudaMemcpyAsync((void*)(d.state + (size_t)b * ldp), hs.data(), ldp, cudaMemcpyHostToDevice, s));
     KB_CUDA(cudaMemcpyAsync(d.beta + ((size_t)b * 3 + 1) * ldp, hb.data(), ldp * 8, cudaMemcpyHostToDevice, s));
@@ -482,7 +535,9 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
   KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
   launch_binit_copy(d, ws->dlist, cnt, s);
   pr->launches += 1;
-  for (int b : *slots) anchor(se, b, true);
+  ksc_status st;
+  if ((st = anchor(se, *slots, true)) != KSC_OK) return st;
+  KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
   launch_binit_node(d, ws->dlist, cnt, s);
   pr->launches += 1;
   KB_CUDA(cudaGetLastError());
@@ -527,6 +582,9 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
   for (int b = 0; b < B; ++b)
     if (se->slot[b].busy && !se->slot[b].fin && hn[b].done != kRunning) fired.push_back(b);
   // FP64 certificates of the nodes whose in-loop test fired
+  Phase cert_phase{pr, ws, s, KSC_KERNEL_B_CERT};
+  cert_phase.count = (int)fired.size();
+  if (!fired.empty()) cert_phase.begin();
   for (int b : fired) {
     launch_bcert_load(d, b, pr->dev, s);
     launch_certificate(pr->dev, s, se->slot[b].want_z);
@@ -536,9 +594,13 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
   }
   if (!fired.empty()) {
     KB_CUDA(cudaGetLastError());
+    cert_phase.end();
     KB_CUDA(cudaMemcpyAsync(hc, d.cert, (size_t)B * sizeof(BCert), cudaMemcpyDeviceToHost, s));
     KB_CUDA(cudaStreamSynchronize(s));
   }
+  Phase anchor_phase{pr, ws, s, KSC_KERNEL_B_ANCHOR};
+  anchor_phase.begin();
+  const int64_t anchors0 = se->anchors;
   for (int b : fired) {
     SlotHost& sl = se->slot[b];
     const BNode& h = hn[b];
@@ -553,34 +615,40 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
       finished->push_back(b);
       continue;
     }
-    // the in-loop test fired on values the certificate does not confirm:
-    // re-anchor at the current iterate, tighten, go on
+    // the in-loop test fired on values the certificate does not confirm: go on
+    // from the certificate's exact values (not from in-loop bests that rounding
+    // may have moved past them), with a tighter in-loop tolerance
     BNode upd = h;
-    if (h.done == kDoneGap) upd.tol_loop = std::max(h.gap * 0.25, 1e-16);
+    // halve the in-loop tolerance (bounded below: an in-loop gap near the rounding
+    // floor is noise, and chasing it would keep the node from ever stopping)
+    if (h.done == kDoneGap) upd.tol_loop = std::max(0.5 * std::min(h.tol_loop, std::max(h.gap, 0.0)), 1e-3 * sl.tol);
     if (h.done == kDonePruned) upd.incumbent = sl.inc + 2.0 * std::fabs(h.best_dual - c.dual) + 1e-12 * std::fabs(sl.inc);
     upd.done = kRunning;
     upd.best_dual = c.dual > -INFINITY ? std::max(c.dual, -1e300) : -INFINITY;
+    if (std::isfinite(c.primal)) upd.best_primal = c.primal;
+    upd.gap = (upd.best_primal - upd.best_dual) / std::max(std::fabs(upd.best_primal), 1e-300);
     KB_CUDA(cudaMemcpyAsync(d.nodes + b, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
     KB_CUDA(cudaStreamSynchronize(s));
     hn[b] = upd;
-    anchor(se, b, false);
-    sl.last_anchor = upd.iter;
-    sl.anchors += 1;
   }
   // anchors of running nodes whose gap fell (or that ran long without one)
+  std::vector<int> alist;
   for (int b = 0; b < B; ++b) {
     SlotHost& sl = se->slot[b];
     const BNode& h = hn[b];
     if (!sl.busy || sl.fin || h.done != kRunning) continue;
-    const bool by_gap = h.gap <= sl.anchor_gap;
-    const bool by_age = h.iter - sl.last_anchor >= 512 && h.gap > sl.tol;
+    const bool by_gap = h.gap > 0.0 && h.gap <= sl.anchor_gap;
+    const bool by_age = h.iter - sl.last_anchor >= 256 && h.gap > sl.tol;
     if (by_gap || by_age) {
-      anchor(se, b, false);
+      alist.push_back(b);
       sl.last_anchor = h.iter;
       sl.anchors += 1;
-      if (by_gap) sl.anchor_gap = std::max(h.gap * 0.01, sl.tol * 1e-4);
+      if (by_gap) sl.anchor_gap = std::max(h.gap * 0.03, sl.tol * 1e-3);
     }
   }
+  if ((st = anchor(se, alist, false)) != KSC_OK) return st;
+  anchor_phase.count = (int)(se->anchors - anchors0);
+  anchor_phase.end();
   KB_CUDA(cudaGetLastError());
   KB_CUDA(cudaStreamSynchronize(s));
   return KSC_OK;

@@ -102,15 +102,20 @@ void launch_bstep(const BatchDev& d, cudaStream_t s);
 void launch_binit_copy(const BatchDev& d, const int* list, int count, cudaStream_t s);
 // after the slots' anchors: u slots, F(u^1), g(beta^1), L^1 and the node state
 void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream_t s);
-// anchor of node b at its current iterate: beta_ref = beta^t (mid-solve only),
-// then (after u_ref = X beta_ref) r_ref = grad F(u_ref) and u slot(s) = u_ref
-void launch_banchor_copy(const BatchDev& d, int b, cudaStream_t s);
-void launch_banchor_resid(const BatchDev& d, int b, int init, cudaStream_t s);
+// anchors of the listed nodes (device list, count entries) at their current
+// iterate: beta_ref = beta^t (mid-solve only), then (after u_ref = X beta_ref)
+// r_ref = grad F(u_ref), u slot(s) = u_ref and, mid-solve, fresh in-loop bests
+void launch_banchor_copy(const BatchDev& d, const int* list, int count, cudaStream_t s);
+void launch_banchor_resid(const BatchDev& d, const int* list, int count, int init, cudaStream_t s);
 // FP64 certificate of node b through the single-node workspace d
 void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s);
 void launch_bcert_store(const BatchDev& bd, int b, const Dev& d, int want_z, cudaStream_t s);
 // out = A^T vec with A = X (rows n, vec n -> out p) or A = Xc (vec p -> out n),
 // double-float products (the single-node streaming kernel; uses d's partials)
 void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s);
+// D[list[r]] = A^T V[list[r]] for r < R: the same product for many nodes in one
+// launch (rows of V and D with strides ldv, ldd)
+void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
+                   int64_t ldd, cudaStream_t s);
 
 }  // namespace ksc

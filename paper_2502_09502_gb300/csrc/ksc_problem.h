@@ -18,7 +18,7 @@ void free_batch(BatchWs* ws);
 }  // namespace ksc
 
 static constexpr int kStepsPerGraph = 16;
-static constexpr int kKernelIds = 8;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
+static constexpr int kKernelIds = 10;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
 
 struct ksc_problem {
   int device = 0;
