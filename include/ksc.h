@@ -281,6 +281,16 @@ ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t
  * beyond 8 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
 ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n);
 
+/* In-loop state of node `index` of the last batched ksc_solve_batch call on this
+ * problem, for diagnosing convergence (the values the gap and restart tests saw
+ * when the node stopped), written to state[0..n):
+ *   0  in-loop tolerance   1  best primal    2  best dual       3  in-loop gap
+ *   4  last primal         5  last dual      6  g of the iterate 7 restarts
+ *   8  FISTA steps         9  certificate gap
+ * KSC_ERR_INVALID_ARG when index is outside the last batch (or it was not
+ * batched). */
+ksc_status ksc_problem_batch_node_state(const ksc_problem* problem, int32_t index, double* state, int32_t n);
+
 /* Number of kernel launches the library has issued for this problem (setup,
  * every kernel node of every replayed step graph, certificates). */
 ksc_status ksc_problem_launch_count(const ksc_problem* problem, int64_t* launches);

@@ -69,6 +69,9 @@ constexpr int kBatchStepsPerGraph = 16;
 constexpr int kLaunchesPerBatchStep = 5;   // residual, X^T r, prox, X beta, step
 constexpr int kLaunchesPerBatchCert = 7;   // load, 5 certificate kernels, store
 constexpr int kLaunchesPerAnchor = 4;      // copy, X beta_ref, grad F, X^T r_ref
+// relative accuracy of the in-loop gap: the FP32 loss and entropy terms (summed in
+// FP64) carry ~1e-8; a tighter in-loop tolerance could never be met
+constexpr double kInLoopFloor = 3e-8;
 
 #define KB_CUDA(call)                                                                        \
   do {                                                                                       \
@@ -578,9 +581,18 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
         pr->k_launches[KSC_KERNEL_B_RESID + j] += 1;
       }
   }
+  // nodes whose in-loop test fired, and nodes that have sat near their target for
+  // a while without firing (their in-loop values can be off by the FP32 rounding
+  // of the loss terms, ~1e-8 relative): certify both
   std::vector<int> fired;
-  for (int b = 0; b < B; ++b)
-    if (se->slot[b].busy && !se->slot[b].fin && hn[b].done != kRunning) fired.push_back(b);
+  for (int b = 0; b < B; ++b) {
+    const SlotHost& sl = se->slot[b];
+    if (!sl.busy || sl.fin) continue;
+    const BNode& h = hn[b];
+    const bool stopped = h.done != kRunning;
+    const bool overdue = h.iter - sl.last_cert >= 128 && h.gap <= 10.0 * sl.tol;
+    if (stopped || overdue) fired.push_back(b);
+  }
   // FP64 certificates of the nodes whose in-loop test fired
   Phase cert_phase{pr, ws, s, KSC_KERNEL_B_CERT};
   cert_phase.count = (int)fired.size();
@@ -605,6 +617,7 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     SlotHost& sl = se->slot[b];
     const BNode& h = hn[b];
     const BCert& c = hc[b];
+    sl.last_cert = h.iter;
     bool done = false;
     if (std::isfinite(sl.inc) && c.dual > sl.inc) { sl.pruned = 1; done = true; }
     else if (c.gap <= sl.tol) done = true;
@@ -613,6 +626,13 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     if (done) {
       sl.fin = true;
       finished->push_back(b);
+      if (h.done == kRunning) {   // certified while running: stop it on the device
+        BNode fz = h;
+        fz.done = kDoneGap;
+        KB_CUDA(cudaMemcpyAsync(d.nodes + b, &fz, sizeof fz, cudaMemcpyHostToDevice, s));
+        KB_CUDA(cudaStreamSynchronize(s));
+        hn[b] = fz;
+      }
       continue;
     }
     // the in-loop test fired on values the certificate does not confirm: go on
@@ -621,7 +641,8 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     BNode upd = h;
     // halve the in-loop tolerance (bounded below: an in-loop gap near the rounding
     // floor is noise, and chasing it would keep the node from ever stopping)
-    if (h.done == kDoneGap) upd.tol_loop = std::max(0.5 * std::min(h.tol_loop, std::max(h.gap, 0.0)), 1e-3 * sl.tol);
+    if (h.done == kDoneGap)
+      upd.tol_loop = std::max(0.5 * std::min(h.tol_loop, std::max(h.gap, 0.0)), std::max(1e-3 * sl.tol, kInLoopFloor));
     if (h.done == kDonePruned) upd.incumbent = sl.inc + 2.0 * std::fabs(h.best_dual - c.dual) + 1e-12 * std::fabs(sl.inc);
     upd.done = kRunning;
     upd.best_dual = c.dual > -INFINITY ? std::max(c.dual, -1e300) : -INFINITY;
@@ -739,8 +760,21 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       }
       if ((st = session_collect(&se, &fin)) != KSC_OK) return st;
     }
+    if (g0 == 0) pr->batch_state.assign((size_t)count * 10, NAN);
     for (int i = 0; i < cnt; ++i) {
       const int idx = batch[g0 + i];
+      const BNode& h = hnodes(&se)[slots[i]];
+      double* bs = &pr->batch_state[(size_t)idx * 10];
+      bs[0] = h.tol_loop;
+      bs[1] = h.best_primal;
+      bs[2] = h.best_dual;
+      bs[3] = h.gap;
+      bs[4] = h.last_primal;
+      bs[5] = h.last_dual;
+      bs[6] = h.g_cur;
+      bs[7] = h.restarts;
+      bs[8] = h.iter - 1;
+      bs[9] = hcerts(&se)[slots[i]].gap;
       if ((st = session_fetch(&se, slots[i], &results[idx])) != KSC_OK) return st;
       iters += results[idx].iters;
       if (first == KSC_OK && results[idx].status != KSC_OK) first = results[idx].status;
@@ -764,5 +798,13 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
   if (first != KSC_OK && first != KSC_ERR_INFEASIBLE_NODE)
     return api_fail(first, "a node reached max_iter before the gap target");
   if (first == KSC_ERR_INFEASIBLE_NODE) return api_fail(first, "a node is infeasible: |S1| > k or S0 and S1 intersect");
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_problem_batch_node_state(const ksc_problem* pr, int32_t index, double* state, int32_t n) {
+  if (!pr || (n > 0 && !state) || n < 0) return api_fail(KSC_ERR_INVALID_ARG, "bad arguments");
+  if (index < 0 || (size_t)index * 10 >= pr->batch_state.size() || std::isnan(pr->batch_state[(size_t)index * 10]))
+    return api_fail(KSC_ERR_INVALID_ARG, "index is not a node of the last batched call");
+  for (int32_t i = 0; i < n; ++i) state[i] = i < 10 ? pr->batch_state[(size_t)index * 10 + i] : 0.0;
   return KSC_OK;
 }

@@ -43,6 +43,7 @@ struct ksc_problem {
   int64_t launches = 0;   // every kernel launch issued for this problem
   int32_t last_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   ksc::BatchWs* batch = nullptr;   // batched-solve workspace (created on first use)
+  std::vector<double> batch_state; // 10 in-loop values per node of the last batched call
 };
 
 namespace ksc {

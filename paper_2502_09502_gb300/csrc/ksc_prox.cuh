@@ -329,6 +329,15 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
       }
       if (found) {
         cand_sorted = true;
+        // the next call's candidate count: the top set, twice the pooled tail found
+        // here, and a margin (the pooled block moves little between FISTA steps)
+        int lo2 = q, hi2 = out.qused;
+        while (lo2 < hi2) {
+          const int mid = (lo2 + hi2) >> 1;
+          if (sm.cand[mid] <= theta) hi2 = mid; else lo2 = mid + 1;
+        }
+        const int next = q + 2 * (lo2 - q) + 32;
+        out.qused = next < out.qused ? next : out.qused;
       } else {
         out.fallback = 1;
         theta = root_fullpass<T, BLOCK>(m, keyval, thr_k, need_k, eq_k,

@@ -23,6 +23,7 @@ struct SlotHost {
   double tol = 0.0, inc = 0.0;
   double anchor_gap = 0.0; // re-anchor when the in-loop gap falls below this
   int last_anchor = 0;     // iteration of the last anchor
+  int last_cert = 0;       // iteration of the last certificate
   int anchors = 0;
   int pruned = 0;
   ksc_status status = KSC_OK;

@@ -37,7 +37,7 @@ EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ks
            "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
            "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
-           "ksc_server_stats", "ksc_server_destroy",
+           "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state",
            "ksc_last_error", "ksc_version"]
 
 
@@ -102,6 +102,7 @@ def _load():
     L.ksc_server_latency.argtypes = [C.c_void_p, C.c_uint64, dp]
     L.ksc_server_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]
     L.ksc_server_destroy.argtypes = [C.c_void_p]
+    L.ksc_problem_batch_node_state.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int32]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -221,6 +222,16 @@ def ksc_problem_kernel_time(h, kernel, reset=False):
     ms = C.c_double()
     _check(lib.ksc_problem_kernel_time(h, int(kernel), C.byref(n), C.byref(ms), int(bool(reset))))
     return n.value, ms.value
+
+
+BATCH_NODE_STATE = ("tol_loop", "best_primal", "best_dual", "gap", "last_primal", "last_dual", "g",
+                    "restarts", "iters", "cert_gap")
+
+
+def ksc_problem_batch_node_state(h, index):
+    buf = (C.c_double * len(BATCH_NODE_STATE))()
+    _check(lib.ksc_problem_batch_node_state(h, int(index), buf, len(BATCH_NODE_STATE)))
+    return dict(zip(BATCH_NODE_STATE, list(buf)))
 
 
 def ksc_problem_launch_count(h) -> int:
