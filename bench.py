@@ -405,6 +405,7 @@ def run_batched(args):
         "lockstep_steps_per_call": kt["xt_r"][0] / max(args.steps, 1),
         "certificates_per_call": bstats["batch_certificates"],
         "anchors_per_call": bstats["batch_anchors"],
+        "prox_fallbacks_per_call": bstats["prox_fallback"],
         "device_ms_per_call": {k: round(v[1] / max(args.steps, 1), 2) for k, v in kt.items()},
         "plain_single_node": {"value": round(plain, 3), "unit": UNIT, "nodes": len(sub),
                               "ratio": round(value / plain, 2)},

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   io.nnz_cap = 0;
   io.top_out = nullptr;
   io.qhint = nd->qhint;
+  io.theta0 = nd->theta;
   const SegOut o = prox_segment<double, kBProxBlock>(io, sm);
   __syncthreads();
   // BF16 pieces of fl32(beta^{t+1} - beta_ref)
@@ -152,7 +153,12 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   __nv_bfloat16* prow = d.bpc + (size_t)b * d.ldp;
   const double* bn = io.beta;
   const double* br = d.beta_ref + (size_t)b * d.ldp;
-  for (int j = threadIdx.x; j < p; j += kBProxBlock) split_store((float)(bn[j] - br[j]), prow + j, pstride, d.P);
+  for (int j = threadIdx.x; j < p; j += kBProxBlock) {
+    const double x = bn[j], r = br[j];
+    // both zero (most coordinates of a sparse iterate): no FP64 arithmetic
+    const float v = ((__double_as_longlong(x) | __double_as_longlong(r)) << 1) == 0 ? 0.0f : (float)(x - r);
+    split_store(v, prow + j, pstride, d.P);
+  }
   if (threadIdx.x == 0) {
     double nc = 0.0;
     for (int t = 0; t < d.nrt; ++t) nc += d.ncpart[(size_t)b * d.nrt + t];

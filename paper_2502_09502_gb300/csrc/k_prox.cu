@@ -137,6 +137,7 @@ k_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, i
   io.nnz_cap = 0;
   io.top_out = top;
   io.qhint = 0;
+  io.theta0 = -1.0;
   prox_segment<double, kProxBlock>(io, sm);
 }
 

@@ -749,7 +749,7 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
     if (batch_supported(pr) && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
     else single.push_back(i);
   }
-  int64_t iters = 0, anchors = 0, certs = 0;
+  int64_t iters = 0, anchors = 0, certs = 0, fallbacks = 0;
   for (size_t g0 = 0; g0 < batch.size(); g0 += kBatchMax) {
     const int cnt = (int)std::min<size_t>(kBatchMax, batch.size() - g0);
     Session se;
@@ -787,6 +787,7 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       bs[7] = h.restarts;
       bs[8] = h.iter - 1;
       bs[9] = hcerts(&se)[slots[i]].gap;
+      fallbacks += h.fallback;
       if ((st = session_fetch(&se, slots[i], &results[idx])) != KSC_OK) return st;
       iters += results[idx].iters;
       if (first == KSC_OK && results[idx].status != KSC_OK) first = results[idx].status;
@@ -798,6 +799,7 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
   if (!batch.empty()) {
     for (int i = 0; i < 8; ++i) pr->last_stats[i] = 0;
     pr->last_stats[0] = (int32_t)std::min<int64_t>(iters, INT32_MAX);
+    pr->last_stats[2] = (int32_t)std::min<int64_t>(fallbacks, INT32_MAX);
     pr->last_stats[5] = pr->power_iters;
     pr->last_stats[6] = (int32_t)std::min<int64_t>(certs, INT32_MAX);
     pr->last_stats[7] = (int32_t)std::min<int64_t>(anchors, INT32_MAX);

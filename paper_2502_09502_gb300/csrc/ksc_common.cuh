@@ -210,12 +210,51 @@ __device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist,
     gt += cab;
     q_rem -= cab;
     hi = lo;
+    if (hi > DIG && eq <= 32) {
+      // at most 32 keys share the prefix and two or more passes remain: gather
+      // them (hist is free until the next pass) and rank them directly.  The
+      // q_rem-th largest key t of the bin has #{> t} < q_rem <= #{>= t}.
+      U* keys = reinterpret_cast<U*>(hist + 4);   // 32 keys, then the result at keys[32]
+      if (threadIdx.x == 0) hist[0] = 0u;
+      __syncthreads();
+      const U mask = ~(U)0 << hi;
+      for (int i = threadIdx.x; i < m; i += BLOCK) {
+        const U k = load(i);
+        if ((k & mask) == prefix) {
+          const unsigned pos = atomicAdd(&hist[0], 1u);
+          if (pos < 32u) keys[pos] = k;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < (unsigned)eq) {
+        const U kt = keys[threadIdx.x];
+        int ngt = 0, neq = 0;
+        for (int s = 0; s < eq; ++s) {
+          const U ks = keys[s];
+          ngt += ks > kt;
+          neq += ks == kt;
+        }
+        if (ngt < q_rem && q_rem <= ngt + neq) {   // equal keys write equal values
+          keys[32] = kt;
+          hist[1] = (unsigned)ngt;
+          hist[2] = (unsigned)neq;
+        }
+      }
+      __syncthreads();
+      prefix = keys[32];
+      gt += (int)hist[1];
+      eq = (int)hist[2];
+      __syncthreads();
+      break;
+    }
   }
   return SelectResult<U>{prefix, gt, eq};
 }
 
 // ---------------------------------------------------------- bitonic sort
-// In-place descending sort of N (power of two) values in shared memory.
+// In-place descending sort of N (power of two) values in shared memory.  Sorting
+// non-negative doubles as their 64-bit patterns gives the same order with integer
+// compares (sort_desc_nonneg), which matters where FP64 issue is slow.
 template <typename T, int BLOCK>
 __device__ void block_bitonic_sort_desc(T* s, int N) {
   for (int size = 2; size <= N; size <<= 1) {
@@ -231,6 +270,15 @@ __device__ void block_bitonic_sort_desc(T* s, int N) {
     }
   }
 }
+
+// descending sort of N non-negative doubles (padding: +0.0)
+template <int BLOCK>
+__device__ __forceinline__ void sort_desc_nonneg(double* s, int N) {
+  block_bitonic_sort_desc<unsigned long long, BLOCK>(reinterpret_cast<unsigned long long*>(s), N);
+}
+
+// the bit pattern of a non-negative double: ordered like the value
+__device__ __forceinline__ unsigned long long nnbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
 // ---------------------------------------------------------- Huber
 

@@ -102,18 +102,23 @@ struct PhiEval {
 
 __device__ __forceinline__ PhiEval phi_sorted(double th, const double* cand, const double* pref,
                                               int q, int Q, double rho, double M) {
-  // t0: first t in [0,q) with top_break(cand[t]) < th (top_break non-increasing in t)
+  // top member t is active iff a_t < h(theta) = theta + min(rho theta, M) (h is the
+  // inverse of top_break); all values are non-negative, so the searches compare bits
+  const double h = th + fmin(rho * th, M);
+  const unsigned long long hb = nnbits(h), tb = nnbits(th);
+  const unsigned long long* cb = reinterpret_cast<const unsigned long long*>(cand);
+  // t0: first t in [0,q) with cand[t] < h (cand descending)
   int lo = 0, hi = q;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
-    if (top_break(cand[mid], rho, M) < th) hi = mid; else lo = mid + 1;
+    if (cb[mid] < hb) hi = mid; else lo = mid + 1;
   }
   const int t0 = lo;
   // j0: first j in [q,Q) with cand[j] <= th
   lo = q; hi = Q;
   while (lo < hi) {
     int mid = (lo + hi) >> 1;
-    if (cand[mid] <= th) hi = mid; else lo = mid + 1;
+    if (cb[mid] <= tb) hi = mid; else lo = mid + 1;
   }
   const int j0 = lo;
   PhiEval e;
@@ -121,7 +126,7 @@ __device__ __forceinline__ PhiEval phi_sorted(double th, const double* cand, con
   e.SA = pref[q] - pref[t0];
   e.nB = j0 - q;
   e.SB = pref[j0] - pref[q];
-  e.phi = (double)e.nA * (th + fmin(rho * th, M)) - e.SA - (e.SB - (double)e.nB * th);
+  e.phi = (double)e.nA * h - e.SA - (e.SB - (double)e.nB * th);
   return e;
 }
 
@@ -133,24 +138,50 @@ __device__ __forceinline__ double solve_piece(int nA, double SA, int nB, double 
 }
 
 // Bracket the root on the sorted candidates.  Returns false if the root lies
-// below `floorv` (more candidates needed).  All threads call it.
+// below `floorv` (more candidates needed).  All threads call it.  The top
+// breakpoints, M/rho and the floor are evaluated one per thread; the tail
+// breakpoints cand[q..Q) (descending, all >= floorv) have Phi(cand[j])
+// non-increasing in j, so the first j with Phi <= 0 is found by a BLOCK-ary
+// search (two rounds for Q <= BLOCK^2) instead of evaluating every one.
 template <int BLOCK>
 __device__ bool root_from_sorted(const double* cand, const double* pref, int q, int Q, double floorv,
-                                 double rho, double M, double* red, double* theta_out) {
+                                 double rho, double M, double* red, int* sh, double* theta_out) {
   const double thM = M / rho;
-  // candidate breakpoints: idx in [0, Q) (top: top_break, tail: value), Q: floor, Q+1: M/rho
   double lo = -1.0, hi = INFINITY;
-  for (int e = threadIdx.x; e < Q + 2; e += BLOCK) {
+  for (int e = threadIdx.x; e < q + 2; e += BLOCK) {
     double th;
     if (e < q) th = top_break(cand[e], rho, M);
-    else if (e < Q) th = cand[e];
-    else if (e == Q) th = floorv;
+    else if (e == q) th = floorv;
     else th = thM;
     if (th < floorv) continue;
     PhiEval v = phi_sorted(th, cand, pref, q, Q, rho, M);
     if (v.phi <= 0.0) lo = fmax(lo, th);
     if (v.phi >= 0.0) hi = fmin(hi, th);
   }
+  // J: first j in [q, Q) with Phi(cand[j]) <= 0, or Q.  Invariant: J in [a, b],
+  // Phi(cand[j]) > 0 for j < a.
+  int a = q, b = Q;
+  while (a < b) {
+    const int len = b - a;
+    const int step = (len + BLOCK - 1) / BLOCK;
+    const int j = a + (int)threadIdx.x * step;
+    int first = b;
+    if (j < b && phi_sorted(cand[j], cand, pref, q, Q, rho, M).phi <= 0.0) first = j;
+    first = block_min<int, BLOCK>(first, sh, b);
+    if (first < b) {
+      const int na = first - step + 1;
+      a = na > a ? na : a;
+      b = first;
+    } else {
+      a = a + ((len - 1) / step) * step + 1;
+    }
+  }
+  const int J = a;
+  if (J < Q) {
+    lo = fmax(lo, cand[J]);
+    if (phi_sorted(cand[J], cand, pref, q, Q, rho, M).phi >= 0.0) hi = fmin(hi, cand[J]);
+  }
+  if (J > q) hi = fmin(hi, cand[J - 1]);
   lo = block_max<double, BLOCK>(lo, red, -1.0);
   hi = block_min<double, BLOCK>(hi, red, INFINITY);
   if (lo < floorv) return false;  // Phi(floor) > 0: the pooled block extends below the candidates
@@ -188,7 +219,8 @@ struct SegIO {
   T* nnz_val;
   int nnz_cap;               // 0: do not compact
   int* top_out;              // optional: the top-k' indices in sorted order
-  int qhint;
+  int qhint;                 // candidates to start from; above the capacity: full pass
+  double theta0;             // previous theta (warm start of the full pass), or <= 0
 };
 
 struct SegOut {
@@ -196,46 +228,119 @@ struct SegOut {
   int nnz, qused, fallback;
 };
 
-// Full-pass bracketed Newton on Phi (for pooled blocks wider than the
-// candidate capacity).  T members: keys > thr_k plus need_k of the keys equal
-// to thr_k; tail: the rest.  hi0 has Phi(hi0) > 0.
-template <typename T, int BLOCK, typename KeyVal>
-__device__ double root_fullpass(int m, KeyVal keyval, double thr_k, int need_k, int eq_k,
-                                double hi0, double rho, double M, double* red) {
-  double lo = 0.0, hi = hi0, th = hi0;
-  for (int it = 0; it < 200; ++it) {
-    double nA = 0, SA = 0, nB = 0, SB = 0;
+// Full-pass root of Phi, for pooled blocks wider than the candidate capacity.
+// T members: keys > thr_k plus need_k of the keys equal to thr_k; tail: the rest.
+// Each pass evaluates Phi at theta from all m keys (integer compares on the key
+// bits; FP64 adds only for the active keys) together with the nearest keys on
+// either side of theta (tail) and of h(theta) (top): these bound the linear piece
+// of Phi through theta.  The Newton point c of that piece is Phi's root when no
+// breakpoint separates c from theta, which ends the iteration (usually one or two
+// passes from the previous step's theta); otherwise c, or the bisection point
+// when c leaves the bracket, is the next theta.  Phi(0) <= 0 <= Phi(hi0).
+// scratch: >= (BLOCK/32 + 1) * 8 64-bit words of shared memory.  *nb_out: the
+// active tail count at the root.
+template <int BLOCK, typename KeyBits>
+__device__ double root_fullpass(int m, KeyBits keybits, double thr_k, int need_k, int eq_k, double hi0,
+                                double th0, double rho, double M, unsigned long long* scratch, int* nb_out) {
+  using ULL = unsigned long long;
+  constexpr int NW = BLOCK / 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const ULL thr_b = nnbits(thr_k);
+  double lo = 0.0, hi = hi0;
+  double th = (th0 > lo && th0 < hi) ? th0 : hi0;
+  for (int it = 0; it < 100; ++it) {
+    const double h = th + fmin(rho * th, M);
+    const ULL tb = nnbits(th), hb = nnbits(h);
+    long long nA = 0, nB = 0;
+    double SA = 0.0, SB = 0.0;
+    // tail: max key <= theta, min key > theta; top: max key < h, min key >= h
+    ULL tl = 0ull, tg = ~0ull, al = 0ull, ag = ~0ull;
     for (int i = threadIdx.x; i < m; i += BLOCK) {
-      const double a = keyval(i);
-      if (a > thr_k) {
-        if (top_break(a, rho, M) < th) { nA += 1; SA += a; }
-      } else if (a == thr_k) {
-        // need_k copies belong to the top set, eq_k - need_k to the tail
-      } else if (a > th) { nB += 1; SB += a; }
+      const ULL kb = keybits(i);
+      if (kb > thr_b) {
+        if (kb < hb) { ++nA; SA += __longlong_as_double((long long)kb); al = kb > al ? kb : al; }
+        else ag = kb < ag ? kb : ag;
+      } else if (kb < thr_b) {
+        if (kb > tb) { ++nB; SB += __longlong_as_double((long long)kb); tg = kb < tg ? kb : tg; }
+        else tl = kb > tl ? kb : tl;
+      }
     }
-    nA = block_sum<double, BLOCK>(nA, red);
-    SA = block_sum<double, BLOCK>(SA, red);
-    nB = block_sum<double, BLOCK>(nB, red);
-    SB = block_sum<double, BLOCK>(SB, red);
-    if (top_break(thr_k, rho, M) < th) { nA += need_k; SA += need_k * thr_k; }
-    if (thr_k > th) { nB += (eq_k - need_k); SB += (eq_k - need_k) * thr_k; }
-    const double phi = nA * (th + fmin(rho * th, M)) - SA - (SB - nB * th);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nA += __shfl_xor_sync(0xffffffffu, nA, o);
+      nB += __shfl_xor_sync(0xffffffffu, nB, o);
+      SA += __shfl_xor_sync(0xffffffffu, SA, o);
+      SB += __shfl_xor_sync(0xffffffffu, SB, o);
+      ULL v;
+      v = __shfl_xor_sync(0xffffffffu, tl, o); tl = v > tl ? v : tl;
+      v = __shfl_xor_sync(0xffffffffu, al, o); al = v > al ? v : al;
+      v = __shfl_xor_sync(0xffffffffu, tg, o); tg = v < tg ? v : tg;
+      v = __shfl_xor_sync(0xffffffffu, ag, o); ag = v < ag ? v : ag;
+    }
+    if (lane == 0) {
+      ULL* w = scratch + wid * 8;
+      w[0] = (ULL)nA; w[1] = (ULL)nB;
+      w[2] = (ULL)__double_as_longlong(SA); w[3] = (ULL)__double_as_longlong(SB);
+      w[4] = tl; w[5] = tg; w[6] = al; w[7] = ag;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {   // warps in order: the same sums on every call
+      ULL* w = scratch;
+      long long a0 = 0, b0 = 0;
+      double sa = 0.0, sb = 0.0;
+      ULL x4 = 0ull, x5 = ~0ull, x6 = 0ull, x7 = ~0ull;
+      for (int k = 0; k < NW; ++k, w += 8) {
+        a0 += (long long)w[0]; b0 += (long long)w[1];
+        sa += __longlong_as_double((long long)w[2]); sb += __longlong_as_double((long long)w[3]);
+        x4 = w[4] > x4 ? w[4] : x4; x5 = w[5] < x5 ? w[5] : x5;
+        x6 = w[6] > x6 ? w[6] : x6; x7 = w[7] < x7 ? w[7] : x7;
+      }
+      ULL* r = scratch + NW * 8;
+      r[0] = (ULL)a0; r[1] = (ULL)b0;
+      r[2] = (ULL)__double_as_longlong(sa); r[3] = (ULL)__double_as_longlong(sb);
+      r[4] = x4; r[5] = x5; r[6] = x6; r[7] = x7;
+    }
+    __syncthreads();
+    {
+      const ULL* r = scratch + NW * 8;
+      nA = (long long)r[0]; nB = (long long)r[1];
+      SA = __longlong_as_double((long long)r[2]); SB = __longlong_as_double((long long)r[3]);
+      tl = r[4]; tg = r[5]; al = r[6]; ag = r[7];
+    }
+    // the keys equal to thr_k: need_k of them in the top set, eq_k - need_k in the tail
+    if (need_k > 0) {
+      if (thr_b < hb) { nA += need_k; SA += (double)need_k * thr_k; al = thr_b > al ? thr_b : al; }
+      else ag = thr_b < ag ? thr_b : ag;
+    }
+    if (eq_k > need_k) {
+      if (thr_b > tb) { nB += eq_k - need_k; SB += (double)(eq_k - need_k) * thr_k; tg = thr_b < tg ? thr_b : tg; }
+      else tl = thr_b > tl ? thr_b : tl;
+    }
+    *nb_out = (int)nB;
+    const double phi = (double)nA * h - SA - (SB - (double)nB * th);
     if (phi == 0.0) return th;
     if (phi < 0.0) lo = th; else hi = th;
-    double cand = solve_piece((int)nA, SA, (int)nB, SB, rho * th < M, rho, M);
-    const bool newton_ok = (nA + nB > 0) && cand > lo && cand < hi;
-    const double next = newton_ok ? cand : 0.5 * (lo + hi);
-    // the Newton step from the piece containing th lands on th itself: th is the
-    // root of a piece that is active at th, hence the root of Phi
-    if (newton_ok && it > 0 && fabs(next - th) <= 2e-15 * fabs(th)) return next;
-    if (hi - lo <= 2e-16 * hi) return newton_ok ? next : hi;
-    th = next;
+    const bool rb = rho * th < M;
+    const double c = solve_piece((int)nA, SA, (int)nB, SB, rb, rho, M);
+    if (nA + nB > 0 && c > lo && c < hi) {
+      const double hc = c + fmin(rho * c, M);
+      const ULL cb = nnbits(c), hcb = nnbits(hc);
+      bool same = (rho * c < M) == rb;
+      if (c < th) same = same && tl <= cb && al < hcb;   // no key in (c, th] (tail) or [h(c), h(th)) (top)
+      else same = same && tg > cb && ag >= hcb;         // no key in (th, c] (tail) or [h(th), h(c)) (top)
+      if (same) return c;
+      th = c;
+    } else {
+      th = 0.5 * (lo + hi);
+    }
+    if (!(hi - lo > 2e-16 * hi)) return hi;
   }
   return th;
 }
 
 template <typename T, int BLOCK>
 __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
+  static_assert(sizeof(T) == 8, "prox_segment: FP64 segments (64-bit key bits)");
   using B = Bits<T>;
   using U = typename B::U;
   const int m = io.m;
@@ -293,9 +398,11 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     } else {
       int Q = io.qhint > q + 1 ? io.qhint : q + 1;
       if (Q > m) Q = m;
+      // the previous call's pooled tail did not fit the candidates: straight to the full pass
+      const bool wide = Q > sm.cap;
       bool found = false;
       double last_floor = INFINITY;
-      while (!found && Q <= sm.cap) {
+      while (!wide && !found && Q <= sm.cap) {
         double floorv = 0.0;
         if (Q < m) {
           SelectResult<U> RQ = block_select<U, BLOCK>(m, Q, keybits, sm.hist, sm.sh);
@@ -315,11 +422,11 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
           for (int i = threadIdx.x; i < m; i += BLOCK) sm.cand[i] = keyval(i);
         }
         const int N = next_pow2(Q);
-        for (int j = Q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+        for (int j = Q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = 0.0;
         __syncthreads();
-        block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+        sort_desc_nonneg<BLOCK>(sm.cand, N);
         block_prefix<BLOCK>(sm.cand, sm.pref, Q, sm.red);
-        found = root_from_sorted<BLOCK>(sm.cand, sm.pref, q, Q, floorv, rho, M, sm.red, &theta);
+        found = root_from_sorted<BLOCK>(sm.cand, sm.pref, q, Q, floorv, rho, M, sm.red, sm.sh, &theta);
         out.qused = Q;
         last_floor = floorv;
         if (!found) {
@@ -340,8 +447,13 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
         out.qused = next < out.qused ? next : out.qused;
       } else {
         out.fallback = 1;
-        theta = root_fullpass<T, BLOCK>(m, keyval, thr_k, need_k, eq_k,
-                                        isinf(last_floor) ? thr_k : last_floor, rho, M, sm.red);
+        int nb = 0;
+        // Phi(last_floor) > 0 when the candidates were tried; Phi(thr_k) >= 0 always
+        const double hi0 = isinf(last_floor) ? thr_k : last_floor;
+        theta = root_fullpass<BLOCK>(m, keybits, thr_k, need_k, eq_k, hi0, io.theta0, rho, M,
+                                     reinterpret_cast<unsigned long long*>(sm.hist), &nb);
+        // the pooled tail at the root sizes the next call (above the capacity: full pass again)
+        out.qused = q + 2 * nb + 32;
       }
     }
   }
@@ -365,16 +477,20 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     int ex = block_exclusive_scan<int, BLOCK>(lane == 0 ? cnt : 0, sm.sh, &tot);
     tie_base = __shfl_sync(0xffffffffu, ex, 0);
   }
-  // main output pass
+  // main output pass.  Magnitudes and thresholds are non-negative, so the
+  // membership tests compare bit patterns; FP64 arithmetic runs only for the
+  // coordinates that come out nonzero (the top set and the tail above theta).
   const double shrink = rho / (1.0 + rho);
+  const unsigned long long thr_b = nnbits(thr_k), theta_b = nnbits(theta);
   double l1 = 0.0;
   int nzc = 0, tie_run = 0;
   for (int base = c0; base < c1; base += 32) {
     const int i = base + lane;
     const bool valid = i < c1;
     const int8_t st = (valid && io.state) ? io.state[i] : (int8_t)kFree;
-    double a = valid ? keyval(i) : 0.0;
-    bool tie = valid && st == kFree && q > 0 && a == thr_k;
+    const T wt = valid ? wv[i] : T(0);
+    const unsigned long long ab = valid ? nnbits(fabs(to_d(wt))) : 0ull;
+    bool tie = valid && st == kFree && q > 0 && ab == thr_b;
     int tie_rank = 0;
     if (tie_split) {
       const unsigned bal = __ballot_sync(0xffffffffu, tie);
@@ -384,16 +500,20 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     bool nz = false;
     if (valid) {
       if (st == kFree) {
-        const bool in_top = (q > 0) && (a > thr_k || (tie && (!tie_split || tie_rank < need_k)));
-        double mag;
-        if (in_top) mag = fmin(fmin(M, shrink * a), a - theta);
-        else mag = fmax(0.0, a - theta);
-        if (!(mag > 0.0)) mag = 0.0;
-        const T wt = wv[i];
-        const T bt = (T)(to_d(wt) < 0 ? -mag : mag);
+        const bool in_top = (q > 0) && (ab > thr_b || (tie && (!tie_split || tie_rank < need_k)));
+        double mag = 0.0;
+        if (in_top || ab > theta_b) {
+          const double a = fabs(to_d(wt));
+          mag = in_top ? fmin(fmin(M, shrink * a), a - theta) : a - theta;
+          if (!(mag > 0.0)) mag = 0.0;
+        }
+        T bt = T(0);
+        if (mag > 0.0) {
+          bt = (T)(to_d(wt) < 0 ? -mag : mag);
+          l1 += fabs(to_d(bt));
+          nz = true;
+        }
         io.beta[i] = bt;
-        l1 += fabs(to_d(bt));
-        nz = mag > 0.0;
       } else {
         nz = to_d(io.beta[i]) != 0.0;
       }
@@ -442,9 +562,9 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
       __syncthreads();
       for (int j = (q - need_k) + threadIdx.x; j < q; j += BLOCK) sm.cand[j] = thr_k;
       const int N = next_pow2(q);
-      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = 0.0;
       __syncthreads();
-      block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+      sort_desc_nonneg<BLOCK>(sm.cand, N);
     }
     // |b_t| into cand (in place), prefix sums in pref
     for (int t = threadIdx.x; t < q; t += BLOCK) {
@@ -493,7 +613,7 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     }
     __syncthreads();
     const int N = next_pow2(q);
-    for (int j = q + threadIdx.x; j < N; j += BLOCK) { sm.cand[j] = -1.0; sm.cidx[j] = 0x7fffffff; }
+    for (int j = q + threadIdx.x; j < N; j += BLOCK) { sm.cand[j] = 0.0; sm.cidx[j] = 0x7fffffff; }
     __syncthreads();
     // bitonic sort of (value desc, index asc)
     for (int size = 2; size <= N; size <<= 1) {
@@ -503,8 +623,9 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
           const int hi = lo + stride;
           const bool desc = ((lo & size) == 0);
           const double a = sm.cand[lo], b = sm.cand[hi];
+          const unsigned long long ab = nnbits(a), bb = nnbits(b);
           const int ia = sm.cidx[lo], ib = sm.cidx[hi];
-          const bool a_before_b = (a > b) || (a == b && ia < ib);
+          const bool a_before_b = (ab > bb) || (ab == bb && ia < ib);
           if (a_before_b != desc) {
             sm.cand[lo] = b; sm.cand[hi] = a; sm.cidx[lo] = ib; sm.cidx[hi] = ia;
           }
@@ -576,9 +697,9 @@ __device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, 
       const double thr = B::val(R.thr);
       for (int j = R.gt + threadIdx.x; j < q; j += BLOCK) sm.cand[j] = thr;
       const int N = next_pow2(q);
-      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = -1.0;
+      for (int j = q + threadIdx.x; j < N; j += BLOCK) sm.cand[j] = 0.0;
       __syncthreads();
-      block_bitonic_sort_desc<double, BLOCK>(sm.cand, N);
+      sort_desc_nonneg<BLOCK>(sm.cand, N);
       block_prefix<BLOCK>(sm.cand, sm.pref, q, sm.red);
       int jst = q;
       for (int j = threadIdx.x; j < q; j += BLOCK) {

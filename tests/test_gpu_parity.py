@@ -64,13 +64,15 @@ def test_prox_primitive_matches_oracle(K, case):
 
 
 def test_prox_primitive_wide_pooled_block_fallback(K):
-    # values nearly equal and a small rho: the pooled block takes most of the tail,
-    # beyond the shared-memory candidate capacity -> full-pass root finder
+    # values nearly equal, rho and M large: the top k' terms of Phi grow like
+    # theta + M, so the pooled block (the tail above theta, all nonzero in the
+    # output) holds ~6300 coordinates, beyond the 4096 shared-memory candidates ->
+    # full-pass root finder
     rng = np.random.default_rng(7)
     p, k = 20000, 5
     w = rng.uniform(0.95, 1.0, p) * np.where(rng.random(p) < 0.5, -1, 1)
-    beta, top = K.ksc_prox_g(w, k, 3.0, 0.01)
-    ref, perm = O.prox_g(w, k, 0.01, 3.0)
+    beta, top = K.ksc_prox_g(w, k, 10.0, 10.0)
+    ref, perm = O.prox_g(w, k, 10.0, 10.0)
     assert np.count_nonzero(ref) > 4096
     assert np.max(np.abs(beta - ref)) <= 1e-12
     assert np.array_equal(top, perm[:k].astype(np.int32))
