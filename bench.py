@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="single workload: leave out the batched comparison object")
     ap.add_argument("--small", action="store_true",
                     help="8000 x 20000 instance of the same generator (640 MB X, still larger "
                          "than L2) for profiler captures; not a benchmark line")
@@ -335,8 +337,6 @@ def run_batched(args):
         check(prob.solve_batch(nodes, want_beta=False))
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     clocks = ClockSampler(vis.split(",")[0] if vis else "0")
-    K.ksc_problem_profile(prob.h, True)
-    K.ksc_problem_kernel_time(prob.h, 0, reset=True)
     l0 = K.ksc_problem_launch_count(prob.h)
     torch.cuda.synchronize()
     clocks.start()
@@ -354,6 +354,13 @@ def run_batched(args):
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     launches = K.ksc_problem_launch_count(prob.h) - l0
+    value = B * args.steps / (ms / 1e3)
+    # per-phase device time: one more call with events around every kernel of the
+    # lock-step graph and around the certificate and anchor phases (not timed above)
+    K.ksc_problem_profile(prob.h, True)
+    K.ksc_problem_kernel_time(prob.h, 0, reset=True)
+    pres = prob.solve_batch(nodes, want_beta=False)
+    check(pres)
     kt = {name: K.ksc_problem_kernel_time(prob.h, kid)
           for name, kid in [("residual", K.KSC_KERNEL_B_RESID), ("xt_r", K.KSC_KERNEL_B_GRAD),
                             ("prox", K.KSC_KERNEL_B_PROX), ("x_dbeta", K.KSC_KERNEL_B_FWD),
@@ -361,14 +368,14 @@ def run_batched(args):
                             ("anchors", K.KSC_KERNEL_B_ANCHOR)]}
     bstats = K.ksc_problem_solve_stats(prob.h)
     K.ksc_problem_profile(prob.h, False)
-    value = B * args.steps / (ms / 1e3)
     tot = sum(v[1] for v in kt.values())
     shares = {k: round(v[1] / max(tot, 1e-9), 4) for k, v in kt.items()}
-    # tensor roofline of the X^T r product: algorithmic flops 2 n p B per launch
+    # tensor roofline of the X^T r product: algorithmic flops 2 n p per running node
+    # per step (tiles whose nodes have all stopped are skipped), over its device time
     nl, gms = kt["xt_r"]
-    g_ms = gms / max(nl, 1)
-    alg = 2.0 * n * p * B
-    achieved = alg / (g_ms / 1e3) / 1e12
+    node_steps = float(sum(r.iters for r in pres))
+    alg = 2.0 * n * p * node_steps
+    achieved = alg / (gms / 1e3) / 1e12
     try:
         pk = json.load(open(PEAKS_FILE))
         peak, peak_kind = float(pk["bf16_tflops"]), "measured"
@@ -402,21 +409,21 @@ def run_batched(args):
         "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                        "p99": round(float(np.percentile(lat_ms, 99)), 3)},
         "iters_per_bound": float(np.mean(iters)),
-        "lockstep_steps_per_call": kt["xt_r"][0] / max(args.steps, 1),
+        "lockstep_steps_per_call": kt["xt_r"][0],
         "certificates_per_call": bstats["batch_certificates"],
         "anchors_per_call": bstats["batch_anchors"],
         "prox_fallbacks_per_call": bstats["prox_fallback"],
-        "device_ms_per_call": {k: round(v[1] / max(args.steps, 1), 2) for k, v in kt.items()},
+        "device_ms_per_call": {k: round(v[1], 2) for k, v in kt.items()},
         "plain_single_node": {"value": round(plain, 3), "unit": UNIT, "nodes": len(sub),
                               "ratio": round(value / plain, 2)},
         "clocks": clk, "gpu_launches": int(launches), "kernel_time_share": shares,
         "e2e": {"value": round(B / e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
                 "d2h_bytes_per_step": int(B * (p * 8 + 64))},
-        "roofline": {"bound": "tensor", "kernel": "X^T r for all nodes (k_tcgemm, 3 BF16 pieces)",
+        "roofline": {"bound": "tensor", "kernel": "X^T r for the running nodes (k_tcgemm, 3 BF16 pieces)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
                      "peak_kind": peak_kind, "frac": round(achieved / peak, 4), "traffic": None,
-                     "flops_per_launch": alg, "executed_flops_per_launch": 3 * alg,
-                     "avg_launch_ms": round(g_ms, 5), "launches": nl},
+                     "flops_per_launch": alg / max(nl, 1), "pieces": 3,
+                     "node_steps": node_steps, "avg_launch_ms": round(gms / max(nl, 1), 5), "launches": nl},
     }
     return line
 
@@ -506,6 +513,15 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(P, float(np.mean(stats["iters"])),
                                                float(np.mean(stats["pow"])))
+        if not args.no_batched and world == 1 and not args.small:
+            # the batched mixed-precision form on its own workload, timed the same
+            # way, beside the plain single-node solver on the same nodes
+            del P
+            b = run_batched(args)
+            out["batched"] = {k: b[k] for k in (
+                "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "latency_ms",
+                "iters_per_bound", "plain_single_node", "e2e", "roofline", "device_ms_per_call",
+                "clocks", "gpu_launches")}
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

@@ -176,23 +176,29 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
 // ------------------------------------------------------------------ step
 
 __global__ void __launch_bounds__(128) k_bstep(BatchDev d) {
+  // one block per 128 slots (the products' M tile)
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= d.B) return;
-  BNode* nd = d.nodes + b;
-  if (nd->done != kRunning) return;
-  double f = 0.0, df = 0.0;
-  const double* fp = d.fpart + (size_t)2 * b * d.nft;
-  for (int t = 0; t < d.nft; ++t) {
-    f += fp[2 * t];
-    df += fp[2 * t + 1];
+  int run = 0;
+  if (b < d.B && d.nodes[b].done == kRunning) {
+    BNode* nd = d.nodes + b;
+    double f = 0.0, df = 0.0;
+    const double* fp = d.fpart + (size_t)2 * b * d.nft;
+    for (int t = 0; t < d.nft; ++t) {
+      f += fp[2 * t];
+      df += fp[2 * t + 1];
+    }
+    // L^{t+1} - L^t = sum_i [F_i(u^{t+1}) - F_i(u^t)] + 2 lambda2 (g(beta^{t+1}) - g(beta^t))
+    const double dL = df + 2.0 * nd->lambda2 * (nd->g_next - nd->g_cur);
+    fista_step_logic(nd, f, &dL);
+    nd->g_cur = nd->g_next;
+    nd->prev = nd->cur;
+    nd->cur = d.slot_new[b];
+    d.slot_cur[b] = nd->cur;
+    run = nd->done == kRunning;
   }
-  // L^{t+1} - L^t = sum_i [F_i(u^{t+1}) - F_i(u^t)] + 2 lambda2 (g(beta^{t+1}) - g(beta^t))
-  const double dL = df + 2.0 * nd->lambda2 * (nd->g_next - nd->g_cur);
-  fista_step_logic(nd, f, &dL);
-  nd->g_cur = nd->g_next;
-  nd->prev = nd->cur;
-  nd->cur = d.slot_new[b];
-  d.slot_cur[b] = nd->cur;
+  // the next step's products skip the tile once all its nodes have stopped
+  run = __syncthreads_or(run);
+  if (threadIdx.x == 0) d.tile_run[blockIdx.x] = run;
 }
 
 // ------------------------------------------------------------------ admission

@@ -196,6 +196,8 @@ template <int P, int BN, int MODE>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_tcgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
              TcEpi ep) {
+  // every row of this M tile belongs to a finished node: nothing to compute
+  if (ep.tile_active != nullptr && ep.tile_active[blockIdx.y] == 0) return;
   constexpr int S = tc_stages(P, BN);
   constexpr uint32_t B_TILE = BN * 128;
   constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;

@@ -118,6 +118,7 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   b += Bc * (sizeof(BNode) + sizeof(BCert)) + 2 * Bc * p * 8 + Bc * 4 + n * 12;
   b += 2 * Bc * ldn * 8 + Bc * ldp * 8 + Bc * batch_nrt((int)n) * 32;   // certificate vectors
   b += kDfWsElems * 8;                          // split partials of the exact product
+  b += (size_t)(Bc + 127) / 128 * 4;            // tile flags
   if (p > 2048) b += Bc * ldp * 8;              // prox scratch
   if (needs_xcopy(pr)) b += n * ldp * 2;
   return b;
@@ -164,6 +165,8 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
   BA(d.cert_a, (size_t)Bc * ldp * 8);
   BA(d.cpart, (size_t)Bc * batch_nrt(n) * 4 * 8);
   BA(d.dfws, kDfWsElems * 8);
+  BA(d.tile_run, (size_t)(Bc + 127) / 128 * 4);
+  KB_CUDA(cudaMemsetAsync(d.tile_run, 1, (size_t)(Bc + 127) / 128 * 4, s));   // nonzero: run every tile
   d.colnorm = pr->dev.colnorm;
   float* yf = nullptr;
   BA(yf, (size_t)n * 4);
@@ -228,6 +231,7 @@ TcEpi fwd_epi(const BatchWs* ws) {
   e.loss = d.loss;
   e.npart = d.nft;
   e.part = d.fpart;
+  e.tile_active = d.tile_run;
   return e;
 }
 
@@ -238,6 +242,7 @@ TcEpi grad_epi(const BatchWs* ws) {
   e.ldb = d.ldp;
   e.out64 = d.G;
   e.ldo = d.ldp;
+  e.tile_active = d.tile_run;
   return e;
 }
 
@@ -561,7 +566,14 @@ bool session_advance(Session* se, ksc_status* st) {
   *st = KSC_OK;
   if (session_running(se) == 0) return false;
   ksc_problem* pr = se->pr;
-  cudaError_t e = cudaGraphLaunch(pr->profile ? se->ws->graph_prof : se->ws->graph, se->s);
+  // tiles with a running node (k_bstep clears a tile's flag when its last node stops)
+  const int tiles = (se->B + 127) / 128;
+  se->tile_flags.assign(tiles, 0);
+  for (int b = 0; b < se->B; ++b)
+    if (se->slot[b].busy && !se->slot[b].fin) se->tile_flags[b / 128] = 1;
+  cudaError_t e = cudaMemcpyAsync(se->ws->bd.tile_run, se->tile_flags.data(), (size_t)tiles * 4,
+                                  cudaMemcpyHostToDevice, se->s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(pr->profile ? se->ws->graph_prof : se->ws->graph, se->s);
   if (e != cudaSuccess) {
     *st = api_fail(KSC_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     return false;
@@ -625,6 +637,7 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
   Phase anchor_phase{pr, ws, s, KSC_KERNEL_B_ANCHOR};
   anchor_phase.begin();
   const int64_t anchors0 = se->anchors;
+  bool upload = false;
   for (int b : fired) {
     SlotHost& sl = se->slot[b];
     const BNode& h = hn[b];
@@ -639,11 +652,8 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
       sl.fin = true;
       finished->push_back(b);
       if (h.done == kRunning) {   // certified while running: stop it on the device
-        BNode fz = h;
-        fz.done = kDoneGap;
-        KB_CUDA(cudaMemcpyAsync(d.nodes + b, &fz, sizeof fz, cudaMemcpyHostToDevice, s));
-        KB_CUDA(cudaStreamSynchronize(s));
-        hn[b] = fz;
+        hn[b].done = kDoneGap;
+        upload = true;
       }
       continue;
     }
@@ -660,9 +670,14 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     upd.best_dual = c.dual > -INFINITY ? std::max(c.dual, -1e300) : -INFINITY;
     if (std::isfinite(c.primal)) upd.best_primal = c.primal;
     upd.gap = (upd.best_primal - upd.best_dual) / std::max(std::fabs(upd.best_primal), 1e-300);
-    KB_CUDA(cudaMemcpyAsync(d.nodes + b, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaStreamSynchronize(s));
     hn[b] = upd;
+    upload = true;
+  }
+  // hn mirrors the device array (copied after the replay; only the certificate
+  // kernels ran since, and they do not write nodes): one upload of every change
+  if (upload) {
+    KB_CUDA(cudaMemcpyAsync(d.nodes, hn, (size_t)B * sizeof(BNode), cudaMemcpyHostToDevice, s));
+    KB_CUDA(cudaStreamSynchronize(s));
   }
   // anchors of running nodes whose gap fell (or that ran long without one)
   std::vector<int> alist;
@@ -749,6 +764,9 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
     if (batch_supported(pr) && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
     else single.push_back(i);
   }
+  // nodes with more free support entries run longer: grouping them in the same
+  // 128-slot tiles lets the products skip the tiles of the faster nodes sooner
+  std::stable_sort(batch.begin(), batch.end(), [&](int a, int b) { return setups[a].kp > setups[b].kp; });
   int64_t iters = 0, anchors = 0, certs = 0, fallbacks = 0;
   for (size_t g0 = 0; g0 < batch.size(); g0 += kBatchMax) {
     const int cnt = (int)std::min<size_t>(kBatchMax, batch.size() - g0);

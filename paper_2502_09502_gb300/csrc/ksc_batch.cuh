@@ -95,6 +95,7 @@ struct BatchDev {
   double* cert_a;      // B x ldp: X^T zeta
   double* cpart;       // B x nrt x 4: F, -F*(-zeta), its rounding weights, ||zeta||^2
   double* dfws;        // kDfWsElems: split partials of the tiled exact product
+  int* tile_run;       // per 128 slots: any node running (k_bstep and the host keep it)
 };
 
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }

@@ -40,6 +40,7 @@ struct Session {
   std::vector<char> hc_raw;    // host mirror of the BCert array
   int64_t anchors = 0;         // anchor products issued (statistics)
   int64_t certificates = 0;
+  std::vector<int> tile_flags; // staging of the per-tile running flags
   size_t bytes() const;
 };
 

@@ -45,6 +45,7 @@ struct TcEpi {
   int loss;
   int npart;
   double* part;
+  const int* tile_active;   // per 128-row M tile: 0 = every row finished, skip the tile (NULL: none)
 };
 
 struct TcPlan {
