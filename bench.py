@@ -57,10 +57,18 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="8000 x 20000 instance of the same generator (640 MB X, still larger "
                          "than L2) for profiler captures; not a benchmark line")
-    ap.add_argument("--workload", default="single", choices=["single", "batched"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "prox"],
                     help="single: the single-node FP32 line (default); batched: 512 nodes of "
                          "the batched logistic BF16 workload in one ksc_solve_batch call")
     ap.add_argument("--nodes", type=int, default=512, help="batched: nodes per call")
+    ap.add_argument("--pool", type=int, default=4, help="serving: resident problems drawn from the mix")
+    ap.add_argument("--requests", type=int, default=2048, help="serving: distinct requests (reused cyclically)")
+    ap.add_argument("--burst", type=int, default=256, help="serving: requests of the saturation burst")
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.3, 0.6, 0.9],
+                    help="serving: Poisson rates as fractions of the saturation throughput")
+    ap.add_argument("--window", type=float, default=8.0, help="serving: seconds of arrivals per rate")
+    ap.add_argument("--slots", type=int, default=256, help="serving: slots per problem session")
+    ap.add_argument("--max-iter", type=int, default=4000, help="serving: iteration cap per request")
     ap.add_argument("--plain-nodes", type=int, default=16,
                     help="batched: nodes of the same batch solved one at a time by the "
                          "single-node solver for the comparison")
@@ -302,6 +310,208 @@ def run_ours(args, rank, world, dist):
     return out, P, stats
 
 
+# ------------------------------------------------------------------ prox micro-benchmark
+
+PROX = dict(workload="prox of g on many vectors (Sec. 5.1 / Fig. 1 shapes): gamma ~ N(0, I), k=10, M=1, "
+                     "rho=1, p = 100 * 2^i for i = 0..10, >= 2^24 elements per launch (>= 608 rows), "
+                     "inputs larger than L2 from p = 100 on")
+
+
+def run_prox(args, reps=10):
+    """Elements per second of ksc_prox_g_batch (one CTA per vector) over the prox
+    timing experiment's sizes; 16 algorithmic bytes per element (read w, write beta)."""
+    import torch
+    from paper_2502_09502_gb300 import ksc as K
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(int(args.seed))
+    try:
+        hbm = float(json.load(open(PEAKS_FILE))["hbm_gbs"])
+    except Exception:
+        hbm = 6800.0
+    sweep = []
+    for i in range(11):
+        p = 100 * 2 ** i
+        count = max(4 * 152, -(-(1 << 24) // p))
+        W = torch.randn((count, p), generator=g, device="cuda", dtype=torch.float64)
+        out = torch.empty_like(W)
+        torch.cuda.synchronize()
+
+        def launch():
+            K._check(K.ksc_prox_g_batch(W.data_ptr(), p, out.data_ptr(), p, p, count, 10, 1.0, 1.0, stream))
+
+        for _ in range(3):
+            launch()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        elems = count * p
+        sweep.append({"p": p, "vectors": count, "ms_per_launch": round(ms, 4),
+                      "elements_per_s": round(elems / (ms / 1e3), 1),
+                      "algorithmic_gbs": round(16.0 * elems / (ms / 1e3) / 1e9, 1)})
+        del W, out
+    # the oracle (sort + PAVA merge) on a bounded sample of the same shapes
+    from oracle import oracle as O
+    rng = np.random.default_rng(args.seed)
+    t0, elems = time.perf_counter(), 0
+    for p in (1600, 12800, 102400):
+        for _ in range(3):
+            O.prox_g(rng.standard_normal(p), 10, 1.0, 1.0)
+            elems += p
+    cpu_s = time.perf_counter() - t0
+    big = sweep[-1]
+    return {
+        "metric": "prox elements/s", "value": big["elements_per_s"], "unit": "elements/s", "n_gpus": 1,
+        "steps": reps, "warmup": 3, "ms_per_step": big["ms_per_launch"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (torch Philox normals)",
+        "config": dict(PROX, parallelism="single GPU"), "sweep": sweep,
+        "roofline": {"bound": "hbm", "kernel": "k_prox_rows (p = 102400)", "achieved": big["algorithmic_gbs"],
+                     "peak": hbm, "unit": "GB/s", "frac": round(big["algorithmic_gbs"] / hbm, 4),
+                     "traffic": None, "bytes_per_element": 16},
+        "cpu_baseline": {"value": round(elems / cpu_s, 1), "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": "3 vectors each of p = 1600, 12800, 102400 (same distribution and k, M, rho)"},
+    }
+
+
+# ------------------------------------------------------------------ serving workload
+
+SERVING = dict(workload="serving stream: Poisson arrivals of single-node requests over a resident pool "
+                        "drawn from the mix (least squares or logistic, n~U{2000..40000}, "
+                        "p~U{1000..100000}, k~U{5..50}, lambda2 in {1e-3,1e-2,1e-1}, M~U[1,5], "
+                        "Toeplitz r in {0.1,0.5,0.9}, 5 x +-1, SNR 5, BF16 X), nodes as in the batched "
+                        "workload (|S0|~U{0..200}, |S1|~U{0..min(9,k)}, warm start = the problem's root "
+                        "iterate + N(0,1e-2)), rel gap 1e-6, HBM admission budget 120 GB")
+
+
+def run_serving(args):
+    """Continuous batching through ksc_server_*: a pool of resident problems, a
+    burst of requests for the saturation throughput, then Poisson streams at
+    fractions of it with the latency of every request (submission to completion,
+    as the server records it)."""
+    import torch
+    import ksc_inputs as G
+    from paper_2502_09502_gb300 import ksc as K
+    torch.cuda.set_device(0)
+    budget = 120e9
+    stream = torch.cuda.Stream()
+    t_setup = time.perf_counter()
+    pool, used = [], 0
+    for sp in G.serving_mix(args.pool, seed=args.seed):
+        X, y, _ = G.device_problem(sp["n"], sp["p"], r=sp["r"], seed=sp["seed"], loss=sp["loss"],
+                                   k_true=5, snr=5.0)
+        torch.cuda.synchronize()
+        prob = K.Problem(X, y, sp["loss"], stream=stream)
+        del X
+        used += prob.bytes
+        root = prob.solve(K.Node(sp["lambda2"], sp["M"], sp["k"], rel_gap_tol=1e-6, max_iter=args.max_iter),
+                          want_z=False)
+        pool.append(dict(spec=sp, prob=prob, root=root.beta, root_iters=root.iters))
+    setup_s = time.perf_counter() - t_setup
+    u = G.uniform(args.seed, 11, 4 * args.requests)
+
+    def request(i):
+        e = pool[min(int(u[4 * i] * len(pool)), len(pool) - 1)]
+        sp, p = e["spec"], e["prob"].p
+        z, o = G.node_sets(p, 1, seed=1000003 * args.seed + i, max_zero=200, max_one=min(9, sp["k"]))[0]
+        warm = e["root"] + G.warm_perturbation(p, 1, seed=1000003 * args.seed + i)[0]
+        return e, K.Node(sp["lambda2"], sp["M"], sp["k"], fixed_zero=z, fixed_one=o, warm_beta=warm,
+                         rel_gap_tol=1e-6, max_iter=args.max_iter)
+
+    memo = {}
+
+    def req(i):
+        i %= args.requests
+        if i not in memo:
+            memo[i] = request(i)
+        return memo[i]
+
+    server = K.Server(budget - used, max_slots=args.slots)
+
+    def drive(times, first):
+        """Submit request first+j at times[j] (seconds from now); poll until all finish."""
+        for j in range(len(times)):
+            req(first + j)            # built before the clock starts
+        t0 = time.perf_counter()
+        pending, done, j = {}, [], 0
+        while j < len(times) or pending:
+            now = time.perf_counter() - t0
+            while j < len(times) and times[j] <= now:
+                e, nd = req(first + j)
+                pending[server.submit(e["prob"], nd)] = (e, nd, first + j)
+                j += 1
+            for tk in list(pending):
+                r = server.poll(tk, timeout_ms=0, want_beta=False)
+                if r is not None:
+                    e, nd, idx = pending.pop(tk)
+                    done.append((idx, e, r, server.latency(tk), time.perf_counter() - t0))
+            if pending:
+                time.sleep(0.0005)
+        return done, time.perf_counter() - t0
+
+    def summary(done, span, offered):
+        lat = np.array([d[3] for d in done]) * 1e3
+        ok = [d for d in done if (d[2].status == "ok" and d[2].rel_gap <= 1e-6) or d[2].pruned]
+        flops = sum(12.0 * d[1]["prob"].n * d[1]["prob"].p * d[2].iters for d in done)
+        return {"offered_per_s": None if offered is None else round(offered, 3),
+                "achieved_per_s": round(len(ok) / span, 3), "requests": len(done), "certified": len(ok),
+                "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                "span_s": round(span, 3), "tensor_tflops_executed": round(flops / span / 1e12, 1)}
+
+    def per_problem(done):
+        out = []
+        for j, e in enumerate(pool):
+            mine = [d for d in done if d[1] is e]
+            if not mine:
+                continue
+            out.append({"problem": j, "requests": len(mine),
+                        "certified": sum((d[2].status == "ok" and d[2].rel_gap <= 1e-6) or d[2].pruned for d in mine),
+                        "mean_iters": round(float(np.mean([d[2].iters for d in mine])), 1),
+                        "p50_ms": round(float(np.percentile([1e3 * d[3] for d in mine], 50)), 1)})
+        return out
+
+    # saturation: every request of a burst at once
+    burst = min(args.burst, args.requests)
+    done, span = drive(np.zeros(burst), 0)
+    sat = summary(done, span, None)
+    sat["per_problem"] = per_problem(done)
+    cap = max(sat["achieved_per_s"], 1e-3)
+    curve, nxt = [], burst
+    for frac in args.rates:
+        arr = G.poisson_arrivals(frac * cap, args.window, seed=args.seed + int(frac * 1000))
+        done, span = drive(arr, nxt)
+        nxt += len(arr)
+        curve.append(dict(summary(done, span, frac * cap), fraction_of_saturation=frac))
+    st = server.stats()
+    # the same requests alone: each result is the same alone and in the mix
+    inv = []
+    for (idx, e, r, _, _) in done[:4]:
+        alone = e["prob"].solve_batch([req(idx)[1]], want_beta=False)[0]
+        inv.append(abs(alone.dual_bound - r.dual_bound) / max(abs(r.dual_bound), 1e-300))
+    server.close()
+    try:
+        peak = float(json.load(open(PEAKS_FILE))["bf16_tflops_sustained"])
+    except Exception:
+        peak = 1700.0
+    return {
+        "metric": METRIC, "value": sat["achieved_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1 + len(args.rates),
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Toeplitz AR(1) rows drawn on the device, standardised columns)",
+        "config": dict(SERVING, pool=[dict({k: e["spec"][k] for k in ("loss", "n", "p", "k", "lambda2", "M", "r")},
+                                           root_iters=e["root_iters"]) for e in pool],
+                       pool_bytes=int(used), max_slots=args.slots, max_iter=args.max_iter,
+                       parallelism="single GPU"),
+        "setup_s": round(setup_s, 1),
+        "saturation": sat, "latency_vs_throughput": curve,
+        "tensor_frac_of_sustained_peak": round(sat["tensor_tflops_executed"] / peak, 4),
+        "server": st, "alone_vs_mix_max_rel_dual_diff": float(max(inv)) if inv else None,
+    }
+
+
 # ------------------------------------------------------------------ batched workload
 
 BATCHED = dict(workload="batched logistic BF16 X n=10000 p=5000 k=10 lambda2=0.01 M=3 toeplitz 0.5, "
@@ -503,10 +713,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         D.init_process_group("nccl")
         dist = D
-    if args.workload == "batched":
+    if args.workload in ("batched", "serving", "prox"):
         if world > 1:
-            raise SystemExit("the batched workload runs on one GPU")
-        print(json.dumps(run_batched(args)), flush=True)
+            raise SystemExit(f"the {args.workload} workload runs on one GPU")
+        run = {"batched": run_batched, "serving": run_serving, "prox": run_prox}[args.workload]
+        print(json.dumps(run(args)), flush=True)
         return
     out, P, stats = run_ours(args, rank, world, dist)
     if rank == 0:

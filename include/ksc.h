@@ -190,6 +190,22 @@ ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* ou
 ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, double rho,
                               double* beta_out, int32_t* top_out, void* cuda_stream);
 
+/* The prox of ksc_prox_g (Moreau identity, Sec. 3.3; Alg. 1 + 4 in their
+ * threshold form) for `count` independent vectors of length p at once, on DEVICE
+ * buffers: row r of beta_out (p doubles at beta_out + r * ldb) = prox_{rho^-1 g}
+ * of row r of w (p doubles at w + r * ldw), every row with the same k, M, rho.
+ * This is the throughput form of the paper's prox timing experiment (Sec. 5.1,
+ * Fig. 1: many vectors instead of one).  The caller owns both buffers; they must
+ * not overlap (KSC_ERR_INVALID_ARG).  ldw, ldb >= p.  min(k, p) must be below 2048
+ * (KSC_ERR_UNIMPLEMENTED; ksc_prox_g takes up to 4095).  count = 0 does nothing.
+ * One CTA per row; work is enqueued on cuda_stream and the call returns without
+ * waiting.  No device memory is allocated (w is read in place); the first call
+ * on a device does the one-time set-up of ksc_prox_g_noalloc.  Results agree with
+ * ksc_prox_g to rounding (the two kernels order their FP64 sums differently).
+ * Non-finite entries of w give unspecified (but bounded-time) results. */
+ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* beta_out, int64_t ldb, int64_t p,
+                            int32_t count, int32_t k, double M, double rho, void* cuda_stream);
+
 /* ---- serving -------------------------------------------------------------- */
 
 /* A request loop on the current device for dual-bound solves of many nodes of

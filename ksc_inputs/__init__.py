@@ -28,6 +28,7 @@ _DT_CODE = {F64: 0, F32: 1, BF16: 2}
 
 # stream ids (second Philox key word)
 _S_SUPPORT, _S_SIGN, _S_NOISE, _S_LABEL, _S_NODES, _S_WARM = 2, 3, 4, 5, 6, 7
+_S_MIX, _S_ARRIVAL = 8, 9
 
 
 def build(force: bool = False) -> str:
@@ -166,6 +167,82 @@ def node_sets(p, count, *, seed=0, max_zero=200, max_one=9):
 def warm_perturbation(p, count, *, seed=0, var=1e-2):
     """N(0, var) perturbations (count x p) for warm starts."""
     return np.sqrt(var) * normal(seed, _S_WARM, count * p).reshape(count, p)
+
+
+# --------------------------------------------------------------------------
+# Device-side generation (large serving problems)
+
+def device_problem(n, p, *, r=0.5, seed=0, loss=LSQ, k_true=5, snr=5.0, device="cuda", block=256):
+    """The ``make_problem`` recipe drawn on a CUDA device with torch's generator:
+    the same distribution (AR(1) Toeplitz rows, standardised columns, BF16 X,
+    +-1 ground truth at seeded positions, the same label rules), not the same
+    numbers.  Used where host generation of multi-GB matrices would dominate.
+    The AR(1) recursion runs over blocks of ``block`` columns: inside a block the
+    columns are x_{j0+t} = r^{t+1} x_{j0-1} + sum_{l<=t} s r^{t-l} e_{j0+l}
+    (s = sqrt(1 - r^2)), one small product per block.
+    Returns (X as an n x p torch.bfloat16 device tensor, y float64, beta*)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    support = np.sort(_choose(seed, _S_SUPPORT, p, min(k_true, p)))
+    signs = np.where(uniform(seed, _S_SIGN, support.size) < 0.5, -1.0, 1.0)
+    beta_star = np.zeros(p)
+    beta_star[support] = signs
+    s = float(np.sqrt(1.0 - r * r))
+    t = torch.arange(block, device=device, dtype=torch.float64)
+    d = t[None, :] - t[:, None]
+    T = torch.where(d >= 0, s * torch.pow(torch.tensor(float(r), dtype=torch.float64, device=device),
+                                             d.clamp(min=0)), torch.zeros_like(d)).float()
+    rpow = torch.pow(torch.tensor(float(r), dtype=torch.float64, device=device), t + 1).float()
+    X = torch.empty((n, p), dtype=torch.bfloat16, device=device)
+    prev = torch.zeros(n, device=device)
+    xb = torch.zeros(n, dtype=torch.float64, device=device)
+    for j0 in range(0, p, block):
+        w = min(block, p - j0)
+        E = torch.randn((n, w), generator=g, device=device)
+        if j0 == 0:
+            E[:, 0] /= s           # x_0 = e_0
+        raw = prev[:, None] * rpow[None, :w] + E @ T[:w, :w]
+        prev = raw[:, w - 1].clone()
+        mu = raw.mean(0, keepdim=True)
+        sd = (raw - mu).pow(2).mean(0, keepdim=True).sqrt()
+        X[:, j0:j0 + w] = ((raw - mu) / sd).to(torch.bfloat16)
+        sel = support[(support >= j0) & (support < j0 + w)]
+        for j in sel:
+            xb += beta_star[j] * X[:, int(j)].double()
+    xb_h = xb.cpu().numpy()
+    if loss == LSQ:
+        sigma = np.sqrt(float(xb_h @ xb_h) / (n * snr))
+        y = xb_h + sigma * torch.randn(n, generator=g, device=device, dtype=torch.float64).cpu().numpy()
+    else:
+        prob = 1.0 / (1.0 + np.exp(-xb_h))
+        y = np.where(torch.rand(n, generator=g, device=device, dtype=torch.float64).cpu().numpy() < prob,
+                     1.0, -1.0)
+    return X, y, beta_star
+
+
+def serving_mix(count, *, seed=0):
+    """Problem parameters of the serving stream: least squares or logistic,
+    n ~ U{2000..40000}, p ~ U{1000..100000}, k ~ U{5..50},
+    lambda2 in {1e-3, 1e-2, 1e-1}, M ~ U[1, 5], Toeplitz r in {0.1, 0.5, 0.9}."""
+    u = uniform(seed, _S_MIX, 8 * count)
+    out = []
+    for i in range(count):
+        v = u[8 * i:8 * i + 8]
+        out.append(dict(loss=LSQ if v[0] < 0.5 else LOGISTIC,
+                        n=2000 + int(v[1] * 38001), p=1000 + int(v[2] * 99001),
+                        k=5 + int(v[3] * 46), lambda2=(1e-3, 1e-2, 1e-1)[min(int(v[4] * 3), 2)],
+                        M=1.0 + 4.0 * float(v[5]), r=(0.1, 0.5, 0.9)[min(int(v[6] * 3), 2)],
+                        seed=int(v[7] * 2**31)))
+    return out
+
+
+def poisson_arrivals(rate, duration, *, seed=0):
+    """Arrival times (seconds) of a Poisson stream of the given rate over [0, duration)."""
+    m = int(rate * duration * 3 + 64)
+    gaps = -np.log(np.maximum(uniform(seed, _S_ARRIVAL, m), 1e-300)) / rate
+    t = np.cumsum(gaps)
+    return t[t < duration]
 
 
 # --------------------------------------------------------------------------

@@ -141,6 +141,40 @@ k_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, i
   prox_segment<double, kProxBlock>(io, sm);
 }
 
+// many independent vectors, one CTA each: row r of w -> row r of beta.  w is read
+// in place (every coordinate free, no copy); the first round of candidates is
+// sized for a pooled tail of a few times k.
+constexpr int kRowsBlock = 256, kRowsCap = 2048;
+
+__global__ void __launch_bounds__(kRowsBlock)
+k_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int k, double M, double rho) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kRowsCap, 0);
+  const int64_t r = blockIdx.x;
+  SegIO<double> io;
+  io.m = p;
+  io.state = nullptr;
+  io.w = w + r * ldw;
+  io.bc = io.bp = nullptr;
+  io.grad = nullptr;
+  io.gradf = nullptr;
+  io.c = 0.0;
+  io.invL = 0.0;
+  io.rho = rho;
+  io.M = M;
+  io.kp = k;
+  io.wbuf = nullptr;
+  io.beta = beta + r * ldb;
+  io.nnz_idx = nullptr;
+  io.nnz_val = nullptr;
+  io.nnz_cap = 0;
+  io.top_out = nullptr;
+  const int q = k < p ? k : p;
+  io.qhint = 4 * q + 64 < kRowsCap ? 4 * q + 64 : kRowsCap;
+  io.theta0 = -1.0;
+  prox_segment<double, kRowsBlock>(io, sm);
+}
+
 __global__ void __launch_bounds__(kProxBlock, 1)
 k_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -176,6 +210,7 @@ void prox_prepare() {
   cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
   cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
@@ -204,6 +239,14 @@ void launch_prox_prim(const double* w, int p, int k, double M, double rho, doubl
   if (base + (size_t)p * 8 + 16 <= g_smem_max) wsm = p;
   k_prox_prim<<<1, kProxBlock, prox_bytes(kProxCap, wsm, 8), s>>>(w, p, k, M, rho, beta, top, wbuf,
                                                                  wsm);
+}
+
+int prox_rows_cap() { return kRowsCap; }
+
+void launch_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int count, int k,
+                      double M, double rho, cudaStream_t s) {
+  if (count <= 0) return;
+  k_prox_rows<<<count, kRowsBlock, prox_bytes(kRowsCap, 0, 8), s>>>(w, ldw, beta, ldb, p, k, M, rho);
 }
 
 void launch_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z,

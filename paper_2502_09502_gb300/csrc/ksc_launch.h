@@ -134,6 +134,10 @@ void launch_transpose(const Dev& d, cudaStream_t s);
 void prox_prepare();
 
 // primitives (one CTA, FP64)
+// prox of g for `count` vectors (device rows with leading dims ldw, ldb), one CTA each
+int prox_rows_cap();
+void launch_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int count, int k,
+                      double M, double rho, cudaStream_t s);
 void launch_prox_prim(const double* w, int p, int k, double M, double rho, double* beta,
                       int* top, double* wbuf, cudaStream_t s);
 void launch_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z,

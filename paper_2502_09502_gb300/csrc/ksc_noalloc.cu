@@ -1,5 +1,5 @@
-// ksc_noalloc.cu -- ksc_prox_g_noalloc: the prox of g on device buffers, with no
-// device allocation at all.
+// ksc_noalloc.cu -- the prox of g on device buffers with no device allocation at
+// all: ksc_prox_g_noalloc (one vector) and ksc_prox_g_batch (many vectors).
 //
 // Some callers cannot call cudaMalloc: code running while a CUDA graph is being
 // captured (cudaMalloc is not capturable), runtimes that own every byte of device
@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/ksc.h"
@@ -36,6 +37,60 @@ bool g_ready[kMaxDevices] = {};
 
 }  // namespace
 
+// one-time set-up on the current device (the scratch's address and the kernels'
+// shared-memory limits); returns the scratch or NULL with the error recorded
+static void* prepare_device(ksc_status* st) {
+  *st = KSC_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    *st = ksc_internal_fail(KSC_ERR_CUDA, "no usable current CUDA device");
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_ready[dev]) {
+    cudaError_t e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_prox_scratch);
+    if (e != cudaSuccess) {
+      g_scratch_ptr[dev] = nullptr;
+      *st = ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+      return nullptr;
+    }
+    ksc::prox_prepare();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      *st = ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+      return nullptr;
+    }
+    g_ready[dev] = true;
+  }
+  return g_scratch_ptr[dev];
+}
+
+extern "C" ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* beta_out, int64_t ldb, int64_t p,
+                                       int32_t count, int32_t k, double M, double rho, void* cuda_stream) {
+  if (count < 0) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "count must be >= 0");
+  if (count > 0 && (!w || !beta_out)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "w and beta_out must be non-NULL");
+  if (p < 1 || p > INT32_MAX) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "p must be in [1, 2^31)");
+  if (ldw < p || ldb < p) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldw and ldb must be >= p");
+  if (k < 0) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "k must be >= 0");
+  if (!(M > 0) || !std::isfinite(M)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "M must be > 0");
+  if (!(rho > 0) || !std::isfinite(rho)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "rho must be > 0");
+  if ((k < p ? (int64_t)k : p) >= ksc::prox_rows_cap())
+    return ksc_internal_fail(KSC_ERR_UNIMPLEMENTED, "min(k, p) must be < 2048 (per-vector candidate capacity)");
+  if (count > 0) {
+    const char* a = (const char*)w;
+    const char* b = (const char*)beta_out;
+    const int64_t wb = ((int64_t)(count - 1) * ldw + p) * 8, bb = ((int64_t)(count - 1) * ldb + p) * 8;
+    if (a < b + bb && b < a + wb) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "w and beta_out overlap");
+  }
+  if (count == 0) return KSC_OK;
+  ksc_status st;
+  if (!prepare_device(&st)) return st;
+  ksc::launch_prox_rows(w, ldw, beta_out, ldb, (int)p, count, k, M, rho, (cudaStream_t)cuda_stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+  return KSC_OK;
+}
+
 extern "C" ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M,
                                          double rho, double* beta_out, int32_t* top_out,
                                          void* cuda_stream) {
@@ -50,27 +105,9 @@ extern "C" ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, 
   if ((k < p ? (int64_t)k : p) >= ksc::kProxCap)
     return ksc_internal_fail(KSC_ERR_UNIMPLEMENTED,
                              "min(k, p) must be < 4096 (prox candidate capacity)");
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return ksc_internal_fail(KSC_ERR_CUDA, "no usable current CUDA device");
-  void* scratch = nullptr;
-  {
-    // one-time set-up on this device (the device is current): the scratch
-    // address and the kernel's shared-memory limit
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ready[dev]) {
-      cudaError_t e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_prox_scratch);
-      if (e != cudaSuccess) {
-        g_scratch_ptr[dev] = nullptr;
-        return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
-      }
-      ksc::prox_prepare();
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
-      g_ready[dev] = true;
-    }
-    scratch = g_scratch_ptr[dev];
-  }
+  ksc_status st;
+  void* scratch = prepare_device(&st);
+  if (!scratch) return st;
   // every entry of the scratch that the kernel reads it has written first in the
   // same call, so nothing needs clearing between calls
   ksc::launch_prox_prim(w, (int)p, k, M, rho, beta_out, top_out, (double*)scratch,

@@ -345,12 +345,14 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
   using U = typename B::U;
   const int m = io.m;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T* wv = sm.wsm ? sm.wsm : io.wbuf;
+  // a direct input with every coordinate free is read in place (no copy)
+  const bool direct = io.w != nullptr && io.state == nullptr && sm.wsm == nullptr && io.wbuf == nullptr;
+  T* wv = direct ? const_cast<T*>(io.w) : (sm.wsm ? sm.wsm : io.wbuf);
   const double rho = io.rho, M = io.M;
 
   // pass 1: w (rounded to T), the fixed coordinates' outputs
   double s1sq = 0.0;
-  for (int i = threadIdx.x; i < m; i += BLOCK) {
+  for (int i = direct ? m : threadIdx.x; i < m; i += BLOCK) {
     double w;
     if (io.w) w = to_d(io.w[i]);
     else {

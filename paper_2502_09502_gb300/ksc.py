@@ -34,7 +34,7 @@ KSC_KERNEL_B_CERT, KSC_KERNEL_B_ANCHOR = 8, 9
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
-           "ksc_prox_g_noalloc", "ksc_problem_profile", "ksc_problem_kernel_time",
+           "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
            "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
            "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state",
@@ -93,6 +93,8 @@ def _load():
     L.ksc_problem_solve_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
     L.ksc_prox_g_noalloc.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_double,
                                      C.c_void_p, C.c_void_p, C.c_void_p]
+    L.ksc_prox_g_batch.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
+                                   C.c_int32, C.c_double, C.c_double, C.c_void_p]
     L.ksc_tc_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                               C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.c_void_p]
@@ -204,6 +206,24 @@ def ksc_prox_g_noalloc(w_ptr, p, k, M, rho, beta_ptr, top_ptr=None, stream=None)
     return lib.ksc_prox_g_noalloc(C.c_void_p(w_ptr), int(p), int(k), float(M), float(rho),
                                   C.c_void_p(beta_ptr), C.c_void_p(top_ptr) if top_ptr else None,
                                   _stream_ptr(stream))
+
+
+def ksc_prox_g_batch(w_ptr, ldw, beta_ptr, ldb, p, count, k, M, rho, stream=None):
+    """Prox of g for `count` device rows at once (see include/ksc.h).  Returns the
+    ksc_status; the work is enqueued on `stream`."""
+    return lib.ksc_prox_g_batch(C.c_void_p(w_ptr), int(ldw), C.c_void_p(beta_ptr), int(ldb), int(p),
+                                int(count), int(k), float(M), float(rho), _stream_ptr(stream))
+
+
+def prox_g_rows(W, k, M, rho, out=None, stream=None):
+    """W: 2-D float64 CUDA tensor (rows contiguous); returns the prox of every row."""
+    import torch
+    assert W.is_cuda and W.dtype == torch.float64 and W.dim() == 2 and W.stride(1) == 1
+    if out is None:
+        out = torch.empty_like(W)
+    _check(ksc_prox_g_batch(W.data_ptr(), W.stride(0), out.data_ptr(), out.stride(0), W.shape[1],
+                            W.shape[0], k, M, rho, stream))
+    return out
 
 
 def ksc_tc_gemm(a_ptr, pieces, m, m_pad, k, lda, b_ptr, n, ldb, d_ptr, ldd, tile_n, stream=None):

@@ -68,6 +68,19 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
     assert ksc.lib.ksc_gstar(w.ctypes.data_as(dp), 4, 1, 0.0, w.ctypes.data_as(dp)) == \
         ksc.KSC_ERR_INVALID_ARG
     assert ksc.lib.ksc_solve_node(None, None, None, None) == ksc.KSC_ERR_INVALID_ARG
+    # batched prox on device rows: every argument check comes before any CUDA call
+    fb = ksc.lib.ksc_prox_g_batch
+    assert fb(None, 8, None, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG   # NULL rows
+    assert fb(None, 8, None, 8, 8, 0, 2, 1.0, 1.0, None) == ksc.KSC_OK                 # nothing to do
+    assert fb(16, 8, 4096, 8, 0, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG      # p = 0
+    assert fb(16, 4, 4096, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG      # ldw < p
+    assert "ldw" in ksc.ksc_last_error()
+    assert fb(16, 8, 4096, 8, 8, -3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG     # count < 0
+    assert fb(16, 8, 4096, 8, 8, 3, 2, 0.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG      # M <= 0
+    assert fb(16, 8, 4096, 8, 8, 3, 2, 1.0, float("nan"), None) == ksc.KSC_ERR_INVALID_ARG
+    assert fb(16, 4096, 1 << 20, 4096, 4096, 3, 2048, 1.0, 1.0, None) == ksc.KSC_ERR_UNIMPLEMENTED
+    assert fb(4096, 8, 4096 + 64, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG   # overlap
+    assert "overlap" in ksc.ksc_last_error()
     assert ksc.lib.ksc_problem_info(None, None, None) == ksc.KSC_ERR_INVALID_ARG
     assert ksc.lib.ksc_problem_bytes(None) == 0
     assert ksc.lib.ksc_problem_destroy(None) == ksc.KSC_OK
