@@ -25,7 +25,6 @@
 #include "ksc_common.cuh"
 #include "ksc_launch.h"
 #include "ksc_state.cuh"
-#include "ksc_batch.cuh"
 
 namespace ksc {
 
@@ -61,25 +60,6 @@ template <> struct Vec<__nv_bfloat16> {
     }
   }
 };
-
-template <typename A> __device__ __forceinline__ A xval(float x) { return (A)x; }
-template <typename A> __device__ __forceinline__ A xval(double x) { return (A)x; }
-template <typename A> __device__ __forceinline__ A xval(__nv_bfloat16 x) { return (A)__bfloat162float(x); }
-
-// Double-float accumulation of x * (rh + rl) into hi + lo.  x*rh = p + e exactly
-// (e by fma); hi + p = s + err exactly (Knuth's TwoSum); lo collects err, e and
-// x*rl, whose own rounding is ~u^2 of the sum.  The result hi + lo (taken in
-// double) is accurate to ~1e-13 relative.  __fmul_rn/__fadd_rn/__fsub_rn are never
-// contracted into an FMA, which would break the exactness of p and of TwoSum.
-__device__ __forceinline__ void df_add(float& hi, float& lo, float x, float rh, float rl) {
-  const float p = __fmul_rn(x, rh);
-  const float e = fmaf(x, rh, -p);
-  const float s = __fadd_rn(hi, p);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, fmaf(x, rl, e)));
-}
 
 __device__ __forceinline__ double sigmoid(double t) {
   return t >= 0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
@@ -827,143 +807,6 @@ void launch_grad_raw(const Dev& d, cudaStream_t s) {
     colsum_launch<float>((const float*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
   else
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
-}
-
-// ----------------------------------------------------------- batched exact product
-// D[list[r]][c] = sum_k A[k][c] V[list[r]][k] for the rows r < R of a node list
-// (A row-major K x C with leading dim lda): the exact products of many nodes in
-// one launch.  Each CTA stages a 32 x 128 tile of A once for 16 node vectors
-// (split into float hi + lo).  Within a block of kDfBlock consecutive k the terms
-// are summed in double-float (df_add); each block result hi + lo is added to an
-// FP64 accumulator.  Error bound (u = 2^-24, U = 2^-53, S = sum_k |A[k][c] V[k]|):
-//   |D - exact| <= [ (K_b^2/2 + 6 K_b + 5) u^2 + (blocks + splits + 2) U ] * 1.01 * S,
-// K_b = kDfBlock: per block the lo word collects the exact TwoSum and product errors
-// with its own rounding (<= u^2 (K_b^2/2 + 6 K_b + 4) S_block), the split of V costs
-// u^2 S, and the FP64 conversions and sums add the U terms.  With K split over
-// gridDim.z CTAs the partial sums go to ws and k_dfsum adds them in split order.
-// Every output element sums its terms in an order fixed by K alone.
-constexpr int kDfCols = 128, kDfNodes = 16, kDfK = 32, kDfBlock = 64;
-
-template <typename TX>
-__global__ void __launch_bounds__(256) k_dfprod(const TX* __restrict__ A, int64_t lda, int K, int C,
-                                                const double* __restrict__ V, int64_t ldv,
-                                                const int* __restrict__ list, int R, double* __restrict__ D,
-                                                int64_t ldd, int kchunk, double* __restrict__ ws) {
-  __shared__ __align__(16) float As[kDfK][kDfCols + 4];
-  __shared__ float Vh[kDfNodes][kDfK + 1];
-  __shared__ float Vl[kDfNodes][kDfK + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 4 columns x 2 nodes per thread
-  const int c0 = blockIdx.x * kDfCols, r0 = blockIdx.y * kDfNodes;
-  const int kb = blockIdx.z * kchunk, ke = min(K, kb + kchunk);
-  float hi[2][4], lo[2][4];
-  double acc[2][4];
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { hi[q][j] = 0.f; lo[q][j] = 0.f; acc[q][j] = 0.0; }
-  for (int k0 = kb; k0 < ke; k0 += kDfK) {
-    for (int e = threadIdx.x; e < kDfK * kDfCols; e += 256) {
-      const int kk = e / kDfCols, cc = e % kDfCols;
-      const int k = k0 + kk, c = c0 + cc;
-      As[kk][cc] = (k < ke && c < C) ? xval<float>(A[(size_t)k * lda + c]) : 0.f;
-    }
-    for (int e = threadIdx.x; e < kDfNodes * kDfK; e += 256) {
-      const int rr = e / kDfK, kk = e % kDfK;
-      const int r = r0 + rr, k = k0 + kk;
-      const double v = (r < R && k < ke) ? V[(size_t)list[r] * ldv + k] : 0.0;
-      const float h = (float)v;
-      Vh[rr][kk] = h;
-      Vl[rr][kk] = (float)(v - (double)h);
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int kk = 0; kk < kDfK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float vh = Vh[ty * 2 + q][kk], vl = Vl[ty * 2 + q][kk];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) df_add(hi[q][j], lo[q][j], av[j], vh, vl);
-      }
-    }
-    __syncthreads();
-    if (((k0 - kb + kDfK) % kDfBlock) == 0 || k0 + kDfK >= ke) {   // close the block
-#pragma unroll
-      for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          acc[q][j] += (double)hi[q][j] + (double)lo[q][j];
-          hi[q][j] = 0.f;
-          lo[q][j] = 0.f;
-        }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int r = r0 + ty * 2 + q;
-    if (r >= R) continue;
-    double* drow = ws ? ws + ((size_t)blockIdx.z * R + r) * C : D + (size_t)list[r] * ldd;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = c0 + tx * 4 + j;
-      if (c < C) drow[c] = acc[q][j];
-    }
-  }
-}
-
-// D[list[r]][c] = sum over splits z (in order) of ws[z][r][c]
-__global__ void __launch_bounds__(256) k_dfsum(const double* __restrict__ ws, int splits, int R, int C,
-                                               const int* __restrict__ list, double* __restrict__ D, int64_t ldd) {
-  const int r = blockIdx.y;
-  for (int c = blockIdx.x * 256 + (int)threadIdx.x; c < C; c += gridDim.x * 256) {
-    double t = 0.0;
-    for (int z = 0; z < splits; ++z) t += ws[((size_t)z * R + r) * C + c];
-    D[(size_t)list[r] * ldd + c] = t;
-  }
-}
-
-// K splits so that few nodes still fill ~2 CTAs per SM; splits x tiles stays below
-// 2 x 304, so the split partials fit kDfWsElems doubles
-int dfprod_splits(int R, int C) {
-  const int tiles = ((C + kDfCols - 1) / kDfCols) * ((R + kDfNodes - 1) / kDfNodes);
-  if (tiles >= 2 * 152) return 1;
-  const int sp = (2 * 152 + tiles - 1) / tiles;
-  return sp < kDfMaxSplits ? sp : kDfMaxSplits;
-}
-
-double dfprod_error_factor(int K, int R, int C) {
-  const double u = 5.9604644775390625e-08, U = 1.1102230246251565e-16;
-  const int splits = dfprod_splits(R, C);
-  const double kb = kDfBlock;
-  const double blocks = (double)((K + kDfBlock - 1) / kDfBlock) + splits;
-  return 1.01 * ((kb * kb / 2 + 6 * kb + 5) * u * u + (blocks + splits + 2) * U);
-}
-
-// D rows = A^T V rows for the listed nodes (A = X: V of length n, D of length p;
-// A = Xc: V of length p, D of length n); ws: dfprod_ws_elems doubles when the
-// product is split over K (few nodes)
-void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
-                   int64_t ldd, double* ws, cudaStream_t s) {
-  if (R <= 0) return;
-  const int K = use_xc ? d.p : d.n, C = use_xc ? d.n : d.p;
-  const int64_t lda = use_xc ? d.ldc : d.ldx;
-  const void* A = use_xc ? d.Xc : d.X;
-  const int splits = ws ? dfprod_splits(R, C) : 1;
-  const int kchunk = ((K + splits - 1) / splits + kDfBlock - 1) / kDfBlock * kDfBlock;
-  dim3 grid((C + kDfCols - 1) / kDfCols, (R + kDfNodes - 1) / kDfNodes, splits);
-  double* w = splits > 1 ? ws : nullptr;
-  if (d.xdt == kXF64)
-    k_dfprod<double><<<grid, 256, 0, s>>>((const double*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, w);
-  else if (d.xdt == kXF32)
-    k_dfprod<float><<<grid, 256, 0, s>>>((const float*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, w);
-  else
-    k_dfprod<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)A, lda, K, C, V, ldv, list, R, D, ldd,
-                                                 kchunk, w);
-  if (splits > 1) {
-    dim3 g2((C + 255) / 256 < 64 ? (C + 255) / 256 : 64, R);
-    k_dfsum<<<g2, 256, 0, s>>>(ws, splits, R, C, list, D, ldd);
-  }
 }
 
 // out = A^T vec for A = X (vec of length n, out of length p) or A = Xc (vec of

@@ -130,8 +130,8 @@ void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out
 // launch (rows of V and D with strides ldv, ldd), blocked double-float with a
 // rigorous error bound (dfprod_error_factor * sum |A V|).  Few nodes split K over
 // more CTAs through ws (kDfWsElems doubles).
-constexpr int kDfMaxSplits = 8;
-constexpr size_t kDfWsElems = (size_t)2 * 304 * 128 * 16;
+constexpr int kDfMaxSplits = 16;
+constexpr size_t kDfWsElems = (size_t)2 * 608 * 128 * 16;
 void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
                    int64_t ldd, double* ws, cudaStream_t s);
 int dfprod_splits(int R, int C);

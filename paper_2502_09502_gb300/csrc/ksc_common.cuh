@@ -280,6 +280,28 @@ __device__ __forceinline__ void sort_desc_nonneg(double* s, int N) {
 // the bit pattern of a non-negative double: ordered like the value
 __device__ __forceinline__ unsigned long long nnbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
+// ---------------------------------------------------------- double-float products
+
+// X entries read in their storage type, as A
+template <typename A> __device__ __forceinline__ A xval(float x) { return (A)x; }
+template <typename A> __device__ __forceinline__ A xval(double x) { return (A)x; }
+template <typename A> __device__ __forceinline__ A xval(__nv_bfloat16 x) { return (A)__bfloat162float(x); }
+
+// Double-float accumulation of x * (rh + rl) into hi + lo.  x*rh = p + e exactly
+// (e by fma); hi + p = s + err exactly (Knuth's TwoSum); lo collects err, e and
+// x*rl, whose own rounding is ~u^2 of the sum.  The result hi + lo (taken in
+// double) is accurate to ~1e-13 relative.  __fmul_rn/__fadd_rn/__fsub_rn are never
+// contracted into an FMA, which would break the exactness of p and of TwoSum.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x, float rh, float rl) {
+  const float p = __fmul_rn(x, rh);
+  const float e = fmaf(x, rh, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, fmaf(x, rl, e)));
+}
+
 // ---------------------------------------------------------- Huber
 
 __device__ __forceinline__ double huber(double a, double M) {

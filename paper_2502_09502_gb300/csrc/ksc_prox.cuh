@@ -491,7 +491,7 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
     const bool valid = i < c1;
     const int8_t st = (valid && io.state) ? io.state[i] : (int8_t)kFree;
     const T wt = valid ? wv[i] : T(0);
-    const unsigned long long ab = valid ? nnbits(fabs(to_d(wt))) : 0ull;
+    const unsigned long long ab = valid ? (unsigned long long)abs_bits<T>(wt) : 0ull;   // |w| bits, integer ops
     bool tie = valid && st == kFree && q > 0 && ab == thr_b;
     int tie_rank = 0;
     if (tie_split) {
