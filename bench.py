@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="8000 x 20000 instance of the same generator (640 MB X, still larger "
                          "than L2) for profiler captures; not a benchmark line")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "prox"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "prox", "bnb"],
                     help="single: the single-node FP32 line (default); batched: 512 nodes of "
                          "the batched logistic BF16 workload in one ksc_solve_batch call")
     ap.add_argument("--nodes", type=int, default=512, help="batched: nodes per call")
@@ -69,6 +69,11 @@ def parse():
     ap.add_argument("--window", type=float, default=8.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--slots", type=int, default=256, help="serving: slots per problem session")
     ap.add_argument("--max-iter", type=int, default=4000, help="serving: iteration cap per request")
+    ap.add_argument("--bnb-seconds", type=float, default=90.0, help="bnb: time limit")
+    ap.add_argument("--bnb-batch", type=int, default=256, help="bnb: nodes in flight")
+    ap.add_argument("--bnb-gap", type=float, default=1e-4, help="bnb: relative gap to certify")
+    ap.add_argument("--bnb-n", type=int, default=20000, help="bnb: rows")
+    ap.add_argument("--bnb-p", type=int, default=200000, help="bnb: columns")
     ap.add_argument("--plain-nodes", type=int, default=16,
                     help="batched: nodes of the same batch solved one at a time by the "
                          "single-node solver for the comparison")
@@ -308,6 +313,44 @@ def run_ours(args, rank, world, dist):
                          "avg_launch_ms": round(grad_ms, 5), "launches": nl},
         }
     return out, P, stats
+
+
+# ------------------------------------------------------------------ branch and bound
+
+BNB = dict(workload="best-first branch and bound, least squares BF16 X n=20000 p=200000 k=15 lambda2=0.1 M=2 "
+                    "toeplitz 0.7, 15 x +-1, SNR 3 (X drawn on the device), node bounds from the batched "
+                    "solver with continuous batching")
+
+
+def run_bnb(args):
+    """ksc_bnb_solve on the full branch-and-bound workload within a time limit:
+    node relaxations per second, the certified gap reached, and the time to
+    certify when it is reached."""
+    import torch
+    import ksc_inputs as G
+    from paper_2502_09502_gb300 import ksc as K
+    torch.cuda.set_device(0)
+    n, p, k = args.bnb_n, args.bnb_p, 15
+    t0 = time.perf_counter()
+    X, y, bstar = G.device_problem(n, p, r=0.7, seed=args.seed, loss=G.LSQ, k_true=15, snr=3.0)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    prob = K.Problem(X, y, K.KSC_LOSS_LSQ, stream=stream)
+    setup = time.perf_counter() - t0
+    beta, res = prob.bnb(0.1, 2.0, k, opt_gap=args.bnb_gap, time_limit_s=args.bnb_seconds, batch=args.bnb_batch,
+                         node_rel_gap=1e-6, node_max_iter=20000)
+    supp = set(np.nonzero(beta)[0].tolist())
+    truth = set(np.nonzero(bstar)[0].tolist())
+    return {
+        "metric": "branch-and-bound nodes/s", "value": round(res["nodes"] / max(res["seconds"], 1e-9), 2),
+        "unit": "nodes/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded Toeplitz AR(1) rows drawn on the device)",
+        "config": dict(BNB, n=n, p=p, k=k, opt_gap=args.bnb_gap, time_limit_s=args.bnb_seconds,
+                       batch=args.bnb_batch, parallelism="single GPU"),
+        "setup_s": round(setup, 1), "result": {kk: (round(v, 6) if isinstance(v, float) else v) for kk, v in res.items()},
+        "time_to_certify_s": round(res["seconds"], 2) if res["certified"] else None,
+        "incumbent_support_size": len(supp), "true_support_recovered": len(supp & truth),
+    }
 
 
 # ------------------------------------------------------------------ prox micro-benchmark
@@ -713,10 +756,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         D.init_process_group("nccl")
         dist = D
-    if args.workload in ("batched", "serving", "prox"):
+    if args.workload in ("batched", "serving", "prox", "bnb"):
         if world > 1:
             raise SystemExit(f"the {args.workload} workload runs on one GPU")
-        run = {"batched": run_batched, "serving": run_serving, "prox": run_prox}[args.workload]
+        run = {"batched": run_batched, "serving": run_serving, "prox": run_prox, "bnb": run_bnb}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     out, P, stats = run_ours(args, rank, world, dist)

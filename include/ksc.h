@@ -157,6 +157,56 @@ ksc_status ksc_solve_node(ksc_problem* problem, const ksc_node* node, ksc_result
 ksc_status ksc_solve_batch(ksc_problem* problem, const ksc_node* nodes, int32_t count,
                            ksc_result* results, void* cuda_stream);
 
+/* ---- branch and bound ------------------------------------------------------ */
+
+/* Best-first branch and bound for Eq. (1) (the minimal framework of Sec. 5.3 and
+ * App. B.3): node lower bounds are the certified bounds of the node relaxations,
+ * computed by the batched solver with continuous batching (one session of
+ * `batch` slots: a finished node's children take free slots at once, best bound
+ * first), the node's early-termination rules (Sec. 5.3: primal below the
+ * incumbent -> stop and branch; bound above it -> prune) use the incumbent of the
+ * moment the node starts.  Incumbents: at every processed node the support
+ * S1 + the k' largest free |b_j| of its relaxed solution is solved as a
+ * restricted problem (a node with S1 = that support and k = its size, whose
+ * relaxation is the box-constrained ridge on the support), in the same slots; its
+ * certified primal value is the objective of a feasible point.  Branching: on the
+ * free coordinate of that support whose removal raises the objective most to
+ * second order, b_j^2 (c ||x_j||^2 + lambda2), c = 1 (least squares) or 1/4
+ * (logistic).  A node whose relaxed solution already has at most k' free
+ * nonzeros and a certified gap closes (its value is a feasible objective).
+ * Stops when (incumbent - lower bound) / max(|incumbent|, 1e-300) <= opt_gap, when
+ * every node is pruned or closed, or at max_nodes node solves (0: none) or
+ * time_limit_s seconds (0: none).  Needs BF16 X (KSC_ERR_UNIMPLEMENTED
+ * otherwise); k < 2048; 1 <= batch <= 1024. */
+typedef struct {
+  double lambda2, M;
+  int32_t k;
+  double opt_gap;          /* relative optimality gap to certify, e.g. 1e-4 */
+  int64_t max_nodes;       /* node relaxations to solve at most (0 = no limit) */
+  double time_limit_s;     /* wall-clock limit (0 = no limit) */
+  int32_t batch;           /* session slots (nodes in flight) */
+  double node_rel_gap;     /* rel_gap_tol of every node solve */
+  int32_t node_max_iter;   /* max_iter of every node solve */
+} ksc_bnb_params;
+
+typedef struct {
+  double* beta;            /* caller-owned, length p (or NULL): the incumbent */
+  double incumbent;        /* its objective F(X beta) + lambda2 ||beta||^2 (+inf if none) */
+  double lower_bound;      /* certified lower bound on the optimum of Eq. (1) */
+  double gap;              /* (incumbent - lower_bound) / max(|incumbent|, 1e-300) */
+  int64_t nodes;           /* node relaxations solved */
+  int64_t pruned;          /* nodes pruned by their bound (at start or after solving) */
+  int64_t closed;          /* nodes whose relaxation was already feasible */
+  int64_t heuristic_solves;
+  int64_t replays;         /* lock-step graph replays (16 steps each) */
+  int64_t max_open;        /* largest number of open nodes */
+  double seconds;
+  int32_t certified;       /* 1: gap <= opt_gap (or nothing left open) */
+} ksc_bnb_result;
+
+ksc_status ksc_bnb_solve(ksc_problem* problem, const ksc_bnb_params* params, ksc_bnb_result* result,
+                         void* cuda_stream);
+
 /* ---- primitives (host pointers, FP64, one GPU launch each) -------------- */
 
 /* beta = prox_{rho^-1 g}(w) (Moreau identity, Sec. 3.3; Alg. 1 + 4), with the

@@ -33,7 +33,7 @@ KSC_KERNEL_B_CERT, KSC_KERNEL_B_ANCHOR = 8, 9
 
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
-           "ksc_solve_node", "ksc_solve_batch", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
+           "ksc_solve_node", "ksc_solve_batch", "ksc_bnb_solve", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
            "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
@@ -68,6 +68,19 @@ class ResultC(C.Structure):
                 ("status", C.c_int)]
 
 
+class BnbParams(C.Structure):
+    _fields_ = [("lambda2", C.c_double), ("M", C.c_double), ("k", C.c_int32), ("opt_gap", C.c_double),
+                ("max_nodes", C.c_int64), ("time_limit_s", C.c_double), ("batch", C.c_int32),
+                ("node_rel_gap", C.c_double), ("node_max_iter", C.c_int32)]
+
+
+class BnbResultC(C.Structure):
+    _fields_ = [("beta", C.POINTER(C.c_double)), ("incumbent", C.c_double), ("lower_bound", C.c_double),
+                ("gap", C.c_double), ("nodes", C.c_int64), ("pruned", C.c_int64), ("closed", C.c_int64),
+                ("heuristic_solves", C.c_int64), ("replays", C.c_int64), ("max_open", C.c_int64),
+                ("seconds", C.c_double), ("certified", C.c_int32)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
@@ -83,6 +96,7 @@ def _load():
     L.ksc_solve_node.argtypes = [C.c_void_p, C.POINTER(NodeC), C.POINTER(ResultC), C.c_void_p]
     L.ksc_solve_batch.argtypes = [C.c_void_p, C.POINTER(NodeC), C.c_int32, C.POINTER(ResultC),
                                   C.c_void_p]
+    L.ksc_bnb_solve.argtypes = [C.c_void_p, C.POINTER(BnbParams), C.POINTER(BnbResultC), C.c_void_p]
     L.ksc_prox_g.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, C.c_double, dp, ip]
     L.ksc_g_value.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, dp, dp]
     L.ksc_gstar.argtypes = [dp, C.c_int64, C.c_int32, C.c_double, dp]
@@ -361,6 +375,20 @@ class Problem:
         _check(st, allow)
         return Result(beta, z, res.primal, res.dual_bound, res.rel_gap, res.iters, res.restarts,
                       bool(res.pruned), STATUS_NAMES[res.status if st == KSC_OK else st])
+
+    def bnb(self, lambda2, M, k, opt_gap=1e-4, max_nodes=0, time_limit_s=0.0, batch=256,
+            node_rel_gap=1e-6, node_max_iter=20000):
+        """ksc_bnb_solve: best-first branch and bound over the node relaxations.
+        Returns (incumbent beta, dict of the result fields)."""
+        prm = BnbParams(float(lambda2), float(M), int(k), float(opt_gap), int(max_nodes),
+                        float(time_limit_s), int(batch), float(node_rel_gap), int(node_max_iter))
+        beta = np.zeros(self.p)
+        res = BnbResultC()
+        res.beta = _dptr(beta)
+        _check(lib.ksc_bnb_solve(self.h, C.byref(prm), C.byref(res), _stream_ptr(self.stream)))
+        out = {name: getattr(res, name) for name, _ in BnbResultC._fields_ if name != "beta"}
+        out["certified"] = bool(out["certified"])
+        return beta, out
 
     def solve_batch(self, nodes, want_beta=True, want_z=False,
                     allow=(KSC_OK, KSC_NOT_CONVERGED, KSC_ERR_INFEASIBLE_NODE)):

@@ -94,6 +94,23 @@ def test_struct_layouts_match_header(ksc):
     assert ksc.NodeC.warm_beta.offset == 56 and ksc.NodeC.flags.offset == 84
     assert C.sizeof(ksc.ResultC) == 56
     assert ksc.ResultC.status.offset == 52
+    assert C.sizeof(ksc.BnbParams) == 72
+    assert ksc.BnbParams.opt_gap.offset == 24 and ksc.BnbParams.node_max_iter.offset == 64
+    assert C.sizeof(ksc.BnbResultC) == 96
+    assert ksc.BnbResultC.seconds.offset == 80 and ksc.BnbResultC.certified.offset == 88
+
+
+def test_bnb_arguments_are_rejected_before_cuda(ksc):
+    prm = ksc.BnbParams(0.1, 1.0, 3, 1e-4, 0, 0.0, 64, 1e-6, 1000)
+    res = ksc.BnbResultC()
+    f = ksc.lib.ksc_bnb_solve
+    assert f(None, C.byref(prm), C.byref(res), None) == ksc.KSC_ERR_INVALID_ARG
+    bad = ksc.BnbParams(0.1, 1.0, 3, 1e-4, 0, 0.0, 0, 1e-6, 1000)          # batch 0
+    assert f(C.c_void_p(8), C.byref(bad), C.byref(res), None) == ksc.KSC_ERR_INVALID_ARG
+    bad = ksc.BnbParams(-0.1, 1.0, 3, 1e-4, 0, 0.0, 64, 1e-6, 1000)        # lambda2 < 0
+    assert f(C.c_void_p(8), C.byref(bad), C.byref(res), None) == ksc.KSC_ERR_INVALID_ARG
+    bad = ksc.BnbParams(0.1, 1.0, 4096, 1e-4, 0, 0.0, 64, 1e-6, 1000)      # k beyond capacity
+    assert f(C.c_void_p(8), C.byref(bad), C.byref(res), None) == ksc.KSC_ERR_UNIMPLEMENTED
 
 
 def test_server_arguments_are_rejected_before_cuda(ksc):
