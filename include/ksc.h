@@ -310,6 +310,14 @@ ksc_status ksc_server_destroy(ksc_server* server);
 ksc_status ksc_tc_gemm(const void* A, int32_t pieces, int32_t m, int32_t m_pad, int32_t k, int64_t lda,
                        const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd, int32_t tile_n,
                        void* cuda_stream);
+/* The same product with the stream-K schedule of the batched solver: the
+ * 128 x tile_n tiles times their K blocks of 64 are split evenly over `grid`
+ * persistent CTAs (1..4096); tiles that span several CTAs are summed from FP32
+ * partials in CTA order by a second kernel.  Arguments and errors as
+ * ksc_tc_gemm; m <= 1024.  Allocates (and frees) the partials' device buffer. */
+ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, int32_t m_pad, int32_t k, int64_t lda,
+                          const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd, int32_t tile_n,
+                          int32_t grid, void* cuda_stream);
 
 /* ---- profiling ------------------------------------------------------------ */
 

@@ -391,6 +391,339 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 1) tmem_dealloc(tmem, TCOLS);
 }
 
+// ------------------------------------------------------------------ stream-K
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+constexpr int kSkMaxMTiles = 8;   // M <= 1024
+
+// The work assignment, computed identically by every CTA of both kernels from the
+// tile flags (which do not change between them): active M tiles in order, tiles
+// numbered N-major (CTAs that run at the same time share B tiles in L2), K blocks
+// of every tile consecutive; CTA c owns iterations [c I / G, (c+1) I / G).
+struct SkMap {
+  int act[kSkMaxMTiles];
+  int A, nN, KB, G;
+  int64_t I;
+};
+
+__device__ __forceinline__ void sk_map(const TcShape& sh, const TcEpi& ep, int bn, int G, SkMap& mp) {
+  const int nM = (sh.M + kTcBM - 1) / kTcBM;
+  mp.A = 0;
+  for (int t = 0; t < nM && t < kSkMaxMTiles; ++t)
+    if (ep.tile_active == nullptr || ep.tile_active[t] != 0) mp.act[mp.A++] = t;
+  mp.nN = (sh.N + bn - 1) / bn;
+  mp.KB = (sh.K + kTcBK - 1) / kTcBK;
+  mp.G = G;
+  mp.I = (int64_t)mp.A * mp.nN * mp.KB;
+}
+__device__ __forceinline__ int64_t sk_begin(const SkMap& mp, int c) { return (int64_t)c * mp.I / mp.G; }
+__device__ __forceinline__ int sk_owner(const SkMap& mp, int64_t i) { return (int)(((i + 1) * mp.G - 1) / mp.I); }
+
+// row pointers of the epilogue and one 16-column chunk of it (the same rules as
+// k_tcgemm's epilogue; nc = first column of the chunk, a multiple of 16)
+struct EpiRow {
+  float* orow;
+  const double* brow;
+  double* o64;
+  const double* uin;
+  double* uout;
+  bool ok;
+};
+
+template <int MODE>
+__device__ __forceinline__ EpiRow epi_row(const TcShape& sh, const TcEpi& ep, int m) {
+  EpiRow r{nullptr, nullptr, nullptr, nullptr, nullptr, m < sh.M};
+  if (!r.ok) return r;
+  if (MODE == kTcStore) {
+    r.orow = ep.out + (int64_t)m * ep.ldo;
+  } else if (MODE == kTcAdd) {
+    r.brow = ep.base + (int64_t)m * ep.ldb;
+    r.o64 = ep.out64 + (int64_t)m * ep.ldo;
+  } else {
+    r.brow = ep.base + (int64_t)m * ep.ldb;
+    r.uin = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_in[m] * ep.slot_stride;
+    r.uout = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_out[m] * ep.slot_stride;
+  }
+  return r;
+}
+
+template <int MODE>
+__device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, const EpiRow& r, int m, int nc,
+                                          const float* v, double& fsum, double& dsum) {
+  if (!r.ok || nc >= sh.N) return;
+  if (MODE == kTcStore) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (nc + i < sh.N) r.orow[nc + i] = v[i];
+  } else if (MODE == kTcAdd) {
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i)
+      if (nc + i < sh.N) r.o64[nc + i] = r.brow[nc + i] + (double)v[i];
+  } else {
+    float fa = 0.0f, da = 0.0f;
+    double fd = 0.0;
+#pragma unroll 4
+    for (int i = 0; i < 16; ++i) {
+      if (nc + i < sh.N) {
+        const double uo = r.uin[nc + i];
+        const double un = r.brow[nc + i] + (double)v[i];
+        r.uout[nc + i] = un;
+        const float yi = __ldg(&ep.y[nc + i]);
+        if (ep.loss == kLossLsq) {
+          const double rr = un - (double)yi;
+          fd += rr * rr;
+        } else {
+          fa += loss_term((float)un, yi, ep.loss);
+        }
+        da += loss_change(uo, (float)(un - uo), yi, ep.loss);
+      }
+    }
+    fsum += (double)fa + fd;
+    dsum += (double)da;
+    if (((nc + 16) & 63) == 0 || nc + 16 >= sh.N) {   // one pair of partials per 64 columns
+      double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
+      pp[0] = fsum;
+      pp[1] = dsum;
+      fsum = 0.0;
+      dsum = 0.0;
+    }
+  }
+}
+
+__host__ __device__ constexpr uint32_t tc_tmem_cols2(int BN) {
+  return 2 * BN <= 32 ? 32u : 2 * BN <= 64 ? 64u : 2 * BN <= 128 ? 128u : 2 * BN <= 256 ? 256u : 512u;
+}
+
+// partial tile layout in skws: [slot][chunk of 16 columns][128 rows][16]
+__device__ __forceinline__ float* sk_part(float* ws, int bn, int slot, int chunk, int row) {
+  return ws + (((size_t)slot * (bn / 16) + chunk) * kTcBM + row) * 16;
+}
+
+template <int P, int BN, int MODE>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tcgemm_sk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
+                TcEpi ep) {
+  constexpr int S = tc_stages(P, BN);
+  constexpr uint32_t B_TILE = BN * 128;
+  constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
+  constexpr uint32_t TCOLS = tc_tmem_cols2(BN);
+  static_assert(S >= 2, "at least two pipeline stages");
+  SkMap mp;
+  sk_map(sh, ep, BN, gridDim.x, mp);
+  const int c = blockIdx.x;
+  const int64_t ib = sk_begin(mp, c), ie = sk_begin(mp, c + 1);
+  if (mp.I == 0 || ib >= ie) return;   // nothing to do (uniform over the CTA)
+  const int t_first = (int)(ib / mp.KB);
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + S * P * kTcATile;
+  uint64_t* full = (uint64_t*)(sB + S * B_TILE);
+  uint64_t* empty = full + S;
+  uint64_t* tfull = empty + S;     // [2]: accumulator buffer ready for the epilogue
+  uint64_t* tempty = tfull + 2;    // [2]: epilogue done with the buffer
+  uint64_t* drain = tempty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);
+      mbar_init(&tempty[i], 4);   // one arrive per epilogue warp
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      int64_t g = 0;
+      bool ok = true;
+      for (int64_t i = ib; i < ie && ok;) {
+        const int t = (int)(i / mp.KB), kb0 = (int)(i % mp.KB);
+        const int kb1 = (int)((ie - i) < (int64_t)(mp.KB - kb0) ? kb0 + (ie - i) : mp.KB);
+        const int m0 = mp.act[t % mp.A] * kTcBM, n0 = (t / mp.A) * BN;
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
+          const int s = (int)(g % S);
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+            atomicExch(&g_tc_err, 4);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&full[s], STAGE_TX);
+#pragma unroll
+          for (int q = 0; q < P; ++q)
+            tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * kTcBK, q * sh.Mpad + m0);
+          tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * kTcBK, n0);
+        }
+        i += kb1 - kb0;
+      }
+      if (!ok) {
+        for (int64_t gg = g - S < 0 ? 0 : g - S; gg < g; ++gg) {
+          volatile int never = 0;
+          mbar_wait(&full[gg % S], (uint32_t)(gg / S) & 1u, &never);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = tc_idesc(kTcBM, BN);
+      int64_t g = 0;
+      int sg = 0;
+      bool ok = true;
+      for (int64_t i = ib; i < ie && ok; ++sg) {
+        const int kb0 = (int)(i % mp.KB);
+        const int kb1 = (int)((ie - i) < (int64_t)(mp.KB - kb0) ? kb0 + (ie - i) : mp.KB);
+        const int ab = sg & 1;
+        if (!mbar_wait(&tempty[ab], ((uint32_t)(sg >> 1) & 1u) ^ 1u, abort_flag)) {
+          atomicExch(&g_tc_err, 5);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + (uint32_t)(ab * BN);
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
+          const int s = (int)(g % S);
+          const uint32_t ph = (uint32_t)(g / S) & 1u;
+          if (!mbar_wait(&full[s], ph, abort_flag)) {
+            atomicExch(&g_tc_err, 6);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t b_addr = smem_u32(sB + s * B_TILE);
+#pragma unroll
+          for (int q = 0; q < P; ++q) {
+            const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
+#pragma unroll
+            for (int kk = 0; kk < kTcBK / 16; ++kk)
+              umma_bf16(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                        ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+          }
+          umma_commit(&empty[s]);
+        }
+        if (ok) umma_commit(&tfull[ab]);
+        i += kb1 - kb0;
+      }
+      if (!ok) {
+        umma_commit(drain);
+        volatile int never = 0;
+        mbar_wait(drain, 0, &never);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int qd = warp & 3;   // TMEM lanes 32 qd .. 32 qd + 31
+    const int row = 32 * qd + lane;
+    int sg = 0;
+    for (int64_t i = ib; i < ie; ++sg) {
+      const int t = (int)(i / mp.KB), kb0 = (int)(i % mp.KB);
+      const int kb1 = (int)((ie - i) < (int64_t)(mp.KB - kb0) ? kb0 + (ie - i) : mp.KB);
+      const int m0 = mp.act[t % mp.A] * kTcBM, n0 = (t / mp.A) * BN;
+      const int ab = sg & 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(&tfull[ab], (uint32_t)(sg >> 1) & 1u, abort_flag) ? 1 : 0) != 0;
+      if (!ok) {
+        atomicExch(&g_tc_err, 7);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ab * BN);
+      if (kb0 == 0 && kb1 == mp.KB) {   // the whole tile: the epilogue
+        const int m = m0 + row;
+        const EpiRow er = epi_row<MODE>(sh, ep, m);
+        double fsum = 0.0, dsum = 0.0;
+#pragma unroll 1
+        for (int cc = 0; cc < BN; cc += 16) {
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)cc, v);
+          epi_chunk<MODE>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
+        }
+      } else {                          // part of the tile: FP32 partial for the fix-up kernel
+        const int slot = t == t_first ? 2 * c : 2 * c + 1;
+#pragma unroll 1
+        for (int cc = 0; cc < BN; cc += 16) {
+          float v[16];
+          tmem_ld16(tbase + (uint32_t)cc, v);
+          float4* dst = reinterpret_cast<float4*>(sk_part(ep.skws, BN, slot, cc / 16, row));
+#pragma unroll
+          for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[ab]);
+      i += kb1 - kb0;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
+// the tiles whose K blocks span several CTAs: one CTA per CTA boundary inside a
+// tile (the first such boundary of each tile does its work), summing the partial
+// tiles in CTA order and applying the epilogue
+template <int BN, int MODE>
+__global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int G) {
+  SkMap mp;
+  sk_map(sh, ep, BN, G, mp);
+  const int c = blockIdx.x + 1;
+  if (mp.I == 0 || c >= G) return;
+  const int64_t b = sk_begin(mp, c);
+  if (b >= mp.I || b % mp.KB == 0) return;
+  const int t = (int)(b / mp.KB);
+  const int64_t t0 = (int64_t)t * mp.KB;
+  if (sk_begin(mp, c - 1) > t0) return;   // an earlier boundary lies inside this tile
+  const int clo = sk_owner(mp, t0), chi = sk_owner(mp, t0 + mp.KB - 1);
+  const int m0 = mp.act[t % mp.A] * kTcBM, n0 = (t / mp.A) * BN;
+  const int row = threadIdx.x;
+  const int m = m0 + row;
+  const EpiRow er = epi_row<MODE>(sh, ep, m);
+  double fsum = 0.0, dsum = 0.0;
+  for (int cc = 0; cc < BN; cc += 16) {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = 0.0f;
+    for (int q = clo; q <= chi; ++q) {
+      if (sk_begin(mp, q) == sk_begin(mp, q + 1)) continue;   // an empty range (fewer iterations than CTAs)
+      const int slot = sk_begin(mp, q) >= t0 ? 2 * q : 2 * q + 1;
+      const float4* src = reinterpret_cast<const float4*>(sk_part(ep.skws, BN, slot, cc / 16, row));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 x = src[j];
+        v[4 * j] += x.x;
+        v[4 * j + 1] += x.y;
+        v[4 * j + 2] += x.z;
+        v[4 * j + 3] += x.w;
+      }
+    }
+    epi_chunk<MODE>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
+  }
+}
+
 // ------------------------------------------------------------------ host
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -450,19 +783,43 @@ bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t
   plan->K = K;
   plan->bn = bn;
   plan->ok = 1;
+  plan->sk = 0;
+  plan->grid = 0;
   return true;
 }
 
+bool tc_plan_stream_k(TcPlan* plan, int grid, const char** why) {
+  if (!plan->ok) { *why = "plan the product first"; return false; }
+  if (plan->M > kSkMaxMTiles * kTcBM) { *why = "stream-K schedule takes M <= 1024"; return false; }
+  if (grid < 1) { *why = "grid must be >= 1"; return false; }
+  plan->sk = 1;
+  plan->grid = grid;
+  return true;
+}
+
+size_t tc_skws_floats(int grid, int bn) { return (size_t)2 * grid * kTcBM * bn; }
+
 template <int P, int BN, int MODE>
 static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
-  static bool attr = false;
   constexpr int bytes = tc_smem_bytes(P, BN);
+  TcShape sh{g.M, g.Mpad, g.N, g.K};
+  if (g.sk) {
+    static bool attr_sk = false;
+    if (!attr_sk) {
+      cudaFuncSetAttribute(k_tcgemm_sk<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      attr_sk = true;
+    }
+    k_tcgemm_sk<P, BN, MODE><<<g.grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA,
+                                                              *(const CUtensorMap*)g.tmB, sh, e);
+    if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<g.grid - 1, kTcBM, 0, s>>>(sh, e, g.grid);
+    return;
+  }
+  static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tcgemm<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + kTcBM - 1) / kTcBM);
-  TcShape sh{g.M, g.Mpad, g.N, g.K};
   k_tcgemm<P, BN, MODE><<<grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA, *(const CUtensorMap*)g.tmB,
                                                         sh, e);
 }

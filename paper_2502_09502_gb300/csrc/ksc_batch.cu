@@ -33,6 +33,9 @@ struct BatchWs {
   int ldp = 0, ldn = 0;
   int B = -1;        // nodes of the current plans and graphs
   int bn_fwd = 0, bn_grad = 0;
+  int sk_fwd = 0, sk_grad = 0;   // stream-K schedule chosen for each product
+  int nsm = 0;                   // SMs (persistent CTAs of a stream-K product)
+  float* skws = nullptr;         // stream-K partial tiles (shared by both products)
   std::vector<void*> allocs;
   size_t bytes = 0;
   BatchDev bd{};
@@ -100,6 +103,13 @@ bool batch_supported(const ksc_problem* pr) { return pr->xdt == kXBF16; }
 
 int pad8(int64_t v) { return (int)((v + 7) / 8 * 8); }
 
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  return n;
+}
+
 bool needs_xcopy(const ksc_problem* pr) { return !((pr->ldx * 2) % 16 == 0 && ((uintptr_t)pr->X % 16) == 0); }
 
 // workspace bytes for `need` slots (the allocations of alloc_ws)
@@ -119,6 +129,7 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   b += 2 * Bc * ldn * 8 + Bc * ldp * 8 + Bc * batch_nrt((int)n) * 32;   // certificate vectors
   b += kDfWsElems * 8;                          // split partials of the exact product
   b += (size_t)(Bc + 127) / 128 * 4;            // tile flags
+  b += tc_skws_floats(sm_count(), 256) * 4;     // stream-K partial tiles
   if (p > 2048) b += Bc * ldp * 8;              // prox scratch
   if (needs_xcopy(pr)) b += n * ldp * 2;
   return b;
@@ -166,6 +177,8 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
   BA(d.cpart, (size_t)Bc * batch_nrt(n) * 4 * 8);
   BA(d.dfws, kDfWsElems * 8);
   BA(d.tile_run, (size_t)(Bc + 127) / 128 * 4);
+  ws->nsm = sm_count();
+  BA(ws->skws, tc_skws_floats(ws->nsm, 256) * 4);
   KB_CUDA(cudaMemsetAsync(d.tile_run, 1, (size_t)(Bc + 127) / 128 * 4, s));   // nonzero: run every tile
   d.colnorm = pr->dev.colnorm;
   float* yf = nullptr;
@@ -232,6 +245,7 @@ TcEpi fwd_epi(const BatchWs* ws) {
   e.npart = d.nft;
   e.part = d.fpart;
   e.tile_active = d.tile_run;
+  e.skws = ws->skws;
   return e;
 }
 
@@ -243,6 +257,7 @@ TcEpi grad_epi(const BatchWs* ws) {
   e.out64 = d.G;
   e.ldo = d.ldp;
   e.tile_active = d.tile_run;
+  e.skws = ws->skws;
   return e;
 }
 
@@ -306,38 +321,47 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   KB_CUDA(cudaEventCreate(&e0));
   KB_CUDA(cudaEventCreate(&e1));
   float best_f = 1e30f, best_g = 1e30f;
-  int bf = 128, bg = 128;
+  int bf = 128, bg = 128, sf = 0, sg = 0;
   std::vector<int> two(B, 2), zero(B, 0);
   KB_CUDA(cudaMemcpyAsync(d.slot_new, two.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
   KB_CUDA(cudaMemcpyAsync(d.slot_cur, zero.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
+  // tile width x schedule (one CTA per tile, or stream-K over the SMs)
   for (int bn : kTcBNs) {
-    if (!make(bn, bn)) {
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
-      return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
+    for (int sk = 0; sk < 2; ++sk) {
+      bool ok = make(bn, bn);
+      if (ok && sk) ok = tc_plan_stream_k(&ws->fwd, ws->nsm, &why) && tc_plan_stream_k(&ws->grad, ws->nsm, &why);
+      if (!ok) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
+      }
+      for (int rep = 0; rep < 3; ++rep) {
+        float ms = 0.f;
+        KB_CUDA(cudaEventRecord(e0, s));
+        tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
+        KB_CUDA(cudaEventRecord(e1, s));
+        KB_CUDA(cudaEventSynchronize(e1));
+        KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && ms < best_f) { best_f = ms; bf = bn; sf = sk; }
+        KB_CUDA(cudaEventRecord(e0, s));
+        tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
+        KB_CUDA(cudaEventRecord(e1, s));
+        KB_CUDA(cudaEventSynchronize(e1));
+        KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rep > 0 && ms < best_g) { best_g = ms; bg = bn; sg = sk; }
+      }
+      pr->launches += sk ? 12 : 6;
     }
-    for (int rep = 0; rep < 3; ++rep) {
-      float ms = 0.f;
-      KB_CUDA(cudaEventRecord(e0, s));
-      tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
-      KB_CUDA(cudaEventRecord(e1, s));
-      KB_CUDA(cudaEventSynchronize(e1));
-      KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0 && ms < best_f) { best_f = ms; bf = bn; }
-      KB_CUDA(cudaEventRecord(e0, s));
-      tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
-      KB_CUDA(cudaEventRecord(e1, s));
-      KB_CUDA(cudaEventSynchronize(e1));
-      KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (rep > 0 && ms < best_g) { best_g = ms; bg = bn; }
-    }
-    pr->launches += 6;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (!make(bf, bg)) return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
+  if (!make(bf, bg) || (sf && !tc_plan_stream_k(&ws->fwd, ws->nsm, &why)) ||
+      (sg && !tc_plan_stream_k(&ws->grad, ws->nsm, &why)))
+    return api_fail(KSC_ERR_INVALID_ARG, std::string("batched products: ") + why);
   ws->bn_fwd = bf;
   ws->bn_grad = bg;
+  ws->sk_fwd = sf;
+  ws->sk_grad = sg;
   ksc_status st;
   if ((st = capture(ws, false)) != KSC_OK) return st;
   if ((st = capture(ws, true)) != KSC_OK) return st;
@@ -578,7 +602,7 @@ bool session_advance(Session* se, ksc_status* st) {
     *st = api_fail(KSC_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     return false;
   }
-  pr->launches += (int64_t)kLaunchesPerBatchStep * kBatchStepsPerGraph;
+  pr->launches += (int64_t)(kLaunchesPerBatchStep + se->ws->sk_fwd + se->ws->sk_grad) * kBatchStepsPerGraph;
   return true;
 }
 

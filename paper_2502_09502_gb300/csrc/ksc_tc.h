@@ -46,6 +46,7 @@ struct TcEpi {
   int npart;
   double* part;
   const int* tile_active;   // per 128-row M tile: 0 = every row finished, skip the tile (NULL: none)
+  float* skws;              // stream-K partial tiles: 2 * grid * 128 * BN floats (stream-K plans only)
 };
 
 struct TcPlan {
@@ -53,7 +54,19 @@ struct TcPlan {
   alignas(64) unsigned char tmB[128];   // CUtensorMap of B
   int P, M, Mpad, N, K, bn;
   int ok;
+  int sk;      // 1: stream-K schedule over `grid` persistent CTAs (M <= 1024)
+  int grid;
 };
+
+// Stream-K schedule (tc_plan_stream_k): the active 128 x BN tiles times their
+// K blocks of 64 form one iteration space, split evenly over `grid` CTAs (one per
+// SM).  A CTA runs its range tile by tile with a double-buffered TMEM accumulator,
+// so the epilogue of one tile overlaps the products of the next; a tile whose
+// K blocks span several CTAs leaves FP32 partial tiles in skws, summed in CTA
+// order by a second kernel that applies the epilogue.  Every tile of a launch is
+// then processed once and every SM works until the end of the launch.
+bool tc_plan_stream_k(TcPlan* plan, int grid, const char** why);
+size_t tc_skws_floats(int grid, int bn);
 
 // tile widths (columns of B per CTA) the kernel is built for
 constexpr int kTcBNs[3] = {64, 128, 256};

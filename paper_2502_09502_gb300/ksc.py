@@ -35,7 +35,7 @@ KSC_KERNEL_B_CERT, KSC_KERNEL_B_ANCHOR = 8, 9
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_bnb_solve", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
-           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm",
+           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
            "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state",
            "ksc_last_error", "ksc_version"]
@@ -112,6 +112,9 @@ def _load():
     L.ksc_tc_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                               C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.c_void_p]
+    L.ksc_tc_gemm_sk.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                 C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
+                                 C.c_int32, C.c_void_p]
     L.ksc_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)]
     L.ksc_server_submit.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(NodeC), C.POINTER(C.c_uint64)]
     L.ksc_server_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(ResultC), C.c_int32]
@@ -245,6 +248,13 @@ def ksc_tc_gemm(a_ptr, pieces, m, m_pad, k, lda, b_ptr, n, ldb, d_ptr, ldd, tile
     _check(lib.ksc_tc_gemm(C.c_void_p(a_ptr), int(pieces), int(m), int(m_pad), int(k), int(lda),
                            C.c_void_p(b_ptr), int(n), int(ldb), C.c_void_p(d_ptr), int(ldd),
                            int(tile_n), _stream_ptr(stream)))
+
+
+def ksc_tc_gemm_sk(a_ptr, pieces, m, m_pad, k, lda, b_ptr, n, ldb, d_ptr, ldd, tile_n, grid, stream=None):
+    """Stream-K tensor-core product on device buffers (see include/ksc.h); blocks until done."""
+    _check(lib.ksc_tc_gemm_sk(C.c_void_p(a_ptr), int(pieces), int(m), int(m_pad), int(k), int(lda),
+                              C.c_void_p(b_ptr), int(n), int(ldb), C.c_void_p(d_ptr), int(ldd),
+                              int(tile_n), int(grid), _stream_ptr(stream)))
 
 
 def ksc_problem_profile(h, enable: bool):

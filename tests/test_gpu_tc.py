@@ -23,7 +23,7 @@ def K():
     return ksc
 
 
-def _run(K, pieces, m, m_pad, k, lda, n, ldb, tile_n, seed):
+def _run(K, pieces, m, m_pad, k, lda, n, ldb, tile_n, seed, grid=0):
     gen = torch.Generator().manual_seed(seed)
     A = torch.randn(pieces, m_pad, lda, generator=gen).to(torch.bfloat16)
     B = torch.randn(n, ldb, generator=gen).to(torch.bfloat16)
@@ -33,8 +33,12 @@ def _run(K, pieces, m, m_pad, k, lda, n, ldb, tile_n, seed):
     ldd = (n + 3) // 4 * 4
     Ad, Bd = A.cuda(), B.cuda()
     D = torch.full((m, ldd), float("nan"), device="cuda", dtype=torch.float32)
-    K.ksc_tc_gemm(Ad.data_ptr(), pieces, m, m_pad, k, lda, Bd.data_ptr(), n, ldb, D.data_ptr(), ldd,
-                  tile_n)
+    if grid:
+        K.ksc_tc_gemm_sk(Ad.data_ptr(), pieces, m, m_pad, k, lda, Bd.data_ptr(), n, ldb, D.data_ptr(), ldd,
+                         tile_n, grid)
+    else:
+        K.ksc_tc_gemm(Ad.data_ptr(), pieces, m, m_pad, k, lda, Bd.data_ptr(), n, ldb, D.data_ptr(), ldd,
+                      tile_n)
     torch.cuda.synchronize()
     a = A[:, :m, :k].double()
     b = B[:, :k].double()
@@ -76,3 +80,29 @@ def test_tc_gemm_rejects_bad_shapes(K):
         K.ksc_tc_gemm(A.data_ptr(), 1, 128, 128, 60, 60, B.data_ptr(), 64, 64, D.data_ptr(), 64, 64)
     with pytest.raises(K.KscError):   # tile width
         K.ksc_tc_gemm(A.data_ptr(), 1, 128, 128, 64, 64, B.data_ptr(), 64, 64, D.data_ptr(), 64, 96)
+
+
+# stream-K: tiles split over CTAs at any K block, partials summed by the fix-up
+# kernel; grids from 1 (everything in one CTA, several tiles and both TMEM
+# buffers) to more CTAs than K blocks (empty ranges, tiles spread over many CTAs)
+SK_CASES = [
+    # pieces, m, m_pad, k, lda, n, ldb, tile_n, grid
+    (1, 128, 128, 640, 640, 300, 640, 64, 1),
+    (3, 200, 256, 777, 784, 1000, 784, 256, 3),
+    (3, 512, 512, 5000, 5000, 1000, 5000, 128, 152),
+    (2, 384, 384, 2000, 2000, 777, 2008, 64, 7),
+    (1, 1, 128, 40, 40, 17, 40, 64, 5),
+    (3, 1024, 1024, 3000, 3000, 700, 3000, 256, 152),
+    (3, 130, 256, 10000, 10000, 530, 10000, 128, 64),
+    (1, 128, 128, 128, 128, 64, 128, 64, 400),
+]
+
+
+@pytest.mark.parametrize("case", SK_CASES, ids=lambda c: "P{}m{}k{}n{}bn{}g{}".format(c[0], c[1], c[3], c[5], c[7], c[8]))
+def test_tc_gemm_stream_k_matches_fp64_product(K, case):
+    pieces, m, m_pad, k, lda, n, ldb, tile_n, grid = case
+    got, ref, mag = _run(K, pieces, m, m_pad, k, lda, n, ldb, tile_n, seed=sum(case), grid=grid)
+    assert torch.isfinite(got).all()
+    bound = (k * pieces + 2) * U32 * mag + 1e-30
+    err = (got - ref).abs()
+    assert (err <= bound).all(), float((err / bound).max())
