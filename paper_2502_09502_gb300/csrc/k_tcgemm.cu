@@ -454,14 +454,56 @@ template <int MODE>
 __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, const EpiRow& r, int m, int nc,
                                           const float* v, double& fsum, double& dsum) {
   if (!r.ok || nc >= sh.N) return;
+  const bool whole = nc + 16 <= sh.N;   // rows are 64-byte aligned (strides padded to 8 elements)
   if (MODE == kTcStore) {
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       if (nc + i < sh.N) r.orow[nc + i] = v[i];
   } else if (MODE == kTcAdd) {
+    if (whole) {
+      const double2* b2 = reinterpret_cast<const double2*>(r.brow + nc);
+      double2* o2 = reinterpret_cast<double2*>(r.o64 + nc);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const double2 b = b2[i];
+        o2[i] = make_double2(b.x + (double)v[2 * i], b.y + (double)v[2 * i + 1]);
+      }
+    } else {
 #pragma unroll 4
-    for (int i = 0; i < 16; ++i)
-      if (nc + i < sh.N) r.o64[nc + i] = r.brow[nc + i] + (double)v[i];
+      for (int i = 0; i < 16; ++i)
+        if (nc + i < sh.N) r.o64[nc + i] = r.brow[nc + i] + (double)v[i];
+    }
+  } else if (whole) {
+    float fa = 0.0f, da = 0.0f;
+    double fd = 0.0;
+    const double2* u2 = reinterpret_cast<const double2*>(r.uin + nc);
+    const double2* b2 = reinterpret_cast<const double2*>(r.brow + nc);
+    double2* w2 = reinterpret_cast<double2*>(r.uout + nc);
+    const float4* y4 = reinterpret_cast<const float4*>(ep.y + nc);
+#pragma unroll 2
+    for (int i = 0; i < 8; ++i) {
+      const double2 uo = u2[i], b = b2[i];
+      const float4 yq = __ldg(&y4[i >> 1]);
+      const float y0 = (i & 1) ? yq.z : yq.x, y1 = (i & 1) ? yq.w : yq.y;
+      const double un0 = b.x + (double)v[2 * i], un1 = b.y + (double)v[2 * i + 1];
+      w2[i] = make_double2(un0, un1);
+      if (ep.loss == kLossLsq) {
+        const double r0 = un0 - (double)y0, r1 = un1 - (double)y1;
+        fd += r0 * r0 + r1 * r1;
+      } else {
+        fa += loss_term((float)un0, y0, ep.loss) + loss_term((float)un1, y1, ep.loss);
+      }
+      da += loss_change(uo.x, (float)(un0 - uo.x), y0, ep.loss) + loss_change(uo.y, (float)(un1 - uo.y), y1, ep.loss);
+    }
+    fsum += (double)fa + fd;
+    dsum += (double)da;
+    if (((nc + 16) & 63) == 0 || nc + 16 >= sh.N) {
+      double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
+      pp[0] = fsum;
+      pp[1] = dsum;
+      fsum = 0.0;
+      dsum = 0.0;
+    }
   } else {
     float fa = 0.0f, da = 0.0f;
     double fd = 0.0;
@@ -502,8 +544,13 @@ __device__ __forceinline__ float* sk_part(float* ws, int bn, int slot, int chunk
   return ws + (((size_t)slot * (bn / 16) + chunk) * kTcBM + row) * 16;
 }
 
+// epilogue warps of the stream-K kernel: two per TMEM lane quadrant (each on half
+// of the columns, a multiple of 64) when the tile is at least 128 wide
+__host__ __device__ constexpr int sk_epi_warps(int BN) { return BN >= 128 ? 8 : 4; }
+__host__ __device__ constexpr int sk_threads(int BN) { return 64 + 32 * sk_epi_warps(BN); }
+
 template <int P, int BN, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(sk_threads(BN), 1)
     k_tcgemm_sk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
                 TcEpi ep) {
   constexpr int S = tc_stages(P, BN);
@@ -538,7 +585,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);   // one arrive per epilogue warp
+      mbar_init(&tempty[i], sk_epi_warps(BN));   // one arrive per epilogue warp
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -635,7 +682,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     __syncwarp();
   } else {
-    const int qd = warp & 3;   // TMEM lanes 32 qd .. 32 qd + 31
+    constexpr int EW = sk_epi_warps(BN);
+    constexpr int CW = BN * 4 / EW;      // columns per epilogue warp
+    const int qd = warp & 3;             // TMEM lanes 32 qd .. 32 qd + 31
+    const int c_lo = ((warp - 2) / 4) * CW;
     const int row = 32 * qd + lane;
     int sg = 0;
     for (int64_t i = ib; i < ie; ++sg) {
@@ -656,7 +706,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const EpiRow er = epi_row<MODE>(sh, ep, m);
         double fsum = 0.0, dsum = 0.0;
 #pragma unroll 1
-        for (int cc = 0; cc < BN; cc += 16) {
+        for (int cc = c_lo; cc < c_lo + CW; cc += 16) {
           float v[16];
           tmem_ld16(tbase + (uint32_t)cc, v);
           epi_chunk<MODE>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
@@ -664,7 +714,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       } else {                          // part of the tile: FP32 partial for the fix-up kernel
         const int slot = t == t_first ? 2 * c : 2 * c + 1;
 #pragma unroll 1
-        for (int cc = 0; cc < BN; cc += 16) {
+        for (int cc = c_lo; cc < c_lo + CW; cc += 16) {
           float v[16];
           tmem_ld16(tbase + (uint32_t)cc, v);
           float4* dst = reinterpret_cast<float4*>(sk_part(ep.skws, BN, slot, cc / 16, row));
@@ -809,7 +859,7 @@ static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
       cudaFuncSetAttribute(k_tcgemm_sk<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       attr_sk = true;
     }
-    k_tcgemm_sk<P, BN, MODE><<<g.grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA,
+    k_tcgemm_sk<P, BN, MODE><<<g.grid, sk_threads(BN), bytes, s>>>(*(const CUtensorMap*)g.tmA,
                                                               *(const CUtensorMap*)g.tmB, sh, e);
     if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<g.grid - 1, kTcBM, 0, s>>>(sh, e, g.grid);
     return;
