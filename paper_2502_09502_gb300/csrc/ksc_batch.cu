@@ -436,8 +436,7 @@ ksc_status anchor(Session* se, const std::vector<int>& list, bool init) {
   se->pr->launches += tiled ? kLaunchesPerAnchor + (dfprod_splits(cnt, d.n) > 1) + (dfprod_splits(cnt, d.p) > 1)
                              : 2 + 2 * cnt;
   se->anchors += cnt;
-  KB_CUDA(cudaStreamSynchronize(s));   // the list buffer is reused by the next anchor
-  return KSC_OK;
+  return KSC_OK;   // the list buffer's next upload is ordered after these kernels
 }
 
 }  // namespace
@@ -530,48 +529,65 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
   const size_t ldp = ws->ldp;
   cudaStream_t s = se->s;
   BNode* hn = hnodes(se);
-  std::vector<int8_t> hs(ldp);
-  std::vector<double> hb(ldp);
+  // the nodes' state and warm-start rows are staged on the host in chunks of at
+  // most 64 MB; each run of consecutive slots goes to the device in one copy per
+  // array (a pageable source is staged by the copy before it returns, so the
+  // buffers can be refilled without waiting for the device)
+  const int chunk = (int)std::max<size_t>(1, ((size_t)64 << 20) / (ldp * 9));
+  std::vector<int8_t> hs;
+  std::vector<double> hb;
   int next = 0;
-  for (int i = 0; i < cnt; ++i) {
-    while (se->slot[next].busy) ++next;
-    const int b = next++;
-    slots->push_back(b);
-    const ksc_node* nd = nodes[i];
-    const NodeSetup& setup = *ns[i];
-    std::fill(hs.begin(), hs.end(), (int8_t)kZero);
-    std::memcpy(hs.data(), setup.state.data(), p);
-    std::fill(hb.begin(), hb.end(), 0.0);
-    if (nd->warm_beta)
-      for (int j = 0; j < p; ++j)
-        hb[j] = setup.state[j] == kZero ? 0.0 : std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
-    BNode& h = hn[b];
-    std::memset(&h, 0, sizeof h);
-    h.lambda2 = nd->lambda2;
-    h.M = nd->M;
-    h.rho = pr->L / (2.0 * nd->lambda2);
-    h.invL = 1.0 / pr->L;
-    h.tol_loop = nd->rel_gap_tol;
-    h.incumbent = nd->incumbent;
-    h.kp = setup.kp;
-    h.max_iter = nd->max_iter;
-    h.restart_on = (nd->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
-    h.momentum_on = (nd->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;
-    h.done = kSlotIdle;   // k_binit_node starts it
-    h.cur = 1;
-    h.prev = 0;
-    SlotHost& sl = se->slot[b];
-    sl = SlotHost();
-    sl.busy = true;
-    sl.want_z = want_z[i];
-    sl.tol = nd->rel_gap_tol;
-    sl.inc = nd->incumbent;
-    sl.anchor_gap = std::max(1e-3, 100.0 * nd->rel_gap_tol);
-    // pageable sources: each copy completes before the host buffers are reused
-    KB_CUDA(cudaMemcpyAsync((void*)(d.state + (size_t)b * ldp), hs.data(), ldp, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaMemcpyAsync(d.beta + ((size_t)b * 3 + 1) * ldp, hb.data(), ldp * 8, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaMemcpyAsync(d.nodes + b, &h, sizeof h, cudaMemcpyHostToDevice, s));
-    KB_CUDA(cudaStreamSynchronize(s));
+  for (int c0 = 0; c0 < cnt; c0 += chunk) {
+    const int cn = std::min(chunk, cnt - c0);
+    hs.assign((size_t)cn * ldp, (int8_t)kZero);
+    hb.assign((size_t)cn * ldp, 0.0);
+    for (int i = c0; i < c0 + cn; ++i) {
+      while (se->slot[next].busy) ++next;
+      const int b = next++;
+      slots->push_back(b);
+      const ksc_node* nd = nodes[i];
+      const NodeSetup& setup = *ns[i];
+      int8_t* hsr = hs.data() + (size_t)(i - c0) * ldp;
+      double* hbr = hb.data() + (size_t)(i - c0) * ldp;
+      std::memcpy(hsr, setup.state.data(), p);
+      if (nd->warm_beta)
+        for (int j = 0; j < p; ++j)
+          hbr[j] = setup.state[j] == kZero ? 0.0 : std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
+      BNode& h = hn[b];
+      std::memset(&h, 0, sizeof h);
+      h.lambda2 = nd->lambda2;
+      h.M = nd->M;
+      h.rho = pr->L / (2.0 * nd->lambda2);
+      h.invL = 1.0 / pr->L;
+      h.tol_loop = nd->rel_gap_tol;
+      h.incumbent = nd->incumbent;
+      h.kp = setup.kp;
+      h.max_iter = nd->max_iter;
+      h.restart_on = (nd->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
+      h.momentum_on = (nd->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;
+      h.done = kSlotIdle;   // k_binit_node starts it
+      h.cur = 1;
+      h.prev = 0;
+      SlotHost& sl = se->slot[b];
+      sl = SlotHost();
+      sl.busy = true;
+      sl.want_z = want_z[i];
+      sl.tol = nd->rel_gap_tol;
+      sl.inc = nd->incumbent;
+      sl.anchor_gap = std::max(1e-3, 100.0 * nd->rel_gap_tol);
+    }
+    for (int i0 = c0; i0 < c0 + cn;) {
+      int i1 = i0 + 1;
+      while (i1 < c0 + cn && (*slots)[i1] == (*slots)[i1 - 1] + 1) ++i1;
+      const int b0 = (*slots)[i0];
+      const size_t run = (size_t)(i1 - i0);
+      KB_CUDA(cudaMemcpyAsync((void*)(d.state + (size_t)b0 * ldp), hs.data() + (size_t)(i0 - c0) * ldp, run * ldp,
+                              cudaMemcpyHostToDevice, s));
+      KB_CUDA(cudaMemcpy2DAsync(d.beta + ((size_t)b0 * 3 + 1) * ldp, 3 * ldp * 8, hb.data() + (size_t)(i0 - c0) * ldp,
+                                ldp * 8, ldp * 8, run, cudaMemcpyHostToDevice, s));
+      KB_CUDA(cudaMemcpyAsync(d.nodes + b0, hn + b0, run * sizeof(BNode), cudaMemcpyHostToDevice, s));
+      i0 = i1;
+    }
   }
   KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
   launch_binit_copy(d, ws->dlist, cnt, s);
@@ -582,8 +598,7 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
   launch_binit_node(d, ws->dlist, cnt, s);
   pr->launches += 1;
   KB_CUDA(cudaGetLastError());
-  KB_CUDA(cudaStreamSynchronize(s));
-  return KSC_OK;
+  return KSC_OK;   // stream order: the next replay runs after the admission
 }
 
 bool session_advance(Session* se, ksc_status* st) {
@@ -722,8 +737,7 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
   anchor_phase.count = (int)(se->anchors - anchors0);
   anchor_phase.end();
   KB_CUDA(cudaGetLastError());
-  KB_CUDA(cudaStreamSynchronize(s));
-  return KSC_OK;
+  return KSC_OK;   // the anchors run while the host fetches results and launches the next replay
 }
 
 ksc_status session_fetch(Session* se, int b, ksc_result* r) {
@@ -746,7 +760,9 @@ ksc_status session_fetch(Session* se, int b, ksc_result* r) {
   BNode idle = h;
   idle.done = kSlotIdle;
   KB_CUDA(cudaMemcpyAsync(d.nodes + b, &idle, sizeof idle, cudaMemcpyHostToDevice, se->s));
-  KB_CUDA(cudaStreamSynchronize(se->s));
+  // the caller's arrays may be pinned (then the copies are asynchronous): results
+  // must be in host memory on return
+  if (r->beta || r->z) KB_CUDA(cudaStreamSynchronize(se->s));
   hnodes(se)[b] = idle;
   sl = SlotHost();
   return KSC_OK;
@@ -815,6 +831,25 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       if ((st = session_collect(&se, &fin)) != KSC_OK) return st;
     }
     if (g0 == 0) pr->batch_state.assign((size_t)count * 10, NAN);
+    // the certified iterates (and relaxed z) of the whole group in one copy each
+    bool any_beta = false, any_z = false;
+    int smax = 0;
+    for (int i = 0; i < cnt; ++i) {
+      any_beta |= results[batch[g0 + i]].beta != nullptr;
+      any_z |= results[batch[g0 + i]].z != nullptr;
+      smax = std::max(smax, slots[i] + 1);
+    }
+    std::vector<double> hbeta, hz;
+    const size_t pp = (size_t)pr->p;
+    if (any_beta) {
+      hbeta.resize((size_t)smax * pp);
+      KB_CUDA(cudaMemcpyAsync(hbeta.data(), se.ws->bd.beta_out, hbeta.size() * 8, cudaMemcpyDeviceToHost, s));
+    }
+    if (any_z) {
+      hz.resize((size_t)smax * pp);
+      KB_CUDA(cudaMemcpyAsync(hz.data(), se.ws->bd.z_out, hz.size() * 8, cudaMemcpyDeviceToHost, s));
+    }
+    if (any_beta || any_z) KB_CUDA(cudaStreamSynchronize(s));
     for (int i = 0; i < cnt; ++i) {
       const int idx = batch[g0 + i];
       const BNode& h = hnodes(&se)[slots[i]];
@@ -830,7 +865,17 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       bs[8] = h.iter - 1;
       bs[9] = hcerts(&se)[slots[i]].gap;
       fallbacks += h.fallback;
-      if ((st = session_fetch(&se, slots[i], &results[idx])) != KSC_OK) return st;
+      ksc_result* rr = &results[idx];
+      double* ub = rr->beta;
+      double* uz = rr->z;
+      rr->beta = nullptr;
+      rr->z = nullptr;
+      st = session_fetch(&se, slots[i], rr);
+      rr->beta = ub;
+      rr->z = uz;
+      if (st != KSC_OK) return st;
+      if (ub) std::memcpy(ub, hbeta.data() + (size_t)slots[i] * pp, pp * 8);
+      if (uz) std::memcpy(uz, hz.data() + (size_t)slots[i] * pp, pp * 8);
       iters += results[idx].iters;
       if (first == KSC_OK && results[idx].status != KSC_OK) first = results[idx].status;
     }
