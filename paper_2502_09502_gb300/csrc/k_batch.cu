@@ -214,16 +214,21 @@ __global__ void __launch_bounds__(256) k_binit_copy(BatchDev d, const int* list)
   }
 }
 
-// u^0 = u^1 = u_ref (set by the anchor), F(u^1) in FP64, g(beta^1) (Alg. 2),
-// L^1 = F(u^1) + 2 lambda2 g(beta^1)  (Algorithm 3 line 2)
-__global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const int* list) {
+// u^0 = u^1 = u_ref (set by the anchor) -- or, after the zero anchor, u^1 from the
+// admission product in slot 1, copied to slot 0 --, F(u^1) in FP64, g(beta^1)
+// (Alg. 2), L^1 = F(u^1) + 2 lambda2 g(beta^1)  (Algorithm 3 line 2)
+__global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const int* list, int zero) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = list[blockIdx.x];
   BNode* nd = d.nodes + b;
   SegSmem<double> sm = carve_seg_smem<double>(smem, kBatchCap, 0);
-  const double* ur = d.u_ref + (size_t)b * d.ldn;
+  double* U = d.U + (size_t)b * 3 * d.ldn;
+  const double* ur = zero ? U + d.ldn : d.u_ref + (size_t)b * d.ldn;
   double f = 0.0;
-  for (int i = threadIdx.x; i < d.n; i += kBProxBlock) f += loss_d(ur[i], d.y[i], d.loss);
+  for (int i = threadIdx.x; i < d.n; i += kBProxBlock) {
+    f += loss_d(ur[i], d.y[i], d.loss);
+    if (zero) U[i] = ur[i];
+  }
   f = block_sum<double, kBProxBlock>(f, sm.red);
   const double* b1 = d.beta + ((size_t)b * 3 + 1) * d.ldp;
   const int8_t* st = d.state + (size_t)b * d.ldp;
@@ -255,6 +260,45 @@ __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const in
 }
 
 // ------------------------------------------------------------------ anchors
+
+// The zero anchor of an admission: beta_ref = 0, u_ref = X 0 = 0 exactly,
+// r_ref = grad F(0), G_ref = X^T grad F(0) (the same for every node: computed
+// once per workspace, exactly), and the BF16 pieces of beta^1 - 0 for the
+// admission's forward product u^1 = X beta^1 (FP32 accumulation; the node's first
+// exact anchor comes when its gap falls to the anchor threshold).
+__global__ void __launch_bounds__(256) k_bzero_anchor(BatchDev d, const int* list, const double* r0,
+                                                      const double* G0) {
+  const int b = list[blockIdx.y];
+  const size_t pstride = (size_t)d.Bpad * d.ldp;
+  const double* b1 = d.beta + ((size_t)b * 3 + 1) * d.ldp;
+  for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
+    d.beta_ref[(size_t)b * d.ldp + j] = 0.0;
+    d.G_ref[(size_t)b * d.ldp + j] = G0[j];
+    split_store((float)b1[j], d.bpc + (size_t)b * d.ldp + j, pstride, d.P);
+  }
+  for (int i = blockIdx.x * 256 + (int)threadIdx.x; i < d.n; i += gridDim.x * 256) {
+    d.u_ref[(size_t)b * d.ldn + i] = 0.0;
+    d.r_ref[(size_t)b * d.ldn + i] = r0[i];
+  }
+}
+
+// slot maps of the admission product: admitted rows write u^1 into slot 1; every
+// other row writes its free slot (3 - cur - prev), which no step reads
+__global__ void k_bslots_admit(BatchDev d, const int* list, int count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < d.B) {
+    const BNode* nd = d.nodes + t;
+    d.slot_new[t] = 3 - nd->cur - nd->prev;
+    d.slot_cur[t] = nd->cur;
+  }
+}
+__global__ void k_bslots_admitted(BatchDev d, const int* list, int count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) {
+    d.slot_new[list[t]] = 1;
+    d.slot_cur[list[t]] = 1;
+  }
+}
 
 __global__ void __launch_bounds__(256) k_banchor_copy(BatchDev d, const int* list) {
   const int b = list[blockIdx.y];
@@ -458,8 +502,15 @@ void launch_binit_copy(const BatchDev& d, const int* list, int count, cudaStream
   k_binit_copy<<<dim3(vec_blocks(d.p), count), 256, 0, s>>>(d, list);
 }
 
-void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream_t s) {
-  k_binit_node<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list);
+void launch_binit_node(const BatchDev& d, const int* list, int count, int zero, cudaStream_t s) {
+  k_binit_node<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list, zero);
+}
+
+void launch_bzero_anchor(const BatchDev& d, const int* list, int count, const double* r0, const double* G0,
+                         cudaStream_t s) {
+  k_bzero_anchor<<<dim3(vec_blocks(d.n > d.p ? d.n : d.p), count), 256, 0, s>>>(d, list, r0, G0);
+  k_bslots_admit<<<(d.B + 255) / 256, 256, 0, s>>>(d, list, count);
+  k_bslots_admitted<<<(count + 255) / 256, 256, 0, s>>>(d, list, count);
 }
 
 void launch_banchor_copy(const BatchDev& d, const int* list, int count, cudaStream_t s) {

@@ -734,8 +734,9 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
 }
 
 // the tiles whose K blocks span several CTAs: one CTA per CTA boundary inside a
-// tile (the first such boundary of each tile does its work), summing the partial
-// tiles in CTA order and applying the epilogue
+// tile (the first such boundary of each tile does its work) and per 64 columns
+// (blockIdx.y; one loss-partial group), summing the partial tiles in CTA order
+// and applying the epilogue
 template <int BN, int MODE>
 __global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int G) {
   SkMap mp;
@@ -753,7 +754,8 @@ __global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int 
   const int m = m0 + row;
   const EpiRow er = epi_row<MODE>(sh, ep, m);
   double fsum = 0.0, dsum = 0.0;
-  for (int cc = 0; cc < BN; cc += 16) {
+  const int c_lo = (int)blockIdx.y * 64;
+  for (int cc = c_lo; cc < c_lo + 64 && cc < BN; cc += 16) {
     float v[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = 0.0f;
@@ -861,7 +863,7 @@ static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
     }
     k_tcgemm_sk<P, BN, MODE><<<g.grid, sk_threads(BN), bytes, s>>>(*(const CUtensorMap*)g.tmA,
                                                               *(const CUtensorMap*)g.tmB, sh, e);
-    if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<g.grid - 1, kTcBM, 0, s>>>(sh, e, g.grid);
+    if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<dim3(g.grid - 1, (BN + 63) / 64), kTcBM, 0, s>>>(sh, e, g.grid);
     return;
   }
   static bool attr = false;

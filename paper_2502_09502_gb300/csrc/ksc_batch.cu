@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -36,6 +37,9 @@ struct BatchWs {
   int sk_fwd = 0, sk_grad = 0;   // stream-K schedule chosen for each product
   int nsm = 0;                   // SMs (persistent CTAs of a stream-K product)
   float* skws = nullptr;         // stream-K partial tiles (shared by both products)
+  double* r0 = nullptr;          // grad F(0) (n) and G0 = X^T grad F(0) (p), exact: the zero anchor
+  double* G0 = nullptr;
+  bool zero_ready = false;
   std::vector<void*> allocs;
   size_t bytes = 0;
   BatchDev bd{};
@@ -72,6 +76,9 @@ constexpr int kBatchStepsPerGraph = 16;
 constexpr int kLaunchesPerBatchStep = 5;   // residual, X^T r, prox, X beta, step
 constexpr int kLaunchesPerBatchCert = 5;   // prep, X b^, rows, X^T zeta, final (per fired group)
 constexpr int kLaunchesPerAnchor = 4;      // copy, X beta_ref, grad F, X^T r_ref
+// admissions of at least this many nodes start from the zero anchor (one forward
+// product for all of them instead of two exact products per node)
+constexpr int kZeroAnchorMin = 32;
 // relative accuracy of the in-loop gap: the FP32 loss and entropy terms (summed in
 // FP64) carry ~1e-8; a tighter in-loop tolerance could never be met
 constexpr double kInLoopFloor = 3e-8;
@@ -130,6 +137,7 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   b += kDfWsElems * 8;                          // split partials of the exact product
   b += (size_t)(Bc + 127) / 128 * 4;            // tile flags
   b += tc_skws_floats(sm_count(), 256) * 4;     // stream-K partial tiles
+  b += (ldn + ldp) * 8;                         // zero anchor r0, G0
   if (p > 2048) b += Bc * ldp * 8;              // prox scratch
   if (needs_xcopy(pr)) b += n * ldp * 2;
   return b;
@@ -179,6 +187,8 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
   BA(d.tile_run, (size_t)(Bc + 127) / 128 * 4);
   ws->nsm = sm_count();
   BA(ws->skws, tc_skws_floats(ws->nsm, 256) * 4);
+  BA(ws->r0, ldn * 8);
+  BA(ws->G0, ldp * 8);
   KB_CUDA(cudaMemsetAsync(d.tile_run, 1, (size_t)(Bc + 127) / 128 * 4, s));   // nonzero: run every tile
   d.colnorm = pr->dev.colnorm;
   float* yf = nullptr;
@@ -325,9 +335,14 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   std::vector<int> two(B, 2), zero(B, 0);
   KB_CUDA(cudaMemcpyAsync(d.slot_new, two.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
   KB_CUDA(cudaMemcpyAsync(d.slot_cur, zero.data(), (size_t)B * 4, cudaMemcpyHostToDevice, s));
-  // tile width x schedule (one CTA per tile, or stream-K over the SMs)
+  // tile width x schedule (one CTA per tile, or stream-K over the SMs).  The
+  // environment variable KSC_TC_SCHEDULE = tiled | stream_k restricts the choice
+  // to one schedule (profilers distort the timings the choice is made on).
+  const char* sched = std::getenv("KSC_TC_SCHEDULE");
+  const int sk_lo = (sched && std::strcmp(sched, "stream_k") == 0) ? 1 : 0;
+  const int sk_hi = (sched && std::strcmp(sched, "tiled") == 0) ? 0 : 1;
   for (int bn : kTcBNs) {
-    for (int sk = 0; sk < 2; ++sk) {
+    for (int sk = sk_lo; sk <= sk_hi; ++sk) {
       bool ok = make(bn, bn);
       if (ok && sk) ok = tc_plan_stream_k(&ws->fwd, ws->nsm, &why) && tc_plan_stream_k(&ws->grad, ws->nsm, &why);
       if (!ok) {
@@ -516,6 +531,37 @@ int session_running(const Session* se) {
   return r;
 }
 
+// tiles with a running node (k_bstep clears a tile's flag when its last node stops)
+ksc_status upload_tile_flags(Session* se) {
+  const int tiles = (se->B + 127) / 128;
+  se->tile_flags.assign(tiles, 0);
+  for (int b = 0; b < se->B; ++b)
+    if (se->slot[b].busy && !se->slot[b].fin) se->tile_flags[b / 128] = 1;
+  KB_CUDA(cudaMemcpyAsync(se->ws->bd.tile_run, se->tile_flags.data(), (size_t)tiles * 4, cudaMemcpyHostToDevice,
+                          se->s));
+  return KSC_OK;
+}
+
+// r0 = grad F(0) and G0 = X^T r0 (exact double-float product), once per workspace
+ksc_status zero_anchor_prepare(Session* se) {
+  BatchWs* ws = se->ws;
+  if (ws->zero_ready) return KSC_OK;
+  ksc_problem* pr = se->pr;
+  const int n = (int)pr->n;
+  std::vector<double> r0(n);
+  for (int i = 0; i < n; ++i)
+    r0[i] = pr->loss == KSC_LOSS_LSQ ? -2.0 * pr->y_host[i] : -0.5 * pr->y_host[i];   // grad F at u = 0
+  cudaStream_t s = se->s;
+  KB_CUDA(cudaMemcpyAsync(ws->r0, r0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+  const int zero_row = 0;
+  KB_CUDA(cudaMemcpyAsync(ws->dlist, &zero_row, 4, cudaMemcpyHostToDevice, s));
+  launch_dfprod(pr->dev, false, ws->r0, ws->ldn, ws->dlist, 1, ws->G0, ws->ldp, ws->bd.dfws, s);
+  pr->launches += 1 + (dfprod_splits(1, (int)pr->p) > 1);
+  KB_CUDA(cudaGetLastError());
+  ws->zero_ready = true;
+  return KSC_OK;
+}
+
 ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes, const std::vector<const NodeSetup*>& ns,
                          const std::vector<int>& want_z, std::vector<int>* slots) {
   const int cnt = (int)nodes.size();
@@ -593,9 +639,21 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
   launch_binit_copy(d, ws->dlist, cnt, s);
   pr->launches += 1;
   ksc_status st;
-  if ((st = anchor(se, *slots, true)) != KSC_OK) return st;
+  const bool zero = cnt >= kZeroAnchorMin;
+  if (zero) {
+    // the zero anchor and one forward product for all admitted nodes (instead of
+    // two exact products per node)
+    if ((st = zero_anchor_prepare(se)) != KSC_OK) return st;
+    KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
+    launch_bzero_anchor(d, ws->dlist, cnt, ws->r0, ws->G0, s);
+    if ((st = upload_tile_flags(se)) != KSC_OK) return st;
+    tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
+    pr->launches += 4 + ws->sk_fwd;
+  } else {
+    if ((st = anchor(se, *slots, true)) != KSC_OK) return st;
+  }
   KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
-  launch_binit_node(d, ws->dlist, cnt, s);
+  launch_binit_node(d, ws->dlist, cnt, zero ? 1 : 0, s);
   pr->launches += 1;
   KB_CUDA(cudaGetLastError());
   return KSC_OK;   // stream order: the next replay runs after the admission
@@ -605,14 +663,8 @@ bool session_advance(Session* se, ksc_status* st) {
   *st = KSC_OK;
   if (session_running(se) == 0) return false;
   ksc_problem* pr = se->pr;
-  // tiles with a running node (k_bstep clears a tile's flag when its last node stops)
-  const int tiles = (se->B + 127) / 128;
-  se->tile_flags.assign(tiles, 0);
-  for (int b = 0; b < se->B; ++b)
-    if (se->slot[b].busy && !se->slot[b].fin) se->tile_flags[b / 128] = 1;
-  cudaError_t e = cudaMemcpyAsync(se->ws->bd.tile_run, se->tile_flags.data(), (size_t)tiles * 4,
-                                  cudaMemcpyHostToDevice, se->s);
-  if (e == cudaSuccess) e = cudaGraphLaunch(pr->profile ? se->ws->graph_prof : se->ws->graph, se->s);
+  if ((*st = upload_tile_flags(se)) != KSC_OK) return false;
+  cudaError_t e = cudaGraphLaunch(pr->profile ? se->ws->graph_prof : se->ws->graph, se->s);
   if (e != cudaSuccess) {
     *st = api_fail(KSC_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     return false;

@@ -108,8 +108,14 @@ void launch_bstep(const BatchDev& d, cudaStream_t s);
 // admission of the slots in `list` (device int array, count entries): beta slots
 // 0 and 1 and the anchor from the warm start uploaded into slot 1
 void launch_binit_copy(const BatchDev& d, const int* list, int count, cudaStream_t s);
-// after the slots' anchors: u slots, F(u^1), g(beta^1), L^1 and the node state
-void launch_binit_node(const BatchDev& d, const int* list, int count, cudaStream_t s);
+// after the slots' anchors: u slots, F(u^1), g(beta^1), L^1 and the node state;
+// zero != 0: after the zero anchor, u^1 is in u slot 1 (the admission product)
+void launch_binit_node(const BatchDev& d, const int* list, int count, int zero, cudaStream_t s);
+// the zero anchor of the listed slots (beta_ref = 0, u_ref = 0, r_ref = r0 =
+// grad F(0), G_ref = G0 = X^T r0, pieces of beta^1) and the slot maps of the
+// admission's forward product (admitted rows -> slot 1, others -> their free slot)
+void launch_bzero_anchor(const BatchDev& d, const int* list, int count, const double* r0, const double* G0,
+                         cudaStream_t s);
 // anchors of the listed nodes (device list, count entries) at their current
 // iterate: beta_ref = beta^t (mid-solve only), then (after u_ref = X beta_ref)
 // r_ref = grad F(u_ref), u slot(s) = u_ref and, mid-solve, fresh in-loop bests
