@@ -14,22 +14,23 @@ namespace ksc {
 // D[list[r]][c] = sum_k A[k][c] V[list[r]][k] for the rows r < R of a node list
 // (A row-major K x C with leading dim lda): the exact products of many nodes in
 // one launch.  Each CTA stages a 32 x 128 tile of A once for 16 node vectors
-// (split into float hi + lo).  Within a block of kDfBlock consecutive k the terms
+// (split into float hi + lo).  Within a block of K_b consecutive k the terms
 // are summed in double-float (df_add); each block result hi + lo is added to an
 // FP64 accumulator.  Error bound (u = 2^-24, U = 2^-53, S = sum_k |A[k][c] V[k]|):
 //   |D - exact| <= [ (K_b^2/2 + 6 K_b + 5) u^2 + (blocks + splits + 2) U ] * 1.01 * S,
-// K_b = kDfBlock: per block the lo word collects the exact TwoSum and product errors
+// K_b = kblock (a multiple of 32; the certificates use 64, the anchors, which need
+// accuracy but no rigorous bound, 256 -- fewer FP64 block sums): per block the lo word collects the exact TwoSum and product errors
 // with its own rounding (<= u^2 (K_b^2/2 + 6 K_b + 4) S_block), the split of V costs
 // u^2 S, and the FP64 conversions and sums add the U terms.  With K split over
 // gridDim.z CTAs the partial sums go to ws and k_dfsum adds them in split order.
 // Every output element sums its terms in an order fixed by K alone.
-constexpr int kDfCols = 128, kDfNodes = 16, kDfK = 32, kDfBlock = 64;
+constexpr int kDfCols = 128, kDfNodes = 16, kDfK = 32;
 
 template <typename TX>
 __global__ void __launch_bounds__(256, 3) k_dfprod(const TX* __restrict__ A, int64_t lda, int K, int C,
                                                 const double* __restrict__ V, int64_t ldv,
                                                 const int* __restrict__ list, int R, double* __restrict__ D,
-                                                int64_t ldd, int kchunk, double* __restrict__ ws) {
+                                                int64_t ldd, int kchunk, int kblock, double* __restrict__ ws) {
   __shared__ __align__(16) float As[kDfK][kDfCols + 4];
   __shared__ float Vh[kDfNodes][kDfK + 1];
   __shared__ float Vl[kDfNodes][kDfK + 1];
@@ -69,27 +70,33 @@ __global__ void __launch_bounds__(256, 3) k_dfprod(const TX* __restrict__ A, int
       As[e / kDfCols][e % kDfCols] = ra[t];
     }
 #pragma unroll
+    int nz = 0;
     for (int t = 0; t < kVPer; ++t) {
       const int e = (int)threadIdx.x + t * 256;
       const float h = (float)rv[t];
       Vh[e / kDfK][e % kDfK] = h;
       Vl[e / kDfK][e % kDfK] = (float)(rv[t] - (double)h);
+      nz |= rv[t] != 0.0;
     }
-    __syncthreads();
+    // a chunk where every node's vector is zero adds nothing (sparse iterates:
+    // the nodes of one problem concentrate on the same columns)
+    const bool any = __syncthreads_or(nz) != 0;
     if (k0 + kDfK < ke) load(k0 + kDfK);
+    if (any) {
 #pragma unroll 4
-    for (int kk = 0; kk < kDfK; ++kk) {
-      const float4 a = *reinterpret_cast<const float4*>(&As[kk][tx * 4]);
-      const float av[4] = {a.x, a.y, a.z, a.w};
+      for (int kk = 0; kk < kDfK; ++kk) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[kk][tx * 4]);
+        const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const float vh = Vh[ty * 2 + q][kk], vl = Vl[ty * 2 + q][kk];
+        for (int q = 0; q < 2; ++q) {
+          const float vh = Vh[ty * 2 + q][kk], vl = Vl[ty * 2 + q][kk];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) df_add(hi[q][j], lo[q][j], av[j], vh, vl);
+          for (int j = 0; j < 4; ++j) df_add(hi[q][j], lo[q][j], av[j], vh, vl);
+        }
       }
     }
     __syncthreads();
-    if (((k0 - kb + kDfK) % kDfBlock) == 0 || k0 + kDfK >= ke) {   // close the block
+    if (((k0 - kb + kDfK) % kblock) == 0 || k0 + kDfK >= ke) {   // close the block
 #pragma unroll
       for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -133,11 +140,11 @@ int dfprod_splits(int R, int C) {
   return sp < kDfMaxSplits ? sp : kDfMaxSplits;
 }
 
-double dfprod_error_factor(int K, int R, int C) {
+double dfprod_error_factor(int K, int R, int C, int kblock) {
   const double u = 5.9604644775390625e-08, U = 1.1102230246251565e-16;
   const int splits = dfprod_splits(R, C);
-  const double kb = kDfBlock;
-  const double blocks = (double)((K + kDfBlock - 1) / kDfBlock) + splits;
+  const double kb = kblock;
+  const double blocks = (double)((K + kblock - 1) / kblock) + splits;
   return 1.01 * ((kb * kb / 2 + 6 * kb + 5) * u * u + (blocks + splits + 2) * U);
 }
 
@@ -145,22 +152,23 @@ double dfprod_error_factor(int K, int R, int C) {
 // A = Xc: V of length p, D of length n); ws: dfprod_ws_elems doubles when the
 // product is split over K (few nodes)
 void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
-                   int64_t ldd, double* ws, cudaStream_t s) {
+                   int64_t ldd, double* ws, int kblock, cudaStream_t s) {
   if (R <= 0) return;
   const int K = use_xc ? d.p : d.n, C = use_xc ? d.n : d.p;
   const int64_t lda = use_xc ? d.ldc : d.ldx;
   const void* A = use_xc ? d.Xc : d.X;
   const int splits = ws ? dfprod_splits(R, C) : 1;
-  const int kchunk = ((K + splits - 1) / splits + kDfBlock - 1) / kDfBlock * kDfBlock;
+  // split ranges are whole 32-row chunks; blocks (<= kDfBlock terms) restart in every split
+  const int kchunk = ((K + splits - 1) / splits + kDfK - 1) / kDfK * kDfK;
   dim3 grid((C + kDfCols - 1) / kDfCols, (R + kDfNodes - 1) / kDfNodes, splits);
   double* w = splits > 1 ? ws : nullptr;
   if (d.xdt == kXF64)
-    k_dfprod<double><<<grid, 256, 0, s>>>((const double*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, w);
+    k_dfprod<double><<<grid, 256, 0, s>>>((const double*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, kblock, w);
   else if (d.xdt == kXF32)
-    k_dfprod<float><<<grid, 256, 0, s>>>((const float*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, w);
+    k_dfprod<float><<<grid, 256, 0, s>>>((const float*)A, lda, K, C, V, ldv, list, R, D, ldd, kchunk, kblock, w);
   else
     k_dfprod<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)A, lda, K, C, V, ldv, list, R, D, ldd,
-                                                 kchunk, w);
+                                                 kchunk, kblock, w);
   if (splits > 1) {
     dim3 g2((C + 255) / 256 < 64 ? (C + 255) / 256 : 64, R);
     k_dfsum<<<g2, 256, 0, s>>>(ws, splits, R, C, list, D, ldd);

@@ -438,13 +438,13 @@ ksc_status anchor(Session* se, const std::vector<int>& list, bool init) {
   if (!init) launch_banchor_copy(d, ws->dlist, cnt, s);
   const bool tiled = cnt >= kAnchorTiled;
   if (tiled) {
-    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, d.dfws, s);
+    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, d.dfws, kDfBlockAnchor, s);
   } else {
     for (int b : list) launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, s);
   }
   launch_banchor_resid(d, ws->dlist, cnt, init ? 1 : 0, s);
   if (tiled) {
-    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, d.dfws, s);
+    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, d.dfws, kDfBlockAnchor, s);
   } else {
     for (int b : list) launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, s);
   }
@@ -555,7 +555,7 @@ ksc_status zero_anchor_prepare(Session* se) {
   KB_CUDA(cudaMemcpyAsync(ws->r0, r0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
   const int zero_row = 0;
   KB_CUDA(cudaMemcpyAsync(ws->dlist, &zero_row, 4, cudaMemcpyHostToDevice, s));
-  launch_dfprod(pr->dev, false, ws->r0, ws->ldn, ws->dlist, 1, ws->G0, ws->ldp, ws->bd.dfws, s);
+  launch_dfprod(pr->dev, false, ws->r0, ws->ldn, ws->dlist, 1, ws->G0, ws->ldp, ws->bd.dfws, kDfBlockAnchor, s);
   pr->launches += 1 + (dfprod_splits(1, (int)pr->p) > 1);
   KB_CUDA(cudaGetLastError());
   ws->zero_ready = true;
@@ -714,10 +714,10 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     const Dev& sd = pr->dev;
     KB_CUDA(cudaMemcpyAsync(ws->dlist, fired.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s));
     launch_bcert_prep(d, ws->dlist, R, s);
-    launch_dfprod(sd, true, d.beta_out, d.p, ws->dlist, R, d.cert_u, d.ldn, d.dfws, s);
+    launch_dfprod(sd, true, d.beta_out, d.p, ws->dlist, R, d.cert_u, d.ldn, d.dfws, kDfBlockCert, s);
     launch_bcert_rows(d, ws->dlist, R, s);
-    launch_dfprod(sd, false, d.cert_z, d.ldn, ws->dlist, R, d.cert_a, d.ldp, d.dfws, s);
-    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p), s);
+    launch_dfprod(sd, false, d.cert_z, d.ldn, ws->dlist, R, d.cert_a, d.ldp, d.dfws, kDfBlockCert, s);
+    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p, kDfBlockCert), s);
     pr->launches += kLaunchesPerBatchCert + (dfprod_splits(R, d.n) > 1) + (dfprod_splits(R, d.p) > 1);
     se->certificates += R;
     KB_CUDA(cudaGetLastError());

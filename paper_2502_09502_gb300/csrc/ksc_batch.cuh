@@ -138,9 +138,12 @@ void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out
 // more CTAs through ws (kDfWsElems doubles).
 constexpr int kDfMaxSplits = 16;
 constexpr size_t kDfWsElems = (size_t)2 * 608 * 128 * 16;
+// kblock: terms per double-float block (a multiple of 32): kDfBlockCert for the
+// certificates (the bound below), kDfBlockAnchor for anchors (no bound needed)
+constexpr int kDfBlockCert = 64, kDfBlockAnchor = 256;
 void launch_dfprod(const Dev& d, bool use_xc, const double* V, int64_t ldv, const int* list, int R, double* D,
-                   int64_t ldd, double* ws, cudaStream_t s);
+                   int64_t ldd, double* ws, int kblock, cudaStream_t s);
 int dfprod_splits(int R, int C);
-double dfprod_error_factor(int K, int R, int C);
+double dfprod_error_factor(int K, int R, int C, int kblock);
 
 }  // namespace ksc
