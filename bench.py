@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--x-dtype", default="f32", choices=["f32", "fp8"],
+                    help="single workload: X in FP32 (default) or FP8 e4m3 with per-column power-of-two "
+                         "scales quantized from the same FP32 instance (the experiment of the precision pattern)")
     ap.add_argument("--no-batched", action="store_true",
                     help="single workload: leave out the batched comparison object")
     ap.add_argument("--small", action="store_true",
@@ -202,12 +205,20 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     P = make_problem(args)
     n, p = P.n, P.p
-    Xd = torch.from_numpy(P.X).cuda()
+    fp8 = args.x_dtype == "fp8"
+    scales = None
+    if fp8:
+        import ksc_inputs as G
+        bits, scales = G.quantize_fp8(P.X)
+        Xd = torch.from_numpy(bits).cuda().view(torch.float8_e4m3fn)
+    else:
+        Xd = torch.from_numpy(P.X).cuda()
+    xbytes = 1 if fp8 else 4
     stream = torch.cuda.Stream()
     node = K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=100000)
 
     def step(profile=False, stats=None):
-        prob = K.Problem(Xd, P.y, K.KSC_LOSS_LSQ, stream=stream)
+        prob = K.Problem(Xd, P.y, K.KSC_LOSS_LSQ, stream=stream, col_scale=scales)
         if profile:
             K.ksc_problem_profile(prob.h, True)
         t0 = time.perf_counter()
@@ -261,7 +272,7 @@ def run_ours(args, rank, world, dist):
     # roofline of the dominant kernel (the gradient pass over X)
     nl, kms = stats["k"][0]
     grad_ms = kms / max(nl, 1)
-    alg_bytes = n * p * 4 + 3 * n * 8 + p * 8    # X (FP32) + u_t, u_{t-1}, y + grad
+    alg_bytes = n * p * xbytes + 3 * n * 8 + p * 8    # X (FP32 or FP8) + u_t, u_{t-1}, y + grad
     achieved = alg_bytes / (grad_ms / 1e3) / 1e9
     peak, peak_kind = _peaks()
     shares = {name: round(stats["k"][i][1] / max(1e-9, sum(x[1] for x in stats["k"])), 4)
@@ -271,18 +282,19 @@ def run_ours(args, rank, world, dist):
     # timed region, D2H of beta and z
     e2e = None
     if args.e2e_steps > 0:
-        Xh = torch.from_numpy(P.X).pin_memory()
+        Xh = torch.from_numpy(bits if fp8 else P.X).pin_memory()
         e_lat = []
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            prob = K.Problem(Xh.numpy(), P.y, K.KSC_LOSS_LSQ, stream=stream)
+            prob = K.Problem(Xh.numpy(), P.y, K.KSC_LOSS_LSQ, stream=stream,
+                             x_dtype=K.KSC_FP8 if fp8 else None, col_scale=scales)
             r = prob.solve(node, want_beta=True, want_z=True)
             prob.close()
             assert r.status == "ok"
         e_s = time.perf_counter() - t0
         e2e = {"value": args.e2e_steps * world / e_s if not dist else None, "unit": UNIT,
-               "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
+               "h2d_bytes_per_step": int(Xh.numpy().nbytes + P.y.nbytes),
                "d2h_bytes_per_step": int(2 * p * 8 + 64)}
         if dist:
             e2e["value"] = args.e2e_steps * world / max_over_ranks(e_s, dist)
@@ -293,9 +305,12 @@ def run_ours(args, rank, world, dist):
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8" if fp8 else "f32",
             "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
-            "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "single GPU"),
+            "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                           **({"x_dtype": "fp8 e4m3, per-column power-of-two scales, quantized from the FP32 "
+                                          "instance (the solved matrix is the quantized one)",
+                               "l2": "X (1 GB) larger than L2; no flush"} if fp8 else {})),
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
             "iters_per_bound": float(np.mean(stats["iters"])),
@@ -309,7 +324,7 @@ def run_ours(args, rank, world, dist):
             "roofline": {"bound": "hbm", "kernel": "gradient pass X^T r (k_grad)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "peak_kind": peak_kind, "frac": round(achieved / peak, 4),
-                         "traffic": _traffic(n, p), "bytes_per_launch": alg_bytes,
+                         "traffic": None if fp8 else _traffic(n, p), "bytes_per_launch": alg_bytes,
                          "avg_launch_ms": round(grad_ms, 5), "launches": nl},
         }
     return out, P, stats

@@ -64,7 +64,10 @@ typedef enum {
 typedef enum {
   KSC_F64 = 0,                  /* X in double                                      */
   KSC_F32 = 1,                  /* X in float                                       */
-  KSC_BF16 = 2                  /* X in bfloat16 bits; the problem is the stored X  */
+  KSC_BF16 = 2,                 /* X in bfloat16 bits; the problem is the stored X  */
+  KSC_FP8_E4M3_COLSCALE = 3     /* X in FP8 e4m3 bits with a per-column scale s_j, a
+                                   power of two in [2^-100, 2^100]; the problem's matrix
+                                   is X_ij * s_j, exact in FP32 (single-node solver)  */
   /* X is streamed from HBM in its storage type.  The iterate vectors (beta, X beta,
      the gradient) are FP64 for every type; products with FP32/BF16 X are made
      error-free (exact product error by fma, compensated sums). */
@@ -91,11 +94,14 @@ typedef struct {
   double lipschitz;     /* > 0: the step constant L of Algorithm 3 to use.
                            <= 0: L = c_f * lambda_max(X^T X) * 1.01, c_f = 2 (least
                            squares) or 1/4 (logistic), lambda_max by power iteration */
+  const float* col_scale; /* KSC_FP8_E4M3_COLSCALE: host pointer, p scales (copied);
+                           NULL for the other types                                */
 } ksc_problem_desc;
 
 /* Create a problem: copies (or borrows) X, copies y, computes L on the device.
  * Errors: KSC_ERR_INVALID_ARG (null pointers, n or p < 1, ldx < p, unknown enum,
- * logistic labels not +-1), KSC_ERR_OOM, KSC_ERR_CUDA.  *out is NULL on error. */
+ * logistic labels not +-1, FP8 X without power-of-two column scales),
+ * KSC_ERR_OOM, KSC_ERR_CUDA.  *out is NULL on error. */
 ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cuda_stream,
                               ksc_problem** out);
 /* Free every device buffer the problem owns.  NULL is accepted. */

@@ -151,6 +151,27 @@ def make_problem(n, p, *, r=0.5, seed=0, loss=LSQ, k_true=5, snr=5.0, x_dtype=F6
                    dict(n=n, p=p, r=r, seed=seed, k_true=k_true, snr=snr))
 
 
+def quantize_fp8(X):
+    """FP8 e4m3 storage of a matrix with one power-of-two scale per column:
+    s_j = 2^ceil(log2(max_i |X_ij| / 448)), bits = e4m3(X / s) (round to nearest
+    even).  Returns (uint8 bits, float32 scales); the represented matrix is
+    fp8_values(bits) * s, exact in FP32."""
+    import torch
+    Xf = np.asarray(X, dtype=np.float32)
+    amax = np.abs(Xf).max(axis=0)
+    e = np.ceil(np.log2(np.maximum(amax, 1e-30) / 448.0)).astype(np.int32)
+    e = np.clip(e, -100, 100)
+    s = np.ldexp(np.float32(1.0), e).astype(np.float32)
+    q = torch.from_numpy(Xf / s).to(torch.float8_e4m3fn)
+    return q.view(torch.uint8).numpy().copy(), s
+
+
+def fp8_values(bits):
+    """The e4m3 values of FP8 bits (exact in float32)."""
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(bits)).view(torch.float8_e4m3fn).to(torch.float32).numpy()
+
+
 def node_sets(p, count, *, seed=0, max_zero=200, max_one=9):
     """Seeded branch-and-bound nodes: |S0| ~ U{0..max_zero}, |S1| ~ U{0..max_one},
     disjoint, positions uniform.  Returns a list of (S0, S1) int32 arrays."""

@@ -61,6 +61,26 @@ template <> struct Vec<__nv_bfloat16> {
   }
 };
 
+// FP8 e4m3: 8 columns per 8-byte load (the values are exact in half and float)
+template <> struct Vec<__nv_fp8_e4m3> {
+  static constexpr int N = 8;
+  template <typename A>
+  __device__ __forceinline__ static void load(const __nv_fp8_e4m3* p, A (&v)[8]) {
+    const uint2 t = __ldcs(reinterpret_cast<const uint2*>(p));
+    const unsigned w[2] = {t.x, t.y};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const __half2_raw r = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[k] >> (16 * h)), __NV_E4M3);
+        const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&r));
+        v[4 * k + 2 * h] = (A)f.x;
+        v[4 * k + 2 * h + 1] = (A)f.y;
+      }
+    }
+  }
+};
+
 __device__ __forceinline__ double sigmoid(double t) {
   return t >= 0 ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
 }
@@ -203,6 +223,10 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
     if (col < p) {
       double s = 0.0;
       for (int b = 0; b < (int)gridDim.y; ++b) s += __ldcg(&ws[(size_t)b * p + col]);
+      if constexpr (is_fp8<TX>()) {   // the matrix is X s: power-of-two scale, exact
+        const double sc = (double)d.xscale[col];
+        s *= (MODE == kGColsq) ? sc * sc : sc;
+      }
       if constexpr (MODE == kGStep) {
         d.grad[col] = s;
         const double b0 = bc[col];
@@ -465,8 +489,10 @@ __global__ void __launch_bounds__(kFwdThreads) k_fwd(Dev d) {
       const int cw = min(CH, p - c0);
       __syncthreads();
       for (int j = threadIdx.x; j < cw; j += kFwdThreads) {
-        if (FP64ACC) sh_d[j] = bfull[c0 + j];
-        else { sh_hi[j] = bh[c0 + j]; sh_lo[j] = bl[c0 + j]; }
+        // FP8 X: (X s) b = X (s b), s a power of two (exact)
+        const float sc = is_fp8<TX>() ? d.xscale[c0 + j] : 1.0f;
+        if (FP64ACC) sh_d[j] = bfull[c0 + j] * (double)sc;
+        else { sh_hi[j] = bh[c0 + j] * sc; sh_lo[j] = bl[c0 + j] * sc; }
       }
       __syncthreads();
       for (int cc = lane * CPT; cc < cw; cc += 32 * CPT) {
@@ -560,8 +586,9 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
       }
       const int j = __ldcg(&d.nnz_idx[a * kSegLen + (E - soff[a])]);
       sj[e] = j;
-      if (FP64ACC) sv[e] = __ldcg(&bfull[j]);
-      else { sh[e] = __ldcg(&d.bhi[j]); sl[e] = __ldcg(&d.blo[j]); }
+      const float sc = is_fp8<TX>() ? d.xscale[j] : 1.0f;   // FP8 X: (X s) b = X (s b), exact
+      if (FP64ACC) sv[e] = __ldcg(&bfull[j]) * (double)sc;
+      else { sh[e] = __ldcg(&d.bhi[j]) * sc; sl[e] = __ldcg(&d.blo[j]) * sc; }
     }
     __syncthreads();
     if (row < n) {
@@ -569,7 +596,7 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
       for (; e + 8 <= cnt; e += 8) {
         A x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = xval<A>(__ldcs(&Xc[(size_t)sj[e + k] * d.ldc + row]));
+        for (int k = 0; k < 8; ++k) x[k] = xval<A>(ldcs_x(&Xc[(size_t)sj[e + k] * d.ldc + row]));
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           if constexpr (FP64ACC) acc += x[k] * (A)sv[e + k];
@@ -577,7 +604,7 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
         }
       }
       for (; e < cnt; ++e) {
-        const A x = xval<A>(__ldcs(&Xc[(size_t)sj[e] * d.ldc + row]));
+        const A x = xval<A>(ldcs_x(&Xc[(size_t)sj[e] * d.ldc + row]));
         if constexpr (FP64ACC) acc += x * (A)sv[e];
         else df_add(acc, lo, x, sh[e], sl[e]);
       }
@@ -611,7 +638,8 @@ template <typename TX, bool VEC>
 __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ A, int64_t lda, int rows,
                                                          int cols, const double* __restrict__ vec,
                                                          double* __restrict__ out, double* __restrict__ ws,
-                                                         int* __restrict__ cnt) {
+                                                         int* __restrict__ cnt, const float* __restrict__ sin,
+                                                         const float* __restrict__ sout) {
   constexpr bool FP64ACC = std::is_same<TX, double>::value;
   using Acc = typename std::conditional<FP64ACC, double, float>::type;
   constexpr int CPT = Vec<TX>::N;
@@ -622,7 +650,8 @@ __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ 
   const int r0 = rb * kGradRows;
   const int rn = min(kGradRows, rows - r0);
   for (int i = threadIdx.x; i < rn; i += kGradThreads) {
-    const double r = vec[r0 + i];
+    // sin / sout: FP8 column scales (powers of two: exact) on the input rows or the outputs
+    const double r = sin ? vec[r0 + i] * (double)sin[r0 + i] : vec[r0 + i];
     rs[i] = (Acc)r;
     rl[i] = FP64ACC ? 0.f : (float)(r - (double)(float)r);
   }
@@ -677,7 +706,7 @@ __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ 
     if (col < cols) {
       double sum = 0.0;
       for (int b = 0; b < (int)gridDim.y; ++b) sum += __ldcg(&ws[(size_t)b * cols + col]);
-      out[col] = sum;
+      out[col] = sout ? sum * (double)sout[col] : sum;
     }
   }
   if (threadIdx.x == 0) cnt[ct] = 0;
@@ -685,12 +714,13 @@ __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ 
 
 template <typename TX>
 static void colsum_launch(const TX* A, int64_t lda, int rows, int cols, const double* vec, double* out,
-                          double* ws, int* cnt, cudaStream_t s) {
+                          double* ws, int* cnt, cudaStream_t s, const float* sin = nullptr,
+                          const float* sout = nullptr) {
   const int tile = kGradThreads * Vec<TX>::N;
   dim3 grid((cols + tile - 1) / tile, (rows + kGradRows - 1) / kGradRows);
   const bool vec_ok = (lda % Vec<TX>::N) == 0 && ((uintptr_t)A % 16) == 0;
-  if (vec_ok) k_colsum<TX, true><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt);
-  else k_colsum<TX, false><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt);
+  if (vec_ok) k_colsum<TX, true><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt, sin, sout);
+  else k_colsum<TX, false><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt, sin, sout);
 }
 
 // ----------------------------------------------------------- column-major copy
@@ -759,6 +789,7 @@ static void step_impl(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
 void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   if (d.xdt == kXF64) step_impl<double, double>(d, s, ev);
   else if (d.xdt == kXF32) step_impl<float, double>(d, s, ev);
+  else if (d.xdt == kXFP8) step_impl<__nv_fp8_e4m3, double>(d, s, ev);
   else step_impl<__nv_bfloat16, double>(d, s, ev);
 }
 
@@ -771,6 +802,7 @@ static void init_impl(const Dev& d, cudaStream_t s) {
 void launch_init(const Dev& d, cudaStream_t s) {
   if (d.xdt == kXF64) init_impl<double, double>(d, s);
   else if (d.xdt == kXF32) init_impl<float, double>(d, s);
+  else if (d.xdt == kXFP8) init_impl<__nv_fp8_e4m3, double>(d, s);
   else init_impl<__nv_bfloat16, double>(d, s);
 }
 
@@ -785,6 +817,7 @@ static void cert_impl(const Dev& d, cudaStream_t s, int want_z) {
 void launch_certificate(const Dev& d, cudaStream_t s, int want_z) {
   if (d.xdt == kXF64) cert_impl<double, double>(d, s, want_z);
   else if (d.xdt == kXF32) cert_impl<float, double>(d, s, want_z);
+  else if (d.xdt == kXFP8) cert_impl<__nv_fp8_e4m3, double>(d, s, want_z);
   else cert_impl<__nv_bfloat16, double>(d, s, want_z);
 }
 
@@ -795,6 +828,9 @@ void launch_fwd_raw(const Dev& d, cudaStream_t s) {
     colsum_launch<double>((const double*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
   else if (d.xdt == kXF32)
     colsum_launch<float>((const float*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXFP8)
+    colsum_launch<__nv_fp8_e4m3>((const __nv_fp8_e4m3*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s,
+                                 d.xscale, nullptr);
   else
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.Xc, d.ldc, d.p, d.n, d.vcur, d.u, (double*)d.ws, cnt, s);
 }
@@ -805,6 +841,9 @@ void launch_grad_raw(const Dev& d, cudaStream_t s) {
     colsum_launch<double>((const double*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
   else if (d.xdt == kXF32)
     colsum_launch<float>((const float*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXFP8)
+    colsum_launch<__nv_fp8_e4m3>((const __nv_fp8_e4m3*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s,
+                                 nullptr, d.xscale);
   else
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)d.X, d.ldx, d.n, d.p, d.u, d.grad, (double*)d.ws, cnt, s);
 }
@@ -820,6 +859,9 @@ void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out
     colsum_launch<double>((const double*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
   else if (d.xdt == kXF32)
     colsum_launch<float>((const float*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
+  else if (d.xdt == kXFP8)
+    colsum_launch<__nv_fp8_e4m3>((const __nv_fp8_e4m3*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s,
+                                 use_xc ? d.xscale : nullptr, use_xc ? nullptr : d.xscale);
   else
     colsum_launch<__nv_bfloat16>((const __nv_bfloat16*)A, lda, rows, cols, vec, out, (double*)d.ws, cnt, s);
 }
@@ -830,6 +872,9 @@ void launch_transpose(const Dev& d, cudaStream_t s) {
     k_transpose<double><<<grid, 256, 0, s>>>((const double*)d.X, d.ldx, (double*)d.Xc, d.ldc, d.n, d.p);
   else if (d.xdt == kXF32)
     k_transpose<float><<<grid, 256, 0, s>>>((const float*)d.X, d.ldx, (float*)d.Xc, d.ldc, d.n, d.p);
+  else if (d.xdt == kXFP8)
+    k_transpose<__nv_fp8_e4m3><<<grid, 256, 0, s>>>((const __nv_fp8_e4m3*)d.X, d.ldx, (__nv_fp8_e4m3*)d.Xc, d.ldc,
+                                                    d.n, d.p);
   else
     k_transpose<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)d.X, d.ldx,
                                                      (__nv_bfloat16*)d.Xc, d.ldc, d.n, d.p);
@@ -838,6 +883,7 @@ void launch_transpose(const Dev& d, cudaStream_t s) {
 void launch_colnorm(const Dev& d, cudaStream_t s) {
   if (d.xdt == kXF64) Launch<double, double>::grad<kGColsq>(d, s);
   else if (d.xdt == kXF32) Launch<float, double>::grad<kGColsq>(d, s);
+  else if (d.xdt == kXFP8) Launch<__nv_fp8_e4m3, double>::grad<kGColsq>(d, s);
   else Launch<__nv_bfloat16, double>::grad<kGColsq>(d, s);
 }
 

@@ -65,7 +65,7 @@ static constexpr int kLaunchesPerLanczos = 5;   // forward, gradient, three vect
 
 // the iterate vectors are FP64 for every storage type of X
 static size_t tbytes(int) { return 8; }
-static size_t xbytes(int xdt) { return xdt == kXF64 ? 8 : (xdt == kXF32 ? 4 : 2); }
+static size_t xbytes(int xdt) { return xdt == kXF64 ? 8 : (xdt == kXF32 ? 4 : (xdt == kXFP8 ? 1 : 2)); }
 
 template <typename P>
 static ksc_status dmalloc(ksc_problem* pr, P** ptr, size_t bytes) {
@@ -233,8 +233,20 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   if (desc->n < 1 || desc->p < 1) return fail(KSC_ERR_INVALID_ARG, "n and p must be >= 1");
   if (desc->n > (1ll << 31) - 1 || desc->p > (1ll << 31) - 1)
     return fail(KSC_ERR_INVALID_ARG, "n and p must be < 2^31");
-  if (desc->x_dtype != KSC_F64 && desc->x_dtype != KSC_F32 && desc->x_dtype != KSC_BF16)
+  if (desc->x_dtype != KSC_F64 && desc->x_dtype != KSC_F32 && desc->x_dtype != KSC_BF16 &&
+      desc->x_dtype != KSC_FP8_E4M3_COLSCALE)
     return fail(KSC_ERR_INVALID_ARG, "unknown x_dtype");
+  if (desc->x_dtype == KSC_FP8_E4M3_COLSCALE) {
+    // power-of-two scales: X_ij s_j is exact in FP32 (e4m3 has 4 significant bits)
+    if (!desc->col_scale) return fail(KSC_ERR_INVALID_ARG, "FP8 X needs col_scale");
+    for (int64_t j = 0; j < desc->p; ++j) {
+      const float v = desc->col_scale[j];
+      int e = 0;
+      const float m = std::frexp(v, &e);
+      if (!(v > 0.0f) || !std::isfinite(v) || m != 0.5f || e < -99 || e > 101)
+        return fail(KSC_ERR_INVALID_ARG, "col_scale entries must be powers of two in [2^-100, 2^100]");
+    }
+  }
   if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC)
     return fail(KSC_ERR_INVALID_ARG, "unknown loss");
   if (!desc->X || !desc->y) return fail(KSC_ERR_INVALID_ARG, "X and y must be non-NULL");
@@ -278,6 +290,14 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
     pr->own_x = true;
   }
   d.X = pr->X;
+  d.xscale = nullptr;
+  if (pr->xdt == kXFP8) {
+    float* sc = nullptr;
+    if ((st = dmalloc(pr, &sc, (size_t)pr->p * 4)) != KSC_OK) return bail(st);
+    cudaError_t e = cudaMemcpyAsync(sc, desc->col_scale, (size_t)pr->p * 4, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("copy col_scale: ") + cudaGetErrorString(e)));
+    d.xscale = sc;
+  }
   const int cpt = cols_per_thread(pr->xdt);
   d.vec = ((ldx % cpt) == 0 && ((uintptr_t)pr->X % 16) == 0) ? 1 : 0;
   if ((st = dmalloc(pr, &pr->y, pr->n * 8)) != KSC_OK) return bail(st);

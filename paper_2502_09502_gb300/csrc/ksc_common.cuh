@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 namespace ksc {
@@ -286,6 +287,17 @@ __device__ __forceinline__ unsigned long long nnbits(double x) { return (unsigne
 template <typename A> __device__ __forceinline__ A xval(float x) { return (A)x; }
 template <typename A> __device__ __forceinline__ A xval(double x) { return (A)x; }
 template <typename A> __device__ __forceinline__ A xval(__nv_bfloat16 x) { return (A)__bfloat162float(x); }
+// FP8 e4m3 values are exact in half and float
+template <typename A> __device__ __forceinline__ A xval(__nv_fp8_e4m3 x) { return (A)(float)x; }
+template <typename TX> __host__ __device__ constexpr bool is_fp8() { return false; }
+template <> __host__ __device__ constexpr bool is_fp8<__nv_fp8_e4m3>() { return true; }
+// one element of X, streamed (evict-first)
+template <typename TX> __device__ __forceinline__ TX ldcs_x(const TX* p) { return __ldcs(p); }
+template <> __device__ __forceinline__ __nv_fp8_e4m3 ldcs_x(const __nv_fp8_e4m3* p) {
+  __nv_fp8_e4m3 v;
+  v.__x = (__nv_fp8_storage_t)__ldcs(reinterpret_cast<const unsigned char*>(p));
+  return v;
+}
 
 // Double-float accumulation of x * (rh + rl) into hi + lo.  x*rh = p + e exactly
 // (e by fma); hi + p = s + err exactly (Knuth's TwoSum); lo collects err, e and

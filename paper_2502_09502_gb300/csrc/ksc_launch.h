@@ -10,7 +10,7 @@
 
 namespace ksc {
 
-enum XDtype : int { kXF64 = 0, kXF32 = 1, kXBF16 = 2 };
+enum XDtype : int { kXF64 = 0, kXF32 = 1, kXBF16 = 2, kXFP8 = 3 };
 
 // Tile shapes (kept in one place: the host sizes workspaces with them).
 constexpr int kGradThreads = 256;   // gradient pass: threads per CTA
@@ -26,12 +26,13 @@ constexpr int kSpSplit = 16;        // sparse forward pass: chunks of the nonzer
 constexpr int kSpStage = 1024;      // sparse forward pass: list entries staged per round
 constexpr int kLanczosMax = 512;    // Lanczos steps for lambda_max(X^T X)
 
-__host__ __device__ inline int cols_per_thread(int xdt) { return xdt == kXF64 ? 2 : (xdt == kXF32 ? 4 : 8); }
+__host__ __device__ inline int cols_per_thread(int xdt) { return xdt == kXF64 ? 2 : (xdt == kXF32 ? 4 : 8); }   // FP8: 8 per 8-byte load
 
 struct Dev {
   int xdt;
   const void* X;
   int64_t ldx;
+  const float* xscale;     // FP8 X: p power-of-two column scales (the matrix is X_ij s_j); else NULL
   const void* Xc;          // column-major copy of X (ldc >= n), for the sparse forward pass
   int64_t ldc;
   int n, p;

@@ -24,7 +24,7 @@ KSC_ERR_CUDA, KSC_ERR_UNIMPLEMENTED = 7, 8
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "admission", 4: "infeasible_node",
                 5: "not_converged", 6: "timeout", 7: "cuda", 8: "unimplemented"}
 KSC_LOSS_LSQ, KSC_LOSS_LOGISTIC = 0, 1
-KSC_F64, KSC_F32, KSC_BF16 = 0, 1, 2
+KSC_F64, KSC_F32, KSC_BF16, KSC_FP8 = 0, 1, 2, 3   # KSC_FP8: e4m3 with power-of-two column scales
 KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF = 1, 2
 KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 KSC_KERNEL_B_RESID, KSC_KERNEL_B_GRAD, KSC_KERNEL_B_PROX, KSC_KERNEL_B_FWD, KSC_KERNEL_B_STEP = (
@@ -50,7 +50,7 @@ class KscError(RuntimeError):
 class ProblemDesc(C.Structure):
     _fields_ = [("n", C.c_int64), ("p", C.c_int64), ("x_dtype", C.c_int), ("X", C.c_void_p),
                 ("ldx", C.c_int64), ("y", C.POINTER(C.c_double)), ("loss", C.c_int),
-                ("x_on_device", C.c_int32), ("lipschitz", C.c_double)]
+                ("x_on_device", C.c_int32), ("lipschitz", C.c_double), ("col_scale", C.POINTER(C.c_float))]
 
 
 class NodeC(C.Structure):
@@ -333,13 +333,15 @@ class Problem:
     """Owns a ksc_problem handle.  X: numpy array (copied to the device; bf16 as
     uint16 bits) or a CUDA torch tensor (borrowed: kept alive by this object)."""
 
-    def __init__(self, X, y, loss=KSC_LOSS_LSQ, lipschitz=0.0, stream=None, x_dtype=None):
+    def __init__(self, X, y, loss=KSC_LOSS_LSQ, lipschitz=0.0, stream=None, x_dtype=None, col_scale=None):
+        """col_scale: FP8 X only -- p power-of-two column scales (the matrix is X_ij s_j)."""
         self._keep = []
         y = np.ascontiguousarray(y, dtype=np.float64)
         if hasattr(X, "data_ptr"):  # torch tensor on the device
             import torch
             assert X.is_cuda and X.is_contiguous()
-            code = {torch.float64: KSC_F64, torch.float32: KSC_F32, torch.bfloat16: KSC_BF16}[X.dtype]
+            code = {torch.float64: KSC_F64, torch.float32: KSC_F32, torch.bfloat16: KSC_BF16,
+                    torch.float8_e4m3fn: KSC_FP8}[X.dtype]
             ptr, on_dev = X.data_ptr(), 1
             n, p = X.shape
             self._keep.append(X)
@@ -351,8 +353,14 @@ class Problem:
             self._keep.append(X)
         self.n, self.p = int(n), int(p)
         self._keep.append(y)
+        sc = None
+        if code == KSC_FP8:
+            if col_scale is None:
+                raise ValueError("FP8 X needs col_scale")
+            sc = np.ascontiguousarray(col_scale, dtype=np.float32)
+            self._keep.append(sc)
         self.desc = ProblemDesc(self.n, self.p, code, ptr, self.p, _dptr(y), int(loss), on_dev,
-                                float(lipschitz))
+                                float(lipschitz), sc.ctypes.data_as(C.POINTER(C.c_float)) if sc is not None else None)
         self.h = ksc_problem_create(self.desc, stream)
         self.stream = stream
 

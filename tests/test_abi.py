@@ -55,6 +55,15 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
                         ksc.KSC_LOSS_LOGISTIC, 0, 0.0)
     assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
     assert "labels" in ksc.ksc_last_error()
+    # FP8 X: power-of-two column scales required (checked before any CUDA call)
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_FP8, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "col_scale" in ksc.ksc_last_error()
+    for bad in ([1.0, 0.75, 2.0, 4.0], [1.0, 2.0 ** -101, 1.0, 1.0], [1.0, -2.0, 1.0, 1.0]):
+        sc = np.array(bad, dtype=np.float32)
+        d = ksc.ProblemDesc(3, 4, ksc.KSC_FP8, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0,
+                            sc.ctypes.data_as(C.POINTER(C.c_float)))
+        assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
     w = np.ones(4)
     dp = C.POINTER(C.c_double)
     assert ksc.lib.ksc_prox_g(w.ctypes.data_as(dp), 4, 2, 1.0, -1.0, w.ctypes.data_as(dp),
@@ -88,8 +97,9 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
 
 def test_struct_layouts_match_header(ksc):
     # offsets the C compiler uses for the ABI structs (x86-64 and aarch64 LP64)
-    assert C.sizeof(ksc.ProblemDesc) == 64
+    assert C.sizeof(ksc.ProblemDesc) == 72
     assert ksc.ProblemDesc.X.offset == 24 and ksc.ProblemDesc.lipschitz.offset == 56
+    assert ksc.ProblemDesc.col_scale.offset == 64
     assert C.sizeof(ksc.NodeC) == 88
     assert ksc.NodeC.warm_beta.offset == 56 and ksc.NodeC.flags.offset == 84
     assert C.sizeof(ksc.ResultC) == 56
