@@ -13,7 +13,8 @@
  *      |b| <= M and leave the budget, k' = k - |ONE|.  Its conjugate follows
  *      from Lemma 3.1 with the separable-sum and scaling rules of App. D.
  *  R3  L (Algorithm 3 input) = c_f lambda_max(X^T X) (1 + 1e-6), c_f = 2 for
- *      least squares (F = ||u-y||^2), 1/4 for logistic.
+ *      least squares (F = ||u-y||^2) and squared hinge (F'' <= 2 where it
+ *      exists, F' 2-Lipschitz), 1/4 for logistic.
  *  R4  Relative gap (Sec. 4.2, eps = 1e-6): (primal - dual) / max(|primal|, 1e-300).
  *  R5  Algorithm 4 typos: nu_1 := nuhat_1; loop bound n := p; v_prev := nu_prev;
  *      the look-forward test reads "j < p and nu <= nuhat_{j+1}".
@@ -297,6 +298,7 @@ double kso_loss(int loss, const double *u, const double *y, int64_t n) {
   double f = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     if (loss == KSO_LOSS_LSQ) { double r = u[i] - y[i]; f += r * r; }
+    else if (loss == KSO_LOSS_SQHINGE) { double m = fmax(0.0, 1.0 - y[i] * u[i]); f += m * m; }
     else f += log1pexp(-y[i] * u[i]);
   }
   return f;
@@ -305,6 +307,7 @@ double kso_loss(int loss, const double *u, const double *y, int64_t n) {
 void kso_loss_grad(int loss, const double *u, const double *y, int64_t n, double *grad) {
   for (int64_t i = 0; i < n; ++i) {
     if (loss == KSO_LOSS_LSQ) grad[i] = 2.0 * (u[i] - y[i]);
+    else if (loss == KSO_LOSS_SQHINGE) grad[i] = -2.0 * y[i] * fmax(0.0, 1.0 - y[i] * u[i]);
     else {  /* d/du log(1+exp(-y u)) = -y sigma(-y u) */
       double t = -y[i] * u[i];
       double sig = (t >= 0) ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
@@ -315,12 +318,19 @@ void kso_loss_grad(int loss, const double *u, const double *y, int64_t n, double
 
 /* -F*(-zeta), App. D.1.  Least squares: y^T zeta - ||zeta||^2 / 4.
  * Logistic (y in {-1,+1}): with q = zeta / y, -sum[(1-q)log(1-q) + q log q],
- * 0 log 0 = 0, and -inf outside q in [0,1]. */
+ * 0 log 0 = 0, and -inf outside q in [0,1].
+ * Squared hinge (y in {-1,+1}): F*(-zeta) = sum h(-y_i zeta_i) with
+ * h(z) = z + z^2/4 for z <= 0 and +inf for z > 0, so -F*(-zeta) =
+ * sum [y_i zeta_i - zeta_i^2 / 4] (y_i^2 = 1) on y_i zeta_i >= 0, -inf elsewhere. */
 double kso_neg_conj(int loss, const double *zeta, const double *y, int64_t n) {
   double t = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     if (loss == KSO_LOSS_LSQ) t += y[i] * zeta[i] - 0.25 * zeta[i] * zeta[i];
-    else {
+    else if (loss == KSO_LOSS_SQHINGE) {
+      double z = -y[i] * zeta[i];
+      if (z > 0.0) return -INFINITY;
+      t -= z + 0.25 * z * z;
+    } else {
       double q = zeta[i] / y[i];
       if (q < 0.0 || q > 1.0) return -INFINITY;
       double h = 0.0;
@@ -391,7 +401,7 @@ double kso_power_iteration(const void *X, int xdt, int64_t n, int64_t p, int64_t
 static double lipschitz(const kso_solve_args *a) {
   if (a->L > 0) return a->L;
   double lmax = kso_power_iteration(a->X, a->x_dtype, a->n, a->p, a->ldx, 1e-10, 10000, NULL);
-  double cf = (a->loss == KSO_LOSS_LSQ) ? 2.0 : 0.25;
+  double cf = (a->loss == KSO_LOSS_LOGISTIC) ? 0.25 : 2.0;
   return cf * lmax * (1.0 + 1e-6);
 }
 

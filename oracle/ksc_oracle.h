@@ -35,7 +35,9 @@
 extern "C" {
 #endif
 
-enum { KSO_LOSS_LSQ = 0, KSO_LOSS_LOGISTIC = 1 };
+/* losses (App. D.1): least squares ||u - y||^2, logistic sum log(1 + e^{-y u}),
+ * squared hinge sum max(0, 1 - y u)^2 (y in {-1, +1} for the last two) */
+enum { KSO_LOSS_LSQ = 0, KSO_LOSS_LOGISTIC = 1, KSO_LOSS_SQHINGE = 2 };
 enum { KSO_X_F64 = 0, KSO_X_F32 = 1 };
 enum { KSO_FREE = 0, KSO_ZERO = 1, KSO_ONE = 2 };
 enum {

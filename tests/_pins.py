@@ -180,10 +180,10 @@ def prox_threshold_form(w, k, rho, M):
 
 def ridge_box(X, y, lam, M, loss=0):
     """min F(X b) + lam ||b||^2 s.t. |b| <= M (least squares via bounded LS,
-    logistic via L-BFGS-B)."""
+    logistic and squared hinge via L-BFGS-B)."""
     n, s = X.shape
     if s == 0:
-        return (float(y @ y) if loss == 0 else float(n * np.log(2.0))), np.zeros(0)
+        return float({0: y @ y, 1: n * np.log(2.0), 2: n}[loss]), np.zeros(0)
     if loss == 0:
         A = np.vstack([X, np.sqrt(lam) * np.eye(s)])
         rhs = np.concatenate([y, np.zeros(s)])
@@ -192,6 +192,9 @@ def ridge_box(X, y, lam, M, loss=0):
         return float(np.sum((X @ b - y) ** 2) + lam * b @ b), b
 
     def f(b):
+        if loss == 2:                      # squared hinge, C^1: L-BFGS-B still applies
+            m = np.maximum(0.0, 1.0 - y * (X @ b))
+            return float(m @ m + lam * b @ b), X.T @ (-2.0 * y * m) + 2 * lam * b
         t = -y * (X @ b)
         v = np.logaddexp(0, t).sum() + lam * b @ b
         sg = 1.0 / (1.0 + np.exp(-t))
@@ -256,6 +259,8 @@ def conj_numeric(loss, zeta, y):
     for zi, yi in zip(zeta, y):
         if loss == 0:
             f = lambda u: (u - yi) ** 2 + zi * u
+        elif loss == 2:
+            f = lambda u: max(0.0, 1.0 - yi * u) ** 2 + zi * u
         else:
             f = lambda u: np.logaddexp(0, -yi * u) + zi * u
         r = optimize.minimize_scalar(f, bounds=(-60, 60), method="bounded",

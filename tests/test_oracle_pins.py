@@ -234,25 +234,48 @@ def test_gstar_is_attained_at_lemma_maximiser():
 
 # ------------------------------------------------------ losses (App. D.1)
 
-@pytest.mark.parametrize("loss", [0, 1])
+@pytest.mark.parametrize("loss", [0, 1, 2])
 def test_negative_conjugate_vs_numeric_inf(loss):
     rng = np.random.default_rng(1200 + loss)
     n = 12
     if loss == 0:
         y = rng.standard_normal(n)
         zeta = rng.standard_normal(n)
-    else:
+    elif loss == 1:
         y = np.where(rng.random(n) < 0.5, -1.0, 1.0)
         zeta = y * rng.uniform(0.02, 0.98, n)
+    else:
+        y = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+        zeta = y * rng.uniform(0.0, 3.0, n)
     assert abs(O.neg_conj(loss, zeta, y) - P.conj_numeric(loss, zeta, y)) < 1e-7
+
+
+def test_squared_hinge_conjugate_domain_and_fenchel_young():
+    # outside y zeta >= 0 the infimum of F(u) + zeta^T u is unbounded below; at
+    # zeta = -grad F(u) Fenchel-Young holds with equality, elsewhere as >=
+    rng = np.random.default_rng(1250)
+    n = 15
+    y = np.where(rng.random(n) < 0.5, -1.0, 1.0)
+    bad = y * rng.uniform(0.0, 2.0, n)
+    bad[3] = -0.1 * y[3]
+    assert O.neg_conj(2, bad, y) == -np.inf
+    u = 2.0 * rng.standard_normal(n)
+    zeta = -O.loss_grad(2, u, y)
+    assert np.all(y * zeta >= 0)
+    assert abs(O.loss(2, u, y) + zeta @ u - O.neg_conj(2, zeta, y)) < 1e-12 * n
+    for _ in range(20):
+        v = rng.standard_normal(n)
+        assert O.loss(2, v, y) + zeta @ v >= O.neg_conj(2, zeta, y) - 1e-12
 
 
 def test_loss_gradients_by_finite_differences():
     rng = np.random.default_rng(1300)
     n = 9
-    for loss in (0, 1):
+    for loss in (0, 1, 2):
         y = rng.standard_normal(n) if loss == 0 else np.where(rng.random(n) < .5, -1., 1.)
         u = rng.standard_normal(n)
+        if loss == 2:                 # keep off the kink 1 - y u = 0
+            u = np.where(np.abs(1 - y * u) < 1e-3, u + 0.01, u)
         g = O.loss_grad(loss, u, y)
         h = 1e-6
         for i in range(n):
@@ -305,7 +328,22 @@ def test_k_equals_p_with_active_box_matches_bounded_ls():
     assert abs(r.primal - v) < 1e-9 * v
 
 
-@pytest.mark.parametrize("loss", [0, 1])
+def test_squared_hinge_k_equals_p_is_box_l2_svm():
+    # k = p: the perspective term is lambda2 ||b||^2 on the box, so the relaxation
+    # is the box-constrained squared-hinge ridge problem (an L2-SVM)
+    rng = np.random.default_rng(1450)
+    n, p = 40, 7
+    X = rng.standard_normal((n, p))
+    y = np.where(X[:, 0] - 0.5 * X[:, 1] + 0.4 * rng.standard_normal(n) > 0, 1.0, -1.0)
+    lam, M = 0.3, 0.6
+    r = O.solve(X, y, 2, lam, M, p, tol=1e-13, max_iter=200000)
+    v, b = P.ridge_box(X, y, lam, M, loss=2)
+    assert r.status == "converged"
+    assert abs(r.primal - v) < 1e-8 * v
+    assert np.max(np.abs(r.beta - b)) < 1e-4
+
+
+@pytest.mark.parametrize("loss", [0, 1, 2])
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_weak_duality_against_mip_enumeration(loss, seed):
     rng = np.random.default_rng(1500 + seed)
