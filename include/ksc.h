@@ -58,7 +58,8 @@ typedef enum {
 
 typedef enum {
   KSC_LOSS_LSQ = 0,             /* F(u) = ||u - y||^2                     (App. D.1) */
-  KSC_LOSS_LOGISTIC = 1         /* F(u) = sum log(1 + exp(-y_i u_i)), y = +-1        */
+  KSC_LOSS_LOGISTIC = 1,        /* F(u) = sum log(1 + exp(-y_i u_i)), y = +-1        */
+  KSC_LOSS_SQHINGE = 2          /* F(u) = sum max(0, 1 - y_i u_i)^2, y = +-1         */
 } ksc_loss;
 
 typedef enum {

@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "gen.c")
 _OUT = os.path.join(_HERE, "_build", "libksc_gen.so")
 _lib = None
 
-LSQ, LOGISTIC = 0, 1
+LSQ, LOGISTIC, SQHINGE = 0, 1, 2   # labels +-1 for the last two
 F64, F32, BF16 = "f64", "f32", "bf16"
 _DT_CODE = {F64: 0, F32: 1, BF16: 2}
 
@@ -128,7 +128,8 @@ def make_problem(n, p, *, r=0.5, seed=0, loss=LSQ, k_true=5, snr=5.0, x_dtype=F6
                  lambda2=1.0, M=2.0, k=5) -> Problem:
     """Rows ~ N(0, Toeplitz r^|j-l|), standardised columns, beta* with k_true
     entries +-1 at seeded positions; least squares: y = X beta* + noise with
-    sigma^2 = ||X beta*||^2 / (n SNR); logistic: P(y_i = +1) = sigmoid(x_i^T beta*)."""
+    sigma^2 = ||X beta*||^2 / (n SNR); logistic and squared hinge:
+    P(y_i = +1) = sigmoid(x_i^T beta*)."""
     support = np.sort(_choose(seed, _S_SUPPORT, p, min(k_true, p)))
     signs = np.where(uniform(seed, _S_SIGN, support.size) < 0.5, -1.0, 1.0)
     beta_star = np.zeros(p)

@@ -51,6 +51,10 @@ __device__ __forceinline__ double loss_d(double u, double y, int loss) {
     const double r = u - y;
     return r * r;
   }
+  if (loss == kLossSqHinge) {
+    const double m = fmax(0.0, 1.0 - y * u);
+    return m * m;
+  }
   const double t = -y * u;
   return t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
 }
@@ -83,6 +87,15 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
         dr = (float)(2.0 * du);                          // grad F = 2 (u - y)
         const double z = -2.0 * (ug - (double)y);        // zeta = -grad F (FP64: u - y cancels)
         nc += (double)y * z - 0.25 * z * z;              // -F*(-zeta), App. D.1
+        term = 0.0f;
+      } else if (d.loss == kLossSqHinge) {
+        // grad F = -2 y max(0, 1 - y u): where both margins are positive the
+        // difference is 2 (u - u_ref) exactly; elsewhere from the two margins
+        const double mg = fmax(0.0, 1.0 - (double)y * ug);
+        const double mr = fmax(0.0, 1.0 - (double)y * __ldg(&Ur[i]));
+        dr = (mg > 0.0 && mr > 0.0) ? (float)(2.0 * du) : (float)(-2.0 * (double)y * (mg - mr));
+        const double z = 2.0 * (double)y * mg;          // zeta = -grad F, y zeta = 2 m >= 0
+        nc += (double)y * z - 0.25 * z * z;
         term = 0.0f;
       } else {
         // grad F = -y sigma(t), t = -y u;  sigma(t) - sigma(t_ref)
@@ -325,7 +338,9 @@ __global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, const int* li
   const int cur = nd->cur;
   for (int i = blockIdx.x * 256 + (int)threadIdx.x; i < d.n; i += gridDim.x * 256) {
     const double u = ur[i], y = d.y[i];
-    rr[i] = d.loss == kLossLsq ? 2.0 * (u - y) : -y * sigmoid_d(-y * u);
+    rr[i] = d.loss == kLossLsq       ? 2.0 * (u - y)
+            : d.loss == kLossSqHinge ? -2.0 * y * fmax(0.0, 1.0 - y * u)
+                                     : -y * sigmoid_d(-y * u);
     if (init) {
       U[i] = u;
       U[(size_t)d.ldn + i] = u;
@@ -381,6 +396,14 @@ __global__ void __launch_bounds__(kBThreads) k_bcert_rows(BatchDev d, const int*
       const double res = ui - yi;
       f += res * res;
       const double zi = -2.0 * res;
+      z[i] = zi;
+      nc += yi * zi - 0.25 * zi * zi;
+      mg += fabs(yi * zi) + 0.25 * zi * zi;
+      zsq += zi * zi;
+    } else if (d.loss == kLossSqHinge) {
+      const double m = fmax(0.0, 1.0 - yi * ui);
+      f += m * m;
+      const double zi = 2.0 * yi * m;   // y zeta = 2 m >= 0: inside dom F*
       z[i] = zi;
       nc += yi * zi - 0.25 * zi * zi;
       mg += fabs(yi * zi) + 0.25 * zi * zi;
@@ -455,7 +478,7 @@ __global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const i
                                                       d.z_out + (size_t)b * p);
   if (threadIdx.x == 0) {
     const double nn = (double)d.n + 8.0;
-    const double margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
+    const double margin_f = 1.01 * nn * ur * mgs + (d.loss != kLossLogistic ? 4.0 * ur * mgs : 0.0);
     const double znorm = sqrt(zs) * (1.0 + ((double)d.n + 4.0) * ur);
     const double eps_a = err_a * cmax * znorm + 1e-30;
     const int nsel = (kp < p ? kp : p) + n1;

@@ -69,8 +69,8 @@ __global__ void __launch_bounds__(256, 3) k_dfprod(const TX* __restrict__ A, int
       const int e = (int)threadIdx.x + t * 256;
       As[e / kDfCols][e % kDfCols] = ra[t];
     }
-#pragma unroll
     int nz = 0;
+#pragma unroll
     for (int t = 0; t < kVPer; ++t) {
       const int e = (int)threadIdx.x + t * 256;
       const float h = (float)rv[t];

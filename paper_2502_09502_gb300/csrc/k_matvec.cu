@@ -136,6 +136,11 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         r = 2.0 * (ug - yi);
         const double z = -r;
         nc += yi * z - 0.25 * z * z;
+      } else if (d.loss == kLossSqHinge) {
+        const double m = fmax(0.0, 1.0 - yi * ug);   // grad F = -2 y max(0, 1 - y u)
+        r = -2.0 * yi * m;
+        const double z = -r;                        // y z = 2 m >= 0: in dom F*
+        nc += yi * z - 0.25 * z * z;
       } else {
         const double s = sigmoid(-yi * ug);
         r = -yi * s;
@@ -339,6 +344,19 @@ __device__ __forceinline__ void row_epilogue(const Dev& d, int row, double u, in
       a.mg += fabs(yi * z) + 0.25 * z * z;
       a.zsq += z * z;
     }
+  } else if (d.loss == kLossSqHinge) {
+    const double m = fmax(0.0, 1.0 - yi * u);
+    a.f += m * m;
+    if (MODE == kFCert) {
+      // zeta = 2 y m (y = +-1: y zeta = 2 m >= 0 exactly, inside dom F*);
+      // -F*(-zeta) = y^T zeta - ||zeta||^2 / 4, App. D.1, as for least squares
+      const double z = 2.0 * yi * m;
+      d.u64[row] = u;
+      d.zeta[row] = z;
+      a.nc += yi * z - 0.25 * z * z;
+      a.mg += fabs(yi * z) + 0.25 * z * z;
+      a.zsq += z * z;
+    }
   } else {
     const double t = -yi * u;
     a.f += t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
@@ -424,7 +442,7 @@ __device__ void finish_rows(const Dev& d, RowAcc a, double* red, int* s_last, in
       const double nn = (double)d.n + 8.0;
       nd->cert_f = f;
       nd->cert_negconj = ncs;
-      nd->cert_margin_f = 1.01 * nn * ur * mgs + (d.loss == kLossLsq ? 4.0 * ur * mgs : 0.0);
+      nd->cert_margin_f = 1.01 * nn * ur * mgs + (d.loss != kLossLogistic ? 4.0 * ur * mgs : 0.0);
       nd->cert_zeta_sq = zs;
     }
   }

@@ -173,13 +173,35 @@ __device__ __forceinline__ float loss_term(float u, float y, int loss) {
   return fmaxf(t, 0.0f) + log1pf(expf(-fabsf(t)));
 }
 
+// F_i(u) added to an FP64 sum (least squares, squared hinge: the difference
+// u - y or 1 - y u cancels near the fit) or to an FP32 one (logistic)
+__device__ __forceinline__ void add_loss(double u, float y, int loss, double& fd, float& fa) {
+  if (loss == kLossLsq) {
+    const double r = u - (double)y;
+    fd += r * r;
+  } else if (loss == kLossSqHinge) {
+    const double m = fmax(0.0, 1.0 - (double)y * u);
+    fd += m * m;
+  } else {
+    fa += loss_term((float)u, y, loss);
+  }
+}
+
 // F_i(u + d) - F_i(u) without cancellation: least squares d (2 (u - y) + d);
-// logistic log1p(expm1(-y d) sigma(-y u)), since
+// squared hinge with s = 1 - y u, t = -y d: t (2 s + t) where s and s + t are
+// both positive, else max(0, s + t)^2 - max(0, s)^2; logistic
+// log1p(expm1(-y d) sigma(-y u)), since
 // (1 + e^{-y(u+d)}) / (1 + e^{-y u}) = 1 + (e^{-y d} - 1) e^{-y u} / (1 + e^{-y u})
 __device__ __forceinline__ float loss_change(double u, float d, float y, int loss) {
   if (loss == kLossLsq) {
     const float r = (float)(u - (double)y);
     return d * (2.0f * r + d);
+  }
+  if (loss == kLossSqHinge) {
+    const float s = (float)(1.0 - (double)y * u), t = -y * d;
+    if (s > 0.0f && s + t > 0.0f) return t * (2.0f * s + t);
+    const float m = fmaxf(s, 0.0f), mn = fmaxf(s + t, 0.0f);
+    return mn * mn - m * m;
   }
   if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
   const float s = 1.0f / (1.0f + expf(y * (float)u));   // sigma(-y u)
@@ -357,13 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const double un = brow[nc + i] + (double)v[i];
                 uout[nc + i] = un;
                 const float yi = __ldg(&ep.y[nc + i]);
-                if (ep.loss == kLossLsq) {
-                  // (u - y)^2 in FP64: u - y cancels when the fit is good
-                  const double r = un - (double)yi;
-                  fd += r * r;
-                } else {
-                  fa += loss_term((float)un, yi, ep.loss);
-                }
+                add_loss(un, yi, ep.loss, fd, fa);
                 da += loss_change(uo, (float)(un - uo), yi, ep.loss);
               }
             }
@@ -487,12 +503,8 @@ __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, co
       const float y0 = (i & 1) ? yq.z : yq.x, y1 = (i & 1) ? yq.w : yq.y;
       const double un0 = b.x + (double)v[2 * i], un1 = b.y + (double)v[2 * i + 1];
       w2[i] = make_double2(un0, un1);
-      if (ep.loss == kLossLsq) {
-        const double r0 = un0 - (double)y0, r1 = un1 - (double)y1;
-        fd += r0 * r0 + r1 * r1;
-      } else {
-        fa += loss_term((float)un0, y0, ep.loss) + loss_term((float)un1, y1, ep.loss);
-      }
+      add_loss(un0, y0, ep.loss, fd, fa);
+      add_loss(un1, y1, ep.loss, fd, fa);
       da += loss_change(uo.x, (float)(un0 - uo.x), y0, ep.loss) + loss_change(uo.y, (float)(un1 - uo.y), y1, ep.loss);
     }
     fsum += (double)fa + fd;
@@ -514,12 +526,7 @@ __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, co
         const double un = r.brow[nc + i] + (double)v[i];
         r.uout[nc + i] = un;
         const float yi = __ldg(&ep.y[nc + i]);
-        if (ep.loss == kLossLsq) {
-          const double rr = un - (double)yi;
-          fd += rr * rr;
-        } else {
-          fa += loss_term((float)un, yi, ep.loss);
-        }
+        add_loss(un, yi, ep.loss, fd, fa);
         da += loss_change(uo, (float)(un - uo), yi, ep.loss);
       }
     }

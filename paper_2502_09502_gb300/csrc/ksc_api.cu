@@ -220,7 +220,8 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-7 * theta)) break;
     prev = theta;
   }
-  const double cf = pr->loss == KSC_LOSS_LSQ ? 2.0 : 0.25;
+  // F' is 2-Lipschitz for least squares and the squared hinge, 1/4 for logistic
+  const double cf = pr->loss == KSC_LOSS_LOGISTIC ? 0.25 : 2.0;
   pr->L = cf * theta * 1.01;
   return KSC_OK;
 }
@@ -247,7 +248,7 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
         return fail(KSC_ERR_INVALID_ARG, "col_scale entries must be powers of two in [2^-100, 2^100]");
     }
   }
-  if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC)
+  if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC && desc->loss != KSC_LOSS_SQHINGE)
     return fail(KSC_ERR_INVALID_ARG, "unknown loss");
   if (!desc->X || !desc->y) return fail(KSC_ERR_INVALID_ARG, "X and y must be non-NULL");
   const int64_t ldx = desc->ldx == 0 ? desc->p : desc->ldx;
@@ -255,8 +256,8 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   for (int64_t i = 0; i < desc->n; ++i) {
     const double v = desc->y[i];
     if (!std::isfinite(v)) return fail(KSC_ERR_INVALID_ARG, "y has a non-finite entry");
-    if (desc->loss == KSC_LOSS_LOGISTIC && v != 1.0 && v != -1.0)
-      return fail(KSC_ERR_INVALID_ARG, "logistic labels must be +1 or -1");
+    if (desc->loss != KSC_LOSS_LSQ && v != 1.0 && v != -1.0)
+      return fail(KSC_ERR_INVALID_ARG, "logistic and squared-hinge labels must be +1 or -1");
   }
   ksc_status st = ensure_prepared();
   if (st != KSC_OK) return st;

@@ -550,7 +550,8 @@ ksc_status zero_anchor_prepare(Session* se) {
   const int n = (int)pr->n;
   std::vector<double> r0(n);
   for (int i = 0; i < n; ++i)
-    r0[i] = pr->loss == KSC_LOSS_LSQ ? -2.0 * pr->y_host[i] : -0.5 * pr->y_host[i];   // grad F at u = 0
+    // grad F at u = 0: least squares -2 y, squared hinge -2 y (margin 1), logistic -y/2
+    r0[i] = pr->loss == KSC_LOSS_LOGISTIC ? -0.5 * pr->y_host[i] : -2.0 * pr->y_host[i];
   cudaStream_t s = se->s;
   KB_CUDA(cudaMemcpyAsync(ws->r0, r0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
   const int zero_row = 0;

@@ -80,7 +80,7 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
   std::vector<double> cn(p);
   if (cudaMemcpy(cn.data(), pr->dev.colnorm, (size_t)p * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
     return api_fail(KSC_ERR_CUDA, "column norms");
-  const double curv = pr->loss == KSC_LOSS_LSQ ? 1.0 : 0.25;
+  const double curv = pr->loss == KSC_LOSS_LOGISTIC ? 0.25 : 1.0;
 
   Session se;
   if ((st = session_open(&se, pr, prm->batch, true, s)) != KSC_OK) return st;

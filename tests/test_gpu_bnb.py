@@ -26,7 +26,12 @@ def K():
 
 def _objective(X, y, loss, lam, b):
     u = X @ b
-    f = np.sum((u - y) ** 2) if loss == G.LSQ else np.sum(np.logaddexp(0.0, -y * u))
+    if loss == G.LSQ:
+        f = np.sum((u - y) ** 2)
+    elif loss == G.SQHINGE:
+        f = np.sum(np.maximum(0.0, 1.0 - y * u) ** 2)
+    else:
+        f = np.sum(np.logaddexp(0.0, -y * u))
     return float(f + lam * b @ b)
 
 
@@ -35,17 +40,18 @@ CASES = [  # loss, n, p, k, lambda2, M, r, seed
     (G.LSQ, 200, 14, 4, 0.1, 2.0, 0.9, 2),
     (G.LOGISTIC, 160, 11, 3, 0.2, 2.0, 0.5, 3),
     (G.LOGISTIC, 240, 12, 2, 0.05, 3.0, 0.1, 4),
+    (G.SQHINGE, 160, 11, 3, 0.2, 2.0, 0.5, 5),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{'ls' if c[0] == G.LSQ else 'logit'}_p{c[2]}_k{c[3]}")
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{['ls', 'logit', 'sqhinge'][c[0]]}_p{c[2]}_k{c[3]}")
 def test_bnb_certifies_the_enumerated_optimum(K, case):
     loss, n, p, k, lam, M, r, seed = case
     Pm = G.make_problem(n, p, r=r, seed=seed, loss=loss, k_true=min(k, 3), snr=3.0, x_dtype=G.BF16,
                         lambda2=lam, M=M, k=k)
     X = Pm.X64()
     opt = P.mip_enumerate(X, Pm.y, lam, M, k, loss)
-    prob = K.Problem(Pm.X, Pm.y, K.KSC_LOSS_LSQ if loss == G.LSQ else K.KSC_LOSS_LOGISTIC, x_dtype=K.KSC_BF16)
+    prob = K.Problem(Pm.X, Pm.y, loss, x_dtype=K.KSC_BF16)
     beta, res = prob.bnb(lam, M, k, opt_gap=1e-5, batch=64, node_rel_gap=1e-7, node_max_iter=30000)
     assert res["certified"], res
     assert res["lower_bound"] <= opt + 1e-9 * abs(opt)
