@@ -27,6 +27,16 @@
  *      +inf (the value of g there, by the convention of Sec. 3).
  *  R10 Warm start: S0 coordinates set to 0 and all coordinates clipped to
  *      [-M, M] before the first step (Algorithm 3 starts from beta^0 = beta^1).
+ *  R20 Eigen-perspective bound (App. D.2): the objective keeps its constant
+ *      ||y||^2 (so that the bound is one of ||X b - y||^2 + lambda2 ||b||^2 and
+ *      equals the Sec. 3.4 bound at lambda = 0): F(b) = b^T Q b and G(b) =
+ *      -2 y^T X b + ||y||^2 + 2 lambda_eig g(b), whence the bound
+ *      ||y||^2 - b^T Q b - 2 lambda_eig g*((X^T y - Q b) / lambda_eig); the
+ *      printed final inequality carries the signs of -F* and -G* as +.  The
+ *      smooth part that Algorithm 3 steps on is b^T Q b - 2 y^T X b + ||y||^2,
+ *      with gradient 2 X^T (X b - y) - 2 lambda b and Lipschitz constant
+ *      2 (lambda_max - lambda); the prox is that of 2 lambda_eig g.  With fixed
+ *      sets the same g_node replaces g (R2).
  */
 #include "ksc_oracle.h"
 
@@ -402,7 +412,14 @@ static double lipschitz(const kso_solve_args *a) {
   if (a->L > 0) return a->L;
   double lmax = kso_power_iteration(a->X, a->x_dtype, a->n, a->p, a->ldx, 1e-10, 10000, NULL);
   double cf = (a->loss == KSO_LOSS_LOGISTIC) ? 0.25 : 2.0;
+  if (a->eig > 0) return 2.0 * (lmax * (1.0 + 1e-6) - a->eig);   /* R20 */
   return cf * lmax * (1.0 + 1e-6);
+}
+
+static double sumsq(const double *v, int64_t m) {
+  double s = 0.0;
+  for (int64_t i = 0; i < m; ++i) s += v[i] * v[i];
+  return s;
 }
 
 double kso_primal(const kso_solve_args *a, const double *beta) {
@@ -411,10 +428,35 @@ double kso_primal(const kso_solve_args *a, const double *beta) {
   double f = kso_loss(a->loss, u, a->y, a->n);
   double g = kso_g_node(beta, a->p, a->state, a->k, a->M, NULL);
   free(u);
+  if (a->eig > 0)   /* b^T Q b - 2 y^T X b + ||y||^2 + 2 lambda_eig g(b), R20 */
+    return f - a->eig * sumsq(beta, a->p) + 2.0 * (a->lambda2 + a->eig) * g;
   return f + 2.0 * a->lambda2 * g;
 }
 
+/* App. D.2: ||y||^2 - b^T Q b - G*_node(2 (X^T y - Q b)) with Q b = X^T X b - eig b
+ * and G*_node the conjugate of 2 lambda_eig g_node (R20). */
+static double eig_dual_bound(const kso_solve_args *a, const double *beta) {
+  int64_t n = a->n, p = a->p;
+  double *u = (double *)malloc((size_t)n * sizeof(double));
+  double *qb = (double *)malloc((size_t)p * sizeof(double));
+  double *xty = (double *)malloc((size_t)p * sizeof(double));
+  kso_matvec(a->X, a->x_dtype, n, p, a->ldx, beta, u);
+  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, u, qb);
+  for (int64_t j = 0; j < p; ++j) qb[j] -= a->eig * beta[j];          /* Q b */
+  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, a->y, xty);
+  double bqb = 0.0;
+  for (int64_t j = 0; j < p; ++j) {
+    bqb += beta[j] * qb[j];
+    xty[j] = 2.0 * (xty[j] - qb[j]);                                  /* a */
+  }
+  double d = sumsq(a->y, n) - bqb
+           - kso_Gstar_node(xty, p, a->state, a->k, a->lambda2 + a->eig, a->M);
+  free(u); free(qb); free(xty);
+  return d;
+}
+
 double kso_dual_bound(const kso_solve_args *a, const double *beta) {
+  if (a->eig > 0) return eig_dual_bound(a, beta);
   int64_t n = a->n, p = a->p;
   double *u = (double *)malloc((size_t)n * sizeof(double));
   double *zeta = (double *)malloc((size_t)n * sizeof(double));
@@ -439,7 +481,8 @@ int kso_solve(const kso_solve_args *a, double *beta, double *z, double *trace,
     return 0;
   }
   double L = lipschitz(a);
-  double rho = L / (2.0 * a->lambda2);
+  double lam = a->lambda2 + (a->eig > 0 ? a->eig : 0.0);   /* lambda_eig, R20 */
+  double rho = L / (2.0 * lam);
   out->L = L;
   double *bprev = (double *)malloc((size_t)p * sizeof(double));
   double *bcur = (double *)malloc((size_t)p * sizeof(double));
@@ -465,6 +508,8 @@ int kso_solve(const kso_solve_args *a, double *beta, double *z, double *trace,
     kso_matvec(a->X, a->x_dtype, n, p, a->ldx, gam, u);
     kso_loss_grad(a->loss, u, a->y, n, r);
     kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, r, grad);   /* grad F(gamma) */
+    if (a->eig > 0)                                          /* - 2 eig gamma, R20 */
+      for (int64_t j = 0; j < p; ++j) grad[j] -= 2.0 * a->eig * gam[j];
     for (int64_t j = 0; j < p; ++j) gam[j] -= grad[j] / L;  /* line 7 */
     memcpy(bprev, bcur, (size_t)p * sizeof(double));
     kso_prox_g_node(gam, p, a->state, a->k, rho, a->M, bcur, NULL);  /* line 8 */

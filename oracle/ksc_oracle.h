@@ -101,6 +101,11 @@ typedef struct {
   int64_t max_iter;
   int32_t restart, momentum;   /* Algorithm 3 as printed: both 1      */
   double incumbent;        /* +inf: no early termination              */
+  double eig;              /* least squares only: 0 = the perspective
+                              relaxation; lambda in (0, lambda_min(X^T X)]
+                              = the eigen-perspective relaxation of App. D.2
+                              with Q = X^T X - lambda I, lambda_eig =
+                              lambda2 + lambda                         */
 } kso_solve_args;
 
 typedef struct {
@@ -116,9 +121,11 @@ typedef struct {
  * per iteration. */
 int kso_solve(const kso_solve_args *a, double *beta, double *z, double *trace,
               kso_solve_out *out);
-/* The weak-duality bound -F*(-zeta) - G*(X^T zeta) at zeta = -grad F(X beta). */
+/* The weak-duality bound -F*(-zeta) - G*(X^T zeta) at zeta = -grad F(X beta);
+ * with eig > 0 the eigen-perspective bound of App. D.2 at zeta = -2 Q beta. */
 double kso_dual_bound(const kso_solve_args *a, const double *beta);
-/* The primal value F(X beta) + 2 lambda2 g_node(beta). */
+/* The primal value F(X beta) + 2 lambda2 g_node(beta); with eig > 0
+ * ||X beta - y||^2 - eig ||beta||^2 + 2 (lambda2 + eig) g_node(beta). */
 double kso_primal(const kso_solve_args *a, const double *beta);
 
 #ifdef __cplusplus

@@ -57,7 +57,8 @@ class SolveArgs(C.Structure):
                 ("ldx", C.c_int64), ("y", _dp), ("loss", C.c_int32), ("lambda2", C.c_double),
                 ("M", C.c_double), ("k", C.c_int64), ("state", _i8p), ("warm", _dp),
                 ("L", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int64),
-                ("restart", C.c_int32), ("momentum", C.c_int32), ("incumbent", C.c_double)]
+                ("restart", C.c_int32), ("momentum", C.c_int32), ("incumbent", C.c_double),
+                ("eig", C.c_double)]
 
 
 class SolveOut(C.Structure):
@@ -255,7 +256,9 @@ class _Args:
 
     def __init__(self, X, y, loss_kind, lambda2, M, k, state=None, warm=None, L=0.0,
                  tol=1e-12, max_iter=100000, restart=True, momentum=True,
-                 incumbent=float("inf")):
+                 incumbent=float("inf"), eig=0.0):
+        if eig and loss_kind != 0:
+            raise ValueError("the eigen-perspective relaxation is for least squares")
         self.X, dt = _xptr(X)
         n, p = self.X.shape
         self.y, py = _d(y)
@@ -268,16 +271,17 @@ class _Args:
             self.warm, pwm = None, None
         self.c = SolveArgs(self.X.ctypes.data, dt, n, p, p, py, int(loss_kind), float(lambda2),
                            float(M), int(k), ps, pwm, float(L), float(tol), int(max_iter),
-                           int(bool(restart)), int(bool(momentum)), float(incumbent))
+                           int(bool(restart)), int(bool(momentum)), float(incumbent), float(eig))
         self.n, self.p = n, p
 
 
 def solve(X, y, loss_kind, lambda2, M, k, state=None, warm=None, L=0.0, tol=1e-12,
           max_iter=100000, restart=True, momentum=True, incumbent=float("inf"),
-          want_trace=False):
-    """Restarted FISTA (Algorithm 3) on the node problem, in FP64."""
+          want_trace=False, eig=0.0):
+    """Restarted FISTA (Algorithm 3) on the node problem, in FP64; eig > 0: the
+    eigen-perspective relaxation of App. D.2 with Q = X^T X - eig I."""
     a = _Args(X, y, loss_kind, lambda2, M, k, state, warm, L, tol, max_iter, restart,
-              momentum, incumbent)
+              momentum, incumbent, eig)
     beta = np.zeros(a.p)
     z = np.zeros(a.p)
     trace = np.zeros(2 * max_iter) if want_trace else None
@@ -289,13 +293,20 @@ def solve(X, y, loss_kind, lambda2, M, k, state=None, warm=None, L=0.0, tol=1e-1
                        STATUS[out.status], tr)
 
 
-def dual_bound(X, y, loss_kind, lambda2, M, k, beta, state=None):
-    a = _Args(X, y, loss_kind, lambda2, M, k, state)
+def dual_bound(X, y, loss_kind, lambda2, M, k, beta, state=None, eig=0.0):
+    a = _Args(X, y, loss_kind, lambda2, M, k, state, eig=eig)
     b, pb = _d(beta)
     return lib().kso_dual_bound(C.byref(a.c), pb)
 
 
-def primal(X, y, loss_kind, lambda2, M, k, beta, state=None):
-    a = _Args(X, y, loss_kind, lambda2, M, k, state)
+def primal(X, y, loss_kind, lambda2, M, k, beta, state=None, eig=0.0):
+    a = _Args(X, y, loss_kind, lambda2, M, k, state, eig=eig)
     b, pb = _d(beta)
     return lib().kso_primal(C.byref(a.c), pb)
+
+
+def lambda_min(X):
+    """lambda_min(X^T X) (App. D.2) by a dense symmetric eigensolver in FP64
+    (numpy's LAPACK routine as the step), clipped at 0."""
+    X = np.asarray(X, dtype=np.float64)
+    return max(0.0, float(np.linalg.eigvalsh(X.T @ X)[0]))

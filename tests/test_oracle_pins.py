@@ -432,3 +432,87 @@ def test_dual_bound_is_valid_at_any_iterate():
     for _ in range(5):
         b = rng.standard_normal(15) * 0.3
         assert O.dual_bound(X, y, 0, 0.4, 1.5, 3, b) <= r.primal + 1e-10 * r.primal
+
+
+# ------------------------------------------- eigen-perspective bound (App. D.2)
+
+def _eig_problem(seed, n=40, p=8, k=3, noise=0.4):
+    rng = np.random.default_rng(1700 + seed)
+    X = rng.standard_normal((n, p))
+    X[:, 1] += 0.6 * X[:, 0]            # correlated columns: lambda_min well below the mean
+    bt = np.zeros(p)
+    bt[rng.choice(p, k, replace=False)] = rng.choice([-1.0, 1.0], k)
+    return X, X @ bt + noise * rng.standard_normal(n), rng
+
+
+def test_lambda_min_is_the_smallest_eigenvalue():
+    X, _, rng = _eig_problem(0)
+    lam = O.lambda_min(X)
+    A = X.T @ X
+    # positive semidefinite at lambda_min and not above it (Rayleigh quotients)
+    assert np.all(np.linalg.eigvalsh(A - lam * np.eye(8)) >= -1e-9 * lam)
+    for _ in range(50):
+        v = rng.standard_normal(8)
+        assert v @ A @ v / (v @ v) >= lam * (1 - 1e-12)
+    assert O.lambda_min(rng.standard_normal((5, 9))) == 0.0   # n < p: singular
+
+
+def test_eig_bound_at_lambda_to_zero_is_the_perspective_bound():
+    # the eigen bound's lambda-free part is the Sec. 3.4 bound for least squares
+    X, y, rng = _eig_problem(1)
+    for _ in range(5):
+        b = rng.uniform(-1, 1, 8)
+        for st in (None, np.array([0, 1, 0, 2, 0, 0, 1, 0], np.int8)):
+            d0 = O.dual_bound(X, y, 0, 0.6, 1.5, 3, b, state=st)
+            de = O.dual_bound(X, y, 0, 0.6, 1.5, 3, b, state=st, eig=1e-9)
+            assert abs(de - d0) <= 1e-7 * (1 + abs(d0))
+
+
+def test_eig_relaxation_at_k_equals_p_is_the_box_ridge_problem():
+    # with k = p, 2 lambda_eig g(b) = lambda_eig ||b||^2 on the box, so the eigen
+    # relaxation's objective is ||X b - y||^2 + lambda2 ||b||^2 itself
+    X, y, _ = _eig_problem(2)
+    y = 2.5 * y
+    lam, M = 0.3, 0.7
+    eig = 0.9 * O.lambda_min(X)
+    r = O.solve(X, y, 0, lam, M, 8, tol=1e-13, max_iter=200000, eig=eig)
+    v, b = P.ridge_box(X, y, lam, M)
+    assert r.status == "converged"
+    assert abs(r.primal - v) < 1e-9 * v and abs(r.dual - v) < 1e-9 * v
+    assert np.max(np.abs(r.beta - b)) < 1e-6
+
+
+@pytest.mark.parametrize("seed", [3, 4, 5])
+def test_eig_bound_is_valid_and_tighter_than_the_perspective_bound(seed):
+    X, y, rng = _eig_problem(seed)
+    lam, M, k = 0.4, 1.5, 3
+    eig = O.lambda_min(X)
+    mip = P.mip_enumerate(X, y, lam, M, k, 0)
+    persp = O.solve(X, y, 0, lam, M, k, tol=1e-12, max_iter=200000)
+    r = O.solve(X, y, 0, lam, M, k, tol=1e-12, max_iter=200000, eig=eig)
+    assert r.status == "converged"
+    assert r.dual <= mip + 1e-9 * abs(mip)          # weak duality against P_MIP*
+    assert r.primal <= mip + 1e-9 * abs(mip)        # still a relaxation
+    assert r.dual >= persp.dual + 1e-3 * abs(mip)   # P_eig* > P_persp* on these instances
+    # a smaller shift interpolates between the two relaxations
+    r2 = O.solve(X, y, 0, lam, M, k, tol=1e-12, max_iter=200000, eig=0.5 * eig)
+    assert persp.dual - 1e-9 * abs(mip) <= r2.dual <= r.dual + 1e-9 * abs(mip)
+    # the bound holds at any point, not only at the optimum
+    for _ in range(10):
+        b = rng.uniform(-M, M, 8)
+        assert O.dual_bound(X, y, 0, lam, M, k, b, eig=eig) <= mip + 1e-9 * abs(mip)
+
+
+def test_eig_node_bound_against_node_enumeration():
+    X, y, _ = _eig_problem(6, p=9)
+    lam, M, k = 0.3, 2.0, 3
+    st = np.zeros(9, np.int8)
+    st[[2, 5]] = O.ZERO
+    st[[0]] = O.ONE
+    eig = O.lambda_min(X)
+    mip = P.mip_enumerate(X, y, lam, M, k, 0, zero=(2, 5), one=(0,))
+    r = O.solve(X, y, 0, lam, M, k, state=st, tol=1e-12, max_iter=200000, eig=eig)
+    rp = O.solve(X, y, 0, lam, M, k, state=st, tol=1e-12, max_iter=200000)
+    assert r.status == "converged"
+    assert rp.dual - 1e-9 * abs(mip) <= r.dual <= mip + 1e-9 * abs(mip)
+    assert r.beta[2] == 0 and r.beta[5] == 0
