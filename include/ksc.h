@@ -77,6 +77,13 @@ typedef enum {
 /* Node flags (ksc_node.flags): the ablations of Fig. 3. */
 #define KSC_FLAG_RESTART_OFF  0x1u   /* plain FISTA: never reset the momentum       */
 #define KSC_FLAG_MOMENTUM_OFF 0x2u   /* proximal gradient (ISTA): no momentum       */
+#define KSC_FLAG_EIG          0x4u   /* eigen-perspective relaxation (App. D.2), least
+                                        squares only: Q = X^T X - lambda I and lambda2 +
+                                        lambda on the perspective term, lambda the
+                                        problem's certified shift (ksc_problem_eig_lambda,
+                                        computed on first use by ksc_solve_batch and
+                                        ksc_bnb_solve).  Batched path only (BF16 X):
+                                        ksc_solve_node returns KSC_ERR_UNIMPLEMENTED    */
 
 typedef struct ksc_problem ksc_problem;
 typedef struct ksc_server ksc_server;
@@ -112,6 +119,24 @@ size_t ksc_problem_bytes(const ksc_problem* problem);
 /* L (Algorithm 3's step constant) and the number of power iterations used. */
 ksc_status ksc_problem_info(const ksc_problem* problem, double* lipschitz,
                             int32_t* power_iters);
+
+/* The shift lambda of the eigen-perspective relaxation (App. D.2): a certified
+ * lower bound on lambda_min(X^T X) (0 when n < p), so that Q = X^T X - lambda I is
+ * positive semidefinite whatever the rounding.  A = X^T X is formed in FP64 and
+ * bracketed by bisection on shifts c whose Cholesky factorisation of A - c I runs
+ * to completion (to 1e-3 relative); lambda is the last such c minus the rounding
+ * bound of the factorisation and of A (Higham, Thm 10.3).  Computed once per
+ * problem, then returned from the cache.  Errors: KSC_ERR_INVALID_ARG (NULL),
+ * KSC_ERR_UNIMPLEMENTED (n >= p > 8192), KSC_ERR_OOM (2 p^2 doubles of workspace),
+ * KSC_ERR_CUDA. */
+ksc_status ksc_problem_eig_lambda(ksc_problem* problem, void* cuda_stream, double* lambda);
+/* Make lambda the problem's eigen shift after certifying it: lambda = 0 is always
+ * accepted; lambda > 0 when the Cholesky factorisation of X^T X - c I, c = lambda
+ * plus its rounding margin, runs to completion (the test of
+ * ksc_problem_eig_lambda).  Errors: KSC_ERR_INVALID_ARG (NULL problem, lambda < 0
+ * or not finite, lambda not certified below lambda_min), KSC_ERR_UNIMPLEMENTED
+ * (p > 8192), KSC_ERR_OOM, KSC_ERR_CUDA. */
+ksc_status ksc_problem_set_eig_lambda(ksc_problem* problem, void* cuda_stream, double lambda);
 
 /* One branch-and-bound node (App. B.3) with its parameters (Sec. 1, Sec. 4.2). */
 typedef struct {
@@ -194,6 +219,8 @@ typedef struct {
   int32_t batch;           /* session slots (nodes in flight) */
   double node_rel_gap;     /* rel_gap_tol of every node solve */
   int32_t node_max_iter;   /* max_iter of every node solve */
+  uint32_t node_flags;     /* KSC_FLAG_* of every node solve (KSC_FLAG_EIG: the
+                              eigen-perspective node bounds of App. D.2) */
 } ksc_bnb_params;
 
 typedef struct {

@@ -132,9 +132,25 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   const int p = d.p;
   const int8_t* st = d.state + (size_t)b * d.ldp;
   double* brow = d.beta + (size_t)b * 3 * d.ldp;
-  const double* G = d.G + (size_t)b * d.ldp;
+  double* G = d.G + (size_t)b * d.ldp;
   const double lambda2 = nd->lambda2, M = nd->M;
   const int kp = nd->kp;
+  const double eig = nd->eig;
+  double gsq = 0.0;
+  if (eig > 0.0) {
+    // eigen-perspective (App. D.2): the smooth part b^T Q b - 2 y^T X b + ||y||^2
+    // has the gradient X^T grad F(X gamma) - 2 eig gamma at the momentum point
+    const double* bc = brow + (size_t)cur * d.ldp;
+    const double* bp = brow + (size_t)prev * d.ldp;
+    const double c = nd->c;
+    for (int j = threadIdx.x; j < p; j += kBProxBlock) {
+      const double g = bc[j] + c * (bc[j] - bp[j]);
+      G[j] -= 2.0 * eig * g;
+      gsq += g * g;
+    }
+    gsq = block_sum<double, kBProxBlock>(gsq, sm.red);
+    __syncthreads();
+  }
   // in-loop dual term at gamma: a = X^T zeta_gamma = -G, |a| = |G|
   const double gs = gstar_segment<double, kBProxBlock>(p, [&](int i) { return G[i]; }, st, kp, M,
                                                        0.5 / lambda2, sm);
@@ -166,16 +182,21 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   __nv_bfloat16* prow = d.bpc + (size_t)b * d.ldp;
   const double* bn = io.beta;
   const double* br = d.beta_ref + (size_t)b * d.ldp;
+  double bsq = 0.0;
   for (int j = threadIdx.x; j < p; j += kBProxBlock) {
     const double x = bn[j], r = br[j];
     // both zero (most coordinates of a sparse iterate): no FP64 arithmetic
     const float v = ((__double_as_longlong(x) | __double_as_longlong(r)) << 1) == 0 ? 0.0f : (float)(x - r);
     split_store(v, prow + j, pstride, d.P);
+    if (eig > 0.0) bsq += x * x;
   }
+  if (eig > 0.0) bsq = block_sum<double, kBProxBlock>(bsq, sm.red);
   if (threadIdx.x == 0) {
     double nc = 0.0;
     for (int t = 0; t < d.nrt; ++t) nc += d.ncpart[(size_t)b * d.nrt + t];
-    nd->negconj = nc;
+    // -F*(-zeta) at zeta = -2 Q gamma: ||y||^2 - ||X gamma||^2 + eig ||gamma||^2
+    nd->negconj = nc + eig * gsq;
+    nd->bsq_next = bsq;
     nd->gstar = gs;
     nd->g_next = o.g;
     nd->theta = o.theta;
@@ -201,9 +222,14 @@ __global__ void __launch_bounds__(128) k_bstep(BatchDev d) {
       df += fp[2 * t + 1];
     }
     // L^{t+1} - L^t = sum_i [F_i(u^{t+1}) - F_i(u^t)] + 2 lambda2 (g(beta^{t+1}) - g(beta^t))
-    const double dL = df + 2.0 * nd->lambda2 * (nd->g_next - nd->g_cur);
+    double dL = df + 2.0 * nd->lambda2 * (nd->g_next - nd->g_cur);
+    if (nd->eig > 0.0) {   // eigen-perspective: - eig ||beta||^2 in the objective
+      f -= nd->eig * nd->bsq_next;
+      dL -= nd->eig * (nd->bsq_next - nd->bsq_cur);
+    }
     fista_step_logic(nd, f, &dL);
     nd->g_cur = nd->g_next;
+    nd->bsq_cur = nd->bsq_next;
     nd->prev = nd->cur;
     nd->cur = d.slot_new[b];
     d.slot_cur[b] = nd->cur;
@@ -247,8 +273,16 @@ __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const in
   const int8_t* st = d.state + (size_t)b * d.ldp;
   const GOut o = gvalue_segment<double, kBProxBlock>(d.p, [&](int i) { return b1[i]; }, st, nd->kp, nd->M, sm,
                                                      nullptr, 1e-12);
+  double bsq = 0.0;
+  if (nd->eig > 0.0) {
+    for (int j = threadIdx.x; j < d.p; j += kBProxBlock) bsq += b1[j] * b1[j];
+    bsq = block_sum<double, kBProxBlock>(bsq, sm.red);
+  }
   if (threadIdx.x == 0) {
-    const double L1 = f + 2.0 * nd->lambda2 * o.g;
+    // eigen-perspective: F(u) - eig ||beta||^2 + 2 (lambda2 + eig) g(beta)
+    const double L1 = f - nd->eig * bsq + 2.0 * nd->lambda2 * o.g;
+    nd->bsq_cur = bsq;
+    nd->bsq_next = bsq;
     nd->g_next = o.g;
     nd->g_cur = o.g;
     nd->Lcur = L1;
@@ -443,7 +477,8 @@ __global__ void __launch_bounds__(kBThreads) k_bcert_rows(BatchDev d, const int*
 // the rounding margins of -F*(-zeta) and of a = X^T zeta (err_a * ||x_j|| ||zeta||
 // per coordinate, H_M M-Lipschitz, TopSum 1-Lipschitz per selected entry), g(b^)
 // by Algorithm 2 with the relaxed z, the primal value and the gap
-__global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const int* list, double err_a) {
+__global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const int* list, double err_a,
+                                                             double err_u) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = list[blockIdx.x];
   const BNode* nd = d.nodes + b;
@@ -464,29 +499,54 @@ __global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const i
     }
   }
   const double* a = d.cert_a + (size_t)b * d.ldp;
-  const double gs = gstar_segment<double, kBProxBlock>(p, [&](int i) { return a[i]; }, st, kp, M, 0.5 / l2, sm);
-  double cmax = 0.0;
+  const double* bh = d.beta_out + (size_t)b * p;
+  // eigen-perspective (App. D.2): G* at 2 (X^T y - Q b^) = X^T zeta + 2 eig b^
+  const double eig = nd->eig;
+  const double gs = gstar_segment<double, kBProxBlock>(
+      p, [&](int i) { return eig > 0.0 ? a[i] + 2.0 * eig * bh[i] : a[i]; }, st, kp, M, 0.5 / l2, sm);
+  double cmax = 0.0, amax = 0.0, bsq = 0.0;
   int n1 = 0;
   for (int j = threadIdx.x; j < p; j += kBProxBlock) {
-    if (st[j] != kZero) cmax = fmax(cmax, d.colnorm[j]);
+    if (st[j] != kZero) {
+      cmax = fmax(cmax, d.colnorm[j]);
+      amax = fmax(amax, fabs(a[j]) + 2.0 * eig * fabs(bh[j]));
+    }
     if (st[j] == kOne) n1 += 1;
+    bsq += bh[j] * bh[j];
   }
   cmax = block_max<double, kBProxBlock>(cmax, sm.red, 0.0);
+  amax = block_max<double, kBProxBlock>(amax, sm.red, 0.0);
+  bsq = block_sum<double, kBProxBlock>(bsq, sm.red);
   n1 = (int)block_sum<double, kBProxBlock>((double)n1, sm.red);
-  const double* bh = d.beta_out + (size_t)b * p;
   const GOut go = gvalue_segment<double, kBProxBlock>(p, [&](int i) { return bh[i]; }, st, kp, M, sm,
                                                       d.z_out + (size_t)b * p);
   if (threadIdx.x == 0) {
     const double nn = (double)d.n + 8.0;
     const double margin_f = 1.01 * nn * ur * mgs + (d.loss != kLossLogistic ? 4.0 * ur * mgs : 0.0);
     const double znorm = sqrt(zs) * (1.0 + ((double)d.n + 4.0) * ur);
-    const double eps_a = err_a * cmax * znorm + 1e-30;
+    double eps_a = err_a * cmax * znorm + 1e-30;
+    double nce = nc, margin_e = 0.0;
+    if (eig > 0.0) {
+      // The bound at b^ is ||y||^2 - ||X b^||^2 + eig ||b^||^2 - G*(2 X^T (y - X b^)
+      // + 2 eig b^).  nc is ||y||^2 - ||u~||^2 exactly (up to margin_f) for
+      // u~ = y - zeta/2, and X^T zeta = 2 X^T (y - u~); with
+      // ||u~ - X b^|| <= delta = err_u ||X||_F ||b^|| (the exact product's bound,
+      // row by row by Cauchy-Schwarz) + u ||zeta|| (the rounding of u - y):
+      //   | ||u~||^2 - ||X b^||^2 | <= delta (2 ||u~|| + delta),
+      //   per coordinate |a - a_computed| <= eps_a + 2 ||x_j|| delta + rounding of the sum
+      const double bnorm = sqrt(bsq) * (1.0 + ((double)p + 4.0) * ur);
+      const double delta = (err_u * d.xfro * bnorm + ur * znorm) * 1.01;
+      const double unorm = d.ynorm + 0.5 * znorm;
+      margin_e = delta * (2.0 * unorm + delta) + ((double)p + 4.0) * ur * eig * bsq * 1.01;
+      eps_a += 2.0 * cmax * delta + 2.0 * ur * (amax + 2.0 * eig * M) * 1.01;
+      nce = nc + eig * bsq;
+    }
     const int nsel = (kp < p ? kp : p) + n1;
     const double margin_g = (double)nsel * M * eps_a * (1.0 + 4.0 * ur) + 2.0 * l2 * gs * ((double)nsel + 8.0) * 4.0 * ur;
     const double gst = 2.0 * l2 * gs;
-    double dual = nc - margin_f - gst - margin_g;
-    dual -= 4.0 * ur * (fabs(nc) + gst);
-    const double primal = f + 2.0 * l2 * go.g;
+    double dual = nce - margin_f - margin_e - gst - margin_g;
+    dual -= 4.0 * ur * (fabs(nce) + gst);
+    const double primal = f - eig * bsq + 2.0 * l2 * go.g;
     BCert c;
     c.primal = primal;
     c.dual = dual;
@@ -554,8 +614,9 @@ void launch_bcert_rows(const BatchDev& d, const int* list, int count, cudaStream
   k_bcert_rows<<<dim3(d.nrt, count), kBThreads, 0, s>>>(d, list);
 }
 
-void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, cudaStream_t s) {
-  k_bcert_final<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list, err_a);
+void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, double err_u,
+                        cudaStream_t s) {
+  k_bcert_final<<<count, kBProxBlock, bprox_smem_bytes(0), s>>>(d, list, err_a, err_u);
 }
 
 }  // namespace ksc

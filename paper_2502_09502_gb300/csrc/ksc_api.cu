@@ -410,6 +410,10 @@ ksc_status ksc::check_node(const ksc_problem* pr, const ksc_node* node, NodeSetu
   if (node->n_zero < 0 || node->n_one < 0) return fail(KSC_ERR_INVALID_ARG, "negative set size");
   if ((node->n_zero > 0 && !node->fixed_zero) || (node->n_one > 0 && !node->fixed_one))
     return fail(KSC_ERR_INVALID_ARG, "fixed-set pointer is NULL");
+  if (node->flags & KSC_FLAG_EIG) {
+    if (pr->loss != KSC_LOSS_LSQ) return fail(KSC_ERR_INVALID_ARG, "the eigen-perspective relaxation is for least squares");
+    if (!pr->eig_ready) return fail(KSC_ERR_INVALID_ARG, "eigen shift not computed (ksc_problem_eig_lambda)");
+  }
   ns->state.assign(pr->p, (int8_t)kFree);
   for (int i = 0; i < node->n_zero; ++i) {
     const int j = node->fixed_zero[i];
@@ -462,6 +466,8 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
                                      void* cuda_stream) {
   if (!pr) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
   if (!res) return fail(KSC_ERR_INVALID_ARG, "result is NULL");
+  if (node && (node->flags & KSC_FLAG_EIG))
+    return fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on the batched path (ksc_solve_batch)");
   NodeSetup ns;
   ksc_status st = check_node(pr, node, &ns);
   if (st != KSC_OK) return st;

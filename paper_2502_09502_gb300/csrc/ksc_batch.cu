@@ -225,7 +225,16 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
     for (int i = 0; i < n; ++i) yh[i] = (float)pr->y_host[i];
     KB_CUDA(cudaMemcpyAsync(yf, yh.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
     KB_CUDA(cudaMemcpyAsync(yd, pr->y_host.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
+    // ||X||_F and ||y||_2 rounded up, for the eigen-perspective certificate
+    std::vector<double> cn(p);
+    KB_CUDA(cudaMemcpyAsync(cn.data(), pr->dev.colnorm, (size_t)p * 8, cudaMemcpyDeviceToHost, s));
     KB_CUDA(cudaStreamSynchronize(s));
+    const double ur = 1.1102230246251565e-16;
+    double xf2 = 0.0, y2 = 0.0;
+    for (int j = 0; j < p; ++j) xf2 += cn[j] * cn[j];
+    for (int i = 0; i < n; ++i) y2 += pr->y_host[i] * pr->y_host[i];
+    d.xfro = std::sqrt(xf2 * (1.0 + (p + 4.0) * ur)) * (1.0 + 4.0 * ur);
+    d.ynorm = std::sqrt(y2 * (1.0 + (n + 4.0) * ur)) * (1.0 + 4.0 * ur);
   }
   d.n = n;
   d.p = p;
@@ -602,10 +611,15 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
           hbr[j] = setup.state[j] == kZero ? 0.0 : std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
       BNode& h = hn[b];
       std::memset(&h, 0, sizeof h);
-      h.lambda2 = nd->lambda2;
+      // eigen-perspective (App. D.2): lambda2 + eig on the perspective term, the
+      // smooth part's constant 2 (lambda_max - eig) <= L - 2 eig
+      const double eig = (nd->flags & KSC_FLAG_EIG) ? pr->eig_lambda : 0.0;
+      const double Ln = pr->L - 2.0 * eig;
+      h.lambda2 = nd->lambda2 + eig;
+      h.eig = eig;
       h.M = nd->M;
-      h.rho = pr->L / (2.0 * nd->lambda2);
-      h.invL = 1.0 / pr->L;
+      h.rho = Ln / (2.0 * h.lambda2);
+      h.invL = 1.0 / Ln;
       h.tol_loop = nd->rel_gap_tol;
       h.incumbent = nd->incumbent;
       h.kp = setup.kp;
@@ -718,7 +732,8 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     launch_dfprod(sd, true, d.beta_out, d.p, ws->dlist, R, d.cert_u, d.ldn, d.dfws, kDfBlockCert, s);
     launch_bcert_rows(d, ws->dlist, R, s);
     launch_dfprod(sd, false, d.cert_z, d.ldn, ws->dlist, R, d.cert_a, d.ldp, d.dfws, kDfBlockCert, s);
-    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p, kDfBlockCert), s);
+    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p, kDfBlockCert),
+                       dfprod_error_factor(d.p, R, d.n, kDfBlockCert), s);
     pr->launches += kLaunchesPerBatchCert + (dfprod_splits(R, d.n) > 1) + (dfprod_splits(R, d.p) > 1);
     se->certificates += R;
     KB_CUDA(cudaGetLastError());
@@ -835,6 +850,13 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
   int cur_dev = 0;
   cudaGetDevice(&cur_dev);
   if (cur_dev != pr->device) KB_CUDA(cudaSetDevice(pr->device));
+  // the eigen shift, computed on first use
+  for (int32_t i = 0; i < count; ++i)
+    if ((nodes[i].flags & KSC_FLAG_EIG) && !pr->eig_ready) {
+      double lam = 0.0;
+      if ((st = ksc_problem_eig_lambda(pr, cuda_stream, &lam)) != KSC_OK) return st;
+      break;
+    }
   // validate every node first: nothing runs on a bad batch
   std::vector<NodeSetup> setups(count);
   std::vector<int> batch, single;
@@ -855,6 +877,8 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       continue;
     }
     if (batch_supported(pr) && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
+    else if (nodes[i].flags & KSC_FLAG_EIG)
+      return api_fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on the batched path (BF16 X, k' < 2048)");
     else single.push_back(i);
   }
   // nodes with more free support entries run longer: grouping them in the same

@@ -54,6 +54,10 @@ struct BNode {
   double phi, c, Lcur, best_primal, best_dual, gap;
   double g_next, negconj, gstar, theta, last_primal, last_dual;
   double g_cur;        // g_node(beta^t) (the restart test's difference)
+  // eigen-perspective relaxation (App. D.2; 0: the perspective relaxation):
+  // lambda2 above is then lambda2 + eig, rho and invL those of L - 2 eig
+  double eig;
+  double bsq_cur, bsq_next;   // ||beta^t||^2, ||beta^{t+1}||^2
 };
 
 // FP64 certificate of one node (copied out of the single-node workspace)
@@ -96,6 +100,8 @@ struct BatchDev {
   double* cpart;       // B x nrt x 4: F, -F*(-zeta), its rounding weights, ||zeta||^2
   double* dfws;        // kDfWsElems: split partials of the tiled exact product
   int* tile_run;       // per 128 slots: any node running (k_bstep and the host keep it)
+  double xfro;         // ||X||_F, rounded up (eigen-perspective certificate)
+  double ynorm;        // ||y||_2, rounded up
 };
 
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }
@@ -128,7 +134,9 @@ void launch_banchor_resid(const BatchDev& d, const int* list, int count, int ini
 // factor (dfprod_error_factor).
 void launch_bcert_prep(const BatchDev& d, const int* list, int count, cudaStream_t s);
 void launch_bcert_rows(const BatchDev& d, const int* list, int count, cudaStream_t s);
-void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, cudaStream_t s);
+// err_u: the forward product's error factor (the eigen-perspective bound's margin)
+void launch_bcert_final(const BatchDev& d, const int* list, int count, double err_a, double err_u,
+                        cudaStream_t s);
 // out = A^T vec with A = X (rows n, vec n -> out p) or A = Xc (vec p -> out n),
 // double-float products (the single-node streaming kernel; uses d's partials)
 void launch_colsum_any(const Dev& d, bool use_xc, const double* vec, double* out, cudaStream_t s);

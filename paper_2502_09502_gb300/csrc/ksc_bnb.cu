@@ -73,6 +73,11 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
     return api_fail(KSC_ERR_CUDA, "cannot select the problem's device");
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t s = (cudaStream_t)cuda_stream;
+  if (prm->node_flags & KSC_FLAG_EIG) {   // the eigen shift, computed on first use
+    if (pr->loss != KSC_LOSS_LSQ) return api_fail(KSC_ERR_INVALID_ARG, "the eigen-perspective relaxation is for least squares");
+    double lam = 0.0;
+    if ((st = ksc_problem_eig_lambda(pr, cuda_stream, &lam)) != KSC_OK) return st;
+  }
   const int p = (int)pr->p;
   const int k = prm->k;
 
@@ -154,6 +159,7 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
       nd.incumbent = (who[i].first || on->plain) ? INFINITY : inc;
       nd.rel_gap_tol = prm->node_rel_gap;
       nd.max_iter = prm->node_max_iter;
+      nd.flags = prm->node_flags;
       if ((st = check_node(pr, &nd, &setup[i])) != KSC_OK) { free_all(); return st; }
     }
     if (!who.empty()) {

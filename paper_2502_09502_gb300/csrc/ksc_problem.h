@@ -18,6 +18,7 @@ void free_batch(BatchWs* ws);
 }  // namespace ksc
 
 static constexpr int kStepsPerGraph = 16;
+static constexpr int kEigMaxP = 8192;   // largest p of the eigen shift's Cholesky test
 static constexpr int kKernelIds = 10;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
 
 struct ksc_problem {
@@ -44,6 +45,8 @@ struct ksc_problem {
   int32_t last_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   ksc::BatchWs* batch = nullptr;   // batched-solve workspace (created on first use)
   std::vector<double> batch_state; // 10 in-loop values per node of the last batched call
+  double eig_lambda = 0.0;         // certified lower bound on lambda_min(X^T X)
+  bool eig_ready = false;          // eig_lambda computed (ksc_problem_eig_lambda)
 };
 
 namespace ksc {

@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "admission", 4: "infeasi
                 5: "not_converged", 6: "timeout", 7: "cuda", 8: "unimplemented"}
 KSC_LOSS_LSQ, KSC_LOSS_LOGISTIC, KSC_LOSS_SQHINGE = 0, 1, 2
 KSC_F64, KSC_F32, KSC_BF16, KSC_FP8 = 0, 1, 2, 3   # KSC_FP8: e4m3 with power-of-two column scales
-KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF = 1, 2
+KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF, KSC_FLAG_EIG = 1, 2, 4
 KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 KSC_KERNEL_B_RESID, KSC_KERNEL_B_GRAD, KSC_KERNEL_B_PROX, KSC_KERNEL_B_FWD, KSC_KERNEL_B_STEP = (
     3, 4, 5, 6, 7)
@@ -37,7 +37,8 @@ EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ks
            "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
            "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
-           "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state",
+           "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state", "ksc_problem_eig_lambda",
+           "ksc_problem_set_eig_lambda",
            "ksc_last_error", "ksc_version"]
 
 
@@ -71,7 +72,7 @@ class ResultC(C.Structure):
 class BnbParams(C.Structure):
     _fields_ = [("lambda2", C.c_double), ("M", C.c_double), ("k", C.c_int32), ("opt_gap", C.c_double),
                 ("max_nodes", C.c_int64), ("time_limit_s", C.c_double), ("batch", C.c_int32),
-                ("node_rel_gap", C.c_double), ("node_max_iter", C.c_int32)]
+                ("node_rel_gap", C.c_double), ("node_max_iter", C.c_int32), ("node_flags", C.c_uint32)]
 
 
 class BnbResultC(C.Structure):
@@ -122,6 +123,8 @@ def _load():
     L.ksc_server_stats.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_int32]
     L.ksc_server_destroy.argtypes = [C.c_void_p]
     L.ksc_problem_batch_node_state.argtypes = [C.c_void_p, C.c_int32, dp, C.c_int32]
+    L.ksc_problem_eig_lambda.argtypes = [C.c_void_p, C.c_void_p, dp]
+    L.ksc_problem_set_eig_lambda.argtypes = [C.c_void_p, C.c_void_p, C.c_double]
     L.ksc_last_error.restype = C.c_char_p
     L.ksc_version.restype = C.c_char_p
     for name in EXPORTS:
@@ -278,6 +281,16 @@ def ksc_problem_batch_node_state(h, index):
     return dict(zip(BATCH_NODE_STATE, list(buf)))
 
 
+def ksc_problem_eig_lambda(h, stream=None) -> float:
+    lam = C.c_double()
+    _check(lib.ksc_problem_eig_lambda(h, _stream_ptr(stream), C.byref(lam)))
+    return lam.value
+
+
+def ksc_problem_set_eig_lambda(h, lam, stream=None):
+    _check(lib.ksc_problem_set_eig_lambda(h, _stream_ptr(stream), float(lam)))
+
+
 def ksc_problem_launch_count(h) -> int:
     n = C.c_int64()
     _check(lib.ksc_problem_launch_count(h, C.byref(n)))
@@ -394,12 +407,22 @@ class Problem:
         return Result(beta, z, res.primal, res.dual_bound, res.rel_gap, res.iters, res.restarts,
                       bool(res.pruned), STATUS_NAMES[res.status if st == KSC_OK else st])
 
+    def eig_lambda(self):
+        """ksc_problem_eig_lambda: the certified shift of the eigen-perspective
+        relaxation (a lower bound on lambda_min(X^T X))."""
+        return ksc_problem_eig_lambda(self.h, self.stream)
+
+    def set_eig_lambda(self, lam):
+        """ksc_problem_set_eig_lambda: certify lam below lambda_min(X^T X) and use it."""
+        ksc_problem_set_eig_lambda(self.h, lam, self.stream)
+
     def bnb(self, lambda2, M, k, opt_gap=1e-4, max_nodes=0, time_limit_s=0.0, batch=256,
-            node_rel_gap=1e-6, node_max_iter=20000):
+            node_rel_gap=1e-6, node_max_iter=20000, node_flags=0):
         """ksc_bnb_solve: best-first branch and bound over the node relaxations.
         Returns (incumbent beta, dict of the result fields)."""
         prm = BnbParams(float(lambda2), float(M), int(k), float(opt_gap), int(max_nodes),
-                        float(time_limit_s), int(batch), float(node_rel_gap), int(node_max_iter))
+                        float(time_limit_s), int(batch), float(node_rel_gap), int(node_max_iter),
+                        int(node_flags))
         beta = np.zeros(self.p)
         res = BnbResultC()
         res.beta = _dptr(beta)

@@ -84,6 +84,9 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
     assert ksc.lib.ksc_gstar(w.ctypes.data_as(dp), 4, 1, 0.0, w.ctypes.data_as(dp)) == \
         ksc.KSC_ERR_INVALID_ARG
     assert ksc.lib.ksc_solve_node(None, None, None, None) == ksc.KSC_ERR_INVALID_ARG
+    lam = C.c_double(-1.0)
+    assert ksc.lib.ksc_problem_eig_lambda(None, None, C.byref(lam)) == ksc.KSC_ERR_INVALID_ARG
+    assert ksc.lib.ksc_problem_set_eig_lambda(None, None, 1.0) == ksc.KSC_ERR_INVALID_ARG
     # batched prox on device rows: every argument check comes before any CUDA call
     fb = ksc.lib.ksc_prox_g_batch
     assert fb(None, 8, None, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG   # NULL rows
@@ -113,6 +116,7 @@ def test_struct_layouts_match_header(ksc):
     assert ksc.ResultC.status.offset == 52
     assert C.sizeof(ksc.BnbParams) == 72
     assert ksc.BnbParams.opt_gap.offset == 24 and ksc.BnbParams.node_max_iter.offset == 64
+    assert ksc.BnbParams.node_flags.offset == 68
     assert C.sizeof(ksc.BnbResultC) == 96
     assert ksc.BnbResultC.seconds.offset == 80 and ksc.BnbResultC.certified.offset == 88
 
