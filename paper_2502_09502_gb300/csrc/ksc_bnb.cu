@@ -106,11 +106,15 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
   open.push(new OpenNode{{}, {}, -INFINITY, {}, {}});
   const double tiny = 1e-300;
   auto prunable = [&](double bound) { return std::isfinite(inc) && inc - bound <= prm->opt_gap * std::fabs(inc); };
+  // the smallest certified bound of the leaves taken off the tree (pruned within the
+  // gap, or closed): a leaf pruned within opt_gap may hold points below the
+  // incumbent, down to its bound, so the tree's lower bound keeps it
+  double done_lb = INFINITY;
   auto lower_bound = [&]() {
     double lb = open.empty() ? INFINITY : open.top()->bound;
     for (const Job& j : job)
       if (j.busy && !j.heuristic) lb = std::min(lb, j.bound);
-    return std::min(lb, inc);
+    return std::min(std::min(lb, done_lb), inc);
   };
   bool certified = false;
 
@@ -133,7 +137,12 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
       } else if (!open.empty() && budget_left) {
         on = open.top();
         open.pop();
-        if (prunable(on->bound)) { ++pruned; delete on; continue; }
+        if (prunable(on->bound)) {
+          ++pruned;
+          done_lb = std::min(done_lb, on->bound);
+          delete on;
+          continue;
+        }
       } else {
         break;
       }
@@ -213,7 +222,12 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
       }
       ++nodes;
       const double bound = std::max(r.dual_bound, on->bound);   // both are valid lower bounds
-      if (r.status == KSC_ERR_INFEASIBLE_NODE || r.pruned || prunable(bound)) { ++pruned; delete on; continue; }
+      if (r.status == KSC_ERR_INFEASIBLE_NODE || r.pruned || prunable(bound)) {
+        ++pruned;
+        if (r.status != KSC_ERR_INFEASIBLE_NODE) done_lb = std::min(done_lb, bound);
+        delete on;
+        continue;
+      }
       // free coordinates of the relaxed solution, largest |b_j| first
       std::vector<char> fixed(p, 0);
       for (int32_t z : on->zero) fixed[z] = 1;
@@ -229,9 +243,11 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
         if (std::isfinite(r.primal) && r.primal < inc) { inc = r.primal; inc_beta = beta; }
         if (r.status == KSC_OK && r.rel_gap <= prm->node_rel_gap) {
           ++closed;
+          done_lb = std::min(done_lb, bound);
           delete on;
         } else if (on->plain) {
           ++closed;   // solved without the rules and still not certified (iteration cap): its point is the incumbent candidate
+          done_lb = std::min(done_lb, bound);
           delete on;
         } else {
           on->bound = bound;
@@ -283,7 +299,7 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
       delete on;
     }
   }
-  const double lb = certified ? std::min(lower_bound(), inc) : lower_bound();
+  const double lb = lower_bound();
   res->incumbent = inc;
   res->lower_bound = lb;
   res->gap = std::isfinite(inc) ? (inc - lb) / std::max(std::fabs(inc), tiny) : INFINITY;
