@@ -466,7 +466,9 @@ __device__ __forceinline__ EpiRow epi_row(const TcShape& sh, const TcEpi& ep, in
   return r;
 }
 
-template <int MODE>
+// PART: write the loss partials when the chunk closes its 64-column group (the
+// fix-up kernel sums its four chunks across threads and writes them itself)
+template <int MODE, bool PART = true>
 __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, const EpiRow& r, int m, int nc,
                                           const float* v, double& fsum, double& dsum) {
   if (!r.ok || nc >= sh.N) return;
@@ -509,7 +511,7 @@ __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, co
     }
     fsum += (double)fa + fd;
     dsum += (double)da;
-    if (((nc + 16) & 63) == 0 || nc + 16 >= sh.N) {
+    if (PART && (((nc + 16) & 63) == 0 || nc + 16 >= sh.N)) {
       double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
       pp[0] = fsum;
       pp[1] = dsum;
@@ -532,7 +534,7 @@ __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, co
     }
     fsum += (double)fa + fd;
     dsum += (double)da;
-    if (((nc + 16) & 63) == 0 || nc + 16 >= sh.N) {   // one pair of partials per 64 columns
+    if (PART && (((nc + 16) & 63) == 0 || nc + 16 >= sh.N)) {   // one pair of partials per 64 columns
       double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
       pp[0] = fsum;
       pp[1] = dsum;
@@ -745,7 +747,8 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
 // (blockIdx.y; one loss-partial group), summing the partial tiles in CTA order
 // and applying the epilogue
 template <int BN, int MODE>
-__global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int G) {
+__global__ void __launch_bounds__(kTcBM * 4) k_tcgemm_fix(TcShape sh, TcEpi ep, int G) {
+  __shared__ double sp[2][4][kTcBM];
   SkMap mp;
   sk_map(sh, ep, BN, G, mp);
   const int c = blockIdx.x + 1;
@@ -757,12 +760,13 @@ __global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int 
   if (sk_begin(mp, c - 1) > t0) return;   // an earlier boundary lies inside this tile
   const int clo = sk_owner(mp, t0), chi = sk_owner(mp, t0 + mp.KB - 1);
   const int m0 = mp.act[t % mp.A] * kTcBM, n0 = (t / mp.A) * BN;
-  const int row = threadIdx.x;
+  // one thread per row and 16-column chunk of the CTA's 64 columns
+  const int row = (int)threadIdx.x % kTcBM, q4 = (int)threadIdx.x / kTcBM;
   const int m = m0 + row;
   const EpiRow er = epi_row<MODE>(sh, ep, m);
   double fsum = 0.0, dsum = 0.0;
-  const int c_lo = (int)blockIdx.y * 64;
-  for (int cc = c_lo; cc < c_lo + 64 && cc < BN; cc += 16) {
+  const int cc = (int)blockIdx.y * 64 + q4 * 16;
+  if (cc < BN) {
     float v[16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) v[j] = 0.0f;
@@ -779,7 +783,26 @@ __global__ void __launch_bounds__(kTcBM) k_tcgemm_fix(TcShape sh, TcEpi ep, int 
         v[4 * j + 3] += x.w;
       }
     }
-    epi_chunk<MODE>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
+    epi_chunk<MODE, false>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
+  }
+  if (MODE == kTcAnchor) {
+    // the 64-column group's loss partials: its four chunks added in column order,
+    // as the product's own epilogue adds them
+    sp[0][q4][row] = fsum;
+    sp[1][q4][row] = dsum;
+    __syncthreads();
+    const int g0 = n0 + (int)blockIdx.y * 64;
+    if (q4 == 0 && er.ok && g0 < sh.N) {
+      double f = sp[0][0][row], dd = sp[1][0][row];
+#pragma unroll
+      for (int k = 1; k < 4; ++k) {
+        f += sp[0][k][row];
+        dd += sp[1][k][row];
+      }
+      double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (g0 >> 6));
+      pp[0] = f;
+      pp[1] = dd;
+    }
   }
 }
 
@@ -870,7 +893,7 @@ static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
     }
     k_tcgemm_sk<P, BN, MODE><<<g.grid, sk_threads(BN), bytes, s>>>(*(const CUtensorMap*)g.tmA,
                                                               *(const CUtensorMap*)g.tmB, sh, e);
-    if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<dim3(g.grid - 1, (BN + 63) / 64), kTcBM, 0, s>>>(sh, e, g.grid);
+    if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<dim3(g.grid - 1, (BN + 63) / 64), kTcBM * 4, 0, s>>>(sh, e, g.grid);
     return;
   }
   static bool attr = false;
