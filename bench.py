@@ -310,7 +310,11 @@ def run_ours(args, rank, world, dist):
             "config": dict(WORKLOAD, parallelism=f"replicas x{world}" if world > 1 else "single GPU",
                            **({"x_dtype": "fp8 e4m3, per-column power-of-two scales, quantized from the FP32 "
                                           "instance (the solved matrix is the quantized one)",
-                               "l2": "X (1 GB) larger than L2; no flush"} if fp8 else {})),
+                               "l2": "X (1 GB) larger than L2; no flush"} if fp8 else {}),
+                           **({"workload": "profiler case: single-node least squares FP32 X n=8000 p=20000 "
+                                           "k=20 lambda2=0.1 M=1.5 toeplitz 0.9 (not a benchmark line)",
+                               "n": 8000, "p": 20000, "l2": "X (640 MB) larger than L2; no flush"}
+                              if args.small else {})),
             "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                            "p99": round(float(np.percentile(lat_ms, 99)), 3)},
             "iters_per_bound": float(np.mean(stats["iters"])),
