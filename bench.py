@@ -60,9 +60,13 @@ def parse():
     ap.add_argument("--small", action="store_true",
                     help="8000 x 20000 instance of the same generator (640 MB X, still larger "
                          "than L2) for profiler captures; not a benchmark line")
-    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "prox", "bnb"],
+    ap.add_argument("--workload", default="single", choices=["single", "batched", "serving", "prox", "bnb", "eig"],
                     help="single: the single-node FP32 line (default); batched: 512 nodes of "
-                         "the batched logistic BF16 workload in one ksc_solve_batch call")
+                         "the batched logistic BF16 workload in one ksc_solve_batch call; eig: the "
+                         "eigen-perspective relaxation on a least-squares instance of the batched shape")
+    ap.add_argument("--loss", default="logistic", choices=["logistic", "sqhinge"],
+                    help="batched workload: logistic (the configuration) or the squared hinge on the "
+                         "same labels")
     ap.add_argument("--nodes", type=int, default=512, help="batched: nodes per call")
     ap.add_argument("--pool", type=int, default=4, help="serving: resident problems drawn from the mix")
     ap.add_argument("--requests", type=int, default=2048, help="serving: distinct requests (reused cyclically)")
@@ -591,10 +595,12 @@ def run_batched(args):
     from paper_2502_09502_gb300 import ksc as K
     torch.cuda.set_device(0)
     P = G.cfg_batched_logistic(seed=args.seed)
+    sq = getattr(args, "loss", "logistic") == "sqhinge"
+    loss = K.KSC_LOSS_SQHINGE if sq else K.KSC_LOSS_LOGISTIC
     n, p, B = P.n, P.p, args.nodes
     Xd = torch.from_numpy(P.X.view(np.int16)).cuda().view(torch.bfloat16)
     stream = torch.cuda.Stream()
-    prob = K.Problem(Xd, P.y, K.KSC_LOSS_LOGISTIC, stream=stream)
+    prob = K.Problem(Xd, P.y, loss, stream=stream)
     root = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
     sets = G.node_sets(p, B, seed=args.seed, max_zero=200, max_one=9)
     pert = G.warm_perturbation(p, B, seed=args.seed)
@@ -666,8 +672,7 @@ def run_batched(args):
     Xh = torch.from_numpy(P.X.view(np.int16)).pin_memory()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prob2 = K.Problem(Xh.numpy().view(np.uint16), P.y, K.KSC_LOSS_LOGISTIC, stream=stream,
-                      x_dtype=K.KSC_BF16)
+    prob2 = K.Problem(Xh.numpy().view(np.uint16), P.y, loss, stream=stream, x_dtype=K.KSC_BF16)
     res = prob2.solve_batch(nodes, want_beta=True)
     e_s = time.perf_counter() - t0
     prob2.close()
@@ -678,7 +683,9 @@ def run_batched(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
         "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
-        "config": dict(BATCHED, nodes=B, parallelism="single GPU"),
+        "config": dict(BATCHED, nodes=B, parallelism="single GPU",
+                       **({"workload": BATCHED["workload"].replace("batched logistic", "batched squared hinge"),
+                           "loss": "squared_hinge"} if sq else {})),
         "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
                        "p99": round(float(np.percentile(lat_ms, 99)), 3)},
         "iters_per_bound": float(np.mean(iters)),
@@ -699,6 +706,69 @@ def run_batched(args):
                      "node_steps": node_steps, "avg_launch_ms": round(gms / max(nl, 1), 5), "launches": nl},
     }
     return line
+
+
+EIG = dict(workload="eigen-perspective relaxation (App. D.2), least squares BF16 X n=10000 p=5000 k=10 "
+                    "lambda2=0.01 M=3 toeplitz 0.5, 10 x +-1, SNR 5, 512 nodes per call as in the batched "
+                    "workload (|S0|~U{0..200}, |S1|~U{0..9}, warm start = root iterate + N(0,1e-2)), "
+                    "rel gap 1e-6",
+           n=10000, p=5000, k=10, lambda2=0.01, M=3.0, r=0.5, x_dtype="bf16", loss="least_squares",
+           rel_gap=1e-6)
+
+
+def run_eig(args):
+    """The certified shift (Gram matrix and Cholesky bisection), then one step = one
+    ksc_solve_batch call over the nodes with KSC_FLAG_EIG, beside the same call with
+    perspective nodes: throughput and how much the bounds rise."""
+    import torch
+    import ksc_inputs as G
+    from paper_2502_09502_gb300 import ksc as K
+    torch.cuda.set_device(0)
+    P = G.make_problem(10000, 5000, r=0.5, seed=args.seed, loss=G.LSQ, k_true=10, snr=5.0, x_dtype=G.BF16,
+                       lambda2=0.01, M=3.0, k=10)
+    n, p, B = P.n, P.p, args.nodes
+    Xd = torch.from_numpy(P.X.view(np.int16)).cuda().view(torch.bfloat16)
+    stream = torch.cuda.Stream()
+    prob = K.Problem(Xd, P.y, K.KSC_LOSS_LSQ, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam = prob.eig_lambda()
+    t_lam = time.perf_counter() - t0
+    root = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
+    sets = G.node_sets(p, B, seed=args.seed, max_zero=200, max_one=9)
+    pert = G.warm_perturbation(p, B, seed=args.seed)
+    mk = lambda fl: [K.Node(P.lambda2, P.M, P.k, fixed_zero=z, fixed_one=o, warm_beta=root.beta + pert[b],
+                            rel_gap_tol=1e-6, max_iter=100000, flags=fl) for b, (z, o) in enumerate(sets)]
+    out = {}
+    for name, fl in (("perspective", 0), ("eigen_perspective", K.KSC_FLAG_EIG)):
+        nodes = mk(fl)
+        for _ in range(args.warmup):
+            prob.solve_batch(nodes, want_beta=False)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = prob.solve_batch(nodes, want_beta=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        assert all((r.status == "ok" and r.rel_gap <= 1e-6) or r.pruned for r in res)
+        out[name] = dict(value=round(B * args.steps / (ms / 1e3), 3), ms_per_step=round(ms / args.steps, 3),
+                         iters_per_bound=float(np.mean([r.iters for r in res])),
+                         bounds=np.array([r.dual_bound for r in res]))
+    bp, be = out["perspective"].pop("bounds"), out["eigen_perspective"].pop("bounds")
+    rise = (be - bp) / np.abs(bp)
+    return {
+        "metric": METRIC, "value": out["eigen_perspective"]["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["eigen_perspective"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
+        "config": dict(EIG, nodes=B, parallelism="single GPU"),
+        "eig_lambda": lam, "eig_lambda_seconds": round(t_lam, 3),
+        "perspective": out["perspective"], "eigen_perspective": out["eigen_perspective"],
+        "bound_rise": {"mean_rel": float(rise.mean()), "max_rel": float(rise.max()),
+                       "nodes_higher": int((rise > 1e-9).sum()), "nodes_lower": int((rise < -1e-9).sum())},
+    }
 
 
 # ------------------------------------------------------------------ oracle timing
@@ -776,10 +846,11 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         D.init_process_group("nccl")
         dist = D
-    if args.workload in ("batched", "serving", "prox", "bnb"):
+    if args.workload in ("batched", "serving", "prox", "bnb", "eig"):
         if world > 1:
             raise SystemExit(f"the {args.workload} workload runs on one GPU")
-        run = {"batched": run_batched, "serving": run_serving, "prox": run_prox, "bnb": run_bnb}[args.workload]
+        run = {"batched": run_batched, "serving": run_serving, "prox": run_prox, "bnb": run_bnb,
+               "eig": run_eig}[args.workload]
         print(json.dumps(run(args)), flush=True)
         return
     out, P, stats = run_ours(args, rank, world, dist)
