@@ -216,8 +216,10 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     }
     theta = tridiag_max_eig(hlz.data(), hlz.data() + kLanczosMax, m);
     pr->power_iters = m;
-    // the Ritz value rises monotonically to lambda_max; L keeps a 1% margin
-    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-7 * theta)) break;
+    // the Ritz value rises monotonically to lambda_max and L keeps a 1% margin: stop
+    // once 8 more steps move it by at most 1e-5 of itself (its remaining error is then
+    // far below the margin: ~4e-8 on the 8000 x 20000 profiler instance)
+    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-5 * theta)) break;
     prev = theta;
   }
   // F' is 2-Lipschitz for least squares and the squared hinge, 1/4 for logistic
