@@ -81,6 +81,10 @@ def parse():
     ap.add_argument("--bnb-gap", type=float, default=1e-4, help="bnb: relative gap to certify")
     ap.add_argument("--bnb-n", type=int, default=20000, help="bnb: rows")
     ap.add_argument("--bnb-p", type=int, default=200000, help="bnb: columns")
+    ap.add_argument("--eig-bnb-seconds", type=float, default=0.0,
+                    help="eig: also run branch and bound on a 4000 x 2000 least-squares instance with "
+                         "perspective and with eigen-perspective node bounds, each within this time "
+                         "limit (0: skip)")
     ap.add_argument("--plain-nodes", type=int, default=16,
                     help="batched: nodes of the same batch solved one at a time by the "
                          "single-node solver for the comparison")
@@ -758,6 +762,21 @@ def run_eig(args):
                          bounds=np.array([r.dual_bound for r in res]))
     bp, be = out["perspective"].pop("bounds"), out["eigen_perspective"].pop("bounds")
     rise = (be - bp) / np.abs(bp)
+    bnb = None
+    if args.eig_bnb_seconds > 0:
+        # branch and bound on a smaller instance of the config-4 generator with n > p
+        Pb = G.make_problem(4000, 2000, r=0.7, seed=args.seed, loss=G.LSQ, k_true=10, snr=3.0,
+                            x_dtype=G.BF16, lambda2=0.1, M=2.0, k=10)
+        pb = K.Problem(torch.from_numpy(Pb.X.view(np.int16)).cuda().view(torch.bfloat16), Pb.y,
+                       K.KSC_LOSS_LSQ, stream=stream)
+        bnb = {"config": "least squares BF16 X n=4000 p=2000 k=10 lambda2=0.1 M=2 toeplitz 0.7, "
+                         "10 x +-1, SNR 3, opt gap 1e-4, 256 nodes in flight",
+               "time_limit_s": args.eig_bnb_seconds}
+        for name, fl in (("perspective", 0), ("eigen_perspective", K.KSC_FLAG_EIG)):
+            _, r = pb.bnb(0.1, 2.0, 10, opt_gap=1e-4, time_limit_s=args.eig_bnb_seconds, batch=256,
+                          node_rel_gap=1e-6, node_max_iter=20000, node_flags=fl)
+            bnb[name] = {kk: r[kk] for kk in ("certified", "gap", "seconds", "nodes", "pruned",
+                                              "heuristic_solves", "incumbent", "lower_bound")}
     return {
         "metric": METRIC, "value": out["eigen_perspective"]["value"], "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["eigen_perspective"]["ms_per_step"],
@@ -768,6 +787,7 @@ def run_eig(args):
         "perspective": out["perspective"], "eigen_perspective": out["eigen_perspective"],
         "bound_rise": {"mean_rel": float(rise.mean()), "max_rel": float(rise.max()),
                        "nodes_higher": int((rise > 1e-9).sum()), "nodes_lower": int((rise < -1e-9).sum())},
+        "branch_and_bound": bnb,
     }
 
 
