@@ -374,7 +374,8 @@ def run_bnb(args):
         "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded Toeplitz AR(1) rows drawn on the device)",
         "config": dict(BNB, n=n, p=p, k=k, opt_gap=args.bnb_gap, time_limit_s=args.bnb_seconds,
                        batch=args.bnb_batch, parallelism="single GPU"),
-        "setup_s": round(setup, 1), "result": {kk: (round(v, 6) if isinstance(v, float) else v) for kk, v in res.items()},
+        "setup_s": round(setup, 1), "result": {kk: (float(f"{v:.10g}") if isinstance(v, float) else v)
+                                                for kk, v in res.items()},
         "time_to_certify_s": round(res["seconds"], 2) if res["certified"] else None,
         "incumbent_support_size": len(supp), "true_support_recovered": len(supp & truth),
     }
