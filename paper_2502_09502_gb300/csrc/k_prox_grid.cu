@@ -46,39 +46,128 @@ struct SelSmem {
 __device__ __forceinline__ double dval(unsigned long long b) { return __longlong_as_double((long long)b); }
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 
-// descending sort of 64-bit keys (non-negative doubles compare like their bits)
-__device__ void sort_u64_desc(unsigned long long* s, int N) {
-  for (int size = 2; size <= N; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < (N >> 1); i += kSelBlock) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool desc = ((lo & size) == 0);
-        const unsigned long long a = s[lo], b = s[hi];
-        if ((a < b) == desc) { s[lo] = b; s[hi] = a; }
+// Bitonic sort into descending order: PAIRS ranks by key, ties by ascending index
+// (Alg. 1's order); otherwise keys alone (non-negative doubles compare like their
+// bits).  N is a power of two <= kProxCap.  With kSelBlock threads, each of
+// W = min(N/32, 32) warps holds a block of B = N/W consecutive elements in
+// registers (R = B/32 per lane: element base + 32 r + lane); the merge stages
+// whose stride is below B run there (strides >= 32 inside a thread, smaller ones
+// by warp shuffles), the wider ones through shared memory.
+__device__ __forceinline__ bool rank_gt(unsigned long long ka, int ia, unsigned long long kb, int ib, bool pairs) {
+  return ka > kb || (pairs && ka == kb && ia < ib);
+}
+
+template <bool PAIRS>
+__device__ void smem_merge_stage(unsigned long long* s, int* ix, int N, int size, int stride) {
+  for (int i = threadIdx.x; i < (N >> 1); i += kSelBlock) {
+    const int lo = 2 * i - (i & (stride - 1));
+    const int hi = lo + stride;
+    const bool desc = ((lo & size) == 0);
+    const unsigned long long a = s[lo], b = s[hi];
+    const int ia = PAIRS ? ix[lo] : 0, ib = PAIRS ? ix[hi] : 0;
+    if (rank_gt(a, ia, b, ib, PAIRS) != desc) {
+      s[lo] = b;
+      s[hi] = a;
+      if (PAIRS) {
+        ix[lo] = ib;
+        ix[hi] = ia;
       }
-      __syncthreads();
     }
+  }
+  __syncthreads();
+}
+
+template <bool PAIRS>
+__device__ void bitonic_desc(unsigned long long* s, int* ix, int N) {
+  if (N < 64) {   // a single small block: shared memory only
+    for (int size = 2; size <= N; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) smem_merge_stage<PAIRS>(s, ix, N, size, stride);
+    return;
+  }
+  const int W = N / 32 < 32 ? N / 32 : 32;
+  const int R = N / (32 * W);   // 1, 2 or 4
+  const int B = 32 * R;
+  const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+  const bool act = warp < W;
+  const int base = warp * B;
+  unsigned long long k[4] = {0ull, 0ull, 0ull, 0ull};
+  int id[4] = {0, 0, 0, 0};
+  auto load = [&]() {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < R) {
+        k[r] = s[base + 32 * r + lane];
+        if (PAIRS) id[r] = ix[base + 32 * r + lane];
+      }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+      if (r < R) {
+        s[base + 32 * r + lane] = k[r];
+        if (PAIRS) ix[base + 32 * r + lane] = id[r];
+      }
+  };
+  // in-thread compare-exchange of registers ra < rb (elements e and e + 32 (rb - ra))
+  auto cx = [&](int ra, int rb, int size) {
+    const int e = base + 32 * ra + lane;
+    const bool desc = ((e & size) == 0);
+    if (rank_gt(k[ra], id[ra], k[rb], id[rb], PAIRS) != desc) {
+      const unsigned long long t = k[ra];
+      k[ra] = k[rb];
+      k[rb] = t;
+      const int u = id[ra];
+      id[ra] = id[rb];
+      id[rb] = u;
+    }
+  };
+  auto reg_stages = [&](int size, int stride_hi) {
+    for (int stride = stride_hi; stride > 0; stride >>= 1) {
+      if (stride >= 64) {          // R = 4: registers 0-2, 1-3
+        cx(0, 2, size);
+        cx(1, 3, size);
+      } else if (stride == 32) {   // registers 0-1 (and 2-3)
+        cx(0, 1, size);
+        if (R == 4) cx(2, 3, size);
+      } else {
+        const bool is_lo = (lane & stride) == 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+          if (r < R) {
+            const unsigned long long b = __shfl_xor_sync(0xffffffffu, k[r], stride);
+            const int ib = PAIRS ? __shfl_xor_sync(0xffffffffu, id[r], stride) : 0;
+            const int e = base + 32 * r + lane;
+            const bool desc = ((e & size) == 0);
+            const bool a_first = rank_gt(k[r], id[r], b, ib, PAIRS);
+            if ((is_lo == desc) != a_first) {
+              k[r] = b;
+              id[r] = ib;
+            }
+          }
+      }
+    }
+  };
+  if (act) {
+    load();
+    for (int size = 2; size <= B; size <<= 1) reg_stages(size, size >> 1);
+    store();
+  }
+  __syncthreads();
+  for (int size = 2 * B; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride >= B; stride >>= 1) smem_merge_stage<PAIRS>(s, ix, N, size, stride);
+    if (act) {
+      load();
+      reg_stages(size, B >> 1);
+      store();
+    }
+    __syncthreads();
   }
 }
 
+__device__ void sort_u64_desc(unsigned long long* s, int N) { bitonic_desc<false>(s, nullptr, N); }
+
 // descending by value, ascending by index
-__device__ void sort_pairs_desc(unsigned long long* s, int* ix, int N) {
-  for (int size = 2; size <= N; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = threadIdx.x; i < (N >> 1); i += kSelBlock) {
-        const int lo = 2 * i - (i & (stride - 1));
-        const int hi = lo + stride;
-        const bool desc = ((lo & size) == 0);
-        const unsigned long long a = s[lo], b = s[hi];
-        const int ia = ix[lo], ib = ix[hi];
-        const bool a_first = (a > b) || (a == b && ia < ib);
-        if (a_first != desc) { s[lo] = b; s[hi] = a; ix[lo] = ib; ix[hi] = ia; }
-      }
-      __syncthreads();
-    }
-  }
-}
+__device__ void sort_pairs_desc(unsigned long long* s, int* ix, int N) { bitonic_desc<true>(s, ix, N); }
 
 // prefix sums pref[0..C] of the candidate values
 __device__ void prefix_values(SelSmem& sm, int C) {
@@ -101,16 +190,19 @@ struct Piece {
 };
 
 __device__ Piece phi_at(const SelSmem& sm, double th, int q, int C, double rho, double M) {
+  // th, theta_t and a_j are non-negative doubles: their bit patterns compare alike
+  // (integer compares; FP64 issues at 1/64 of the FP32 rate)
+  const unsigned long long tk = dbits(th);
   int lo = 0, hi = q;   // first top t with theta_t < th (theta_t non-increasing)
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (sm.tb[mid] < th) hi = mid; else lo = mid + 1;
+    if (dbits(sm.tb[mid]) < tk) hi = mid; else lo = mid + 1;
   }
   const int t0 = lo;
   lo = q; hi = C;       // first tail j with a_j <= th
   while (lo < hi) {
     const int mid = (lo + hi) >> 1;
-    if (dval(sm.cand[mid]) <= th) hi = mid; else lo = mid + 1;
+    if (sm.cand[mid] <= tk) hi = mid; else lo = mid + 1;
   }
   Piece e;
   e.nA = q - t0;
@@ -121,27 +213,41 @@ __device__ Piece phi_at(const SelSmem& sm, double th, int q, int C, double rho, 
   return e;
 }
 
-// Root of Phi on [floorv, inf) by binary search over the two sorted breakpoint
-// sequences (thread 0).  Returns false when Phi(floorv) > 0 and floorv is a
-// true floor (the pooled block reaches below the candidates).
+// First index in [lo, hi) where a predicate that is monotone in the index (false
+// ... false true ... true) holds, hi if none: one warp, 32 probes per round.
+template <class Pred>
+__device__ int warp_first_true(int lo, int hi, Pred pred) {
+  const int lane = (int)threadIdx.x & 31;
+  while (lo < hi) {
+    const int step = (hi - lo + 31) / 32;
+    const int j = lo + lane * step;
+    const unsigned m = __ballot_sync(0xffffffffu, j < hi && pred(j));
+    if (m == 0u) {
+      const int last = (hi - 1 - lo) / step < 31 ? (hi - 1 - lo) / step : 31;   // the last probe below hi
+      lo += last * step + 1;
+    } else {
+      const int f = __ffs(m) - 1;
+      hi = lo + f * step;                    // the first true probe
+      if (f > 0) lo += (f - 1) * step + 1;   // past the last false one
+    }
+  }
+  return lo;
+}
+
+// Root of Phi on [floorv, inf) by search over the two sorted breakpoint
+// sequences (one warp: every lane returns the same).  Returns false when
+// Phi(floorv) > 0 and floorv is a true floor (the pooled block reaches below the
+// candidates).
 __device__ bool root_search(const SelSmem& sm, int q, int C, double floorv, bool floor_is_zero,
                             double rho, double M, double* theta) {
   if (!floor_is_zero && phi_at(sm, floorv, q, C, rho, M).phi > 0.0) return false;
   double lo = floorv, hi = INFINITY;
   // tail breakpoints a_j, j in [q, C): Phi(a_j) is non-increasing in j
-  int a = q, b = C;
-  while (a < b) {
-    const int m = (a + b) >> 1;
-    if (phi_at(sm, dval(sm.cand[m]), q, C, rho, M).phi <= 0.0) b = m; else a = m + 1;
-  }
+  int a = warp_first_true(q, C, [&](int j) { return phi_at(sm, dval(sm.cand[j]), q, C, rho, M).phi <= 0.0; });
   if (a < C) lo = fmax(lo, dval(sm.cand[a]));
   if (a > q) hi = fmin(hi, dval(sm.cand[a - 1]));
   // top breakpoints theta_t, t in [0, q): non-increasing in t
-  a = 0; b = q;
-  while (a < b) {
-    const int m = (a + b) >> 1;
-    if (phi_at(sm, sm.tb[m], q, C, rho, M).phi <= 0.0) b = m; else a = m + 1;
-  }
+  a = warp_first_true(0, q, [&](int t) { return phi_at(sm, sm.tb[t], q, C, rho, M).phi <= 0.0; });
   if (a < q && sm.tb[a] >= floorv) lo = fmax(lo, sm.tb[a]);
   if (a > 0) hi = fmin(hi, sm.tb[a - 1]);
   const double thM = M / rho;
@@ -259,15 +365,17 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
       __syncthreads();
       const bool all = (cg == 0u);
       const double floorv = all ? 0.0 : dval(sm.cand[cc - 1]);
+      double th = 0.0;
+      const bool fnd = threadIdx.x < 32 && root_search(sm, q, cc, floorv, all, rho, M, &th);
       if (threadIdx.x == 0) {
-        double th = 0.0;
-        sm.flag[1] = root_search(sm, q, cc, floorv, all, rho, M, &th) ? 1 : 0;
+        sm.flag[1] = fnd ? 1 : 0;
         sm.root[0] = th;
         // next step's guess: keep about twice the pooled block, 5% below
         int lo = q, hi = cc;
+        const unsigned long long tk = dbits(th);
         while (lo < hi) {
           const int mid = (lo + hi) >> 1;
-          if (dval(sm.cand[mid]) <= th) hi = mid; else lo = mid + 1;
+          if (sm.cand[mid] <= tk) hi = mid; else lo = mid + 1;
         }
         int g = lo + lo / 2 + 32;
         if (g > cc - 1) g = cc - 1;
@@ -351,9 +459,10 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
         for (int t = threadIdx.x; t < q; t += kSelBlock) sm.tb[t] = top_break(dval(sm.cand[t]), rho, M);
         __syncthreads();
         const double floorv = (Q < p) ? dval(sm.cand[C - 1]) : 0.0;
+        double th = 0.0;
+        const bool fnd = threadIdx.x < 32 && root_search(sm, q, C, floorv, Q >= p, rho, M, &th);
         if (threadIdx.x == 0) {
-          double th = 0.0;
-          sm.flag[1] = root_search(sm, q, C, floorv, Q >= p, rho, M, &th) ? 1 : 0;
+          sm.flag[1] = fnd ? 1 : 0;
           sm.root[0] = th;
         }
         __syncthreads();
@@ -440,10 +549,11 @@ __device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
   const int p = d.p;
   const double scale = 1.0 / (2.0 * nd->lambda2), M = nd->M;
   const double* g = d.grad;
-  const int8_t* st = d.state;
+  // S1 from its index list (a scan of the p states would be a chain of dependent
+  // loads per thread: ~50 loads deep at p = 50000)
   double s1 = 0.0;
-  for (int i = threadIdx.x; i < p; i += kSelBlock)
-    if (st && st[i] == kOne) s1 += huber(fabs(g[i]) * scale, M);
+  const int n1 = nd->n_one;
+  for (int t = threadIdx.x; t < n1; t += kSelBlock) s1 += huber(fabs(g[d.one_idx[t]]) * scale, M);
   s1 = block_sum<double, kSelBlock>(s1, sm.red);
   double s = 0.0;
   unsigned next_guess = 0u;

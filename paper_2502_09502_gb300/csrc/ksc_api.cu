@@ -118,6 +118,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(cn, p * 8);
   d.colnorm = cn;
   ALLOC(d.state, p);
+  ALLOC(d.one_idx, (size_t)p * 4);
   d.nseg = (int)((p + kSegLen - 1) / kSegLen);
   ALLOC(d.key, p * 4);
   ALLOC(d.dkey, p * 4);
@@ -499,6 +500,12 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   fill_slots<double>(wb, w0);
   const size_t tb = tbytes(pr->xdt);
   KSC_CUDA(cudaMemcpyAsync(d.state, ns.state.data(), p, cudaMemcpyHostToDevice, s));
+  // S1 as an index list: the in-loop dual term visits |S1| coordinates, not all p
+  std::vector<int> ones;
+  for (int64_t j = 0; j < p; ++j)
+    if (ns.state[j] == kOne) ones.push_back((int)j);
+  if (!ones.empty())
+    KSC_CUDA(cudaMemcpyAsync(d.one_idx, ones.data(), ones.size() * 4, cudaMemcpyHostToDevice, s));
   KSC_CUDA(cudaMemcpyAsync(d.beta, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
   KSC_CUDA(cudaMemcpyAsync((char*)d.beta + p * tb, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
   NodeDev h;
@@ -511,6 +518,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   h.tol_loop = node->rel_gap_tol;
   h.incumbent = node->incumbent;
   h.kp = ns.kp;
+  h.n_one = (int)ones.size();
   h.max_iter = node->max_iter;
   h.restart_on = (node->flags & KSC_FLAG_RESTART_OFF) ? 0 : 1;
   h.momentum_on = (node->flags & KSC_FLAG_MOMENTUM_OFF) ? 0 : 1;

@@ -41,6 +41,7 @@ struct Dev {
   const double* y;         // n
   const double* colnorm;   // p, FP64 column 2-norms rounded up
   int8_t* state;           // p (node coordinate states)
+  int* one_idx;            // p: the indices of S1, ascending (the first NodeDev::n_one)
   void* beta;              // 3 slots x p, FP64
   double* u;               // 3 slots x n: X beta in FP64
   double* grad;            // p: X^T grad F(u_gamma) in FP64

@@ -28,7 +28,7 @@ struct NodeDev {
   int max_iter;
   int restart_on, momentum_on;
   int loss;
-  int pad0;
+  int n_one;         // |S1|: its indices are the first n_one entries of Dev::one_idx
   // ---- state
   int iter;          // t: beta^t is in slot t % 3
   int done;
