@@ -173,14 +173,17 @@ __device__ SelectResult<U> block_select(int m, int q, Load load, unsigned* hist,
     for (int b = threadIdx.x; b < NB; b += BLOCK) hist[b] = given ? __ldcg(&first[b]) : 0u;
     __syncthreads();
     // warp-uniform loop; lanes with the same bin are aggregated (__match_any_sync)
-    // so that runs of equal keys (e.g. zeros) do not serialise on one counter
-    for (int base = 0; base < (given ? 0 : m); base += BLOCK) {
+    // so that runs of equal keys (e.g. zeros) do not serialise on one counter.  The
+    // next key is loaded before this one is binned: its global loads overlap the
+    // match and the atomic instead of waiting behind them
+    const int mm = given ? 0 : m;
+    U kn = ((int)threadIdx.x < mm) ? load((int)threadIdx.x) : (U)0;
+    for (int base = 0; base < mm; base += BLOCK) {
       const int i = base + (int)threadIdx.x;
+      const U k = kn;
+      if (i + BLOCK < mm) kn = load(i + BLOCK);
       int bin = -1;
-      if (i < m) {
-        U k = load(i);
-        if ((k & himask) == (prefix & himask)) bin = (int)((k >> lo) & (U)((1u << w) - 1u));
-      }
+      if (i < mm && (k & himask) == (prefix & himask)) bin = (int)((k >> lo) & (U)((1u << w) - 1u));
       const unsigned peers = __match_any_sync(0xffffffffu, bin);
       if (bin >= 0 && (threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1))
         atomicAdd(&hist[bin], (unsigned)__popc(peers));

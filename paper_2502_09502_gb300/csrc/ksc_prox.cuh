@@ -744,6 +744,7 @@ __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp,
   using B = Bits<T>;
   using U = typename B::U;
   double s1 = 0.0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < m; i += BLOCK)
     if (state && state[i] == kOne) s1 += huber(fabs(to_d(loada(i))) * scale, M);
   s1 = block_sum<double, BLOCK>(s1, sm.red);
@@ -756,6 +757,7 @@ __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp,
   SelectResult<U> R = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
   const double thr = to_d(B::val(R.thr));
   double s = 0.0;
+#pragma unroll 4
   for (int i = threadIdx.x; i < m; i += BLOCK) {
     U kb = keybits(i);
     if (kb > R.thr) s += huber(to_d(B::val(kb)) * scale, M);
