@@ -516,3 +516,29 @@ def test_eig_node_bound_against_node_enumeration():
     assert r.status == "converged"
     assert rp.dual - 1e-9 * abs(mip) <= r.dual <= mip + 1e-9 * abs(mip)
     assert r.beta[2] == 0 and r.beta[5] == 0
+
+
+def test_eig_bound_is_the_mip_optimum_for_orthogonal_columns():
+    # X^T X = n I: with lambda = n the eigen relaxation is separable and tight --
+    # 2 lambda_eig H_M(|c_j| / lambda_eig), c = X^T y, is the best decrease
+    # 2 |c_j| b_j - (n + lambda2) b_j^2 of one coordinate, so the bound equals the
+    # closed-form optimum of Eq. (1): ||y||^2 minus the k largest decreases
+    rng = np.random.default_rng(1800)
+    n, p, k = 30, 8, 3
+    Qm, _ = np.linalg.qr(rng.standard_normal((n, p)))
+    X = np.sqrt(n) * Qm
+    bt = np.zeros(p)
+    bt[[1, 4, 6]] = [1.0, -1.0, 0.5]
+    y = X @ bt + 0.3 * rng.standard_normal(n)
+    lam, M = 0.5, 0.9
+    c = X.T @ y
+    b = np.minimum(np.abs(c) / (n + lam), M)
+    dec = 2 * np.abs(c) * b - (n + lam) * b * b
+    closed = float(y @ y - np.sort(dec)[-k:].sum())
+    assert abs(closed - P.mip_enumerate(X, y, lam, M, k, 0)) <= 1e-9 * closed
+    # Q = X^T X - lambda I is (numerically) 0, so the bound does not depend on b
+    eig = n * (1 - 1e-12)
+    for beta in (np.zeros(p), rng.uniform(-M, M, p), bt):
+        assert abs(O.dual_bound(X, y, 0, lam, M, k, beta, eig=eig) - closed) <= 1e-8 * closed
+    persp = O.solve(X, y, 0, lam, M, k, tol=1e-12, max_iter=100000)
+    assert persp.dual < closed - 1e-3 * closed    # the perspective relaxation is not tight here
