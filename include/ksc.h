@@ -82,8 +82,10 @@ typedef enum {
                                         lambda on the perspective term, lambda the
                                         problem's certified shift (ksc_problem_eig_lambda,
                                         computed on first use by ksc_solve_batch and
-                                        ksc_bnb_solve).  Batched path only (BF16 X):
-                                        ksc_solve_node returns KSC_ERR_UNIMPLEMENTED    */
+                                        ksc_bnb_solve; ksc_server_submit refuses such a
+                                        node with KSC_ERR_INVALID_ARG until it is known).
+                                        Batched path only (BF16 X): ksc_solve_node
+                                        returns KSC_ERR_UNIMPLEMENTED                  */
 
 typedef struct ksc_problem ksc_problem;
 typedef struct ksc_server ksc_server;
