@@ -48,3 +48,41 @@ def test_labels_and_node_sets():
     again = G.node_sets(300, 50, seed=9)
     assert all(np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
                for x, y in zip(nodes, again))
+
+
+def test_squared_hinge_problems_share_the_classification_labels():
+    a = G.make_problem(400, 30, seed=6, loss=G.LOGISTIC)
+    b = G.make_problem(400, 30, seed=6, loss=G.SQHINGE)
+    assert np.array_equal(a.X, b.X) and np.array_equal(a.y, b.y)
+    assert set(np.unique(b.y)) == {-1.0, 1.0}
+
+
+def test_fp8_quantizer_scales_and_values():
+    P = G.make_problem(200, 40, seed=7, x_dtype=G.F32)
+    X = P.X.astype(np.float32)
+    X[:, 3] *= 1e-3                                   # a column of another magnitude
+    bits, s = G.quantize_fp8(X)
+    assert bits.dtype == np.uint8 and bits.shape == X.shape and s.shape == (40,)
+    m, e = np.frexp(s)
+    assert np.all(m == 0.5)                           # powers of two
+    v = G.fp8_values(bits)
+    assert np.abs(v).max() <= 448.0
+    rep = v.astype(np.float64) * s.astype(np.float64)
+    # the represented matrix is exact in FP32 and within e4m3's half ulp of X
+    assert np.array_equal(rep.astype(np.float32).astype(np.float64), rep)
+    amax = np.abs(X).max(0)
+    assert np.all(np.abs(rep - X) <= 2.0 ** -4 * np.abs(X) + 2.0 ** -9 * s)
+    assert np.all(amax / s <= 448.0) and np.all(amax / s > 224.0 - 1e-3)   # the smallest fitting scale
+
+
+def test_serving_mix_and_arrivals():
+    mix = G.serving_mix(64, seed=3)
+    assert mix == G.serving_mix(64, seed=3)
+    for m in mix:
+        assert m["loss"] in (G.LSQ, G.LOGISTIC)
+        assert 2000 <= m["n"] <= 40000 and 1000 <= m["p"] <= 100000 and 5 <= m["k"] <= 50
+        assert m["lambda2"] in (1e-3, 1e-2, 1e-1) and 1.0 <= m["M"] <= 5.0 and m["r"] in (0.1, 0.5, 0.9)
+    t = G.poisson_arrivals(50.0, 40.0, seed=2)
+    assert np.all(np.diff(t) > 0) and t[0] >= 0 and t[-1] < 40.0
+    assert abs(len(t) / 40.0 - 50.0) < 4 * np.sqrt(50.0 / 40.0) + 1     # Poisson count within 4 sigma
+    assert np.array_equal(t, G.poisson_arrivals(50.0, 40.0, seed=2))
