@@ -11,14 +11,16 @@
 //  gradient pass epilogue (k_matvec.cu): w (FP64), 32-bit selection keys = float
 //      bits of |w| (monotone: fl(a) > fl(b) implies a > b), first radix digit
 //      histogram -- fused into the CTA that finishes each column strip.
-//  k_prox_select (2 CTAs): integer radix passes give the top-k' key threshold;
-//      ties of the float key are broken exactly on |w| then index (Alg. 1 order);
-//      the top-Q candidates (float key >= the Q-th) are sorted as 64-bit patterns
-//      of |w| and a binary search over the breakpoints {a_j, theta_t, M/rho} of
-//      Phi finds the linear piece holding the root.  Q grows if the pooled block
-//      reaches below the candidates; beyond the shared-memory capacity a bracketed
-//      Newton iteration over full passes is used.  CTA 1: the in-loop dual term
-//      G*(X^T zeta_gamma) (Lemma 3.1 on the node) from keys of |grad|.
+//  k_prox_select (2 CTAs): the candidates predicted from the previous step (or
+//      integer radix passes) give the top-k' set; ties of the float key are broken
+//      exactly on |w| then index (Alg. 1 order); the top-Q candidates are sorted as
+//      64-bit patterns of |w| (bitonic, warp blocks in registers) and one warp's
+//      k-ary search over the breakpoints {a_j, theta_t, M/rho} of Phi (integer
+//      compares of their bit patterns) finds the linear piece holding the root.
+//      Q grows if the pooled block reaches below the candidates; beyond the
+//      shared-memory capacity a bracketed Newton iteration over full passes is
+//      used.  CTA 1: the in-loop dual term G*(X^T zeta_gamma) (Lemma 3.1 on the
+//      node) from keys of |grad|, with S1 read from its index list.
 //  k_prox_apply (grid): b, its float split for the dense forward pass, the
 //      nonzero list (one compaction segment per CTA, ascending index), sum |b_F|,
 //      and in the last CTA g(b) by the water-filling of Algorithm 2.
