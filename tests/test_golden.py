@@ -41,6 +41,15 @@ def test_closed_form_case(case):
     elif kind == "negconj":
         got = O.neg_conj(int(case[1]), _vec(case[2]), _vec(case[3]))
         exp = float(case[4])
+    elif kind == "loss":
+        got = O.loss(int(case[1]), _vec(case[2]), _vec(case[3]))
+        exp = float(case[4])
+    elif kind == "eigbound":
+        n, p = (int(t) for t in case[2].split())
+        X = _vec(case[1]).reshape(n, p)
+        got = O.dual_bound(X, _vec(case[3]), 0, float(case[4]), float(case[5]), int(case[6]), _vec(case[8]),
+                           eig=float(case[7]))
+        exp = float(case[9])
     else:
         raise AssertionError(kind)
     assert np.allclose(got, exp, rtol=1e-14, atol=1e-14), (got, exp)
