@@ -81,8 +81,8 @@ struct BatchDev {
   double* u_ref;
   double* r_ref;
   __nv_bfloat16* rpc;
-  double* G;
-  double* G_ref;
+  double* G;           // B x ldp: grad at gamma (k_bprox subtracts 2 eig gamma in place for eigen nodes)
+  double* G_ref;       // B x ldp: X^T r_ref, exact
   double* wbuf;        // B x ldp, or NULL
   int* slot_cur;       // B: slot of u^t (read by the forward product)
   int* slot_new;       // B: slot the forward product writes
