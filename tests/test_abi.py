@@ -147,3 +147,21 @@ def test_server_arguments_are_rejected_before_cuda(ksc):
     assert ksc.lib.ksc_server_destroy(None) == ksc.KSC_OK
     st = (C.c_int64 * 6)()
     assert ksc.lib.ksc_server_stats(None, st, 6) == ksc.KSC_ERR_INVALID_ARG
+
+
+def test_header_constants_match_the_binding(ksc):
+    # every KSC_* enumerator and #define of include/ksc.h has the same value in
+    # the Python binding (a drift would pass wrong codes through the ABI)
+    src = open(os.path.join(ROOT, "include", "ksc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    consts = {}
+    for name, val in re.findall(r"\b(KSC_[A-Z0-9_]+)\s*=\s*(\d+)", src):
+        consts[name] = int(val)
+    for name, val in re.findall(r"#define\s+(KSC_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+u?|\d+u?)", src):
+        consts[name] = int(val.rstrip("u"), 0)
+    assert len(consts) >= 20
+    alias = {"KSC_FP8_E4M3_COLSCALE": "KSC_FP8"}
+    for name, val in consts.items():
+        py = alias.get(name, name)
+        assert hasattr(ksc, py), name
+        assert getattr(ksc, py) == val, (name, getattr(ksc, py), val)
