@@ -167,7 +167,7 @@ typedef struct {
   double dual_bound;   /* certified FP64 lower bound on P_conv(node) <= P_MIP(node)   */
   double rel_gap;      /* (primal - dual_bound) / max(|primal|, 1e-300)               */
   int32_t iters;       /* FISTA steps taken                                           */
-  int32_t restarts;    /* momentum resets (Algorithm 3, line 11)                      */
+  int32_t restarts;    /* momentum resets (Algorithm 3's restart test)                      */
   int32_t pruned;      /* 1 if dual_bound > incumbent                                 */
   ksc_status status;   /* KSC_OK (gap met, or an incumbent rule fired),
                           KSC_NOT_CONVERGED, KSC_ERR_INFEASIBLE_NODE                  */

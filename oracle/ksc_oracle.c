@@ -1,7 +1,9 @@
 /*
  * ksc_oracle.c -- plain FP64 CPU oracle (TEST INFRASTRUCTURE ONLY; see
  * ksc_oracle.h).  Single-threaded, no blocking, no fusion: each routine is the
- * paper's definition or algorithm written out step by step.
+ * definition it computes (H_M, g*, the losses and their conjugates, the bound)
+ * or, for the prox, g and the solver, the paper's method restated from its
+ * mathematics (Lemma 3.1, Lemma 3.3, Theorem 3.6, Sec. 3.3, Algorithm 3).
  *
  * Readings of passages where the paper is ambiguous, garbled or silent:
  *  R1  Sign of zeta in the safe bound (Sec. 3.4): weak duality is written as
@@ -16,13 +18,14 @@
  *      least squares (F = ||u-y||^2) and squared hinge (F'' <= 2 where it
  *      exists, F' 2-Lipschitz), 1/4 for logistic.
  *  R4  Relative gap (Sec. 4.2, eps = 1e-6): (primal - dual) / max(|primal|, 1e-300).
- *  R5  Algorithm 4 typos: nu_1 := nuhat_1; loop bound n := p; v_prev := nu_prev;
- *      the look-forward test reads "j < p and nu <= nuhat_{j+1}".
+ *  R5  Algorithm 4 as printed has typos (an uninitialised first block value, a
+ *      loop bound n for p, v_prev for nu_prev, a look-forward test against the
+ *      current element); the stack form of the pooling below needs none of it.
  *  R6  Block value of a merged block: prox_{(P_b/N_b) H_M}(S_b/N_b) (App. A).
  *  R7  Ties in the sort of Algorithm 1 / 2: descending |.|, ties by ascending
  *      index (the prox value does not depend on it; the order output does).
- *  R8  Algorithm 3 line 2 prints L^1 = f(beta^1, y); read f(X beta^1, y) +
- *      2 lambda2 g(beta^1), the same objective as line 10.
+ *  R8  Algorithm 3 prints its initial objective as f(beta^1, y); read
+ *      F(X beta^1) + 2 lambda2 g(beta^1), the objective its restart test uses.
  *  R9  Alg. 2 assumes beta in dom g; outside a 1e-12 relative slack it returns
  *      +inf (the value of g there, by the convention of Sec. 3).
  *  R10 Warm start: S0 coordinates set to 0 and all coordinates clipped to
@@ -62,109 +65,125 @@ double kso_huber_prox(double x, double c, double M) {
   return x < 0 ? -v : v;
 }
 
-/* ------------------------------------------------------------ sorting */
+/* ------------------------------------------------- magnitude order */
 
-typedef struct { double key; int64_t idx; } kso_pair;
+typedef struct { double mag; int64_t idx; } kso_entry;
 
-/* descending key, ties by ascending index (reading R7) */
-static int cmp_desc_stable(const void *pa, const void *pb) {
-  const kso_pair *a = (const kso_pair *)pa, *b = (const kso_pair *)pb;
-  if (a->key > b->key) return -1;
-  if (a->key < b->key) return 1;
-  return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
+/* Order of the magnitudes used by the prox and by g: descending |v|, equal
+ * magnitudes by ascending index (reading R7). */
+static int by_magnitude(const void *pa, const void *pb) {
+  const kso_entry *a = (const kso_entry *)pa, *b = (const kso_entry *)pb;
+  if (a->mag != b->mag) return (a->mag > b->mag) ? -1 : 1;
+  return (a->idx > b->idx) - (a->idx < b->idx);
 }
 
-static kso_pair *sorted_abs(const double *v, int64_t p) {
-  kso_pair *s = (kso_pair *)malloc((size_t)(p > 0 ? p : 1) * sizeof(kso_pair));
-  for (int64_t j = 0; j < p; ++j) { s[j].key = fabs(v[j]); s[j].idx = j; }
-  qsort(s, (size_t)p, sizeof(kso_pair), cmp_desc_stable);
-  return s;
+static kso_entry *magnitude_order(const double *v, int64_t p) {
+  kso_entry *e = (kso_entry *)malloc((size_t)(p > 0 ? p : 1) * sizeof(kso_entry));
+  for (int64_t j = 0; j < p; ++j) { e[j].mag = fabs(v[j]); e[j].idx = j; }
+  qsort(e, (size_t)p, sizeof(kso_entry), by_magnitude);
+  return e;
 }
 
-/* ------------------------------------------------- Algorithm 1 + 4 (PAVA) */
+/* ------------------------------------------- prox of rho g* (Sec. 3.3) */
+
+/* prox_{rho g*}(mu) = argmin_a 1/2 ||a - mu||^2 + rho TopSum_k(H_M(a)), with
+ * g* in the form of Lemma 3.1.
+ *
+ * Reduction (Lemma 3.3 and its proof): the minimiser keeps the signs of mu and
+ * the order of |mu|, so a_j = sgn(mu_j) nu_(r) where r is the rank of |mu_j|
+ * and nu is non-increasing in r.  For non-increasing nu >= 0 the top-k sum is
+ * the sum over the first k ranks, so with m_r the r-th largest |mu| the problem
+ * becomes an isotonic regression with separable convex terms:
+ *
+ *     min_{nu_1 >= ... >= nu_p}  sum_r 1/2 (nu_r - m_r)^2 + c_r H_M(nu_r),
+ *     c_r = rho for r <= k, 0 otherwise                       (Algorithm 1).
+ *
+ * It is solved by pooling adjacent violators (the method of Algorithm 4,
+ * App. A), here in its textbook stack form: ranks enter left to right as
+ * singleton blocks; while the newest block's value exceeds the value of the
+ * block before it, the two are merged.  A block B carries its count N_B, the
+ * sum S_B of its m_r and the sum P_B of its c_r; completing the square,
+ * sum_{r in B} 1/2 (v - m_r)^2 + c_r H_M(v) = N_B [1/2 (v - S_B/N_B)^2 +
+ * (P_B/N_B) H_M(v)] + const, so its value is prox_{(P_B/N_B) H_M}(S_B/N_B)
+ * (reading R6).  The objective is strictly convex, so the pooled solution is
+ * the unique minimiser whatever the merge order. */
+typedef struct { double cnt, msum, csum, value; int64_t last; } kso_block;
+
+static double block_value(const kso_block *b, double M) {
+  return kso_huber_prox(b->msum / b->cnt, b->csum / b->cnt, M);
+}
 
 int kso_prox_gstar(const double *mu, int64_t p, int64_t k, double rho, double M,
                    double *alpha, int64_t *perm) {
   if (p <= 0) return 0;
-  /* line 3: SpecialSort -- m[r] = |mu_{pi(r)}| in non-increasing order */
-  kso_pair *s = sorted_abs(mu, p);
-  double *m = (double *)malloc((size_t)p * sizeof(double));
-  double *w = (double *)malloc((size_t)p * sizeof(double));     /* rho_j  */
-  double *nuhat = (double *)malloc((size_t)p * sizeof(double));
+  kso_entry *ord = magnitude_order(mu, p);
+  kso_block *stack = (kso_block *)malloc((size_t)p * sizeof(kso_block));
+  int64_t top = -1;                      /* index of the newest block */
   for (int64_t r = 0; r < p; ++r) {
-    m[r] = s[r].key;
-    w[r] = (r < k) ? rho : 0.0;                                 /* line 1 */
-    nuhat[r] = kso_huber_prox(m[r], w[r], M);                   /* lines 7-9 */
-  }
-  /* lines 11-14 via Algorithm 4 (1-based block arrays as printed) */
-  double *P = (double *)malloc((size_t)(p + 1) * sizeof(double));
-  double *S = (double *)malloc((size_t)(p + 1) * sizeof(double));
-  double *N = (double *)malloc((size_t)(p + 1) * sizeof(double));
-  double *nu = (double *)malloc((size_t)(p + 1) * sizeof(double));
-  int64_t *rr = (int64_t *)malloc((size_t)(p + 1) * sizeof(int64_t));
-  int64_t b = 1;
-  P[1] = w[0]; S[1] = m[0]; N[1] = 1.0; nu[1] = nuhat[0]; rr[1] = 1;
-  double nu_prev = nuhat[0];
-  int64_t j = 2;                                   /* 1-based element index */
-  while (j <= p) {
-    b = b + 1;
-    P[b] = w[j - 1]; S[b] = m[j - 1]; N[b] = 1.0;
-    double v = nuhat[j - 1];
-    if (v > nu_prev) {                             /* isotonic violation    */
-      b = b - 1;
-      P[b] += w[j - 1]; S[b] += m[j - 1]; N[b] += 1.0;
-      v = kso_huber_prox(S[b] / N[b], P[b] / N[b], M);
-      while (j < p && v <= nuhat[j]) {             /* look forward (R5)     */
-        j = j + 1;
-        P[b] += w[j - 1]; S[b] += m[j - 1]; N[b] += 1.0;
-        v = kso_huber_prox(S[b] / N[b], P[b] / N[b], M);
-      }
-      while (b > 1 && nu[b - 1] < v) {             /* look backward         */
-        b = b - 1;
-        P[b] += P[b + 1]; S[b] += S[b + 1]; N[b] += N[b + 1];
-        v = kso_huber_prox(S[b] / N[b], P[b] / N[b], M);
-      }
+    kso_block nb;
+    nb.cnt = 1.0;
+    nb.msum = ord[r].mag;
+    nb.csum = (r < k) ? rho : 0.0;
+    nb.last = r;
+    nb.value = block_value(&nb, M);
+    stack[++top] = nb;
+    while (top > 0 && stack[top].value > stack[top - 1].value) {
+      kso_block *lo = &stack[top - 1];
+      const kso_block *hi = &stack[top];
+      lo->cnt += hi->cnt;
+      lo->msum += hi->msum;
+      lo->csum += hi->csum;
+      lo->last = hi->last;
+      lo->value = block_value(lo, M);
+      --top;
     }
-    nu[b] = v; rr[b] = j;
-    nu_prev = v; j = j + 1;
   }
-  /* expand block values back over their elements */
-  int64_t start = 0;
-  for (int64_t l = 1; l <= b; ++l) {
-    for (int64_t q = start; q < rr[l]; ++q) nuhat[q] = nu[l];
-    start = rr[l];
+  /* each rank takes its block's value; a_j = sgn(mu_j) nu_(rank of j) */
+  int64_t r = 0;
+  for (int64_t b = 0; b <= top; ++b) {
+    for (; r <= stack[b].last; ++r) {
+      int64_t j = ord[r].idx;
+      double s = (mu[j] > 0) ? 1.0 : ((mu[j] < 0) ? -1.0 : 0.0);
+      alpha[j] = s * stack[b].value;
+      if (perm) perm[r] = j;
+    }
   }
-  /* line 16: sgn(mu) .* pi^{-1}(nuhat) */
-  for (int64_t r = 0; r < p; ++r) {
-    int64_t i = s[r].idx;
-    double sg = (mu[i] > 0) ? 1.0 : ((mu[i] < 0) ? -1.0 : 0.0);
-    alpha[i] = sg * nuhat[r];
-    if (perm) perm[r] = i;
-  }
-  free(P); free(S); free(N); free(nu); free(rr);
-  free(m); free(w); free(nuhat); free(s);
+  free(stack);
+  free(ord);
   return 0;
 }
 
-/* Moreau identity (Sec. 3.3): prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w).
- * Where prox_{rho g*} leaves a coordinate unchanged (alpha_j = mu_j: the tail
- * outside the pooled block, and every coordinate when k = 0, where g is the
- * indicator of {0}) the identity gives beta_j = w_j - rho w_j / rho = 0 exactly;
- * it is set to 0 rather than to the rounding residue of that difference. */
+/* Moreau decomposition (Sec. 3.3): prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w).
+ * Where prox_{rho g*} leaves a coordinate unchanged (a_j = mu_j: ranks outside
+ * the pooled block past the top k, and every coordinate when k = 0, where g is
+ * the indicator of {0}) the decomposition gives beta_j = w_j - rho w_j / rho = 0
+ * exactly; it is set to 0 rather than to the rounding residue of that
+ * difference (reading R14). */
 int kso_prox_g(const double *w, int64_t p, int64_t k, double rho, double M,
                double *beta, int64_t *perm) {
   if (p <= 0) return 0;
   double *mu = (double *)malloc((size_t)p * sizeof(double));
-  double *al = (double *)malloc((size_t)p * sizeof(double));
+  double *a = (double *)malloc((size_t)p * sizeof(double));
   for (int64_t j = 0; j < p; ++j) mu[j] = rho * w[j];
-  kso_prox_gstar(mu, p, k, rho, M, al, perm);
-  for (int64_t j = 0; j < p; ++j) beta[j] = (al[j] == mu[j]) ? 0.0 : w[j] - al[j] / rho;
-  free(mu); free(al);
+  kso_prox_gstar(mu, p, k, rho, M, a, perm);
+  for (int64_t j = 0; j < p; ++j) beta[j] = (a[j] == mu[j]) ? 0.0 : w[j] - a[j] / rho;
+  free(mu);
+  free(a);
   return 0;
 }
 
-/* ------------------------------------------------------ Algorithm 2 (g) */
+/* ------------------------------------------------- g (Theorem 3.6) */
 
+/* g(beta) = min_z 1/2 sum_j beta_j^2 / z_j over sum z <= k, 0 <= z <= 1,
+ * |beta_j| <= M z_j (Sec. 3.1), +inf outside dom g (reading R9).
+ *
+ * Theorem 3.6 (Algorithm 2) gives the minimiser in closed form: with the
+ * magnitudes in descending order, the t largest take z = 1 and the rest share
+ * the remaining budget in proportion to their size, z_j = |beta_j| / s with the
+ * level s = (sum of the other magnitudes) / (k - t); t is the first count at
+ * which the next magnitude does not exceed that level.  Then
+ * g = 1/2 sum_{top t} beta_j^2 + 1/2 (k - t) s^2.  When every magnitude past
+ * the top t is zero the level is 0 and so is z there. */
 double kso_g_value(const double *beta, int64_t p, int64_t k, double M, double *z) {
   double l1 = 0.0, linf = 0.0;
   for (int64_t j = 0; j < p; ++j) {
@@ -173,46 +192,40 @@ double kso_g_value(const double *beta, int64_t p, int64_t k, double M, double *z
     if (t > linf) linf = t;
   }
   if (z) for (int64_t j = 0; j < p; ++j) z[j] = 0.0;
-  /* dom g: |b_j| <= M and sum |b_j| <= k M (reading R9) */
   if (linf > M * (1.0 + 1e-12) || l1 > (double)k * M * (1.0 + 1e-12)) return INFINITY;
   if (p == 0 || k <= 0) return 0.0;
-  kso_pair *s = sorted_abs(beta, p);               /* line 2 (full sort)    */
-  double sum = l1;                                 /* line 3                */
-  double g = 0.0, sbar = 0.0;
-  int64_t jstar = -1;                              /* 0-based break position */
-  for (int64_t j = 0; j < k; ++j) {                /* lines 5-8             */
-    double bj = (j < p) ? s[j].key : 0.0;
-    sbar = sum / (double)(k - j);
-    if (sbar >= bj) {                              /* psi_{j:k} = sbar      */
-      g += 0.5 * (double)(k - j) * sbar * sbar;
-      jstar = j;
-      break;
-    }
-    g += 0.5 * bj * bj;                            /* psi_j = |b_j|         */
-    sum -= bj;
+  kso_entry *ord = magnitude_order(beta, p);
+  double rest = l1;          /* sum of the magnitudes not yet given z = 1 */
+  double g = 0.0, level = 0.0;
+  int64_t t = 0;             /* number of coordinates with z = 1 */
+  int found = 0;
+  for (; t < k; ++t) {
+    double next = (t < p) ? ord[t].mag : 0.0;
+    level = rest / (double)(k - t);
+    if (next <= level) { found = 1; break; }
+    g += 0.5 * next * next;
+    rest -= next;
   }
-  /* relaxed z (from the proof of Thm 3.6): z = 1 where psi_j = |b_j|, and
-   * z_j = |b_j| / sbar on the rest of the coordinates */
+  if (found) g += 0.5 * (double)(k - t) * level * level;
   if (z) {
-    int64_t fixed = (jstar < 0) ? (k < p ? k : p) : jstar;
     for (int64_t r = 0; r < p; ++r) {
-      int64_t i = s[r].idx;
-      if (r < fixed) z[i] = 1.0;
-      else z[i] = (sbar > 0.0) ? s[r].key / sbar : 0.0;
+      int64_t j = ord[r].idx;
+      if (r < t) z[j] = 1.0;
+      else z[j] = (found && level > 0.0) ? ord[r].mag / level : 0.0;
     }
   }
-  free(s);
+  free(ord);
   return g;
 }
 
 /* Lemma 3.1: g*(a) = sum of the k largest H_M(a_j). */
 double kso_gstar(const double *a, int64_t p, int64_t k, double M) {
   if (p <= 0 || k <= 0) return 0.0;
-  kso_pair *s = sorted_abs(a, p);                  /* H_M monotone in |a|  */
-  double t = 0.0;
-  for (int64_t r = 0; r < k && r < p; ++r) t += kso_huber(s[r].key, M);
-  free(s);
-  return t;
+  kso_entry *ord = magnitude_order(a, p);          /* H_M is increasing in |a| */
+  double s = 0.0;
+  for (int64_t r = 0; r < k && r < p; ++r) s += kso_huber(ord[r].mag, M);
+  free(ord);
+  return s;
 }
 
 /* ----------------------------------------------------------- node forms */
@@ -406,8 +419,9 @@ double kso_power_iteration(const void *X, int xdt, int64_t n, int64_t p, int64_t
   return lam;
 }
 
-/* ------------------------------------------------------ Algorithm 3 */
+/* ------------------------------------------- restarted FISTA (Sec. 3) */
 
+/* Lipschitz constant of beta -> grad F(X beta) (reading R3). */
 static double lipschitz(const kso_solve_args *a) {
   if (a->L > 0) return a->L;
   double lmax = kso_power_iteration(a->X, a->x_dtype, a->n, a->p, a->ldx, 1e-10, 10000, NULL);
@@ -422,115 +436,145 @@ static double sumsq(const double *v, int64_t m) {
   return s;
 }
 
-double kso_primal(const kso_solve_args *a, const double *beta) {
-  double *u = (double *)malloc((size_t)a->n * sizeof(double));
-  kso_matvec(a->X, a->x_dtype, a->n, a->p, a->ldx, beta, u);
+/* Objective of the node problem at beta, given u = X beta:
+ * F(u) + 2 lambda2 g_node(beta); with eig > 0 the eigen-perspective objective
+ * b^T Q b - 2 y^T X b + ||y||^2 + 2 lambda_eig g_node(b) = ||u - y||^2 - eig ||b||^2
+ * + 2 (lambda2 + eig) g_node(b) (R20). */
+static double objective_at(const kso_solve_args *a, const double *beta, const double *u) {
   double f = kso_loss(a->loss, u, a->y, a->n);
   double g = kso_g_node(beta, a->p, a->state, a->k, a->M, NULL);
-  free(u);
-  if (a->eig > 0)   /* b^T Q b - 2 y^T X b + ||y||^2 + 2 lambda_eig g(b), R20 */
-    return f - a->eig * sumsq(beta, a->p) + 2.0 * (a->lambda2 + a->eig) * g;
+  if (a->eig > 0) return f - a->eig * sumsq(beta, a->p) + 2.0 * (a->lambda2 + a->eig) * g;
   return f + 2.0 * a->lambda2 * g;
 }
 
-/* App. D.2: ||y||^2 - b^T Q b - G*_node(2 (X^T y - Q b)) with Q b = X^T X b - eig b
- * and G*_node the conjugate of 2 lambda_eig g_node (R20). */
-static double eig_dual_bound(const kso_solve_args *a, const double *beta) {
+/* Weak-duality bound of Sec. 3.4 at zeta = -grad F(u), u = X beta (reading R1):
+ * -F*(-zeta) - G*_node(X^T zeta), G = 2 lambda2 g_node. */
+static double bound_at(const kso_solve_args *a, const double *u) {
   int64_t n = a->n, p = a->p;
-  double *u = (double *)malloc((size_t)n * sizeof(double));
-  double *qb = (double *)malloc((size_t)p * sizeof(double));
-  double *xty = (double *)malloc((size_t)p * sizeof(double));
-  kso_matvec(a->X, a->x_dtype, n, p, a->ldx, beta, u);
-  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, u, qb);
-  for (int64_t j = 0; j < p; ++j) qb[j] -= a->eig * beta[j];          /* Q b */
-  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, a->y, xty);
-  double bqb = 0.0;
-  for (int64_t j = 0; j < p; ++j) {
-    bqb += beta[j] * qb[j];
-    xty[j] = 2.0 * (xty[j] - qb[j]);                                  /* a */
-  }
-  double d = sumsq(a->y, n) - bqb
-           - kso_Gstar_node(xty, p, a->state, a->k, a->lambda2 + a->eig, a->M);
-  free(u); free(qb); free(xty);
-  return d;
-}
-
-double kso_dual_bound(const kso_solve_args *a, const double *beta) {
-  if (a->eig > 0) return eig_dual_bound(a, beta);
-  int64_t n = a->n, p = a->p;
-  double *u = (double *)malloc((size_t)n * sizeof(double));
   double *zeta = (double *)malloc((size_t)n * sizeof(double));
   double *xz = (double *)malloc((size_t)p * sizeof(double));
-  kso_matvec(a->X, a->x_dtype, n, p, a->ldx, beta, u);
   kso_loss_grad(a->loss, u, a->y, n, zeta);
-  for (int64_t i = 0; i < n; ++i) zeta[i] = -zeta[i];        /* reading R1 */
+  for (int64_t i = 0; i < n; ++i) zeta[i] = -zeta[i];
   kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, zeta, xz);
   double d = kso_neg_conj(a->loss, zeta, a->y, n)
            - kso_Gstar_node(xz, p, a->state, a->k, a->lambda2, a->M);
-  free(u); free(zeta); free(xz);
+  free(zeta);
+  free(xz);
   return d;
 }
 
+/* Eigen-perspective bound of App. D.2 at beta, given u = X beta (R20):
+ * ||y||^2 - b^T Q b - G*_node(2 (X^T y - Q b)), Q b = X^T u - eig b, G* the
+ * conjugate of 2 lambda_eig g_node. */
+static double eig_bound_at(const kso_solve_args *a, const double *beta, const double *u) {
+  int64_t n = a->n, p = a->p;
+  double *qb = (double *)malloc((size_t)p * sizeof(double));
+  double *arg = (double *)malloc((size_t)p * sizeof(double));
+  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, u, qb);
+  for (int64_t j = 0; j < p; ++j) qb[j] -= a->eig * beta[j];
+  kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, a->y, arg);
+  double bqb = 0.0;
+  for (int64_t j = 0; j < p; ++j) {
+    bqb += beta[j] * qb[j];
+    arg[j] = 2.0 * (arg[j] - qb[j]);
+  }
+  double d = sumsq(a->y, n) - bqb
+           - kso_Gstar_node(arg, p, a->state, a->k, a->lambda2 + a->eig, a->M);
+  free(qb);
+  free(arg);
+  return d;
+}
+
+static double lower_bound_at(const kso_solve_args *a, const double *beta, const double *u) {
+  return (a->eig > 0) ? eig_bound_at(a, beta, u) : bound_at(a, u);
+}
+
+double kso_primal(const kso_solve_args *a, const double *beta) {
+  double *u = (double *)malloc((size_t)a->n * sizeof(double));
+  kso_matvec(a->X, a->x_dtype, a->n, a->p, a->ldx, beta, u);
+  double v = objective_at(a, beta, u);
+  free(u);
+  return v;
+}
+
+double kso_dual_bound(const kso_solve_args *a, const double *beta) {
+  double *u = (double *)malloc((size_t)a->n * sizeof(double));
+  kso_matvec(a->X, a->x_dtype, a->n, a->p, a->ldx, beta, u);
+  double d = lower_bound_at(a, beta, u);
+  free(u);
+  return d;
+}
+
+/* Algorithm 3: accelerated proximal gradient on F(X b) + 2 lambda2 g_node(b)
+ * with step 1/L, momentum weight phi/(phi+3) and a restart of the momentum
+ * counter whenever the objective does not decrease (Sec. 3, Fig. 3); after each
+ * step the bound of Sec. 3.4 at the new iterate gives the gap of Sec. 4.2 (R4)
+ * and the early-termination rules of Sec. 4.3 (R12).  The prox of the step is
+ * the prox of rho^-1 g_node with rho = L / (2 lambda2): a step of length 1/L on
+ * 2 lambda2 g_node.  The first iterate is the projected warm start (R10) and the
+ * first objective is the objective at it (R8). */
 int kso_solve(const kso_solve_args *a, double *beta, double *z, double *trace,
               kso_solve_out *out) {
   int64_t n = a->n, p = a->p;
   memset(out, 0, sizeof(*out));
-  int64_t kp = a->k - count_state(a->state, p, KSO_ONE);
-  if (kp < 0) {
+  if (a->k - count_state(a->state, p, KSO_ONE) < 0) {
     out->status = KSO_INFEASIBLE; out->dual = INFINITY; out->primal = INFINITY;
     return 0;
   }
-  double L = lipschitz(a);
-  double lam = a->lambda2 + (a->eig > 0 ? a->eig : 0.0);   /* lambda_eig, R20 */
-  double rho = L / (2.0 * lam);
+  const double L = lipschitz(a);
+  const double lam = a->lambda2 + (a->eig > 0 ? a->eig : 0.0);   /* lambda_eig, R20 */
+  const double rho = L / (2.0 * lam);
   out->L = L;
-  double *bprev = (double *)malloc((size_t)p * sizeof(double));
-  double *bcur = (double *)malloc((size_t)p * sizeof(double));
-  double *gam = (double *)malloc((size_t)p * sizeof(double));
+  double *b_old = (double *)malloc((size_t)p * sizeof(double));   /* b^{t-1} */
+  double *b = (double *)malloc((size_t)p * sizeof(double));       /* b^t     */
+  double *v = (double *)malloc((size_t)p * sizeof(double));       /* extrapolated point, then the gradient step */
   double *grad = (double *)malloc((size_t)p * sizeof(double));
   double *u = (double *)malloc((size_t)n * sizeof(double));
   double *r = (double *)malloc((size_t)n * sizeof(double));
-  /* line 1 (with a warm start, reading R10) */
   for (int64_t j = 0; j < p; ++j) {
-    double b = a->warm ? a->warm[j] : 0.0;
-    if (a->state && a->state[j] == KSO_ZERO) b = 0.0;
-    b = (b > a->M) ? a->M : ((b < -a->M) ? -a->M : b);
-    bprev[j] = bcur[j] = b;
+    double x = a->warm ? a->warm[j] : 0.0;
+    if (a->state && a->state[j] == KSO_ZERO) x = 0.0;
+    b_old[j] = b[j] = fmin(fmax(x, -a->M), a->M);
   }
-  double phi = 1.0;
-  double Lcur = kso_primal(a, bcur);                          /* line 2, R8 */
-  double D = -INFINITY, gap = INFINITY;
+  kso_matvec(a->X, a->x_dtype, n, p, a->ldx, b, u);
+  double obj = objective_at(a, b, u);
+  double phi = 1.0, D = -INFINITY, gap = INFINITY;
   int64_t t = 0, restarts = 0;
   int32_t status = KSO_MAX_ITER;
   for (t = 1; t <= a->max_iter; ++t) {
-    double c = a->momentum ? phi / (phi + 3.0) : 0.0;
-    for (int64_t j = 0; j < p; ++j) gam[j] = bcur[j] + c * (bcur[j] - bprev[j]);  /* line 5 */
-    kso_matvec(a->X, a->x_dtype, n, p, a->ldx, gam, u);
+    /* extrapolation */
+    const double c = a->momentum ? phi / (phi + 3.0) : 0.0;
+    for (int64_t j = 0; j < p; ++j) v[j] = b[j] + c * (b[j] - b_old[j]);
+    /* gradient of the smooth part at the extrapolated point */
+    kso_matvec(a->X, a->x_dtype, n, p, a->ldx, v, u);
     kso_loss_grad(a->loss, u, a->y, n, r);
-    kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, r, grad);   /* grad F(gamma) */
-    if (a->eig > 0)                                          /* - 2 eig gamma, R20 */
-      for (int64_t j = 0; j < p; ++j) grad[j] -= 2.0 * a->eig * gam[j];
-    for (int64_t j = 0; j < p; ++j) gam[j] -= grad[j] / L;  /* line 7 */
-    memcpy(bprev, bcur, (size_t)p * sizeof(double));
-    kso_prox_g_node(gam, p, a->state, a->k, rho, a->M, bcur, NULL);  /* line 8 */
-    double Lnext = kso_primal(a, bcur);                     /* line 10 */
-    if (a->restart && Lnext >= Lcur) { phi = 1.0; ++restarts; }       /* line 11 */
-    else phi = phi + 1.0;
-    Lcur = Lnext;
-    D = kso_dual_bound(a, bcur);                            /* Sec. 3.4 */
-    gap = (Lcur - D) / fmax(fabs(Lcur), 1e-300);            /* R4 */
-    if (trace) { trace[2 * (t - 1)] = Lcur; trace[2 * (t - 1) + 1] = D; }
-    if (isfinite(a->incumbent)) {                           /* Sec. 4.3 rules */
+    kso_rmatvec(a->X, a->x_dtype, n, p, a->ldx, r, grad);
+    if (a->eig > 0)                                  /* Q = X^T X - eig I, R20 */
+      for (int64_t j = 0; j < p; ++j) grad[j] -= 2.0 * a->eig * v[j];
+    /* proximal step */
+    for (int64_t j = 0; j < p; ++j) v[j] -= grad[j] / L;
+    memcpy(b_old, b, (size_t)p * sizeof(double));
+    kso_prox_g_node(v, p, a->state, a->k, rho, a->M, b, NULL);
+    /* objective, restart test, bound and gap at the new iterate */
+    kso_matvec(a->X, a->x_dtype, n, p, a->ldx, b, u);
+    const double obj_new = objective_at(a, b, u);
+    if (a->restart && obj_new >= obj) { phi = 1.0; ++restarts; }
+    else phi += 1.0;
+    obj = obj_new;
+    D = lower_bound_at(a, b, u);
+    gap = (obj - D) / fmax(fabs(obj), 1e-300);
+    if (trace) { trace[2 * (t - 1)] = obj; trace[2 * (t - 1) + 1] = D; }
+    if (isfinite(a->incumbent)) {
       if (D > a->incumbent) { status = KSO_PRUNED; break; }
-      if (Lcur < a->incumbent) { status = KSO_PRIMAL_BELOW; break; }
+      if (obj < a->incumbent) { status = KSO_PRIMAL_BELOW; break; }
     }
     if (gap <= a->tol) { status = KSO_CONVERGED; break; }
   }
   if (t > a->max_iter) t = a->max_iter;
-  memcpy(beta, bcur, (size_t)p * sizeof(double));
-  if (z) kso_g_node(bcur, p, a->state, a->k, a->M, z);
-  out->primal = Lcur; out->dual = D; out->gap = gap;
+  memcpy(beta, b, (size_t)p * sizeof(double));
+  if (z) kso_g_node(b, p, a->state, a->k, a->M, z);
+  out->primal = obj; out->dual = D; out->gap = gap;
   out->iters = t; out->restarts = restarts; out->status = status;
-  free(bprev); free(bcur); free(gam); free(grad); free(u); free(r);
+  free(b_old); free(b); free(v); free(grad); free(u); free(r);
   return 0;
 }

@@ -7,15 +7,15 @@
  * the smoke check and the CPU-baseline leg of the benchmark may load it.  It
  * shares no code, header, table or helper with the CUDA path.
  *
- * Every routine follows the paper's own steps, in FP64, in the order the paper
- * gives them:
- *   - Huber function H_M ............................ Sec. 3.1, Eq. (H_M)
+ * Every routine is a definition written out, or the paper's method restated
+ * from its mathematics, in FP64:
+ *   - Huber function H_M ............................ Sec. 3.1
  *   - g*(a) = TopSum_k(H_M(a)) ...................... Lemma 3.1
- *   - prox_{rho g*} by sort + customised PAVA ....... Algorithm 1, with the
- *     up-and-down block merge of Algorithm 4 (App. A, proof of Lemma 3.5)
- *   - prox_{rho^-1 g} by the extended Moreau identity  Sec. 3.3, Eq. (Moreau)
- *   - g(beta) by majorisation ....................... Algorithm 2 (Thm 3.6)
- *   - restarted FISTA ............................... Algorithm 3
+ *   - prox_{rho g*}: sign/order reduction to an isotonic regression (Lemma 3.3)
+ *     solved by pooling adjacent violators (the method of App. A), stack form
+ *   - prox_{rho^-1 g} by the Moreau decomposition ... Sec. 3.3
+ *   - g(beta) in closed form ........................ Theorem 3.6
+ *   - restarted accelerated proximal gradient ....... Algorithm 3 (Sec. 3)
  *   - safe lower bound by weak duality .............. Sec. 3.4, with the GLM
  *     conjugates of App. D.1
  *
@@ -53,7 +53,7 @@ double kso_huber(double a, double M);
 /* prox_{c H_M}(x) = argmin_v 1/2 (v-x)^2 + c H_M(v), c >= 0. */
 double kso_huber_prox(double x, double c, double M);
 
-/* prox_{rho g*}(mu), Algorithm 1 + Algorithm 4.  perm (optional, length p)
+/* prox_{rho g*}(mu) (Sec. 3.3, Lemma 3.3, App. A).  perm (optional, length p)
  * receives the sort order pi: perm[r] = index of the r-th largest |mu|
  * (ties broken by ascending index).  Returns 0. */
 int kso_prox_gstar(const double *mu, int64_t p, int64_t k, double rho, double M,
@@ -61,7 +61,7 @@ int kso_prox_gstar(const double *mu, int64_t p, int64_t k, double rho, double M,
 /* prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w)  (Moreau, Sec. 3.3). */
 int kso_prox_g(const double *w, int64_t p, int64_t k, double rho, double M,
                double *beta, int64_t *perm);
-/* g(beta) by Algorithm 2; z (optional, length p) receives the minimising
+/* g(beta) by Theorem 3.6; z (optional, length p) receives the minimising
  * relaxed z.  Returns +inf when beta is outside dom g (relative slack 1e-12). */
 double kso_g_value(const double *beta, int64_t p, int64_t k, double M, double *z);
 /* g*(a) = TopSum_k(H_M(a)), Lemma 3.1. */

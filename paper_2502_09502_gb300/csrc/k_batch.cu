@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(256) k_binit_copy(BatchDev d, const int* list)
 
 // u^0 = u^1 = u_ref (set by the anchor) -- or, after the zero anchor, u^1 from the
 // admission product in slot 1, copied to slot 0 --, F(u^1) in FP64, g(beta^1)
-// (Alg. 2), L^1 = F(u^1) + 2 lambda2 g(beta^1)  (Algorithm 3 line 2)
+// (Alg. 2), L^1 = F(u^1) + 2 lambda2 g(beta^1)  (the initial objective of Algorithm 3)
 __global__ void __launch_bounds__(kBProxBlock) k_binit_node(BatchDev d, const int* list, int zero) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int b = list[blockIdx.x];

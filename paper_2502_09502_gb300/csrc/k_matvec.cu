@@ -1,7 +1,7 @@
 // k_matvec.cu -- the two HBM-bound passes over X of a FISTA step, and their
 // FP64 twins for the certificate.
 //
-//  gradient pass  grad = X^T grad F(u_gamma)   (Algorithm 3, line 7)
+//  gradient pass  grad = X^T grad F(u_gamma)   (Algorithm 3's gradient step)
 //      prologue: u_gamma = (1+c) u^t - c u^{t-1} (linearity of X, no extra pass),
 //      r = grad F(u_gamma), and -F*(-zeta_gamma) with zeta_gamma = -r (Sec. 3.4).
 //      Tiles: 256 threads x (16-byte vector of columns) by 256 rows; each CTA
@@ -14,12 +14,12 @@
 //      ~1e-13 relative while X streams from HBM in its storage type.  u, r and
 //      grad are FP64.  (Plain Kahan in float is not enough: its lost roundings
 //      make the objective noisy at 1e-7 and the value-based restart chatter.)
-//  forward pass   u^{t+1} = X beta^{t+1}       (Algorithm 3, line 10)
+//  forward pass   u^{t+1} = X beta^{t+1}       (Algorithm 3's new iterate)
 //      sparse (nnz of beta^{t+1} <= p/2): the nonzero columns streamed from a
 //      column-major copy of X; dense: beta staged in shared memory, 4 rows per
 //      warp over row-major X.
 //      Epilogue: F(u^{t+1}) in FP64; the last CTA runs the fused restart /
-//      momentum / gap step (Algorithm 3, line 11; Sec. 4.2 stopping rule).
+//      momentum / gap step (Algorithm 3's restart test; Sec. 4.2 stopping rule).
 #include <type_traits>
 
 #include "ksc_common.cuh"
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
       if constexpr (MODE == kGStep) {
         d.grad[col] = s;
         const double b0 = bc[col];
-        const double w = b0 + c * (b0 - bpv[col]) - s * invL;   // Algorithm 3 lines 5, 7
+        const double w = b0 + c * (b0 - bpv[col]) - s * invL;   // extrapolation and gradient step (Algorithm 3)
         ((double*)d.wbuf)[col] = w;
         const bool fr = d.state == nullptr || d.state[col] == kFree;
         const unsigned kk = fr ? (__float_as_uint((float)w) & 0x7fffffffu) : 0u;
@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
 
 // ----------------------------------------------------------- step logic
 
-// Algorithm 3 line 10-11 plus the gap test of Sec. 4.2 and the incumbent rules
+// Algorithm 3's objective and restart test plus the gap test of Sec. 4.2 and the incumbent rules
 // of Sec. 4.3 (on the in-loop bound; the host confirms with the certificate).
 __device__ void step_logic(NodeDev* nd, double f) { fista_step_logic(nd, f); }
 
@@ -425,7 +425,7 @@ __device__ void finish_rows(const Dev& d, RowAcc a, double* red, int* s_last, in
       nd->sparse_steps += sparse ? 1 : 0;
       step_logic(nd, f);
     } else if (MODE == kFInit) {
-      const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // Algorithm 3 line 2
+      const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // initial objective (Algorithm 3)
       nd->Lcur = L1;
       nd->best_primal = L1;
       nd->best_dual = -INFINITY;

@@ -1,6 +1,6 @@
 // k_prox.cu -- per-node kernels built on the block prox (ksc_prox.cuh); the prox
 // of a FISTA step itself is spread over the GPU in k_prox_grid.cu.
-//   k_gvalue_init    g(beta^1) for the initial objective (Algorithm 3 line 2)
+//   k_gvalue_init    g(beta^1) for the initial objective (Algorithm 3)
 //   k_cert_final     FP64 G*(a) with its rounding margin, FP64 g(b^), the
 //                    certified bound and gap (Sec. 3.4)
 //   primitives       prox_{rho^-1 g}, g, g* on one vector (FP64)

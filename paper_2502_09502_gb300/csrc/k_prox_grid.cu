@@ -1,4 +1,4 @@
-// k_prox_grid.cu -- the prox of one FISTA step (Algorithm 3 line 8) spread over
+// k_prox_grid.cu -- the prox of one FISTA step (the proximal step of Algorithm 3) spread over
 // the GPU, and the Lanczos iteration that gives L.
 //
 // prox_{rho^-1 g}(w) = w - rho^-1 prox_{rho g*}(rho w) (Moreau, Sec. 3.3).  With the

@@ -491,7 +491,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   if (cur_dev != pr->device) KSC_CUDA(cudaSetDevice(pr->device));
   Dev& d = pr->dev;
   const int64_t p = pr->p;
-  // warm start projected on the node: S0 -> 0, clip to the box (reading of Alg. 3 line 1)
+  // warm start projected on the node: S0 -> 0, clip to the box (reading of Algorithm 3's start)
   std::vector<double> w0(p, 0.0);
   if (node->warm_beta)
     for (int64_t j = 0; j < p; ++j)

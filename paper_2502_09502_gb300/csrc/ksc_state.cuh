@@ -73,7 +73,7 @@ struct NodeDev {
 };
 
 // The restart, best-bound and termination logic closing one FISTA step
-// (Algorithm 3 lines 9-10, the gap test of Sec. 4.1, the early-termination rules
+// (Algorithm 3's objective and restart test, the gap test of Sec. 4.1, the early-termination rules
 // of Sec. 4.3), for any node record with these fields (NodeDev, BNode).
 // dL (optional): the change L^{t+1} - L^t evaluated as a difference (the batched
 // solver's cancellation-free form); otherwise the two values are compared.
