@@ -102,8 +102,13 @@ typedef struct {
   ksc_loss loss;
   int32_t x_on_device;
   double lipschitz;     /* > 0: the step constant L of Algorithm 3 to use.
-                           <= 0: L = c_f * lambda_max(X^T X) * 1.01, c_f = 2 (least
-                           squares) or 1/4 (logistic), lambda_max by power iteration */
+                           <= 0: L = c_f * theta * 1.01, c_f = 2 (least squares,
+                           squared hinge) or 1/4 (logistic), theta the largest Ritz
+                           value of Lanczos on X^T X, stopped when 8 further steps
+                           move it by at most 1e-5 of itself.  theta is a lower
+                           estimate of lambda_max, so L is an estimate, not a proven
+                           upper bound; L only changes the iteration's path, every
+                           reported bound is valid for any L                      */
   const float* col_scale; /* KSC_FP8_E4M3_COLSCALE: host pointer, p scales (copied);
                            NULL for the other types                                */
 } ksc_problem_desc;
@@ -260,8 +265,8 @@ ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* ou
 
 /* Allocation-free variant of ksc_prox_g on DEVICE buffers (the paper has no
  * counterpart: this is a deployment convenience).  For callers that must not call
- * cudaMalloc -- code issued during CUDA-graph capture, runtimes that manage all
- * device memory through their own pools, loops that cannot afford the implicit
+ * cudaMalloc -- runtimes that manage all device memory through their own pools
+ * and forbid allocations outside them, loops that cannot afford the implicit
  * synchronisation of an allocation.  w (p doubles), beta_out (p doubles) and
  * top_out (min(k, p) int32, or NULL) are device pointers owned by the caller; the
  * results equal ksc_prox_g's.  Work is enqueued on cuda_stream; the call returns
@@ -272,7 +277,10 @@ ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M, double* ou
  * scratch's device address and a kernel attribute): make it before any stream
  * capture.  All calls on a device share the scratch, so calls that may overlap on
  * the GPU (different streams without ordering) race; order them on one stream.
- * Non-finite entries of w give unspecified (but bounded-time) results. */
+ * A CUDA error already pending on the calling thread when the call is made (from
+ * the caller's earlier asynchronous work) is reported, and cleared, by this call
+ * as KSC_ERR_CUDA.  Non-finite entries of w give unspecified (but bounded-time)
+ * results. */
 ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, double rho,
                               double* beta_out, int32_t* top_out, void* cuda_stream);
 
@@ -288,7 +296,10 @@ ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, d
  * waiting.  No device memory is allocated (w is read in place); the first call
  * on a device does the one-time set-up of ksc_prox_g_noalloc.  Results agree with
  * ksc_prox_g to rounding (the two kernels order their FP64 sums differently).
- * Non-finite entries of w give unspecified (but bounded-time) results. */
+ * ldw and ldb above INT64_MAX / 8 / count are rejected (KSC_ERR_INVALID_ARG).  A
+ * CUDA error already pending on the calling thread is reported (and cleared) by
+ * this call as KSC_ERR_CUDA.  Non-finite entries of w give unspecified (but
+ * bounded-time) results. */
 ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* beta_out, int64_t ldb, int64_t p,
                             int32_t count, int32_t k, double M, double rho, void* cuda_stream);
 

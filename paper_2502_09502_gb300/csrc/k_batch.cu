@@ -560,12 +560,17 @@ __global__ void __launch_bounds__(kBProxBlock) k_bcert_final(BatchDev d, const i
 
 size_t bprox_smem_bytes(int wsm) { return seg_smem_bytes(kBatchCap, wsm, 8); }
 
-void batch_prepare(int optin) {
-  cudaFuncSetAttribute(k_bprox, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  // all of the unified L1 as shared memory: 4 node CTAs of ~50 KB per SM instead of 3
-  cudaFuncSetAttribute(k_bprox, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  cudaFuncSetAttribute(k_binit_node, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_bcert_final, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+cudaError_t batch_prepare(int optin) {
+  const cudaError_t steps[] = {
+      cudaFuncSetAttribute(k_bprox, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      // all of the unified L1 as shared memory: 4 node CTAs of ~50 KB per SM instead of 3
+      cudaFuncSetAttribute(k_bprox, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
+      cudaFuncSetAttribute(k_binit_node, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_bcert_final, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+  };
+  for (cudaError_t st : steps)
+    if (st != cudaSuccess) return st;
+  return cudaSuccess;
 }
 
 static int vec_blocks(int m) {

@@ -4,6 +4,8 @@
 //   k_cert_final     FP64 G*(a) with its rounding margin, FP64 g(b^), the
 //                    certified bound and gap (Sec. 3.4)
 //   primitives       prox_{rho^-1 g}, g, g* on one vector (FP64)
+#include <mutex>
+
 #include "ksc_common.cuh"
 #include "ksc_launch.h"
 #include "ksc_prox.cuh"
@@ -14,8 +16,8 @@ namespace ksc {
 // g* primitive shared memory: hist + scratch only
 constexpr int kDualCap = 16;
 
-void prox_grid_prepare(int optin);   // k_prox_grid.cu
-void batch_prepare(int optin);       // k_batch.cu
+cudaError_t prox_grid_prepare(int optin);   // k_prox_grid.cu
+cudaError_t batch_prepare(int optin);       // k_batch.cu
 
 template <typename T>
 __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
@@ -197,26 +199,49 @@ static size_t prox_bytes(int cap, int wsm, int tb) { return seg_smem_bytes(cap, 
 
 size_t prox_smem_bytes(const Dev& d) { return prox_bytes(kProxCap, d.prox_wsm, 8); }
 
-static size_t g_smem_max = 0;
+// per-device set-up state: kernel attributes are per device, so each device is
+// prepared once, under one lock shared by every entry point of the library
+constexpr int kMaxPrepDevices = 64;
+static std::mutex g_prep_mu;
+static bool g_prep_done[kMaxPrepDevices] = {};
+static size_t g_smem_max[kMaxPrepDevices] = {};
 
-void prox_prepare() {
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int optin = 0;
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  g_smem_max = (size_t)optin;
-  prox_grid_prepare(optin);
-  batch_prepare(optin);
-  cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+static int current_device() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxPrepDevices) return -1;
+  return dev;
 }
 
-size_t prox_smem_limit() { return g_smem_max; }
+cudaError_t prox_prepare() {
+  const int dev = current_device();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_prep_mu);
+  if (g_prep_done[dev]) return cudaSuccess;
+  int optin = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const cudaError_t steps[] = {
+      prox_grid_prepare(optin),
+      batch_prepare(optin),
+      cudaFuncSetAttribute(k_gvalue_init<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_cert_final<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_prox_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
+      cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+  };
+  for (cudaError_t st : steps)
+    if (st != cudaSuccess) return st;
+  g_smem_max[dev] = (size_t)optin;
+  g_prep_done[dev] = true;
+  return cudaSuccess;
+}
+
+size_t prox_smem_limit() {
+  const int dev = current_device();
+  return dev < 0 ? 0 : g_smem_max[dev];
+}
 
 void launch_gvalue_init(const Dev& d, cudaStream_t s) {
   const size_t bytes = prox_bytes(kProxCap, 0, 8);
@@ -237,7 +262,7 @@ void launch_prox_prim(const double* w, int p, int k, double M, double rho, doubl
   // keep w in shared memory when it fits beside the candidate buffers
   const size_t base = prox_bytes(kProxCap, 0, 8);
   int wsm = 0;
-  if (base + (size_t)p * 8 + 16 <= g_smem_max) wsm = p;
+  if (base + (size_t)p * 8 + 16 <= prox_smem_limit()) wsm = p;
   k_prox_prim<<<1, kProxBlock, prox_bytes(kProxCap, wsm, 8), s>>>(w, p, k, M, rho, beta, top, wbuf,
                                                                  wsm);
 }

@@ -827,9 +827,9 @@ __global__ void __launch_bounds__(kVecBlock) k_lz(Dev d, int it) {
 void launch_fwd_raw(const Dev& d, cudaStream_t s);   // k_matvec.cu
 void launch_grad_raw(const Dev& d, cudaStream_t s);
 
-void prox_grid_prepare(int optin) {
-  cudaFuncSetAttribute(k_prox_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(SelSmem) < optin ? (int)sizeof(SelSmem) : optin);
+cudaError_t prox_grid_prepare(int optin) {
+  return cudaFuncSetAttribute(k_prox_select, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sizeof(SelSmem) < optin ? (int)sizeof(SelSmem) : optin);
 }
 
 void launch_prox_select(const Dev& d, cudaStream_t s) {

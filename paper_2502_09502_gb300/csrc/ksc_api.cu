@@ -43,15 +43,10 @@ ksc_status ksc::api_fail(ksc_status st, const std::string& msg) { return fail(st
     }                                                                               \
   } while (0)
 
-static bool g_prepared = false;
-
+// per-device one-time set-up (k_prox.cu keeps the per-device state and its lock)
 ksc_status ksc::ensure_prepared() {
-  if (!g_prepared) {
-    prox_prepare();
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(KSC_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
-    g_prepared = true;
-  }
+  const cudaError_t e = prox_prepare();
+  if (e != cudaSuccess) return fail(KSC_ERR_CUDA, std::string("prepare: ") + cudaGetErrorString(e));
   return KSC_OK;
 }
 

@@ -107,7 +107,7 @@ struct BatchDev {
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }
 
 size_t bprox_smem_bytes(int wsm);
-void batch_prepare(int optin);
+cudaError_t batch_prepare(int optin);
 void launch_bresid(const BatchDev& d, cudaStream_t s);
 void launch_bprox(const BatchDev& d, cudaStream_t s);
 void launch_bstep(const BatchDev& d, cudaStream_t s);

@@ -132,8 +132,10 @@ void launch_split(const double* src, float* hi, float* lo, int n, cudaStream_t s
 void launch_colnorm(const Dev& d, cudaStream_t s);
 // column-major copy Xc of X
 void launch_transpose(const Dev& d, cudaStream_t s);
-// set the prox kernels' dynamic shared memory limits once per process
-void prox_prepare();
+// set the kernels' dynamic shared memory limits, once per device (the first call
+// on each device does it under a lock; later calls return at once); returns the
+// first failing CUDA call's error, and the device is set up again on the next call
+cudaError_t prox_prepare();
 
 // primitives (one CTA, FP64)
 // prox of g for `count` vectors (device rows with leading dims ldw, ldb), one CTA each

@@ -1,11 +1,11 @@
 // ksc_noalloc.cu -- the prox of g on device buffers with no device allocation at
 // all: ksc_prox_g_noalloc (one vector) and ksc_prox_g_batch (many vectors).
 //
-// Some callers cannot call cudaMalloc: code running while a CUDA graph is being
-// captured (cudaMalloc is not capturable), runtimes that own every byte of device
-// memory through their own pool and forbid outside allocations, and latency-
-// critical loops where an allocation's implicit device synchronisation is not
-// acceptable.  This entry point serves them: the caller passes device inputs and
+// Some callers cannot call cudaMalloc: runtimes that own every byte of device
+// memory through their own pool and forbid allocations behind their back (a
+// serving process that reserved the GPU's memory at start-up, a solver embedded
+// in another framework's allocator), and latency-critical loops where an
+// allocation's implicit device synchronisation is not acceptable.  This entry point serves them: the caller passes device inputs and
 // outputs, and the only scratch the kernel needs (the prox's copy of w when p is
 // too large for shared memory) lives in the fixed-size device array below, which
 // every GPU that loads the library holds until the process exits.
@@ -48,18 +48,20 @@ static void* prepare_device(ksc_status* st) {
   }
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_ready[dev]) {
-    cudaError_t e = cudaGetSymbolAddress(&g_scratch_ptr[dev], g_prox_scratch);
-    if (e != cudaSuccess) {
-      g_scratch_ptr[dev] = nullptr;
-      *st = ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
-      return nullptr;
-    }
-    ksc::prox_prepare();
-    e = cudaGetLastError();
+    // each call's own return code is checked, so an error left pending by the
+    // caller's earlier work does not fail (or repeat) this set-up
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_prox_scratch);
     if (e != cudaSuccess) {
       *st = ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
       return nullptr;
     }
+    e = ksc::prox_prepare();
+    if (e != cudaSuccess) {
+      *st = ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+      return nullptr;
+    }
+    g_scratch_ptr[dev] = ptr;
     g_ready[dev] = true;
   }
   return g_scratch_ptr[dev];
@@ -71,6 +73,9 @@ extern "C" ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* bet
   if (count > 0 && (!w || !beta_out)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "w and beta_out must be non-NULL");
   if (p < 1 || p > INT32_MAX) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "p must be in [1, 2^31)");
   if (ldw < p || ldb < p) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldw and ldb must be >= p");
+  // the byte spans below stay within int64: (count - 1) * ld + p <= count * ld <= INT64_MAX / 8
+  const int64_t ld_max = INT64_MAX / 8 / (count > 0 ? count : 1);
+  if (ldw > ld_max || ldb > ld_max) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldw or ldb too large");
   if (k < 0) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "k must be >= 0");
   if (!(M > 0) || !std::isfinite(M)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "M must be > 0");
   if (!(rho > 0) || !std::isfinite(rho)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "rho must be > 0");

@@ -100,6 +100,11 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
     assert fb(16, 4096, 1 << 20, 4096, 4096, 3, 2048, 1.0, 1.0, None) == ksc.KSC_ERR_UNIMPLEMENTED
     assert fb(4096, 8, 4096 + 64, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG   # overlap
     assert "overlap" in ksc.ksc_last_error()
+    # leading dimensions whose byte spans would overflow int64 are refused before
+    # the overlap test
+    assert fb(16, 1 << 61, 1 << 40, 8, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG
+    assert "too large" in ksc.ksc_last_error()
+    assert fb(16, 8, 1 << 40, 1 << 61, 8, 3, 2, 1.0, 1.0, None) == ksc.KSC_ERR_INVALID_ARG
     assert ksc.lib.ksc_problem_info(None, None, None) == ksc.KSC_ERR_INVALID_ARG
     assert ksc.lib.ksc_problem_bytes(None) == 0
     assert ksc.lib.ksc_problem_destroy(None) == ksc.KSC_OK
