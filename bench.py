@@ -85,9 +85,12 @@ def parse():
                     help="eig: also run branch and bound on a 4000 x 2000 least-squares instance with "
                          "perspective and with eigen-perspective node bounds, each within this time "
                          "limit (0: skip)")
-    ap.add_argument("--plain-nodes", type=int, default=16,
-                    help="batched: nodes of the same batch solved one at a time by the "
-                         "single-node solver for the comparison")
+    ap.add_argument("--plain-nodes", type=int, default=64,
+                    help="batched: nodes of the same batch (spread over k') solved one at a time by "
+                         "the single-node solver for the comparison")
+    ap.add_argument("--oracle-nodes", type=int, default=32,
+                    help="batched: nodes of the batch also solved by the FP64 oracle on the host "
+                         "cores (per-node rate and parity; 0: skip)")
     return ap.parse_args()
 
 
@@ -244,6 +247,10 @@ def run_ours(args, rank, world, dist):
                 nl, ms = K.ksc_problem_kernel_time(prob.h, kid)
                 stats["k"][kid][0] += nl
                 stats["k"][kid][1] += ms
+            for key, kid in (("sel", K.KSC_KERNEL_PROX_SELECT), ("app", K.KSC_KERNEL_PROX_APPLY)):
+                nl, ms = K.ksc_problem_kernel_time(prob.h, kid)
+                stats[key][0] += nl
+                stats[key][1] += ms
         prob.close()
         return r, t0
 
@@ -252,7 +259,7 @@ def run_ours(args, rank, world, dist):
         assert r.status == "ok" and r.rel_gap <= 1e-6, r
     stats = {"launches": 0, "pow": [], "iters": [], "sparse": [], "fallback": [], "pfast": [],
              "dfast": [],
-             "k": [[0, 0.0], [0, 0.0], [0, 0.0]]}
+             "k": [[0, 0.0], [0, 0.0], [0, 0.0]], "sel": [0, 0.0], "app": [0, 0.0]}
     lat = []
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[dev] if vis and len(vis.split(",")) > dev else str(dev)
@@ -333,6 +340,10 @@ def run_ours(args, rank, world, dist):
             "dual_predicted_steps_per_bound": float(np.mean(stats["dfast"])),
             "clocks": clk, "e2e": e2e, "gpu_launches": int(stats["launches"]),
             "kernel_time_share": shares,
+            "us_per_step": {name: round(1e3 * stats[key][1] / max(stats[key][0], 1), 2)
+                            for name, key in (("prox_select", "sel"), ("prox_apply", "app"))}
+                           | {"gradient": round(1e3 * grad_ms, 2),
+                              "forward": round(1e3 * stats["k"][2][1] / max(stats["k"][2][0], 1), 2)},
             "roofline": {"bound": "hbm", "kernel": "gradient pass X^T r (k_grad)",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "peak_kind": peak_kind, "frac": round(achieved / peak, 4),
@@ -340,6 +351,52 @@ def run_ours(args, rank, world, dist):
                          "avg_launch_ms": round(grad_ms, 5), "launches": nl},
         }
     return out, P, stats
+
+
+# ------------------------------------------------------------------ small FP64 configuration
+
+SMALL = dict(workload="single-node least squares FP64 X n=500 p=100 k=5 lambda2=1 M=2 toeplitz 0.5, "
+                      "5 x +-1, SNR 5, root node, rel gap 1e-6 (X fits in L2: latency-bound)",
+             n=500, p=100, k=5, lambda2=1.0, M=2.0, r=0.5, x_dtype="f64", loss="least_squares")
+
+
+def run_small(args, reps=20, samples=5):
+    """The FP64 parity configuration: time per certified bound on the GPU (problem
+    resident, L computed once), iterations, and the oracle's full solve on the same
+    inputs (median of `samples`), with the two bounds compared."""
+    import torch
+    import ksc_inputs as G
+    from oracle import oracle as O
+    from paper_2502_09502_gb300 import ksc as K
+    P = G.cfg_small_lsq(seed=args.seed)
+    stream = torch.cuda.Stream()
+    prob = K.Problem(P.X, P.y, K.KSC_LOSS_LSQ, stream=stream)
+    node = K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=100000)
+    for _ in range(3):
+        r = prob.solve(node, want_z=False)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    for _ in range(reps):
+        r = prob.solve(node, want_z=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall_ms = 1e3 * (time.perf_counter() - t0) / reps
+    dev_ms = ev0.elapsed_time(ev1) / reps
+    prob.close()
+    times = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        ref = O.solve(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, tol=1e-6, max_iter=100000)
+        times.append(time.perf_counter() - t0)
+    tight = O.solve(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, tol=1e-12, max_iter=200000)
+    return {"config": SMALL, "ms_per_bound": round(wall_ms, 3), "device_ms_per_bound": round(dev_ms, 3),
+            "bounds_per_s": round(1e3 / wall_ms, 1), "iters": r.iters, "rel_gap": r.rel_gap,
+            "oracle": {"ms_per_bound": round(1e3 * statistics.median(times), 2), "iters": ref.iters,
+                       "cores": 1, "samples": samples},
+            "dual_rel_diff_vs_oracle_1e-12": abs(r.dual_bound - tight.dual) / abs(tight.dual),
+            "bound_below_oracle_primal": bool(r.dual_bound <= tight.primal)}
 
 
 # ------------------------------------------------------------------ branch and bound
@@ -592,6 +649,70 @@ BATCHED = dict(workload="batched logistic BF16 X n=10000 p=5000 k=10 lambda2=0.0
                rel_gap=1e-6, l2="X (100 MB) and its column-major copy read by every step; no flush")
 
 
+_ORACLE_CASE = {}
+
+
+def _oracle_worker_init(seed, warm, L):
+    """Spawned worker: regenerate the batched workload from its seed (no GPU data)."""
+    import ksc_inputs as G
+    P = G.cfg_batched_logistic(seed=seed)
+    _ORACLE_CASE.update(P=P, X=P.X64(), warm=warm, L=L,
+                        sets=G.node_sets(P.p, 512, seed=seed, max_zero=200, max_one=9),
+                        pert=G.warm_perturbation(P.p, 512, seed=seed))
+
+
+def _oracle_node(b):
+    """One node of the batched workload solved by the FP64 oracle to a 1e-6 gap."""
+    from oracle import oracle as O
+    c = _ORACLE_CASE
+    P, (zero, one) = c["P"], c["sets"][b]
+    st = np.zeros(P.p, np.int8)
+    st[zero] = O.ZERO
+    st[one] = O.ONE
+    t0 = time.perf_counter()
+    r = O.solve(c["X"], P.y, P.loss, P.lambda2, P.M, P.k, state=st, warm=c["warm"] + c["pert"][b],
+                L=c["L"], tol=1e-6, max_iter=100000)
+    return b, r.dual, r.primal, r.iters, r.status, time.perf_counter() - t0
+
+
+def oracle_subsample(seed, count, gpu_res):
+    """The FP64 oracle on a seeded subsample of the batched workload's nodes: its own
+    root solve (all cores) for the warm starts, then the nodes in parallel worker
+    processes (one core each), giving a per-node rate on the host and the parity of
+    the GPU's certified bounds on those nodes."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    import ksc_inputs as G
+    from oracle import oracle as O
+    P = G.cfg_batched_logistic(seed=seed)
+    idx = np.sort(np.argsort(G.uniform(seed, 12, len(gpu_res)))[:count])
+    t0 = time.perf_counter()
+    X = P.X64()
+    # L (any valid step constant; it only changes the path): power iteration to 1e-8
+    # with the 1.01 factor of the GPU path, c_f = 1/4 for logistic
+    L = 0.25 * O.power_iteration(X, tol=1e-8, openmp=True)[0] * 1.01
+    root = O.solve(X, P.y, P.loss, P.lambda2, P.M, P.k, L=L, tol=1e-6, max_iter=100000, openmp=True)
+    del X
+    t_root = time.perf_counter() - t0
+    workers = max(1, min(count, os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_worker_init, initargs=(seed, root.beta, L)) as pool:
+        out = list(pool.map(_oracle_node, [int(b) for b in idx]))
+    wall = time.perf_counter() - t0
+    rel = [abs(gpu_res[b].dual_bound - d) / abs(d) for b, d, _, _, _, _ in out]
+    return {"nodes": int(count), "indices": [int(b) for b in idx], "workers": workers,
+            "cpu": host_cpu()["model"],
+            "bounds_per_s_all_cores": round(count / wall, 4),
+            "s_per_node_one_core_mean": round(float(np.mean([x[5] for x in out])), 2),
+            "oracle_iters_mean": round(float(np.mean([x[3] for x in out])), 1),
+            "oracle_root_s": round(t_root, 1),
+            "converged": sum(x[4] == "converged" for x in out),
+            "max_rel_dual_diff": float(max(rel)),
+            "gpu_bound_le_oracle_primal": bool(all(gpu_res[b].dual_bound <= pr for b, _, pr, _, _, _ in out)),
+            "note": "oracle and GPU both at a 1e-6 gap from their own root solutions + the same perturbations"}
+
+
 def run_batched(args):
     """One step = one ksc_solve_batch call over `nodes` nodes of the batched logistic
     workload (X resident; L computed once at problem creation)."""
@@ -653,26 +774,76 @@ def run_batched(args):
     K.ksc_problem_profile(prob.h, False)
     tot = sum(v[1] for v in kt.values())
     shares = {k: round(v[1] / max(tot, 1e-9), 4) for k, v in kt.items()}
-    # tensor roofline of the X^T r product: algorithmic flops 2 n p per running node
-    # per step (tiles whose nodes have all stopped are skipped), over its device time
-    nl, gms = kt["xt_r"]
+    # rooflines.  Tensor products: algorithmic flops 2 n p per running node per
+    # step (tiles whose nodes have all stopped are skipped) over the product's
+    # device time, against the sustained BF16 peak (the products run inside a long
+    # call).  Exact double-float products of anchors and certificates (k_dfprod):
+    # n p multiply-adds per node and product, two products per anchor (X b_ref,
+    # X^T r_ref) and per certificate (X b^, X^T zeta), against the FP32 FMA rate
+    # 152 SMs x 128 lanes x the median SM clock sampled during the timed calls.
     node_steps = float(sum(r.iters for r in pres))
     alg = 2.0 * n * p * node_steps
-    achieved = alg / (gms / 1e3) / 1e12
     try:
         pk = json.load(open(PEAKS_FILE))
-        peak, peak_kind = float(pk["bf16_tflops"]), "measured"
+        peak, peak_kind = float(pk["bf16_tflops_sustained"]), "measured (sustained)"
     except Exception:
-        peak, peak_kind = 1900.0, "fallback"
-    # the plain single-node solver on the same nodes, one at a time
-    sub = nodes[:args.plain_nodes]
-    prob.solve(nodes[-1], want_beta=False, want_z=False)   # untimed: the single-node graph and its buffers
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for nd in sub:
-        r = prob.solve(nd, want_beta=False, want_z=False)
-        assert r.status == "ok" or r.pruned, r
-    plain = len(sub) / (time.perf_counter() - t0)
+        peak, peak_kind = 1700.0, "fallback (sustained)"
+
+    def tensor_line(key, label):
+        nl_, ms_ = kt[key]
+        ach = alg / (ms_ / 1e3) / 1e12
+        return {"bound": "tensor", "kernel": label, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+                "peak_kind": peak_kind, "frac": round(ach / peak, 4), "traffic": None,
+                "flops_per_launch": alg / max(nl_, 1), "pieces": 3, "node_steps": node_steps,
+                "avg_launch_ms": round(ms_ / max(nl_, 1), 5), "launches": nl_}
+
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fma_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # T multiply-adds/s
+    exact_products = 2.0 * (bstats["batch_certificates"] + bstats["batch_anchors"])
+    macs = exact_products * n * p
+    ex_ms = kt["certificates"][1] + kt["anchors"][1]
+    ex_ach = macs / (ex_ms / 1e3) / 1e12
+    exact_line = {"bound": "alu", "kernel": "exact double-float products of anchors and certificates "
+                                            "(k_dfprod; the anchor and certificate phases' device time)",
+                  "achieved": round(ex_ach, 3), "peak": round(fma_peak, 2), "unit": "T multiply-adds/s",
+                  "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median sampled)",
+                  "frac": round(ex_ach / fma_peak, 4), "traffic": None, "products": exact_products,
+                  "multiply_adds": macs, "device_ms": round(ex_ms, 2)}
+    rooflines = {"xt_r": tensor_line("xt_r", "X^T r for the running nodes (k_tcgemm, 3 BF16 pieces)"),
+                 "x_dbeta": tensor_line("x_dbeta", "X (beta - beta_ref) for the running nodes (k_tcgemm, 3 BF16 pieces)"),
+                 "exact_products": exact_line}
+    phase_ms = {"exact_products": ex_ms, "xt_r": kt["xt_r"][1], "x_dbeta": kt["x_dbeta"][1]}
+    dominant = max(phase_ms, key=phase_ms.get)
+
+    # the plain single-node solver on a sample of the same nodes spread over the
+    # budgets k' (every (B / plain)-th node in order of k'), one at a time: on an
+    # FP32 copy of X (the same represented matrix: BF16 widens exactly), the solver
+    # the metric compares against, and on the BF16 X itself
+    order = sorted(range(B), key=lambda b: (len(sets[b][1]), b))
+    take = max(1, min(args.plain_nodes, B))
+    sample = [order[int(i * B / take)] for i in range(take)]
+
+    def plain_rate(pr):
+        pr.solve(nodes[sample[0]], want_beta=False, want_z=False)   # untimed: graph and buffers
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for b in sample:
+            r = pr.solve(nodes[b], want_beta=False, want_z=False)
+            assert r.status == "ok" or r.pruned, r
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return len(sample) / (e0.elapsed_time(e1) / 1e3), len(sample) / wall
+
+    X32 = Xd.float()
+    prob32 = K.Problem(X32, P.y, loss, stream=stream)
+    plain32, plain32_wall = plain_rate(prob32)
+    prob32.close()
+    del X32
+    plain16, plain16_wall = plain_rate(prob)
+    plain = plain32
     # end to end: X from pinned host memory into a new problem, the batched call, results back
     Xh = torch.from_numpy(P.X.view(np.int16)).pin_memory()
     torch.cuda.synchronize()
@@ -699,17 +870,20 @@ def run_batched(args):
         "anchors_per_call": bstats["batch_anchors"],
         "prox_fallbacks_per_call": bstats["prox_fallback"],
         "device_ms_per_call": {k: round(v[1], 2) for k, v in kt.items()},
-        "plain_single_node": {"value": round(plain, 3), "unit": UNIT, "nodes": len(sub),
-                              "ratio": round(value / plain, 2)},
+        "plain_single_node": {"value": round(plain32, 3), "unit": UNIT, "x_dtype": "f32", "nodes": len(sample),
+                              "ratio": round(value / plain32, 2), "wall_value": round(plain32_wall, 3),
+                              "sample": "every (512/nodes)-th node in order of k' = k - |S1|, CUDA events"},
+        "plain_single_node_bf16": {"value": round(plain16, 3), "unit": UNIT, "x_dtype": "bf16",
+                                   "nodes": len(sample), "ratio": round(value / plain16, 2),
+                                   "wall_value": round(plain16_wall, 3)},
         "clocks": clk, "gpu_launches": int(launches), "kernel_time_share": shares,
         "e2e": {"value": round(B / e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
                 "d2h_bytes_per_step": int(B * (p * 8 + 64))},
-        "roofline": {"bound": "tensor", "kernel": "X^T r for the running nodes (k_tcgemm, 3 BF16 pieces)",
-                     "achieved": round(achieved, 1), "peak": peak, "unit": "TFLOP/s",
-                     "peak_kind": peak_kind, "frac": round(achieved / peak, 4), "traffic": None,
-                     "flops_per_launch": alg / max(nl, 1), "pieces": 3,
-                     "node_steps": node_steps, "avg_launch_ms": round(gms / max(nl, 1), 5), "launches": nl},
+        "roofline": dict(rooflines[dominant], dominant_of=sorted(phase_ms)),
+        "rooflines": rooflines,
     }
+    if args.oracle_nodes > 0:
+        line["oracle_subsample"] = oracle_subsample(args.seed, args.oracle_nodes, res)
     return line
 
 
@@ -794,30 +968,78 @@ def run_eig(args):
 
 # ------------------------------------------------------------------ oracle timing
 
-def time_oracle_sample(P, stats_iters=None, stats_pow=None):
+def host_cpu():
+    """The host's CPU model and logical core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"model": model, "nproc": os.cpu_count()}
+
+
+def time_oracle_sample(P, openmp=False):
     """The FP64 oracle on the same workload, on a bounded sample: one power-iteration
-    step (2 passes over X) and one FISTA step of Algorithm 3 (oracle: X gamma, X^T r,
-    the primal X beta, the bound's X beta and X^T zeta), extrapolated to a full bound
-    with the iteration counts of a full solve."""
+    step (2 passes over X) and one step of Algorithm 3 including its set-up (oracle:
+    the initial X beta, then X gamma, X^T r, X beta and the bound's X^T zeta)."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    O.power_iteration(P.X, tol=0.0, max_iter=1)
+    O.power_iteration(P.X, tol=0.0, max_iter=1, openmp=openmp)
     t_pow = time.perf_counter() - t0
     L = 2.0 * float(np.sum(P.X.astype(np.float64) ** 2))   # cheap valid step for timing only
     t0 = time.perf_counter()
-    O.solve(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, L=L, tol=0.0, max_iter=1)
+    O.solve(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, L=L, tol=0.0, max_iter=1, openmp=openmp)
     t_iter = time.perf_counter() - t0
     return t_pow, t_iter
 
 
-def cpu_baseline(P, iters, pows):
-    t_pow, t_iter = time_oracle_sample(P)
-    per_bound = pows * t_pow + iters * t_iter
-    return {"value": 1.0 / per_bound, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"1 power-iteration step ({t_pow:.2f} s) and 1 FISTA step incl. setup "
-                       f"({t_iter:.2f} s) of the FP64 oracle on the full workload, "
-                       f"extrapolated to {pows:.0f} matrix-vector pairs for L + {iters:.0f} "
-                       f"FISTA steps per bound (the counts of the full GPU solve)")}
+def oracle_rate(P, iters, pows, samples=5, openmp=False):
+    """Median over `samples` bounded samples of the seconds per bound, extrapolated
+    to `pows` power-iteration steps and `iters` steps of Algorithm 3."""
+    from oracle import oracle as O
+    per = []
+    for _ in range(samples):
+        t_pow, t_iter = time_oracle_sample(P, openmp=openmp)
+        per.append((pows * t_pow + iters * t_iter, t_pow, t_iter))
+    per.sort()
+    med = per[len(per) // 2]
+    return {"bounds_per_s": 1.0 / med[0], "s_per_bound": med[0], "power_step_s": med[1],
+            "fista_step_s": med[2], "threads": O.threads(openmp), "samples": samples}
+
+
+def cpu_baseline(P, iters, pows, samples=5):
+    """The oracle as it stands on the host cores: single-threaded and with its
+    matrix-vector products on every core (OpenMP build, identical results), each the
+    median of `samples` bounded samples extrapolated to a full bound."""
+    one = oracle_rate(P, iters, pows, samples, openmp=False)
+    try:
+        allc = oracle_rate(P, iters, pows, samples, openmp=True)
+    except Exception as e:          # no OpenMP runtime on the host
+        allc = None
+        err = str(e)
+    best = allc if allc else one
+    cpu = host_cpu()
+    out = {"value": best["bounds_per_s"], "unit": UNIT, "cores": best["threads"], "kind": "oracle",
+           "cpu": cpu["model"], "nproc": cpu["nproc"],
+           "single_thread": {"value": one["bounds_per_s"], "power_step_s": round(one["power_step_s"], 3),
+                             "fista_step_s": round(one["fista_step_s"], 3)},
+           "all_cores": None if allc is None else {
+               "value": allc["bounds_per_s"], "threads": allc["threads"],
+               "power_step_s": round(allc["power_step_s"], 3), "fista_step_s": round(allc["fista_step_s"], 3)},
+           "sample": (f"median of {samples} samples, each 1 power-iteration step and 1 step of Algorithm 3 "
+                      f"(with its set-up) of the FP64 oracle on the full workload, extrapolated to "
+                      f"{pows:.0f} matrix-vector pairs for L + {iters:.0f} steps per bound (the counts "
+                      f"of the full GPU solve); value = the all-cores figure")}
+    if allc is None:
+        out["all_cores_error"] = err
+    return out
 
 
 # iteration counts of a full solve of this workload (matrix-vector pairs for L, FISTA
@@ -827,25 +1049,40 @@ FULL_SOLVE_COUNTS = {"pow": 64, "iters": 350}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores (all-cores build), each
+    step one bounded sample of the same workload, extrapolated to a full bound."""
+    from oracle import oracle as O
     P = make_problem(args)
-    per_step = []
     cnt = FULL_SOLVE_COUNTS
+    try:
+        O.build(openmp=True)
+        openmp = True
+    except Exception:
+        openmp = False
+    per_step, wall = [], 0.0
     for s in range(args.warmup + args.steps):
-        t_pow, t_iter = time_oracle_sample(P)
+        t0 = time.perf_counter()
+        t_pow, t_iter = time_oracle_sample(P, openmp=openmp)
         if s >= args.warmup:
+            wall += time.perf_counter() - t0
             per_step.append(cnt["pow"] * t_pow + cnt["iters"] * t_iter)
-    total = sum(per_step)
-    value = args.steps / total
+    per_bound = statistics.median(per_step)
+    value = 1.0 / per_bound
+    cpu = host_cpu()
     line = {
         "impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT,
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+        "ms_per_step": round(1e3 * wall / args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(WORKLOAD, parallelism="host cores"),
-        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"per step: 1 power-iteration step + 1 FISTA step of the FP64 "
-                                   f"oracle on the full workload, extrapolated to "
-                                   f"{cnt['pow']} power iterations + {cnt['iters']} FISTA steps"},
+        "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": O.threads(openmp), "kind": "oracle",
+                         "cpu": cpu["model"], "nproc": cpu["nproc"],
+                         "s_per_bound_extrapolated": round(per_bound, 1),
+                         "sample": f"each step: 1 power-iteration step + 1 step of Algorithm 3 of the FP64 "
+                                   f"oracle on the full workload ({'all cores' if openmp else '1 core'}); "
+                                   f"value = 1 / the median over steps of the time extrapolated to "
+                                   f"{cnt['pow']} power iterations + {cnt['iters']} steps per bound; "
+                                   f"ms_per_step is the measured time of one sampled step"},
         "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -879,6 +1116,8 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline(P, float(np.mean(stats["iters"])),
                                                float(np.mean(stats["pow"])))
+        if world == 1 and not args.small:
+            out["small_fp64"] = run_small(args)
         if not args.no_batched and world == 1 and not args.small:
             # the batched mixed-precision form on its own workload, timed the same
             # way, beside the plain single-node solver on the same nodes
@@ -886,8 +1125,12 @@ def main():
             b = run_batched(args)
             out["batched"] = {k: b[k] for k in (
                 "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "latency_ms",
-                "iters_per_bound", "plain_single_node", "e2e", "roofline", "device_ms_per_call",
-                "clocks", "gpu_launches")}
+                "iters_per_bound", "plain_single_node", "plain_single_node_bf16", "e2e", "roofline",
+                "rooflines", "device_ms_per_call", "clocks", "gpu_launches", "certificates_per_call",
+                "anchors_per_call", "prox_fallbacks_per_call", "lockstep_steps_per_call")
+                if k in b}
+            if "oracle_subsample" in b:
+                out["batched"]["oracle_subsample"] = b["oracle_subsample"]
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

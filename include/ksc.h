@@ -380,6 +380,9 @@ ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, int32_t m_pa
 #define KSC_KERNEL_B_STEP   7   /* restart / gap step per node                       */
 #define KSC_KERNEL_B_CERT   8   /* FP64 certificates between replays (per node)       */
 #define KSC_KERNEL_B_ANCHOR 9   /* exact anchor products between replays (per node)   */
+/* the two kernels of KSC_KERNEL_PROX (single-node solves), timed separately:   */
+#define KSC_KERNEL_PROX_SELECT 10 /* threshold: top-k' select, candidate sort, root */
+#define KSC_KERNEL_PROX_APPLY  11 /* output pass, nonzero list, g (grid-wide)       */
 /* Enable (1) or disable (0) CUDA-event timing of each kernel launch of the
  * problem's solves; accumulated totals are read with ksc_problem_kernel_time. */
 ksc_status ksc_problem_profile(ksc_problem* problem, int32_t enable);

@@ -46,6 +46,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ---------------------------------------------------------------- Huber */
 
@@ -372,8 +375,20 @@ static double xat(const void *X, int xdt, int64_t ldx, int64_t i, int64_t j) {
   return ((const double *)X)[i * ldx + j];
 }
 
+/* Threads of the all-cores build (-fopenmp): the rows of X v, and blocks of
+ * columns of X^T r, are independent; every output element is summed in the same
+ * order as in the single-threaded build, so both builds give identical results. */
+int kso_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 void kso_matvec(const void *X, int xdt, int64_t n, int64_t p, int64_t ldx,
                 const double *v, double *out) {
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t j = 0; j < p; ++j) s += xat(X, xdt, ldx, i, j) * v[j];
@@ -383,9 +398,14 @@ void kso_matvec(const void *X, int xdt, int64_t n, int64_t p, int64_t ldx,
 
 void kso_rmatvec(const void *X, int xdt, int64_t n, int64_t p, int64_t ldx,
                  const double *r, double *out) {
-  for (int64_t j = 0; j < p; ++j) out[j] = 0.0;
-  for (int64_t i = 0; i < n; ++i)
-    for (int64_t j = 0; j < p; ++j) out[j] += xat(X, xdt, ldx, i, j) * r[i];
+  /* out[j] = sum_i X[i][j] r[i], i ascending, one block of 256 columns at a time */
+#pragma omp parallel for schedule(static)
+  for (int64_t j0 = 0; j0 < p; j0 += 256) {
+    const int64_t j1 = (j0 + 256 < p) ? j0 + 256 : p;
+    for (int64_t j = j0; j < j1; ++j) out[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t j = j0; j < j1; ++j) out[j] += xat(X, xdt, ldx, i, j) * r[i];
+  }
 }
 
 double kso_power_iteration(const void *X, int xdt, int64_t n, int64_t p, int64_t ldx,

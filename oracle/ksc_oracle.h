@@ -81,6 +81,9 @@ double kso_loss(int loss, const double *u, const double *y, int64_t n);
 void kso_loss_grad(int loss, const double *u, const double *y, int64_t n, double *grad);
 double kso_neg_conj(int loss, const double *zeta, const double *y, int64_t n);
 
+/* Threads the matrix-vector products use: 1, or OpenMP's count in the build made
+ * with -fopenmp (the all-cores timing of the benchmark's CPU baseline). */
+int kso_threads(void);
 /* Row-major X (n x p, leading dimension ldx) in FP64 or FP32 (promoted exactly). */
 void kso_matvec(const void *X, int xdt, int64_t n, int64_t p, int64_t ldx,
                 const double *v, double *out);               /* out = X v   */

@@ -18,6 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ksc_oracle.c")
 _HDR = os.path.join(_HERE, "ksc_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "libksc_oracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "libksc_oracle_omp.so")
 
 LOSS_LSQ, LOSS_LOGISTIC = 0, 1
 FREE, ZERO, ONE = 0, 1, 2
@@ -26,25 +27,42 @@ STATUS = {0: "converged", 1: "max_iter", 2: "pruned", 3: "primal_below", 4: "inf
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2, no FP contraction so that x86 and Arm agree)."""
-    stale = not os.path.exists(_OUT) or any(
-        os.path.getmtime(s) > os.path.getmtime(_OUT) for s in (_SRC, _HDR))
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle (plain C, -O2, no FP contraction so that x86 and Arm agree).
+    openmp=True: the all-cores build (-fopenmp), identical results, used only to
+    time the CPU baseline on every host core."""
+    out = _OUT_OMP if openmp else _OUT
+    stale = not os.path.exists(out) or any(
+        os.path.getmtime(s) > os.path.getmtime(out) for s in (_SRC, _HDR))
     if force or stale:
-        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-        tmp = _OUT + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
-                               "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _OUT)
-    return _OUT
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared"]
+                              + (["-fopenmp"] if openmp else []) + ["-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+_lib_omp = None
+
+
+def lib(openmp: bool = False):
+    """The single-threaded oracle library (default) or its all-cores build."""
+    global _lib, _lib_omp
+    if openmp:
+        if _lib_omp is None:
+            _lib_omp = C.CDLL(build(openmp=True))
+            _declare(_lib_omp)
+        return _lib_omp
     if _lib is None:
         _lib = C.CDLL(build())
         _declare(_lib)
     return _lib
+
+
+def threads(openmp: bool = False) -> int:
+    """Threads the oracle's matrix-vector products run on."""
+    return int(lib(openmp).kso_threads())
 
 
 _dp = C.POINTER(C.c_double)
@@ -68,6 +86,8 @@ class SolveOut(C.Structure):
 
 
 def _declare(L):
+    L.kso_threads.restype = C.c_int
+    L.kso_threads.argtypes = []
     L.kso_huber.restype = C.c_double
     L.kso_huber.argtypes = [C.c_double, C.c_double]
     L.kso_huber_prox.restype = C.c_double
@@ -229,10 +249,10 @@ def rmatvec(X, r):
     return out
 
 
-def power_iteration(X, tol=1e-10, max_iter=10000):
+def power_iteration(X, tol=1e-10, max_iter=10000, openmp=False):
     X, dt = _xptr(X)
     it = C.c_int64(0)
-    lam = lib().kso_power_iteration(X.ctypes.data, dt, X.shape[0], X.shape[1], X.shape[1],
+    lam = lib(openmp).kso_power_iteration(X.ctypes.data, dt, X.shape[0], X.shape[1], X.shape[1],
                                     float(tol), int(max_iter), C.byref(it))
     return lam, it.value
 
@@ -277,7 +297,7 @@ class _Args:
 
 def solve(X, y, loss_kind, lambda2, M, k, state=None, warm=None, L=0.0, tol=1e-12,
           max_iter=100000, restart=True, momentum=True, incumbent=float("inf"),
-          want_trace=False, eig=0.0):
+          want_trace=False, eig=0.0, openmp=False):
     """Restarted FISTA (Algorithm 3) on the node problem, in FP64; eig > 0: the
     eigen-perspective relaxation of App. D.2 with Q = X^T X - eig I."""
     a = _Args(X, y, loss_kind, lambda2, M, k, state, warm, L, tol, max_iter, restart,
@@ -286,7 +306,7 @@ def solve(X, y, loss_kind, lambda2, M, k, state=None, warm=None, L=0.0, tol=1e-1
     z = np.zeros(a.p)
     trace = np.zeros(2 * max_iter) if want_trace else None
     out = SolveOut()
-    lib().kso_solve(C.byref(a.c), beta.ctypes.data_as(_dp), z.ctypes.data_as(_dp),
+    lib(openmp).kso_solve(C.byref(a.c), beta.ctypes.data_as(_dp), z.ctypes.data_as(_dp),
                     trace.ctypes.data_as(_dp) if want_trace else None, C.byref(out))
     tr = trace[:2 * out.iters].reshape(-1, 2) if want_trace else None
     return SolveResult(beta, z, out.primal, out.dual, out.gap, out.L, out.iters, out.restarts,

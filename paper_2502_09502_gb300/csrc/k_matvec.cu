@@ -793,11 +793,12 @@ static void step_impl(const Dev& d, cudaStream_t s, cudaEvent_t* ev) {
   Launch<TX, T>::template grad<kGStep>(d, s);
   if (ev) cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal);
   launch_prox_select(d, s);
-  launch_prox_apply(d, s);
   if (ev) cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal);
+  launch_prox_apply(d, s);
+  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
   Launch<TX, T>::template fwd_col<kFStep>(d, s);   // sparse iterate (one of the two runs)
   Launch<TX, T>::template fwd<kFStep>(d, s);       // dense iterate
-  if (ev) cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal);
+  if (ev) cudaEventRecordWithFlags(ev[4], s, cudaEventRecordExternal);
 }
 
 // The iterate (beta, u, grad) is FP64 for every storage type of X: FP32 iterates

@@ -371,7 +371,7 @@ static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof) {
   cudaGraphExec_t* slot = prof ? &pr->graph_prof : &pr->graph;
   if (*slot) return KSC_OK;
   if (prof && pr->events.empty()) {
-    pr->events.resize(4 * kStepsPerGraph);
+    pr->events.resize(kEventsPerStep * kStepsPerGraph);
     for (auto& e : pr->events) KSC_CUDA(cudaEventCreate(&e));
   }
   // capture on a private stream (legacy default stream cannot be captured)
@@ -380,7 +380,7 @@ static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int k = 0; k < kStepsPerGraph; ++k) launch_step(pr->dev, cs, prof ? &pr->events[4 * k] : nullptr);
+    for (int k = 0; k < kStepsPerGraph; ++k) launch_step(pr->dev, cs, prof ? &pr->events[kEventsPerStep * k] : nullptr);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(slot, g, 0);
@@ -448,12 +448,19 @@ static ksc_status replay(ksc_problem* pr, cudaStream_t s, NodeDev* h) {
   KSC_CUDA(cudaStreamSynchronize(s));
   if (prof) {
     const int steps = std::min(kStepsPerGraph, h->iter - before);
+    // events of a step: before the gradient, before the prox's select and apply
+    // kernels, before the forward pass, after it
+    struct Span { int id, from, to; };
+    static constexpr Span spans[] = {{KSC_KERNEL_GRADIENT, 0, 1}, {KSC_KERNEL_PROX, 1, 3},
+                                     {KSC_KERNEL_PROX_SELECT, 1, 2}, {KSC_KERNEL_PROX_APPLY, 2, 3},
+                                     {KSC_KERNEL_FORWARD, 3, 4}};
     for (int k = 0; k < steps; ++k) {
-      for (int j = 0; j < 3; ++j) {   // gradient, prox (select + apply), forward
+      for (const Span& sp : spans) {
         float ms = 0.f;
-        KSC_CUDA(cudaEventElapsedTime(&ms, pr->events[4 * k + j], pr->events[4 * k + j + 1]));
-        pr->k_ms[j] += ms;
-        pr->k_launches[j] += 1;
+        KSC_CUDA(cudaEventElapsedTime(&ms, pr->events[kEventsPerStep * k + sp.from],
+                                      pr->events[kEventsPerStep * k + sp.to]));
+        pr->k_ms[sp.id] += ms;
+        pr->k_launches[sp.id] += 1;
       }
     }
   }

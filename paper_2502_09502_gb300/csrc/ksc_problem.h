@@ -19,7 +19,8 @@ void free_batch(BatchWs* ws);
 
 static constexpr int kStepsPerGraph = 16;
 static constexpr int kEigMaxP = 8192;   // largest p of the eigen shift's Cholesky test
-static constexpr int kKernelIds = 10;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
+static constexpr int kKernelIds = 12;   // KSC_KERNEL_* ids of ksc_problem_kernel_time
+static constexpr int kEventsPerStep = 5;  // profiling events around the kernels of one FISTA step
 
 struct ksc_problem {
   int device = 0;

@@ -30,6 +30,7 @@ KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 KSC_KERNEL_B_RESID, KSC_KERNEL_B_GRAD, KSC_KERNEL_B_PROX, KSC_KERNEL_B_FWD, KSC_KERNEL_B_STEP = (
     3, 4, 5, 6, 7)
 KSC_KERNEL_B_CERT, KSC_KERNEL_B_ANCHOR = 8, 9
+KSC_KERNEL_PROX_SELECT, KSC_KERNEL_PROX_APPLY = 10, 11
 
 # every symbol include/ksc.h declares
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
