@@ -366,6 +366,22 @@ ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, int32_t m_pa
                           const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd, int32_t tile_n,
                           int32_t grid, void* cuda_stream);
 
+/* The exact product of the batched solver's anchors and certificates (Sec. 3.4:
+ * the bound needs X^T zeta to a known accuracy) on the tensor cores, on DEVICE
+ * buffers owned by the caller, exported so that tests can check it on its own:
+ *   D[i][j] = sum_l A[j][l] V[i][l],   i < r, j < c,
+ * A BF16 (c x k, row stride lda elements: X for X v, the transpose of X for
+ * X^T v), V FP64 (r x k, row stride ldv), D FP64 (r x c, row stride ldd).  Both
+ * operands are split into 8-bit fixed-point slices (one exponent per row of A and
+ * per vector), every slice product is summed exactly, and
+ *   |D[i][j] - exact| <= eps ||A_j||_2 ||V_i||_2,
+ * eps written to *err_factor (optional; about 1e-12 for k = 10^4).  r <= 1024.
+ * Allocates and frees its slices; blocks until done.  KSC_ERR_INVALID_ARG on
+ * NULL pointers or bad sizes, KSC_ERR_OOM, KSC_ERR_CUDA, KSC_ERR_TIMEOUT when a
+ * device wait gave up. */
+ksc_status ksc_tc_exact(const void* A, int32_t c, int32_t k, int64_t lda, const double* V, int32_t r,
+                        int64_t ldv, double* D, int64_t ldd, double* err_factor, void* cuda_stream);
+
 /* ---- profiling ------------------------------------------------------------ */
 
 /* Kernel ids for ksc_problem_kernel_time. */

@@ -18,6 +18,7 @@ constexpr int kDualCap = 16;
 
 cudaError_t prox_grid_prepare(int optin);   // k_prox_grid.cu
 cudaError_t batch_prepare(int optin);       // k_batch.cu
+cudaError_t tcx_prepare();                  // k_tcexact.cu
 
 template <typename T>
 __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
@@ -230,6 +231,7 @@ cudaError_t prox_prepare() {
       cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
       cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
       cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      tcx_prepare(),
   };
   for (cudaError_t st : steps)
     if (st != cudaSuccess) return st;

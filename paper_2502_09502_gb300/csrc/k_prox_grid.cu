@@ -41,6 +41,14 @@ struct SelSmem {
   double pref[kProxCap + 1];
   double tb[kProxCap];
   int cidx[kProxCap];
+  unsigned long long tkey[kProxCap];   // the top set (and its ties), sorted in Alg. 1 order
+  int tidx[kProxCap];
+  double rsum[2];
+  int rcnt[2 + 16];
+  double rt[2];                  // root search: result, and the scalars below
+  unsigned long long rtb[2];     // bit patterns of the point t and of t + min(rho t, M)
+  int rflag[2];                  // done, pooled count
+  double cs[2];                  // per-call scalars computed once: rho / (1 + rho), 1 / (2 lambda2)
   double root[2];
   int flag[2];
 };
@@ -286,48 +294,267 @@ __device__ __forceinline__ bool in_top(unsigned kk, double a, int i, unsigned th
   return bnd_a < 0.0 || a > bnd_a || (a == bnd_a && i <= bnd_i);
 }
 
-// bracketed Newton on Phi over full passes of w (pooled blocks wider than the
-// candidate capacity); hi0 has Phi(hi0) > 0
-__device__ double root_fullpass_global(const Dev& d, SelSmem& sm, int q, unsigned thr, double bnd_a,
-                                       int bnd_i, double hi0, double rho, double M) {
-  const int p = d.p;
-  const double* w = (const double*)d.wbuf;
-  double lo = 0.0, hi = hi0, th = hi0;
+// Two counts and two FP64 sums over the block.  FP64 issues at 1/64 of the FP32
+// rate here, so every thread's sums go through shared memory to one warp (each
+// value added once) instead of a tree in every thread; the order is fixed.
+__device__ __forceinline__ void block_reduce_cs(int& na, double& sa, int& nb, double& sb, SelSmem& sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  na = __reduce_add_sync(0xffffffffu, na);
+  nb = __reduce_add_sync(0xffffffffu, nb);
+  sm.pref[threadIdx.x] = sa;
+  sm.pref[kSelBlock + threadIdx.x] = sb;
+  if (lane == 0) {
+    sm.sh[w] = na;
+    sm.sh[32 + w] = nb;
+  }
+  __syncthreads();
+  if (w == 0) {
+    double a = 0.0, b = 0.0;
+    for (int v = 0; v < kSelBlock / 32; ++v) {
+      a += sm.pref[32 * v + lane];
+      b += sm.pref[kSelBlock + 32 * v + lane];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int ca = __reduce_add_sync(0xffffffffu, lane < kSelBlock / 32 ? sm.sh[lane] : 0);
+    const int cb = __reduce_add_sync(0xffffffffu, lane < kSelBlock / 32 ? sm.sh[32 + lane] : 0);
+    if (lane == 0) {
+      sm.rsum[0] = a;
+      sm.rsum[1] = b;
+      sm.rcnt[0] = ca;
+      sm.rcnt[1] = cb;
+    }
+  }
+  __syncthreads();
+  sa = sm.rsum[0];
+  sb = sm.rsum[1];
+  na = sm.rcnt[0];
+  nb = sm.rcnt[1];
+  __syncthreads();
+}
+
+// Root of Phi on [floorv, top_max] over the unsorted candidates (the top set is
+// {key > bk} + {key == bk, index <= bi}, Alg. 1 order).  Every thread evaluates
+// the counts and sums of Phi's linear piece at the broadcast point -- top members
+// active where a < t + min(rho t, M), tail members where a > t, by integer
+// compares of bit patterns -- and thread 0 alone does the scalar FP64 work (FP64
+// issues at 1/64 of the FP32 rate): Newton on the current piece (its root is
+// exact once the next point lies on the same piece), bisection when it leaves the
+// bracket, warm-started at the previous step's threshold.  false when
+// Phi(floorv) > 0 (the pooled block reaches below the candidates).
+__device__ bool root_unsorted(SelSmem& sm, int cc, unsigned long long bk, int bi, double floorv, bool all,
+                              double top_max, double t0, double rho, double M, double* root, int* pooled) {
+  // thread 0's state
+  double lo = floorv, hi = top_max, t = 0.0;
+  int pnA = -1, pnB = -1;
+  double pSA = 0.0, pSB = 0.0;
+  bool pcap = false, at_floor = false;
+  if (threadIdx.x == 0) {
+    at_floor = !all;
+    t = at_floor ? floorv : ((t0 > lo && t0 < hi) ? t0 : 0.5 * (lo + hi));
+    sm.rtb[0] = dbits(t);
+    sm.rtb[1] = dbits(t + fmin(rho * t, M));
+    sm.rflag[0] = 0;
+  }
+  __syncthreads();
   for (int it = 0; it < 200; ++it) {
-    double nA = 0, SA = 0, nB = 0, SB = 0;
-    for (int i = threadIdx.x; i < p; i += kSelBlock) {
-      const unsigned kk = __ldcg(&d.key[i]);
-      const double a = key_value(kk, w, i);
-      if (in_top(kk, a, i, thr, q, bnd_a, bnd_i)) {
-        if (top_break(a, rho, M) < th) { nA += 1; SA += a; }
-      } else if (a > th) {
+    const unsigned long long tb = sm.rtb[0], hb = sm.rtb[1];
+    int nA = 0, nB = 0;
+    double SA = 0.0, SB = 0.0;
+    for (int j = threadIdx.x; j < cc; j += kSelBlock) {
+      const unsigned long long k = sm.cand[j];
+      const bool top = k > bk || (k == bk && sm.cidx[j] <= bi);
+      if (top) {
+        if (k < hb) { nA += 1; SA += dval(k); }
+      } else if (k > tb) {
         nB += 1;
-        SB += a;
+        SB += dval(k);
       }
     }
-    nA = block_sum<double, kSelBlock>(nA, sm.red);
-    SA = block_sum<double, kSelBlock>(SA, sm.red);
-    nB = block_sum<double, kSelBlock>(nB, sm.red);
-    SB = block_sum<double, kSelBlock>(SB, sm.red);
-    const double phi = nA * (th + fmin(rho * th, M)) - SA - (SB - nB * th);
-    if (phi == 0.0) return th;
-    if (phi < 0.0) lo = th; else hi = th;
-    const double cand = (nA + nB > 0) ? ((rho * th < M) ? (SA + SB) / (nA * (1.0 + rho) + nB)
-                                                        : (SA + SB - nA * M) / (nA + nB))
-                                      : 0.5 * (lo + hi);
-    const bool ok = cand > lo && cand < hi;
-    const double next = ok ? cand : 0.5 * (lo + hi);
-    if (ok && it > 0 && fabs(next - th) <= 2e-15 * fabs(th)) return next;
-    if (hi - lo <= 2e-16 * hi) return ok ? next : hi;
-    th = next;
+    block_reduce_cs(nA, SA, nB, SB, sm);
+    if (threadIdx.x == 0) {
+      const bool capped = rho * t >= M;
+      const double phi = (double)nA * dval(hb) - SA - (SB - (double)nB * t);
+      int done = 0;
+      double res = t;
+      if (at_floor) {
+        at_floor = false;
+        if (phi > 0.0) done = 2;                 // the root lies below the candidates
+        else if (phi == 0.0) done = 1;
+        else t = (t0 > lo && t0 < hi) ? t0 : 0.5 * (lo + hi);
+      } else if (phi == 0.0 || (nA == pnA && nB == pnB && capped == pcap && SA == pSA && SB == pSB)) {
+        done = 1;                                // t is the root of the piece it lies on
+      } else {
+        if (phi < 0.0) lo = t; else hi = t;
+        const double den = capped ? (double)(nA + nB) : (double)nA * (1.0 + rho) + (double)nB;
+        const double tn = den > 0.0 ? (capped ? (SA + SB - (double)nA * M) : (SA + SB)) / den : 0.5 * (lo + hi);
+        const bool ok = tn > lo && tn < hi;
+        if (hi - lo <= 2e-16 * hi || it == 199) {
+          done = 1;
+          res = ok ? tn : hi;
+        } else {
+          pnA = ok ? nA : -1;                    // a bisection point: no piece to compare with
+          pnB = nB;
+          pSA = SA;
+          pSB = SB;
+          pcap = capped;
+          t = ok ? tn : 0.5 * (lo + hi);
+        }
+      }
+      sm.rflag[0] = done;
+      sm.rflag[1] = nB;
+      sm.rt[0] = res;
+      sm.rtb[0] = dbits(t);
+      sm.rtb[1] = dbits(t + fmin(rho * t, M));
+    }
+    __syncthreads();
+    const int done = sm.rflag[0];
+    if (done) {
+      *root = sm.rt[0];
+      *pooled = sm.rflag[1];
+      __syncthreads();
+      return done == 1;
+    }
   }
-  return th;
+  return false;   // not reached: thread 0 ends the search by iteration 199
+}
+
+// Root of Phi over full passes of w (pooled blocks wider than the candidate
+// capacity), the same search as root_unsorted: every thread sums the active
+// members of its coordinates -- the float key of |w| decides most of them, the
+// FP64 value (compared as bits) only where the key ties with the boundary's or
+// the point's -- and thread 0 alone runs the Newton / bisection scalars, from the
+// previous step's threshold.  Phi(hi0) > 0; Phi(0) <= 0 always.
+__device__ double root_fullpass_global(const Dev& d, SelSmem& sm, int q, unsigned thr, double bnd_a, int bnd_i,
+                                       double hi0, double t0, double rho, double M) {
+  const int p = d.p;
+  const double* w = (const double*)d.wbuf;
+  double lo = 0.0, hi = hi0, t = 0.0;
+  int pnA = -1, pnB = -1;
+  double pSA = 0.0, pSB = 0.0;
+  bool pcap = false;
+  if (threadIdx.x == 0) {
+    t = (t0 > lo && t0 < hi) ? t0 : 0.5 * hi;
+    sm.rtb[0] = dbits(t);
+    sm.rtb[1] = dbits(t + fmin(rho * t, M));
+    sm.rflag[1] = (int)(__float_as_uint((float)t) & 0x7fffffffu);
+    sm.rflag[0] = 0;
+  }
+  __syncthreads();
+  for (int it = 0; it < 200; ++it) {
+    const unsigned long long tb = sm.rtb[0], hb = sm.rtb[1];
+    const unsigned kt = (unsigned)sm.rflag[1];
+    int nA = 0, nB = 0;
+    double SA = 0.0, SB = 0.0;
+    for (int i = threadIdx.x; i < p; i += kSelBlock) {
+      const unsigned kk = __ldcg(&d.key[i]);
+      if (kk == 0u || (kk < kt && kk < thr)) continue;   // off the free set, or below both the point and the top set
+      const bool maybe_top = kk >= thr;
+      double a = 0.0;
+      bool top = false;
+      if (maybe_top) {
+        a = fabs(__ldcg(&w[i]));
+        top = in_top(kk, a, i, thr, q, bnd_a, bnd_i);
+      }
+      if (top) {
+        if (dbits(a) < hb) { nA += 1; SA += a; }
+      } else if (kk >= kt) {
+        if (!maybe_top) a = fabs(__ldcg(&w[i]));
+        if (dbits(a) > tb) { nB += 1; SB += a; }
+      }
+    }
+    block_reduce_cs(nA, SA, nB, SB, sm);
+    if (threadIdx.x == 0) {
+      const bool capped = rho * t >= M;
+      const double phi = (double)nA * dval(hb) - SA - (SB - (double)nB * t);
+      int done = 0;
+      double res = t;
+      if (phi == 0.0 || (nA == pnA && nB == pnB && capped == pcap && SA == pSA && SB == pSB)) {
+        done = 1;
+      } else {
+        if (phi < 0.0) lo = t; else hi = t;
+        const double den = capped ? (double)(nA + nB) : (double)nA * (1.0 + rho) + (double)nB;
+        const double tn = den > 0.0 ? (capped ? (SA + SB - (double)nA * M) : (SA + SB)) / den : 0.5 * (lo + hi);
+        const bool ok = tn > lo && tn < hi;
+        if (hi - lo <= 2e-16 * hi || it == 199) {
+          done = 1;
+          res = ok ? tn : hi;
+        } else {
+          pnA = ok ? nA : -1;
+          pnB = nB;
+          pSA = SA;
+          pSB = SB;
+          pcap = capped;
+          t = ok ? tn : 0.5 * (lo + hi);
+        }
+      }
+      sm.rflag[0] = done;
+      sm.rt[0] = res;
+      sm.rtb[0] = dbits(t);
+      sm.rtb[1] = dbits(t + fmin(rho * t, M));
+      // the float key below which no coordinate can exceed t: fl32 rounds to nearest,
+      // so key(a) < key(t) implies a < t
+      sm.rflag[1] = (int)(__float_as_uint((float)t) & 0x7fffffffu);
+    }
+    __syncthreads();
+    if (sm.rflag[0]) {
+      const double r = sm.rt[0];
+      __syncthreads();
+      return r;
+    }
+  }
+  return sm.rt[0];
+}
+
+// next step's candidate floor: with x the smallest value of a fixed ladder whose
+// count of candidates at or above x theta stays within `want` (the top set and
+// about 1.5 times the pooled block) and whose x theta is not below this list's
+// floor, 0.98 x theta -- the candidates then reach a little below the pooled
+// block the next step is likely to need; 0 (every free coordinate) when theta is 0
+__device__ unsigned next_floor_key(SelSmem& sm, int cc, double theta, int want, unsigned long long floor_now) {
+  constexpr int NX = 16;
+  if (!(theta > 0.0) || !isfinite(theta)) return 0u;
+  unsigned long long* thr = sm.tkey + kProxCap - 16;   // past any top set of the fast path
+  if (threadIdx.x < NX) {
+    const double xs[NX] = {0.999, 0.995, 0.99, 0.985, 0.98, 0.97, 0.96, 0.94,
+                           0.92,  0.89,  0.85, 0.8,   0.7,  0.6,  0.5,  0.3};
+    thr[threadIdx.x] = dbits(xs[threadIdx.x] * theta);
+    sm.rcnt[2 + threadIdx.x] = 0;
+  }
+  __syncthreads();
+  int c[NX];
+#pragma unroll
+  for (int m = 0; m < NX; ++m) c[m] = 0;
+  for (int j = threadIdx.x; j < cc; j += kSelBlock) {
+    const unsigned long long k = sm.cand[j];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) c[m] += k >= thr[m];
+  }
+#pragma unroll
+  for (int m = 0; m < NX; ++m) {
+    c[m] = __reduce_add_sync(0xffffffffu, c[m]);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&sm.rcnt[2 + m], c[m]);
+  }
+  __syncthreads();
+  // counts below the current list's floor are unknown: the ladder stops there
+  int pick = 0;
+#pragma unroll
+  for (int m = 0; m < NX; ++m)
+    if (sm.rcnt[2 + m] <= want && thr[m] >= floor_now) pick = m;
+  const unsigned key = __float_as_uint((float)(0.98 * dval(thr[pick]))) & 0x7fffffffu;
+  __syncthreads();
+  return key;
 }
 
 __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
   const int p = d.p;
   const double rho = nd->rho, M = nd->M;
-  const double shrink = rho / (1.0 + rho);
+  if (threadIdx.x == 0) sm.cs[0] = rho / (1.0 + rho);   // once, not in every thread
+  __syncthreads();
+  const double shrink = sm.cs[0];
   const unsigned* key = d.key;
   const double* w = (const double*)d.wbuf;
   auto kload = [&](int i) -> unsigned { return __ldcg(&key[i]); };
@@ -346,12 +573,13 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
       sm.cand[j] = __ldcg(&d.cand_a[j]);
       sm.cidx[j] = __ldcg(&d.cand_i[j]);
     }
-    const int N = next_pow2(cc > 0 ? cc : 1);
-    for (int j = cc + threadIdx.x; j < N; j += kSelBlock) { sm.cand[j] = 0ull; sm.cidx[j] = 0x7fffffff; }
     __syncthreads();
-    sort_pairs_desc(sm.cand, sm.cidx, N);   // |w| descending, index ascending (Alg. 1)
     if (cc <= q) {
       // every free coordinate is in the top set (the rest of it are zeros)
+      const int N = next_pow2(cc > 0 ? cc : 1);
+      for (int j = cc + threadIdx.x; j < N; j += kSelBlock) { sm.cand[j] = 0ull; sm.cidx[j] = 0x7fffffff; }
+      __syncthreads();
+      sort_pairs_desc(sm.cand, sm.cidx, N);   // |w| descending, index ascending (Alg. 1)
       thr = 0u;
       bnd_a = -1.0;
       theta = 0.0;
@@ -362,44 +590,72 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
       }
       done = true;
     } else {
-      prefix_values(sm, cc);
-      for (int t = threadIdx.x; t < q; t += kSelBlock) sm.tb[t] = top_break(dval(sm.cand[t]), rho, M);
-      __syncthreads();
-      const bool all = (cg == 0u);
-      const double floorv = all ? 0.0 : dval(sm.cand[cc - 1]);
-      double th = 0.0;
-      const bool fnd = threadIdx.x < 32 && root_search(sm, q, cc, floorv, all, rho, M, &th);
-      if (threadIdx.x == 0) {
-        sm.flag[1] = fnd ? 1 : 0;
-        sm.root[0] = th;
-        // next step's guess: keep about twice the pooled block, 5% below
-        int lo = q, hi = cc;
-        const unsigned long long tk = dbits(th);
-        while (lo < hi) {
-          const int mid = (lo + hi) >> 1;
-          if (sm.cand[mid] <= tk) hi = mid; else lo = mid + 1;
+      // the top set in Alg. 1 order (|w| descending, index ascending): every candidate
+      // at or above a floor that holds at least q of them, sorted -- the floor is just
+      // below the previous step's boundary value (the top set moves little), else
+      // the q-th largest by radix selection
+      auto cload = [&](int i) -> unsigned long long { return sm.cand[i]; };
+      auto gather = [&](unsigned long long fk) {
+        if (threadIdx.x == 0) sm.flag[0] = 0;
+        __syncthreads();
+        for (int j = threadIdx.x; j < cc; j += kSelBlock) {
+          if (sm.cand[j] >= fk) {
+            const int pos = atomicAdd(&sm.flag[0], 1);
+            if (pos < kProxCap - 16) {
+              sm.tkey[pos] = sm.cand[j];
+              sm.tidx[pos] = sm.cidx[j];
+            }
+          }
         }
-        int g = lo + lo / 2 + 32;
-        if (g > cc - 1) g = cc - 1;
-        sm.flag[0] = (int)(__float_as_uint((float)(0.98 * dval(sm.cand[g]))) & 0x7fffffffu);
+        __syncthreads();
+        return sm.flag[0];
+      };
+      int G = 0;
+      const double pb = nd->bnd_a;
+      if (pb > 0.0 && isfinite(pb)) {
+        G = gather(dbits(0.98 * pb));
+        if (G < q || G > 1024) G = 0;      // too few (the set grew) or too many to sort cheaply
+      }
+      if (G == 0) {
+        const SelectResult<unsigned long long> R =
+            block_select<unsigned long long, kSelBlock>(cc, q, cload, sm.hist, sm.sh);
+        G = gather(R.thr);
       }
       __syncthreads();
-      if (sm.flag[1]) {
-        theta = sm.root[0];
-        const double aq = dval(sm.cand[q - 1]);
-        bnd_a = aq;
-        bnd_i = sm.cidx[q - 1];
-        thr = __float_as_uint((float)aq) & 0x7fffffffu;   // the key of the boundary element
-        next_guess = (unsigned)sm.flag[0];
+      if (G <= kProxCap - 16) {   // else: massive ties at the boundary, left to the full path below
+      const int NG = next_pow2(G);
+      for (int j = G + threadIdx.x; j < NG; j += kSelBlock) { sm.tkey[j] = 0ull; sm.tidx[j] = 0x7fffffff; }
+      __syncthreads();
+      sort_pairs_desc(sm.tkey, sm.tidx, NG);
+      const unsigned long long bk = sm.tkey[q - 1];
+      const int bi = sm.tidx[q - 1];
+      // the root of Phi over the unsorted candidates (floor: every coordinate off the
+      // candidate list has a key below cg, hence |w| below the float value of cg)
+      const bool all = (cg == 0u);
+      const double floorv = all ? 0.0 : (double)__uint_as_float(cg);
+      double th = 0.0;
+      int pooled = 0;
+      const bool fnd = root_unsorted(sm, cc, bk, bi, floorv, all, dval(sm.tkey[0]), nd->theta, rho, M,
+                                     &th, &pooled);
+      if (fnd) {
+        theta = th;
+        bnd_a = dval(bk);
+        bnd_i = bi;
+        thr = __float_as_uint((float)bnd_a) & 0x7fffffffu;   // the key of the boundary element
         qused = cc;
         for (int t = threadIdx.x; t < q; t += kSelBlock) {
-          const double a = dval(sm.cand[t]);
+          const double a = dval(sm.tkey[t]);
           const double mg = fmin(fmin(M, shrink * a), a - theta);
           d.tbeta[t] = mg > 0.0 ? mg : 0.0;
         }
+        __syncthreads();   // the top set's reads are done before its tail is reused
+        // next step's list: about 1.5 times the top set and pooled block
+        const int want = (q + pooled) + (q + pooled) / 2 + 32;
+        next_guess = next_floor_key(sm, cc, theta, want < kProxCap ? want : kProxCap, dbits(floorv));
         done = true;
       }
       __syncthreads();
+      }
     }
   }
   if (q > 0 && !done) {
@@ -486,7 +742,7 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
         fb = 1;
         theta = root_fullpass_global(d, sm, q, thr, bnd_a, bnd_i,
                                      isinf(last_floor) ? (double)__uint_as_float(thr) * 2.0 + 1e-300
-                                                       : last_floor, rho, M);
+                                                       : last_floor, nd->theta, rho, M);
       }
     }
     // |b| on the top set, descending (its order is the order of |w|), for Alg. 2
@@ -549,30 +805,49 @@ __device__ void prox_select_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
 // G*(a)/(2 lambda2) = TopSum_k'(H_M(|a_F|/2l2)) + sum_S1 H_M(|a_j|/2l2).
 __device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
   const int p = d.p;
-  const double scale = 1.0 / (2.0 * nd->lambda2), M = nd->M;
+  if (threadIdx.x == 0) sm.cs[1] = 1.0 / (2.0 * nd->lambda2);   // once, not in every thread
+  __syncthreads();
+  const double scale = sm.cs[1], M = nd->M;
   const double* g = d.grad;
   // S1 from its index list (a scan of the p states would be a chain of dependent
   // loads per thread: ~50 loads deep at p = 50000)
   double s1 = 0.0;
   const int n1 = nd->n_one;
   for (int t = threadIdx.x; t < n1; t += kSelBlock) s1 += huber(fabs(g[d.one_idx[t]]) * scale, M);
-  s1 = block_sum<double, kSelBlock>(s1, sm.red);
+  {
+    int c0 = 0, c1 = 0;
+    double unused = 0.0;
+    block_reduce_cs(c0, s1, c1, unused, sm);
+  }
   double s = 0.0;
   unsigned next_guess = 0u;
   const int dc = __ldcg(&d.ccount[1]);
   const unsigned dg = nd->dguess;
   if (q > 0 && dc <= kProxCap && (dc >= q || dg == 0u)) {
-    // the predicted candidates hold the top-k' magnitudes of the gradient
+    // the predicted candidates hold the top-k' magnitudes of the gradient (at a
+    // KKT point many of them are nearly equal: the list can be long): the k'-th
+    // largest by radix selection, H_M over the larger ones, the ties at its value
     for (int j = threadIdx.x; j < dc; j += kSelBlock) sm.cand[j] = __ldcg(&d.dcand[j]);
-    const int N = next_pow2(dc > 0 ? dc : 1);
-    for (int j = dc + threadIdx.x; j < N; j += kSelBlock) sm.cand[j] = 0ull;
     __syncthreads();
-    sort_u64_desc(sm.cand, N);
     const int top = q < dc ? q : dc;
-    double b = 0.0;
-    for (int j = threadIdx.x; j < top; j += kSelBlock) b += huber(dval(sm.cand[j]) * scale, M);
-    s = block_sum<double, kSelBlock>(b, sm.red);
-    if (top > 0) next_guess = __float_as_uint((float)(0.995 * dval(sm.cand[top - 1]))) & 0x7fffffffu;
+    if (top > 0) {
+      auto cload = [&](int i) -> unsigned long long { return sm.cand[i]; };
+      const SelectResult<unsigned long long> R =
+          block_select<unsigned long long, kSelBlock>(dc, top, cload, sm.hist, sm.sh);
+      int nb = 0, nz = 0;
+      double b = 0.0, z = 0.0;
+      for (int j = threadIdx.x; j < dc; j += kSelBlock)
+        if (sm.cand[j] > R.thr) b += huber(dval(sm.cand[j]) * scale, M);
+      block_reduce_cs(nb, b, nz, z, sm);
+      if (threadIdx.x == 0) {
+        const double tv = dval(R.thr);
+        sm.rt[1] = b + (double)(top - R.gt) * huber(tv * scale, M);
+        sm.rflag[1] = (int)(__float_as_uint((float)(0.995 * tv)) & 0x7fffffffu);
+      }
+      __syncthreads();
+      s = sm.rt[1];
+      next_guess = (unsigned)sm.rflag[1];
+    }
     if (threadIdx.x == 0) nd->dfast_steps += 1;
   } else if (q > 0) {
     auto kload = [&](int i) -> unsigned { return __ldcg(&d.dkey[i]); };

@@ -25,6 +25,7 @@
 #include "ksc_problem.h"
 #include "ksc_session.h"
 #include "ksc_tc.h"
+#include "ksc_tcx.h"
 
 namespace ksc {
 
@@ -51,10 +52,22 @@ struct BatchWs {
   cudaEvent_t ph0 = nullptr, ph1 = nullptr;   // around certificate / anchor phases (profiling)
   const void* Xb = nullptr;   // X with a TMA-compatible row stride (the problem's, or a copy)
   int64_t ldxb = 0;
+  // exact products of anchors and certificates on the tensor cores (k_tcexact.cu):
+  // slices of X (forward: rows of X, K = p) and of Xc (gradient: columns of X,
+  // K = n), and of the listed nodes' vectors; built for the problem-owned
+  // workspace of ksc_solve_batch and branch and bound (server sessions keep the
+  // streaming double-float product and its smaller footprint)
+  bool tcx = false;
+  TcxSlices xs_fwd, xs_grad;
+  TcxVecs vs_fwd, vs_grad;
 };
 
 void free_batch(BatchWs* ws) {
   if (!ws) return;
+  tcx_slices_free(&ws->xs_fwd);
+  tcx_slices_free(&ws->xs_grad);
+  tcx_vecs_free(&ws->vs_fwd);
+  tcx_vecs_free(&ws->vs_grad);
   if (ws->graph) cudaGraphExecDestroy(ws->graph);
   if (ws->graph_prof) cudaGraphExecDestroy(ws->graph_prof);
   for (auto e : ws->events) cudaEventDestroy(e);
@@ -143,7 +156,9 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   return b;
 }
 
-ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
+bool tcx_enabled();
+
+ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bool exact_tc) {
   BatchWs* ws = new BatchWs();
   *out = ws;
   const int n = (int)pr->n, p = (int)pr->p;
@@ -246,7 +261,41 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out) {
   d.nft = nft;
   d.Bpad = ws->Bpad;
   d.B = Bc;
+  if (exact_tc && tcx_enabled()) {
+    const char* why = "";
+    if (!tcx_slices_build(&ws->xs_fwd, pr->X, n, p, pr->ldx, s, &why) ||
+        !tcx_slices_build(&ws->xs_grad, pr->dev.Xc, p, n, pr->dev.ldc, s, &why) ||
+        !tcx_vecs_alloc(&ws->vs_fwd, Bc, p, &why) || !tcx_vecs_alloc(&ws->vs_grad, Bc, n, &why))
+      return api_fail(KSC_ERR_OOM, std::string("exact tensor-core products: ") + why);
+    ws->tcx = true;
+    ws->bytes += ws->xs_fwd.bytes + ws->xs_grad.bytes + ws->vs_fwd.bytes + ws->vs_grad.bytes;
+  }
   return KSC_OK;
+}
+
+// KSC_EXACT_PRODUCT=stream keeps the streaming double-float product for anchors and
+// certificates (for comparisons); by default they run on the tensor cores
+bool tcx_enabled() {
+  const char* e = std::getenv("KSC_EXACT_PRODUCT");
+  return !(e && std::strcmp(e, "stream") == 0);
+}
+
+// exact products of many nodes' vectors: D rows = X V rows (fwd, V of length p) or
+// X^T V rows (V of length n), on the tensor cores when the workspace holds the
+// slices of X, else the streaming double-float product; returns the error
+// factor of the result (|D - exact| <= f ||x_c|| ||v||)
+double exact_product(ksc_problem* pr, BatchWs* ws, bool fwd, const double* V, int64_t ldv, int R, double* D,
+                     int64_t ldd, int kblock, cudaStream_t s) {
+  const BatchDev& d = ws->bd;
+  if (ws->tcx) {
+    const TcxSlices& x = fwd ? ws->xs_fwd : ws->xs_grad;
+    tcx_product(x, fwd ? ws->vs_fwd : ws->vs_grad, V, ldv, ws->dlist, R, D, ldd, s);
+    pr->launches += tcx_launches(x, R);
+    return tcx_error_factor(x);
+  }
+  launch_dfprod(pr->dev, fwd, V, ldv, ws->dlist, R, D, ldd, d.dfws, kblock, s);
+  pr->launches += 1 + (dfprod_splits(R, fwd ? d.n : d.p) > 1);
+  return fwd ? dfprod_error_factor(d.p, R, d.n, kblock) : dfprod_error_factor(d.n, R, d.p, kblock);
 }
 
 TcEpi fwd_epi(const BatchWs* ws) {
@@ -445,20 +494,19 @@ ksc_status anchor(Session* se, const std::vector<int>& list, bool init) {
   const int cnt = (int)list.size();
   KB_CUDA(cudaMemcpyAsync(ws->dlist, list.data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
   if (!init) launch_banchor_copy(d, ws->dlist, cnt, s);
-  const bool tiled = cnt >= kAnchorTiled;
+  const bool tiled = cnt >= kAnchorTiled || ws->tcx;
   if (tiled) {
-    launch_dfprod(sd, true, d.beta_ref, d.ldp, ws->dlist, cnt, d.u_ref, d.ldn, d.dfws, kDfBlockAnchor, s);
+    exact_product(se->pr, ws, true, d.beta_ref, d.ldp, cnt, d.u_ref, d.ldn, kDfBlockAnchor, s);
   } else {
     for (int b : list) launch_colsum_any(sd, true, d.beta_ref + (size_t)b * d.ldp, d.u_ref + (size_t)b * d.ldn, s);
   }
   launch_banchor_resid(d, ws->dlist, cnt, init ? 1 : 0, s);
   if (tiled) {
-    launch_dfprod(sd, false, d.r_ref, d.ldn, ws->dlist, cnt, d.G_ref, d.ldp, d.dfws, kDfBlockAnchor, s);
+    exact_product(se->pr, ws, false, d.r_ref, d.ldn, cnt, d.G_ref, d.ldp, kDfBlockAnchor, s);
   } else {
     for (int b : list) launch_colsum_any(sd, false, d.r_ref + (size_t)b * d.ldn, d.G_ref + (size_t)b * d.ldp, s);
   }
-  se->pr->launches += tiled ? kLaunchesPerAnchor + (dfprod_splits(cnt, d.n) > 1) + (dfprod_splits(cnt, d.p) > 1)
-                             : 2 + 2 * cnt;
+  se->pr->launches += tiled ? kLaunchesPerAnchor - 2 : 2 + 2 * cnt;
   se->anchors += cnt;
   return KSC_OK;   // the list buffer's next upload is ordered after these kernels
 }
@@ -486,7 +534,7 @@ ksc_status session_open(Session* se, ksc_problem* pr, int slots, bool use_proble
         pr->batch = nullptr;
       }
       BatchWs* ws = nullptr;
-      st = alloc_ws(pr, std::max(slots, 128), s, &ws);
+      st = alloc_ws(pr, std::max(slots, 128), s, &ws, true);
       if (st != KSC_OK) {
         free_batch(ws);
         return st;
@@ -498,7 +546,7 @@ ksc_status session_open(Session* se, ksc_problem* pr, int slots, bool use_proble
     se->own_ws = false;
   } else {
     BatchWs* ws = nullptr;
-    st = alloc_ws(pr, slots, s, &ws);
+    st = alloc_ws(pr, slots, s, &ws, false);
     if (st != KSC_OK) {
       free_batch(ws);
       return st;
@@ -729,12 +777,11 @@ ksc_status session_collect(Session* se, std::vector<int>* finished) {
     const Dev& sd = pr->dev;
     KB_CUDA(cudaMemcpyAsync(ws->dlist, fired.data(), (size_t)R * 4, cudaMemcpyHostToDevice, s));
     launch_bcert_prep(d, ws->dlist, R, s);
-    launch_dfprod(sd, true, d.beta_out, d.p, ws->dlist, R, d.cert_u, d.ldn, d.dfws, kDfBlockCert, s);
+    const double err_u = exact_product(pr, ws, true, d.beta_out, d.p, R, d.cert_u, d.ldn, kDfBlockCert, s);
     launch_bcert_rows(d, ws->dlist, R, s);
-    launch_dfprod(sd, false, d.cert_z, d.ldn, ws->dlist, R, d.cert_a, d.ldp, d.dfws, kDfBlockCert, s);
-    launch_bcert_final(d, ws->dlist, R, dfprod_error_factor(d.n, R, d.p, kDfBlockCert),
-                       dfprod_error_factor(d.p, R, d.n, kDfBlockCert), s);
-    pr->launches += kLaunchesPerBatchCert + (dfprod_splits(R, d.n) > 1) + (dfprod_splits(R, d.p) > 1);
+    const double err_a = exact_product(pr, ws, false, d.cert_z, d.ldn, R, d.cert_a, d.ldp, kDfBlockCert, s);
+    launch_bcert_final(d, ws->dlist, R, err_a, err_u, s);
+    pr->launches += kLaunchesPerBatchCert - 2;
     se->certificates += R;
     KB_CUDA(cudaGetLastError());
     cert_phase.end();

@@ -1,11 +1,14 @@
-// ksc_tc_api.cu -- ksc_tc_gemm: the batched solver's tensor-core product on
-// caller-owned device buffers, exported so that tests can check it on its own.
+// ksc_tc_api.cu -- ksc_tc_gemm, ksc_tc_gemm_sk and ksc_tc_exact: the batched
+// solver's tensor-core products on caller-owned device buffers, exported so that
+// tests can check them on their own.
 #include <cuda_runtime.h>
 
 #include <string>
 
 #include "../../include/ksc.h"
+#include "ksc_launch.h"
 #include "ksc_tc.h"
+#include "ksc_tcx.h"
 
 ksc_status ksc_internal_fail(ksc_status st, const char* msg);
 
@@ -67,5 +70,36 @@ extern "C" ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, i
   int word = 0;
   cudaMemcpy(&word, tc_error_word(), sizeof word, cudaMemcpyDeviceToHost);
   if (word != 0) return ksc_internal_fail(KSC_ERR_TIMEOUT, "stream-K product: a device wait gave up");
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_tc_exact(const void* A, int32_t c, int32_t k, int64_t lda, const double* V, int32_t r,
+                                   int64_t ldv, double* D, int64_t ldd, double* err_factor, void* cuda_stream) {
+  if (!A || !V || !D) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "NULL operand");
+  if (c < 1 || k < 1 || r < 1 || r > kTcxMaxR) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "sizes out of range");
+  if (lda < k || ldv < k || ldd < c) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "row strides too small");
+  cudaError_t e = prox_prepare();
+  if (e != cudaSuccess) return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  TcxSlices x;
+  TcxVecs v;
+  const char* why = "";
+  if (!tcx_slices_build(&x, A, c, k, lda, s, &why)) return ksc_internal_fail(KSC_ERR_OOM, why);
+  if (!tcx_vecs_alloc(&v, r, k, &why)) {
+    tcx_slices_free(&x);
+    return ksc_internal_fail(KSC_ERR_OOM, why);
+  }
+  tcx_clear_error(s);
+  tcx_product(x, v, V, ldv, nullptr, r, D, ldd, s);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  int word = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&word, tcx_error_word(), sizeof word, cudaMemcpyDeviceToHost);
+  if (err_factor) *err_factor = tcx_error_factor(x);
+  tcx_slices_free(&x);
+  tcx_vecs_free(&v);
+  if (e != cudaSuccess)
+    return ksc_internal_fail(KSC_ERR_CUDA, (std::string("exact product: ") + cudaGetErrorString(e)).c_str());
+  if (word != 0) return ksc_internal_fail(KSC_ERR_TIMEOUT, "exact product: a device wait gave up");
   return KSC_OK;
 }
