@@ -23,12 +23,14 @@ _OUT = os.path.join(_HERE, "_build", "libksc_gen.so")
 _lib = None
 
 LSQ, LOGISTIC, SQHINGE = 0, 1, 2   # labels +-1 for the last two
+POISSON, GAMMA = 3, 4               # counts >= 0; positive reals
 F64, F32, BF16 = "f64", "f32", "bf16"
 _DT_CODE = {F64: 0, F32: 1, BF16: 2}
 
 # stream ids (second Philox key word)
 _S_SUPPORT, _S_SIGN, _S_NOISE, _S_LABEL, _S_NODES, _S_WARM = 2, 3, 4, 5, 6, 7
 _S_MIX, _S_ARRIVAL = 8, 9
+_S_COUNT = 10
 
 
 def build(force: bool = False) -> str:
@@ -124,12 +126,55 @@ class Problem:
         return self.X.astype(np.float64)
 
 
+def f64_to_bf16(x: np.ndarray) -> np.ndarray:
+    """BF16 bits (uint16) of x rounded to nearest, ties to even (via FP32)."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    return ((b + 0x7FFF + ((b >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def _poisson(mu, u):
+    """Poisson(mu) draws by inversion of the CDF at the uniforms u."""
+    k = np.zeros(mu.shape)
+    pk = np.exp(-mu)
+    cdf = pk.copy()
+    for j in range(1, 400):
+        more = u > cdf
+        if not more.any():
+            break
+        k += more
+        pk = pk * mu / j
+        cdf = cdf + pk
+    return k
+
+
 def make_problem(n, p, *, r=0.5, seed=0, loss=LSQ, k_true=5, snr=5.0, x_dtype=F64,
                  lambda2=1.0, M=2.0, k=5) -> Problem:
     """Rows ~ N(0, Toeplitz r^|j-l|), standardised columns, beta* with k_true
     entries +-1 at seeded positions; least squares: y = X beta* + noise with
     sigma^2 = ||X beta*||^2 / (n SNR); logistic and squared hinge:
-    P(y_i = +1) = sigmoid(x_i^T beta*)."""
+    P(y_i = +1) = sigmoid(x_i^T beta*).  Poisson and Gamma: columns of unit norm
+    (the convention of the paper's real data), a log link with the linear
+    predictor eta = 0.5 (X beta*) / std(X beta*), y ~ Poisson(e^eta) or
+    y ~ Gamma(shape 2, mean e^eta) (the sum of two exponentials)."""
+    if loss in (POISSON, GAMMA):
+        P = make_problem(n, p, r=r, seed=seed, loss=LSQ, k_true=k_true, snr=snr, x_dtype=F64,
+                         lambda2=lambda2, M=M, k=k)
+        X = P.X / np.sqrt(n)
+        xb = P.X @ P.beta_star
+        eta = 0.5 * xb / max(float(np.std(xb)), 1e-300)
+        mu = np.exp(eta)
+        if loss == POISSON:
+            y = _poisson(mu, uniform(seed, _S_COUNT, n))
+        else:
+            u = uniform(seed, _S_COUNT, 2 * n)
+            y = 0.5 * mu * (-np.log1p(-u[:n]) - np.log1p(-u[n:]))
+            y = np.maximum(y, 1e-300)
+        if x_dtype == F32:
+            X = X.astype(np.float32)
+        elif x_dtype == BF16:
+            X = f64_to_bf16(X)
+        return Problem(X, y, P.beta_star, loss, float(lambda2), float(M), int(k), x_dtype,
+                       dict(n=n, p=p, r=r, seed=seed, k_true=k_true, unit_norm=True))
     support = np.sort(_choose(seed, _S_SUPPORT, p, min(k_true, p)))
     signs = np.where(uniform(seed, _S_SIGN, support.size) < 0.5, -1.0, 1.0)
     beta_star = np.zeros(p)

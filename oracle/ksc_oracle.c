@@ -30,6 +30,18 @@
  *      +inf (the value of g there, by the convention of Sec. 3).
  *  R10 Warm start: S0 coordinates set to 0 and all coordinates clipped to
  *      [-M, M] before the first step (Algorithm 3 starts from beta^0 = beta^1).
+ *  R22 Poisson and Gamma regression (App. D.1): their curvature e^u (Poisson)
+ *      and y e^-u (Gamma) is unbounded, so Algorithm 3's fixed step needs a bound
+ *      on u over the points it evaluates.  Every iterate lies in dom g_node, inside
+ *      {|b_j| <= M, sum |b_j| <= kM}, where |x_i^T b| <= U_i = M TopSum_k(|x_i|);
+ *      the extrapolated point b^t + c (b^t - b^{t-1}), 0 <= c < 1, has
+ *      |x_i^T b| < 3 U_i, and so has every point of the segment the step's descent
+ *      inequality uses.  Hence L = lambda_max(X^T X) max_i c_i with c_i =
+ *      e^{3 U_i} (Poisson) or y_i e^{3 U_i} (Gamma).  The warm start is clipped to
+ *      the box and, for these two losses, scaled into sum |b_j| <= kM.  The
+ *      printed conjugate of the Gamma loss, y h((1 - zeta)/y), is F*(+zeta); with
+ *      zeta = -grad F (R1) the bound takes F*(-zeta) = sum y h((1 + zeta)/y),
+ *      h(z) = z log z - z (h(0) = 0, +inf for z < 0).
  *  R20 Eigen-perspective bound (App. D.2): the objective keeps its constant
  *      ||y||^2 (so that the bound is one of ||X b - y||^2 + lambda2 ||b||^2 and
  *      equals the Sec. 3.4 bound at lambda = 0): F(b) = b^T Q b and G(b) =
@@ -221,6 +233,16 @@ double kso_g_value(const double *beta, int64_t p, int64_t k, double M, double *z
   return g;
 }
 
+/* sum of the k largest |v_j| */
+static double kso_gstar_abs_topsum(const double *v, int64_t p, int64_t k) {
+  if (p <= 0 || k <= 0) return 0.0;
+  kso_entry *ord = magnitude_order(v, p);
+  double s = 0.0;
+  for (int64_t r = 0; r < k && r < p; ++r) s += ord[r].mag;
+  free(ord);
+  return s;
+}
+
 /* Lemma 3.1: g*(a) = sum of the k largest H_M(a_j). */
 double kso_gstar(const double *a, int64_t p, int64_t k, double M) {
   if (p <= 0 || k <= 0) return 0.0;
@@ -325,6 +347,8 @@ double kso_loss(int loss, const double *u, const double *y, int64_t n) {
   for (int64_t i = 0; i < n; ++i) {
     if (loss == KSO_LOSS_LSQ) { double r = u[i] - y[i]; f += r * r; }
     else if (loss == KSO_LOSS_SQHINGE) { double m = fmax(0.0, 1.0 - y[i] * u[i]); f += m * m; }
+    else if (loss == KSO_LOSS_POISSON) f += exp(u[i]) - y[i] * u[i];
+    else if (loss == KSO_LOSS_GAMMA) f += y[i] * exp(-u[i]) + u[i];
     else f += log1pexp(-y[i] * u[i]);
   }
   return f;
@@ -334,6 +358,8 @@ void kso_loss_grad(int loss, const double *u, const double *y, int64_t n, double
   for (int64_t i = 0; i < n; ++i) {
     if (loss == KSO_LOSS_LSQ) grad[i] = 2.0 * (u[i] - y[i]);
     else if (loss == KSO_LOSS_SQHINGE) grad[i] = -2.0 * y[i] * fmax(0.0, 1.0 - y[i] * u[i]);
+    else if (loss == KSO_LOSS_POISSON) grad[i] = exp(u[i]) - y[i];
+    else if (loss == KSO_LOSS_GAMMA) grad[i] = 1.0 - y[i] * exp(-u[i]);
     else {  /* d/du log(1+exp(-y u)) = -y sigma(-y u) */
       double t = -y[i] * u[i];
       double sig = (t >= 0) ? 1.0 / (1.0 + exp(-t)) : exp(t) / (1.0 + exp(t));
@@ -347,10 +373,27 @@ void kso_loss_grad(int loss, const double *u, const double *y, int64_t n, double
  * 0 log 0 = 0, and -inf outside q in [0,1].
  * Squared hinge (y in {-1,+1}): F*(-zeta) = sum h(-y_i zeta_i) with
  * h(z) = z + z^2/4 for z <= 0 and +inf for z > 0, so -F*(-zeta) =
- * sum [y_i zeta_i - zeta_i^2 / 4] (y_i^2 = 1) on y_i zeta_i >= 0, -inf elsewhere. */
+ * sum [y_i zeta_i - zeta_i^2 / 4] (y_i^2 = 1) on y_i zeta_i >= 0, -inf elsewhere.
+ * Poisson (y >= 0): F*(-zeta) = sum h(y_i - zeta_i); Gamma (y > 0):
+ * F*(-zeta) = sum y_i h((1 + zeta_i) / y_i) (reading R22); h(z) = z log z - z,
+ * h(0) = 0, and -F*(-zeta) = -inf where an argument is negative. */
+static double hlog(double z) { return z > 0.0 ? z * log(z) - z : 0.0; }
+
 double kso_neg_conj(int loss, const double *zeta, const double *y, int64_t n) {
   double t = 0.0;
   for (int64_t i = 0; i < n; ++i) {
+    if (loss == KSO_LOSS_POISSON) {
+      const double z = y[i] - zeta[i];
+      if (z < 0.0) return -INFINITY;
+      t -= hlog(z);
+      continue;
+    }
+    if (loss == KSO_LOSS_GAMMA) {
+      const double z = (1.0 + zeta[i]) / y[i];
+      if (z < 0.0) return -INFINITY;
+      t -= y[i] * hlog(z);
+      continue;
+    }
     if (loss == KSO_LOSS_LSQ) t += y[i] * zeta[i] - 0.25 * zeta[i] * zeta[i];
     else if (loss == KSO_LOSS_SQHINGE) {
       double z = -y[i] * zeta[i];
@@ -441,10 +484,27 @@ double kso_power_iteration(const void *X, int xdt, int64_t n, int64_t p, int64_t
 
 /* ------------------------------------------- restarted FISTA (Sec. 3) */
 
-/* Lipschitz constant of beta -> grad F(X beta) (reading R3). */
+/* Poisson and Gamma (reading R22): max_i c_i, c_i = e^{3 U_i} or y_i e^{3 U_i},
+ * U_i = M TopSum_k(|x_i|), the largest |x_i^T b| over |b_j| <= M, sum |b_j| <= kM. */
+static double curvature_bound(const kso_solve_args *a) {
+  double *row = (double *)malloc((size_t)(a->p > 0 ? a->p : 1) * sizeof(double));
+  double c = 0.0;
+  for (int64_t i = 0; i < a->n; ++i) {
+    for (int64_t j = 0; j < a->p; ++j) row[j] = fabs(xat(a->X, a->x_dtype, a->ldx, i, j));
+    const double U = a->M * kso_gstar_abs_topsum(row, a->p, a->k);
+    const double ci = (a->loss == KSO_LOSS_GAMMA ? a->y[i] : 1.0) * exp(3.0 * U);
+    if (ci > c) c = ci;
+  }
+  free(row);
+  return c;
+}
+
+/* Lipschitz constant of beta -> grad F(X beta) (readings R3, R22). */
 static double lipschitz(const kso_solve_args *a) {
   if (a->L > 0) return a->L;
   double lmax = kso_power_iteration(a->X, a->x_dtype, a->n, a->p, a->ldx, 1e-10, 10000, NULL);
+  if (a->loss == KSO_LOSS_POISSON || a->loss == KSO_LOSS_GAMMA)
+    return lmax * (1.0 + 1e-6) * curvature_bound(a);
   double cf = (a->loss == KSO_LOSS_LOGISTIC) ? 0.25 : 2.0;
   if (a->eig > 0) return 2.0 * (lmax * (1.0 + 1e-6) - a->eig);   /* R20 */
   return cf * lmax * (1.0 + 1e-6);
@@ -551,11 +611,15 @@ int kso_solve(const kso_solve_args *a, double *beta, double *z, double *trace,
   double *grad = (double *)malloc((size_t)p * sizeof(double));
   double *u = (double *)malloc((size_t)n * sizeof(double));
   double *r = (double *)malloc((size_t)n * sizeof(double));
+  double l1 = 0.0;
   for (int64_t j = 0; j < p; ++j) {
     double x = a->warm ? a->warm[j] : 0.0;
     if (a->state && a->state[j] == KSO_ZERO) x = 0.0;
     b_old[j] = b[j] = fmin(fmax(x, -a->M), a->M);
+    l1 += fabs(b[j]);
   }
+  if ((a->loss == KSO_LOSS_POISSON || a->loss == KSO_LOSS_GAMMA) && l1 > (double)a->k * a->M)
+    for (int64_t j = 0; j < p; ++j) b_old[j] = b[j] = b[j] * ((double)a->k * a->M / l1);   /* R22 */
   kso_matvec(a->X, a->x_dtype, n, p, a->ldx, b, u);
   double obj = objective_at(a, b, u);
   double phi = 1.0, D = -INFINITY, gap = INFINITY;

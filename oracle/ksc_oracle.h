@@ -36,8 +36,9 @@ extern "C" {
 #endif
 
 /* losses (App. D.1): least squares ||u - y||^2, logistic sum log(1 + e^{-y u}),
- * squared hinge sum max(0, 1 - y u)^2 (y in {-1, +1} for the last two) */
-enum { KSO_LOSS_LSQ = 0, KSO_LOSS_LOGISTIC = 1, KSO_LOSS_SQHINGE = 2 };
+ * squared hinge sum max(0, 1 - y u)^2 (y in {-1, +1} for those two), Poisson
+ * sum e^u - y u (y >= 0), Gamma sum y e^{-u} + u (y > 0) */
+enum { KSO_LOSS_LSQ = 0, KSO_LOSS_LOGISTIC = 1, KSO_LOSS_SQHINGE = 2, KSO_LOSS_POISSON = 3, KSO_LOSS_GAMMA = 4 };
 enum { KSO_X_F64 = 0, KSO_X_F32 = 1 };
 enum { KSO_FREE = 0, KSO_ZERO = 1, KSO_ONE = 2 };
 enum {
@@ -99,7 +100,8 @@ typedef struct {
   double lambda2, M; int64_t k;
   const int8_t *state;     /* length p or NULL */
   const double *warm;      /* length p or NULL */
-  double L;                /* <= 0: c_f * lambda_max(X^T X) * (1 + 1e-6) */
+  double L;                /* <= 0: c_f * lambda_max(X^T X) * (1 + 1e-6); Poisson and
+                              Gamma: the curvature bound of reading R22 */
   double tol;              /* relative gap target                      */
   int64_t max_iter;
   int32_t restart, momentum;   /* Algorithm 3 as printed: both 1      */

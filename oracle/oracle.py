@@ -20,7 +20,7 @@ _HDR = os.path.join(_HERE, "ksc_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "libksc_oracle.so")
 _OUT_OMP = os.path.join(_HERE, "_build", "libksc_oracle_omp.so")
 
-LOSS_LSQ, LOSS_LOGISTIC = 0, 1
+LOSS_LSQ, LOSS_LOGISTIC, LOSS_SQHINGE, LOSS_POISSON, LOSS_GAMMA = 0, 1, 2, 3, 4
 FREE, ZERO, ONE = 0, 1, 2
 STATUS = {0: "converged", 1: "max_iter", 2: "pruned", 3: "primal_below", 4: "infeasible"}
 

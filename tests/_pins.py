@@ -183,7 +183,7 @@ def ridge_box(X, y, lam, M, loss=0):
     logistic and squared hinge via L-BFGS-B)."""
     n, s = X.shape
     if s == 0:
-        return float({0: y @ y, 1: n * np.log(2.0), 2: n}[loss]), np.zeros(0)
+        return float({0: y @ y, 1: n * np.log(2.0), 2: n, 3: n, 4: y.sum()}[loss]), np.zeros(0)
     if loss == 0:
         A = np.vstack([X, np.sqrt(lam) * np.eye(s)])
         rhs = np.concatenate([y, np.zeros(s)])
@@ -195,6 +195,14 @@ def ridge_box(X, y, lam, M, loss=0):
         if loss == 2:                      # squared hinge, C^1: L-BFGS-B still applies
             m = np.maximum(0.0, 1.0 - y * (X @ b))
             return float(m @ m + lam * b @ b), X.T @ (-2.0 * y * m) + 2 * lam * b
+        if loss == 3:                      # Poisson: e^u - y u
+            u = X @ b
+            e = np.exp(u)
+            return float(np.sum(e - y * u) + lam * b @ b), X.T @ (e - y) + 2 * lam * b
+        if loss == 4:                      # Gamma: y e^-u + u
+            u = X @ b
+            e = y * np.exp(-u)
+            return float(np.sum(e + u) + lam * b @ b), X.T @ (1.0 - e) + 2 * lam * b
         t = -y * (X @ b)
         v = np.logaddexp(0, t).sum() + lam * b @ b
         sg = 1.0 / (1.0 + np.exp(-t))
@@ -261,6 +269,10 @@ def conj_numeric(loss, zeta, y):
             f = lambda u: (u - yi) ** 2 + zi * u
         elif loss == 2:
             f = lambda u: max(0.0, 1.0 - yi * u) ** 2 + zi * u
+        elif loss == 3:
+            f = lambda u: np.exp(u) - yi * u + zi * u
+        elif loss == 4:
+            f = lambda u: yi * np.exp(-u) + u + zi * u
         else:
             f = lambda u: np.logaddexp(0, -yi * u) + zi * u
         r = optimize.minimize_scalar(f, bounds=(-60, 60), method="bounded",

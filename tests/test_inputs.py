@@ -86,3 +86,18 @@ def test_serving_mix_and_arrivals():
     assert np.all(np.diff(t) > 0) and t[0] >= 0 and t[-1] < 40.0
     assert abs(len(t) / 40.0 - 50.0) < 4 * np.sqrt(50.0 / 40.0) + 1     # Poisson count within 4 sigma
     assert np.array_equal(t, G.poisson_arrivals(50.0, 40.0, seed=2))
+
+
+def test_count_responses_unit_norm_columns_and_label_ranges():
+    # Poisson counts are non-negative integers, Gamma responses positive; both use
+    # unit-norm columns; BF16 storage rounds the same matrix
+    for loss in (G.POISSON, G.GAMMA):
+        P = G.make_problem(300, 40, seed=4, loss=loss, k_true=3)
+        assert np.allclose(np.linalg.norm(P.X, axis=0), 1.0, atol=1e-12)
+        if loss == G.POISSON:
+            assert np.all(P.y >= 0) and np.all(P.y == np.round(P.y)) and P.y.sum() > 0
+        else:
+            assert np.all(P.y > 0)
+        Pb = G.make_problem(300, 40, seed=4, loss=loss, k_true=3, x_dtype=G.BF16)
+        assert np.array_equal(Pb.y, P.y)
+        assert np.max(np.abs(Pb.X64() - P.X)) <= 2.0 ** -8 * np.abs(P.X).max()

@@ -542,3 +542,115 @@ def test_eig_bound_is_the_mip_optimum_for_orthogonal_columns():
         assert abs(O.dual_bound(X, y, 0, lam, M, k, beta, eig=eig) - closed) <= 1e-8 * closed
     persp = O.solve(X, y, 0, lam, M, k, tol=1e-12, max_iter=100000)
     assert persp.dual < closed - 1e-3 * closed    # the perspective relaxation is not tight here
+
+
+# ------------------------------------------- Poisson and Gamma regression (App. D.1)
+
+def _count_problem(loss, n, p, seed, k_true=3):
+    """Unit-norm columns, log link (as the input generator draws them)."""
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, p))
+    X /= np.linalg.norm(X, axis=0)
+    bt = np.zeros(p)
+    bt[rng.choice(p, k_true, replace=False)] = rng.choice([-3.0, 3.0], k_true)
+    mu = np.exp(X @ bt)
+    y = rng.poisson(mu).astype(float) if loss == 3 else rng.gamma(2.0, mu / 2.0)
+    return X, y
+
+
+@pytest.mark.parametrize("loss", [3, 4])
+def test_count_losses_conjugate_vs_numeric_inf(loss):
+    # -F*(-zeta) = inf_u F(u) + zeta^T u, inside the conjugate's domain
+    rng = np.random.default_rng(1600 + loss)
+    n = 12
+    if loss == 3:
+        y = rng.poisson(2.0, n).astype(float)
+        zeta = y - rng.uniform(0.05, 4.0, n)          # y - zeta > 0
+    else:
+        y = rng.gamma(2.0, 1.0, n)
+        zeta = rng.uniform(-0.95, 3.0, n)             # 1 + zeta > 0
+    assert abs(O.neg_conj(loss, zeta, y) - P.conj_numeric(loss, zeta, y)) < 1e-7
+
+
+@pytest.mark.parametrize("loss", [3, 4])
+def test_count_losses_domain_fenchel_young_and_gradients(loss):
+    rng = np.random.default_rng(1650 + loss)
+    n = 14
+    y = rng.poisson(1.5, n).astype(float) if loss == 3 else rng.gamma(2.0, 1.0, n)
+    # outside the domain the infimum is unbounded below
+    bad = np.zeros(n)
+    if loss == 3:
+        bad[:] = y - 1.0
+        bad[2] = y[2] + 0.5                            # y - zeta < 0
+    else:
+        bad[:] = 0.5
+        bad[4] = -1.5                                  # 1 + zeta < 0
+    assert O.neg_conj(loss, bad, y) == -np.inf
+    # at zeta = -grad F(u): Fenchel-Young with equality, elsewhere >=
+    u = 0.7 * rng.standard_normal(n)
+    zeta = -O.loss_grad(loss, u, y)
+    assert abs(O.loss(loss, u, y) + zeta @ u - O.neg_conj(loss, zeta, y)) < 1e-12 * n
+    for _ in range(20):
+        v = rng.standard_normal(n)
+        assert O.loss(loss, v, y) + zeta @ v >= O.neg_conj(loss, zeta, y) - 1e-12
+    # gradient by central differences
+    g = O.loss_grad(loss, u, y)
+    h = 1e-6
+    for i in range(n):
+        e = np.zeros(n)
+        e[i] = h
+        fd = (O.loss(loss, u + e, y) - O.loss(loss, u - e, y)) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(g[i]))
+
+
+@pytest.mark.parametrize("loss", [3, 4])
+def test_count_losses_k_equals_p_is_box_ridge_glm(loss):
+    # k = p: the relaxation is the box-constrained ridge Poisson / Gamma regression
+    X, y = _count_problem(loss, 60, 6, 1700 + loss)
+    lam, M = 0.3, 1.5
+    r = O.solve(X, y, loss, lam, M, 6, tol=1e-13, max_iter=200000)
+    v, b = P.ridge_box(X, y, lam, M, loss=loss)
+    assert r.status == "converged"
+    assert abs(r.primal - v) < 1e-8 * abs(v)
+    assert np.max(np.abs(r.beta - b)) < 1e-5
+
+
+@pytest.mark.parametrize("loss", [3, 4])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_count_losses_weak_duality_against_mip_enumeration(loss, seed):
+    X, y = _count_problem(loss, 40, 8, 1750 + 10 * loss + seed)
+    lam, M, k = 0.4, 2.0, 3
+    r = O.solve(X, y, loss, lam, M, k, tol=1e-12, max_iter=200000)
+    mip = P.mip_enumerate(X, y, lam, M, k, loss)
+    assert r.status == "converged"
+    assert r.dual <= r.primal + 1e-9 * abs(r.primal)
+    assert r.primal <= mip * (1 + 1e-9)
+    # with fixed sets
+    st = np.zeros(8, np.int8)
+    st[[1, 5]] = O.ZERO
+    st[2] = O.ONE
+    rn = O.solve(X, y, loss, lam, M, k, state=st, tol=1e-12, max_iter=200000)
+    mipn = P.mip_enumerate(X, y, lam, M, k, loss, zero=[1, 5], one=[2])
+    assert rn.dual <= rn.primal + 1e-9 * abs(rn.primal) and rn.primal <= mipn * (1 + 1e-9)
+    assert rn.dual >= r.dual - 1e-9 * abs(r.dual)     # a child's bound is not below the root's optimum
+
+
+@pytest.mark.parametrize("loss", [3, 4])
+def test_count_losses_curvature_bound_holds_where_the_iteration_steps(loss):
+    # the step constant of reading R22 bounds the Hessian X^T diag(F'') X at any point
+    # within three times the largest |x_i^T b| of the box-and-l1 set
+    X, y = _count_problem(loss, 50, 10, 1800 + loss)
+    lam, M, k = 0.5, 1.2, 3
+    L = O.solve(X, y, loss, lam, M, k, tol=1e-6, max_iter=5).L
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        b = rng.uniform(-M, M, 10)
+        b *= min(1.0, k * M / np.abs(b).sum())
+        bp = rng.uniform(-M, M, 10)
+        bp *= min(1.0, k * M / np.abs(bp).sum())
+        c = rng.uniform(0.0, 1.0)
+        g = b + c * (b - bp)                              # an extrapolated point
+        u = X @ g
+        curv = np.exp(u) if loss == 3 else y * np.exp(-u)
+        H = X.T @ (curv[:, None] * X)
+        assert np.linalg.eigvalsh(H)[-1] <= L * (1 + 1e-9)
