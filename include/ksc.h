@@ -59,7 +59,9 @@ typedef enum {
 typedef enum {
   KSC_LOSS_LSQ = 0,             /* F(u) = ||u - y||^2                     (App. D.1) */
   KSC_LOSS_LOGISTIC = 1,        /* F(u) = sum log(1 + exp(-y_i u_i)), y = +-1        */
-  KSC_LOSS_SQHINGE = 2          /* F(u) = sum max(0, 1 - y_i u_i)^2, y = +-1         */
+  KSC_LOSS_SQHINGE = 2,         /* F(u) = sum max(0, 1 - y_i u_i)^2, y = +-1         */
+  KSC_LOSS_POISSON = 3,         /* F(u) = sum e^{u_i} - y_i u_i, y >= 0 (App. D.1)  */
+  KSC_LOSS_GAMMA = 4            /* F(u) = sum y_i e^{-u_i} + u_i, y > 0 (App. D.1)  */
 } ksc_loss;
 
 typedef enum {
@@ -98,7 +100,8 @@ typedef struct {
                            x_on_device = 1: device pointer, BORROWED -- it must stay
                            valid and unchanged until ksc_problem_destroy.          */
   int64_t ldx;          /* leading dimension in elements, >= p; 0 means p         */
-  const double* y;      /* host pointer, length n, always copied; logistic: +-1    */
+  const double* y;      /* host pointer, length n, always copied; logistic and
+                           squared hinge: +-1; Poisson: >= 0; Gamma: > 0          */
   ksc_loss loss;
   int32_t x_on_device;
   double lipschitz;     /* > 0: the step constant L of Algorithm 3 to use.
@@ -108,7 +111,14 @@ typedef struct {
                            move it by at most 1e-5 of itself.  theta is a lower
                            estimate of lambda_max, so L is an estimate, not a proven
                            upper bound; L only changes the iteration's path, every
-                           reported bound is valid for any L                      */
+                           reported bound is valid for any L.  Poisson and Gamma:
+                           their curvature is unbounded, so each node's L is
+                           theta * 1.01 * max_i c_i, c_i = e^{3 U_i} (Poisson) or
+                           y_i e^{3 U_i} (Gamma), U_i = M min(k max_j |x_ij|,
+                           sum_j |x_ij|) -- the curvature over every point the
+                           iteration evaluates (its iterates satisfy |b_j| <= M,
+                           sum |b_j| <= kM; warm starts are scaled into that set);
+                           a caller's L > 0 is used for every node as given     */
   const float* col_scale; /* KSC_FP8_E4M3_COLSCALE: host pointer, p scales (copied);
                            NULL for the other types                                */
 } ksc_problem_desc;

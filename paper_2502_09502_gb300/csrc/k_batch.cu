@@ -55,6 +55,8 @@ __device__ __forceinline__ double loss_d(double u, double y, int loss) {
     const double m = fmax(0.0, 1.0 - y * u);
     return m * m;
   }
+  if (loss == kLossPoisson) return exp(u) - y * u;
+  if (loss == kLossGamma) return y * exp(-u) + u;
   const double t = -y * u;
   return t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
 }
@@ -97,6 +99,18 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
         const double z = 2.0 * (double)y * mg;          // zeta = -grad F, y zeta = 2 m >= 0
         nc += (double)y * z - 0.25 * z * z;
         term = 0.0f;
+      } else if (d.loss == kLossPoisson) {
+        // grad F = e^u - y: the difference e^{u_ref} expm1(u - u_ref) without
+        // cancellation; -F*(-zeta) = e^u (1 - u)
+        const float eg = expf((float)ug);
+        dr = expf((float)__ldg(&Ur[i])) * expm1f((float)du);
+        term = eg * (1.0f - (float)ug);
+      } else if (d.loss == kLossGamma) {
+        // grad F = 1 - y e^-u: the difference -y e^{-u_ref} expm1(-(u - u_ref));
+        // with w = y e^-u, -F*(-zeta) = w (1 + u)
+        const float wg = y * expf(-(float)ug);
+        dr = -y * expf(-(float)__ldg(&Ur[i])) * expm1f(-(float)du);
+        term = wg * (1.0f + (float)ug);
       } else {
         // grad F = -y sigma(t), t = -y u;  sigma(t) - sigma(t_ref)
         //   = sigma(t) (1 - sigma(t_ref)) (1 - e^{-(t - t_ref)})
@@ -374,6 +388,8 @@ __global__ void __launch_bounds__(256) k_banchor_resid(BatchDev d, const int* li
     const double u = ur[i], y = d.y[i];
     rr[i] = d.loss == kLossLsq       ? 2.0 * (u - y)
             : d.loss == kLossSqHinge ? -2.0 * y * fmax(0.0, 1.0 - y * u)
+            : d.loss == kLossPoisson ? exp(u) - y
+            : d.loss == kLossGamma   ? 1.0 - y * exp(-u)
                                      : -y * sigmoid_d(-y * u);
     if (init) {
       U[i] = u;
@@ -441,6 +457,21 @@ __global__ void __launch_bounds__(kBThreads) k_bcert_rows(BatchDev d, const int*
       z[i] = zi;
       nc += yi * zi - 0.25 * zi * zi;
       mg += fabs(yi * zi) + 0.25 * zi * zi;
+      zsq += zi * zi;
+    } else if (d.loss == kLossPoisson || d.loss == kLossGamma) {
+      // zeta = -grad F(u); -F*(-zeta) evaluated at this FP64 zeta as the conjugate
+      // defines it (App. D.1, the Gamma argument read at -zeta): z = y - zeta or
+      // (1 + zeta) / y, minus h(z) (times y for Gamma), h(z) = z log z - z
+      const bool poi = d.loss == kLossPoisson;
+      const double e = poi ? exp(ui) : yi * exp(-ui);
+      f += poi ? e - yi * ui : e + ui;
+      const double zi = poi ? yi - e : e - 1.0;
+      z[i] = zi;
+      const double w = poi ? yi - zi : 1.0 + zi;        // >= 0 by monotone rounding
+      const double arg = poi ? w : w / yi;
+      const double lg = arg > 0.0 ? log(arg) : 0.0;
+      nc -= arg > 0.0 ? w * lg - w : 0.0;
+      mg += 4.0 * (fabs(w * lg) + fabs(w)) + 4.0 * fabs(w);
       zsq += zi * zi;
     } else {
       const double t = -yi * ui;

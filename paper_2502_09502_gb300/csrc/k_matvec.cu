@@ -141,6 +141,16 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         r = -2.0 * yi * m;
         const double z = -r;                        // y z = 2 m >= 0: in dom F*
         nc += yi * z - 0.25 * z * z;
+      } else if (d.loss == kLossPoisson) {
+        // grad F = e^u - y; -F*(-zeta) = -h(y - zeta) = -h(e^u) = e^u (1 - u)
+        const double e = exp(ug);
+        r = e - yi;
+        nc += e * (1.0 - ug);
+      } else if (d.loss == kLossGamma) {
+        // grad F = 1 - y e^-u; with w = y e^-u = 1 + zeta, -F*(-zeta) = -y h(w/y) = w (1 + u)
+        const double w = yi * exp(-ug);
+        r = 1.0 - w;
+        nc += w * (1.0 + ug);
       } else {
         const double s = sigmoid(-yi * ug);
         r = -yi * s;
@@ -355,6 +365,28 @@ __device__ __forceinline__ void row_epilogue(const Dev& d, int row, double u, in
       d.zeta[row] = z;
       a.nc += yi * z - 0.25 * z * z;
       a.mg += fabs(yi * z) + 0.25 * z * z;
+      a.zsq += z * z;
+    }
+  } else if (d.loss == kLossPoisson || d.loss == kLossGamma) {
+    const bool poi = d.loss == kLossPoisson;
+    const double e = poi ? exp(u) : yi * exp(-u);
+    a.f += poi ? e - yi * u : e + u;
+    if (MODE == kFCert) {
+      // zeta = -grad F(u) = y - e^u (Poisson) or y e^-u - 1 (Gamma); the bound
+      // evaluates -F*(-zeta) at this FP64 zeta exactly as the conjugate defines it
+      // (App. D.1, reading R22): z = y - zeta or (1 + zeta) / y, -sum y^{0|1} h(z)
+      const double z = poi ? yi - e : e - 1.0;
+      const double w = poi ? yi - z : 1.0 + z;        // >= 0 by monotone rounding
+      const double arg = poi ? w : w / yi;
+      const double lg = arg > 0.0 ? log(arg) : 0.0;
+      const double t = arg > 0.0 ? w * lg - w : 0.0;  // h(arg), times y for Gamma
+      d.u64[row] = u;
+      d.zeta[row] = z;
+      a.nc -= t;
+      // rounding of one term in units of u (the subtraction or quotient forming
+      // its argument, log within 2 ulp, a product and a difference): the margin is
+      // (n+8) u * sum(mg)
+      a.mg += 4.0 * (fabs(w * lg) + fabs(w)) + 4.0 * fabs(w);
       a.zsq += z * z;
     }
   } else {
@@ -897,6 +929,36 @@ void launch_transpose(const Dev& d, cudaStream_t s) {
   else
     k_transpose<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16*)d.X, d.ldx,
                                                      (__nv_bfloat16*)d.Xc, d.ldc, d.n, d.p);
+}
+
+// Row statistics for the step constant of Poisson and Gamma regression: per row i
+// of the matrix the solver uses (X_ij, times s_j for FP8), the largest |x_ij| and
+// sum_j |x_ij| (FP64), one CTA per row
+template <typename TX>
+__global__ void __launch_bounds__(256) k_rowstats(Dev d, double* rmax, double* rl1) {
+  __shared__ double red[64];
+  const int i = blockIdx.x;
+  const TX* row = (const TX*)d.X + (size_t)i * d.ldx;
+  double m = 0.0, s1 = 0.0;
+  for (int j = threadIdx.x; j < d.p; j += 256) {
+    double v = fabs(xval<double>(row[j]));
+    if (d.xscale) v *= (double)d.xscale[j];
+    m = fmax(m, v);
+    s1 += v;
+  }
+  m = block_max<double, 256>(m, red, 0.0);
+  s1 = block_sum<double, 256>(s1, red);
+  if (threadIdx.x == 0) {
+    rmax[i] = m;
+    rl1[i] = s1 * (1.0 + (double)(d.p + 2) * 1.1102230246251565e-16);   // rounded up
+  }
+}
+
+void launch_rowstats(const Dev& d, double* rmax, double* rl1, cudaStream_t s) {
+  if (d.xdt == kXF64) k_rowstats<double><<<d.n, 256, 0, s>>>(d, rmax, rl1);
+  else if (d.xdt == kXF32) k_rowstats<float><<<d.n, 256, 0, s>>>(d, rmax, rl1);
+  else if (d.xdt == kXFP8) k_rowstats<__nv_fp8_e4m3><<<d.n, 256, 0, s>>>(d, rmax, rl1);
+  else k_rowstats<__nv_bfloat16><<<d.n, 256, 0, s>>>(d, rmax, rl1);
 }
 
 void launch_colnorm(const Dev& d, cudaStream_t s) {

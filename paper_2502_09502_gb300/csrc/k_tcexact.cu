@@ -330,14 +330,16 @@ __global__ void __launch_bounds__(kTcxThreads, 1)
 #pragma unroll
       for (int j = 0; j < 16; ++j)
         zh[j] += (long long)(__float2int_rz(__uint_as_float(a[j])) * 256 + __float2int_rz(__uint_as_float(b[j])));
-      // diagonals 6, 7 in units of 2^-40: acc_6 2^-8 + acc_7 2^-16, rounded
+      // diagonals 6, 7 in units of 2^-40: acc_6 2^-8 + acc_7 2^-16 (below 2^16),
+      // rounded to an int32 on the FP32 pipe (64-bit conversions would run on the
+      // slow FP64 one)
       tmem_ld16_nowait(tb + 6 * kTcxBN, a);
       tmem_ld16_nowait(tb + 7 * kTcxBN, b);
       tmem_wait_ld();
 #pragma unroll
       for (int j = 0; j < 16; ++j)
-        zl[j] += __float2ll_rn(__fmaf_rn(__uint_as_float(a[j]), 0.00390625f,
-                                         __uint_as_float(b[j]) * 1.52587890625e-05f));
+        zl[j] += (long long)__float2int_rn(__fmaf_rn(__uint_as_float(a[j]), 0.00390625f,
+                                                     __uint_as_float(b[j]) * 1.52587890625e-05f));
       // diagonals 2, 3: acc_2 2^24 + acc_3 2^16
       tmem_ld16_nowait(tb + 2 * kTcxBN, a);
       tmem_ld16_nowait(tb + 3 * kTcxBN, b);

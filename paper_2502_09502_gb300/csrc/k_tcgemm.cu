@@ -50,6 +50,8 @@ __device__ __forceinline__ float loss_term(float u, float y, int loss) {
     const float r = u - y;
     return r * r;
   }
+  if (loss == kLossPoisson) return expf(u) - y * u;
+  if (loss == kLossGamma) return y * expf(-u) + u;
   const float t = -y * u;
   return fmaxf(t, 0.0f) + log1pf(expf(-fabsf(t)));
 }
@@ -70,7 +72,8 @@ __device__ __forceinline__ void add_loss(double u, float y, int loss, double& fd
 
 // F_i(u + d) - F_i(u) without cancellation: least squares d (2 (u - y) + d);
 // squared hinge with s = 1 - y u, t = -y d: t (2 s + t) where s and s + t are
-// both positive, else max(0, s + t)^2 - max(0, s)^2; logistic
+// both positive, else max(0, s + t)^2 - max(0, s)^2; Poisson e^u expm1(d) - y d;
+// Gamma y e^-u expm1(-d) + d; logistic
 // log1p(expm1(-y d) sigma(-y u)), since
 // (1 + e^{-y(u+d)}) / (1 + e^{-y u}) = 1 + (e^{-y d} - 1) e^{-y u} / (1 + e^{-y u})
 __device__ __forceinline__ float loss_change(double u, float d, float y, int loss) {
@@ -84,6 +87,8 @@ __device__ __forceinline__ float loss_change(double u, float d, float y, int los
     const float m = fmaxf(s, 0.0f), mn = fmaxf(s + t, 0.0f);
     return mn * mn - m * m;
   }
+  if (loss == kLossPoisson) return expf((float)u) * expm1f(d) - y * d;            // e^u (e^d - 1) - y d
+  if (loss == kLossGamma) return y * expf(-(float)u) * expm1f(-d) + d;         // y e^-u (e^-d - 1) + d
   if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
   const float s = 1.0f / (1.0f + expf(y * (float)u));   // sigma(-y u)
   return log1pf(expm1f(-y * d) * s);

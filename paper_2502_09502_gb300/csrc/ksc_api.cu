@@ -218,10 +218,43 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-5 * theta)) break;
     prev = theta;
   }
-  // F' is 2-Lipschitz for least squares and the squared hinge, 1/4 for logistic
-  const double cf = pr->loss == KSC_LOSS_LOGISTIC ? 0.25 : 2.0;
+  // F' is 2-Lipschitz for least squares and the squared hinge, 1/4 for logistic;
+  // Poisson and Gamma: lambda_max alone here, each node multiplies in its
+  // curvature bound (node_lipschitz)
+  const double cf = pr->loss == KSC_LOSS_LOGISTIC ? 0.25 : (loss_counts(pr->loss) ? 1.0 : 2.0);
   pr->L = cf * theta * 1.01;
   return KSC_OK;
+}
+
+bool ksc::loss_counts(int loss) { return loss == KSC_LOSS_POISSON || loss == KSC_LOSS_GAMMA; }
+
+// Poisson and Gamma regression have no global Lipschitz constant (their curvature
+// is e^u, y e^-u).  Every iterate lies in {|b_j| <= M, sum |b_j| <= kM}, where
+// |x_i^T b| <= U_i = M min(k max_j |x_ij|, sum_j |x_ij|), and the extrapolated
+// point of a step within 3 U_i; there the Hessian of F(X b) is at most
+// lambda_max(X^T X) max_i c_i with c_i = e^{3 U_i} or y_i e^{3 U_i}.
+double ksc::node_lipschitz(const ksc_problem* pr, double M, int k) {
+  if (!loss_counts(pr->loss) || pr->l_fixed) return pr->L;
+  double lc = -INFINITY;   // log max_i c_i
+  for (int64_t i = 0; i < pr->n; ++i) {
+    const double U = M * std::min((double)k * pr->row_max[i], pr->row_l1[i]);
+    double l = 3.0 * U * (1.0 + 1e-12);
+    if (pr->loss == KSC_LOSS_GAMMA) l += std::log(pr->y_host[i]);
+    lc = std::max(lc, l);
+  }
+  return pr->L * std::exp(lc) * (1.0 + 1e-12);
+}
+
+void ksc::project_warm(const ksc_problem* pr, const NodeSetup& ns, double M, int k, double* b) {
+  double l1 = 0.0;
+  for (int64_t j = 0; j < pr->p; ++j) {
+    b[j] = ns.state[j] == kZero ? 0.0 : std::min(M, std::max(-M, b[j]));
+    l1 += std::fabs(b[j]);
+  }
+  if (loss_counts(pr->loss) && l1 > (double)k * M) {
+    const double sc = (double)k * M / l1 * (1.0 - 1e-15);
+    for (int64_t j = 0; j < pr->p; ++j) b[j] *= sc;
+  }
 }
 
 extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cuda_stream,
@@ -246,7 +279,8 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
         return fail(KSC_ERR_INVALID_ARG, "col_scale entries must be powers of two in [2^-100, 2^100]");
     }
   }
-  if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC && desc->loss != KSC_LOSS_SQHINGE)
+  if (desc->loss != KSC_LOSS_LSQ && desc->loss != KSC_LOSS_LOGISTIC && desc->loss != KSC_LOSS_SQHINGE &&
+      desc->loss != KSC_LOSS_POISSON && desc->loss != KSC_LOSS_GAMMA)
     return fail(KSC_ERR_INVALID_ARG, "unknown loss");
   if (!desc->X || !desc->y) return fail(KSC_ERR_INVALID_ARG, "X and y must be non-NULL");
   const int64_t ldx = desc->ldx == 0 ? desc->p : desc->ldx;
@@ -254,8 +288,12 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   for (int64_t i = 0; i < desc->n; ++i) {
     const double v = desc->y[i];
     if (!std::isfinite(v)) return fail(KSC_ERR_INVALID_ARG, "y has a non-finite entry");
-    if (desc->loss != KSC_LOSS_LSQ && v != 1.0 && v != -1.0)
+    if ((desc->loss == KSC_LOSS_LOGISTIC || desc->loss == KSC_LOSS_SQHINGE) && v != 1.0 && v != -1.0)
       return fail(KSC_ERR_INVALID_ARG, "logistic and squared-hinge labels must be +1 or -1");
+    if (desc->loss == KSC_LOSS_POISSON && !(v >= 0.0))
+      return fail(KSC_ERR_INVALID_ARG, "Poisson responses must be >= 0");
+    if (desc->loss == KSC_LOSS_GAMMA && !(v > 0.0))
+      return fail(KSC_ERR_INVALID_ARG, "Gamma responses must be > 0");
   }
   ksc_status st = ensure_prepared();
   if (st != KSC_OK) return st;
@@ -320,8 +358,22 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   if (cudaGetLastError() != cudaSuccess) return bail(fail(KSC_ERR_CUDA, "colnorm launch failed"));
   if (desc->lipschitz > 0) {
     pr->L = desc->lipschitz;
+    pr->l_fixed = true;
   } else if ((st = lanczos_lmax(pr, s)) != KSC_OK) {
     return bail(st);
+  }
+  if (loss_counts(pr->loss) && !pr->l_fixed) {
+    // the rows' largest entries and absolute sums, for each node's step constant
+    double* rs = nullptr;
+    if ((st = dmalloc(pr, &rs, (size_t)pr->n * 16)) != KSC_OK) return bail(st);
+    launch_rowstats(d, rs, rs + pr->n, s);
+    pr->launches += 1;
+    pr->row_max.resize(pr->n);
+    pr->row_l1.resize(pr->n);
+    cudaError_t e1 = cudaMemcpyAsync(pr->row_max.data(), rs, (size_t)pr->n * 8, cudaMemcpyDeviceToHost, s);
+    if (e1 == cudaSuccess)
+      e1 = cudaMemcpyAsync(pr->row_l1.data(), rs + pr->n, (size_t)pr->n * 8, cudaMemcpyDeviceToHost, s);
+    if (e1 != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("row statistics: ") + cudaGetErrorString(e1)));
   }
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return bail(fail(KSC_ERR_CUDA, std::string("problem setup: ") + cudaGetErrorString(e)));
@@ -493,11 +545,14 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   if (cur_dev != pr->device) KSC_CUDA(cudaSetDevice(pr->device));
   Dev& d = pr->dev;
   const int64_t p = pr->p;
-  // warm start projected on the node: S0 -> 0, clip to the box (reading of Algorithm 3's start)
+  // warm start projected on the node: S0 -> 0, clip to the box (reading of Algorithm
+  // 3's start); Poisson / Gamma: scaled into the l1 ball of radius k M as well
   std::vector<double> w0(p, 0.0);
-  if (node->warm_beta)
-    for (int64_t j = 0; j < p; ++j)
-      w0[j] = ns.state[j] == kZero ? 0.0 : std::min(node->M, std::max(-node->M, node->warm_beta[j]));
+  if (node->warm_beta) {
+    for (int64_t j = 0; j < p; ++j) w0[j] = node->warm_beta[j];
+    project_warm(pr, ns, node->M, node->k, w0.data());
+  }
+  const double Lnode = node_lipschitz(pr, node->M, node->k);
   std::vector<unsigned char> wb;
   fill_slots<double>(wb, w0);
   const size_t tb = tbytes(pr->xdt);
@@ -514,9 +569,9 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   std::memset(&h, 0, sizeof h);
   h.lambda2 = node->lambda2;
   h.M = node->M;
-  h.L = pr->L;
-  h.invL = 1.0 / pr->L;
-  h.rho = pr->L / (2.0 * node->lambda2);
+  h.L = Lnode;
+  h.invL = 1.0 / Lnode;
+  h.rho = Lnode / (2.0 * node->lambda2);
   h.tol_loop = node->rel_gap_tol;
   h.incumbent = node->incumbent;
   h.kp = ns.kp;

@@ -607,8 +607,11 @@ ksc_status zero_anchor_prepare(Session* se) {
   const int n = (int)pr->n;
   std::vector<double> r0(n);
   for (int i = 0; i < n; ++i)
-    // grad F at u = 0: least squares -2 y, squared hinge -2 y (margin 1), logistic -y/2
-    r0[i] = pr->loss == KSC_LOSS_LOGISTIC ? -0.5 * pr->y_host[i] : -2.0 * pr->y_host[i];
+    // grad F at u = 0: least squares -2 y, squared hinge -2 y (margin 1), logistic
+    // -y/2, Poisson 1 - y (e^0 - y), Gamma 1 - y (1 - y e^0)
+    r0[i] = pr->loss == KSC_LOSS_LOGISTIC ? -0.5 * pr->y_host[i]
+            : loss_counts(pr->loss)       ? 1.0 - pr->y_host[i]
+                                          : -2.0 * pr->y_host[i];
   cudaStream_t s = se->s;
   KB_CUDA(cudaMemcpyAsync(ws->r0, r0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
   const int zero_row = 0;
@@ -654,15 +657,16 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
       int8_t* hsr = hs.data() + (size_t)(i - c0) * ldp;
       double* hbr = hb.data() + (size_t)(i - c0) * ldp;
       std::memcpy(hsr, setup.state.data(), p);
-      if (nd->warm_beta)
-        for (int j = 0; j < p; ++j)
-          hbr[j] = setup.state[j] == kZero ? 0.0 : std::min(nd->M, std::max(-nd->M, nd->warm_beta[j]));
+      if (nd->warm_beta) {
+        std::memcpy(hbr, nd->warm_beta, (size_t)p * 8);
+        project_warm(pr, setup, nd->M, nd->k, hbr);
+      }
       BNode& h = hn[b];
       std::memset(&h, 0, sizeof h);
       // eigen-perspective (App. D.2): lambda2 + eig on the perspective term, the
       // smooth part's constant 2 (lambda_max - eig) <= L - 2 eig
       const double eig = (nd->flags & KSC_FLAG_EIG) ? pr->eig_lambda : 0.0;
-      const double Ln = pr->L - 2.0 * eig;
+      const double Ln = node_lipschitz(pr, nd->M, nd->k) - 2.0 * eig;
       h.lambda2 = nd->lambda2 + eig;
       h.eig = eig;
       h.M = nd->M;

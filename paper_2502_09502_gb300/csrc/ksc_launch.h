@@ -132,6 +132,8 @@ void launch_split(const double* src, float* hi, float* lo, int n, cudaStream_t s
 void launch_colnorm(const Dev& d, cudaStream_t s);
 // column-major copy Xc of X
 void launch_transpose(const Dev& d, cudaStream_t s);
+// per row of X: max_j |x_ij| and sum_j |x_ij| (the Poisson / Gamma step constant)
+void launch_rowstats(const Dev& d, double* rmax, double* rl1, cudaStream_t s);
 // set the kernels' dynamic shared memory limits, once per device (the first call
 // on each device does it under a lock; later calls return at once); returns the
 // first failing CUDA call's error, and the device is set up again on the next call

@@ -48,6 +48,11 @@ struct ksc_problem {
   std::vector<double> batch_state; // 10 in-loop values per node of the last batched call
   double eig_lambda = 0.0;         // certified lower bound on lambda_min(X^T X)
   bool eig_ready = false;          // eig_lambda computed (ksc_problem_eig_lambda)
+  // Poisson and Gamma regression: L above is lambda_max(X^T X) * 1.01 (or the
+  // caller's constant, l_fixed); each node multiplies it by its curvature bound
+  // from the rows' largest entries and absolute sums
+  bool l_fixed = false;
+  std::vector<double> row_max, row_l1;
 };
 
 namespace ksc {
@@ -61,6 +66,14 @@ struct NodeSetup {
 };
 
 ksc_status check_node(const ksc_problem* pr, const ksc_node* node, NodeSetup* ns);
+// the step constant L of Algorithm 3 for a node (the problem's L, or for Poisson /
+// Gamma regression that L times max_i c_i, c_i = e^{3 U_i} or y_i e^{3 U_i},
+// U_i = M min(k max_j |x_ij|, sum_j |x_ij|))
+double node_lipschitz(const ksc_problem* pr, double M, int k);
+// warm start of a node in place: S0 coordinates 0, every coordinate clipped to the
+// box, and for Poisson / Gamma regression scaled into sum |b_j| <= k M
+void project_warm(const ksc_problem* pr, const NodeSetup& ns, double M, int k, double* b);
+bool loss_counts(int loss);
 ksc_status ensure_prepared();
 ksc_status api_fail(ksc_status st, const std::string& msg);
 

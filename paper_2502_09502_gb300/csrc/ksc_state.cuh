@@ -7,7 +7,7 @@
 namespace ksc {
 
 enum : int8_t { kFree = 0, kZero = 1, kOne = 2 };
-enum : int { kLossLsq = 0, kLossLogistic = 1, kLossSqHinge = 2 };
+enum : int { kLossLsq = 0, kLossLogistic = 1, kLossSqHinge = 2, kLossPoisson = 3, kLossGamma = 4 };
 
 // termination codes written by the fused restart/gap step
 enum : int {

@@ -59,9 +59,20 @@ def test_invalid_arguments_are_rejected_before_cuda(ksc):
                         ksc.KSC_LOSS_SQHINGE, 0, 0.0)
     assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
     assert "labels" in ksc.ksc_last_error()
-    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 3, 0, 0.0)
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 5, 0, 0.0)
     assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
     assert "loss" in ksc.ksc_last_error()
+    # Poisson responses >= 0, Gamma responses > 0 (checked before any CUDA call)
+    yneg = np.array([1.0, -2.0, 0.0])
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 4, yneg.ctypes.data_as(C.POINTER(C.c_double)),
+                        ksc.KSC_LOSS_POISSON, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "Poisson" in ksc.ksc_last_error()
+    yzero = np.array([1.0, 0.5, 0.0])
+    d = ksc.ProblemDesc(3, 4, ksc.KSC_F64, 1, 4, yzero.ctypes.data_as(C.POINTER(C.c_double)),
+                        ksc.KSC_LOSS_GAMMA, 0, 0.0)
+    assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
+    assert "Gamma" in ksc.ksc_last_error()
     # FP8 X: power-of-two column scales required (checked before any CUDA call)
     d = ksc.ProblemDesc(3, 4, ksc.KSC_FP8, 1, 4, y.ctypes.data_as(C.POINTER(C.c_double)), 0, 0, 0.0)
     assert ksc.lib.ksc_problem_create(C.byref(d), None, C.byref(out)) == ksc.KSC_ERR_INVALID_ARG
