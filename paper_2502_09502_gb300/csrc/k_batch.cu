@@ -166,8 +166,9 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
     __syncthreads();
   }
   // in-loop dual term at gamma: a = X^T zeta_gamma = -G, |a| = |G|
+  double gthr = 0.0;
   const double gs = gstar_segment<double, kBProxBlock>(p, [&](int i) { return G[i]; }, st, kp, M,
-                                                       0.5 / lambda2, sm);
+                                                       0.5 / lambda2, sm, nd->gthr, &gthr);
   SegIO<double> io;
   io.m = p;
   io.state = st;
@@ -189,6 +190,7 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   io.top_out = nullptr;
   io.qhint = nd->qhint;
   io.theta0 = nd->theta;
+  io.topk_hint = nd->ptop;
   const SegOut o = prox_segment<double, kBProxBlock>(io, sm);
   __syncthreads();
   // BF16 pieces of fl32(beta^{t+1} - beta_ref)
@@ -212,6 +214,8 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
     nd->negconj = nc + eig * gsq;
     nd->bsq_next = bsq;
     nd->gstar = gs;
+    nd->gthr = gthr;
+    nd->ptop = o.topk;
     nd->g_next = o.g;
     nd->theta = o.theta;
     nd->nnz = o.nnz;

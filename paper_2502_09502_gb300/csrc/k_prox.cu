@@ -148,6 +148,8 @@ k_prox_prim(const double* w, int p, int k, double M, double rho, double* beta, i
 // in place (every coordinate free, no copy); the first round of candidates is
 // sized for a pooled tail of a few times k.
 constexpr int kRowsBlock = 256, kRowsCap = 2048;
+static_assert(kRowsCap + 1 >= 2 * kRowsBlock && kProxCap + 1 >= 2 * kProxBlock,
+              "the prox's full-pass sums use the prefix buffer");
 
 __global__ void __launch_bounds__(kRowsBlock)
 k_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int k, double M, double rho) {

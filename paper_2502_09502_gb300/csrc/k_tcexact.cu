@@ -2,7 +2,7 @@
 // tensor cores (ksc_tcx.h): the anchors and certificates of the batched solver.
 //
 // One CTA computes a 128 x kTcxBN tile of D^T (128 rows c of A, kTcxBN vectors)
-// over a range of K blocks of 64:
+// over a range of K blocks of 64 (grid: vector tiles, row tiles, K splits):
 //   warp 0      TMA producer: per K block the 3 slices of the 128 rows of A and
 //               the 6 slices of the kTcxBN vectors land in one shared-memory
 //               stage (128-byte swizzle);
@@ -188,7 +188,7 @@ struct TcxOut {
   const int* list;
   const int* ex;
   const int* ev;
-  long long* part;   // split partials (gridDim.z > 1): ((z Rt + r) C + c) pairs, Rt = gridDim.y kTcxBN
+  long long* part;   // split partials (gridDim.z > 1): ((z Rt + r) C + c) pairs, Rt = gridDim.x kTcxBN
 };
 
 // instruction descriptor for M = 128, N = kTcxBN (kind::f16, BF16 A and B, FP32 D)
@@ -211,7 +211,9 @@ __global__ void __launch_bounds__(kTcxThreads, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c0 = blockIdx.x * kTcxBM, r0 = blockIdx.y * kTcxBN;
+  // blockIdx.x runs over the vector tiles, so the CTAs that share a tile of X's
+  // slices run together and X streams from DRAM about once
+  const int c0 = blockIdx.y * kTcxBM, r0 = blockIdx.x * kTcxBN;
   const int kb0 = blockIdx.z * sh.kbs;
   const int nb = max(0, min(sh.nkb, kb0 + sh.kbs) - kb0);
 
@@ -377,7 +379,7 @@ __global__ void __launch_bounds__(kTcxThreads, 1)
           }
         }
       } else {
-        const int64_t Rt = (int64_t)gridDim.y * kTcxBN;
+        const int64_t Rt = (int64_t)gridDim.x * kTcxBN;
 #pragma unroll
         for (int j = 0; j < kTcxNodesPerThread; ++j) {
           long long* pp = out.part + 2 * (((int64_t)blockIdx.z * Rt + rb + j) * sh.C + c);
@@ -641,7 +643,7 @@ void tcx_product(const TcxSlices& x, TcxVecs& v, const double* V, int64_t ldv, c
   k_tcx_slice_vecs<<<Rt, 256, 0, s>>>(V, ldv, list, R, x.K, v.sl, v.ld, v.Npad, v.ev);
   TcxShape sh{x.C, x.Cpad, R, v.Npad, p.nkb, p.kbs};
   TcxOut out{D, ldd, list, x.ex, v.ev, v.part};
-  dim3 grid(p.tc, p.tr, p.splits);
+  dim3 grid(p.tr, p.tc, p.splits);
   k_tcx<<<grid, kTcxThreads, kTcxSmem, s>>>(*(const CUtensorMap*)x.tm, *(const CUtensorMap*)v.tm, sh, out);
   if (p.splits > 1) {
     dim3 g2((x.C + 255) / 256 < 64 ? (x.C + 255) / 256 : 64, R);

@@ -38,6 +38,7 @@ constexpr int kBatchPieces = 3;     // BF16 pieces of an FP32 vector (exact sum)
 constexpr int kBatchCap = 2048;     // prox candidates per node in shared memory
 constexpr int kBatchMax = 1024;     // nodes per device pass
 constexpr int kBProxBlock = 256;    // threads of the per-node prox CTA
+static_assert(kBatchCap + 1 >= 2 * kBProxBlock, "the prox's full-pass sums use the prefix buffer");
 constexpr int kBThreads = 256;      // residual kernel
 constexpr int kBRows = 8;           // rows per residual thread
 constexpr int kSlotIdle = 5;        // BNode::done of an empty slot (every kernel skips it)
@@ -58,6 +59,8 @@ struct BNode {
   // lambda2 above is then lambda2 + eig, rho and invL those of L - 2 eig
   double eig;
   double bsq_cur, bsq_next;   // ||beta^t||^2, ||beta^{t+1}||^2
+  double gthr;                // the last in-loop dual term's k'-th largest |G_F| (0: none yet)
+  double ptop;                // the last prox's k'-th largest |w_F| (0: none yet)
 };
 
 // FP64 certificate of one node (copied out of the single-node workspace)

@@ -221,10 +221,12 @@ struct SegIO {
   int* top_out;              // optional: the top-k' indices in sorted order
   int qhint;                 // candidates to start from; above the capacity: full pass
   double theta0;             // previous theta (warm start of the full pass), or <= 0
+  double topk_hint = 0.0;    // previous k'-th largest |w| (> 0: gather above it first), or <= 0
 };
 
 struct SegOut {
   double g, theta, l1, sbar;
+  double topk;               // this call's k'-th largest |w| (the next call's topk_hint)
   int nnz, qused, fallback;
 };
 
@@ -237,20 +239,34 @@ struct SegOut {
 // breakpoint separates c from theta, which ends the iteration (usually one or two
 // passes from the previous step's theta); otherwise c, or the bisection point
 // when c leaves the bracket, is the next theta.  Phi(0) <= 0 <= Phi(hi0).
-// scratch: >= (BLOCK/32 + 1) * 8 64-bit words of shared memory.  *nb_out: the
-// active tail count at the root.
+// scratch: >= (BLOCK/32 + 2) * 8 64-bit words of shared memory; dsum: 2 BLOCK
+// doubles of shared memory (the candidates' prefix-sum buffer, free here).
+// *nb_out: the active tail count at the root.
 template <int BLOCK, typename KeyBits>
 __device__ double root_fullpass(int m, KeyBits keybits, double thr_k, int need_k, int eq_k, double hi0,
-                                double th0, double rho, double M, unsigned long long* scratch, int* nb_out) {
+                                double th0, double rho, double M, unsigned long long* scratch, double* dsum,
+                                int* nb_out) {
+  // FP64 issues at 1/64 of the FP32 rate here: the FP64 sums go through shared
+  // memory (dsum: 2 BLOCK doubles) to one warp (each value added once), and thread
+  // 0 alone runs the scalar Newton / bisection logic, broadcasting the next point's
+  // bit patterns
   using ULL = unsigned long long;
   constexpr int NW = BLOCK / 32;
+  static_assert((NW + 2) * 8 <= 1024, "root_fullpass scratch: the 2048-word histogram");
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const ULL thr_b = nnbits(thr_k);
-  double lo = 0.0, hi = hi0;
-  double th = (th0 > lo && th0 < hi) ? th0 : hi0;
+  ULL* wpart = scratch;                                        // NW x 8 warp partials
+  ULL* bc = wpart + NW * 8;                                    // broadcast: th, h bits, done, nB
+  // thread 0's state
+  double lo = 0.0, hi = hi0, th = (th0 > 0.0 && th0 < hi0) ? th0 : hi0;
+  if (threadIdx.x == 0) {
+    bc[0] = nnbits(th);
+    bc[1] = nnbits(th + fmin(rho * th, M));
+    bc[2] = 0ull;
+  }
+  __syncthreads();
   for (int it = 0; it < 100; ++it) {
-    const double h = th + fmin(rho * th, M);
-    const ULL tb = nnbits(th), hb = nnbits(h);
+    const ULL tb = bc[0], hb = bc[1];
     long long nA = 0, nB = 0;
     double SA = 0.0, SB = 0.0;
     // tail: max key <= theta, min key > theta; top: max key < h, min key >= h
@@ -269,73 +285,85 @@ __device__ double root_fullpass(int m, KeyBits keybits, double thr_k, int need_k
     for (int o = 16; o > 0; o >>= 1) {
       nA += __shfl_xor_sync(0xffffffffu, nA, o);
       nB += __shfl_xor_sync(0xffffffffu, nB, o);
-      SA += __shfl_xor_sync(0xffffffffu, SA, o);
-      SB += __shfl_xor_sync(0xffffffffu, SB, o);
       ULL v;
       v = __shfl_xor_sync(0xffffffffu, tl, o); tl = v > tl ? v : tl;
       v = __shfl_xor_sync(0xffffffffu, al, o); al = v > al ? v : al;
       v = __shfl_xor_sync(0xffffffffu, tg, o); tg = v < tg ? v : tg;
       v = __shfl_xor_sync(0xffffffffu, ag, o); ag = v < ag ? v : ag;
     }
+    dsum[threadIdx.x] = SA;
+    dsum[BLOCK + threadIdx.x] = SB;
     if (lane == 0) {
-      ULL* w = scratch + wid * 8;
+      ULL* w = wpart + wid * 8;
       w[0] = (ULL)nA; w[1] = (ULL)nB;
-      w[2] = (ULL)__double_as_longlong(SA); w[3] = (ULL)__double_as_longlong(SB);
       w[4] = tl; w[5] = tg; w[6] = al; w[7] = ag;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {   // warps in order: the same sums on every call
-      ULL* w = scratch;
-      long long a0 = 0, b0 = 0;
+    if (wid == 0) {   // fixed order: the same sums on every call
       double sa = 0.0, sb = 0.0;
-      ULL x4 = 0ull, x5 = ~0ull, x6 = 0ull, x7 = ~0ull;
-      for (int k = 0; k < NW; ++k, w += 8) {
-        a0 += (long long)w[0]; b0 += (long long)w[1];
-        sa += __longlong_as_double((long long)w[2]); sb += __longlong_as_double((long long)w[3]);
-        x4 = w[4] > x4 ? w[4] : x4; x5 = w[5] < x5 ? w[5] : x5;
-        x6 = w[6] > x6 ? w[6] : x6; x7 = w[7] < x7 ? w[7] : x7;
+      for (int k = lane; k < BLOCK; k += 32) { sa += dsum[k]; sb += dsum[BLOCK + k]; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
       }
-      ULL* r = scratch + NW * 8;
-      r[0] = (ULL)a0; r[1] = (ULL)b0;
-      r[2] = (ULL)__double_as_longlong(sa); r[3] = (ULL)__double_as_longlong(sb);
-      r[4] = x4; r[5] = x5; r[6] = x6; r[7] = x7;
+      if (lane == 0) {
+        long long a0 = 0, b0 = 0;
+        ULL x4 = 0ull, x5 = ~0ull, x6 = 0ull, x7 = ~0ull;
+        const ULL* w = wpart;
+        for (int k = 0; k < NW; ++k, w += 8) {
+          a0 += (long long)w[0]; b0 += (long long)w[1];
+          x4 = w[4] > x4 ? w[4] : x4; x5 = w[5] < x5 ? w[5] : x5;
+          x6 = w[6] > x6 ? w[6] : x6; x7 = w[7] < x7 ? w[7] : x7;
+        }
+        // the keys equal to thr_k: need_k of them in the top set, eq_k - need_k in the tail
+        if (need_k > 0) {
+          if (thr_b < hb) { a0 += need_k; sa += (double)need_k * thr_k; x6 = thr_b > x6 ? thr_b : x6; }
+          else x7 = thr_b < x7 ? thr_b : x7;
+        }
+        if (eq_k > need_k) {
+          if (thr_b > tb) { b0 += eq_k - need_k; sb += (double)(eq_k - need_k) * thr_k; x5 = thr_b < x5 ? thr_b : x5; }
+          else x4 = thr_b > x4 ? thr_b : x4;
+        }
+        const double h = __longlong_as_double((long long)hb);
+        const double phi = (double)a0 * h - sa - (sb - (double)b0 * th);
+        ULL done = 0ull;
+        double res = th;
+        if (phi == 0.0) {
+          done = 1ull;
+        } else {
+          if (phi < 0.0) lo = th; else hi = th;
+          const bool rb = rho * th < M;
+          const double c = solve_piece((int)a0, sa, (int)b0, sb, rb, rho, M);
+          if (a0 + b0 > 0 && c > lo && c < hi) {
+            const double hc = c + fmin(rho * c, M);
+            const ULL cb = nnbits(c), hcb = nnbits(hc);
+            bool same = (rho * c < M) == rb;
+            if (c < th) same = same && x4 <= cb && x6 < hcb;   // no key in (c, th] (tail) or [h(c), h(th)) (top)
+            else same = same && x5 > cb && x7 >= hcb;         // no key in (th, c] (tail) or [h(th), h(c)) (top)
+            if (same) { done = 1ull; res = c; }
+            th = c;
+          } else {
+            th = 0.5 * (lo + hi);
+          }
+          if (!done && !(hi - lo > 2e-16 * hi)) { done = 1ull; res = hi; }
+          if (!done && it == 99) { done = 1ull; res = th; }
+        }
+        bc[0] = nnbits(done ? res : th);
+        bc[1] = nnbits(th + fmin(rho * th, M));
+        bc[2] = done;
+        bc[3] = (ULL)b0;
+      }
     }
     __syncthreads();
-    {
-      const ULL* r = scratch + NW * 8;
-      nA = (long long)r[0]; nB = (long long)r[1];
-      SA = __longlong_as_double((long long)r[2]); SB = __longlong_as_double((long long)r[3]);
-      tl = r[4]; tg = r[5]; al = r[6]; ag = r[7];
+    if (bc[2]) {
+      const double r = __longlong_as_double((long long)bc[0]);
+      *nb_out = (int)(long long)bc[3];
+      __syncthreads();
+      return r;
     }
-    // the keys equal to thr_k: need_k of them in the top set, eq_k - need_k in the tail
-    if (need_k > 0) {
-      if (thr_b < hb) { nA += need_k; SA += (double)need_k * thr_k; al = thr_b > al ? thr_b : al; }
-      else ag = thr_b < ag ? thr_b : ag;
-    }
-    if (eq_k > need_k) {
-      if (thr_b > tb) { nB += eq_k - need_k; SB += (double)(eq_k - need_k) * thr_k; tg = thr_b < tg ? thr_b : tg; }
-      else tl = thr_b > tl ? thr_b : tl;
-    }
-    *nb_out = (int)nB;
-    const double phi = (double)nA * h - SA - (SB - (double)nB * th);
-    if (phi == 0.0) return th;
-    if (phi < 0.0) lo = th; else hi = th;
-    const bool rb = rho * th < M;
-    const double c = solve_piece((int)nA, SA, (int)nB, SB, rb, rho, M);
-    if (nA + nB > 0 && c > lo && c < hi) {
-      const double hc = c + fmin(rho * c, M);
-      const ULL cb = nnbits(c), hcb = nnbits(hc);
-      bool same = (rho * c < M) == rb;
-      if (c < th) same = same && tl <= cb && al < hcb;   // no key in (c, th] (tail) or [h(c), h(th)) (top)
-      else same = same && tg > cb && ag >= hcb;         // no key in (th, c] (tail) or [h(th), h(c)) (top)
-      if (same) return c;
-      th = c;
-    } else {
-      th = 0.5 * (lo + hi);
-    }
-    if (!(hi - lo > 2e-16 * hi)) return hi;
   }
-  return th;
+  return __longlong_as_double((long long)bc[0]);
 }
 
 template <typename T, int BLOCK>
@@ -390,9 +418,38 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
   double theta = INFINITY;   // k' = 0: every free coordinate is soft-thresholded to 0
   bool cand_sorted = false;  // cand[0..q) holds the top-q values, descending
 
+  out.topk = 0.0;
   if (q > 0) {
-    SelectResult<U> Rk = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
+    // the k'-th largest |w|: from the keys at or above 0.99 times the previous
+    // call's (one pass to gather them; the top set moves little between FISTA
+    // steps) when they number at least k' and fit the candidates, else by radix
+    // passes over all m.  Both give the same threshold and counts: every key equal
+    // to it or above is among the gathered ones.
+    SelectResult<U> Rk;
+    bool have = false;
+    if (io.topk_hint > 0.0 && q < m) {
+      const U fk = abs_bits<T>((T)(0.99 * io.topk_hint));
+      if (threadIdx.x == 0) sm.sh[40] = 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += BLOCK) {
+        const U kb = keybits(i);
+        if (kb >= fk) {
+          const int pos = atomicAdd(&sm.sh[40], 1);
+          if (pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
+        }
+      }
+      __syncthreads();
+      const int cnt = sm.sh[40];
+      __syncthreads();
+      if (cnt >= q && cnt <= sm.cap) {
+        auto cbits = [&](int j) -> U { return abs_bits<T>((T)sm.cand[j]); };
+        Rk = block_select<U, BLOCK>(cnt, q, cbits, sm.hist, sm.sh);
+        have = true;
+      }
+    }
+    if (!have) Rk = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
     thr_k = to_d(B::val(Rk.thr));
+    out.topk = thr_k;
     need_k = q - Rk.gt;
     eq_k = Rk.eq;
     if (q == m) {
@@ -453,7 +510,7 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
         // Phi(last_floor) > 0 when the candidates were tried; Phi(thr_k) >= 0 always
         const double hi0 = isinf(last_floor) ? thr_k : last_floor;
         theta = root_fullpass<BLOCK>(m, keybits, thr_k, need_k, eq_k, hi0, io.theta0, rho, M,
-                                     reinterpret_cast<unsigned long long*>(sm.hist), &nb);
+                                     reinterpret_cast<unsigned long long*>(sm.hist), sm.pref, &nb);
         // the pooled tail at the root sizes the next call (above the capacity: full pass again)
         out.qused = q + 2 * nb + 32;
       }
@@ -738,9 +795,15 @@ __device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, 
 // TopSum_{k'}(H_M(|a_F| * scale)) + sum_{S1} H_M(|a_j| * scale)   (Lemma 3.1 on
 // the node, with the separable-sum rule for S1).  Keys are read in T.
 
+// hint (> 0): the previous call's k'-th largest |a_F|; every free |a_j| at or above
+// 0.99 hint is gathered in one pass, and when at least k' of them (and at most the
+// candidate capacity) are found the selection runs on those in shared memory
+// instead of in radix passes over all m.  *thr_out (optional): this call's k'-th
+// largest |a_F|, the next call's hint.
 template <typename T, int BLOCK, typename LoadA>
 __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp, double M,
-                                double scale, const SegSmem<T>& sm) {
+                                double scale, const SegSmem<T>& sm, double hint = 0.0,
+                                double* thr_out = nullptr) {
   using B = Bits<T>;
   using U = typename B::U;
   double s1 = 0.0;
@@ -754,6 +817,34 @@ __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp,
     const int8_t st = state ? state[i] : (int8_t)kFree;
     return st == kFree ? abs_bits<T>(loada(i)) : (U)0;
   };
+  if (hint > 0.0) {
+    const U fk = abs_bits<T>((T)(0.99 * hint));
+    if (threadIdx.x == 0) sm.sh[40] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += BLOCK) {
+      const U kb = keybits(i);
+      if (kb >= fk) {
+        const int pos = atomicAdd(&sm.sh[40], 1);
+        if (pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
+      }
+    }
+    __syncthreads();
+    const int cnt = sm.sh[40];
+    __syncthreads();
+    if (cnt >= q && cnt <= sm.cap) {
+      auto cbits = [&](int j) -> U { return abs_bits<T>((T)sm.cand[j]); };
+      SelectResult<U> R = block_select<U, BLOCK>(cnt, q, cbits, sm.hist, sm.sh);
+      const double thr = to_d(B::val(R.thr));
+      double s = 0.0;
+      for (int j = threadIdx.x; j < cnt; j += BLOCK) {
+        const U kb = cbits(j);
+        if (kb > R.thr) s += huber(sm.cand[j] * scale, M);
+      }
+      s = block_sum<double, BLOCK>(s, sm.red);
+      if (thr_out) *thr_out = thr;
+      return s1 + s + (double)(q - R.gt) * huber(thr * scale, M);
+    }
+  }
   SelectResult<U> R = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
   const double thr = to_d(B::val(R.thr));
   double s = 0.0;
@@ -763,6 +854,7 @@ __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp,
     if (kb > R.thr) s += huber(to_d(B::val(kb)) * scale, M);
   }
   s = block_sum<double, BLOCK>(s, sm.red);
+  if (thr_out) *thr_out = thr;
   return s1 + s + (double)(q - R.gt) * huber(thr * scale, M);
 }
 
