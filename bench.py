@@ -777,10 +777,14 @@ def run_batched(args):
     # rooflines.  Tensor products: algorithmic flops 2 n p per running node per
     # step (tiles whose nodes have all stopped are skipped) over the product's
     # device time, against the sustained BF16 peak (the products run inside a long
-    # call).  Exact double-float products of anchors and certificates (k_dfprod):
-    # n p multiply-adds per node and product, two products per anchor (X b_ref,
-    # X^T r_ref) and per certificate (X b^, X^T zeta), against the FP32 FMA rate
-    # 152 SMs x 128 lanes x the median SM clock sampled during the timed calls.
+    # call).  Exact products of anchors and certificates: two per anchor (X b_ref,
+    # X^T r_ref) and two per certificate (X b^, X^T zeta), n p multiply-adds each.
+    # On the tensor cores (k_tcx, the default) each is executed as 18 BF16 slice
+    # products (3 slices of X times 6 of the FP64 vector), 36 n p flops, against the
+    # sustained BF16 peak; with KSC_EXACT_PRODUCT=stream (k_dfprod, double-float
+    # FP32 arithmetic) against the FP32 FMA rate 152 SMs x 128 lanes x the median
+    # SM clock sampled during the timed calls.  Both over the anchor and
+    # certificate phases' device time (slicing, products, residuals, epilogues).
     node_steps = float(sum(r.iters for r in pres))
     alg = 2.0 * n * p * node_steps
     try:
@@ -797,18 +801,28 @@ def run_batched(args):
                 "flops_per_launch": alg / max(nl_, 1), "pieces": 3, "node_steps": node_steps,
                 "avg_launch_ms": round(ms_ / max(nl_, 1), 5), "launches": nl_}
 
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    fma_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # T multiply-adds/s
     exact_products = 2.0 * (bstats["batch_certificates"] + bstats["batch_anchors"])
     macs = exact_products * n * p
     ex_ms = kt["certificates"][1] + kt["anchors"][1]
-    ex_ach = macs / (ex_ms / 1e3) / 1e12
-    exact_line = {"bound": "alu", "kernel": "exact double-float products of anchors and certificates "
-                                            "(k_dfprod; the anchor and certificate phases' device time)",
-                  "achieved": round(ex_ach, 3), "peak": round(fma_peak, 2), "unit": "T multiply-adds/s",
-                  "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median sampled)",
-                  "frac": round(ex_ach / fma_peak, 4), "traffic": None, "products": exact_products,
-                  "multiply_adds": macs, "device_ms": round(ex_ms, 2)}
+    fp64_rate = macs / (ex_ms / 1e3) / 1e12
+    if os.environ.get("KSC_EXACT_PRODUCT", "") == "stream":
+        sm_mhz = clk.get("sm_mhz") or 2070.0
+        fma_peak = 152 * 128 * sm_mhz * 1e6 / 1e12          # T multiply-adds/s
+        exact_line = {"bound": "alu", "kernel": "exact double-float products of anchors and certificates "
+                                                "(k_dfprod; the anchor and certificate phases' device time)",
+                      "achieved": round(fp64_rate, 3), "peak": round(fma_peak, 2), "unit": "T multiply-adds/s",
+                      "peak_kind": f"derived: 152 SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz (median sampled)",
+                      "frac": round(fp64_rate / fma_peak, 4)}
+    else:
+        ex_flops = 36.0 * macs
+        ex_ach = ex_flops / (ex_ms / 1e3) / 1e12
+        exact_line = {"bound": "tensor", "kernel": "exact products of anchors and certificates on the tensor "
+                                                   "cores (k_tcx, 18 BF16 slice products each; the anchor and "
+                                                   "certificate phases' device time)",
+                      "achieved": round(ex_ach, 1), "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind,
+                      "frac": round(ex_ach / peak, 4), "executed_flops": ex_flops}
+    exact_line.update({"traffic": None, "products": exact_products, "multiply_adds": macs,
+                       "exact_fp64_multiply_adds_per_s": round(fp64_rate * 1e12, 1), "device_ms": round(ex_ms, 2)})
     rooflines = {"xt_r": tensor_line("xt_r", "X^T r for the running nodes (k_tcgemm, 3 BF16 pieces)"),
                  "x_dbeta": tensor_line("x_dbeta", "X (beta - beta_ref) for the running nodes (k_tcgemm, 3 BF16 pieces)"),
                  "exact_products": exact_line}
