@@ -19,6 +19,7 @@
 //              test per node (the step logic shared with the single-node solver)
 #include "ksc_batch.cuh"
 #include "ksc_common.cuh"
+#include "ksc_tc.h"
 #include "ksc_prox.cuh"
 #include "ksc_state.cuh"
 
@@ -37,6 +38,27 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* dst, size_t 
     dst[piece_stride] = m;
     if (P > 2) dst[2 * piece_stride] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
   }
+}
+
+// E4M3 pieces of v (already scaled below 256 in magnitude): each piece is the
+// E4M3 rounding (to nearest) of what the previous pieces left, which FP32 holds
+// exactly; four pieces carry v to 2^-16 of 256 (or to the smallest subnormal)
+__device__ __forceinline__ void split8_store(float v, uint8_t* dst, size_t piece_stride) {
+#pragma unroll
+  for (int q = 0; q < kTcE4m3Pieces; ++q) {
+    const __nv_fp8_e4m3 h(v);
+    dst[q * piece_stride] = h.__x;
+    v = __fsub_rn(v, float(h));
+  }
+}
+
+// the power-of-two exponent e that puts amax * 2^e in [128, 256) (0 for 0)
+__device__ __forceinline__ int e8_exponent(double amax) {
+  if (!(amax > 0.0)) return 0;
+  int ex;
+  frexp(amax, &ex);   // amax = f 2^ex, f in [0.5, 1)
+  const int e = 8 - ex;
+  return e < -120 ? -120 : (e > 120 ? 120 : e);
 }
 
 __device__ __forceinline__ float softplusf(float x) { return fmaxf(x, 0.0f) + log1pf(expf(-fabsf(x))); }
@@ -73,7 +95,9 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
   const double* Up = d.U + ((size_t)b * 3 + nd->prev) * d.ldn;
   const double* Ur = d.u_ref + (size_t)b * d.ldn;
   const size_t pstride = (size_t)d.Bpad * d.ldn;
-  __nv_bfloat16* rrow = d.rpc + (size_t)b * d.ldn;
+  __nv_bfloat16* rrow = d.e8 ? nullptr : d.rpc + (size_t)b * d.ldn;
+  float* rb = d.e8 ? d.rbuf + (size_t)b * d.ldn : nullptr;
+  float amax = 0.0f;
   double nc = 0.0;
   const int i0 = blockIdx.x * kBThreads * kBRows;
 #pragma unroll 2
@@ -101,34 +125,105 @@ __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {
         term = 0.0f;
       } else if (d.loss == kLossPoisson) {
         // grad F = e^u - y: the difference e^{u_ref} expm1(u - u_ref) without
-        // cancellation; -F*(-zeta) = e^u (1 - u)
+        // cancellation (far from the anchor, where expm1 would overflow, the plain
+        // difference, which has none to lose); -F*(-zeta) = e^u (1 - u)
         const float eg = expf((float)ug);
-        dr = expf((float)__ldg(&Ur[i])) * expm1f((float)du);
+        dr = fabs(du) > 16.0 ? eg - expf((float)__ldg(&Ur[i])) : expf((float)__ldg(&Ur[i])) * expm1f((float)du);
         term = eg * (1.0f - (float)ug);
       } else if (d.loss == kLossGamma) {
         // grad F = 1 - y e^-u: the difference -y e^{-u_ref} expm1(-(u - u_ref));
         // with w = y e^-u, -F*(-zeta) = w (1 + u)
         const float wg = y * expf(-(float)ug);
-        dr = -y * expf(-(float)__ldg(&Ur[i])) * expm1f(-(float)du);
+        dr = fabs(du) > 16.0 ? -(wg - y * expf(-(float)__ldg(&Ur[i])))
+                             : -y * expf(-(float)__ldg(&Ur[i])) * expm1f(-(float)du);
         term = wg * (1.0f + (float)ug);
       } else {
         // grad F = -y sigma(t), t = -y u;  sigma(t) - sigma(t_ref)
-        //   = sigma(t) (1 - sigma(t_ref)) (1 - e^{-(t - t_ref)})
+        //   = sigma(t) (1 - sigma(t_ref)) (1 - e^{-(t - t_ref)}),
+        // or, far from the anchor (|t - t_ref| > 16: e^{-(t - t_ref)} can overflow,
+        // and the two values differ by orders of magnitude), the plain difference
         const float t = -y * (float)ug;
         const float tr = -y * (float)__ldg(&Ur[i]);
         const float dt = (float)(-(double)y * du);
         const float s = 1.0f / (1.0f + expf(-t));
-        const float sr = 1.0f / (1.0f + expf(tr));    // 1 - sigma(t_ref)
-        dr = -y * (s * sr * (-expm1f(-dt)));
+        if (fabsf(dt) > 16.0f) {
+          dr = -y * (s - 1.0f / (1.0f + expf(-tr)));
+        } else {
+          const float sr = 1.0f / (1.0f + expf(tr));    // 1 - sigma(t_ref)
+          dr = -y * (s * sr * (-expm1f(-dt)));
+        }
         // binary entropy of q = zeta_i y_i = sigma(t)
         term = s * softplusf(-t) + (1.0f - s) * softplusf(t);
       }
-      split_store(dr, rrow + i, pstride, d.P);
+      if (d.e8) {
+        rb[i] = dr;
+        amax = fmaxf(amax, fabsf(dr));
+      } else {
+        split_store(dr, rrow + i, pstride, d.P);
+      }
       nc += (double)term;
     }
   }
   nc = block_sum<double, kBThreads>(nc, red);
   if (threadIdx.x == 0) d.ncpart[(size_t)b * d.nrt + blockIdx.x] = nc;
+  if (d.e8) {
+    const double am = block_max<double, kBThreads>((double)amax, red, 0.0);
+    if (threadIdx.x == 0) d.rmaxp[(size_t)b * d.nrt + blockIdx.x] = (float)am;
+  }
+}
+
+// E4M3 pieces of the residual differences: the node's largest |dr| from the
+// residual CTAs' maxima, then the same rows as the residual kernel
+__global__ void __launch_bounds__(kBThreads) k_bsplit8_resid(BatchDev d) {
+  const int b = blockIdx.y;
+  if (d.nodes[b].done != kRunning) return;
+  float amax = 0.0f;
+  for (int t = 0; t < d.nrt; ++t) amax = fmaxf(amax, d.rmaxp[(size_t)b * d.nrt + t]);
+  const int e = e8_exponent((double)amax);
+  const float sc = scalbnf(1.0f, e);
+  if (blockIdx.x == 0 && threadIdx.x == 0) d.rs_grad[b] = scalbnf(1.0f, -e);
+  const float* rb = d.rbuf + (size_t)b * d.ldn;
+  uint8_t* row = d.rpc8 + (size_t)b * d.ldn8;
+  const size_t pstride = (size_t)d.Bpad * d.ldn8;
+  const int i0 = blockIdx.x * kBThreads * kBRows;
+  for (int r = 0; r < kBRows; ++r) {
+    const int i = i0 + r * kBThreads + (int)threadIdx.x;
+    if (i < d.n) split8_store(rb[i] * sc, row + i, pstride);
+  }
+}
+
+// E4M3 pieces of s_j (beta_j - beta_ref_j) for one node (one CTA of BLOCK
+// threads): its largest magnitude first, then the pieces; returns the inverse scale
+template <int BLOCK>
+__device__ float split8_beta_row(const BatchDev& d, int b, const double* bn, const double* br, double* red) {
+  double amax = 0.0;
+  for (int j = threadIdx.x; j < d.p; j += BLOCK) {
+    const double x = bn[j], r = br[j];
+    if (((__double_as_longlong(x) | __double_as_longlong(r)) << 1) != 0)
+      amax = fmax(amax, fabs((x - r) * (double)d.xscale[j]));
+  }
+  amax = block_max<double, BLOCK>(amax, red, 0.0);
+  const int e = e8_exponent(amax);
+  const double sc = ldexp(1.0, e);
+  uint8_t* row = d.bpc8 + (size_t)b * d.ldp8;
+  const size_t pstride = (size_t)d.Bpad * d.ldp8;
+  for (int j = threadIdx.x; j < d.p; j += BLOCK) {
+    const double x = bn[j], r = br[j];
+    const float v = ((__double_as_longlong(x) | __double_as_longlong(r)) << 1) == 0
+                        ? 0.0f
+                        : (float)((x - r) * ((double)d.xscale[j] * sc));
+    split8_store(v, row + j, pstride);
+  }
+  return scalbnf(1.0f, -e);
+}
+
+__global__ void __launch_bounds__(256) k_bsplit8_beta(BatchDev d, const int* list) {
+  __shared__ double red[64];
+  const int b = list[blockIdx.x];
+  const double* b1 = d.beta + ((size_t)b * 3 + 1) * d.ldp;
+  const double* br = d.beta_ref + (size_t)b * d.ldp;
+  const float rs = split8_beta_row<256>(d, b, b1, br, red);
+  if (threadIdx.x == 0) d.rs_fwd[b] = rs;
 }
 
 // ------------------------------------------------------------------ prox
@@ -193,13 +288,17 @@ __global__ void __launch_bounds__(kBProxBlock) k_bprox(BatchDev d) {
   io.topk_hint = nd->ptop;
   const SegOut o = prox_segment<double, kBProxBlock>(io, sm);
   __syncthreads();
-  // BF16 pieces of fl32(beta^{t+1} - beta_ref)
+  // BF16 pieces of fl32(beta^{t+1} - beta_ref) (E4M3: pieces of s_j times it)
   const size_t pstride = (size_t)d.Bpad * d.ldp;
   __nv_bfloat16* prow = d.bpc + (size_t)b * d.ldp;
   const double* bn = io.beta;
   const double* br = d.beta_ref + (size_t)b * d.ldp;
   double bsq = 0.0;
-  for (int j = threadIdx.x; j < p; j += kBProxBlock) {
+  if (d.e8) {
+    const float rs = split8_beta_row<kBProxBlock>(d, b, bn, br, sm.red);
+    if (threadIdx.x == 0) d.rs_fwd[b] = rs;
+  }
+  for (int j = d.e8 ? p : (int)threadIdx.x; j < p; j += kBProxBlock) {
     const double x = bn[j], r = br[j];
     // both zero (most coordinates of a sparse iterate): no FP64 arithmetic
     const float v = ((__double_as_longlong(x) | __double_as_longlong(r)) << 1) == 0 ? 0.0f : (float)(x - r);
@@ -339,7 +438,7 @@ __global__ void __launch_bounds__(256) k_bzero_anchor(BatchDev d, const int* lis
   for (int j = blockIdx.x * 256 + (int)threadIdx.x; j < d.p; j += gridDim.x * 256) {
     d.beta_ref[(size_t)b * d.ldp + j] = 0.0;
     d.G_ref[(size_t)b * d.ldp + j] = G0[j];
-    split_store((float)b1[j], d.bpc + (size_t)b * d.ldp + j, pstride, d.P);
+    if (!d.e8) split_store((float)b1[j], d.bpc + (size_t)b * d.ldp + j, pstride, d.P);
   }
   for (int i = blockIdx.x * 256 + (int)threadIdx.x; i < d.n; i += gridDim.x * 256) {
     d.u_ref[(size_t)b * d.ldn + i] = 0.0;
@@ -615,6 +714,14 @@ static int vec_blocks(int m) {
 
 void launch_bresid(const BatchDev& d, cudaStream_t s) {
   k_bresid<<<dim3(d.nrt, d.B), kBThreads, 0, s>>>(d);
+}
+
+void launch_bsplit8_resid(const BatchDev& d, cudaStream_t s) {
+  k_bsplit8_resid<<<dim3(d.nrt, d.B), kBThreads, 0, s>>>(d);
+}
+
+void launch_bsplit8_beta(const BatchDev& d, const int* list, int count, cudaStream_t s) {
+  k_bsplit8_beta<<<count, 256, 0, s>>>(d, list);
 }
 
 void launch_bprox(const BatchDev& d, cudaStream_t s) {

@@ -87,241 +87,24 @@ __device__ __forceinline__ float loss_change(double u, float d, float y, int los
     const float m = fmaxf(s, 0.0f), mn = fmaxf(s + t, 0.0f);
     return mn * mn - m * m;
   }
+  // far from u (|d| > 16) the plain difference: expm1 could overflow, and there is
+  // no cancellation to avoid
+  if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
   if (loss == kLossPoisson) return expf((float)u) * expm1f(d) - y * d;            // e^u (e^d - 1) - y d
   if (loss == kLossGamma) return y * expf(-(float)u) * expm1f(-d) + d;         // y e^-u (e^-d - 1) + d
-  if (fabsf(d) > 16.0f) return loss_term((float)(u + (double)d), y, loss) - loss_term((float)u, y, loss);
   const float s = 1.0f / (1.0f + expf(y * (float)u));   // sigma(-y u)
   return log1pf(expm1f(-y * d) * s);
 }
 
 // ------------------------------------------------------------------ kernel
 
+// bk: elements per K block of 128 bytes (64 BF16 or 128 E4M3)
 struct TcShape {
-  int M, Mpad, N, K;
+  int M, Mpad, N, K, bk;
 };
 
-template <int P, int BN, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    k_tcgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
-             TcEpi ep) {
-  // every row of this M tile belongs to a finished node: nothing to compute
-  if (ep.tile_active != nullptr && ep.tile_active[blockIdx.y] == 0) return;
-  constexpr int S = tc_stages(P, BN);
-  constexpr uint32_t B_TILE = BN * 128;
-  constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
-  constexpr uint32_t TCOLS = tc_tmem_cols(BN);
-  static_assert(S >= 2, "at least two pipeline stages");
-  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N for M = 128");
-
-  extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + S * P * kTcATile;
-  uint64_t* full = (uint64_t*)(sB + S * B_TILE);
-  uint64_t* empty = full + S;
-  uint64_t* accf = empty + S;
-  uint64_t* drain = accf + 1;
-  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
-  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
-  const int nkb = (sh.K + kTcBK - 1) / kTcBK;
-
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) {
-      mbar_init(&full[i], 1);
-      mbar_init(&empty[i], 1);
-    }
-    mbar_init(accf, 1);
-    mbar_init(drain, 1);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) tmem_alloc(tmem_slot, TCOLS);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  if (warp == 0) {
-    if (lane == 0) {
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
-      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
-      int issued = 0;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % S;
-        const uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
-          atomicExch(&g_tc_err, 1);
-          *abort_flag = 1;
-          break;
-        }
-        mbar_expect_tx(&full[s], STAGE_TX);
-#pragma unroll
-        for (int q = 0; q < P; ++q)
-          tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * kTcBK, q * sh.Mpad + m0);
-        tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * kTcBK, n0);
-        issued = kb + 1;
-      }
-      if (*abort_flag) {
-        // let the copies already issued land before the CTA leaves
-        for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb) {
-          volatile int never = 0;
-          mbar_wait(&full[kb % S], (uint32_t)(kb / S) & 1u, &never);
-        }
-      }
-    }
-    __syncwarp();
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = tc_idesc(kTcBM, BN);
-      bool ok = true;
-      for (int kb = 0; kb < nkb; ++kb) {
-        const int s = kb % S;
-        const uint32_t ph = (uint32_t)(kb / S) & 1u;
-        if (!mbar_wait(&full[s], ph, abort_flag)) {
-          atomicExch(&g_tc_err, 2);
-          *abort_flag = 1;
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t b_addr = smem_u32(sB + s * B_TILE);
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-          const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
-#pragma unroll
-          for (int kk = 0; kk < kTcBK / 16; ++kk)
-            umma_bf16(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                      (kb | q | kk) != 0 ? 1u : 0u);
-        }
-        umma_commit(&empty[s]);
-      }
-      if (ok) {
-        umma_commit(accf);
-      } else {
-        // wait for the MMAs already issued before TMEM is released
-        umma_commit(drain);
-        volatile int never = 0;
-        mbar_wait(drain, 0, &never);
-      }
-    }
-    __syncwarp();
-  } else {
-    const int qd = warp & 3;   // TMEM lanes 32 qd .. 32 qd + 31
-    const int m = m0 + 32 * qd + lane;
-    // warp-uniform: tcgen05.ld is a warp-collective instruction
-    const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0, abort_flag) ? 1 : 0) != 0;
-    tc_fence_after();
-    if (ok) {
-      const bool row_ok = m < sh.M;
-      float* orow = nullptr;
-      const double* brow = nullptr;
-      double* o64 = nullptr;
-      const double* uin = nullptr;
-      double* uout = nullptr;
-      if (row_ok) {
-        if (MODE == kTcStore) {
-          orow = ep.out + (int64_t)m * ep.ldo;
-        } else if (MODE == kTcAdd) {
-          brow = ep.base + (int64_t)m * ep.ldb;
-          o64 = ep.out64 + (int64_t)m * ep.ldo;
-        } else {
-          brow = ep.base + (int64_t)m * ep.ldb;
-          uin = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_in[m] * ep.slot_stride;
-          uout = ep.u64 + (int64_t)m * ep.ldo + (int64_t)ep.slot_out[m] * ep.slot_stride;
-        }
-      }
-      double fsum = 0.0, dsum = 0.0;
-      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16);
-#pragma unroll 1
-      for (int c = 0; c < BN; c += 16) {
-        float v[16];
-        tmem_ld16(tbase + (uint32_t)c, v);
-        const int nc = n0 + c;
-        if (row_ok && nc < sh.N) {
-          if (MODE == kTcStore) {
-            if (nc + 16 <= sh.N) {
-              float4* o4 = (float4*)(orow + nc);
-#pragma unroll
-              for (int i = 0; i < 4; ++i) o4[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-            } else {
-#pragma unroll
-              for (int i = 0; i < 16; ++i)
-                if (nc + i < sh.N) orow[nc + i] = v[i];
-            }
-          } else if (MODE == kTcAdd) {
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i)
-              if (nc + i < sh.N) o64[nc + i] = brow[nc + i] + (double)v[i];
-          } else {
-            float fa = 0.0f, da = 0.0f;
-            double fd = 0.0;
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-              if (nc + i < sh.N) {
-                const double uo = uin[nc + i];
-                const double un = brow[nc + i] + (double)v[i];
-                uout[nc + i] = un;
-                const float yi = __ldg(&ep.y[nc + i]);
-                add_loss(un, yi, ep.loss, fd, fa);
-                da += loss_change(uo, (float)(un - uo), yi, ep.loss);
-              }
-            }
-            fsum += (double)fa + fd;
-            dsum += (double)da;
-            // one pair of partials per 64 columns, whatever the tile width: the
-            // sums do not depend on the tiling
-            if (((c + 16) & 63) == 0 || nc + 16 >= sh.N) {
-              double* pp = ep.part + 2 * ((int64_t)m * ep.npart + (nc >> 6));
-              pp[0] = fsum;
-              pp[1] = dsum;
-              fsum = 0.0;
-              dsum = 0.0;
-            }
-          }
-        }
-      }
-    } else {
-      atomicExch(&g_tc_err, 3);
-      *abort_flag = 1;
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, TCOLS);
-}
-
-// ------------------------------------------------------------------ stream-K
-
-constexpr int kSkMaxMTiles = 8;   // M <= 1024
-
-// The work assignment, computed identically by every CTA of both kernels from the
-// tile flags (which do not change between them): active M tiles in order, tiles
-// numbered N-major (CTAs that run at the same time share B tiles in L2), K blocks
-// of every tile consecutive; CTA c owns iterations [c I / G, (c+1) I / G).
-struct SkMap {
-  int act[kSkMaxMTiles];
-  int A, nN, KB, G;
-  int64_t I;
-};
-
-__device__ __forceinline__ void sk_map(const TcShape& sh, const TcEpi& ep, int bn, int G, SkMap& mp) {
-  const int nM = (sh.M + kTcBM - 1) / kTcBM;
-  mp.A = 0;
-  for (int t = 0; t < nM && t < kSkMaxMTiles; ++t)
-    if (ep.tile_active == nullptr || ep.tile_active[t] != 0) mp.act[mp.A++] = t;
-  mp.nN = (sh.N + bn - 1) / bn;
-  mp.KB = (sh.K + kTcBK - 1) / kTcBK;
-  mp.G = G;
-  mp.I = (int64_t)mp.A * mp.nN * mp.KB;
-}
-__device__ __forceinline__ int64_t sk_begin(const SkMap& mp, int c) { return (int64_t)c * mp.I / mp.G; }
-__device__ __forceinline__ int sk_owner(const SkMap& mp, int64_t i) { return (int)(((i + 1) * mp.G - 1) / mp.I); }
-
-// row pointers of the epilogue and one 16-column chunk of it (the same rules as
-// k_tcgemm's epilogue; nc = first column of the chunk, a multiple of 16)
+// row pointers of the epilogue and one 16-column chunk of it (nc = first column
+// of the chunk, a multiple of 16), shared by both schedules and the fix-up
 struct EpiRow {
   float* orow;
   const double* brow;
@@ -352,9 +135,17 @@ __device__ __forceinline__ EpiRow epi_row(const TcShape& sh, const TcEpi& ep, in
 // fix-up kernel sums its four chunks across threads and writes them itself)
 template <int MODE, bool PART = true>
 __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, const EpiRow& r, int m, int nc,
-                                          const float* v, double& fsum, double& dsum) {
+                                          float* v, double& fsum, double& dsum) {
   if (!r.ok || nc >= sh.N) return;
   const bool whole = nc + 16 <= sh.N;   // rows are 64-byte aligned (strides padded to 8 elements)
+  if (ep.rscale != nullptr) {
+    // E4M3 operands: undo the row's power-of-two scale and apply the columns'
+    // (both exact in FP32)
+    const float rs = ep.rscale[m];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      v[i] *= (ep.cscale != nullptr && nc + i < sh.N) ? rs * ep.cscale[nc + i] : rs;
+  }
   if (MODE == kTcStore) {
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -426,6 +217,173 @@ __device__ __forceinline__ void epi_chunk(const TcShape& sh, const TcEpi& ep, co
   }
 }
 
+// ------------------------------------------------------------------ stream-K
+
+constexpr int kSkMaxMTiles = 8;   // M <= 1024
+
+// The work assignment, computed identically by every CTA of both kernels from the
+// tile flags (which do not change between them): active M tiles in order, tiles
+// numbered N-major (CTAs that run at the same time share B tiles in L2), K blocks
+// of every tile consecutive; CTA c owns iterations [c I / G, (c+1) I / G).
+struct SkMap {
+  int act[kSkMaxMTiles];
+  int A, nN, KB, G;
+  int64_t I;
+};
+
+__device__ __forceinline__ void sk_map(const TcShape& sh, const TcEpi& ep, int bn, int G, SkMap& mp) {
+  const int nM = (sh.M + kTcBM - 1) / kTcBM;
+  mp.A = 0;
+  for (int t = 0; t < nM && t < kSkMaxMTiles; ++t)
+    if (ep.tile_active == nullptr || ep.tile_active[t] != 0) mp.act[mp.A++] = t;
+  mp.nN = (sh.N + bn - 1) / bn;
+  mp.KB = (sh.K + sh.bk - 1) / sh.bk;
+  mp.G = G;
+  mp.I = (int64_t)mp.A * mp.nN * mp.KB;
+}
+__device__ __forceinline__ int64_t sk_begin(const SkMap& mp, int c) { return (int64_t)c * mp.I / mp.G; }
+__device__ __forceinline__ int sk_owner(const SkMap& mp, int64_t i) { return (int)(((i + 1) * mp.G - 1) / mp.I); }
+
+// E8: A and B hold E4M3 bytes (kind::f8f6f4) instead of BF16 (kind::f16)
+template <int P, int BN, int MODE, int E8>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_tcgemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
+             TcEpi ep) {
+  // every row of this M tile belongs to a finished node: nothing to compute
+  if (ep.tile_active != nullptr && ep.tile_active[blockIdx.y] == 0) return;
+  constexpr int S = tc_stages(P, BN);
+  constexpr uint32_t B_TILE = BN * 128;
+  constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
+  constexpr uint32_t TCOLS = tc_tmem_cols(BN);
+  static_assert(S >= 2, "at least two pipeline stages");
+  static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N for M = 128");
+
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + S * P * kTcATile;
+  uint64_t* full = (uint64_t*)(sB + S * B_TILE);
+  uint64_t* empty = full + S;
+  uint64_t* accf = empty + S;
+  uint64_t* drain = accf + 1;
+  uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * BN;
+  const int nkb = (sh.K + sh.bk - 1) / sh.bk;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(accf, 1);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, TCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+      asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % S;
+        const uint32_t ph = (uint32_t)(kb / S) & 1u;
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) {
+          atomicExch(&g_tc_err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        mbar_expect_tx(&full[s], STAGE_TX);
+#pragma unroll
+        for (int q = 0; q < P; ++q)
+          tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * sh.bk, q * sh.Mpad + m0);
+        tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * sh.bk, n0);
+        issued = kb + 1;
+      }
+      if (*abort_flag) {
+        // let the copies already issued land before the CTA leaves
+        for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb) {
+          volatile int never = 0;
+          mbar_wait(&full[kb % S], (uint32_t)(kb / S) & 1u, &never);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = E8 ? tc_idesc_e4m3(kTcBM, BN) : tc_idesc(kTcBM, BN);
+      bool ok = true;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % S;
+        const uint32_t ph = (uint32_t)(kb / S) & 1u;
+        if (!mbar_wait(&full[s], ph, abort_flag)) {
+          atomicExch(&g_tc_err, 2);
+          *abort_flag = 1;
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t b_addr = smem_u32(sB + s * B_TILE);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+          const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of the 128-byte row per MMA
+            if (E8)
+              umma_e4m3(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                        (kb | q | kk) != 0 ? 1u : 0u);
+            else
+              umma_bf16(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                        (kb | q | kk) != 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(&empty[s]);
+      }
+      if (ok) {
+        umma_commit(accf);
+      } else {
+        // wait for the MMAs already issued before TMEM is released
+        umma_commit(drain);
+        volatile int never = 0;
+        mbar_wait(drain, 0, &never);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int qd = warp & 3;   // TMEM lanes 32 qd .. 32 qd + 31
+    const int m = m0 + 32 * qd + lane;
+    // warp-uniform: tcgen05.ld is a warp-collective instruction
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(accf, 0, abort_flag) ? 1 : 0) != 0;
+    tc_fence_after();
+    if (ok) {
+      const EpiRow er = epi_row<MODE>(sh, ep, m);
+      double fsum = 0.0, dsum = 0.0;
+      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tmem_ld16(tbase + (uint32_t)c, v);
+        epi_chunk<MODE>(sh, ep, er, m, n0 + c, v, fsum, dsum);
+      }
+    } else {
+      atomicExch(&g_tc_err, 3);
+      *abort_flag = 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) tmem_dealloc(tmem, TCOLS);
+}
+
 __host__ __device__ constexpr uint32_t tc_tmem_cols2(int BN) {
   return 2 * BN <= 32 ? 32u : 2 * BN <= 64 ? 64u : 2 * BN <= 128 ? 128u : 2 * BN <= 256 ? 256u : 512u;
 }
@@ -440,7 +398,7 @@ __device__ __forceinline__ float* sk_part(float* ws, int bn, int slot, int chunk
 __host__ __device__ constexpr int sk_epi_warps(int BN) { return BN >= 128 ? 8 : 4; }
 __host__ __device__ constexpr int sk_threads(int BN) { return 64 + 32 * sk_epi_warps(BN); }
 
-template <int P, int BN, int MODE>
+template <int P, int BN, int MODE, int E8>
 __global__ void __launch_bounds__(sk_threads(BN), 1)
     k_tcgemm_sk(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TcShape sh,
                 TcEpi ep) {
@@ -510,8 +468,8 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
           mbar_expect_tx(&full[s], STAGE_TX);
 #pragma unroll
           for (int q = 0; q < P; ++q)
-            tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * kTcBK, q * sh.Mpad + m0);
-          tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * kTcBK, n0);
+            tma_load_2d(sA + (s * P + q) * kTcATile, &tmA, &full[s], kb * sh.bk, q * sh.Mpad + m0);
+          tma_load_2d(sB + s * B_TILE, &tmB, &full[s], kb * sh.bk, n0);
         }
         i += kb1 - kb0;
       }
@@ -525,7 +483,7 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = tc_idesc(kTcBM, BN);
+      constexpr uint32_t idesc = E8 ? tc_idesc_e4m3(kTcBM, BN) : tc_idesc(kTcBM, BN);
       int64_t g = 0;
       int sg = 0;
       bool ok = true;
@@ -556,9 +514,14 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
           for (int q = 0; q < P; ++q) {
             const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
 #pragma unroll
-            for (int kk = 0; kk < kTcBK / 16; ++kk)
-              umma_bf16(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                        ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+            for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of the 128-byte row per MMA
+              if (E8)
+                umma_e4m3(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                          ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+              else
+                umma_bf16(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
+                          ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+            }
           }
           umma_commit(&empty[s]);
         }
@@ -705,18 +668,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// e8: E4M3 bytes (128 per swizzle row) instead of BF16 (64)
 static bool make_map(void* out, const void* base, uint64_t inner, uint64_t rows, int64_t ld, uint32_t box_rows,
-                     const char** why) {
+                     int e8, const char** why) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
   if (!fn) {
     *why = "cuTensorMapEncodeTiled is not available from the driver";
     return false;
   }
   cuuint64_t dims[2] = {inner, rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)kTcBK, box_rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * (e8 ? 1 : 2)};
+  cuuint32_t box[2] = {(cuuint32_t)(e8 ? 128 : kTcBK), box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn((CUtensorMap*)out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides,
+  CUresult r = fn((CUtensorMap*)out, e8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                  const_cast<void*>(base), dims, strides,
                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -727,19 +692,22 @@ static bool make_map(void* out, const void* base, uint64_t inner, uint64_t rows,
 }
 
 bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t lda, const void* B, int N,
-             int64_t ldb, int bn, const char** why) {
+             int64_t ldb, int bn, const char** why, int e8) {
   plan->ok = 0;
-  if (P < 1 || P > 3) { *why = "pieces must be 1, 2 or 3"; return false; }
+  if (!e8 && (P < 1 || P > 3)) { *why = "BF16 pieces must be 1, 2 or 3"; return false; }
+  if (e8 && P != kTcE4m3Pieces) { *why = "E4M3 products take 4 pieces"; return false; }
   if (bn != 64 && bn != 128 && bn != 256) { *why = "tile width must be 64, 128 or 256"; return false; }
   if (M <= 0 || N <= 0 || K <= 0) { *why = "empty product"; return false; }
   if (Mpad % kTcBM != 0 || Mpad < M) { *why = "Mpad must be a multiple of 128 and >= M"; return false; }
-  if ((lda * 2) % 16 != 0 || (ldb * 2) % 16 != 0 || lda < K || ldb < K) {
+  const int64_t es = e8 ? 1 : 2;
+  if ((lda * es) % 16 != 0 || (ldb * es) % 16 != 0 || lda < K || ldb < K) {
     *why = "row strides must be >= K and multiples of 16 bytes";
     return false;
   }
   if (((uintptr_t)A % 16) != 0 || ((uintptr_t)B % 16) != 0) { *why = "operands must be 16-byte aligned"; return false; }
-  if (!make_map(plan->tmA, A, (uint64_t)K, (uint64_t)P * Mpad, lda, kTcBM, why)) return false;
-  if (!make_map(plan->tmB, B, (uint64_t)K, (uint64_t)N, ldb, (uint32_t)bn, why)) return false;
+  if (!make_map(plan->tmA, A, (uint64_t)K, (uint64_t)P * Mpad, lda, kTcBM, e8, why)) return false;
+  if (!make_map(plan->tmB, B, (uint64_t)K, (uint64_t)N, ldb, (uint32_t)bn, e8, why)) return false;
+  plan->e8 = e8 ? 1 : 0;
   plan->P = P;
   plan->M = M;
   plan->Mpad = Mpad;
@@ -763,41 +731,42 @@ bool tc_plan_stream_k(TcPlan* plan, int grid, const char** why) {
 
 size_t tc_skws_floats(int grid, int bn) { return (size_t)2 * grid * kTcBM * bn; }
 
-template <int P, int BN, int MODE>
+template <int P, int BN, int MODE, int E8>
 static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
   constexpr int bytes = tc_smem_bytes(P, BN);
-  TcShape sh{g.M, g.Mpad, g.N, g.K};
+  TcShape sh{g.M, g.Mpad, g.N, g.K, E8 ? 128 : kTcBK};
   if (g.sk) {
     static bool attr_sk = false;
     if (!attr_sk) {
-      cudaFuncSetAttribute(k_tcgemm_sk<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      cudaFuncSetAttribute(k_tcgemm_sk<P, BN, MODE, E8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
       attr_sk = true;
     }
-    k_tcgemm_sk<P, BN, MODE><<<g.grid, sk_threads(BN), bytes, s>>>(*(const CUtensorMap*)g.tmA,
-                                                              *(const CUtensorMap*)g.tmB, sh, e);
+    k_tcgemm_sk<P, BN, MODE, E8><<<g.grid, sk_threads(BN), bytes, s>>>(*(const CUtensorMap*)g.tmA,
+                                                                  *(const CUtensorMap*)g.tmB, sh, e);
     if (g.grid > 1) k_tcgemm_fix<BN, MODE><<<dim3(g.grid - 1, (BN + 63) / 64), kTcBM * 4, 0, s>>>(sh, e, g.grid);
     return;
   }
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tcgemm<P, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaFuncSetAttribute(k_tcgemm<P, BN, MODE, E8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     attr = true;
   }
   dim3 grid((g.N + BN - 1) / BN, (g.M + kTcBM - 1) / kTcBM);
-  k_tcgemm<P, BN, MODE><<<grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA, *(const CUtensorMap*)g.tmB,
-                                                        sh, e);
+  k_tcgemm<P, BN, MODE, E8><<<grid, kTcThreads, bytes, s>>>(*(const CUtensorMap*)g.tmA,
+                                                            *(const CUtensorMap*)g.tmB, sh, e);
 }
 
-template <int P, int MODE>
+template <int P, int MODE, int E8 = 0>
 static void launch_bn(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
-  if (g.bn == 64) launch_one<P, 64, MODE>(g, e, s);
-  else if (g.bn == 128) launch_one<P, 128, MODE>(g, e, s);
-  else launch_one<P, 256, MODE>(g, e, s);
+  if (g.bn == 64) launch_one<P, 64, MODE, E8>(g, e, s);
+  else if (g.bn == 128) launch_one<P, 128, MODE, E8>(g, e, s);
+  else launch_one<P, 256, MODE, E8>(g, e, s);
 }
 
 template <int MODE>
 static void launch_p(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
-  if (g.P == 1) launch_bn<1, MODE>(g, e, s);
+  if (g.e8) launch_bn<kTcE4m3Pieces, MODE, 1>(g, e, s);
+  else if (g.P == 1) launch_bn<1, MODE>(g, e, s);
   else if (g.P == 2) launch_bn<2, MODE>(g, e, s);
   else launch_bn<3, MODE>(g, e, s);
 }

@@ -138,7 +138,8 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.cnt_sp, (size_t)sp_nrb(d) * 4);
   {
     void* xc = nullptr;
-    d.ldc = (n + 7) / 8 * 8;
+    // a multiple of 16 bytes (TMA row stride of the batched products)
+    d.ldc = pr->xdt == kXFP8 ? (n + 15) / 16 * 16 : (n + 7) / 8 * 8;
     ALLOC(xc, (size_t)d.ldc * p * xbytes(pr->xdt));
     d.Xc = xc;
   }

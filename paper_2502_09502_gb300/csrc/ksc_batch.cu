@@ -119,9 +119,10 @@ ksc_status balloc(BatchWs* ws, P** ptr, size_t bytes) {
   return KSC_OK;
 }
 
-bool batch_supported(const ksc_problem* pr) { return pr->xdt == kXBF16; }
+bool batch_supported(const ksc_problem* pr) { return pr->xdt == kXBF16 || pr->xdt == kXFP8; }
 
 int pad8(int64_t v) { return (int)((v + 7) / 8 * 8); }
+int pad16(int64_t v) { return (int)((v + 15) / 16 * 16); }
 
 int sm_count() {
   int dev = 0, n = 0;
@@ -130,7 +131,10 @@ int sm_count() {
   return n;
 }
 
-bool needs_xcopy(const ksc_problem* pr) { return !((pr->ldx * 2) % 16 == 0 && ((uintptr_t)pr->X % 16) == 0); }
+static size_t xelem(const ksc_problem* pr) { return pr->xdt == kXFP8 ? 1 : 2; }
+bool needs_xcopy(const ksc_problem* pr) {
+  return !((pr->ldx * xelem(pr)) % 16 == 0 && ((uintptr_t)pr->X % 16) == 0);
+}
 
 // workspace bytes for `need` slots (the allocations of alloc_ws)
 size_t ws_bytes(const ksc_problem* pr, int need) {
@@ -140,9 +144,14 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   size_t b = 0;
   b += Bc * ldp;                                // state
   b += Bc * 3 * ldp * 8 + Bc * ldp * 8;         // beta slots, beta_ref
-  b += (size_t)kBatchPieces * Bp * ldp * 2;     // pieces of beta - beta_ref
+  const bool e8 = pr->xdt == kXFP8;
+  if (e8) {
+    b += (size_t)kTcE4m3Pieces * Bp * (pad16(p) + pad16(n));                 // E4M3 pieces
+    b += Bc * ldn * 4 + Bc * batch_nrt((int)n) * 4 + 2 * Bc * 4;            // rbuf, rmaxp, scales
+  } else {
+    b += (size_t)kBatchPieces * Bp * (ldp + ldn) * 2;                       // BF16 pieces
+  }
   b += Bc * 3 * ldn * 8 + 2 * Bc * ldn * 8;     // u slots, u_ref, r_ref
-  b += (size_t)kBatchPieces * Bp * ldn * 2;     // pieces of r - r_ref
   b += 2 * Bc * ldp * 8;                        // G, G_ref
   b += 2 * Bc * 4 + Bc * nft * 16 + Bc * batch_nrt((int)n) * 8;
   b += Bc * (sizeof(BNode) + sizeof(BCert)) + 2 * Bc * p * 8 + Bc * 4 + n * 12;
@@ -152,7 +161,7 @@ size_t ws_bytes(const ksc_problem* pr, int need) {
   b += tc_skws_floats(sm_count(), 256) * 4;     // stream-K partial tiles
   b += (ldn + ldp) * 8;                         // zero anchor r0, G0
   if (p > 2048) b += Bc * ldp * 8;              // prox scratch
-  if (needs_xcopy(pr)) b += n * ldp * 2;
+  if (needs_xcopy(pr)) b += n * (e8 ? pad16(p) : ldp * 2);
   return b;
 }
 
@@ -178,11 +187,29 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bo
   d.state = state;
   BA(d.beta, (size_t)Bc * 3 * ldp * 8);
   BA(d.beta_ref, (size_t)Bc * ldp * 8);
-  BA(d.bpc, (size_t)P * Bp * ldp * 2);
+  const bool e8 = pr->xdt == kXFP8;
+  d.e8 = e8 ? 1 : 0;
+  d.ldp8 = pad16(p);
+  d.ldn8 = pad16(n);
+  if (e8) {
+    if (!tcx_enabled())
+      return api_fail(KSC_ERR_UNIMPLEMENTED, "batched solves on E4M3 X take the tensor-core exact products");
+    d.bpc = nullptr;
+    d.rpc = nullptr;
+    BA(d.bpc8, (size_t)kTcE4m3Pieces * Bp * d.ldp8);
+    BA(d.rpc8, (size_t)kTcE4m3Pieces * Bp * d.ldn8);
+    BA(d.rbuf, (size_t)Bc * ldn * 4);
+    BA(d.rmaxp, (size_t)Bc * batch_nrt(n) * 4);
+    BA(d.rs_fwd, (size_t)Bc * 4);
+    BA(d.rs_grad, (size_t)Bc * 4);
+    d.xscale = pr->dev.xscale;
+  } else {
+    BA(d.bpc, (size_t)P * Bp * ldp * 2);
+    BA(d.rpc, (size_t)P * Bp * ldn * 2);
+  }
   BA(d.U, (size_t)Bc * 3 * ldn * 8);
   BA(d.u_ref, (size_t)Bc * ldn * 8);
   BA(d.r_ref, (size_t)Bc * ldn * 8);
-  BA(d.rpc, (size_t)P * Bp * ldn * 2);
   BA(d.G, (size_t)Bc * ldp * 8);
   BA(d.G_ref, (size_t)Bc * ldp * 8);
   BA(d.slot_cur, (size_t)Bc * 4);
@@ -221,16 +248,25 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bo
     ws->Xb = pr->X;
     ws->ldxb = pr->ldx;
   } else {
+    // row stride in elements (BF16: ldp, E4M3: ldp8), a multiple of 16 bytes
+    const size_t es = xelem(pr), lde = e8 ? (size_t)d.ldp8 : ldp;
     void* xb = nullptr;
-    BA(xb, (size_t)n * ldp * 2);
-    KB_CUDA(cudaMemcpy2DAsync(xb, ldp * 2, pr->X, pr->ldx * 2, (size_t)p * 2, n, cudaMemcpyDeviceToDevice, s));
+    BA(xb, (size_t)n * lde * es);
+    KB_CUDA(cudaMemcpy2DAsync(xb, lde * es, pr->X, pr->ldx * es, (size_t)p * es, n, cudaMemcpyDeviceToDevice, s));
     ws->Xb = xb;
-    ws->ldxb = (int64_t)ldp;
+    ws->ldxb = (int64_t)lde;
   }
 #undef BA
-  // every row the products read must be finite: zero the buffers once
-  KB_CUDA(cudaMemsetAsync(d.bpc, 0, (size_t)P * Bp * ldp * 2, s));
-  KB_CUDA(cudaMemsetAsync(d.rpc, 0, (size_t)P * Bp * ldn * 2, s));
+  // every row the products read must be finite: zero the buffers once (E4M3 0x00 is +0)
+  if (e8) {
+    KB_CUDA(cudaMemsetAsync(d.bpc8, 0, (size_t)kTcE4m3Pieces * Bp * d.ldp8, s));
+    KB_CUDA(cudaMemsetAsync(d.rpc8, 0, (size_t)kTcE4m3Pieces * Bp * d.ldn8, s));
+    KB_CUDA(cudaMemsetAsync(d.rs_fwd, 0, (size_t)Bc * 4, s));
+    KB_CUDA(cudaMemsetAsync(d.rs_grad, 0, (size_t)Bc * 4, s));
+  } else {
+    KB_CUDA(cudaMemsetAsync(d.bpc, 0, (size_t)P * Bp * ldp * 2, s));
+    KB_CUDA(cudaMemsetAsync(d.rpc, 0, (size_t)P * Bp * ldn * 2, s));
+  }
   KB_CUDA(cudaMemsetAsync(d.beta, 0, (size_t)Bc * 3 * ldp * 8, s));
   KB_CUDA(cudaMemsetAsync(d.U, 0, (size_t)Bc * 3 * ldn * 8, s));
   KB_CUDA(cudaMemsetAsync(d.u_ref, 0, (size_t)Bc * ldn * 8, s));
@@ -261,11 +297,29 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bo
   d.nft = nft;
   d.Bpad = ws->Bpad;
   d.B = Bc;
-  if (exact_tc && tcx_enabled()) {
+  if ((exact_tc || e8) && tcx_enabled()) {
     const char* why = "";
-    if (!tcx_slices_build(&ws->xs_fwd, pr->X, n, p, pr->ldx, s, &why) ||
-        !tcx_slices_build(&ws->xs_grad, pr->dev.Xc, p, n, pr->dev.ldc, s, &why) ||
-        !tcx_vecs_alloc(&ws->vs_fwd, Bc, p, &why) || !tcx_vecs_alloc(&ws->vs_grad, Bc, n, &why))
+    bool ok;
+    if (e8) {
+      // the slices are cut from the represented matrix X_ij s_j, exact in BF16
+      // (4 significant bits times a power of two), held only while they are built
+      void* t = nullptr;
+      const size_t ldt = (size_t)std::max(d.ldp8, d.ldn8);
+      KB_CUDA(cudaMalloc(&t, (size_t)std::max(n, p) * ldt * 2));
+      launch_fp8_to_bf16(pr->X, pr->ldx, n, p, pr->dev.xscale, 1, t, (int64_t)d.ldp8, s);
+      ok = tcx_slices_build(&ws->xs_fwd, t, n, p, d.ldp8, s, &why);
+      if (ok) {
+        launch_fp8_to_bf16(pr->dev.Xc, pr->dev.ldc, p, n, pr->dev.xscale, 0, t, (int64_t)d.ldn8, s);
+        ok = tcx_slices_build(&ws->xs_grad, t, p, n, d.ldn8, s, &why);
+      }
+      const cudaError_t se = cudaStreamSynchronize(s);
+      cudaFree(t);
+      KB_CUDA(se);
+    } else {
+      ok = tcx_slices_build(&ws->xs_fwd, pr->X, n, p, pr->ldx, s, &why) &&
+           tcx_slices_build(&ws->xs_grad, pr->dev.Xc, p, n, pr->dev.ldc, s, &why);
+    }
+    if (!ok || !tcx_vecs_alloc(&ws->vs_fwd, Bc, p, &why) || !tcx_vecs_alloc(&ws->vs_grad, Bc, n, &why))
       return api_fail(KSC_ERR_OOM, std::string("exact tensor-core products: ") + why);
     ws->tcx = true;
     ws->bytes += ws->xs_fwd.bytes + ws->xs_grad.bytes + ws->vs_fwd.bytes + ws->vs_grad.bytes;
@@ -314,6 +368,7 @@ TcEpi fwd_epi(const BatchWs* ws) {
   e.part = d.fpart;
   e.tile_active = d.tile_run;
   e.skws = ws->skws;
+  if (d.e8) e.rscale = d.rs_fwd;
   return e;
 }
 
@@ -326,6 +381,10 @@ TcEpi grad_epi(const BatchWs* ws) {
   e.ldo = d.ldp;
   e.tile_active = d.tile_run;
   e.skws = ws->skws;
+  if (d.e8) {
+    e.rscale = d.rs_grad;
+    e.cscale = d.xscale;
+  }
   return e;
 }
 
@@ -336,6 +395,7 @@ void enqueue_step(const BatchWs* ws, cudaStream_t s, const cudaEvent_t* ev) {
   };
   mark(0);
   launch_bresid(ws->bd, s);
+  if (ws->bd.e8) launch_bsplit8_resid(ws->bd, s);
   mark(1);
   tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
   mark(2);
@@ -380,6 +440,10 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   const char* why = "";
   const Dev& sd = pr->dev;
   auto make = [&](int bf, int bg) -> bool {
+    if (d.e8)
+      return tc_plan(&ws->fwd, d.bpc8, kTcE4m3Pieces, B, ws->Bpad, d.p, d.ldp8, ws->Xb, d.n, ws->ldxb, bf, &why,
+                     1) &&
+             tc_plan(&ws->grad, d.rpc8, kTcE4m3Pieces, B, ws->Bpad, d.n, d.ldn8, sd.Xc, d.p, sd.ldc, bg, &why, 1);
     return tc_plan(&ws->fwd, d.bpc, d.P, B, ws->Bpad, d.p, d.ldp, ws->Xb, d.n, ws->ldxb, bf, &why) &&
            tc_plan(&ws->grad, d.rpc, d.P, B, ws->Bpad, d.n, d.ldn, sd.Xc, d.p, sd.ldc, bg, &why);
   };
@@ -713,6 +777,7 @@ ksc_status session_admit(Session* se, const std::vector<const ksc_node*>& nodes,
     if ((st = zero_anchor_prepare(se)) != KSC_OK) return st;
     KB_CUDA(cudaMemcpyAsync(ws->dlist, slots->data(), (size_t)cnt * 4, cudaMemcpyHostToDevice, s));
     launch_bzero_anchor(d, ws->dlist, cnt, ws->r0, ws->G0, s);
+    if (d.e8) launch_bsplit8_beta(d, ws->dlist, cnt, s);
     if ((st = upload_tile_flags(se)) != KSC_OK) return st;
     tc_launch(ws->fwd, fwd_epi(ws), kTcAnchor, s);
     pr->launches += 4 + ws->sk_fwd;
@@ -736,7 +801,8 @@ bool session_advance(Session* se, ksc_status* st) {
     *st = api_fail(KSC_ERR_CUDA, std::string("batch graph launch: ") + cudaGetErrorString(e));
     return false;
   }
-  pr->launches += (int64_t)(kLaunchesPerBatchStep + se->ws->sk_fwd + se->ws->sk_grad) * kBatchStepsPerGraph;
+  pr->launches += (int64_t)(kLaunchesPerBatchStep + se->ws->bd.e8 + se->ws->sk_fwd + se->ws->sk_grad) *
+                  kBatchStepsPerGraph;
   return true;
 }
 
@@ -927,7 +993,8 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
       if (first == KSC_OK) first = KSC_ERR_INFEASIBLE_NODE;
       continue;
     }
-    if (batch_supported(pr) && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
+    const bool eig_fp8 = (nodes[i].flags & KSC_FLAG_EIG) && pr->xdt == kXFP8;
+    if (batch_supported(pr) && !eig_fp8 && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
     else if (nodes[i].flags & KSC_FLAG_EIG)
       return api_fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on the batched path (BF16 X, k' < 2048)");
     else single.push_back(i);

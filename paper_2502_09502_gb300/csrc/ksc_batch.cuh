@@ -23,9 +23,19 @@
 //   r_ref     B x ldn       FP64 grad F(u_ref)
 //   rpc       P x Bpad x ldn  BF16 pieces of fl32(grad F(u_gamma) - r_ref)
 //   G, G_ref  B x ldp       FP64 X^T grad F(u_gamma), X^T r_ref
+//
+// E4M3 X (per-column power-of-two scales s_j, e8 = 1): the products read E4M3 X
+// and kTcE4m3Pieces E4M3 pieces of each difference, scaled per node by a power
+// of two (k_tcgemm.cu, ksc_tc.h): bpc8 holds the pieces of s_j (beta_j -
+// beta_ref_j) (the column scales folded into the vector), rpc8 those of
+// grad F(u_gamma) - r_ref (the column scales applied to X^T r in the epilogue);
+// rs_fwd / rs_grad hold each node's inverse scale.  The residual differences go
+// through rbuf (FP32) with per-CTA maxima in rmaxp, so that the pieces are cut
+// once the node's largest entry is known.
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -105,6 +115,16 @@ struct BatchDev {
   int* tile_run;       // per 128 slots: any node running (k_bstep and the host keep it)
   double xfro;         // ||X||_F, rounded up (eigen-perspective certificate)
   double ynorm;        // ||y||_2, rounded up
+  // E4M3 X (e8 = 1): see the header comment
+  int e8;
+  int ldp8, ldn8;      // byte strides of the E4M3 pieces (multiples of 16)
+  uint8_t* bpc8;       // kTcE4m3Pieces x Bpad x ldp8
+  uint8_t* rpc8;       // kTcE4m3Pieces x Bpad x ldn8
+  float* rs_fwd;       // B: inverse scale of the node's forward pieces
+  float* rs_grad;      // B: inverse scale of the node's residual pieces
+  float* rbuf;         // B x ldn: FP32 residual differences
+  float* rmaxp;        // B x nrt: their per-CTA largest magnitudes
+  const float* xscale; // p: the column scales s_j
 };
 
 __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows - 1) / (kBThreads * kBRows); }
@@ -112,6 +132,11 @@ __host__ __device__ inline int batch_nrt(int n) { return (n + kBThreads * kBRows
 size_t bprox_smem_bytes(int wsm);
 cudaError_t batch_prepare(int optin);
 void launch_bresid(const BatchDev& d, cudaStream_t s);
+// E4M3: the residual differences' pieces from rbuf, once every CTA's maximum is in
+void launch_bsplit8_resid(const BatchDev& d, cudaStream_t s);
+// E4M3: the pieces of beta slot 1 - beta_ref of the listed nodes (the zero anchor's
+// admission product)
+void launch_bsplit8_beta(const BatchDev& d, const int* list, int count, cudaStream_t s);
 void launch_bprox(const BatchDev& d, cudaStream_t s);
 void launch_bstep(const BatchDev& d, cudaStream_t s);
 // admission of the slots in `list` (device int array, count entries): beta slots

@@ -132,6 +132,9 @@ void launch_split(const double* src, float* hi, float* lo, int n, cudaStream_t s
 void launch_colnorm(const Dev& d, cudaStream_t s);
 // column-major copy Xc of X
 void launch_transpose(const Dev& d, cudaStream_t s);
+// BF16 copy of E4M3 rows times their column (per_col) or row scales; padding zeroed
+void launch_fp8_to_bf16(const void* src, int64_t ld_src, int rows, int cols, const float* scale, int per_col,
+                        void* dst, int64_t ld_dst, cudaStream_t s);
 // per row of X: max_j |x_ij| and sum_j |x_ij| (the Poisson / Gamma step constant)
 void launch_rowstats(const Dev& d, double* rmax, double* rl1, cudaStream_t s);
 // set the kernels' dynamic shared memory limits, once per device (the first call

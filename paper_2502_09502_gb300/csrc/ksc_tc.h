@@ -18,6 +18,15 @@ namespace ksc {
 
 enum : int { kTcStore = 0, kTcAdd = 1, kTcAnchor = 2 };
 
+// E4M3 operands (plan e8 = 1): B is E4M3 X (its power-of-two column scales kept
+// apart), A holds kTcE4m3Pieces E4M3 pieces of the vectors, each row scaled by a
+// power of two so that its largest entry lies in [128, 256); the epilogue
+// multiplies row m by rscale[m] (the inverse scale) and, when cscale is given,
+// column j by cscale[j] -- both exact in FP32.  Four pieces (4 significant bits
+// each, the smallest subnormal 2^-9) carry each entry to 2^-16 of the row's
+// largest, about the FP32 accumulation error of the K-long sums they feed.
+constexpr int kTcE4m3Pieces = 4;
+
 // Epilogues (row m of the product D, columns j < N):
 //   kTcStore   out[m * ldo + j] = D                                   (FP32)
 //   kTcAdd     out64[m * ldo + j] = base[m * ldb + j] + D             (FP64)
@@ -46,6 +55,8 @@ struct TcEpi {
   int npart;
   double* part;
   const int* tile_active;   // per 128-row M tile: 0 = every row finished, skip the tile (NULL: none)
+  const float* rscale;      // E4M3 plans: per row m, the inverse of its pieces' scale (NULL: 1)
+  const float* cscale;      // E4M3 plans: per column j of D (NULL: 1)
   float* skws;              // stream-K partial tiles: 2 * grid * 128 * BN floats (stream-K plans only)
 };
 
@@ -53,13 +64,14 @@ struct TcPlan {
   alignas(64) unsigned char tmA[128];   // CUtensorMap of the stacked A pieces
   alignas(64) unsigned char tmB[128];   // CUtensorMap of B
   int P, M, Mpad, N, K, bn;
+  int e8;      // 1: E4M3 operands (kind::f8f6f4), K blocks of 128
   int ok;
   int sk;      // 1: stream-K schedule over `grid` persistent CTAs (M <= 1024)
   int grid;
 };
 
 // Stream-K schedule (tc_plan_stream_k): the active 128 x BN tiles times their
-// K blocks of 64 form one iteration space, split evenly over `grid` CTAs (one per
+// K blocks of 128 bytes form one iteration space, split evenly over `grid` CTAs (one per
 // SM).  A CTA runs its range tile by tile with a double-buffered TMEM accumulator,
 // so the epilogue of one tile overlaps the products of the next; a tile whose
 // K blocks span several CTAs leaves FP32 partial tiles in skws, summed in CTA
@@ -71,13 +83,13 @@ size_t tc_skws_floats(int grid, int bn);
 // tile widths (columns of B per CTA) the kernel is built for
 constexpr int kTcBNs[3] = {64, 128, 256};
 
-// Build the tensor maps.  A: device BF16, (P * Mpad) x lda elements, lda * 2 a
-// multiple of 16 bytes, Mpad (the row stride of the pieces) a multiple of 128;
-// rows M .. round_up(M, 128) - 1 of each piece are read (and must be finite) but
-// not stored.  B: device BF16, N x ldb.  Returns false (with a message in *why)
-// when the shapes or the driver refuse.
+// Build the tensor maps.  A: device BF16 (e8: E4M3), (P * Mpad) x lda elements,
+// the row stride in bytes a multiple of 16, Mpad (the row stride of the pieces) a
+// multiple of 128; rows M .. round_up(M, 128) - 1 of each piece are read (and must
+// be finite) but not stored.  B: device BF16 (e8: E4M3), N x ldb.  Returns false
+// (with a message in *why) when the shapes or the driver refuse.
 bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t lda, const void* B,
-             int N, int64_t ldb, int bn, const char** why);
+             int N, int64_t ldb, int bn, const char** why, int e8 = 0);
 // enqueue one product; mode kTcStore, kTcAdd or kTcAnchor
 void tc_launch(const TcPlan& plan, const TcEpi& epi, int mode, cudaStream_t s);
 // device error word of the product kernels (nonzero: a wait gave up); reset by tc_clear_error

@@ -1,4 +1,4 @@
-// ksc_tc_api.cu -- ksc_tc_gemm, ksc_tc_gemm_sk and ksc_tc_exact: the batched
+// ksc_tc_api.cu -- ksc_tc_gemm, ksc_tc_gemm_sk, ksc_tc_gemm_e4m3 and ksc_tc_exact: the batched
 // solver's tensor-core products on caller-owned device buffers, exported so that
 // tests can check them on their own.
 #include <cuda_runtime.h>
@@ -70,6 +70,42 @@ extern "C" ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, i
   int word = 0;
   cudaMemcpy(&word, tc_error_word(), sizeof word, cudaMemcpyDeviceToHost);
   if (word != 0) return ksc_internal_fail(KSC_ERR_TIMEOUT, "stream-K product: a device wait gave up");
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_tc_gemm_e4m3(const void* A, int32_t m, int32_t m_pad, int32_t k, int64_t lda,
+                                       const void* B, int32_t n, int64_t ldb, const float* row_scale,
+                                       const float* col_scale, float* D, int64_t ldd, int32_t tile_n, int32_t grid,
+                                       void* cuda_stream) {
+  if (!A || !B || !D || !row_scale) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "NULL operand");
+  if (ldd < n || (ldd % 4) != 0 || ((uintptr_t)D % 16) != 0)
+    return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldd must be >= n, a multiple of 4, D 16-byte aligned");
+  if (grid < 0 || grid > 4096) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "grid must be in [0, 4096]");
+  TcPlan plan;
+  const char* why = "";
+  if (!tc_plan(&plan, A, kTcE4m3Pieces, m, m_pad, k, lda, B, n, ldb, tile_n, &why, 1) ||
+      (grid > 0 && !tc_plan_stream_k(&plan, grid, &why)))
+    return ksc_internal_fail(KSC_ERR_INVALID_ARG, why);
+  float* ws = nullptr;
+  if (grid > 0 && cudaMalloc(&ws, tc_skws_floats(grid, tile_n) * sizeof(float)) != cudaSuccess)
+    return ksc_internal_fail(KSC_ERR_OOM, "stream-K partials");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  tc_clear_error(s);
+  TcEpi e{};
+  e.out = D;
+  e.ldo = ldd;
+  e.skws = ws;
+  e.rscale = row_scale;
+  e.cscale = col_scale;
+  tc_launch(plan, e, kTcStore, s);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (ws) cudaFree(ws);
+  if (err != cudaSuccess)
+    return ksc_internal_fail(KSC_ERR_CUDA, (std::string("E4M3 product: ") + cudaGetErrorString(err)).c_str());
+  int word = 0;
+  cudaMemcpy(&word, tc_error_word(), sizeof word, cudaMemcpyDeviceToHost);
+  if (word != 0) return ksc_internal_fail(KSC_ERR_TIMEOUT, "E4M3 product: a device wait gave up");
   return KSC_OK;
 }
 

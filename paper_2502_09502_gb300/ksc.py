@@ -36,7 +36,8 @@ KSC_KERNEL_PROX_SELECT, KSC_KERNEL_PROX_APPLY = 10, 11
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_bnb_solve", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
-           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk", "ksc_tc_exact",
+           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk", "ksc_tc_gemm_e4m3",
+           "ksc_tc_exact",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
            "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state", "ksc_problem_eig_lambda",
            "ksc_problem_set_eig_lambda",
@@ -117,6 +118,9 @@ def _load():
     L.ksc_tc_gemm_sk.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                                  C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                                  C.c_int32, C.c_void_p]
+    L.ksc_tc_gemm_e4m3.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_int32,
+                                   C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_int32,
+                                   C.c_void_p]
     L.ksc_tc_exact.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int64, C.c_void_p, C.c_int32, C.c_int64,
                                C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p]
     L.ksc_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(C.c_void_p)]
@@ -263,6 +267,14 @@ def ksc_tc_exact(a_ptr, c, k, lda, v_ptr, r, ldv, d_ptr, ldd, stream=None) -> fl
     _check(lib.ksc_tc_exact(C.c_void_p(a_ptr), int(c), int(k), int(lda), C.c_void_p(v_ptr), int(r), int(ldv),
                             C.c_void_p(d_ptr), int(ldd), C.byref(eps), _stream_ptr(stream)))
     return eps.value
+
+
+def ksc_tc_gemm_e4m3(a_ptr, m, m_pad, k, lda, b_ptr, n, ldb, rs_ptr, cs_ptr, d_ptr, ldd, tile_n, grid,
+                     stream=None):
+    """E4M3 tensor-core product on device buffers (see include/ksc.h); blocks until done."""
+    _check(lib.ksc_tc_gemm_e4m3(C.c_void_p(a_ptr), int(m), int(m_pad), int(k), int(lda), C.c_void_p(b_ptr),
+                                int(n), int(ldb), C.c_void_p(rs_ptr), C.c_void_p(cs_ptr) if cs_ptr else None,
+                                C.c_void_p(d_ptr), int(ldd), int(tile_n), int(grid), _stream_ptr(stream)))
 
 
 def ksc_tc_gemm_sk(a_ptr, pieces, m, m_pad, k, lda, b_ptr, n, ldb, d_ptr, ldd, tile_n, grid, stream=None):
