@@ -75,9 +75,13 @@ def parse():
                     help="serving: Poisson rates as fractions of the saturation throughput")
     ap.add_argument("--window", type=float, default=8.0, help="serving: seconds of arrivals per rate")
     ap.add_argument("--slots", type=int, default=256, help="serving: slots per problem session")
-    ap.add_argument("--max-iter", type=int, default=4000, help="serving: iteration cap per request")
+    ap.add_argument("--max-iter", type=int, default=20000, help="serving: iteration cap per request")
+    ap.add_argument("--root-max-iter", type=int, default=0,
+                    help="serving: iteration cap of the pool's root solves (warm starts; 0: --max-iter)")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default line: leave out the compact serving leg")
     ap.add_argument("--bnb-seconds", type=float, default=90.0, help="bnb: time limit")
-    ap.add_argument("--bnb-batch", type=int, default=256, help="bnb: nodes in flight")
+    ap.add_argument("--bnb-batch", type=int, default=1024, help="bnb: nodes in flight (per launch)")
     ap.add_argument("--bnb-gap", type=float, default=1e-4, help="bnb: relative gap to certify")
     ap.add_argument("--bnb-n", type=int, default=20000, help="bnb: rows")
     ap.add_argument("--bnb-p", type=int, default=200000, help="bnb: columns")
@@ -401,9 +405,10 @@ def run_small(args, reps=20, samples=5):
 
 # ------------------------------------------------------------------ branch and bound
 
-BNB = dict(workload="best-first branch and bound, least squares BF16 X n=20000 p=200000 k=15 lambda2=0.1 M=2 "
-                    "toeplitz 0.7, 15 x +-1, SNR 3 (X drawn on the device), node bounds from the batched "
-                    "solver with continuous batching")
+BNB = dict(workload="best-first branch and bound, least squares X n=20000 p=200000 k=15 lambda2=0.1 M=2 "
+                    "toeplitz 0.7, 15 x +-1, SNR 3 (X drawn on the device in BF16; --x-dtype fp8: FP8 e4m3 "
+                    "with power-of-two column scales), node bounds from the batched solver with continuous "
+                    "batching")
 
 
 def run_bnb(args):
@@ -419,7 +424,20 @@ def run_bnb(args):
     X, y, bstar = G.device_problem(n, p, r=0.7, seed=args.seed, loss=G.LSQ, k_true=15, snr=3.0)
     torch.cuda.synchronize()
     stream = torch.cuda.Stream()
-    prob = K.Problem(X, y, K.KSC_LOSS_LSQ, stream=stream)
+    fp8 = args.x_dtype == "fp8"
+    if fp8:
+        # E4M3 with one power-of-two scale per column: s_j = 2^ceil(log2(max_i |X_ij| / 448))
+        amax = X.float().abs().amax(dim=0).clamp_min(1e-30)
+        s = torch.exp2(torch.ceil(torch.log2(amax / 448.0)))
+        X8 = torch.empty((n, p), dtype=torch.float8_e4m3fn, device="cuda")
+        for j0 in range(0, n, 2048):    # in row blocks: no FP32 copy of the whole matrix
+            X8[j0:j0 + 2048] = (X[j0:j0 + 2048].float() / s).to(torch.float8_e4m3fn)
+        del X
+        torch.cuda.synchronize()
+        prob = K.Problem(X8, y, K.KSC_LOSS_LSQ, stream=stream, col_scale=s.cpu().numpy().astype(np.float32))
+        del X8
+    else:
+        prob = K.Problem(X, y, K.KSC_LOSS_LSQ, stream=stream)
     setup = time.perf_counter() - t0
     beta, res = prob.bnb(0.1, 2.0, k, opt_gap=args.bnb_gap, time_limit_s=args.bnb_seconds, batch=args.bnb_batch,
                          node_rel_gap=1e-6, node_max_iter=20000)
@@ -428,8 +446,10 @@ def run_bnb(args):
     return {
         "metric": "branch-and-bound nodes/s", "value": round(res["nodes"] / max(res["seconds"], 1e-9), 2),
         "unit": "nodes/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16", "data": "synthetic (seeded Toeplitz AR(1) rows drawn on the device)",
-        "config": dict(BNB, n=n, p=p, k=k, opt_gap=args.bnb_gap, time_limit_s=args.bnb_seconds,
+        "vs_baseline": None, "dtype": "fp8-e4m3" if fp8 else "bf16",
+        "data": "synthetic (seeded Toeplitz AR(1) rows drawn on the device)",
+        "config": dict(BNB, n=n, p=p, k=k, x_dtype="fp8-e4m3" if fp8 else "bf16", opt_gap=args.bnb_gap,
+                       time_limit_s=args.bnb_seconds,
                        batch=args.bnb_batch, parallelism="single GPU"),
         "setup_s": round(setup, 1), "result": {kk: (float(f"{v:.10g}") if isinstance(v, float) else v)
                                                 for kk, v in res.items()},
@@ -536,8 +556,8 @@ def run_serving(args):
         prob = K.Problem(X, y, sp["loss"], stream=stream)
         del X
         used += prob.bytes
-        root = prob.solve(K.Node(sp["lambda2"], sp["M"], sp["k"], rel_gap_tol=1e-6, max_iter=args.max_iter),
-                          want_z=False)
+        root = prob.solve(K.Node(sp["lambda2"], sp["M"], sp["k"], rel_gap_tol=1e-6,
+                                 max_iter=args.root_max_iter or args.max_iter), want_z=False)
         pool.append(dict(spec=sp, prob=prob, root=root.beta, root_iters=root.iters))
     setup_s = time.perf_counter() - t_setup
     u = G.uniform(args.seed, 11, 4 * args.requests)
@@ -587,6 +607,7 @@ def run_serving(args):
         flops = sum(12.0 * d[1]["prob"].n * d[1]["prob"].p * d[2].iters for d in done)
         return {"offered_per_s": None if offered is None else round(offered, 3),
                 "achieved_per_s": round(len(ok) / span, 3), "requests": len(done), "certified": len(ok),
+                "certified_fraction": round(len(ok) / max(len(done), 1), 4),
                 "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
                 "span_s": round(span, 3), "tensor_tflops_executed": round(flops / span / 1e12, 1)}
 
@@ -638,6 +659,24 @@ def run_serving(args):
         "tensor_frac_of_sustained_peak": round(sat["tensor_tflops_executed"] / peak, 4),
         "server": st, "alone_vs_mix_max_rel_dual_diff": float(max(inv)) if inv else None,
     }
+
+
+def serving_leg(args):
+    """The compact serving leg of the default line: a pool of 8 problems from the
+    mix, a burst of 64 requests (saturation) and one Poisson stream at half of it,
+    with p50/p99 latency and the certified fraction of each.  Requests (and the
+    pool's root solves) are capped at 4000 iterations here so that the leg ends in
+    a few minutes; the serving workload's own default cap is 20000."""
+    a = argparse.Namespace(**vars(args))
+    a.pool, a.burst, a.rates, a.window, a.requests = 8, 64, [0.5], 10.0, 256
+    a.max_iter, a.root_max_iter, a.slots = 4000, 4000, 256
+    r = run_serving(a)
+    keep = ("metric", "value", "unit", "config", "setup_s", "saturation", "latency_vs_throughput",
+            "tensor_frac_of_sustained_peak", "alone_vs_mix_max_rel_dual_diff")
+    out = {k: r[k] for k in keep if k in r}
+    out["config"] = {k: v for k, v in out["config"].items() if k != "pool"}
+    out["config"]["pool_problems"] = a.pool
+    return out
 
 
 # ------------------------------------------------------------------ batched workload
@@ -1145,6 +1184,8 @@ def main():
                 if k in b}
             if "oracle_subsample" in b:
                 out["batched"]["oracle_subsample"] = b["oracle_subsample"]
+        if not args.no_serving and world == 1 and not args.small:
+            out["serving"] = serving_leg(args)
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

@@ -70,7 +70,8 @@ typedef enum {
   KSC_BF16 = 2,                 /* X in bfloat16 bits; the problem is the stored X  */
   KSC_FP8_E4M3_COLSCALE = 3     /* X in FP8 e4m3 bits with a per-column scale s_j, a
                                    power of two in [2^-100, 2^100]; the problem's matrix
-                                   is X_ij * s_j, exact in FP32 (single-node solver)  */
+                                   is X_ij * s_j, exact in FP32 (single-node and
+                                   batched solvers, branch and bound)                */
   /* X is streamed from HBM in its storage type.  The iterate vectors (beta, X beta,
      the gradient) are FP64 for every type; products with FP32/BF16 X are made
      error-free (exact product error by fma, compensated sums). */
@@ -86,7 +87,7 @@ typedef enum {
                                         computed on first use by ksc_solve_batch and
                                         ksc_bnb_solve; ksc_server_submit refuses such a
                                         node with KSC_ERR_INVALID_ARG until it is known).
-                                        Batched path only (BF16 X): ksc_solve_node
+                                        Batched path only, BF16 X: ksc_solve_node
                                         returns KSC_ERR_UNIMPLEMENTED                  */
 
 typedef struct ksc_problem ksc_problem;
@@ -197,11 +198,12 @@ ksc_status ksc_solve_node(ksc_problem* problem, const ksc_node* node, ksc_result
 /* Solve `count` nodes of one problem together (blocking); result[i] belongs to
  * node[i].  Each result equals what ksc_solve_node returns for that node, within
  * the stated tolerance.  Returns the first non-OK per-node status, else KSC_OK.
- * With BF16 X the nodes advance in lock step (up to 1024 per device pass): both
- * products of every FISTA step run on the tensor cores for all nodes at once, on
- * differences from per-node anchor points whose products are exact, and every
- * reported bound is the FP64 certificate.  Other storage types (and nodes with
- * k' >= 2048) are solved one by one by the single-node path.  The problem's
+ * With BF16 or FP8 X the nodes advance in lock step (up to 1024 per device pass):
+ * both products of every FISTA step run on the tensor cores for all nodes at once
+ * (FP8: four E4M3 pieces of each difference against E4M3 X), on differences from
+ * per-node anchor points whose products are exact, and every reported bound is the
+ * FP64 certificate.  Other storage types (and nodes with k' >= 2048, and
+ * eigen-perspective nodes on FP8 X) are solved one by one by the single-node path.  The problem's
  * batched workspace is allocated on first use and kept (ksc_problem_bytes). */
 ksc_status ksc_solve_batch(ksc_problem* problem, const ksc_node* nodes, int32_t count,
                            ksc_result* results, void* cuda_stream);
@@ -225,8 +227,8 @@ ksc_status ksc_solve_batch(ksc_problem* problem, const ksc_node* nodes, int32_t 
  * nonzeros and a certified gap closes (its value is a feasible objective).
  * Stops when (incumbent - lower bound) / max(|incumbent|, 1e-300) <= opt_gap, when
  * every node is pruned or closed, or at max_nodes node solves (0: none) or
- * time_limit_s seconds (0: none).  Needs BF16 X (KSC_ERR_UNIMPLEMENTED
- * otherwise); k < 2048; 1 <= batch <= 1024. */
+ * time_limit_s seconds (0: none).  Needs BF16 or FP8 X (KSC_ERR_UNIMPLEMENTED
+ * otherwise; the eigen-perspective flag needs BF16); k < 2048; 1 <= batch <= 1024. */
 typedef struct {
   double lambda2, M;
   int32_t k;

@@ -64,7 +64,10 @@ extern "C" ksc_status ksc_bnb_solve(ksc_problem* pr, const ksc_bnb_params* prm, 
   if (!(prm->opt_gap >= 0) || !(prm->node_rel_gap > 0) || prm->node_max_iter < 1 || prm->max_nodes < 0 ||
       !(prm->time_limit_s >= 0))
     return api_fail(KSC_ERR_INVALID_ARG, "opt_gap >= 0, node_rel_gap > 0, node_max_iter >= 1, limits >= 0");
-  if (pr->xdt != kXBF16) return api_fail(KSC_ERR_UNIMPLEMENTED, "branch and bound needs BF16 X (batched solver)");
+  if (pr->xdt != kXBF16 && pr->xdt != kXFP8)
+    return api_fail(KSC_ERR_UNIMPLEMENTED, "branch and bound needs BF16 or FP8 X (batched solver)");
+  if (pr->xdt == kXFP8 && (prm->node_flags & KSC_FLAG_EIG))
+    return api_fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on BF16 X");
   ksc_status st = ensure_prepared();
   if (st != KSC_OK) return st;
   int cur_dev = 0;
