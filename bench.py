@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--x-dtype", default="f32", choices=["f32", "fp8"],
                     help="single workload: X in FP32 (default) or FP8 e4m3 with per-column power-of-two "
-                         "scales quantized from the same FP32 instance (the experiment of the precision pattern)")
+                         "scales quantized from the same FP32 instance (the experiment of the precision pattern); "
+                         "batched and bnb workloads: fp8 replaces their BF16 X the same way")
     ap.add_argument("--no-batched", action="store_true",
                     help="single workload: leave out the batched comparison object")
     ap.add_argument("--small", action="store_true",
@@ -763,9 +764,17 @@ def run_batched(args):
     sq = getattr(args, "loss", "logistic") == "sqhinge"
     loss = K.KSC_LOSS_SQHINGE if sq else K.KSC_LOSS_LOGISTIC
     n, p, B = P.n, P.p, args.nodes
+    fp8 = getattr(args, "x_dtype", "f32") == "fp8"
     Xd = torch.from_numpy(P.X.view(np.int16)).cuda().view(torch.bfloat16)
     stream = torch.cuda.Stream()
-    prob = K.Problem(Xd, P.y, loss, stream=stream)
+    if fp8:
+        # FP8 e4m3 with power-of-two column scales, quantized from the BF16 instance;
+        # the solved problem is the represented matrix X_ij s_j
+        bits, sc = G.quantize_fp8(G.bf16_to_f32(P.X))
+        Xd = torch.from_numpy(bits).cuda().view(torch.float8_e4m3fn)
+        prob = K.Problem(Xd, P.y, loss, stream=stream, col_scale=sc)
+    else:
+        prob = K.Problem(Xd, P.y, loss, stream=stream)
     root = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6))
     sets = G.node_sets(p, B, seed=args.seed, max_zero=200, max_one=9)
     pert = G.warm_perturbation(p, B, seed=args.seed)
@@ -831,13 +840,18 @@ def run_batched(args):
         peak, peak_kind = float(pk["bf16_tflops_sustained"]), "measured (sustained)"
     except Exception:
         peak, peak_kind = 1700.0, "fallback (sustained)"
+    bf16_peak = peak
+    if fp8:
+        # E4M3 products: the BF16 peak times the nominal FP8 / BF16 ratio (4.5 / 2.25)
+        peak, peak_kind = 2.0 * peak, peak_kind + " BF16 x 2 (nominal FP8/BF16 ratio)"
+    pieces_label = "4 E4M3 pieces" if fp8 else "3 BF16 pieces"
 
     def tensor_line(key, label):
         nl_, ms_ = kt[key]
         ach = alg / (ms_ / 1e3) / 1e12
         return {"bound": "tensor", "kernel": label, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
                 "peak_kind": peak_kind, "frac": round(ach / peak, 4), "traffic": None,
-                "flops_per_launch": alg / max(nl_, 1), "pieces": 3, "node_steps": node_steps,
+                "flops_per_launch": alg / max(nl_, 1), "pieces": 4 if fp8 else 3, "node_steps": node_steps,
                 "avg_launch_ms": round(ms_ / max(nl_, 1), 5), "launches": nl_}
 
     exact_products = 2.0 * (bstats["batch_certificates"] + bstats["batch_anchors"])
@@ -858,12 +872,14 @@ def run_batched(args):
         exact_line = {"bound": "tensor", "kernel": "exact products of anchors and certificates on the tensor "
                                                    "cores (k_tcx, 18 BF16 slice products each; the anchor and "
                                                    "certificate phases' device time)",
-                      "achieved": round(ex_ach, 1), "peak": peak, "unit": "TFLOP/s", "peak_kind": peak_kind,
-                      "frac": round(ex_ach / peak, 4), "executed_flops": ex_flops}
+                      "achieved": round(ex_ach, 1), "peak": bf16_peak, "unit": "TFLOP/s",
+                      "peak_kind": "measured (sustained)" if "measured" in peak_kind else "fallback (sustained)",
+                      "frac": round(ex_ach / bf16_peak, 4), "executed_flops": ex_flops}
     exact_line.update({"traffic": None, "products": exact_products, "multiply_adds": macs,
                        "exact_fp64_multiply_adds_per_s": round(fp64_rate * 1e12, 1), "device_ms": round(ex_ms, 2)})
-    rooflines = {"xt_r": tensor_line("xt_r", "X^T r for the running nodes (k_tcgemm, 3 BF16 pieces)"),
-                 "x_dbeta": tensor_line("x_dbeta", "X (beta - beta_ref) for the running nodes (k_tcgemm, 3 BF16 pieces)"),
+    rooflines = {"xt_r": tensor_line("xt_r", f"X^T r for the running nodes (k_tcgemm, {pieces_label})"),
+                 "x_dbeta": tensor_line("x_dbeta", f"X (beta - beta_ref) for the running nodes (k_tcgemm, "
+                                                   f"{pieces_label})"),
                  "exact_products": exact_line}
     phase_ms = {"exact_products": ex_ms, "xt_r": kt["xt_r"][1], "x_dbeta": kt["x_dbeta"][1]}
     dominant = max(phase_ms, key=phase_ms.get)
@@ -890,7 +906,10 @@ def run_batched(args):
         wall = time.perf_counter() - t0
         return len(sample) / (e0.elapsed_time(e1) / 1e3), len(sample) / wall
 
-    X32 = Xd.float()
+    if fp8:
+        X32 = (torch.from_numpy(G.fp8_values(bits)) * torch.from_numpy(sc)[None, :]).cuda()
+    else:
+        X32 = Xd.float()
     prob32 = K.Problem(X32, P.y, loss, stream=stream)
     plain32, plain32_wall = plain_rate(prob32)
     prob32.close()
@@ -898,10 +917,16 @@ def run_batched(args):
     plain16, plain16_wall = plain_rate(prob)
     plain = plain32
     # end to end: X from pinned host memory into a new problem, the batched call, results back
-    Xh = torch.from_numpy(P.X.view(np.int16)).pin_memory()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    prob2 = K.Problem(Xh.numpy().view(np.uint16), P.y, loss, stream=stream, x_dtype=K.KSC_BF16)
+    if fp8:
+        Xh = torch.from_numpy(bits).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob2 = K.Problem(Xh.numpy(), P.y, loss, stream=stream, x_dtype=K.KSC_FP8, col_scale=sc)
+    else:
+        Xh = torch.from_numpy(P.X.view(np.int16)).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prob2 = K.Problem(Xh.numpy().view(np.uint16), P.y, loss, stream=stream, x_dtype=K.KSC_BF16)
     res = prob2.solve_batch(nodes, want_beta=True)
     e_s = time.perf_counter() - t0
     prob2.close()
@@ -910,9 +935,11 @@ def run_batched(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "fp8-e4m3" if fp8 else "bf16",
         "data": "synthetic (seeded Toeplitz AR(1) rows, standardised columns)",
         "config": dict(BATCHED, nodes=B, parallelism="single GPU",
+                       **({"x_dtype": "fp8-e4m3 (power-of-two column scales, quantized from the BF16 instance)",
+                           "workload": BATCHED["workload"].replace("BF16 X", "FP8 e4m3 X")} if fp8 else {}),
                        **({"workload": BATCHED["workload"].replace("batched logistic", "batched squared hinge"),
                            "loss": "squared_hinge"} if sq else {})),
         "latency_ms": {"p50": round(float(np.percentile(lat_ms, 50)), 3),
@@ -926,16 +953,18 @@ def run_batched(args):
         "plain_single_node": {"value": round(plain32, 3), "unit": UNIT, "x_dtype": "f32", "nodes": len(sample),
                               "ratio": round(value / plain32, 2), "wall_value": round(plain32_wall, 3),
                               "sample": "every (512/nodes)-th node in order of k' = k - |S1|, CUDA events"},
-        "plain_single_node_bf16": {"value": round(plain16, 3), "unit": UNIT, "x_dtype": "bf16",
+        "plain_single_node_bf16" if not fp8 else "plain_single_node_fp8":
+            {"value": round(plain16, 3), "unit": UNIT, "x_dtype": "fp8-e4m3" if fp8 else "bf16",
                                    "nodes": len(sample), "ratio": round(value / plain16, 2),
                                    "wall_value": round(plain16_wall, 3)},
         "clocks": clk, "gpu_launches": int(launches), "kernel_time_share": shares,
-        "e2e": {"value": round(B / e_s, 3), "unit": UNIT, "h2d_bytes_per_step": int(P.X.nbytes + P.y.nbytes),
+        "e2e": {"value": round(B / e_s, 3), "unit": UNIT,
+                "h2d_bytes_per_step": int((bits.nbytes if fp8 else P.X.nbytes) + P.y.nbytes),
                 "d2h_bytes_per_step": int(B * (p * 8 + 64))},
         "roofline": dict(rooflines[dominant], dominant_of=sorted(phase_ms)),
         "rooflines": rooflines,
     }
-    if args.oracle_nodes > 0:
+    if args.oracle_nodes > 0 and not fp8:
         line["oracle_subsample"] = oracle_subsample(args.seed, args.oracle_nodes, res)
     return line
 

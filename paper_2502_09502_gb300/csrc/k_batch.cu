@@ -83,6 +83,28 @@ __device__ __forceinline__ double loss_d(double u, double y, int loss) {
   return t > 0 ? t + log1p(exp(-t)) : log1p(exp(t));
 }
 
+// The represented matrix of E4M3 X in BF16: dst[r][c] = src[r][c] * scale (the
+// scale of column c when per_col, else of row r), exact (4 significant bits times
+// a power of two); the padding columns [cols, ld_dst) are zeroed
+__global__ void __launch_bounds__(256) k_fp8_to_bf16(const __nv_fp8_e4m3* src, int64_t ld_src, int rows, int cols,
+                                                     const float* scale, int per_col, __nv_bfloat16* dst,
+                                                     int64_t ld_dst) {
+  const int r = blockIdx.y;
+  for (int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x; c < ld_dst; c += (int64_t)gridDim.x * 256) {
+    float v = 0.0f;
+    if (c < cols) v = float(src[(int64_t)r * ld_src + c]) * (per_col ? scale[c] : scale[r]);
+    dst[(int64_t)r * ld_dst + c] = __float2bfloat16_rn(v);
+  }
+}
+
+void launch_fp8_to_bf16(const void* src, int64_t ld_src, int rows, int cols, const float* scale, int per_col,
+                        void* dst, int64_t ld_dst, cudaStream_t s) {
+  const int64_t g = (ld_dst + 255) / 256;
+  const int gx = g < 64 ? (int)g : 64;
+  k_fp8_to_bf16<<<dim3(gx, rows), 256, 0, s>>>((const __nv_fp8_e4m3*)src, ld_src, rows, cols, scale, per_col,
+                                                (__nv_bfloat16*)dst, ld_dst);
+}
+
 // ------------------------------------------------------------------ residual
 
 __global__ void __launch_bounds__(kBThreads) k_bresid(BatchDev d) {

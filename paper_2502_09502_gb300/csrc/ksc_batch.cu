@@ -304,8 +304,7 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bo
       // the slices are cut from the represented matrix X_ij s_j, exact in BF16
       // (4 significant bits times a power of two), held only while they are built
       void* t = nullptr;
-      const size_t ldt = (size_t)std::max(d.ldp8, d.ldn8);
-      KB_CUDA(cudaMalloc(&t, (size_t)std::max(n, p) * ldt * 2));
+      KB_CUDA(cudaMalloc(&t, std::max((size_t)n * d.ldp8, (size_t)p * d.ldn8) * 2));
       launch_fp8_to_bf16(pr->X, pr->ldx, n, p, pr->dev.xscale, 1, t, (int64_t)d.ldp8, s);
       ok = tcx_slices_build(&ws->xs_fwd, t, n, p, d.ldp8, s, &why);
       if (ok) {
