@@ -378,18 +378,23 @@ ksc_status ksc_tc_gemm_sk(const void* A, int32_t pieces, int32_t m, int32_t m_pa
                           const void* B, int32_t n, int64_t ldb, float* D, int64_t ldd, int32_t tile_n,
                           int32_t grid, void* cuda_stream);
 
+/* E4M3 pieces of each vector row in the batched solver's products for FP8 X. */
+#define KSC_E4M3_PIECES 5
 /* The batched solver's product for E4M3 X (FP8 with power-of-two column scales),
  * exported so that it can be tested on its own; the paper has no counterpart (its
- * products are FP64).  Four E4M3 pieces of each row of the vectors, scaled by a
- * power of two per row, against E4M3 B, on the tensor cores (kind::f8f6f4):
- *   D[i][j] = row_scale[i] * col_scale[j] *
- *             sum_{q < 4} sum_{t < k} A[q * m_pad + i][t] * B[j][t]   (FP32 accumulation)
- * A, B: device E4M3 bytes, row-major with row strides lda, ldb (bytes; >= k and
- * multiples of 16), 16-byte aligned; A has 4 * m_pad rows (m_pad a multiple of
+ * products are FP64).  KSC_E4M3_PIECES E4M3 pieces of each row of the vectors, scaled by a
+ * power of two per row, against E4M3 B, on the tensor cores (kind::f8f6f4); the
+ * first three pieces and the last two go to separate accumulators, the latter
+ * weighted by 2^-12 (they carry the remainder of the first three times 2^12):
+ *   S_q[i][j] = sum_{t < k} A[q * m_pad + i][t] * B[j][t]
+ *   D[i][j] = row_scale[i] * col_scale[j] * (sum_{q < 3} S_q + 2^-12 sum_{q >= 3} S_q)
+ * (FP32 accumulation).  A, B: device E4M3 bytes, row-major with row strides lda,
+ * ldb (bytes; >= k and multiples of 16), 16-byte aligned; A has
+ * KSC_E4M3_PIECES * m_pad rows (m_pad a multiple of
  * 128; rows m..m_pad-1 of each piece are read but not stored).  row_scale: device
  * FP32, m entries; col_scale: device FP32, n entries, or NULL for 1.  D: device
  * FP32, m rows of stride ldd (>= n, a multiple of 4), 16-byte aligned.  tile_n in
- * {64, 128, 256}; grid 0: one CTA per tile, else the stream-K schedule over `grid`
+ * {64, 128}; grid 0: one CTA per tile, else the stream-K schedule over `grid`
  * CTAs (m <= 1024; allocates and frees the partials' buffer).  Blocks until done.
  * Errors as ksc_tc_gemm. */
 ksc_status ksc_tc_gemm_e4m3(const void* A, int32_t m, int32_t m_pad, int32_t k, int64_t lda, const void* B,

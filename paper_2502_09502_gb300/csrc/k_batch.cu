@@ -42,10 +42,13 @@ __device__ __forceinline__ void split_store(float v, __nv_bfloat16* dst, size_t 
 
 // E4M3 pieces of v (already scaled below 256 in magnitude): each piece is the
 // E4M3 rounding (to nearest) of what the previous pieces left, which FP32 holds
-// exactly; four pieces carry v to 2^-16 of 256 (or to the smallest subnormal)
+// exactly; pieces kTcE4m3Hi.. are cut from that remainder times 2^kTcE4m3Shift
+// (the product's second accumulator), so that no entry stops at the smallest
+// E4M3 subnormal: the pieces carry v to about 2^-30 of 256
 __device__ __forceinline__ void split8_store(float v, uint8_t* dst, size_t piece_stride) {
 #pragma unroll
   for (int q = 0; q < kTcE4m3Pieces; ++q) {
+    if (q == kTcE4m3Hi) v *= (float)(1 << kTcE4m3Shift);
     const __nv_fp8_e4m3 h(v);
     dst[q * piece_stride] = h.__x;
     v = __fsub_rn(v, float(h));
@@ -89,8 +92,8 @@ __device__ __forceinline__ double loss_d(double u, double y, int loss) {
 __global__ void __launch_bounds__(256) k_fp8_to_bf16(const __nv_fp8_e4m3* src, int64_t ld_src, int rows, int cols,
                                                      const float* scale, int per_col, __nv_bfloat16* dst,
                                                      int64_t ld_dst) {
-  const int r = blockIdx.y;
-  for (int64_t c = (int64_t)blockIdx.x * 256 + threadIdx.x; c < ld_dst; c += (int64_t)gridDim.x * 256) {
+  const int r = blockIdx.x;   // one CTA per row (rows can exceed the 65535 limit of grid y)
+  for (int64_t c = threadIdx.x; c < ld_dst; c += 256) {
     float v = 0.0f;
     if (c < cols) v = float(src[(int64_t)r * ld_src + c]) * (per_col ? scale[c] : scale[r]);
     dst[(int64_t)r * ld_dst + c] = __float2bfloat16_rn(v);
@@ -99,10 +102,8 @@ __global__ void __launch_bounds__(256) k_fp8_to_bf16(const __nv_fp8_e4m3* src, i
 
 void launch_fp8_to_bf16(const void* src, int64_t ld_src, int rows, int cols, const float* scale, int per_col,
                         void* dst, int64_t ld_dst, cudaStream_t s) {
-  const int64_t g = (ld_dst + 255) / 256;
-  const int gx = g < 64 ? (int)g : 64;
-  k_fp8_to_bf16<<<dim3(gx, rows), 256, 0, s>>>((const __nv_fp8_e4m3*)src, ld_src, rows, cols, scale, per_col,
-                                                (__nv_bfloat16*)dst, ld_dst);
+  k_fp8_to_bf16<<<rows, 256, 0, s>>>((const __nv_fp8_e4m3*)src, ld_src, rows, cols, scale, per_col,
+                                     (__nv_bfloat16*)dst, ld_dst);
 }
 
 // ------------------------------------------------------------------ residual

@@ -41,7 +41,22 @@ __host__ __device__ constexpr int tc_smem_bytes(int P, int BN) {
   return tc_stages(P, BN) * tc_stage_bytes(P, BN) + 1024 + 256;
 }
 __host__ __device__ constexpr uint32_t tc_tmem_cols(int BN) {
-  return BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+  return BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : BN <= 256 ? 256u : 512u;
+}
+
+// E4M3 plans keep two accumulators per tile: pieces [0, kTcE4m3Hi) in the tile's
+// first BN TMEM columns, the rest (cut from the residual scaled by 2^kTcE4m3Shift)
+// in the next BN; the epilogue adds them as hi + 2^-kTcE4m3Shift lo
+template <int E8>
+__device__ __forceinline__ void tmem_ld_tile16(uint32_t taddr, int bn, float* v) {
+  tmem_ld16(taddr, v);
+  if (E8) {
+    float w[16];
+    tmem_ld16(taddr + (uint32_t)bn, w);
+    constexpr float lo = 1.0f / (float)(1 << kTcE4m3Shift);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaf(w[i], lo, v[i]);
+  }
 }
 
 // F_i(u) in FP32 (summed in FP64 by the caller)
@@ -254,9 +269,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr int S = tc_stages(P, BN);
   constexpr uint32_t B_TILE = BN * 128;
   constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
-  constexpr uint32_t TCOLS = tc_tmem_cols(BN);
+  constexpr uint32_t TCOLS = tc_tmem_cols((E8 ? 2 : 1) * BN);
   static_assert(S >= 2, "at least two pipeline stages");
   static_assert(BN % 16 == 0 && BN >= 16 && BN <= 256, "MMA N for M = 128");
+  static_assert(!E8 || BN <= 128, "two E4M3 accumulators of BN columns each");
 
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -338,12 +354,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of the 128-byte row per MMA
+            const bool lo = E8 && q >= kTcE4m3Hi;   // the second accumulator's pieces
+            const uint32_t acc = (kb | (lo ? q - kTcE4m3Hi : q) | kk) != 0 ? 1u : 0u;
             if (E8)
-              umma_e4m3(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                        (kb | q | kk) != 0 ? 1u : 0u);
+              umma_e4m3(tmem + (lo ? (uint32_t)BN : 0u), sw128_desc(a_addr + kk * 32),
+                        sw128_desc(b_addr + kk * 32), idesc, acc);
             else
-              umma_bf16(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                        (kb | q | kk) != 0 ? 1u : 0u);
+              umma_bf16(tmem, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc, acc);
           }
         }
         umma_commit(&empty[s]);
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll 1
       for (int c = 0; c < BN; c += 16) {
         float v[16];
-        tmem_ld16(tbase + (uint32_t)c, v);
+        tmem_ld_tile16<E8>(tbase + (uint32_t)c, BN, v);
         epi_chunk<MODE>(sh, ep, er, m, n0 + c, v, fsum, dsum);
       }
     } else {
@@ -405,8 +422,10 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
   constexpr int S = tc_stages(P, BN);
   constexpr uint32_t B_TILE = BN * 128;
   constexpr uint32_t STAGE_TX = P * kTcATile + B_TILE;
-  constexpr uint32_t TCOLS = tc_tmem_cols2(BN);
+  constexpr int AW = (E8 ? 2 : 1) * BN;   // TMEM columns of one tile's accumulator(s)
+  constexpr uint32_t TCOLS = tc_tmem_cols2(AW);
   static_assert(S >= 2, "at least two pipeline stages");
+  static_assert(2 * AW <= 512, "two buffers of the tile's accumulators in TMEM");
   SkMap mp;
   sk_map(sh, ep, BN, gridDim.x, mp);
   const int c = blockIdx.x;
@@ -498,7 +517,7 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)(ab * BN);
+        const uint32_t dt = tmem + (uint32_t)(ab * AW);
         for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int s = (int)(g % S);
           const uint32_t ph = (uint32_t)(g / S) & 1u;
@@ -515,12 +534,13 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
             const uint32_t a_addr = smem_u32(sA + (s * P + q) * kTcATile);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {   // 32 bytes of the 128-byte row per MMA
+              const bool lo = E8 && q >= kTcE4m3Hi;   // the second accumulator's pieces
+              const uint32_t acc = ((kb - kb0) | (lo ? q - kTcE4m3Hi : q) | kk) != 0 ? 1u : 0u;
               if (E8)
-                umma_e4m3(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                          ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+                umma_e4m3(dt + (lo ? (uint32_t)BN : 0u), sw128_desc(a_addr + kk * 32),
+                          sw128_desc(b_addr + kk * 32), idesc, acc);
               else
-                umma_bf16(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc,
-                          ((kb - kb0) | q | kk) != 0 ? 1u : 0u);
+                umma_bf16(dt, sw128_desc(a_addr + kk * 32), sw128_desc(b_addr + kk * 32), idesc, acc);
             }
           }
           umma_commit(&empty[s]);
@@ -554,7 +574,7 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
         break;
       }
       tc_fence_after();
-      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ab * BN);
+      const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(ab * AW);
       if (kb0 == 0 && kb1 == mp.KB) {   // the whole tile: the epilogue
         const int m = m0 + row;
         const EpiRow er = epi_row<MODE>(sh, ep, m);
@@ -562,7 +582,7 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
 #pragma unroll 1
         for (int cc = c_lo; cc < c_lo + CW; cc += 16) {
           float v[16];
-          tmem_ld16(tbase + (uint32_t)cc, v);
+          tmem_ld_tile16<E8>(tbase + (uint32_t)cc, BN, v);
           epi_chunk<MODE>(sh, ep, er, m, n0 + cc, v, fsum, dsum);
         }
       } else {                          // part of the tile: FP32 partial for the fix-up kernel
@@ -570,7 +590,7 @@ __global__ void __launch_bounds__(sk_threads(BN), 1)
 #pragma unroll 1
         for (int cc = c_lo; cc < c_lo + CW; cc += 16) {
           float v[16];
-          tmem_ld16(tbase + (uint32_t)cc, v);
+          tmem_ld_tile16<E8>(tbase + (uint32_t)cc, BN, v);
           float4* dst = reinterpret_cast<float4*>(sk_part(ep.skws, BN, slot, cc / 16, row));
 #pragma unroll
           for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
@@ -695,7 +715,8 @@ bool tc_plan(TcPlan* plan, const void* A, int P, int M, int Mpad, int K, int64_t
              int64_t ldb, int bn, const char** why, int e8) {
   plan->ok = 0;
   if (!e8 && (P < 1 || P > 3)) { *why = "BF16 pieces must be 1, 2 or 3"; return false; }
-  if (e8 && P != kTcE4m3Pieces) { *why = "E4M3 products take 4 pieces"; return false; }
+  if (e8 && P != kTcE4m3Pieces) { *why = "E4M3 products take KSC_E4M3_PIECES pieces"; return false; }
+  if (e8 && bn > 128) { *why = "E4M3 tile width must be 64 or 128 (two accumulators)"; return false; }
   if (bn != 64 && bn != 128 && bn != 256) { *why = "tile width must be 64, 128 or 256"; return false; }
   if (M <= 0 || N <= 0 || K <= 0) { *why = "empty product"; return false; }
   if (Mpad % kTcBM != 0 || Mpad < M) { *why = "Mpad must be a multiple of 128 and >= M"; return false; }
@@ -759,8 +780,8 @@ static void launch_one(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
 template <int P, int MODE, int E8 = 0>
 static void launch_bn(const TcPlan& g, const TcEpi& e, cudaStream_t s) {
   if (g.bn == 64) launch_one<P, 64, MODE, E8>(g, e, s);
-  else if (g.bn == 128) launch_one<P, 128, MODE, E8>(g, e, s);
-  else launch_one<P, 256, MODE, E8>(g, e, s);
+  else if (g.bn == 128 || E8) launch_one<P, 128, MODE, E8>(g, e, s);   // E4M3 plans: bn <= 128
+  else launch_one<P, E8 ? 128 : 256, MODE, E8>(g, e, s);
 }
 
 template <int MODE>

@@ -306,10 +306,14 @@ ksc_status alloc_ws(ksc_problem* pr, int need, cudaStream_t s, BatchWs** out, bo
       void* t = nullptr;
       KB_CUDA(cudaMalloc(&t, std::max((size_t)n * d.ldp8, (size_t)p * d.ldn8) * 2));
       launch_fp8_to_bf16(pr->X, pr->ldx, n, p, pr->dev.xscale, 1, t, (int64_t)d.ldp8, s);
-      ok = tcx_slices_build(&ws->xs_fwd, t, n, p, d.ldp8, s, &why);
+      ok = cudaGetLastError() == cudaSuccess;
+      if (!ok) why = "the represented matrix could not be formed";
+      ok = ok && tcx_slices_build(&ws->xs_fwd, t, n, p, d.ldp8, s, &why);
       if (ok) {
         launch_fp8_to_bf16(pr->dev.Xc, pr->dev.ldc, p, n, pr->dev.xscale, 0, t, (int64_t)d.ldn8, s);
-        ok = tcx_slices_build(&ws->xs_grad, t, p, n, d.ldn8, s, &why);
+        ok = cudaGetLastError() == cudaSuccess;
+        if (!ok) why = "the represented matrix could not be formed";
+        ok = ok && tcx_slices_build(&ws->xs_grad, t, p, n, d.ldn8, s, &why);
       }
       const cudaError_t se = cudaStreamSynchronize(s);
       cudaFree(t);
@@ -346,6 +350,8 @@ double exact_product(ksc_problem* pr, BatchWs* ws, bool fwd, const double* V, in
     pr->launches += tcx_launches(x, R);
     return tcx_error_factor(x);
   }
+  // (E4M3 X always has the slices: alloc_ws refuses it otherwise; the streaming
+  // product reads F64, F32 and BF16 X only)
   launch_dfprod(pr->dev, fwd, V, ldv, ws->dlist, R, D, ldd, d.dfws, kblock, s);
   pr->launches += 1 + (dfprod_splits(R, fwd ? d.n : d.p) > 1);
   return fwd ? dfprod_error_factor(d.p, R, d.n, kblock) : dfprod_error_factor(d.n, R, d.p, kblock);
@@ -463,6 +469,7 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   const int sk_lo = (sched && std::strcmp(sched, "stream_k") == 0) ? 1 : 0;
   const int sk_hi = (sched && std::strcmp(sched, "tiled") == 0) ? 0 : 1;
   for (int bn : kTcBNs) {
+    if (d.e8 && bn > 128) continue;   // E4M3 tiles: two accumulators, at most 128 wide
     for (int sk = sk_lo; sk <= sk_hi; ++sk) {
       bool ok = make(bn, bn);
       if (ok && sk) ok = tc_plan_stream_k(&ws->fwd, ws->nsm, &why) && tc_plan_stream_k(&ws->grad, ws->nsm, &why);
@@ -679,8 +686,9 @@ ksc_status zero_anchor_prepare(Session* se) {
   KB_CUDA(cudaMemcpyAsync(ws->r0, r0.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s));
   const int zero_row = 0;
   KB_CUDA(cudaMemcpyAsync(ws->dlist, &zero_row, 4, cudaMemcpyHostToDevice, s));
-  launch_dfprod(pr->dev, false, ws->r0, ws->ldn, ws->dlist, 1, ws->G0, ws->ldp, ws->bd.dfws, kDfBlockAnchor, s);
-  pr->launches += 1 + (dfprod_splits(1, (int)pr->p) > 1);
+  // G0 = X^T r0 by the workspace's exact product (the tensor-core slices when it
+  // holds them -- always for FP8 X, which the streaming product cannot read)
+  exact_product(pr, ws, false, ws->r0, ws->ldn, 1, ws->G0, ws->ldp, kDfBlockAnchor, s);
   KB_CUDA(cudaGetLastError());
   ws->zero_ready = true;
   return KSC_OK;

@@ -14,18 +14,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/ksc.h"
+
 namespace ksc {
 
 enum : int { kTcStore = 0, kTcAdd = 1, kTcAnchor = 2 };
 
 // E4M3 operands (plan e8 = 1): B is E4M3 X (its power-of-two column scales kept
 // apart), A holds kTcE4m3Pieces E4M3 pieces of the vectors, each row scaled by a
-// power of two so that its largest entry lies in [128, 256); the epilogue
+// power of two so that its largest entry lies in [128, 256): pieces 0..2 are the
+// E4M3 roundings of what the previous ones left, pieces 3..4 those of the
+// remainder times 2^kTcE4m3Shift, accumulated in a second TMEM accumulator (the
+// epilogue adds hi + 2^-12 lo).  One scale for all pieces would stop every entry
+// at the smallest E4M3 subnormal, 2^-18 of the row's largest; the second scale
+// takes that floor to 2^-30, below the FP32 accumulation error.  The epilogue
 // multiplies row m by rscale[m] (the inverse scale) and, when cscale is given,
-// column j by cscale[j] -- both exact in FP32.  Four pieces (4 significant bits
-// each, the smallest subnormal 2^-9) carry each entry to 2^-16 of the row's
-// largest, about the FP32 accumulation error of the K-long sums they feed.
-constexpr int kTcE4m3Pieces = 4;
+// column j by cscale[j] -- both exact in FP32.  Tiles are at most 128 wide (two
+// double-buffered accumulators fill the 512 TMEM columns).
+constexpr int kTcE4m3Pieces = KSC_E4M3_PIECES;
+constexpr int kTcE4m3Hi = 3;       // pieces in the first accumulator
+constexpr int kTcE4m3Shift = 12;   // the remainder's scale, 2^12
 
 // Epilogues (row m of the product D, columns j < N):
 //   kTcStore   out[m * ldo + j] = D                                   (FP32)

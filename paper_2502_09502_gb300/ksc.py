@@ -25,6 +25,7 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "oom", 3: "admission", 4: "infeasi
                 5: "not_converged", 6: "timeout", 7: "cuda", 8: "unimplemented"}
 KSC_LOSS_LSQ, KSC_LOSS_LOGISTIC, KSC_LOSS_SQHINGE, KSC_LOSS_POISSON, KSC_LOSS_GAMMA = 0, 1, 2, 3, 4
 KSC_F64, KSC_F32, KSC_BF16, KSC_FP8 = 0, 1, 2, 3   # KSC_FP8: e4m3 with power-of-two column scales
+KSC_E4M3_PIECES = 5                                 # E4M3 pieces per vector row (ksc_tc_gemm_e4m3)
 KSC_FLAG_RESTART_OFF, KSC_FLAG_MOMENTUM_OFF, KSC_FLAG_EIG = 1, 2, 4
 KSC_KERNEL_GRADIENT, KSC_KERNEL_PROX, KSC_KERNEL_FORWARD = 0, 1, 2
 KSC_KERNEL_B_RESID, KSC_KERNEL_B_GRAD, KSC_KERNEL_B_PROX, KSC_KERNEL_B_FWD, KSC_KERNEL_B_STEP = (

@@ -2,11 +2,13 @@
 ABI, against a plain FP64 product of the same E4M3 values.
 
 This is the product of the batched solver when X is stored in FP8 e4m3 with
-power-of-two column scales: four E4M3 pieces of each vector row, the row scaled
-by a power of two, against E4M3 X; the epilogue multiplies row i by its inverse
-scale and column j by the column scale.  Products of E4M3 values are exact in
+power-of-two column scales: KSC_E4M3_PIECES E4M3 pieces of each vector row, the row scaled
+by a power of two, against E4M3 X; the first three pieces and the last two (a
+remainder scaled by 2^12) accumulate separately and are added as hi + 2^-12 lo;
+the epilogue multiplies row i by its inverse scale and column j by the column
+scale.  Products of E4M3 values are exact in
 FP32 and the scales are powers of two, so only the FP32 accumulation rounds:
-|D - D_ref| <= (K' + 2) u_32 sum |a||b| with K' = 4 k.  A descriptor or layout
+|D - D_ref| <= (K' + 2) u_32 sum |a||b| with K' = pieces x k.  A descriptor or layout
 mistake (a wrong K step of 32 bytes, a transposed or shifted operand, a lost
 piece, a scale on the wrong axis) gives errors of the size of the entries.
 """
@@ -17,14 +19,16 @@ import torch
 pytestmark = pytest.mark.gpu
 
 U32 = 2.0 ** -24
-PIECES = 4
+PIECES = None   # the library's KSC_E4M3_PIECES, read in the fixture
 
 
 @pytest.fixture(scope="module")
 def K():
+    global PIECES
     import __graft_entry__ as g
     g.build()
     from paper_2502_09502_gb300 import ksc
+    PIECES = ksc.KSC_E4M3_PIECES
     return ksc
 
 
@@ -52,8 +56,9 @@ def _run(K, m, m_pad, k, lda, n, ldb, tile_n, grid, seed, with_cs=True):
     torch.cuda.synchronize()
     a = Av[:, :m, :k]
     b = Bv[:, :k]
-    ref = sum(a[q] @ b.T for q in range(PIECES))
-    mag = sum(a[q].abs() @ b.abs().T for q in range(PIECES))
+    w = [1.0 if q < 3 else 2.0 ** -12 for q in range(PIECES)]   # the low pieces' accumulator
+    ref = sum(w[q] * (a[q] @ b.T) for q in range(PIECES))
+    mag = sum(w[q] * (a[q].abs() @ b.abs().T) for q in range(PIECES))
     sc = rs.double()[:, None] * (cs.double()[None, :] if with_cs else 1.0)
     return D[:, :n].double().cpu(), ref * sc, mag * sc
 
@@ -62,9 +67,9 @@ CASES = [
     # m, m_pad, k, lda, n, ldb, tile_n, grid
     (128, 128, 128, 128, 64, 128, 64, 0),
     (200, 256, 1000, 1008, 300, 1008, 128, 0),
-    (512, 512, 4000, 4000, 1000, 4000, 256, 0),
+    (512, 512, 4000, 4000, 1000, 4000, 128, 0),
     (1, 128, 40, 48, 17, 48, 64, 0),
-    (384, 384, 3000, 3008, 777, 3008, 256, 152),
+    (384, 384, 3000, 3008, 777, 3008, 128, 152),
     (1000, 1024, 2000, 2000, 530, 2000, 128, 152),
     (128, 128, 5000, 5008, 200, 5008, 64, 7),
 ]
@@ -86,7 +91,7 @@ def test_e4m3_product_without_column_scales(K):
 
 
 def test_e4m3_product_rejects_bad_shapes(K):
-    A = torch.zeros(PIECES * 128, 128, dtype=torch.uint8, device="cuda")
+    A = torch.zeros(PIECES * 128, 128, dtype=torch.uint8, device="cuda")   # pieces x m_pad rows
     B = torch.zeros(64, 128, dtype=torch.uint8, device="cuda")
     rs = torch.ones(128, dtype=torch.float32, device="cuda")
     D = torch.zeros(128, 64, dtype=torch.float32, device="cuda")
@@ -96,6 +101,9 @@ def test_e4m3_product_rejects_bad_shapes(K):
     with pytest.raises(K.KscError):   # m_pad not a multiple of 128
         K.ksc_tc_gemm_e4m3(A.data_ptr(), 100, 100, 128, 128, B.data_ptr(), 64, 128, rs.data_ptr(), 0,
                            D.data_ptr(), 64, 64, 0)
+    with pytest.raises(K.KscError):   # tiles wider than 128 (two accumulators)
+        K.ksc_tc_gemm_e4m3(A.data_ptr(), 128, 128, 128, 128, B.data_ptr(), 64, 128, rs.data_ptr(), 0,
+                           D.data_ptr(), 64, 256, 0)
     with pytest.raises(K.KscError):   # no row scales
         K.ksc_tc_gemm_e4m3(A.data_ptr(), 128, 128, 128, 128, B.data_ptr(), 64, 128, 0, 0,
                            D.data_ptr(), 64, 64, 0)
