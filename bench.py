@@ -949,6 +949,8 @@ def run_batched(args):
         "certificates_per_call": bstats["batch_certificates"],
         "anchors_per_call": bstats["batch_anchors"],
         "prox_fallbacks_per_call": bstats["prox_fallback"],
+        "product_tiles": {"x_dbeta": [bstats["tile_fwd"], "stream-K" if bstats["stream_k_fwd"] else "tiled"],
+                          "xt_r": [bstats["tile_grad"], "stream-K" if bstats["stream_k_grad"] else "tiled"]},
         "device_ms_per_call": {k: round(v[1], 2) for k, v in kt.items()},
         "plain_single_node": {"value": round(plain32, 3), "unit": UNIT, "x_dtype": "f32", "nodes": len(sample),
                               "ratio": round(value / plain32, 2), "wall_value": round(plain32_wall, 3),
@@ -1209,7 +1211,7 @@ def main():
                 "value", "unit", "steps", "warmup", "ms_per_step", "dtype", "config", "latency_ms",
                 "iters_per_bound", "plain_single_node", "plain_single_node_bf16", "e2e", "roofline",
                 "rooflines", "device_ms_per_call", "clocks", "gpu_launches", "certificates_per_call",
-                "anchors_per_call", "prox_fallbacks_per_call", "lockstep_steps_per_call")
+                "anchors_per_call", "prox_fallbacks_per_call", "lockstep_steps_per_call", "product_tiles")
                 if k in b}
             if "oracle_subsample" in b:
                 out["batched"]["oracle_subsample"] = b["oracle_subsample"]

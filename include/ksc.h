@@ -452,8 +452,12 @@ ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kernel, int64_t
  *   5  Lanczos steps taken for L when the problem was created
  *   6  batched: FP64 certificates computed (one per in-loop stop)
  *   7  batched: anchor products computed (exact X beta_ref and X^T r_ref)
- * Entries 1-4 are 0 after a batched solve, 6-7 after a single-node one; entries
- * beyond 8 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
+ *   8  batched: tile width of the X beta product (columns of X per CTA)
+ *   9  batched: 1 if that product ran the stream-K schedule
+ *  10  batched: tile width of the X^T r product
+ *  11  batched: 1 if that product ran the stream-K schedule
+ * Entries 1-4 are 0 after a batched solve, 6-11 after a single-node one; entries
+ * beyond 12 are set to 0.  n < 0 or a NULL stats with n > 0 is rejected. */
 ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n);
 
 /* In-loop state of node `index` of the last batched ksc_solve_batch call on this

@@ -621,8 +621,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
     KSC_CUDA(cudaMemcpyAsync(d.nd, &upd, sizeof upd, cudaMemcpyHostToDevice, s));
     h = upd;
   }
-  pr->last_stats[6] = 0;
-  pr->last_stats[7] = 0;
+  for (int i = 6; i < 12; ++i) pr->last_stats[i] = 0;
   pr->last_stats[0] = h.iter - 1;
   pr->last_stats[1] = h.sparse_steps;
   pr->last_stats[2] = h.fallback;
@@ -721,7 +720,7 @@ extern "C" ksc_status ksc_gstar(const double* a, int64_t p, int32_t k, double M,
 extern "C" ksc_status ksc_problem_solve_stats(const ksc_problem* problem, int32_t* stats, int32_t n) {
   if (!problem) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
   if (n < 0 || (n > 0 && !stats)) return fail(KSC_ERR_INVALID_ARG, "bad stats buffer");
-  for (int32_t i = 0; i < n; ++i) stats[i] = i < 8 ? problem->last_stats[i] : 0;
+  for (int32_t i = 0; i < n; ++i) stats[i] = i < 12 ? problem->last_stats[i] : 0;
   return KSC_OK;
 }
 

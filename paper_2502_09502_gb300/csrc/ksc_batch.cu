@@ -468,10 +468,18 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
   const char* sched = std::getenv("KSC_TC_SCHEDULE");
   const int sk_lo = (sched && std::strcmp(sched, "stream_k") == 0) ? 1 : 0;
   const int sk_hi = (sched && std::strcmp(sched, "tiled") == 0) ? 0 : 1;
+  // KSC_TC_TILE_FWD / KSC_TC_TILE_GRAD = 64 | 128 | 256 fix one product's tile width
+  // (the other product's candidates are still timed)
+  auto fixed_tile = [](const char* name) {
+    const char* v = std::getenv(name);
+    return v ? std::atoi(v) : 0;
+  };
+  const int fix_f = fixed_tile("KSC_TC_TILE_FWD"), fix_g = fixed_tile("KSC_TC_TILE_GRAD");
   for (int bn : kTcBNs) {
     if (d.e8 && bn > 128) continue;   // E4M3 tiles: two accumulators, at most 128 wide
+    const int bnf = fix_f ? fix_f : bn, bng = fix_g ? fix_g : bn;
     for (int sk = sk_lo; sk <= sk_hi; ++sk) {
-      bool ok = make(bn, bn);
+      bool ok = make(bnf, bng);
       if (ok && sk) ok = tc_plan_stream_k(&ws->fwd, ws->nsm, &why) && tc_plan_stream_k(&ws->grad, ws->nsm, &why);
       if (!ok) {
         cudaEventDestroy(e0);
@@ -485,13 +493,13 @@ ksc_status plan_batch(ksc_problem* pr, BatchWs* ws, int B, cudaStream_t s) {
         KB_CUDA(cudaEventRecord(e1, s));
         KB_CUDA(cudaEventSynchronize(e1));
         KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0 && ms < best_f) { best_f = ms; bf = bn; sf = sk; }
+        if (rep > 0 && ms < best_f) { best_f = ms; bf = bnf; sf = sk; }
         KB_CUDA(cudaEventRecord(e0, s));
         tc_launch(ws->grad, grad_epi(ws), kTcAdd, s);
         KB_CUDA(cudaEventRecord(e1, s));
         KB_CUDA(cudaEventSynchronize(e1));
         KB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (rep > 0 && ms < best_g) { best_g = ms; bg = bn; sg = sk; }
+        if (rep > 0 && ms < best_g) { best_g = ms; bg = bng; sg = sk; }
       }
       pr->launches += sk ? 12 : 6;
     }
@@ -1010,6 +1018,7 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
   // 128-slot tiles lets the products skip the tiles of the faster nodes sooner
   std::stable_sort(batch.begin(), batch.end(), [&](int a, int b) { return setups[a].kp > setups[b].kp; });
   int64_t iters = 0, anchors = 0, certs = 0, fallbacks = 0;
+  int tiles[4] = {0, 0, 0, 0};   // the products' tile widths and schedules (last pass)
   for (size_t g0 = 0; g0 < batch.size(); g0 += kBatchMax) {
     const int cnt = (int)std::min<size_t>(kBatchMax, batch.size() - g0);
     Session se;
@@ -1083,10 +1092,15 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
     }
     anchors += se.anchors;
     certs += se.certificates;
+    tiles[0] = se.ws->bn_fwd;
+    tiles[1] = se.ws->sk_fwd;
+    tiles[2] = se.ws->bn_grad;
+    tiles[3] = se.ws->sk_grad;
     session_close(&se);
   }
   if (!batch.empty()) {
-    for (int i = 0; i < 8; ++i) pr->last_stats[i] = 0;
+    for (int i = 0; i < 12; ++i) pr->last_stats[i] = 0;
+    for (int i = 0; i < 4; ++i) pr->last_stats[8 + i] = tiles[i];
     pr->last_stats[0] = (int32_t)std::min<int64_t>(iters, INT32_MAX);
     pr->last_stats[2] = (int32_t)std::min<int64_t>(fallbacks, INT32_MAX);
     pr->last_stats[5] = pr->power_iters;

@@ -43,7 +43,7 @@ struct ksc_problem {
   int64_t k_launches[kKernelIds] = {};
   double k_ms[kKernelIds] = {};
   int64_t launches = 0;   // every kernel launch issued for this problem
-  int32_t last_stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t last_stats[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   ksc::BatchWs* batch = nullptr;   // batched-solve workspace (created on first use)
   std::vector<double> batch_state; // 10 in-loop values per node of the last batched call
   double eig_lambda = 0.0;         // certified lower bound on lambda_min(X^T X)

@@ -323,7 +323,8 @@ def ksc_problem_launch_count(h) -> int:
 
 
 SOLVE_STATS = ("iters", "sparse_forward", "prox_fallback", "prox_predicted", "dual_predicted",
-               "lanczos", "batch_certificates", "batch_anchors")
+               "lanczos", "batch_certificates", "batch_anchors", "tile_fwd", "stream_k_fwd", "tile_grad",
+               "stream_k_grad")
 
 
 def ksc_problem_solve_stats(h):
