@@ -461,7 +461,7 @@ def run_bnb(args):
 
 # ------------------------------------------------------------------ prox micro-benchmark
 
-PROX = dict(workload="prox of g on many vectors (Sec. 5.1 / Fig. 1 shapes): gamma ~ N(0, I), k=10, M=1, "
+PROX = dict(workload="prox of g (and g itself, of the prox outputs) on many vectors (Sec. 5.1 / Fig. 1 shapes): gamma ~ N(0, I), k=10, M=1, "
                      "rho=1, p = 100 * 2^i for i = 0..10, >= 2^24 elements per launch (>= 608 rows), "
                      "inputs larger than L2 from p = 100 on")
 
@@ -500,19 +500,41 @@ def run_prox(args, reps=10):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         elems = count * p
+        # g (Algorithm 2) of the prox outputs, one CTA per vector: 8 algorithmic
+        # bytes per element (read b)
+        gout = torch.empty(count, dtype=torch.float64, device="cuda")
+
+        def glaunch():
+            K._check(K.ksc_g_value_batch(out.data_ptr(), p, p, count, 10, 1.0, gout.data_ptr(), stream))
+
+        for _ in range(3):
+            glaunch()
+        e0.record(stream)
+        for _ in range(reps):
+            glaunch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gms = e0.elapsed_time(e1) / reps
         sweep.append({"p": p, "vectors": count, "ms_per_launch": round(ms, 4),
                       "elements_per_s": round(elems / (ms / 1e3), 1),
-                      "algorithmic_gbs": round(16.0 * elems / (ms / 1e3) / 1e9, 1)})
-        del W, out
+                      "algorithmic_gbs": round(16.0 * elems / (ms / 1e3) / 1e9, 1),
+                      "g_ms_per_launch": round(gms, 4), "g_elements_per_s": round(elems / (gms / 1e3), 1),
+                      "g_algorithmic_gbs": round(8.0 * elems / (gms / 1e3) / 1e9, 1)})
+        del W, out, gout
     # the oracle (sort + PAVA merge) on a bounded sample of the same shapes
     from oracle import oracle as O
     rng = np.random.default_rng(args.seed)
     t0, elems = time.perf_counter(), 0
+    bs = []
     for p in (1600, 12800, 102400):
         for _ in range(3):
-            O.prox_g(rng.standard_normal(p), 10, 1.0, 1.0)
+            bs.append(O.prox_g(rng.standard_normal(p), 10, 1.0, 1.0)[0])
             elems += p
     cpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for b in bs:
+        O.g_value(b, 10, 1.0)
+    cpu_g_s = time.perf_counter() - t0
     big = sweep[-1]
     return {
         "metric": "prox elements/s", "value": big["elements_per_s"], "unit": "elements/s", "n_gpus": 1,
@@ -523,7 +545,11 @@ def run_prox(args, reps=10):
                      "peak": hbm, "unit": "GB/s", "frac": round(big["algorithmic_gbs"] / hbm, 4),
                      "traffic": None, "bytes_per_element": 16},
         "cpu_baseline": {"value": round(elems / cpu_s, 1), "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": "3 vectors each of p = 1600, 12800, 102400 (same distribution and k, M, rho)"},
+                         "sample": "3 vectors each of p = 1600, 12800, 102400 (same distribution and k, M, rho)",
+                         "g_value": round(elems / max(cpu_g_s, 1e-9), 1)},
+        "g_value": {"kernel": "k_gvalue_rows (ksc_g_value_batch, Algorithm 2 per vector)",
+                    "elements_per_s": big["g_elements_per_s"], "algorithmic_gbs": big["g_algorithmic_gbs"],
+                    "frac_of_hbm": round(big["g_algorithmic_gbs"] / hbm, 4), "p": big["p"]},
     }
 
 

@@ -315,6 +315,20 @@ ksc_status ksc_prox_g_noalloc(const double* w, int64_t p, int32_t k, double M, d
 ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* beta_out, int64_t ldb, int64_t p,
                             int32_t count, int32_t k, double M, double rho, void* cuda_stream);
 
+/* g(beta) of ksc_g_value (Algorithm 2, Sec. 3.2; +inf outside dom g: some
+ * |beta_j| > M or sum |beta_j| > kM) for `count` independent vectors of length p
+ * at once, on DEVICE buffers: g_out[r] (a device array of count doubles) = g of
+ * row r of beta (p doubles at beta + r * ldb).  The throughput form of the
+ * g-value evaluation the restart test of Algorithm 3 needs every step (the
+ * paper's g experiment, many vectors instead of one).  ldb >= p (and at most
+ * INT64_MAX / 8 / count); min(k, p) must be below 2048 (KSC_ERR_UNIMPLEMENTED).
+ * count = 0 does nothing.  One CTA per row; work is enqueued on cuda_stream and
+ * the call returns without waiting; no device memory is allocated.  Results agree
+ * with ksc_g_value to rounding.  A CUDA error already pending on the calling
+ * thread is reported (and cleared) as KSC_ERR_CUDA. */
+ksc_status ksc_g_value_batch(const double* beta, int64_t ldb, int64_t p, int32_t count, int32_t k, double M,
+                             double* g_out, void* cuda_stream);
+
 /* ---- serving -------------------------------------------------------------- */
 
 /* A request loop on the current device for dual-bound solves of many nodes of

@@ -180,6 +180,16 @@ k_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int 
   prox_segment<double, kRowsBlock>(io, sm);
 }
 
+// g(b) (Algorithm 2) of many rows, one CTA per row, every coordinate free
+__global__ void __launch_bounds__(kRowsBlock)
+k_gvalue_rows(const double* beta, int64_t ldb, int p, int k, double M, double* g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  SegSmem<double> sm = carve_seg_smem<double>(smem, kRowsCap, 0);
+  const double* b = beta + (int64_t)blockIdx.x * ldb;
+  const GOut o = gvalue_segment<double, kRowsBlock>(p, [&](int i) { return b[i]; }, nullptr, k, M, sm, nullptr);
+  if (threadIdx.x == 0) g[blockIdx.x] = o.g;
+}
+
 __global__ void __launch_bounds__(kProxBlock, 1)
 k_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -232,6 +242,7 @@ cudaError_t prox_prepare() {
       cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
       cudaFuncSetAttribute(k_prox_rows, cudaFuncAttributePreferredSharedMemoryCarveout, 100),
       cudaFuncSetAttribute(k_gvalue_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
+      cudaFuncSetAttribute(k_gvalue_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
       cudaFuncSetAttribute(k_gstar_prim, cudaFuncAttributeMaxDynamicSharedMemorySize, optin),
       tcx_prepare(),
   };
@@ -277,6 +288,12 @@ void launch_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, i
                       double M, double rho, cudaStream_t s) {
   if (count <= 0) return;
   k_prox_rows<<<count, kRowsBlock, prox_bytes(kRowsCap, 0, 8), s>>>(w, ldw, beta, ldb, p, k, M, rho);
+}
+
+void launch_gvalue_rows(const double* beta, int64_t ldb, int p, int count, int k, double M, double* g,
+                        cudaStream_t s) {
+  if (count <= 0) return;
+  k_gvalue_rows<<<count, kRowsBlock, prox_bytes(kRowsCap, 0, 8), s>>>(beta, ldb, p, k, M, g);
 }
 
 void launch_gvalue_prim(const double* beta, int p, int k, double M, double* g, double* z,

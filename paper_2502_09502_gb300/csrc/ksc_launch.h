@@ -145,6 +145,9 @@ cudaError_t prox_prepare();
 // primitives (one CTA, FP64)
 // prox of g for `count` vectors (device rows with leading dims ldw, ldb), one CTA each
 int prox_rows_cap();
+// g (Algorithm 2) of `count` device rows of length p (row stride ldb), one CTA per row
+void launch_gvalue_rows(const double* beta, int64_t ldb, int p, int count, int k, double M, double* g,
+                        cudaStream_t s);
 void launch_prox_rows(const double* w, int64_t ldw, double* beta, int64_t ldb, int p, int count, int k,
                       double M, double rho, cudaStream_t s);
 void launch_prox_prim(const double* w, int p, int k, double M, double rho, double* beta,

@@ -1,5 +1,6 @@
-// ksc_noalloc.cu -- the prox of g on device buffers with no device allocation at
-// all: ksc_prox_g_noalloc (one vector) and ksc_prox_g_batch (many vectors).
+// ksc_noalloc.cu -- the prox of g and g itself on device buffers with no device
+// allocation at all: ksc_prox_g_noalloc (one vector), ksc_prox_g_batch and
+// ksc_g_value_batch (many vectors).
 //
 // Some callers cannot call cudaMalloc: runtimes that own every byte of device
 // memory through their own pool and forbid allocations behind their back (a
@@ -91,6 +92,27 @@ extern "C" ksc_status ksc_prox_g_batch(const double* w, int64_t ldw, double* bet
   ksc_status st;
   if (!prepare_device(&st)) return st;
   ksc::launch_prox_rows(w, ldw, beta_out, ldb, (int)p, count, k, M, rho, (cudaStream_t)cuda_stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
+  return KSC_OK;
+}
+
+extern "C" ksc_status ksc_g_value_batch(const double* beta, int64_t ldb, int64_t p, int32_t count, int32_t k,
+                                        double M, double* g_out, void* cuda_stream) {
+  if (count < 0) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "count must be >= 0");
+  if (count > 0 && (!beta || !g_out)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "beta and g_out must be non-NULL");
+  if (p < 1 || p > INT32_MAX) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "p must be in [1, 2^31)");
+  if (ldb < p) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldb must be >= p");
+  const int64_t ld_max = INT64_MAX / 8 / (count > 0 ? count : 1);
+  if (ldb > ld_max) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "ldb too large");
+  if (k < 0) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "k must be >= 0");
+  if (!(M > 0) || !std::isfinite(M)) return ksc_internal_fail(KSC_ERR_INVALID_ARG, "M must be > 0");
+  if ((k < p ? (int64_t)k : p) >= ksc::prox_rows_cap())
+    return ksc_internal_fail(KSC_ERR_UNIMPLEMENTED, "min(k, p) must be < 2048 (per-vector candidate capacity)");
+  if (count == 0) return KSC_OK;
+  ksc_status st;
+  if (!prepare_device(&st)) return st;
+  ksc::launch_gvalue_rows(beta, ldb, (int)p, count, k, M, g_out, (cudaStream_t)cuda_stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return ksc_internal_fail(KSC_ERR_CUDA, cudaGetErrorString(e));
   return KSC_OK;

@@ -37,7 +37,7 @@ KSC_KERNEL_PROX_SELECT, KSC_KERNEL_PROX_APPLY = 10, 11
 EXPORTS = ["ksc_problem_create", "ksc_problem_destroy", "ksc_problem_bytes", "ksc_problem_info",
            "ksc_solve_node", "ksc_solve_batch", "ksc_bnb_solve", "ksc_prox_g", "ksc_g_value", "ksc_gstar",
            "ksc_prox_g_noalloc", "ksc_prox_g_batch", "ksc_problem_profile", "ksc_problem_kernel_time",
-           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk", "ksc_tc_gemm_e4m3",
+           "ksc_problem_launch_count", "ksc_problem_solve_stats", "ksc_tc_gemm", "ksc_tc_gemm_sk", "ksc_tc_gemm_e4m3", "ksc_g_value_batch",
            "ksc_tc_exact",
            "ksc_server_create", "ksc_server_submit", "ksc_server_poll", "ksc_server_latency",
            "ksc_server_stats", "ksc_server_destroy", "ksc_problem_batch_node_state", "ksc_problem_eig_lambda",
@@ -113,6 +113,8 @@ def _load():
                                      C.c_void_p, C.c_void_p, C.c_void_p]
     L.ksc_prox_g_batch.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_int64, C.c_int32,
                                    C.c_int32, C.c_double, C.c_double, C.c_void_p]
+    L.ksc_g_value_batch.argtypes = [C.c_void_p, C.c_int64, C.c_int64, C.c_int32, C.c_int32, C.c_double,
+                                    C.c_void_p, C.c_void_p]
     L.ksc_tc_gemm.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
                               C.c_void_p, C.c_int32, C.c_int64, C.c_void_p, C.c_int64, C.c_int32,
                               C.c_void_p]
@@ -241,6 +243,22 @@ def ksc_prox_g_batch(w_ptr, ldw, beta_ptr, ldb, p, count, k, M, rho, stream=None
     ksc_status; the work is enqueued on `stream`."""
     return lib.ksc_prox_g_batch(C.c_void_p(w_ptr), int(ldw), C.c_void_p(beta_ptr), int(ldb), int(p),
                                 int(count), int(k), float(M), float(rho), _stream_ptr(stream))
+
+
+def ksc_g_value_batch(beta_ptr, ldb, p, count, k, M, g_ptr, stream=None):
+    """g of `count` device rows at once (see include/ksc.h).  Returns the ksc_status;
+    the work is enqueued on `stream`."""
+    return lib.ksc_g_value_batch(C.c_void_p(beta_ptr), int(ldb), int(p), int(count), int(k), float(M),
+                                 C.c_void_p(g_ptr), _stream_ptr(stream))
+
+
+def g_value_rows(B, k, M, stream=None):
+    """B: 2-D float64 CUDA tensor (rows contiguous); returns g of every row (device)."""
+    import torch
+    assert B.is_cuda and B.dtype == torch.float64 and B.dim() == 2 and B.stride(1) == 1
+    g = torch.empty(B.shape[0], dtype=torch.float64, device=B.device)
+    _check(ksc_g_value_batch(B.data_ptr(), B.stride(0), B.shape[1], B.shape[0], k, M, g.data_ptr(), stream))
+    return g
 
 
 def prox_g_rows(W, k, M, rho, out=None, stream=None):

@@ -286,10 +286,13 @@ def test_device_resident_matrix_is_borrowed(K):
 
 
 def test_full_size_single_node_f32_properties(K):
-    # least squares, FP32, n=20000, p=50000, k=20, lambda2=0.1, M=1.5, Toeplitz 0.9:
+    # least squares, FP32, n=20000, p=50000, k=20, lambda2=0.1, M=1.5, Toeplitz 0.9
+    # (the benchmark's single-node workload, in the launch configuration it times):
     # the oracle cannot solve it in test time, so check what holds at any size --
     # the gap target, and the certified bound below a feasible k-sparse value
-    # (ridge on the true support, computed on the host).
+    # (ridge on the true support, computed on the host) -- and what the oracle can
+    # evaluate one point at a time: its FP64 objective and dual bound (Sec. 3.4) at
+    # the returned iterate, over the same FP32 matrix.
     P = G.cfg_single_node_f32(seed=0)
     prob = K.Problem(P.X, P.y)
     r = prob.solve(K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=20000))
@@ -299,6 +302,11 @@ def test_full_size_single_node_f32_properties(K):
     ub, _ = _pins.ridge_box(P.X[:, S].astype(np.float64), P.y, P.lambda2, P.M)
     assert r.dual_bound <= r.primal <= ub * (1 + 1e-9)
     assert np.count_nonzero(r.beta) >= 1 and np.all(np.abs(r.beta) <= P.M)
+    p_o = O.primal(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, r.beta)
+    d_o = O.dual_bound(P.X, P.y, O.LOSS_LSQ, P.lambda2, P.M, P.k, r.beta)
+    assert _rel(r.primal, p_o) <= 1e-8, (r.primal, p_o)
+    # the certified bound carries its rounding margins: at or below the exact one
+    assert r.dual_bound <= d_o + 1e-12 * abs(d_o) and _rel(r.dual_bound, d_o) <= 1e-8, (r.dual_bound, d_o)
 
 
 def test_sparse_forward_path_matches_oracle(K):

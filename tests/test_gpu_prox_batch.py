@@ -76,3 +76,52 @@ def test_batch_equals_single_vector_prox(K):
     for r in range(6):
         single, _ = K.ksc_prox_g(w[r], 12, 1.5, 3.0)
         assert np.max(np.abs(out[r].cpu().numpy() - single)) <= 1e-12 * max(1.0, np.abs(w).max())
+
+
+# ---- ksc_g_value_batch: g (Algorithm 2) of many device rows against the oracle's
+# Algorithm 2 row by row (1e-12 relative), +inf outside dom g
+
+def _g_check(K, B, k, M):
+    import torch
+    count, p = B.shape
+    Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    g = K.g_value_rows(Bd, k, M)
+    torch.cuda.synchronize()
+    got = g.cpu().numpy()
+    for r in range(count):
+        ref = O.g_value(B[r], k, M)
+        if np.isinf(ref):
+            assert np.isinf(got[r]) and got[r] > 0, (r, got[r])
+        else:
+            assert abs(got[r] - ref) <= 1e-12 * max(1.0, abs(ref)), (r, p, k, got[r], ref)
+
+
+@pytest.mark.parametrize("p,k", [(1, 1), (50, 5), (1000, 10), (1000, 1000), (12800, 10), (20011, 25)])
+def test_g_value_rows_match_oracle(K, p, k):
+    rng = np.random.default_rng(p + 7 * k)
+    M = 1.5
+    rows = []
+    for r in range(6):
+        # prox outputs lie in dom g: sparse, pooled (many equal magnitudes) and mixed rows
+        w = rng.standard_normal(p) * (0.1 if r % 2 else 3.0)
+        b, _ = O.prox_g(w, k, float(10 ** rng.uniform(-1, 2)), M)
+        rows.append(b)
+    flat = np.full(p, min(M, k * M / p) * 0.999)          # max |b| <= ||b||_1 / k: g = ||b||_1^2 / 2k
+    rows.append(flat)
+    over = rows[0].copy()
+    over[0] = 1.01 * M                                      # outside the box
+    rows.append(over)
+    if k < p:
+        wide = np.full(p, M * 0.999)                        # outside the l1 budget kM
+        rows.append(wide)
+    _g_check(K, np.array(rows), k, M)
+
+
+def test_g_value_rows_reject_bad_arguments(K):
+    import torch
+    B = torch.zeros((2, 10), dtype=torch.float64, device="cuda")
+    g = torch.zeros(2, dtype=torch.float64, device="cuda")
+    assert K.ksc_g_value_batch(B.data_ptr(), 5, 10, 2, 3, 1.0, g.data_ptr()) == K.KSC_ERR_INVALID_ARG   # ldb < p
+    assert K.ksc_g_value_batch(B.data_ptr(), 10, 10, 2, 3, 0.0, g.data_ptr()) == K.KSC_ERR_INVALID_ARG  # M <= 0
+    assert K.ksc_g_value_batch(B.data_ptr(), 10, 10, -1, 3, 1.0, g.data_ptr()) == K.KSC_ERR_INVALID_ARG
+    assert K.ksc_g_value_batch(B.data_ptr(), 10, 10, 0, 3, 1.0, g.data_ptr()) == K.KSC_OK              # no rows
