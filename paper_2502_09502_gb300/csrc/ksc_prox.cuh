@@ -199,6 +199,22 @@ __device__ bool root_from_sorted(const double* cand, const double* pref, int q, 
 }
 
 // ------------------------------------------------------------------------
+// Appending to a shared list: one shared-memory atomic per warp (a leader adds
+// the warp's count) instead of one per element, which serialised on the single
+// counter when thousands of coordinates qualified.  Every lane of the warp must
+// call it (take = false for lanes with nothing to add); returns the lane's slot
+// or -1.
+__device__ __forceinline__ int warp_append(bool take, int* counter) {
+  const unsigned bal = __ballot_sync(0xffffffffu, take);
+  if (bal == 0u) return -1;
+  const int lane = threadIdx.x & 31, leader = __ffs(bal) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(counter, __popc(bal));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return take ? base + __popc(bal & ((1u << lane) - 1u)) : -1;
+}
+
+// ------------------------------------------------------------------------
 // The prox of one segment.
 
 template <typename T>
@@ -431,12 +447,11 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
       const U fk = abs_bits<T>((T)(0.99 * io.topk_hint));
       if (threadIdx.x == 0) sm.sh[40] = 0;
       __syncthreads();
-      for (int i = threadIdx.x; i < m; i += BLOCK) {
-        const U kb = keybits(i);
-        if (kb >= fk) {
-          const int pos = atomicAdd(&sm.sh[40], 1);
-          if (pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
-        }
+      for (int i0 = 0; i0 < m; i0 += BLOCK) {   // warp-uniform trip count (warp_append)
+        const int i = i0 + (int)threadIdx.x;
+        const U kb = i < m ? keybits(i) : U(0);
+        const int pos = warp_append(i < m && kb >= fk, &sm.sh[40]);
+        if (pos >= 0 && pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
       }
       __syncthreads();
       const int cnt = sm.sh[40];
@@ -468,12 +483,11 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
           floorv = to_d(B::val(RQ.thr));
           if (threadIdx.x == 0) sm.sh[40] = 0;
           __syncthreads();
-          for (int i = threadIdx.x; i < m; i += BLOCK) {
-            U kb = keybits(i);
-            if (kb > RQ.thr) {
-              int pos = atomicAdd(&sm.sh[40], 1);
-              sm.cand[pos] = to_d(B::val(kb));
-            }
+          for (int i0 = 0; i0 < m; i0 += BLOCK) {
+            const int i = i0 + (int)threadIdx.x;
+            const U kb = i < m ? keybits(i) : U(0);
+            const int pos = warp_append(i < m && kb > RQ.thr, &sm.sh[40]);
+            if (pos >= 0) sm.cand[pos] = to_d(B::val(kb));
           }
           __syncthreads();
           for (int j = RQ.gt + threadIdx.x; j < Q; j += BLOCK) sm.cand[j] = floorv;
@@ -614,9 +628,11 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
       if (threadIdx.x == 0) sm.sh[40] = 0;
       __syncthreads();
       const U tb = B::of((T)thr_k);
-      for (int i = threadIdx.x; i < m; i += BLOCK) {
-        U kb = keybits(i);
-        if (kb > tb) { int pos = atomicAdd(&sm.sh[40], 1); sm.cand[pos] = to_d(B::val(kb)); }
+      for (int i0 = 0; i0 < m; i0 += BLOCK) {
+        const int i = i0 + (int)threadIdx.x;
+        const U kb = i < m ? keybits(i) : U(0);
+        const int pos = warp_append(i < m && kb > tb, &sm.sh[40]);
+        if (pos >= 0) sm.cand[pos] = to_d(B::val(kb));
       }
       __syncthreads();
       for (int j = (q - need_k) + threadIdx.x; j < q; j += BLOCK) sm.cand[j] = thr_k;
@@ -664,8 +680,8 @@ __device__ SegOut prox_segment(const SegIO<T>& io, const SegSmem<T>& sm) {
       const int rank = tie_base + run + __popc(bal & ((1u << lane) - 1u));
       run += __popc(bal);
       const bool mem = fr && (a > thr_k || (tie && (!tie_split || rank < need_k)));
-      if (mem) {
-        int pos = atomicAdd(&sm.sh[40], 1);
+      const int pos = warp_append(mem, &sm.sh[40]);
+      if (pos >= 0) {
         sm.cand[pos] = a;
         sm.cidx[pos] = i;
       }
@@ -748,9 +764,11 @@ __device__ GOut gvalue_segment(int m, LoadB loadb, const int8_t* state, int kp, 
       SelectResult<U> R = block_select<U, BLOCK>(m, q, keybits, sm.hist, sm.sh);
       if (threadIdx.x == 0) sm.sh[40] = 0;
       __syncthreads();
-      for (int i = threadIdx.x; i < m; i += BLOCK) {
-        U kb = keybits(i);
-        if (kb > R.thr) { int pos = atomicAdd(&sm.sh[40], 1); sm.cand[pos] = B::val(kb); }
+      for (int i0 = 0; i0 < m; i0 += BLOCK) {
+        const int i = i0 + (int)threadIdx.x;
+        const U kb = i < m ? keybits(i) : U(0);
+        const int pos = warp_append(i < m && kb > R.thr, &sm.sh[40]);
+        if (pos >= 0) sm.cand[pos] = B::val(kb);
       }
       __syncthreads();
       const double thr = B::val(R.thr);
@@ -821,12 +839,11 @@ __device__ double gstar_segment(int m, LoadA loada, const int8_t* state, int kp,
     const U fk = abs_bits<T>((T)(0.99 * hint));
     if (threadIdx.x == 0) sm.sh[40] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += BLOCK) {
-      const U kb = keybits(i);
-      if (kb >= fk) {
-        const int pos = atomicAdd(&sm.sh[40], 1);
-        if (pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
-      }
+    for (int i0 = 0; i0 < m; i0 += BLOCK) {
+      const int i = i0 + (int)threadIdx.x;
+      const U kb = i < m ? keybits(i) : U(0);
+      const int pos = warp_append(i < m && kb >= fk, &sm.sh[40]);
+      if (pos >= 0 && pos < sm.cap) sm.cand[pos] = to_d(B::val(kb));
     }
     __syncthreads();
     const int cnt = sm.sh[40];
