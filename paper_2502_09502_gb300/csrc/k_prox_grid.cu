@@ -340,75 +340,138 @@ __device__ __forceinline__ void block_reduce_cs(int& na, double& sa, int& nb, do
 // {key > bk} + {key == bk, index <= bi}, Alg. 1 order).  Every thread evaluates
 // the counts and sums of Phi's linear piece at the broadcast point -- top members
 // active where a < t + min(rho t, M), tail members where a > t, by integer
-// compares of bit patterns -- and thread 0 alone does the scalar FP64 work (FP64
-// issues at 1/64 of the FP32 rate): Newton on the current piece (its root is
-// exact once the next point lies on the same piece), bisection when it leaves the
-// bracket, warm-started at the previous step's threshold.  false when
-// Phi(floorv) > 0 (the pooled block reaches below the candidates).
+// compares of bit patterns -- together with the nearest keys on either side of t
+// (tail) and of t + min(rho t, M) (top), which bound that piece; thread 0 alone
+// does the scalar FP64 work (FP64 issues at 1/64 of the FP32 rate): the Newton
+// point of the piece is the root when no key separates it from t (no second
+// pass to confirm it), bisection when it leaves the bracket, warm-started at the
+// previous step's threshold.  The first pass also evaluates Phi at the floor.
+// false when Phi(floorv) > 0 (the pooled block reaches below the candidates).
 __device__ bool root_unsorted(SelSmem& sm, int cc, unsigned long long bk, int bi, double floorv, bool all,
                               double top_max, double t0, double rho, double M, double* root, int* pooled) {
+  using ULL = unsigned long long;
+  __shared__ int s_cnt[4][32];
+  __shared__ ULL s_x[4][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = kSelBlock / 32;
   // thread 0's state
   double lo = floorv, hi = top_max, t = 0.0;
-  int pnA = -1, pnB = -1;
-  double pSA = 0.0, pSB = 0.0;
-  bool pcap = false, at_floor = false;
   if (threadIdx.x == 0) {
-    at_floor = !all;
-    t = at_floor ? floorv : ((t0 > lo && t0 < hi) ? t0 : 0.5 * (lo + hi));
+    t = (t0 > lo && t0 < hi) ? t0 : 0.5 * (lo + hi);
     sm.rtb[0] = dbits(t);
     sm.rtb[1] = dbits(t + fmin(rho * t, M));
     sm.rflag[0] = 0;
   }
+  const ULL fb = dbits(floorv), hfb = dbits(floorv + fmin(rho * floorv, M));
   __syncthreads();
   for (int it = 0; it < 200; ++it) {
-    const unsigned long long tb = sm.rtb[0], hb = sm.rtb[1];
-    int nA = 0, nB = 0;
-    double SA = 0.0, SB = 0.0;
+    const bool first = it == 0 && !all;   // Phi at the floor too
+    const ULL tb = sm.rtb[0], hb = sm.rtb[1];
+    int c[4] = {0, 0, 0, 0};              // nA, nB at t; nA, nB at the floor
+    double sum[4] = {0.0, 0.0, 0.0, 0.0};
+    ULL tl = 0ull, tg = ~0ull, al = 0ull, ag = ~0ull;
     for (int j = threadIdx.x; j < cc; j += kSelBlock) {
-      const unsigned long long k = sm.cand[j];
+      const ULL k = sm.cand[j];
+      const double v = dval(k);
       const bool top = k > bk || (k == bk && sm.cidx[j] <= bi);
       if (top) {
-        if (k < hb) { nA += 1; SA += dval(k); }
-      } else if (k > tb) {
-        nB += 1;
-        SB += dval(k);
+        if (k < hb) { c[0] += 1; sum[0] += v; al = k > al ? k : al; }
+        else ag = k < ag ? k : ag;
+        if (first && k < hfb) { c[2] += 1; sum[2] += v; }
+      } else {
+        if (k > tb) { c[1] += 1; sum[1] += v; tg = k < tg ? k : tg; }
+        else tl = k > tl ? k : tl;
+        if (first && k > fb) { c[3] += 1; sum[3] += v; }
       }
     }
-    block_reduce_cs(nA, SA, nB, SB, sm);
-    if (threadIdx.x == 0) {
-      const bool capped = rho * t >= M;
-      const double phi = (double)nA * dval(hb) - SA - (SB - (double)nB * t);
-      int done = 0;
-      double res = t;
-      if (at_floor) {
-        at_floor = false;
-        if (phi > 0.0) done = 2;                 // the root lies below the candidates
-        else if (phi == 0.0) done = 1;
-        else t = (t0 > lo && t0 < hi) ? t0 : 0.5 * (lo + hi);
-      } else if (phi == 0.0 || (nA == pnA && nB == pnB && capped == pcap && SA == pSA && SB == pSB)) {
-        done = 1;                                // t is the root of the piece it lies on
-      } else {
-        if (phi < 0.0) lo = t; else hi = t;
-        const double den = capped ? (double)(nA + nB) : (double)nA * (1.0 + rho) + (double)nB;
-        const double tn = den > 0.0 ? (capped ? (SA + SB - (double)nA * M) : (SA + SB)) / den : 0.5 * (lo + hi);
-        const bool ok = tn > lo && tn < hi;
-        if (hi - lo <= 2e-16 * hi || it == 199) {
-          done = 1;
-          res = ok ? tn : hi;
-        } else {
-          pnA = ok ? nA : -1;                    // a bisection point: no piece to compare with
-          pnB = nB;
-          pSA = SA;
-          pSB = SB;
-          pcap = capped;
-          t = ok ? tn : 0.5 * (lo + hi);
-        }
+    // block reduction: counts and extremes per warp, the FP64 sums through shared
+    // memory to one warp (fixed order)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c[i] = __reduce_add_sync(0xffffffffu, c[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ULL v;
+      v = __shfl_xor_sync(0xffffffffu, tl, o); tl = v > tl ? v : tl;
+      v = __shfl_xor_sync(0xffffffffu, al, o); al = v > al ? v : al;
+      v = __shfl_xor_sync(0xffffffffu, tg, o); tg = v < tg ? v : tg;
+      v = __shfl_xor_sync(0xffffffffu, ag, o); ag = v < ag ? v : ag;
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sm.pref[i * kSelBlock + threadIdx.x] = sum[i];
+    if (lane == 0) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) s_cnt[i][wid] = c[i];
+      s_x[0][wid] = tl;
+      s_x[1][wid] = al;
+      s_x[2][wid] = tg;
+      s_x[3][wid] = ag;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int v = 0; v < NW; ++v)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += sm.pref[i * kSelBlock + 32 * v + lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+      int n[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) n[i] = __reduce_add_sync(0xffffffffu, lane < NW ? s_cnt[i][lane] : 0);
+      ULL x0 = lane < NW ? s_x[0][lane] : 0ull, x1 = lane < NW ? s_x[1][lane] : 0ull;
+      ULL x2 = lane < NW ? s_x[2][lane] : ~0ull, x3 = lane < NW ? s_x[3][lane] : ~0ull;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        ULL v;
+        v = __shfl_xor_sync(0xffffffffu, x0, o); x0 = v > x0 ? v : x0;
+        v = __shfl_xor_sync(0xffffffffu, x1, o); x1 = v > x1 ? v : x1;
+        v = __shfl_xor_sync(0xffffffffu, x2, o); x2 = v < x2 ? v : x2;
+        v = __shfl_xor_sync(0xffffffffu, x3, o); x3 = v < x3 ? v : x3;
       }
-      sm.rflag[0] = done;
-      sm.rflag[1] = nB;
-      sm.rt[0] = res;
-      sm.rtb[0] = dbits(t);
-      sm.rtb[1] = dbits(t + fmin(rho * t, M));
+      if (lane == 0) {
+        // thread 0: the scalar step
+        int done = 0;
+        double res = t;
+        if (first) {
+          const double hf = dval(hfb);
+          const double phif = (double)n[2] * hf - a[2] - (a[3] - (double)n[3] * floorv);
+          if (phif > 0.0) done = 2;               // the root lies below the candidates
+          else if (phif == 0.0) { done = 1; res = floorv; }
+        }
+        if (!done) {
+          const double phi = (double)n[0] * dval(hb) - a[0] - (a[1] - (double)n[1] * t);
+          if (phi == 0.0) {
+            done = 1;
+          } else {
+            if (phi < 0.0) lo = t; else hi = t;
+            const bool capped = rho * t >= M;
+            const double den = capped ? (double)(n[0] + n[1]) : (double)n[0] * (1.0 + rho) + (double)n[1];
+            const double tn = den > 0.0 ? (capped ? (a[0] + a[1] - (double)n[0] * M) : (a[0] + a[1])) / den
+                                        : 0.5 * (lo + hi);
+            const bool ok = den > 0.0 && tn > lo && tn < hi;
+            if (ok) {
+              // the Newton point is the root when it lies on the same linear piece:
+              // no tail key in (tn, t] or (t, tn], no top key between the two h values
+              const double hn = tn + fmin(rho * tn, M);
+              const ULL cb = dbits(tn), hcb = dbits(hn);
+              bool same = (rho * tn >= M) == capped;
+              if (tn < t) same = same && x0 <= cb && x1 < hcb;
+              else same = same && x2 > cb && x3 >= hcb;
+              if (same) { done = 1; res = tn; }
+              t = tn;
+            } else {
+              t = 0.5 * (lo + hi);
+            }
+            if (!done && (hi - lo <= 2e-16 * hi || it == 199)) { done = 1; res = ok ? tn : hi; }
+          }
+        }
+        sm.rflag[0] = done;
+        sm.rflag[1] = n[1];
+        sm.rt[0] = res;
+        sm.rtb[0] = dbits(t);
+        sm.rtb[1] = dbits(t + fmin(rho * t, M));
+      }
     }
     __syncthreads();
     const int done = sm.rflag[0];
