@@ -1047,6 +1047,23 @@ def run_eig(args):
                          bounds=np.array([r.dual_bound for r in res]))
     bp, be = out["perspective"].pop("bounds"), out["eigen_perspective"].pop("bounds")
     rise = (be - bp) / np.abs(bp)
+    # the root relaxation on the single-node path (one ksc_solve_node call), both bounds
+    single = {}
+    for name, fl in (("perspective", 0), ("eigen_perspective", K.KSC_FLAG_EIG)):
+        nd = K.Node(P.lambda2, P.M, P.k, rel_gap_tol=1e-6, max_iter=100000, flags=fl)
+        prob.solve(nd)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            r = prob.solve(nd)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        assert r.status == "ok" and r.rel_gap <= 1e-6
+        single[name] = dict(ms_per_solve=round(ev0.elapsed_time(ev1) / args.steps, 3), iters=int(r.iters),
+                            dual_bound=float(r.dual_bound), primal=float(r.primal))
+    single["bound_rise_rel"] = ((single["eigen_perspective"]["dual_bound"] - single["perspective"]["dual_bound"])
+                                / abs(single["perspective"]["dual_bound"]))
     bnb = None
     if args.eig_bnb_seconds > 0:
         # branch and bound on a smaller instance of the config-4 generator with n > p
@@ -1072,6 +1089,7 @@ def run_eig(args):
         "perspective": out["perspective"], "eigen_perspective": out["eigen_perspective"],
         "bound_rise": {"mean_rel": float(rise.mean()), "max_rel": float(rise.max()),
                        "nodes_higher": int((rise > 1e-9).sum()), "nodes_lower": int((rise < -1e-9).sum())},
+        "single_node_root": single,
         "branch_and_bound": bnb,
     }
 

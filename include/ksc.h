@@ -84,11 +84,12 @@ typedef enum {
                                         squares only: Q = X^T X - lambda I and lambda2 +
                                         lambda on the perspective term, lambda the
                                         problem's certified shift (ksc_problem_eig_lambda,
-                                        computed on first use by ksc_solve_batch and
-                                        ksc_bnb_solve; ksc_server_submit refuses such a
-                                        node with KSC_ERR_INVALID_ARG until it is known).
-                                        Batched path only, BF16 X: ksc_solve_node
-                                        returns KSC_ERR_UNIMPLEMENTED                  */
+                                        computed on first use by ksc_solve_node,
+                                        ksc_solve_batch and ksc_bnb_solve;
+                                        ksc_server_submit refuses such a node with
+                                        KSC_ERR_INVALID_ARG until it is known).  Both
+                                        the single-node path (every storage type) and
+                                        the batched path (BF16 X) run it             */
 
 typedef struct ksc_problem ksc_problem;
 typedef struct ksc_server ksc_server;
@@ -200,7 +201,7 @@ ksc_status ksc_solve_node(ksc_problem* problem, const ksc_node* node, ksc_result
  * the stated tolerance.  Returns the first non-OK per-node status, else KSC_OK.
  * With BF16 or FP8 X the nodes advance in lock step (up to 1024 per device pass):
  * both products of every FISTA step run on the tensor cores for all nodes at once
- * (FP8: four E4M3 pieces of each difference against E4M3 X), on differences from
+ * (FP8: KSC_E4M3_PIECES E4M3 pieces of each difference against E4M3 X), on differences from
  * per-node anchor points whose products are exact, and every reported bound is the
  * FP64 certificate.  Other storage types (and nodes with k' >= 2048, and
  * eigen-perspective nodes on FP8 X) are solved one by one by the single-node path.  The problem's

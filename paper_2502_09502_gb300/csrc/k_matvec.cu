@@ -226,6 +226,7 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
   const double* bc = (const double*)d.beta + (size_t)cur * p;
   const double* bpv = (const double*)d.beta + (size_t)prev * p;
   const double invL = (MODE == kGStep) ? nd->invL : 0.0;
+  const double eig = (MODE == kGStep) ? nd->eig : 0.0;
   const unsigned cg = (MODE == kGStep) ? nd->cguess : 0u;
   const unsigned dg = (MODE == kGStep) ? nd->dguess : 0u;
   const int lane = threadIdx.x & 31;
@@ -243,9 +244,18 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
         s *= (MODE == kGColsq) ? sc * sc : sc;
       }
       if constexpr (MODE == kGStep) {
-        d.grad[col] = s;
         const double b0 = bc[col];
-        const double w = b0 + c * (b0 - bpv[col]) - s * invL;   // extrapolation and gradient step (Algorithm 3)
+        double w;
+        if (eig > 0.0) {
+          // eigen-perspective (App. D.2): the smooth part b^T Q b - 2 y^T X b + ||y||^2,
+          // Q = X^T X - eig I, has the gradient X^T grad F(X gamma) - 2 eig gamma
+          const double gam = b0 + c * (b0 - bpv[col]);
+          s -= 2.0 * eig * gam;
+          w = gam - s * invL;
+        } else {
+          w = b0 + c * (b0 - bpv[col]) - s * invL;   // extrapolation and gradient step (Algorithm 3)
+        }
+        d.grad[col] = s;
         ((double*)d.wbuf)[col] = w;
         const bool fr = d.state == nullptr || d.state[col] == kFree;
         const unsigned kk = fr ? (__float_as_uint((float)w) & 0x7fffffffu) : 0u;
@@ -455,8 +465,10 @@ __device__ void finish_rows(const Dev& d, RowAcc a, double* red, int* s_last, in
     d.cnt[cidx] = 0;
     if (MODE == kFStep) {
       nd->sparse_steps += sparse ? 1 : 0;
-      step_logic(nd, f);
+      // eigen-perspective: F(X b) - eig ||b||^2 in the objective
+      step_logic(nd, nd->eig > 0.0 ? f - nd->eig * nd->bsq_next : f);
     } else if (MODE == kFInit) {
+      if (nd->eig > 0.0) f -= nd->eig * nd->bsq_next;
       const double L1 = f + 2.0 * nd->lambda2 * nd->g_next;   // initial objective (Algorithm 3)
       nd->Lcur = L1;
       nd->best_primal = L1;

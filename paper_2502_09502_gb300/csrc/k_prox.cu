@@ -29,7 +29,18 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_gvalue_init(Dev d) {
   GOut o = gvalue_segment<double, kProxBlock>(d.p, [&](int i) { return to_d(b1[i]); }, d.state,
                                               nd->kp, nd->M, sm, nullptr,
                                               sizeof(T) == 8 ? 1e-12 : 1e-6);
-  if (threadIdx.x == 0) nd->g_next = o.g;
+  double bsq = 0.0;
+  if (nd->eig > 0.0) {   // eigen-perspective: ||b^1||^2 for the initial objective
+    for (int j = threadIdx.x; j < d.p; j += kProxBlock) {
+      const double v = to_d(b1[j]);
+      bsq += v * v;
+    }
+    bsq = block_sum<double, kProxBlock>(bsq, sm.red);
+  }
+  if (threadIdx.x == 0) {
+    nd->g_next = o.g;
+    nd->bsq_next = bsq;
+  }
 }
 
 // The certificate's iterate: the final beta promoted to FP64, clipped to the box,
@@ -71,24 +82,60 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_cert_final(Dev d, int want_z)
   const double ur = 1.1102230246251565e-16;
   const double l2 = nd->lambda2, M = nd->M;
   const double scale = 1.0 / (2.0 * l2);
+  // eigen-perspective (App. D.2): G* at 2 (X^T y - Q b^) = X^T zeta + 2 eig b^
+  const double eig = nd->eig;
   // G*(a) / (2 lambda2) over the node: TopSum_k'(H_M(|a_F|/2l2)) + sum_S1 H_M(a_j/2l2)
-  const double gs = gstar_segment<double, kProxBlock>(p, [&](int i) { return d.a64[i]; }, d.state,
-                                                      nd->kp, M, scale, sm);
+  const double gs = gstar_segment<double, kProxBlock>(
+      p, [&](int i) { return eig > 0.0 ? d.a64[i] + 2.0 * eig * d.b64[i] : d.a64[i]; }, d.state, nd->kp, M,
+      scale, sm);
   // error bound of a = X^T zeta (FP64, any summation order):
   //   |a^_j - a_j| <= gamma_{n+1} sum_i |x_ij zeta_i| <= gamma_{n+1} ||x_j|| ||zeta||
-  double cmax = 0.0;
+  double cmax = 0.0, amax = 0.0, bsq = 0.0, xf2 = 0.0, y2 = 0.0;
   int n1 = 0;
   for (int j = threadIdx.x; j < p; j += kProxBlock) {
     const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
     if (st != kZero) cmax = fmax(cmax, d.colnorm[j]);
     if (st == kOne) n1 += 1;
+    if (eig > 0.0) {
+      if (st != kZero) amax = fmax(amax, fabs(d.a64[j]) + 2.0 * eig * fabs(d.b64[j]));
+      bsq += d.b64[j] * d.b64[j];
+      xf2 += d.colnorm[j] * d.colnorm[j];
+    }
   }
+  if (eig > 0.0)
+    for (int i = threadIdx.x; i < d.n; i += kProxBlock) y2 += d.y[i] * d.y[i];
   cmax = block_max<double, kProxBlock>(cmax, sm.red, 0.0);
   n1 = (int)block_sum<double, kProxBlock>((double)n1, sm.red);
+  if (eig > 0.0) {
+    amax = block_max<double, kProxBlock>(amax, sm.red, 0.0);
+    bsq = block_sum<double, kProxBlock>(bsq, sm.red);
+    xf2 = block_sum<double, kProxBlock>(xf2, sm.red);
+    y2 = block_sum<double, kProxBlock>(y2, sm.red);
+  }
   const double nn = (double)d.n + 2.0;
   const double gam = nn * ur / (1.0 - nn * ur);
   const double znorm = sqrt(nd->cert_zeta_sq) * (1.0 + (nn + 2.0) * ur);
-  const double eps_a = 1.01 * gam * cmax * znorm;
+  double eps_a = 1.01 * gam * cmax * znorm;
+  double nce = nd->cert_negconj, margin_e = 0.0;
+  if (eig > 0.0) {
+    // The bound at b^ is ||y||^2 - ||X b^||^2 + eig ||b^||^2 - G*(2 X^T (y - X b^) + 2 eig b^).
+    // cert_negconj is ||y||^2 - ||u~||^2 (up to its margin) for u~ = y - zeta/2, and
+    // X^T zeta = 2 X^T (y - u~); the forward product u = X b^ (FP64, or error-free
+    // products with compensated sums) is within gamma_{p+1} ||x_i|| ||b^|| per row, so
+    // ||u~ - X b^|| <= delta = gamma_{p+1} ||X||_F ||b^|| + u ||zeta|| (the rounding of u - y):
+    //   | ||u~||^2 - ||X b^||^2 | <= delta (2 ||u~|| + delta),
+    //   per coordinate of the G* argument: eps_a + 2 ||x_j|| delta + its own rounding
+    const double pp = (double)p + 2.0;
+    const double gp = pp * ur / (1.0 - pp * ur);
+    const double bnorm = sqrt(bsq) * (1.0 + ((double)p + 4.0) * ur);
+    const double xfro = sqrt(xf2 * (1.0 + ((double)p + 4.0) * ur)) * (1.0 + 4.0 * ur);
+    const double ynorm = sqrt(y2 * (1.0 + ((double)d.n + 4.0) * ur)) * (1.0 + 4.0 * ur);
+    const double delta = (gp * xfro * bnorm + ur * znorm) * 1.01;
+    const double unorm = ynorm + 0.5 * znorm;
+    margin_e = delta * (2.0 * unorm + delta) + ((double)p + 4.0) * ur * eig * bsq * 1.01;
+    eps_a += 2.0 * cmax * delta + 2.0 * ur * (amax + 2.0 * eig * M) * 1.01;
+    nce += eig * bsq;
+  }
   const int kp = nd->kp;
   const int nsel = (kp < p ? kp : p) + n1;
   // H_M is M-Lipschitz and TopSum is 1-Lipschitz per selected entry; the factors
@@ -101,9 +148,9 @@ __global__ void __launch_bounds__(kProxBlock, 1) k_cert_final(Dev d, int want_z)
                                                sm, want_z ? d.z64 : nullptr);
   if (threadIdx.x == 0) {
     const double gst = 2.0 * l2 * gs;
-    double dual = nd->cert_negconj - nd->cert_margin_f - gst - margin_g;
-    dual -= 4.0 * ur * (fabs(nd->cert_negconj) + gst);
-    const double primal = nd->cert_f + 2.0 * l2 * go.g;
+    double dual = nce - nd->cert_margin_f - margin_e - gst - margin_g;
+    dual -= 4.0 * ur * (fabs(nce) + gst);
+    const double primal = nd->cert_f - eig * bsq + 2.0 * l2 * go.g;
     nd->cert_gstar = gst;
     nd->cert_margin_g = margin_g;
     nd->cert_g = go.g;

@@ -942,8 +942,26 @@ __device__ void dual_cta(const Dev& d, NodeDev* nd, SelSmem& sm, int q) {
     }
     next_guess = __float_as_uint(0.995f * __uint_as_float(R.thr)) & 0x7fffffffu;
   }
+  // eigen-perspective (App. D.2): the in-loop dual point -2 Q gamma adds eig ||gamma||^2
+  // to -F*(-zeta) (||y||^2 - ||X gamma||^2 + eig ||gamma||^2)
+  double gsq = 0.0;
+  const double eig = nd->eig;
+  if (eig > 0.0) {
+    const int t = nd->iter;
+    const double* bc = (const double*)d.beta + (size_t)(t % 3) * p;
+    const double* bp = (const double*)d.beta + (size_t)((t + 2) % 3) * p;
+    const double c = nd->c;
+    for (int j = threadIdx.x; j < p; j += kSelBlock) {
+      const double g = bc[j] + c * (bc[j] - bp[j]);
+      gsq += g * g;
+    }
+    int c0 = 0, c1 = 0;
+    double unused = 0.0;
+    block_reduce_cs(c0, gsq, c1, unused, sm);
+  }
   if (threadIdx.x == 0) {
     nd->gstar = s1 + s;
+    if (eig > 0.0) nd->negconj += eig * gsq;
     nd->dguess = next_guess;
     d.ccount[1] = 0;
   }
@@ -980,7 +998,7 @@ __global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
   const double shrink = rho / (1.0 + rho);
   const unsigned thr = nd->thr_kf;
   const int q = nd->q, bnd_i = nd->bnd_i;
-  double l1 = 0.0, s1 = 0.0;
+  double l1 = 0.0, s1 = 0.0, bsq = 0.0;
   bool nz = false;
   if (j < p) {
     const int8_t st = d.state ? d.state[j] : (int8_t)kFree;
@@ -993,6 +1011,7 @@ __global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
       if (!(mag > 0.0)) mag = 0.0;
       b = w < 0.0 ? -mag : mag;
       l1 = mag;
+      bsq = mag * mag;
     } else if (st == kZero) {
       b = 0.0;
     } else {   // z_j = 1: argmin 1/2 (b - w)^2 + b^2/(2 rho) on the box
@@ -1017,10 +1036,13 @@ __global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
   if (nz) d.nnz_idx[seg * kSegLen + base + __popc(bal & ((1u << lane) - 1u))] = j;
   l1 = block_sum<double, kSegLen>(l1, red);
   s1 = block_sum<double, kSegLen>(s1, red);
+  const bool eig = nd->eig > 0.0;   // eigen-perspective: ||b^{t+1}||^2 for the objective
+  if (eig) bsq = block_sum<double, kSegLen>(bsq, red);
   if (threadIdx.x == 0) {
     d.seg_cnt[seg] = tot;
     d.segpart[seg] = l1;
     d.segpart[d.nseg + seg] = s1;
+    if (eig) d.segpart[2 * d.nseg + seg] = bsq;
   }
   __threadfence();
   __syncthreads();
@@ -1040,13 +1062,15 @@ __global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
     if (i < d.nseg) d.seg_off[i] = running + ex;
     running += t2;
   }
-  double L1 = 0.0, S1 = 0.0;
+  double L1 = 0.0, S1 = 0.0, BQ = 0.0;
   for (int i = threadIdx.x; i < d.nseg; i += kSegLen) {
     L1 += __ldcg(&d.segpart[i]);
     S1 += __ldcg(&d.segpart[d.nseg + i]);
+    if (eig) BQ += __ldcg(&d.segpart[2 * d.nseg + i]);
   }
   L1 = block_sum<double, kSegLen>(L1, red);
   S1 = block_sum<double, kSegLen>(S1, red);
+  if (eig) BQ = block_sum<double, kSegLen>(BQ, red);
   if (threadIdx.x == 0) {
     d.seg_off[d.nseg] = running;
     nd->nnz = running;
@@ -1075,6 +1099,7 @@ __global__ void __launch_bounds__(kSegLen) k_prox_apply(Dev d) {
       }
     }
     nd->g_next = 0.5 * S1 + g;
+    nd->bsq_next = BQ + S1;
     d.cnt[ci] = 0;
   }
 }

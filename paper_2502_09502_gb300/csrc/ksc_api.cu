@@ -122,7 +122,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.blo, p * 4);
   ALLOC(d.seg_cnt, (size_t)d.nseg * 4);
   ALLOC(d.seg_off, (size_t)(d.nseg + 1) * 4);
-  ALLOC(d.segpart, (size_t)2 * d.nseg * 8);
+  ALLOC(d.segpart, (size_t)3 * d.nseg * 8);
   ALLOC(d.tbeta, (size_t)kProxCap * 8);
   ALLOC(d.cand_a, (size_t)kProxCap * 8);
   ALLOC(d.cand_i, (size_t)kProxCap * 4);
@@ -524,8 +524,12 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
                                      void* cuda_stream) {
   if (!pr) return fail(KSC_ERR_INVALID_ARG, "problem is NULL");
   if (!res) return fail(KSC_ERR_INVALID_ARG, "result is NULL");
-  if (node && (node->flags & KSC_FLAG_EIG))
-    return fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on the batched path (ksc_solve_batch)");
+  if (node && (node->flags & KSC_FLAG_EIG) && pr->loss == KSC_LOSS_LSQ && !pr->eig_ready) {
+    // the certified shift, computed on first use
+    double lam = 0.0;
+    ksc_status se = ksc_problem_eig_lambda(pr, cuda_stream, &lam);
+    if (se != KSC_OK) return se;
+  }
   NodeSetup ns;
   ksc_status st = check_node(pr, node, &ns);
   if (st != KSC_OK) return st;
@@ -568,11 +572,16 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   KSC_CUDA(cudaMemcpyAsync((char*)d.beta + p * tb, wb.data(), p * tb, cudaMemcpyHostToDevice, s));
   NodeDev h;
   std::memset(&h, 0, sizeof h);
-  h.lambda2 = node->lambda2;
+  // eigen-perspective (App. D.2): lambda2 + eig on the perspective term, the smooth
+  // part's constant 2 (lambda_max - eig) <= L - 2 eig
+  const double eig = (node->flags & KSC_FLAG_EIG) ? pr->eig_lambda : 0.0;
+  const double Ln = Lnode - 2.0 * eig;
+  h.eig = eig;
+  h.lambda2 = node->lambda2 + eig;
   h.M = node->M;
-  h.L = Lnode;
-  h.invL = 1.0 / Lnode;
-  h.rho = Lnode / (2.0 * node->lambda2);
+  h.L = Ln;
+  h.invL = 1.0 / Ln;
+  h.rho = Ln / (2.0 * h.lambda2);
   h.tol_loop = node->rel_gap_tol;
   h.incumbent = node->incumbent;
   h.kp = ns.kp;

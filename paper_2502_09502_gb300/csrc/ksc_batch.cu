@@ -1010,8 +1010,6 @@ extern "C" ksc_status ksc_solve_batch(ksc_problem* pr, const ksc_node* nodes, in
     }
     const bool eig_fp8 = (nodes[i].flags & KSC_FLAG_EIG) && pr->xdt == kXFP8;
     if (batch_supported(pr) && !eig_fp8 && std::min<int64_t>(setups[i].kp, pr->p) < kBatchCap) batch.push_back(i);
-    else if (nodes[i].flags & KSC_FLAG_EIG)
-      return api_fail(KSC_ERR_UNIMPLEMENTED, "the eigen-perspective relaxation runs on the batched path (BF16 X, k' < 2048)");
     else single.push_back(i);
   }
   // nodes with more free support entries run longer: grouping them in the same

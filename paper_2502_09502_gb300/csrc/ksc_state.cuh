@@ -54,6 +54,10 @@ struct NodeDev {
   int bnd_i;         // its index (ties broken by ascending index)
   int pad1;
   double l1, s1sq;   // sum |b_F| and sum_{S1} b^2 of the newest iterate
+  // eigen-perspective relaxation (App. D.2; 0: the perspective relaxation): lambda2
+  // above is then lambda2 + eig, rho and invL those of L - 2 eig
+  double eig;
+  double bsq_next;   // ||beta^{t+1}||^2 (eig > 0 only)
   // warm-started candidate selection: float-bit key thresholds predicted from the
   // previous step (0 = take every coordinate, i.e. no prediction yet)
   unsigned cguess;   // prox: keys >= cguess are appended by the gradient epilogue

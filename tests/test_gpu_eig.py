@@ -99,15 +99,55 @@ def test_eig_batched_matches_oracle(K):
     assert sum(r.dual_bound - q.dual_bound for r, q in zip(res, plain)) > 0
 
 
-def test_eig_needs_least_squares_and_the_batched_path(K):
+def test_eig_needs_least_squares(K):
     P1 = G.make_problem(300, 60, r=0.5, seed=4, loss=G.LOGISTIC, x_dtype=G.BF16)
     prob = K.Problem(P1.X, P1.y, K.KSC_LOSS_LOGISTIC)
     with pytest.raises(K.KscError):
         prob.solve_batch([K.Node(0.1, 2.0, 5, flags=K.KSC_FLAG_EIG)])
-    P2 = G.make_problem(300, 60, r=0.5, seed=5, x_dtype=G.BF16)
-    prob2 = K.Problem(P2.X, P2.y, K.KSC_LOSS_LSQ)
     with pytest.raises(K.KscError):
-        prob2.solve(K.Node(0.1, 2.0, 5, flags=K.KSC_FLAG_EIG))
+        prob.solve(K.Node(0.1, 2.0, 5, flags=K.KSC_FLAG_EIG))
+
+
+@pytest.mark.parametrize("dt", [G.F64, G.F32, G.BF16, "fp8"])
+def test_eig_single_node_matches_oracle(K, dt):
+    # the single-node path with the eigen-perspective relaxation (App. D.2): the
+    # shifted gradient in the gradient pass, -eig ||b||^2 in the objective, eig
+    # ||gamma||^2 in the in-loop dual term and the eigen bound with its margins in
+    # the FP64 certificate -- against the oracle on the stored (represented) matrix
+    P1 = G.make_problem(500, 100, r=0.5, seed=37, loss=G.LSQ, k_true=5, x_dtype=G.F32 if dt == "fp8" else dt,
+                        lambda2=0.5, M=2.0, k=5)
+    if dt == "fp8":
+        bits, sc = G.quantize_fp8(P1.X)
+        X = G.fp8_values(bits).astype(np.float64) * sc.astype(np.float64)
+        prob = K.Problem(bits, P1.y, K.KSC_LOSS_LSQ, x_dtype=K.KSC_FP8, col_scale=sc)
+    else:
+        X = P1.X64() if dt == G.BF16 else np.asarray(P1.X, dtype=np.float64)
+        prob = K.Problem(P1.X, P1.y, K.KSC_LOSS_LSQ)
+    lam = float(0.999 * O.lambda_min(X))
+    assert lam > 0
+    prob.set_eig_lambda(lam)
+    zero, one = np.array([3, 17, 40], np.int32), np.array([8], np.int32)
+    st = _state(P1.p, zero, one)
+    node = K.Node(P1.lambda2, P1.M, P1.k, fixed_zero=zero, fixed_one=one, rel_gap_tol=1e-8, max_iter=50000,
+                  flags=K.KSC_FLAG_EIG)
+    r = prob.solve(node)
+    ref = O.solve(X, P1.y, 0, P1.lambda2, P1.M, P1.k, state=st, tol=1e-12, max_iter=200000, eig=lam)
+    assert r.status == "ok" and r.rel_gap <= 1e-8
+    assert ref.status == "converged"
+    assert _rel(r.dual_bound, ref.dual) <= 1e-6 and _rel(r.primal, ref.primal) <= 1e-6
+    assert r.dual_bound <= ref.primal
+    assert np.all(r.beta[zero] == 0) and np.all(r.z[zero] == 0) and np.all(r.z[one] == 1)
+    # the oracle's eigen bound at the GPU's iterate agrees with the certificate, which
+    # stays below it (its margins)
+    d_o = O.dual_bound(X, P1.y, 0, P1.lambda2, P1.M, P1.k, r.beta, state=st, eig=lam)
+    assert r.dual_bound <= d_o + 1e-12 * abs(d_o) and _rel(r.dual_bound, d_o) <= 1e-8
+    # tighter than the perspective bound of the same node
+    plain = prob.solve(K.Node(P1.lambda2, P1.M, P1.k, fixed_zero=zero, fixed_one=one, rel_gap_tol=1e-8,
+                              max_iter=50000))
+    assert r.dual_bound > plain.dual_bound
+    if dt == G.BF16:   # the batched path on the same node agrees
+        rb = prob.solve_batch([node])[0]
+        assert _rel(rb.dual_bound, r.dual_bound) <= 1e-6 and _rel(rb.primal, r.primal) <= 1e-6
 
 
 def test_bnb_with_eig_node_bounds(K):
