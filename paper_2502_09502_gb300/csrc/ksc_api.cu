@@ -81,6 +81,8 @@ static void free_problem(ksc_problem* pr) {
   cudaSetDevice(pr->device);
   if (pr->graph) cudaGraphExecDestroy(pr->graph);
   if (pr->graph_prof) cudaGraphExecDestroy(pr->graph_prof);
+  if (pr->graph_eig) cudaGraphExecDestroy(pr->graph_eig);
+  if (pr->graph_eig_prof) cudaGraphExecDestroy(pr->graph_eig_prof);
   free_batch(pr->batch);
   for (auto e : pr->events) cudaEventDestroy(e);
   for (void* v : pr->allocs) cudaFree(v);
@@ -420,8 +422,12 @@ extern "C" ksc_status ksc_problem_kernel_time(ksc_problem* problem, int32_t kern
 
 // ------------------------------------------------------------------ solve
 
-static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof) {
-  cudaGraphExec_t* slot = prof ? &pr->graph_prof : &pr->graph;
+static cudaGraphExec_t* graph_slot(ksc_problem* pr, bool prof, bool eig) {
+  return eig ? (prof ? &pr->graph_eig_prof : &pr->graph_eig) : (prof ? &pr->graph_prof : &pr->graph);
+}
+
+static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof, bool eig) {
+  cudaGraphExec_t* slot = graph_slot(pr, prof, eig);
   if (*slot) return KSC_OK;
   if (prof && pr->events.empty()) {
     pr->events.resize(kEventsPerStep * kStepsPerGraph);
@@ -433,7 +439,7 @@ static ksc_status build_graph(ksc_problem* pr, cudaStream_t s, bool prof) {
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    for (int k = 0; k < kStepsPerGraph; ++k) launch_step(pr->dev, cs, prof ? &pr->events[kEventsPerStep * k] : nullptr);
+    for (int k = 0; k < kStepsPerGraph; ++k) launch_step(pr->dev, cs, prof ? &pr->events[kEventsPerStep * k] : nullptr, eig);
     e = cudaStreamEndCapture(cs, &g);
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(slot, g, 0);
@@ -493,7 +499,7 @@ ksc_status ksc::check_node(const ksc_problem* pr, const ksc_node* node, NodeSetu
 
 static ksc_status replay(ksc_problem* pr, cudaStream_t s, NodeDev* h) {
   const bool prof = pr->profile;
-  cudaGraphExec_t g = prof ? pr->graph_prof : pr->graph;
+  cudaGraphExec_t g = *graph_slot(pr, prof, h->eig > 0.0);
   const int before = h->iter;
   KSC_CUDA(cudaGraphLaunch(g, s));
   pr->launches += (int64_t)kLaunchesPerStep * kStepsPerGraph;
@@ -597,7 +603,7 @@ extern "C" ksc_status ksc_solve_node(ksc_problem* pr, const ksc_node* node, ksc_
   launch_init(d, s);
   pr->launches += kLaunchesPerInit;
   KSC_CUDA(cudaGetLastError());
-  if ((st = build_graph(pr, s, pr->profile)) != KSC_OK) return st;
+  if ((st = build_graph(pr, s, pr->profile, h.eig > 0.0)) != KSC_OK) return st;
   KSC_CUDA(cudaMemcpyAsync(&h, d.nd, sizeof h, cudaMemcpyDeviceToHost, s));
   KSC_CUDA(cudaStreamSynchronize(s));
 

@@ -116,7 +116,7 @@ __host__ __device__ inline size_t ws_elems(const Dev& d) {
 // one FISTA step: gradient pass (+ prox input and keys), prox select and apply
 // (+ g, dual TopSum), forward pass + step logic.  ev (optional): 4 events around
 // the gradient pass, the prox kernels and the forward pass.
-void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev);
+void launch_step(const Dev& d, cudaStream_t s, cudaEvent_t* ev, bool eig);   // eig: the eigen-perspective step
 // g(beta^1), u^1 = X beta^1 and the objective L^1 (the start of Algorithm 3)
 void launch_init(const Dev& d, cudaStream_t s);
 // FP64 certificate at the current iterate (projection onto dom g, u, zeta,

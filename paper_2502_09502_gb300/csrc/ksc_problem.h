@@ -38,6 +38,8 @@ struct ksc_problem {
   std::vector<void*> allocs;
   cudaGraphExec_t graph = nullptr;
   cudaGraphExec_t graph_prof = nullptr;
+  cudaGraphExec_t graph_eig = nullptr;        // the eigen-perspective step
+  cudaGraphExec_t graph_eig_prof = nullptr;
   bool profile = false;
   std::vector<cudaEvent_t> events;   // 4 per step of the profiling graph
   int64_t k_launches[kKernelIds] = {};
