@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
   __shared__ int s_last;
   const int ct = blockIdx.x, rb = blockIdx.y;
   const int n = d.n, p = d.p;
-  const int r0 = rb * kGradRows;
-  const int rn = min(kGradRows, n - r0);
+  const int r0 = rb * d.grow;
+  const int rn = min(d.grow, n - r0);
 
   // prologue: residual of the rows of this CTA
   double nc = 0.0;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
 
 template <typename TX, bool VEC>
 __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ A, int64_t lda, int rows,
-                                                         int cols, const double* __restrict__ vec,
+                                                         int cols, int rpc, const double* __restrict__ vec,
                                                          double* __restrict__ out, double* __restrict__ ws,
                                                          int* __restrict__ cnt, const float* __restrict__ sin,
                                                          const float* __restrict__ sout) {
@@ -714,8 +714,8 @@ __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ 
   __shared__ float rl[kGradRows];
   __shared__ int s_last;
   const int ct = blockIdx.x, rb = blockIdx.y;
-  const int r0 = rb * kGradRows;
-  const int rn = min(kGradRows, rows - r0);
+  const int r0 = rb * rpc;
+  const int rn = min(rpc, rows - r0);
   for (int i = threadIdx.x; i < rn; i += kGradThreads) {
     // sin / sout: FP8 column scales (powers of two: exact) on the input rows or the outputs
     const double r = sin ? vec[r0 + i] * (double)sin[r0 + i] : vec[r0 + i];
@@ -779,15 +779,28 @@ __global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ 
   if (threadIdx.x == 0) cnt[ct] = 0;
 }
 
+// CTAs of kGradThreads threads of `kernel` resident on the whole device at once
+template <typename K>
+static int resident_slots(K kernel) {
+  int dev = 0, sms = 1, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kGradThreads, 0);
+  return (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+}
+
 template <typename TX>
 static void colsum_launch(const TX* A, int64_t lda, int rows, int cols, const double* vec, double* out,
                           double* ws, int* cnt, cudaStream_t s, const float* sin = nullptr,
                           const float* sout = nullptr) {
   const int tile = kGradThreads * Vec<TX>::N;
-  dim3 grid((cols + tile - 1) / tile, (rows + kGradRows - 1) / kGradRows);
+  const int strips = (cols + tile - 1) / tile;
+  static const int slots = resident_slots(k_colsum<TX, true>);
+  const int rpc = balanced_rows(rows, strips, slots);
+  dim3 grid(strips, (rows + rpc - 1) / rpc);
   const bool vec_ok = (lda % Vec<TX>::N) == 0 && ((uintptr_t)A % 16) == 0;
-  if (vec_ok) k_colsum<TX, true><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt, sin, sout);
-  else k_colsum<TX, false><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, vec, out, ws, cnt, sin, sout);
+  if (vec_ok) k_colsum<TX, true><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, rpc, vec, out, ws, cnt, sin, sout);
+  else k_colsum<TX, false><<<grid, kGradThreads, 0, s>>>(A, lda, rows, cols, rpc, vec, out, ws, cnt, sin, sout);
 }
 
 // ----------------------------------------------------------- column-major copy
@@ -810,6 +823,18 @@ __global__ void __launch_bounds__(256) k_transpose(const TX* __restrict__ X, int
 }
 
 // ----------------------------------------------------------- launchers
+
+template <typename TX>
+static int grad_rows_t(const Dev& d) {
+  static const int slots = resident_slots(k_grad<TX, double, kGStep, true>);
+  return balanced_rows(d.n, grad_ncol(d), slots);
+}
+int grad_rows(const Dev& d) {
+  if (d.xdt == kXF64) return grad_rows_t<double>(d);
+  if (d.xdt == kXF32) return grad_rows_t<float>(d);
+  if (d.xdt == kXFP8) return grad_rows_t<__nv_fp8_e4m3>(d);
+  return grad_rows_t<__nv_bfloat16>(d);
+}
 
 template <typename TX, typename T>
 struct Launch {

@@ -104,7 +104,7 @@ static ksc_status alloc_workspace(ksc_problem* pr) {
   ALLOC(d.nnz_idx, p * sizeof(int));
   ALLOC(d.ws, ws_elems(d) * 8);
   ALLOC(d.cnt, (size_t)cnt_total(d) * sizeof(int));
-  ALLOC(d.ncpart, (size_t)grad_nrb(d) * 8);
+  ALLOC(d.ncpart, (size_t)grad_nrb_max(d) * 8);
   ALLOC(d.fpart, (size_t)fwd_ntiles(d) * 4 * 8);
   ALLOC(d.u64, n * 8);
   ALLOC(d.zeta, n * 8);
@@ -340,6 +340,7 @@ extern "C" ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cud
   }
   const int cpt = cols_per_thread(pr->xdt);
   d.vec = ((ldx % cpt) == 0 && ((uintptr_t)pr->X % 16) == 0) ? 1 : 0;
+  d.grow = grad_rows(d);
   if ((st = dmalloc(pr, &pr->y, pr->n * 8)) != KSC_OK) return bail(st);
   {
     cudaError_t e = cudaMemcpyAsync(pr->y, desc->y, pr->n * 8, cudaMemcpyHostToDevice, s);

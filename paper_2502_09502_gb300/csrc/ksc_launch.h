@@ -14,7 +14,8 @@ enum XDtype : int { kXF64 = 0, kXF32 = 1, kXBF16 = 2, kXFP8 = 3 };
 
 // Tile shapes (kept in one place: the host sizes workspaces with them).
 constexpr int kGradThreads = 256;   // gradient pass: threads per CTA
-constexpr int kGradRows = 256;      // gradient pass: rows per CTA (split-n)
+constexpr int kGradRows = 256;      // gradient pass: most rows per CTA (split-n)
+constexpr int kGradRowsMin = 128;   // gradient pass: fewest rows per CTA the balancing picks
 constexpr int kFwdThreads = 256;    // forward pass: 8 warps
 constexpr int kFwdRows = 32;        // forward pass: 4 rows per warp
 constexpr int kFwdChunk = 2048;     // forward pass: staged columns of beta
@@ -36,6 +37,7 @@ struct Dev {
   const void* Xc;          // column-major copy of X (ldc >= n), for the sparse forward pass
   int64_t ldc;
   int n, p;
+  int grow;                // gradient pass: rows per CTA (kGradRowsMin..kGradRows, grad_rows())
   int vec;                 // rows are 16-byte aligned: vector loads
   int loss;
   const double* y;         // n
@@ -88,7 +90,24 @@ __host__ __device__ inline int grad_ncol(const Dev& d) {
   const int tile = kGradThreads * cols_per_thread(d.xdt);
   return (d.p + tile - 1) / tile;
 }
-__host__ __device__ inline int grad_nrb(const Dev& d) { return (d.n + kGradRows - 1) / kGradRows; }
+__host__ __device__ inline int grad_nrb(const Dev& d) { return (d.n + d.grow - 1) / d.grow; }
+__host__ __device__ inline int grad_nrb_max(const Dev& d) { return (d.n + kGradRowsMin - 1) / kGradRowsMin; }
+// Rows per CTA of a streaming pass over `rows` x (strips column strips) whose CTAs
+// all do equal work: `slots` CTAs run at once (SMs x CTAs per SM), so the pass
+// takes whole waves of them; the choice in [kGradRowsMin, kGradRows] (a multiple
+// of 4, the main loop's row step) minimises waves x rows per CTA, the larger on ties.
+inline int balanced_rows(int rows, int strips, int slots) {
+  int best = kGradRows;
+  double best_cost = 1e300;
+  for (int r = kGradRows; r >= kGradRowsMin; r -= 4) {
+    const long long ctas = (long long)((rows + r - 1) / r) * strips;
+    const long long waves = (ctas + slots - 1) / slots;
+    const double cost = (double)waves * r;
+    if (cost < best_cost * (1.0 - 1e-12)) { best_cost = cost; best = r; }
+  }
+  return best;
+}
+int grad_rows(const Dev& d);   // balanced_rows for the gradient pass of this problem
 __host__ __device__ inline int fwd_ntiles(const Dev& d) { return (d.n + kFwdRows - 1) / kFwdRows; }
 __host__ __device__ inline int sp_nrb(const Dev& d) { return (d.n + kSpRows - 1) / kSpRows; }
 size_t prox_smem_bytes(const Dev& d);
@@ -108,8 +127,8 @@ __host__ __device__ inline int colsum_strips(const Dev& d) {
 __host__ __device__ inline int cnt_total(const Dev& d) { return grad_ncol(d) + 8 + colsum_strips(d) + 1; }
 // gradient-partials workspace (doubles): max of the two streaming shapes
 __host__ __device__ inline size_t ws_elems(const Dev& d) {
-  const size_t a = (size_t)((d.n + kGradRows - 1) / kGradRows) * d.p;
-  const size_t b = (size_t)((d.p + kGradRows - 1) / kGradRows) * d.n;
+  const size_t a = (size_t)((d.n + kGradRowsMin - 1) / kGradRowsMin) * d.p;
+  const size_t b = (size_t)((d.p + kGradRowsMin - 1) / kGradRowsMin) * d.n;
   return a > b ? a : b;
 }
 
