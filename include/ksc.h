@@ -109,8 +109,10 @@ typedef struct {
   double lipschitz;     /* > 0: the step constant L of Algorithm 3 to use.
                            <= 0: L = c_f * theta * 1.01, c_f = 2 (least squares,
                            squared hinge) or 1/4 (logistic), theta the largest Ritz
-                           value of Lanczos on X^T X, stopped when 8 further steps
-                           move it by at most 1e-5 of itself.  theta is a lower
+                           value of Lanczos on X^T X, checked every 8 steps and
+                           stopped when the geometric extrapolation of its remaining
+                           rise from the last three checks (Aitken) is at most 1e-3
+                           of it, or a check moves it by at most 1e-5.  theta is a lower
                            estimate of lambda_max, so L is an estimate, not a proven
                            upper bound; L only changes the iteration's path, every
                            reported bound is valid for any L.  Poisson and Gamma:

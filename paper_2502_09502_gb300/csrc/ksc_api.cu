@@ -199,7 +199,7 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
   KSC_CUDA(cudaGetLastError());
   std::vector<double> hlz(2 * kLanczosMax);
   const int maxit = (int)std::min<int64_t>(kLanczosMax, pr->p);
-  double theta = 0.0, prev = -1.0;
+  double theta = 0.0, prev = -1.0, prev2 = -1.0;
   int it = 0;
   while (it < maxit) {
     const int upto = std::min(maxit, it + 8);
@@ -215,10 +215,25 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     }
     theta = tridiag_max_eig(hlz.data(), hlz.data() + kLanczosMax, m);
     pr->power_iters = m;
-    // the Ritz value rises monotonically to lambda_max and L keeps a 1% margin: stop
-    // once 8 more steps move it by at most 1e-5 of itself (its remaining error is then
-    // far below the margin: ~4e-8 on the 8000 x 20000 profiler instance)
-    if (breakdown || (prev > 0 && std::fabs(theta - prev) <= 1e-5 * theta)) break;
+    // the Ritz value rises monotonically to lambda_max and L keeps a 1% margin.  With
+    // the rises d1, d2 over the last two 8-step blocks shrinking (q = d2/d1 < 1), the
+    // geometric tail d2 q / (1 - q) estimates what is left (Aitken); stop once that is
+    // at most 1e-3 of theta, or a block moves it by at most 1e-5 of itself.  On the
+    // 20000 x 50000 Toeplitz(0.9) instance this stops after 32 steps, 3e-4 below
+    // lambda_max (64 steps under an 8-step rise of 1e-5)
+    if (breakdown) break;
+    if (prev > 0) {
+      const double d2 = theta - prev;
+      if (std::fabs(d2) <= 1e-5 * theta) break;
+      if (prev2 > 0) {
+        const double d1 = prev - prev2;
+        if (d1 > 0 && d2 >= 0 && d2 < d1) {
+          const double q = d2 / d1;
+          if (d2 * q / (1.0 - q) <= 1e-3 * theta) break;
+        }
+      }
+    }
+    prev2 = prev;
     prev = theta;
   }
   // F' is 2-Lipschitz for least squares and the squared hinge, 1/4 for logistic;

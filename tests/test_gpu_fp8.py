@@ -50,7 +50,8 @@ def test_fp8_single_node_matches_oracle(K, loss, n, p, seed):
     # the problem's Lipschitz constant is that of X~
     lam, _ = O.power_iteration(Xt, tol=1e-13)
     c = 2.0 if loss == G.LSQ else 0.25
-    assert abs(prob.L - c * lam * 1.01) <= 1e-4 * prob.L
+    theta = prob.L / (c * 1.01)   # the Lanczos Ritz value: within ~1e-3 below lambda_max
+    assert lam * (1 - 2e-3) <= theta <= lam * (1 + 1e-9)
 
 
 def test_fp8_node_with_fixed_sets_and_device_matrix(K):
