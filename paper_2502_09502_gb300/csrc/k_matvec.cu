@@ -99,8 +99,15 @@ enum FwdMode : int { kFStep = 0, kFRaw = 1, kFInit = 2, kFCert = 3 };
 
 // ----------------------------------------------------------- gradient pass
 
+// CTAs per SM the FP32 FISTA step (vector loads) is compiled for: 40 registers (no
+// spills) give 6 resident CTAs instead of 5, and more loads of X in flight
+template <typename TX, int MODE, bool VEC>
+constexpr int grad_min_blocks() {
+  return (VEC && std::is_same<TX, float>::value && (MODE == kGStep || MODE == kGStepEig)) ? 6 : 1;
+}
+
 template <typename TX, typename T, int MODE, bool VEC>
-__global__ void __launch_bounds__(kGradThreads) k_grad(Dev d) {
+__global__ void __launch_bounds__(kGradThreads, grad_min_blocks<TX, MODE, VEC>()) k_grad(Dev d) {
   // FP64 X, the certificate and the column norms accumulate in double; FP32/BF16 X
   // in double-float (error-free products, compensated sums)
   constexpr bool FP64ACC = (MODE == kGCert || MODE == kGColsq || std::is_same<TX, double>::value);
@@ -702,7 +709,7 @@ __global__ void __launch_bounds__(kSpRows) k_fwd_col(Dev d) {
 // and with A = Xc (the column-major copy, p x n) for X v.
 
 template <typename TX, bool VEC>
-__global__ void __launch_bounds__(kGradThreads) k_colsum(const TX* __restrict__ A, int64_t lda, int rows,
+__global__ void __launch_bounds__(kGradThreads, std::is_same<TX, float>::value ? 6 : 1) k_colsum(const TX* __restrict__ A, int64_t lda, int rows,
                                                          int cols, int rpc, const double* __restrict__ vec,
                                                          double* __restrict__ out, double* __restrict__ ws,
                                                          int* __restrict__ cnt, const float* __restrict__ sin,
