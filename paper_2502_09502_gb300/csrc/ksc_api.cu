@@ -215,24 +215,7 @@ static ksc_status lanczos_lmax(ksc_problem* pr, cudaStream_t s) {
     }
     theta = tridiag_max_eig(hlz.data(), hlz.data() + kLanczosMax, m);
     pr->power_iters = m;
-    // the Ritz value rises monotonically to lambda_max and L keeps a 1% margin.  With
-    // the rises d1, d2 over the last two 8-step blocks shrinking (q = d2/d1 < 1), the
-    // geometric tail d2 q / (1 - q) estimates what is left (Aitken); stop once that is
-    // at most 1e-3 of theta, or a block moves it by at most 1e-5 of itself.  On the
-    // 20000 x 50000 Toeplitz(0.9) instance this stops after 32 steps, 3e-4 below
-    // lambda_max (64 steps under an 8-step rise of 1e-5)
-    if (breakdown) break;
-    if (prev > 0) {
-      const double d2 = theta - prev;
-      if (std::fabs(d2) <= 1e-5 * theta) break;
-      if (prev2 > 0) {
-        const double d1 = prev - prev2;
-        if (d1 > 0 && d2 >= 0 && d2 < d1) {
-          const double q = d2 / d1;
-          if (d2 * q / (1.0 - q) <= 1e-3 * theta) break;
-        }
-      }
-    }
+    if (breakdown || lanczos_stop(theta, prev, prev2)) break;
     prev2 = prev;
     prev = theta;
   }
