@@ -1173,7 +1173,7 @@ def cpu_baseline(P, iters, pows, samples=5):
 # iteration counts of a full solve of this workload (matrix-vector pairs for L, FISTA
 # steps), as the GPU solve reports them; they extrapolate the oracle's bounded sample
 # when it runs on its own
-FULL_SOLVE_COUNTS = {"pow": 64, "iters": 350}
+FULL_SOLVE_COUNTS = {"pow": 32, "iters": 344}
 
 
 def run_reference(args):
