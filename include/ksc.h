@@ -137,7 +137,8 @@ ksc_status ksc_problem_create(const ksc_problem_desc* desc, void* cuda_stream,
 ksc_status ksc_problem_destroy(ksc_problem* problem);
 /* Device bytes the problem holds now (X copy if owned, y, workspaces). */
 size_t ksc_problem_bytes(const ksc_problem* problem);
-/* L (Algorithm 3's step constant) and the number of power iterations used. */
+/* L (Algorithm 3's step constant) and the number of Lanczos steps taken for it
+ * (power_iters; 0 when the caller gave L in ksc_problem_desc.lipschitz). */
 ksc_status ksc_problem_info(const ksc_problem* problem, double* lipschitz,
                             int32_t* power_iters);
 
